@@ -1,0 +1,165 @@
+"""Seeded synthetic inputs for the fine-mesh correction step.
+
+This module is the only code that both the CUDA path's callers (tests, bench, smoke) and the CPU oracle use.
+It holds none of the method's arithmetic: box meshes made of cubes, sampled molecules, occupation numbers and
+closed-form trial functions evaluated at points that the caller supplies.
+
+Workload shapes follow the paper's experiments (Sec. 4): all-electron molecules with nuclear charges of H..O in
+boxes of half-width 6..15 bohr, N = 1..64 doubly occupied orbitals, meshes of tetrahedra obtained by uniform
+refinement of a cube mesh (the paper's coarsest mesh is such a mesh with 24,576 tetrahedra).
+"""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+
+# Kuhn (Freudenthal) split of a cube: one tetrahedron per permutation of the axes, walking from the
+# corner (0,0,0) to (1,1,1) one unit step per axis.  The six are nested under 2x refinement.
+_PERMS = list(itertools.permutations((0, 1, 2)))
+_PERM_SIGN = [1, -1, -1, 1, 1, -1]
+
+
+def cube_mesh(n: int, half: float):
+    """Kuhn triangulation of [-half, half]^3 into n^3 cubes x 6 positively oriented tetrahedra.
+
+    Returns (coords [(n+1)^3, 3] float64, tets [6 n^3, 4] int32).  Vertex (i,j,k) has index
+    i + (n+1) (j + (n+1) k); tetrahedron 6 c + p belongs to cube c = i + n (j + n k) and permutation p.
+    """
+    h = 2.0 * half / n
+    g = np.arange(n + 1)
+    k, j, i = np.meshgrid(g, g, g, indexing="ij")
+    coords = np.stack([-half + i.ravel() * h, -half + j.ravel() * h, -half + k.ravel() * h], axis=1)
+
+    def vid(ii, jj, kk):
+        return ii + (n + 1) * (jj + (n + 1) * kk)
+
+    c = np.arange(n ** 3)
+    ci, cj, ck = c % n, (c // n) % n, c // (n * n)
+    tets = np.empty((n ** 3, 6, 4), dtype=np.int64)
+    for p, perm in enumerate(_PERMS):
+        pos = [ci.copy(), cj.copy(), ck.copy()]
+        path = [vid(*pos)]
+        for ax in perm:
+            pos[ax] = pos[ax] + 1
+            path.append(vid(*pos))
+        if _PERM_SIGN[p] < 0:  # swap the last two vertices to make the orientation positive
+            path[2], path[3] = path[3], path[2]
+        tets[:, p, :] = np.stack(path, axis=1)
+    return coords, tets.reshape(-1, 4).astype(np.int32)
+
+
+def nested_cube_meshes(n_coarse: int, levels: int, half: float):
+    """Coarse and fine Kuhn meshes of the same box, the fine one `levels` uniform 2x refinements deeper.
+
+    Returns (coarse_coords, coarse_tets, fine_coords, fine_tets, fine_parent) with fine_parent[e] the
+    coarse tetrahedron that contains fine tetrahedron e.
+    """
+    cc, ct = cube_mesh(n_coarse, half)
+    r = 2 ** levels
+    nf = n_coarse * r
+    fc, ft = cube_mesh(nf, half)
+    e = np.arange(ft.shape[0])
+    cube = e // 6
+    fi, fj, fk = cube % nf, (cube // nf) % nf, cube // (nf * nf)
+    coarse_cube = (fi // r) + n_coarse * ((fj // r) + n_coarse * (fk // r))
+    # centroid of the fine tetrahedron in the unit cube of its coarse cube
+    hc = 2.0 * half / n_coarse
+    cen = fc[ft].mean(axis=1)
+    ccorner = np.stack([-half + (fi // r) * hc, -half + (fj // r) * hc, -half + (fk // r) * hc], axis=1)
+    frac = (cen - ccorner) / hc
+    # the coarse Kuhn tetrahedron of permutation p is {x : x[p0] >= x[p1] >= x[p2]}
+    order = np.argsort(-frac, axis=1, kind="stable")
+    perm_index = {perm: p for p, perm in enumerate(_PERMS)}
+    pidx = np.array([perm_index[tuple(o)] for o in order.tolist()], dtype=np.int64)
+    parent = (6 * coarse_cube + pidx).astype(np.int32)
+    return cc, ct, fc, ft, parent
+
+
+def molecule(seed: int, n_nuclei: int, zmax: int = 8, half: float = 3.0, dmin: float = 1.5):
+    """Nuclei with charges uniform in {1..zmax}, positions uniform in [-half, half]^3 by sequential
+    rejection so that every pair is at least dmin bohr apart.  Returns (Z [M], R [M,3])."""
+    rng = np.random.default_rng(seed)
+    Z = rng.integers(1, zmax + 1, size=n_nuclei).astype(np.float64)
+    R = []
+    while len(R) < n_nuclei:
+        p = rng.uniform(-half, half, size=3)
+        if all(np.linalg.norm(p - q) >= dmin for q in R):
+            R.append(p)
+    return Z, np.array(R, dtype=np.float64).reshape(n_nuclei, 3)
+
+
+def occupations(Z) -> np.ndarray:
+    """Spin-unpolarised filling: N = ceil(sum Z / 2) orbitals, each holding 2 electrons except that the
+    last one holds the remainder (1 when the electron count is odd)."""
+    ne = int(round(float(np.sum(Z))))
+    n = (ne + 1) // 2
+    f = np.full(n, 2.0)
+    f[-1] = ne - 2 * (n - 1)
+    return f
+
+
+# Shells used for trial orbitals, in filling order: (principal n, angular polynomial selector)
+_SHELLS = [(1, "s"), (2, "s"), (2, "x"), (2, "y"), (2, "z"), (3, "s"), (3, "x"), (3, "y"), (3, "z")]
+
+
+def trial_orbitals(points, Z, R, n_orb: int, width: float = 1.25):
+    """Closed-form smooth trial orbitals (Gaussian-damped atomic-like shapes) evaluated at `points` [P,3].
+
+    Orbital k sits on nucleus k mod M (nuclei ordered by decreasing charge) with shell k // M of the list
+    above; the Gaussian width grows with the shell so that coarse meshes resolve the function.
+    Returns (values [P, n_orb], guess eigenvalues [n_orb]).  They stand in for the coarse-mesh eigenpairs
+    that the method takes as its starting point; they are not eigenfunctions of anything.
+    """
+    points = np.asarray(points, dtype=np.float64)
+    order = np.argsort(-np.asarray(Z), kind="stable")
+    M = len(Z)
+    vals = np.zeros((points.shape[0], n_orb))
+    lam = np.zeros(n_orb)
+    for k in range(n_orb):
+        m = order[k % M]
+        nsh, kind = _SHELLS[min(k // M, len(_SHELLS) - 1)]
+        w = width * (1.0 + 0.35 * (nsh - 1))
+        d = points - R[m]
+        r2 = np.sum(d * d, axis=1)
+        g = np.exp(-0.5 * r2 / (w * w))
+        if kind == "s":
+            poly = 1.0 - (nsh - 1) * 0.5 * r2 / (w * w)
+        else:
+            poly = d[:, "xyz".index(kind)] / w
+        vals[:, k] = poly * g
+        lam[k] = -0.5 * Z[m] / (nsh * nsh) - 0.05 * k
+    return vals, lam
+
+
+def hydrogen():
+    """One proton at the origin."""
+    return np.array([1.0]), np.zeros((1, 3))
+
+
+def lanczos_start(n: int, seed: int = 7) -> np.ndarray:
+    """Seeded start vector for an extreme-eigenvalue Lanczos estimate."""
+    return np.random.default_rng(seed).standard_normal(n)
+
+
+def workload(name: str):
+    """Named workloads of the paper's kind, with their sizes.
+
+    'h_p1'  : hydrogen, box [-10,10]^3, P1, coarse 4^3 cubes, fine 16^3 cubes (24,576 tetrahedra).
+    'mol4_p2': 4 nuclei (seed 2), box [-15,15]^3, P2, coarse 4^3 cubes, fine 32^3 cubes (196,608
+               tetrahedra, 250,047 free fine DOF), N = ceil(sum Z / 2) <= 16, LDA.
+    'mol4_p2_small': the same molecule on fine 8^3 cubes (parity-test size).
+    """
+    if name == "h_p1":
+        Z, R = hydrogen()
+        return dict(name=name, Z=Z, R=R, order=1, half=10.0, n_coarse=4, levels=2, xc="slater")
+    if name in ("mol4_p2", "mol4_p2_small", "mol4_p2_mid"):
+        Z, R = molecule(2, 4)
+        lv = {"mol4_p2": 3, "mol4_p2_mid": 2, "mol4_p2_small": 1}[name]
+        return dict(name=name, Z=Z, R=R, order=2, half=15.0, n_coarse=4, levels=lv, xc="lda")
+    raise KeyError(name)
+
+
+def n_orbitals(Z) -> int:
+    return int(math.ceil(float(np.sum(Z)) / 2.0))
