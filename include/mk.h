@@ -1,0 +1,213 @@
+/* mk — the fine-mesh correction step of the multilevel-correction adaptive finite element method for the
+ * Kohn-Sham equation (Hu, Xie, Xu, "On accelerating a multilevel correction adaptive finite element method for
+ * Kohn-Sham equation"), on one NVIDIA GB300 (sm_103a).
+ *
+ * One step, per occupied orbital i (Algorithm 1, steps 5-7, with the frozen potential V_Hxc(rho_H) on the
+ * right-hand side):
+ *   mk_prolongate         u_i = P psi_{H,i}                                   (V_H subset V_h, Sec. 2)
+ *   mk_hartree_poisson    (grad w, grad v) = 4 pi (rho_H, v)                   (Eq. (W_h_equation), Sec. 2)
+ *   mk_assemble_rhs       b_i(v) = (lambda_{H,i}+sigma)(u_i,v) - ((w+V_xc(rho_H)) u_i, v)
+ *   mk_correction_solve   (1/2)(grad x,grad v) + (V_ext x,v) + sigma (x,v) = b_i(v)   (Eq. (Aux_Linear_Problem))
+ *   mk_augmented_project  A_H, M_H, b_i, c_i, beta_i, gamma_i                   (Eqs. (Adef), (bdef), (betadef))
+ *   mk_small_eigensolve   Eq. (Eigenvalue_H_h), selection of Algorithm 2 (a)
+ *   mk_orbital_assemble   psi_i = P phi_{i,H} + theta_{2,i} psi^_i              (Algorithm 3, output)
+ *
+ * Conventions shared by every entry point
+ *   - Return value: MK_OK (0) or a negative MK_ERR_* code; mk_last_error() gives a message (thread-local).
+ *   - Device pointers are caller-owned (e.g. torch tensors).  Nothing is allocated per call except scratch held
+ *     by the mk_ctx, which grows on demand and is reused; calls on one ctx must not overlap on different streams.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = default stream).  Calls are asynchronous on it, except
+ *     where a report is filled: those synchronise the stream before returning.
+ *   - Fine-mesh vectors are node-major with orbitals contiguous: X[node * ld + i], node over ALL fine nodes
+ *     (boundary nodes included and held at 0 for orbitals), i < N <= ld.  Coarse vectors are over the coarse
+ *     FREE DOF (interior nodes, in increasing node order): Y[k * ldc + i].
+ *   - Node numbering (both levels): the mesh vertices first, then, for P2, one node per edge in order of first
+ *     appearance when tetrahedra are scanned in index order with local edges (01,02,03,12,13,23).
+ *   - All arithmetic that a report or an output depends on is FP64 unless mk_solve_opts.precision says MIXED.
+ */
+#ifndef MK_H
+#define MK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MK_OK 0
+#define MK_ERR_INVALID_ARG (-1)
+#define MK_ERR_CUDA (-2)
+#define MK_ERR_OOM (-3)
+#define MK_ERR_NOT_CONVERGED (-4) /* outputs still written, report filled */
+#define MK_ERR_BREAKDOWN (-5)     /* p^T A p <= 0 met: operator not positive definite (sigma too small) */
+#define MK_ERR_TIMEOUT (-6)       /* a bounded device-side wait gave up */
+#define MK_ERR_SINGULAR_AUG (-7)  /* per-orbital status: psi^ lies in V_H, coarse Ritz pair returned */
+#define MK_ERR_UNSUPPORTED (-8)
+
+#define MK_MAX_RHS 64
+
+typedef struct mk_ctx mk_ctx;
+typedef struct mk_mesh mk_mesh;
+
+/* A conforming tetrahedral mesh (Sec. 2, T_h).  Host arrays, read during mk_mesh_upload only.
+ * coords [n_vertices*3] (x,y,z), tets [n_elems*4] vertex indices with positive orientation (det J > 0). */
+typedef struct {
+  int order; /* 1 (P1) or 2 (P2); both levels of one mesh pair use the same order */
+  int64_t n_vertices;
+  const double* coords;
+  int64_t n_elems;
+  const int32_t* tets;
+} mk_mesh_desc;
+
+/* Nuclei of V_ext = -sum_k Z_k / |x - R_k| (Sec. 2).  Host arrays Z [n], R [n*3]. */
+typedef struct {
+  int n_nuclei;
+  const double* Z;
+  const double* R;
+} mk_molecule;
+
+/* Exchange-correlation (Sec. 4): Slater exchange V_x = -(3 rho/pi)^(1/3); X-alpha -(3/2) alpha (3 rho/pi)^(1/3);
+ * LDA = Slater + Perdew-Zunger correlation with the constants printed in Sec. 4. */
+enum { MK_XC_NONE = 0, MK_XC_SLATER = 1, MK_XC_XALPHA = 2, MK_XC_LDA_PZ = 3 };
+typedef struct {
+  int kind;
+  double alpha; /* X-alpha only */
+} mk_xc;
+
+enum { MK_PREC_FP64 = 0, MK_PREC_MIXED = 1 };
+enum { MK_PRECOND_JACOBI = 0, MK_PRECOND_CHEBYSHEV = 1, MK_PRECOND_LEARNED = 2 };
+enum { MK_BC_ZERO = 0, MK_BC_MULTIPOLE = 1 };
+
+typedef struct {
+  int precision;     /* MK_PREC_FP64: plain FP64 PCG.  MK_PREC_MIXED: FP32 inner PCG + FP64 residual refinement */
+  int precond;       /* MK_PRECOND_* */
+  double rtol;       /* stop when ||b_i - A x_i||_2 / ||b_i||_2 <= rtol for every column (FP64, free DOF) */
+  int maxit;         /* cap on PCG iterations (inner iterations summed for MIXED) */
+  double inner_rtol; /* MIXED: relative reduction asked of each FP32 inner solve */
+  int max_refine;    /* MIXED: cap on FP64 refinement cycles */
+  int check_every;   /* iterations between host convergence checks (>= 1) */
+} mk_solve_opts;
+
+typedef struct {
+  int status;        /* MK_OK, MK_ERR_NOT_CONVERGED or MK_ERR_BREAKDOWN */
+  int iterations;    /* PCG iterations run (all columns advance together) */
+  int refinements;   /* FP64 residual refinements (MIXED) */
+  int n_rhs;
+  double max_rel_residual;              /* max over columns of the final FP64 relative residual */
+  int iters[MK_MAX_RHS];                /* per column: iterations until it met rtol */
+  double rel_residual[MK_MAX_RHS];      /* per column: final FP64 ||b - A x|| / ||b|| */
+} mk_solve_report;
+
+typedef struct {
+  int order, nloc;
+  int64_t n_nodes, n_free, n_elems, n_colours;            /* fine level */
+  int64_t n_nodes_coarse, n_free_coarse, n_elems_coarse;  /* coarse level */
+  int n_quad;                                             /* quadrature points per element */
+} mk_mesh_info;
+
+/* ---------------------------------------------------------------------------------------------- context */
+/* Creates a context on CUDA device `device`.  Errors: MK_ERR_CUDA (no device / bad id). */
+int mk_ctx_create(mk_ctx** ctx, int device);
+int mk_ctx_destroy(mk_ctx* ctx);
+/* Copies the calling thread's last error message into buf (always NUL-terminated); returns its length. */
+int mk_last_error(char* buf, size_t len);
+/* Version string of the library build. */
+const char* mk_version(void);
+
+/* ---------------------------------------------------------------------------------------------- mesh (A0) */
+/* Uploads a nested fine/coarse mesh pair (Sec. 2: V_H subset V_h needs T_h to refine T_H).  fine_parent [n_elems
+ * of fine] gives, for each fine tetrahedron, the coarse tetrahedron containing it.  Computed here on the host:
+ * P2 edge-node numbering, boundary nodes (nodes on faces that belong to one tetrahedron), greedy element
+ * colouring (elements in index order, smallest colour not used by an earlier element sharing a vertex), the
+ * coarse-to-fine interpolation P (coarse basis functions evaluated at fine nodes), the element patches used by
+ * the FP32 operator.  Device copies are owned by the returned handle.  Errors: MK_ERR_INVALID_ARG (orders differ,
+ * index out of range, det J <= 0, a fine element outside its parent), MK_ERR_OOM, MK_ERR_CUDA. */
+int mk_mesh_upload(mk_ctx* ctx, const mk_mesh_desc* fine, const mk_mesh_desc* coarse, const int32_t* fine_parent,
+                   mk_mesh** out);
+int mk_mesh_destroy(mk_mesh* mesh);
+int mk_mesh_get_info(const mk_mesh* mesh, mk_mesh_info* info);
+/* Host copies of the A0 results, for checking: level 0 = fine, 1 = coarse.  Any pointer may be NULL.
+ * nodes [n_nodes*3], boundary [n_nodes] (1 = boundary), elem [n_elems*nloc] node indices, colour [n_elems]. */
+int mk_mesh_get_topology(const mk_mesh* mesh, int level, double* nodes, uint8_t* boundary, int32_t* elem,
+                         int32_t* colour);
+
+/* ---------------------------------------------------------------------------------------------- A1 */
+/* u = P psi_H: psiH [N_H * ldc] (coarse free DOF) -> u [n_nodes * ld] fine, boundary rows 0 (Sec. 2, V_H subset
+ * V_h: exact interpolation).  Errors: MK_ERR_INVALID_ARG (N < 1, N > ld, N > ldc). */
+int mk_prolongate(mk_ctx* ctx, const mk_mesh* mesh, const double* psiH, int ldc, int N, double* u, int ld,
+                  void* stream);
+
+/* ---------------------------------------------------------------------------------------------- A2 */
+/* Hartree potential (Sec. 2, -Delta V_Har = 4 pi rho; Eq. (W_h_equation)): solves (grad w, grad v) =
+ * 4 pi (rho_H, v) for all free v with rho_H(x) = sum_i occ[i] u_i(x)^2 evaluated at the quadrature points.
+ * bc = MK_BC_MULTIPOLE: boundary values from the multipole expansion of int rho(y)/|x-y| dy about the origin
+ * through l = 2 (Remark after Algorithm 3); MK_BC_ZERO: w = 0 on the boundary.
+ * u [n_nodes*ld] device, occ [N] host, w [n_nodes] device output (boundary values included).  The report is
+ * filled (stream synchronised).  Errors: MK_ERR_NOT_CONVERGED, MK_ERR_BREAKDOWN, MK_ERR_INVALID_ARG. */
+int mk_hartree_poisson(mk_ctx* ctx, const mk_mesh* mesh, const double* u, int ld, const double* occ, int N, int bc,
+                       double* w, const mk_solve_opts* opts, mk_solve_report* report, void* stream);
+
+/* ---------------------------------------------------------------------------------------------- A3 */
+/* Right-hand sides of the correction problems (Eq. (Aux_Linear_Problem) with V_Hxc(rho_H) moved to the right):
+ * rhs_i(v) = (lambdaH[i] + sigma)(u_i, v) - ((w + V_xc(rho_H)) u_i, v), rho_H = sum_i occ[i] u_i^2, for all
+ * fine nodes v (boundary rows written as 0).  Also writes the frozen potential w + V_xc(rho_H) at the quadrature
+ * points, vq [n_elems * n_quad] (element order of the upload), which mk_augmented_project reuses.
+ * u, rhs [n_nodes*ld] device; w [n_nodes] device or NULL (= 0); lambdaH, occ [N] host. */
+int mk_assemble_rhs(mk_ctx* ctx, const mk_mesh* mesh, const double* u, int ld, const double* lambdaH,
+                    const double* occ, int N, const double* w, double sigma, mk_xc xc, double* rhs, double* vq,
+                    void* stream);
+
+/* ---------------------------------------------------------------------------------------------- A4 */
+/* Solves (K/2 + M_{V_ext} + sigma M) x_i = rhs_i on the free fine DOF for i < N at once (Eq. (Aux_Linear_Problem),
+ * one boundary-value problem per orbital, Algorithm 1 step 5), matrix-free element by element.
+ * x [n_nodes*ld] device: initial guess in, solution psi^ out (boundary rows 0).  opts->precision selects plain
+ * FP64 PCG or FP32 inner PCG with FP64 residual refinement; either way convergence is judged on the FP64
+ * residual.  The report is filled (stream synchronised).  Errors: MK_ERR_NOT_CONVERGED (x still written),
+ * MK_ERR_BREAKDOWN (sigma too small), MK_ERR_INVALID_ARG, MK_ERR_UNSUPPORTED (precond not built). */
+int mk_correction_solve(mk_ctx* ctx, const mk_mesh* mesh, const mk_molecule* mol, double sigma, const double* rhs,
+                        double* x, int ld, int N, const mk_solve_opts* opts, mk_solve_report* report, void* stream);
+
+/* ---------------------------------------------------------------------------------------------- A6 */
+/* Projection on the augmented spaces V_H + span{psi^_i} (Eqs. (Eigenvalue_H_h), (Adef), (bdef), (betadef)) with
+ * H = K/2 + M_{V_ext} + M_{vq} the Hamiltonian at the frozen density (vq from mk_assemble_rhs):
+ *   AH = P^T H P, MH = P^T M P           [N_H*N_H] row-major, coarse free DOF (shared by all orbitals)
+ *   b[:,i] = P^T H psi^_i, c[:,i] = P^T M psi^_i      [N_H*N] (ld = N)
+ *   beta[i] = psi^_i^T H psi^_i, gamma[i] = psi^_i^T M psi^_i                    [N]
+ *   gramA = Psi^T H Psi, gramM = Psi^T M Psi   [N*N] (may be NULL)
+ * All device FP64. */
+int mk_augmented_project(mk_ctx* ctx, const mk_mesh* mesh, const mk_molecule* mol, const double* vq,
+                         const double* psihat, int ld, int N, double* AH, double* MH, double* b, double* c,
+                         double* beta, double* gamma, double* gramA, double* gramM, void* stream);
+
+/* ---------------------------------------------------------------------------------------------- A7 */
+/* For each orbital i < N, all eigenpairs of the (N_H+1) pencil of Eq. (Eigenvalue_H_h)
+ *   [[AH, b_i], [b_i^T, beta_i]] x = lambda [[MH, c_i], [c_i^T, gamma_i]] x
+ * and the one "with the largest component in span{psi^_i}" (Algorithm 2 (a)), read as the largest
+ * |(x, psi^_i)_M| over M-normalised eigenvectors (ties within 1e-12 relative: lower eigenvalue).  Computed as one
+ * shared FP64 eigen-decomposition of (AH, MH) plus, per orbital, the roots of the secular equation of the
+ * bordered problem.  Outputs: lambda [N], coef [(N_H+1)*N] (column i = (phi_{i,H}, theta_{2,i}), M-normalised,
+ * sign with (x, psi^_i)_M >= 0), status [N] (MK_OK or MK_ERR_SINGULAR_AUG when ||u||_M/||psi^||_M < 1e-7 with
+ * u = psi^ - Pi_H psi^; then the coarse Ritz pair with the largest |(x, Pi_H psi^)_M| and theta = 0).
+ * All device FP64 (status int32).  Errors: MK_ERR_INVALID_ARG, MK_ERR_CUDA. */
+int mk_small_eigensolve(mk_ctx* ctx, int N_H, int N, const double* AH, const double* MH, const double* b,
+                        const double* c, const double* beta, const double* gamma, double* lambda, double* coef,
+                        int32_t* status, void* stream);
+
+/* ---------------------------------------------------------------------------------------------- A8 */
+/* psi_i = P phi_{i,H} + theta_{2,i} psi^_i (Algorithm 3, output), sign chosen so that (psi_i, u_i)_M > 0.
+ * coef [(N_H+1)*N] from mk_small_eigensolve, psihat/u/psi [n_nodes*ld] device. */
+int mk_orbital_assemble(mk_ctx* ctx, const mk_mesh* mesh, const double* coef, const double* psihat,
+                        const double* u, int ld, int N, double* psi, void* stream);
+
+/* ---------------------------------------------------------------------------------------------- shift */
+/* Lowest Ritz value of `steps` Lanczos steps on the pencil (K/2 + M_{V_ext}, M) over the free fine DOF, from the
+ * start vector v0 [n_free] (host, free-DOF order); M^-1 applied by an inner CG.  Used for the shift rule
+ * sigma = 1.05 max(0, -theta) + 0.5 that keeps the correction operator positive definite. */
+int mk_lowest_ritz(mk_ctx* ctx, const mk_mesh* mesh, const mk_molecule* mol, const double* v0, int steps,
+                   double* theta, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MK_H */

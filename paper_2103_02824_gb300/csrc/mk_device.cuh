@@ -1,0 +1,110 @@
+// Device building blocks shared by the mk translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "mk_internal.h"
+
+namespace mk {
+
+constexpr int kRedBlocksPerSM = 2;
+constexpr int kRedThreads = 256;
+
+inline int red_blocks(const mk_ctx* ctx) { return ctx->n_sms * kRedBlocksPerSM; }
+
+__device__ __forceinline__ double nuclear_potential(const double* __restrict__ nuc, int nnuc, double x, double y,
+                                                    double z) {
+  double v = 0.0;
+  for (int k = 0; k < nnuc; ++k) {
+    double dx = x - nuc[4 * k + 1], dy = y - nuc[4 * k + 2], dz = z - nuc[4 * k + 3];
+    double r = sqrt(dx * dx + dy * dy + dz * dz);
+    v -= nuc[4 * k] / fmax(r, 1e-8);
+  }
+  return v;
+}
+
+// y[node(e,a)][j] += sum_b A_e[a][b] x[node(e,b)][j] for the elements of one colour (no two share a node, so the
+// read-modify-write scatter needs no atomics and the summation order is fixed: colour by colour).
+template <int NLOC, typename T>
+__global__ void k_apply_colour(const int32_t* __restrict__ celems, int count, const int32_t* __restrict__ elem,
+                               const T* __restrict__ Ae, const T* __restrict__ x, T* __restrict__ y, int N, int ld) {
+  constexpr int NP = NLOC * (NLOC + 1) / 2;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)count * N) return;
+  const int i = (int)(t / N), j = (int)(t % N);
+  const int e = celems[i];
+  int nd[NLOC];
+  T xv[NLOC];
+#pragma unroll
+  for (int a = 0; a < NLOC; ++a) {
+    nd[a] = elem[(int64_t)e * NLOC + a];
+    xv[a] = x[(int64_t)nd[a] * ld + j];
+  }
+  const T* A = Ae + (int64_t)e * NP;
+#pragma unroll
+  for (int a = 0; a < NLOC; ++a) {
+    T s = 0;
+#pragma unroll
+    for (int b = 0; b < NLOC; ++b) s += A[sym_index(a, b, NLOC)] * xv[b];
+    y[(int64_t)nd[a] * ld + j] += s;
+  }
+}
+
+// Launches the colour sweep y += A x (y must hold its starting value).
+template <typename T>
+inline void apply_coloured(const Level& L, const T* Ae, const T* x, T* y, int N, int ld, cudaStream_t s) {
+  const int th = 256;
+  for (int c = 0; c < L.n_colours; ++c) {
+    const int64_t off = L.colour_off[c], cnt = L.colour_off[c + 1] - off;
+    const int64_t work = cnt * N;
+    const int blocks = (int)((work + th - 1) / th);
+    if (L.nloc == 4)
+      k_apply_colour<4, T><<<blocks, th, 0, s>>>(L.d_colour_elems + off, (int)cnt, L.d_elem, Ae, x, y, N, ld);
+    else
+      k_apply_colour<10, T><<<blocks, th, 0, s>>>(L.d_colour_elems + off, (int)cnt, L.d_elem, Ae, x, y, N, ld);
+  }
+}
+
+// Column-wise partial dot products over all nodes: part[blk*N + j] = sum_{nodes in blk's stride} a[n][j]*b[n][j].
+// Deterministic: fixed grid, fixed node->thread map, fixed reduction tree.
+template <typename T>
+__global__ void k_dot_partial(int64_t n_nodes, const T* __restrict__ a, const T* __restrict__ b, int N, int ld,
+                              double* __restrict__ part) {
+  extern __shared__ double sh[];
+  const int rows = blockDim.x / N;  // node rows handled per pass
+  const int r = threadIdx.x / N, j = threadIdx.x % N;
+  double acc = 0.0;
+  if (r < rows) {
+    for (int64_t nd = (int64_t)blockIdx.x * rows + r; nd < n_nodes; nd += (int64_t)gridDim.x * rows)
+      acc += (double)a[nd * ld + j] * (double)b[nd * ld + j];
+  }
+  sh[threadIdx.x] = (r < rows) ? acc : 0.0;
+  __syncthreads();
+  if (threadIdx.x < N) {
+    double s = 0.0;
+    for (int k = 0; k < rows; ++k) s += sh[k * N + threadIdx.x];
+    part[(int64_t)blockIdx.x * N + threadIdx.x] = s;
+  }
+}
+
+// Sums partials in block order: out[j] = sum_blk part[blk*N + j].
+__global__ void k_sum_partials(const double* __restrict__ part, int nblk, int N, double* __restrict__ out);
+
+int column_dots(mk_ctx* ctx, int64_t n_nodes, const double* a, const double* b, int N, int ld, double* out,
+                cudaStream_t s);
+int column_dots32(mk_ctx* ctx, int64_t n_nodes, const float* a, const float* b, int N, int ld, double* out,
+                  cudaStream_t s);
+
+// element matrices (packed, FP64) of half_k K + vext_scale M_{V_ext} + mass_shift M + M_{vq}
+int element_matrices(mk_ctx* ctx, const Level& L, const mk_molecule* mol, double half_k, double vext_scale,
+                     double mass_shift, const double* vq, double* out, cudaStream_t s);
+// assembled diagonal of the packed element matrices, boundary rows set to 1
+int assemble_diagonal(mk_ctx* ctx, const Level& L, const double* Ae, double* diag, cudaStream_t s);
+// y = A x (y zeroed first), boundary rows of y zeroed if mask_boundary
+int apply64(mk_ctx* ctx, const Level& L, const double* Ae, const double* x, double* y, int N, int ld,
+            bool mask_boundary, cudaStream_t s);
+
+// nuclei packed for the device: [n*4] (Z, x, y, z); returns a device pointer in a ctx slot
+double* upload_nuclei(mk_ctx* ctx, const mk_molecule* mol, int* err, cudaStream_t s);
+
+}  // namespace mk

@@ -1,0 +1,611 @@
+// A7: the small augmented eigenproblem of Eq. (Eigenvalue_H_h) for every orbital, and A8: the corrected orbitals.
+//
+// All orbitals share the coarse pencil (A_H, M_H).  It is decomposed once, in FP64: Cholesky M_H = L L^T,
+// C = L^-1 A_H L^-T, cyclic Jacobi C = Q diag(d) Q^T (parallel round-robin ordering, cooperative grid),
+// V = L^-T Q (M_H-orthonormal, A_H V = M_H V diag(d)).  For orbital i the extra direction psi^ is made
+// M-orthogonal to V_H: with p = V^T c and ||u||^2 = gamma - |p|^2, the pencil becomes, in the orthonormal basis
+// [V, u/||u||], the arrowhead matrix [[diag(d), z], [z^T, alpha]] with z = (V^T b - d .* p)/||u|| and
+// alpha = (beta - 2 p.(V^T b) + p.(d .* p))/||u||^2.  Its eigenvalues are d_k for deflated k (z_k ~ 0, or d_k
+// repeated) and the roots of the secular equation alpha - mu + sum_k z_k^2/(mu - d_k) = 0, one per interlacing
+// interval, found by bisection in the offset from the nearer pole.  Every eigenvector's score |(x, psi^)_M| is
+// formed and the largest kept (Algorithm 2 (a)); ties within 1e-12 go to the lower eigenvalue.
+#include <cooperative_groups.h>
+
+#include <cmath>
+#include <vector>
+
+#include "mk_device.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace mk {
+
+// ------------------------------------------------------------------------------------------------ Cholesky
+// Left-looking Cholesky of the n x n SPD matrix A (row-major); writes LT = L^T row-major (LT[k][i] = L[i][k]).
+__global__ void k_cholesky(int n, const double* __restrict__ A, double* __restrict__ LT, int* __restrict__ flag) {
+  __shared__ double red[1024];
+  __shared__ double ljj;
+  for (int j = 0; j < n; ++j) {
+    double s = 0.0;
+    for (int k = threadIdx.x; k < j; k += blockDim.x) {
+      const double v = LT[(int64_t)k * n + j];
+      s += v * v;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      const double dd = A[(int64_t)j * n + j] - red[0];
+      if (!(dd > 0.0)) *flag = 1;
+      ljj = sqrt(fmax(dd, 1e-300));
+      LT[(int64_t)j * n + j] = ljj;
+    }
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      double t = A[(int64_t)i * n + j];
+      for (int k = 0; k < j; ++k) t -= LT[(int64_t)k * n + i] * LT[(int64_t)k * n + j];
+      LT[(int64_t)j * n + i] = t / ljj;
+    }
+    for (int i = threadIdx.x; i < j; i += blockDim.x) LT[(int64_t)j * n + i] = 0.0;
+    __syncthreads();
+  }
+}
+
+// X = L^-1 B for each column of B (thread per column): forward substitution.
+__global__ void k_forward(int n, const double* __restrict__ LT, const double* __restrict__ B, double* __restrict__ X) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  for (int i = 0; i < n; ++i) {
+    double t = B[(int64_t)i * n + j];
+    for (int k = 0; k < i; ++k) t -= LT[(int64_t)k * n + i] * X[(int64_t)k * n + j];
+    X[(int64_t)i * n + j] = t / LT[(int64_t)i * n + i];
+  }
+}
+
+// X = L^-T B for each column (thread per column): back substitution with L^T.
+__global__ void k_backward(int n, const double* __restrict__ LT, const double* __restrict__ B, double* __restrict__ X,
+                           int ldb, int ldx) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  for (int i = n - 1; i >= 0; --i) {
+    double t = B[(int64_t)i * ldb + j];
+    for (int k = i + 1; k < n; ++k) t -= LT[(int64_t)i * n + k] * X[(int64_t)k * ldx + j];
+    X[(int64_t)i * ldx + j] = t / LT[(int64_t)i * n + i];
+  }
+}
+
+__global__ void k_transpose(int n, const double* __restrict__ A, double* __restrict__ B) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n) return;
+  const int i = (int)(t / n), j = (int)(t % n);
+  B[(int64_t)j * n + i] = A[t];
+}
+
+// C (n x n) -> padded symmetric n2 x n2 (n2 even) with (C + C^T)/2; Q = I.
+__global__ void k_pad_sym(int n, int n2, const double* __restrict__ C, double* __restrict__ S, double* __restrict__ Q,
+                          double pad) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n2 * n2) return;
+  const int i = (int)(t / n2), j = (int)(t % n2);
+  double v = 0.0;
+  if (i < n && j < n) v = 0.5 * (C[(int64_t)i * n + j] + C[(int64_t)j * n + i]);
+  else if (i == j) v = pad;
+  S[t] = v;
+  Q[t] = (i == j) ? 1.0 : 0.0;
+}
+
+struct Rot {
+  int p, q;
+  double c, s;
+};
+
+__device__ __forceinline__ void pair_of(int r, int k, int n2, int* p, int* q) {
+  int a, b;
+  if (k == 0) {
+    a = n2 - 1;
+    b = r;
+  } else {
+    a = (r + k) % (n2 - 1);
+    b = (r - k + (n2 - 1)) % (n2 - 1);
+  }
+  *p = min(a, b);
+  *q = max(a, b);
+}
+
+// Cyclic Jacobi on the symmetric n2 x n2 matrix S (n2 even), accumulating Q <- Q J.  Cooperative launch.
+__global__ void k_jacobi(int n2, double* __restrict__ S, double* __restrict__ Q, Rot* __restrict__ rot,
+                         double* __restrict__ red, int max_sweeps, double tol, int* __restrict__ sweeps_out) {
+  cg::grid_group grid = cg::this_grid();
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  const int np = n2 / 2;
+  const int64_t nblk2 = (int64_t)np * (np + 1) / 2;
+  __shared__ double sh[256];
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    // convergence test: off-diagonal vs total Frobenius norm
+    double off = 0.0, tot = 0.0;
+    for (int64_t t = tid; t < (int64_t)n2 * n2; t += nth) {
+      const double v = S[t];
+      tot += v * v;
+      if (t / n2 != t % n2) off += v * v;
+    }
+    sh[threadIdx.x] = off;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) red[2 * blockIdx.x] = sh[0];
+    __syncthreads();
+    sh[threadIdx.x] = tot;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) red[2 * blockIdx.x + 1] = sh[0];
+    grid.sync();
+    double o = 0.0, f = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+      o += red[2 * b];
+      f += red[2 * b + 1];
+    }
+    grid.sync();
+    if (o <= tol * tol * f) break;
+    for (int r = 0; r < n2 - 1; ++r) {
+      for (int64_t k = tid; k < np; k += nth) {
+        int p, q;
+        pair_of(r, (int)k, n2, &p, &q);
+        const double apq = S[(int64_t)p * n2 + q];
+        double c = 1.0, s = 0.0;
+        if (apq != 0.0) {
+          const double app = S[(int64_t)p * n2 + p], aqq = S[(int64_t)q * n2 + q];
+          const double theta = (aqq - app) / (2.0 * apq);
+          const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+          c = 1.0 / sqrt(t * t + 1.0);
+          s = t * c;
+        }
+        rot[k] = Rot{p, q, c, s};
+      }
+      grid.sync();
+      // 2x2 blocks (k1 <= k2): B' = R1^T B R2 with rows (p1,q1), cols (p2,q2)
+      for (int64_t t = tid; t < nblk2; t += nth) {
+        // decode upper-triangular pair index t -> (k1, k2)
+        int k1 = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) / 2.0);  // row in lower-tri enumeration
+        while ((int64_t)(k1 + 1) * (k1 + 2) / 2 <= t) ++k1;
+        while ((int64_t)k1 * (k1 + 1) / 2 > t) --k1;
+        const int k2 = (int)(t - (int64_t)k1 * (k1 + 1) / 2);  // k2 <= k1
+        const Rot A = rot[k2], B = rot[k1];                    // rows from pair k2, cols from pair k1
+        const double b00 = S[(int64_t)A.p * n2 + B.p], b01 = S[(int64_t)A.p * n2 + B.q];
+        const double b10 = S[(int64_t)A.q * n2 + B.p], b11 = S[(int64_t)A.q * n2 + B.q];
+        // rows: r_p = c b_p - s b_q ; r_q = s b_p + c b_q
+        const double r00 = A.c * b00 - A.s * b10, r01 = A.c * b01 - A.s * b11;
+        const double r10 = A.s * b00 + A.c * b10, r11 = A.s * b01 + A.c * b11;
+        // cols
+        double n00 = B.c * r00 - B.s * r01, n01 = B.s * r00 + B.c * r01;
+        double n10 = B.c * r10 - B.s * r11, n11 = B.s * r10 + B.c * r11;
+        if (k1 == k2) {
+          n01 = 0.0;
+          n10 = 0.0;
+        }
+        S[(int64_t)A.p * n2 + B.p] = n00;
+        S[(int64_t)A.p * n2 + B.q] = n01;
+        S[(int64_t)A.q * n2 + B.p] = n10;
+        S[(int64_t)A.q * n2 + B.q] = n11;
+        if (k1 != k2) {
+          S[(int64_t)B.p * n2 + A.p] = n00;
+          S[(int64_t)B.q * n2 + A.p] = n01;
+          S[(int64_t)B.p * n2 + A.q] = n10;
+          S[(int64_t)B.q * n2 + A.q] = n11;
+        }
+      }
+      for (int64_t t = tid; t < (int64_t)n2 * np; t += nth) {
+        const int row = (int)(t / np), k = (int)(t % np);
+        const Rot R = rot[k];
+        const double vp = Q[(int64_t)row * n2 + R.p], vq = Q[(int64_t)row * n2 + R.q];
+        Q[(int64_t)row * n2 + R.p] = R.c * vp - R.s * vq;
+        Q[(int64_t)row * n2 + R.q] = R.s * vp + R.c * vq;
+      }
+      grid.sync();
+    }
+  }
+  if (tid == 0) *sweeps_out = sweep;
+}
+
+// Sort the n eigenvalues (diag of S, first n of n2) ascending: perm[rank] = index (ties by index).
+__global__ void k_rank(int n, int n2, const double* __restrict__ S, double* __restrict__ d, int* __restrict__ perm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = S[(int64_t)i * n2 + i];
+  int r = 0;
+  for (int k = 0; k < n; ++k) {
+    const double w = S[(int64_t)k * n2 + k];
+    if (w < v || (w == v && k < i)) ++r;
+  }
+  d[r] = v;
+  perm[r] = i;
+}
+
+// Qs[i][r] = Q[i][perm[r]] (n x n, columns sorted)
+__global__ void k_gather_cols(int n, int n2, const double* __restrict__ Q, const int* __restrict__ perm,
+                              double* __restrict__ Qs) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n) return;
+  const int i = (int)(t / n), r = (int)(t % n);
+  Qs[t] = Q[(int64_t)i * n2 + perm[r]];
+}
+
+// G[k][col] = sum_i V[i][k] B[i][col]  (V^T [b|c]); B has 2N columns: b (ld N) then c (ld N)
+__global__ void k_vt_bc(int n, int N, const double* __restrict__ V, const double* __restrict__ b,
+                        const double* __restrict__ c, double* __restrict__ G) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * 2 * N) return;
+  const int k = (int)(t / (2 * N)), col = (int)(t % (2 * N));
+  const double* B = col < N ? b : c;
+  const int j = col < N ? col : col - N;
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) s += V[(int64_t)i * n + k] * B[(int64_t)i * N + j];
+  G[(int64_t)k * 2 * N + col] = s;
+}
+
+// ------------------------------------------------------------------------------------------------ secular
+__device__ __forceinline__ double secular_f(int m, const double* __restrict__ dd, const double* __restrict__ zz,
+                                            double alpha, double origin, double delta) {
+  double f = alpha - (origin + delta);
+  for (int k = 0; k < m; ++k) {
+    const double den = (origin - dd[k]) + delta;
+    f += zz[k] * zz[k] / den;
+  }
+  return f;
+}
+
+constexpr int kEigThreads = 256;
+
+// One block per orbital.  Work arrays in global memory: per orbital kWorkVecs*(n+1) doubles, 4*(n+1) ints.
+constexpr int kWorkVecs = 10;
+
+__global__ void k_secular_select(int n, int N, const double* __restrict__ d, const double* __restrict__ V,
+                                 const double* __restrict__ G, const double* __restrict__ beta,
+                                 const double* __restrict__ gamma, double* __restrict__ work, int* __restrict__ iwork,
+                                 double* __restrict__ lambda, double* __restrict__ coef, int32_t* __restrict__ status,
+                                 double sing_rtol, double tie_rtol) {
+  const int i = blockIdx.x;
+  if (i >= N) return;
+  const int64_t n1 = n + 1;
+  double* zs = work + (int64_t)i * kWorkVecs * n1;  // z in the (rotated) V basis
+  double* ps = zs + n1;                             // p = V^T c in the (rotated) V basis
+  double* dk = ps + n1;                             // poles kept in the secular equation
+  double* zk = dk + n1;                             // their z
+  double* score = zk + n1;                          // per candidate |(x, psi^)_M|
+  double* eig = score + n1;                         // per candidate eigenvalue
+  double* yv = eig + n1;                            // per root: offset delta; later the selected eigenvector
+  double* rcos = yv + n1;                           // deflation rotation of index k with its partner
+  double* rsin = rcos + n1;
+  double* ytmp = rsin + n1;
+  int* kind = iwork + (int64_t)i * 4 * n1;          // candidate t: >= 0 root index, < 0 deflated -(k+1)
+  int* comp = kind + n1;                            // kept pole -> original index
+  int* partner = comp + n1;                         // rotation partner of k (-1 none)
+  int* origin_idx = partner + n1;                   // per root: kept pole used as origin
+  __shared__ double s_alpha, s_un, s_norm, s_sign, s_ylast;
+  __shared__ int s_m, s_ncand, s_sel, s_singular;
+  __shared__ double s_red[kEigThreads];
+  const int tid = threadIdx.x;
+  // p = V^T c, g = V^T b;  ||u||^2 = gamma - |p|^2 (u = psi^ - Pi_H psi^, V is M_H-orthonormal)
+  double pp = 0.0;
+  for (int k = tid; k < n; k += blockDim.x) {
+    const double pk = G[(int64_t)k * 2 * N + N + i];
+    pp += pk * pk;
+  }
+  s_red[tid] = pp;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (tid < st) s_red[tid] += s_red[tid + st];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const double u2 = gamma[i] - s_red[0];
+    s_singular = !(u2 > sing_rtol * sing_rtol * gamma[i]);
+    s_un = s_singular ? 0.0 : sqrt(u2);
+  }
+  __syncthreads();
+  if (s_singular) {  // psi^ in V_H: coarse Ritz pair with the largest |(v_k, Pi_H psi^)_M| = |p_k|
+    if (tid == 0) {
+      double best = -1.0;
+      for (int k = 0; k < n; ++k) best = fmax(best, fabs(G[(int64_t)k * 2 * N + N + i]));
+      int sel = 0;
+      for (int k = 0; k < n; ++k)
+        if (fabs(G[(int64_t)k * 2 * N + N + i]) >= best * (1.0 - tie_rtol)) { sel = k; break; }
+      s_sel = sel;
+      lambda[i] = d[sel];
+      status[i] = MK_ERR_SINGULAR_AUG;
+    }
+    __syncthreads();
+    const double sgn = G[(int64_t)s_sel * 2 * N + N + i] < 0 ? -1.0 : 1.0;
+    for (int r = tid; r < n; r += blockDim.x) coef[(int64_t)r * N + i] = sgn * V[(int64_t)r * n + s_sel];
+    if (tid == 0) coef[(int64_t)n * N + i] = 0.0;
+    return;
+  }
+  // z = (V^T b - d .* p)/||u||, alpha = (beta - 2 p.(V^T b) + p.(d .* p))/||u||^2
+  double a2 = 0.0;
+  for (int k = tid; k < n; k += blockDim.x) {
+    const double gk = G[(int64_t)k * 2 * N + i], pk = G[(int64_t)k * 2 * N + N + i];
+    zs[k] = (gk - d[k] * pk) / s_un;
+    ps[k] = pk;
+    partner[k] = -1;
+    a2 += -2.0 * pk * gk + pk * d[k] * pk;
+  }
+  s_red[tid] = a2;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (tid < st) s_red[tid] += s_red[tid + st];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    s_alpha = (beta[i] + s_red[0]) / (s_un * s_un);
+    // deflation (sequential, O(n)): negligible z_k, then (nearly) equal poles merged by Givens rotations
+    double zn = 0.0, dmax = fabs(s_alpha);
+    for (int k = 0; k < n; ++k) {
+      zn += zs[k] * zs[k];
+      dmax = fmax(dmax, fabs(d[k]));
+    }
+    zn = sqrt(zn);
+    const double tol = 8.0 * 2.220446049250313e-16 * fmax(dmax, zn);
+    int m = 0, nc = 0, last = -1;
+    for (int k = 0; k < n; ++k) {
+      if (fabs(zs[k]) <= tol) {
+        kind[nc] = -(k + 1);
+        eig[nc] = d[k];
+        ++nc;
+        continue;
+      }
+      if (last >= 0 && fabs(d[k] - d[last]) <= tol) {
+        // v_last' = c v_last + s v_k, v_k' = -s v_last + c v_k with z_k' = 0
+        const double r = hypot(zs[last], zs[k]);
+        const double c = zs[last] / r, sn = zs[k] / r;
+        const double pl = ps[last], pk = ps[k];
+        ps[last] = c * pl + sn * pk;
+        ps[k] = -sn * pl + c * pk;
+        zs[last] = r;
+        zs[k] = 0.0;
+        partner[k] = last;
+        rcos[k] = c;
+        rsin[k] = sn;
+        kind[nc] = -(k + 1);
+        eig[nc] = d[k];
+        ++nc;
+        continue;
+      }
+      comp[m++] = k;
+      last = k;
+    }
+    for (int t = 0; t < m; ++t) {
+      dk[t] = d[comp[t]];
+      zk[t] = zs[comp[t]];
+    }
+    for (int t = 0; t <= m; ++t) kind[nc + t] = t;
+    s_m = m;
+    s_ncand = nc + m + 1;
+  }
+  __syncthreads();
+  const int m = s_m, nc0 = s_ncand - (m + 1);
+  const double alpha = s_alpha;
+  double zn2 = 0.0;
+  for (int t = 0; t < m; ++t) zn2 += zk[t] * zk[t];
+  const double zn = sqrt(zn2);
+  // roots of alpha - mu + sum z_t^2/(mu - d_t): one in each of (-inf,d_0), (d_0,d_1), ..., (d_{m-1},inf)
+  for (int r = tid; r <= m; r += blockDim.x) {
+    double origin = alpha, lo = 0.0, hi = 0.0;
+    int oi = -1;
+    if (m > 0) {
+      if (r == 0) {
+        oi = 0; origin = dk[0];
+        lo = fmin(dk[0], alpha) - zn - 1.0 - origin; hi = 0.0;
+      } else if (r == m) {
+        oi = m - 1; origin = dk[m - 1];
+        lo = 0.0; hi = fmax(dk[m - 1], alpha) + zn + 1.0 - origin;
+      } else {
+        const double mid = 0.5 * (dk[r - 1] + dk[r]);
+        if (secular_f(m, dk, zk, alpha, dk[r - 1], mid - dk[r - 1]) > 0) {
+          oi = r; origin = dk[r]; lo = mid - dk[r]; hi = 0.0;   // root in (mid, d_r)
+        } else {
+          oi = r - 1; origin = dk[r - 1]; lo = 0.0; hi = mid - dk[r - 1];
+        }
+      }
+    }
+    double delta = 0.5 * (lo + hi);
+    if (m > 0)
+      for (int it = 0; it < 2100; ++it) {  // bisection to adjacent doubles (bounded)
+        delta = 0.5 * (lo + hi);
+        if (delta == lo || delta == hi) break;
+        if (secular_f(m, dk, zk, alpha, origin, delta) > 0) lo = delta; else hi = delta;
+      }
+    origin_idx[r] = oi;
+    yv[r] = delta;
+    double yy = 1.0, yp = s_un;  // y_last = 1, p_last = ||u||
+    for (int t = 0; t < m; ++t) {
+      const double y = zk[t] / ((origin - dk[t]) + delta);
+      yy += y * y;
+      yp += y * ps[comp[t]];
+    }
+    score[nc0 + r] = fabs(yp) / sqrt(yy);
+    eig[nc0 + r] = origin + delta;
+  }
+  for (int t = tid; t < nc0; t += blockDim.x) score[t] = fabs(ps[-kind[t] - 1]);
+  __syncthreads();
+  if (tid == 0) {  // largest score; ties within tie_rtol go to the lower eigenvalue
+    double best = -1.0;
+    for (int t = 0; t < s_ncand; ++t) best = fmax(best, score[t]);
+    int sel = -1;
+    for (int t = 0; t < s_ncand; ++t)
+      if (score[t] >= best * (1.0 - tie_rtol) && (sel < 0 || eig[t] < eig[sel])) sel = t;
+    s_sel = sel;
+    lambda[i] = eig[sel];
+    status[i] = MK_OK;
+  }
+  __syncthreads();
+  const int sel = s_sel;
+  // selected eigenvector in the rotated V basis (ytmp) and its last component
+  for (int t = tid; t < n; t += blockDim.x) ytmp[t] = 0.0;
+  __syncthreads();
+  if (kind[sel] < 0) {
+    if (tid == 0) {
+      ytmp[-kind[sel] - 1] = 1.0;
+      s_ylast = 0.0;
+    }
+  } else {
+    const int r = kind[sel];
+    const int oi = origin_idx[r];
+    const double origin = oi >= 0 ? dk[oi] : alpha;
+    const double delta = yv[r];
+    for (int t = tid; t < m; t += blockDim.x) ytmp[comp[t]] = zk[t] / ((origin - dk[t]) + delta);
+    if (tid == 0) s_ylast = 1.0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double nn = s_ylast * s_ylast, sp = s_ylast * s_un;
+    for (int t = 0; t < n; ++t) {
+      nn += ytmp[t] * ytmp[t];
+      sp += ytmp[t] * ps[t];
+    }
+    s_norm = sqrt(nn);
+    s_sign = sp < 0 ? -1.0 : 1.0;
+    // back to the original V basis: undo the rotations in reverse order of creation
+    for (int k = n - 1; k >= 0; --k) {
+      const int l = partner[k];
+      if (l < 0) continue;
+      const double a = ytmp[l], b = ytmp[k];
+      ytmp[l] = a * rcos[k] - b * rsin[k];
+      ytmp[k] = a * rsin[k] + b * rcos[k];
+    }
+  }
+  __syncthreads();
+  const double scale = s_sign / s_norm;
+  const double yl = scale * s_ylast;
+  // coarse part: phi_H = V (y - (y_last/||u||) p), theta_2 = y_last/||u||
+  for (int k = tid; k < n; k += blockDim.x) yv[k] = scale * ytmp[k] - (yl / s_un) * G[(int64_t)k * 2 * N + N + i];
+  __syncthreads();
+  for (int r = tid; r < n; r += blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s += V[(int64_t)r * n + k] * yv[k];
+    coef[(int64_t)r * N + i] = s;
+  }
+  if (tid == 0) coef[(int64_t)n * N + i] = yl / s_un;
+}
+
+// ------------------------------------------------------------------------------------------------ A8
+__global__ void k_orbitals(int64_t n_nodes, const int32_t* __restrict__ off, const int32_t* __restrict__ col,
+                           const double* __restrict__ val, const uint8_t* __restrict__ bnd,
+                           const double* __restrict__ coef, int NH, const double* __restrict__ psihat, int N, int ld,
+                           double* __restrict__ psi) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_nodes * ld) return;
+  const int64_t nd = t / ld;
+  const int j = (int)(t % ld);
+  double s = 0.0;
+  if (j < N && !bnd[nd]) {
+    for (int k = off[nd]; k < off[nd + 1]; ++k) s += val[k] * coef[(int64_t)col[k] * N + j];
+    s += coef[(int64_t)NH * N + j] * psihat[t];
+  }
+  psi[t] = s;
+}
+
+__global__ void k_flip(int64_t n_nodes, const double* __restrict__ dots, double* __restrict__ psi, int N, int ld) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_nodes * ld) return;
+  const int j = (int)(t % ld);
+  if (j < N && dots[j] < 0) psi[t] = -psi[t];
+}
+
+}  // namespace mk
+
+using namespace mk;
+
+extern "C" {
+
+int mk_small_eigensolve(mk_ctx* ctx, int NH, int N, const double* AH, const double* MH, const double* b,
+                        const double* c, const double* beta, const double* gamma, double* lambda, double* coef,
+                        int32_t* status, void* stream) {
+  MK_ARG(ctx && AH && MH && b && c && beta && gamma && lambda && coef && status, "mk_small_eigensolve: null argument");
+  MK_ARG(NH >= 1 && N >= 1 && N <= MK_MAX_RHS, "mk_small_eigensolve: bad sizes");
+  MK_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = NH, n2 = (n + 1) / 2 * 2;
+  int err = MK_OK;
+  // workspace layout
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
+  const size_t oLT = take((size_t)n * n * 8), oX = take((size_t)n * n * 8), oC = take((size_t)n * n * 8);
+  const size_t oS = take((size_t)n2 * n2 * 8), oQ = take((size_t)n2 * n2 * 8), oV = take((size_t)n * n * 8);
+  const size_t oRot = take((size_t)(n2 / 2) * sizeof(Rot)), oRed = take(4096 * 8), oD = take((size_t)n * 8);
+  const size_t oPerm = take((size_t)n * 4), oG = take((size_t)n * 2 * N * 8), oFlag = take(64);
+  const size_t oW = take((size_t)N * kWorkVecs * (n + 1) * 8), oIW = take((size_t)N * 4 * (n + 1) * 4);
+  char* ws = (char*)scratch(ctx, S_EIG, off, &err);
+  if (!ws) return err;
+  double *LT = (double*)(ws + oLT), *X = (double*)(ws + oX), *C = (double*)(ws + oC), *S = (double*)(ws + oS);
+  double *Q = (double*)(ws + oQ), *V = (double*)(ws + oV), *red = (double*)(ws + oRed), *d = (double*)(ws + oD);
+  double *G = (double*)(ws + oG), *W = (double*)(ws + oW);
+  int *perm = (int*)(ws + oPerm), *flag = (int*)(ws + oFlag), *IW = (int*)(ws + oIW);
+  Rot* rot = (Rot*)(ws + oRot);
+  MK_CUDA(cudaMemsetAsync(flag, 0, 64, s));
+  k_cholesky<<<1, 1024, 0, s>>>(n, MH, LT, flag);
+  const int tb = 128, nb = (n + tb - 1) / tb;
+  k_forward<<<nb, tb, 0, s>>>(n, LT, AH, X);                         // X = L^-1 A
+  k_transpose<<<(int)(((int64_t)n * n + 255) / 256), 256, 0, s>>>(n, X, C);
+  k_forward<<<nb, tb, 0, s>>>(n, LT, C, X);                          // X = L^-1 (L^-1 A)^T = L^-1 A L^-T
+  k_pad_sym<<<(int)(((int64_t)n2 * n2 + 255) / 256), 256, 0, s>>>(n, n2, X, S, Q, 0.0);
+  // pad row: a decoupled eigenvalue far above the spectrum is not needed because off-diagonals are 0; any value works
+  MK_CUDA(cudaGetLastError());
+  {
+    int dev_blocks = 0;
+    MK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&dev_blocks, k_jacobi, 256, 0));
+    int grid = std::min(ctx->n_sms * std::max(1, dev_blocks), 4096 / 2);
+    grid = std::max(1, std::min(grid, ctx->n_sms * 2));
+    int max_sweeps = 40;
+    double tol = 1e-15;
+    int* sweeps_out = flag + 1;
+    int n2v = n2;
+    void* args[] = {&n2v, &S, &Q, &rot, &red, &max_sweeps, &tol, &sweeps_out};
+    MK_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi, grid, 256, args, 0, s));
+  }
+  k_rank<<<nb, tb, 0, s>>>(n, n2, S, d, perm);
+  k_gather_cols<<<(int)(((int64_t)n * n + 255) / 256), 256, 0, s>>>(n, n2, Q, perm, C);   // C = Q sorted
+  k_backward<<<nb, tb, 0, s>>>(n, LT, C, V, n, n);                                         // V = L^-T Q
+  k_vt_bc<<<(int)(((int64_t)n * 2 * N + 127) / 128), 128, 0, s>>>(n, N, V, b, c, G);
+  k_secular_select<<<N, kEigThreads, 0, s>>>(n, N, d, V, G, beta, gamma, W, IW, lambda, coef, status, 1e-7, 1e-12);
+  MK_CUDA(cudaGetLastError());
+  int hflag[2] = {0, 0};
+  MK_CUDA(cudaMemcpyAsync(hflag, flag, sizeof(hflag), cudaMemcpyDeviceToHost, s));
+  MK_CUDA(cudaStreamSynchronize(s));
+  if (hflag[0]) return fail(MK_ERR_INVALID_ARG, "mk_small_eigensolve: M_H is not positive definite");
+  return MK_OK;
+}
+
+int mk_orbital_assemble(mk_ctx* ctx, const mk_mesh* m, const double* coef, const double* psihat, const double* u,
+                        int ld, int N, double* psi, void* stream) {
+  MK_ARG(ctx && m && coef && psihat && u && psi, "mk_orbital_assemble: null argument");
+  MK_ARG(N >= 1 && N <= ld && N <= MK_MAX_RHS, "mk_orbital_assemble: bad N/ld");
+  MK_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const Level& F = m->fine;
+  int err = MK_OK;
+  const size_t eb = (size_t)F.n_elems * (F.nloc * (F.nloc + 1) / 2) * sizeof(double);
+  double* Me = (double*)scratch(ctx, S_ELEM64B, eb, &err);
+  double* Mu = (double*)scratch(ctx, S_VEC1, (size_t)F.n_nodes * ld * sizeof(double), &err);
+  double* dots = (double*)scratch(ctx, S_COEF, 64 * sizeof(double), &err);
+  if (!Me || !Mu || !dots) return err;
+  const int64_t work = F.n_nodes * ld;
+  k_orbitals<<<(int)((work + 255) / 256), 256, 0, s>>>(F.n_nodes, m->d_P_off, m->d_P_col, m->d_P_val, F.d_boundary,
+                                                       coef, (int)m->coarse.n_free, psihat, N, ld, psi);
+  MK_TRY(element_matrices(ctx, F, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s));
+  MK_TRY(apply64(ctx, F, Me, u, Mu, N, ld, true, s));
+  MK_TRY(column_dots(ctx, F.n_nodes, psi, Mu, N, ld, dots, s));
+  k_flip<<<(int)((work + 255) / 256), 256, 0, s>>>(F.n_nodes, dots, psi, N, ld);
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
+}  // extern "C"

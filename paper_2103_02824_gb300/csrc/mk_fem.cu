@@ -1,0 +1,454 @@
+// Finite-element kernels on the fine mesh: element matrices by reference-element quadrature, coloured
+// element-by-element operator application, reductions, prolongation/restriction, density and potentials.
+#include <cmath>
+
+#include "mk_device.cuh"
+
+namespace mk {
+
+// ------------------------------------------------------------------------------------------------ reductions
+__global__ void k_sum_partials(const double* __restrict__ part, int nblk, int N, double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * N + j];
+  out[j] = s;
+}
+
+template <typename T>
+static int column_dots_t(mk_ctx* ctx, int64_t n_nodes, const T* a, const T* b, int N, int ld, double* out,
+                         cudaStream_t s) {
+  int err = MK_OK;
+  const int nblk = red_blocks(ctx);
+  double* part = (double*)scratch(ctx, S_RED, (size_t)nblk * N * sizeof(double), &err);
+  if (!part) return err;
+  k_dot_partial<T><<<nblk, kRedThreads, kRedThreads * sizeof(double), s>>>(n_nodes, a, b, N, ld, part);
+  k_sum_partials<<<(N + 63) / 64, 64, 0, s>>>(part, nblk, N, out);
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
+int column_dots(mk_ctx* ctx, int64_t n_nodes, const double* a, const double* b, int N, int ld, double* out,
+                cudaStream_t s) {
+  return column_dots_t<double>(ctx, n_nodes, a, b, N, ld, out, s);
+}
+int column_dots32(mk_ctx* ctx, int64_t n_nodes, const float* a, const float* b, int N, int ld, double* out,
+                  cudaStream_t s) {
+  return column_dots_t<float>(ctx, n_nodes, a, b, N, ld, out, s);
+}
+
+// ------------------------------------------------------------------------------------------------ nuclei
+double* upload_nuclei(mk_ctx* ctx, const mk_molecule* mol, int* err, cudaStream_t s) {
+  const int n = mol ? mol->n_nuclei : 0;
+  double* d = (double*)scratch(ctx, S_NUC, (size_t)(4 * n + 4) * sizeof(double), err);
+  if (!d) return nullptr;
+  if (n > 0) {
+    std::vector<double> h(4 * n);
+    for (int k = 0; k < n; ++k) {
+      h[4 * k] = mol->Z[k];
+      for (int c = 0; c < 3; ++c) h[4 * k + 1 + c] = mol->R[3 * k + c];
+    }
+    if (cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      *err = fail(MK_ERR_CUDA, "upload_nuclei: copy failed");
+      return nullptr;
+    }
+    // pageable source: make sure the copy has consumed it before h goes out of scope
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+      *err = fail(MK_ERR_CUDA, "upload_nuclei: sync failed");
+      return nullptr;
+    }
+  }
+  return d;
+}
+
+// ------------------------------------------------------------------------------------------------ element matrices
+// out_e = half_k K_e + vext_scale M_{V_ext,e} + mass_shift M_e + M_{vq,e}, packed upper triangle, FP64.
+// K_e = |det J| sum_{i<=j} (J^-1 J^-T)_{ij} S^{ij} with the reference tensors S^{ij}; the mass-type terms by the
+// 27-point rule at the physical points x_q = x0 + J xi_q.
+template <int NLOC>
+__global__ void k_element_matrices(int64_t E, const RefTables* __restrict__ ref, const Geom* __restrict__ geom,
+                                   int nnuc, const double* __restrict__ nuc, double half_k, double vext_scale,
+                                   double mass_shift, const double* __restrict__ vq, double* __restrict__ out) {
+  constexpr int NP = NLOC * (NLOC + 1) / 2;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const Geom g = geom[e];
+  const double det = fabs(g.det);
+  double acc[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) acc[p] = 0.0;
+  const bool any_mass = (vext_scale != 0.0 && nnuc > 0) || mass_shift != 0.0 || vq != nullptr;
+  if (any_mass) {
+    for (int q = 0; q < kQ; ++q) {
+      const double xi = ref->qx[q][0], et = ref->qx[q][1], ze = ref->qx[q][2];
+      double c = mass_shift;
+      if (vext_scale != 0.0 && nnuc > 0) {
+        const double x = g.x0[0] + g.J[0] * xi + g.J[1] * et + g.J[2] * ze;
+        const double y = g.x0[1] + g.J[3] * xi + g.J[4] * et + g.J[5] * ze;
+        const double z = g.x0[2] + g.J[6] * xi + g.J[7] * et + g.J[8] * ze;
+        c += vext_scale * nuclear_potential(nuc, nnuc, x, y, z);
+      }
+      if (vq) c += vq[e * kQ + q];
+      c *= ref->qw[q] * det;
+      double ph[NLOC];
+#pragma unroll
+      for (int a = 0; a < NLOC; ++a) ph[a] = ref->phi[q][a];
+#pragma unroll
+      for (int a = 0; a < NLOC; ++a)
+#pragma unroll
+        for (int b = a; b < NLOC; ++b) acc[sym_index(a, b, NLOC)] += c * ph[a] * ph[b];
+    }
+  }
+  if (half_k != 0.0) {
+    const double* Ji = g.Jinv;
+    double G[6];  // (J^-1 J^-T)_{ij} for ij = 00,11,22,01,02,12
+    const int I6[6] = {0, 1, 2, 0, 0, 1}, J6[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+      G[c] = Ji[I6[c] * 3] * Ji[J6[c] * 3] + Ji[I6[c] * 3 + 1] * Ji[J6[c] * 3 + 1] + Ji[I6[c] * 3 + 2] * Ji[J6[c] * 3 + 2];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const double f = half_k * det * G[c];
+#pragma unroll
+      for (int p = 0; p < NP; ++p) acc[p] += f * ref->stiff[c][p];
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < NP; ++p) out[e * NP + p] = acc[p];
+}
+
+int element_matrices(mk_ctx* ctx, const Level& L, const mk_molecule* mol, double half_k, double vext_scale,
+                     double mass_shift, const double* vq, double* out, cudaStream_t s) {
+  int err = MK_OK;
+  double* nuc = upload_nuclei(ctx, mol, &err, s);
+  if (!nuc) return err;
+  const int nnuc = mol ? mol->n_nuclei : 0;
+  const int th = 128;
+  const int blocks = (int)((L.n_elems + th - 1) / th);
+  if (L.nloc == 4)
+    k_element_matrices<4><<<blocks, th, 0, s>>>(L.n_elems, ctx->d_ref[1], L.d_geom, nnuc, nuc, half_k, vext_scale,
+                                                mass_shift, vq, out);
+  else
+    k_element_matrices<10><<<blocks, th, 0, s>>>(L.n_elems, ctx->d_ref[2], L.d_geom, nnuc, nuc, half_k, vext_scale,
+                                                 mass_shift, vq, out);
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
+// ------------------------------------------------------------------------------------------------ diagonal
+template <int NLOC>
+__global__ void k_diag_colour(const int32_t* __restrict__ celems, int count, const int32_t* __restrict__ elem,
+                              const double* __restrict__ Ae, double* __restrict__ diag) {
+  constexpr int NP = NLOC * (NLOC + 1) / 2;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int e = celems[i];
+#pragma unroll
+  for (int a = 0; a < NLOC; ++a) diag[elem[(int64_t)e * NLOC + a]] += Ae[(int64_t)e * NP + sym_index(a, a, NLOC)];
+}
+
+__global__ void k_mask_rows(int64_t n, const uint8_t* __restrict__ bnd, double* __restrict__ v, int N, int ld,
+                            double value) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * N) return;
+  const int64_t nd = t / N;
+  const int j = (int)(t % N);
+  if (bnd[nd]) v[nd * ld + j] = value;
+}
+
+int assemble_diagonal(mk_ctx* ctx, const Level& L, const double* Ae, double* diag, cudaStream_t s) {
+  (void)ctx;
+  MK_CUDA(cudaMemsetAsync(diag, 0, L.n_nodes * sizeof(double), s));
+  for (int c = 0; c < L.n_colours; ++c) {
+    const int64_t off = L.colour_off[c], cnt = L.colour_off[c + 1] - off;
+    const int blocks = (int)((cnt + 255) / 256);
+    if (L.nloc == 4)
+      k_diag_colour<4><<<blocks, 256, 0, s>>>(L.d_colour_elems + off, (int)cnt, L.d_elem, Ae, diag);
+    else
+      k_diag_colour<10><<<blocks, 256, 0, s>>>(L.d_colour_elems + off, (int)cnt, L.d_elem, Ae, diag);
+  }
+  k_mask_rows<<<(int)((L.n_nodes + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, diag, 1, 1, 1.0);
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
+int apply64(mk_ctx* ctx, const Level& L, const double* Ae, const double* x, double* y, int N, int ld,
+            bool mask_boundary, cudaStream_t s) {
+  (void)ctx;
+  MK_CUDA(cudaMemsetAsync(y, 0, (size_t)L.n_nodes * ld * sizeof(double), s));
+  apply_coloured<double>(L, Ae, x, y, N, ld, s);
+  if (mask_boundary)
+    k_mask_rows<<<(int)((L.n_nodes * N + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, y, N, ld, 0.0);
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
+// ------------------------------------------------------------------------------------------------ A1, restriction
+__global__ void k_prolong(int64_t n_nodes, const int32_t* __restrict__ off, const int32_t* __restrict__ col,
+                          const double* __restrict__ val, const uint8_t* __restrict__ bnd,
+                          const double* __restrict__ psiH, int ldc, int N, double* __restrict__ u, int ld) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_nodes * ld) return;
+  const int64_t nd = t / ld;
+  const int j = (int)(t % ld);
+  double s = 0.0;
+  if (j < N && !bnd[nd])
+    for (int k = off[nd]; k < off[nd + 1]; ++k) s += val[k] * psiH[(int64_t)col[k] * ldc + j];
+  u[nd * ld + j] = s;
+}
+
+// out[k*ldo + j] = sum over fine nodes n of P[n,k] y[n*ld + j]  (one block per coarse free DOF, fixed tree)
+__global__ void k_restrict(const int32_t* __restrict__ off, const int32_t* __restrict__ col,
+                           const double* __restrict__ val, const double* __restrict__ y, int ld, int N,
+                           double* __restrict__ out, int ldo) {
+  extern __shared__ double sh[];
+  const int k = blockIdx.x;
+  const int b = off[k], e = off[k + 1];
+  for (int j0 = 0; j0 < N; j0 += 8) {
+    double acc[8];
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) acc[jj] = 0.0;
+    for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
+      const double w = val[i];
+      const double* yr = y + (int64_t)col[i] * ld;
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj)
+        if (j0 + jj < N) acc[jj] += w * yr[j0 + jj];
+    }
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) sh[jj * blockDim.x + threadIdx.x] = acc[jj];
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st)
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) sh[jj * blockDim.x + threadIdx.x] += sh[jj * blockDim.x + threadIdx.x + st];
+      __syncthreads();
+    }
+    if (threadIdx.x < 8 && j0 + threadIdx.x < N) out[(int64_t)k * ldo + j0 + threadIdx.x] = sh[threadIdx.x * blockDim.x];
+    __syncthreads();
+  }
+}
+
+int restrict_to_coarse(mk_ctx* ctx, const mk_mesh* m, const double* y, int ld, int N, double* out, int ldo,
+                       cudaStream_t s) {
+  (void)ctx;
+  const int th = 128;
+  k_restrict<<<(int)m->coarse.n_free, th, 8 * th * sizeof(double), s>>>(m->d_PT_off, m->d_PT_col, m->d_PT_val, y,
+                                                                          ld, N, out, ldo);
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
+int prolongate(mk_ctx* ctx, const mk_mesh* m, const double* psiH, int ldc, int N, double* u, int ld,
+               cudaStream_t s) {
+  (void)ctx;
+  const Level& F = m->fine;
+  k_prolong<<<(int)((F.n_nodes * ld + 255) / 256), 256, 0, s>>>(F.n_nodes, m->d_P_off, m->d_P_col, m->d_P_val,
+                                                                 F.d_boundary, psiH, ldc, N, u, ld);
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
+// ------------------------------------------------------------------------------------------------ density, potentials
+// rho[e*Q+q] = sum_j occ[j] u_j(x_q)^2
+template <int NLOC>
+__global__ void k_density(int64_t E, const RefTables* __restrict__ ref, const int32_t* __restrict__ elem,
+                          const double* __restrict__ u, int ld, int N, const double* __restrict__ occ,
+                          double* __restrict__ rho) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  int nd[NLOC];
+#pragma unroll
+  for (int a = 0; a < NLOC; ++a) nd[a] = elem[e * NLOC + a];
+  double r[kQ];
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) r[q] = 0.0;
+  for (int j = 0; j < N; ++j) {
+    double ua[NLOC];
+#pragma unroll
+    for (int a = 0; a < NLOC; ++a) ua[a] = u[(int64_t)nd[a] * ld + j];
+    const double f = occ[j];
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+      double v = 0.0;
+#pragma unroll
+      for (int a = 0; a < NLOC; ++a) v += ref->phi[q][a] * ua[a];
+      r[q] += f * v * v;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) rho[e * kQ + q] = r[q];
+}
+
+// Exchange-correlation potential of Sec. 4 at density rho (rho < 1e-30 -> 0).
+__device__ double vxc_of(double rho, int kind, double alpha) {
+  if (kind == MK_XC_NONE || !(rho >= 1e-30)) return 0.0;
+  const double vx = -cbrt(3.0 * rho / M_PI);
+  if (kind == MK_XC_SLATER) return vx;
+  if (kind == MK_XC_XALPHA) return 1.5 * alpha * vx;
+  // Perdew-Zunger correlation: v_c = eps_c - (r_s/3) d eps_c / d r_s, branch split at r_s = 1
+  const double rs = cbrt(3.0 / (4.0 * M_PI * rho));
+  double ec, dec;
+  if (rs < 1.0) {
+    const double lr = log(rs);
+    ec = 0.0311 * lr - 0.048 + 0.0020 * rs * lr - 0.0116 * rs;
+    dec = 0.0311 / rs + 0.0020 * (lr + 1.0) - 0.0116;
+  } else {
+    const double sq = sqrt(rs);
+    const double den = 1.0 + 1.0529 * sq + 0.3334 * rs;
+    ec = -0.1423 / den;
+    dec = 0.1423 * (0.5 * 1.0529 / sq + 0.3334) / (den * den);
+  }
+  return vx + ec - rs / 3.0 * dec;
+}
+
+// vq[e*Q+q] = w(x_q) + V_xc(rho[e*Q+q])
+template <int NLOC>
+__global__ void k_frozen_potential(int64_t E, const RefTables* __restrict__ ref, const int32_t* __restrict__ elem,
+                                   const double* __restrict__ w, const double* __restrict__ rho, int kind,
+                                   double alpha, double* __restrict__ vq) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  double wa[NLOC];
+#pragma unroll
+  for (int a = 0; a < NLOC; ++a) wa[a] = w ? w[elem[e * NLOC + a]] : 0.0;
+  for (int q = 0; q < kQ; ++q) {
+    double v = 0.0;
+#pragma unroll
+    for (int a = 0; a < NLOC; ++a) v += ref->phi[q][a] * wa[a];
+    vq[e * kQ + q] = v + vxc_of(rho[e * kQ + q], kind, alpha);
+  }
+}
+
+int density(mk_ctx* ctx, const Level& L, const double* u, int ld, int N, const double* occ_host, double* rho,
+            cudaStream_t s) {
+  int err = MK_OK;
+  double* occ = (double*)scratch(ctx, S_OCC, (size_t)(N + 1) * sizeof(double), &err);
+  if (!occ) return err;
+  MK_CUDA(cudaMemcpyAsync(occ, occ_host, N * sizeof(double), cudaMemcpyHostToDevice, s));
+  MK_CUDA(cudaStreamSynchronize(s));
+  const int th = 128, blocks = (int)((L.n_elems + th - 1) / th);
+  if (L.nloc == 4)
+    k_density<4><<<blocks, th, 0, s>>>(L.n_elems, ctx->d_ref[1], L.d_elem, u, ld, N, occ, rho);
+  else
+    k_density<10><<<blocks, th, 0, s>>>(L.n_elems, ctx->d_ref[2], L.d_elem, u, ld, N, occ, rho);
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
+int frozen_potential(mk_ctx* ctx, const Level& L, const double* w, const double* rho, mk_xc xc, double* vq,
+                     cudaStream_t s) {
+  const int th = 128, blocks = (int)((L.n_elems + th - 1) / th);
+  if (L.nloc == 4)
+    k_frozen_potential<4><<<blocks, th, 0, s>>>(L.n_elems, ctx->d_ref[1], L.d_elem, w, rho, xc.kind, xc.alpha, vq);
+  else
+    k_frozen_potential<10><<<blocks, th, 0, s>>>(L.n_elems, ctx->d_ref[2], L.d_elem, w, rho, xc.kind, xc.alpha, vq);
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
+// ------------------------------------------------------------------------------------------------ Poisson pieces
+// F[node(e,a)] += sum_q w_q |det| rho_q phi_a(x_q), one colour at a time
+template <int NLOC>
+__global__ void k_load_colour(const int32_t* __restrict__ celems, int count, const RefTables* __restrict__ ref,
+                              const int32_t* __restrict__ elem, const Geom* __restrict__ geom,
+                              const double* __restrict__ rho, double scale, double* __restrict__ F) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int e = celems[i];
+  const double det = fabs(geom[e].det);
+  double fa[NLOC];
+#pragma unroll
+  for (int a = 0; a < NLOC; ++a) fa[a] = 0.0;
+  for (int q = 0; q < kQ; ++q) {
+    const double c = ref->qw[q] * det * rho[(int64_t)e * kQ + q];
+#pragma unroll
+    for (int a = 0; a < NLOC; ++a) fa[a] += c * ref->phi[q][a];
+  }
+#pragma unroll
+  for (int a = 0; a < NLOC; ++a) F[elem[(int64_t)e * NLOC + a]] += scale * fa[a];
+}
+
+int load_vector(mk_ctx* ctx, const Level& L, const double* rho, double scale, double* F, cudaStream_t s) {
+  MK_CUDA(cudaMemsetAsync(F, 0, L.n_nodes * sizeof(double), s));
+  for (int c = 0; c < L.n_colours; ++c) {
+    const int64_t off = L.colour_off[c], cnt = L.colour_off[c + 1] - off;
+    const int blocks = (int)((cnt + 127) / 128);
+    if (L.nloc == 4)
+      k_load_colour<4><<<blocks, 128, 0, s>>>(L.d_colour_elems + off, (int)cnt, ctx->d_ref[1], L.d_elem, L.d_geom,
+                                             rho, scale, F);
+    else
+      k_load_colour<10><<<blocks, 128, 0, s>>>(L.d_colour_elems + off, (int)cnt, ctx->d_ref[2], L.d_elem, L.d_geom,
+                                              rho, scale, F);
+  }
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
+// moments: part[blk*10 + m] for m = (q0, px, py, pz, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz) with Q_ij = int rho (3 x_i x_j - r^2 d_ij)
+__global__ void k_moments(int64_t E, const RefTables* __restrict__ ref, const Geom* __restrict__ geom,
+                          const double* __restrict__ rho, double* __restrict__ part) {
+  __shared__ double sh[10][kRedThreads];
+  double acc[10];
+#pragma unroll
+  for (int m = 0; m < 10; ++m) acc[m] = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    const Geom g = geom[e];
+    const double det = fabs(g.det);
+    for (int q = 0; q < kQ; ++q) {
+      const double xi = ref->qx[q][0], et = ref->qx[q][1], ze = ref->qx[q][2];
+      const double x = g.x0[0] + g.J[0] * xi + g.J[1] * et + g.J[2] * ze;
+      const double y = g.x0[1] + g.J[3] * xi + g.J[4] * et + g.J[5] * ze;
+      const double z = g.x0[2] + g.J[6] * xi + g.J[7] * et + g.J[8] * ze;
+      const double w = ref->qw[q] * det * rho[e * kQ + q];
+      const double r2 = x * x + y * y + z * z;
+      acc[0] += w;
+      acc[1] += w * x; acc[2] += w * y; acc[3] += w * z;
+      acc[4] += w * (3 * x * x - r2); acc[5] += w * (3 * y * y - r2); acc[6] += w * (3 * z * z - r2);
+      acc[7] += w * 3 * x * y; acc[8] += w * 3 * x * z; acc[9] += w * 3 * y * z;
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 10; ++m) sh[m][threadIdx.x] = acc[m];
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st)
+#pragma unroll
+      for (int m = 0; m < 10; ++m) sh[m][threadIdx.x] += sh[m][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x < 10) part[blockIdx.x * 10 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// w[node] = multipole value on boundary nodes, 0 elsewhere
+__global__ void k_multipole_bc(int64_t n, const double* __restrict__ nodes, const uint8_t* __restrict__ bnd,
+                               const double* __restrict__ mom, int use, double* __restrict__ w) {
+  const int64_t nd = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (nd >= n) return;
+  double v = 0.0;
+  if (bnd[nd] && use) {
+    const double x = nodes[nd * 3], y = nodes[nd * 3 + 1], z = nodes[nd * 3 + 2];
+    const double r2 = x * x + y * y + z * z, r = sqrt(r2);
+    const double quad = mom[4] * x * x + mom[5] * y * y + mom[6] * z * z +
+                        2.0 * (mom[7] * x * y + mom[8] * x * z + mom[9] * y * z);
+    v = mom[0] / r + (mom[1] * x + mom[2] * y + mom[3] * z) / (r2 * r) + 0.5 * quad / (r2 * r2 * r);
+  }
+  w[nd] = v;
+}
+
+int multipole_boundary(mk_ctx* ctx, const Level& L, const double* rho, const double* d_nodes, int bc, double* w,
+                       cudaStream_t s) {
+  int err = MK_OK;
+  const int nblk = red_blocks(ctx);
+  double* part = (double*)scratch(ctx, S_RED, (size_t)nblk * 10 * sizeof(double), &err);
+  double* mom = (double*)scratch(ctx, S_SCAL, 64 * sizeof(double), &err);
+  if (!part || !mom) return err;
+  k_moments<<<nblk, kRedThreads, 0, s>>>(L.n_elems, ctx->d_ref[L.order], L.d_geom, rho, part);
+  k_sum_partials<<<1, 64, 0, s>>>(part, nblk, 10, mom);
+  k_multipole_bc<<<(int)((L.n_nodes + 255) / 256), 256, 0, s>>>(L.n_nodes, d_nodes, L.d_boundary, mom,
+                                                                 bc == MK_BC_MULTIPOLE, w);
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
+}  // namespace mk

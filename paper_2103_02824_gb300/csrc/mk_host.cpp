@@ -1,0 +1,545 @@
+// Host side of the mk library: errors, context, scratch, reference-element tables and mesh preprocessing (A0).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "mk_internal.h"
+
+namespace mk {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+// ------------------------------------------------------------------------------------------------ quadrature
+// Jacobi polynomial P_n^{(a,b)}(x) and its derivative by the three-term recurrence.
+static void jacobi_eval(int n, double a, double b, double x, double* p, double* dp) {
+  double p0 = 1.0, p1 = 0.5 * (a - b + (a + b + 2.0) * x);
+  if (n == 0) { *p = 1.0; *dp = 0.0; return; }
+  // derivative: d/dx P_n^{(a,b)} = (n+a+b+1)/2 P_{n-1}^{(a+1,b+1)}
+  auto raw = [](int n, double a, double b, double x) {
+    double q0 = 1.0, q1 = 0.5 * (a - b + (a + b + 2.0) * x);
+    if (n == 0) return q0;
+    for (int k = 2; k <= n; ++k) {
+      double s = 2.0 * k + a + b;
+      double c1 = 2.0 * k * (k + a + b) * (s - 2.0);
+      double c2 = (s - 1.0) * (s * (s - 2.0) * x + a * a - b * b);
+      double c3 = 2.0 * (k + a - 1.0) * (k + b - 1.0) * s;
+      double q2 = (c2 * q1 - c3 * q0) / c1;
+      q0 = q1;
+      q1 = q2;
+    }
+    return q1;
+  };
+  (void)p0; (void)p1;
+  *p = raw(n, a, b, x);
+  *dp = (n == 0) ? 0.0 : 0.5 * (n + a + b + 1.0) * raw(n - 1, a + 1.0, b + 1.0, x);
+}
+
+// n-point Gauss-Jacobi rule on [-1,1] for (1-x)^a (1+x)^b: Newton iteration on P_n with deflation of the roots
+// already found, weights from w_i = C / ((1 - x_i^2) P_n'(x_i)^2).
+void gauss_jacobi_newton(int n, double a, double b, double* x, double* w) {
+  for (int i = 0; i < n; ++i) {
+    double r = -std::cos((2.0 * i + 1.0) * M_PI / (2.0 * n));  // Chebyshev guess, ascending
+    if (i > 0 && r <= x[i - 1]) r = x[i - 1] + 1e-3;
+    for (int it = 0; it < 100; ++it) {
+      double p, dp;
+      jacobi_eval(n, a, b, r, &p, &dp);
+      double s = 0.0;
+      for (int j = 0; j < i; ++j) s += 1.0 / (r - x[j]);
+      double delta = p / (dp - s * p);
+      r -= delta;
+      if (std::fabs(delta) < 1e-16 * std::max(1.0, std::fabs(r))) break;
+    }
+    x[i] = r;
+  }
+  double C = std::exp(std::lgamma(n + a + 1.0) + std::lgamma(n + b + 1.0) - std::lgamma(n + a + b + 1.0) -
+                      std::lgamma(n + 1.0)) *
+             std::pow(2.0, a + b + 1.0);
+  for (int i = 0; i < n; ++i) {
+    double p, dp;
+    jacobi_eval(n, a, b, x[i], &p, &dp);
+    w[i] = C / ((1.0 - x[i] * x[i]) * dp * dp);
+  }
+}
+
+static const int kEdgeA[6] = {0, 0, 0, 1, 1, 2};
+static const int kEdgeB[6] = {1, 2, 3, 2, 3, 3};
+
+static void basis_host(int order, const double lam[4], double* phi, double (*dphi)[3]) {
+  static const double G[4][3] = {{-1, -1, -1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  if (order == 1) {
+    for (int a = 0; a < 4; ++a) {
+      phi[a] = lam[a];
+      if (dphi) for (int k = 0; k < 3; ++k) dphi[a][k] = G[a][k];
+    }
+    return;
+  }
+  for (int a = 0; a < 4; ++a) {
+    phi[a] = lam[a] * (2.0 * lam[a] - 1.0);
+    if (dphi) for (int k = 0; k < 3; ++k) dphi[a][k] = (4.0 * lam[a] - 1.0) * G[a][k];
+  }
+  for (int e = 0; e < 6; ++e) {
+    int a = kEdgeA[e], b = kEdgeB[e];
+    phi[4 + e] = 4.0 * lam[a] * lam[b];
+    if (dphi) for (int k = 0; k < 3; ++k) dphi[4 + e][k] = 4.0 * (lam[b] * G[a][k] + lam[a] * G[b][k]);
+  }
+}
+
+void build_ref_tables(int order, RefTables* t) {
+  std::memset(t, 0, sizeof(*t));
+  t->order = order;
+  t->nloc = order == 1 ? 4 : 10;
+  t->npack = t->nloc * (t->nloc + 1) / 2;
+  double u[3], wu[3], v[3], wv[3], s[3], ws[3];
+  gauss_jacobi_newton(3, 2.0, 0.0, u, wu);
+  gauss_jacobi_newton(3, 1.0, 0.0, v, wv);
+  gauss_jacobi_newton(3, 0.0, 0.0, s, ws);
+  for (int i = 0; i < 3; ++i) {  // map to [0,1] with weight (1-x)^a
+    u[i] = 0.5 * (1.0 + u[i]); wu[i] *= std::pow(2.0, -3.0);
+    v[i] = 0.5 * (1.0 + v[i]); wv[i] *= std::pow(2.0, -2.0);
+    s[i] = 0.5 * (1.0 + s[i]); ws[i] *= 0.5;
+  }
+  int q = 0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      for (int k = 0; k < 3; ++k, ++q) {
+        t->qx[q][0] = u[i];
+        t->qx[q][1] = v[j] * (1.0 - u[i]);
+        t->qx[q][2] = s[k] * (1.0 - u[i]) * (1.0 - v[j]);
+        t->qw[q] = wu[i] * wv[j] * ws[k];
+      }
+  const int n = t->nloc;
+  static const int I6[6] = {0, 1, 2, 0, 0, 1}, J6[6] = {0, 1, 2, 1, 2, 2};
+  for (q = 0; q < kQ; ++q) {
+    double lam[4] = {1.0 - t->qx[q][0] - t->qx[q][1] - t->qx[q][2], t->qx[q][0], t->qx[q][1], t->qx[q][2]};
+    double phi[kMaxLoc], dphi[kMaxLoc][3];
+    basis_host(order, lam, phi, dphi);
+    for (int a = 0; a < n; ++a) t->phi[q][a] = phi[a];
+    for (int a = 0; a < n; ++a)
+      for (int b = a; b < n; ++b) {
+        int p = sym_index(a, b, n);
+        t->mass[p] += t->qw[q] * phi[a] * phi[b];
+        for (int c = 0; c < 6; ++c) {
+          int i = I6[c], j = J6[c];
+          double v2 = dphi[a][i] * dphi[b][j];
+          if (i != j) v2 += dphi[a][j] * dphi[b][i];
+          t->stiff[c][p] += t->qw[q] * v2;
+        }
+      }
+  }
+  for (int a = 0; a < 4; ++a) t->node_bary[a][a] = 1.0;
+  if (order == 2)
+    for (int e = 0; e < 6; ++e) {
+      t->node_bary[4 + e][kEdgeA[e]] = 0.5;
+      t->node_bary[4 + e][kEdgeB[e]] = 0.5;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------ scratch
+void* scratch(mk_ctx* ctx, int slot, size_t bytes, int* err) {
+  if ((int)ctx->slot_ptr.size() < S_COUNT) {
+    ctx->slot_ptr.assign(S_COUNT, nullptr);
+    ctx->slot_size.assign(S_COUNT, 0);
+  }
+  if (bytes == 0) bytes = 16;
+  if (ctx->slot_size[slot] >= bytes) return ctx->slot_ptr[slot];
+  if (ctx->slot_ptr[slot]) {
+    cudaDeviceSynchronize();  // growth is rare; make sure no in-flight work still uses the old buffer
+    cudaFree(ctx->slot_ptr[slot]);
+    ctx->slot_ptr[slot] = nullptr;
+    ctx->slot_size[slot] = 0;
+  }
+  size_t want = (bytes + 255) / 256 * 256;
+  void* p = nullptr;
+  if (cudaMalloc(&p, want) != cudaSuccess) {
+    cudaGetLastError();
+    *err = fail(MK_ERR_OOM, "scratch allocation of " + std::to_string(want) + " bytes failed");
+    return nullptr;
+  }
+  ctx->slot_ptr[slot] = p;
+  ctx->slot_size[slot] = want;
+  return p;
+}
+
+// ------------------------------------------------------------------------------------------------ mesh (A0)
+static double det3(const double* J) {
+  return J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) + J[2] * (J[3] * J[7] - J[4] * J[6]);
+}
+
+static void inv3(const double* J, double det, double* Ji) {
+  Ji[0] = (J[4] * J[8] - J[5] * J[7]) / det;
+  Ji[1] = (J[2] * J[7] - J[1] * J[8]) / det;
+  Ji[2] = (J[1] * J[5] - J[2] * J[4]) / det;
+  Ji[3] = (J[5] * J[6] - J[3] * J[8]) / det;
+  Ji[4] = (J[0] * J[8] - J[2] * J[6]) / det;
+  Ji[5] = (J[2] * J[3] - J[0] * J[5]) / det;
+  Ji[6] = (J[3] * J[7] - J[4] * J[6]) / det;
+  Ji[7] = (J[1] * J[6] - J[0] * J[7]) / det;
+  Ji[8] = (J[0] * J[4] - J[1] * J[3]) / det;
+}
+
+static int build_level(const mk_mesh_desc* d, Level& L, const char* name) {
+  MK_ARG(d && d->coords && d->tets, std::string(name) + ": null mesh arrays");
+  MK_ARG(d->order == 1 || d->order == 2, std::string(name) + ": order must be 1 or 2");
+  MK_ARG(d->n_vertices > 0 && d->n_elems > 0 && d->n_vertices < (1LL << 30) && d->n_elems < (1LL << 30),
+         std::string(name) + ": bad sizes");
+  const int64_t nv = d->n_vertices, E = d->n_elems;
+  L.order = d->order;
+  L.nloc = d->order == 1 ? 4 : 10;
+  L.n_vertices = nv;
+  L.n_elems = E;
+  const int nloc = L.nloc;
+  for (int64_t i = 0; i < 4 * E; ++i)
+    MK_ARG(d->tets[i] >= 0 && d->tets[i] < nv, std::string(name) + ": vertex index out of range");
+  L.elem.assign(E * nloc, 0);
+  for (int64_t e = 0; e < E; ++e)
+    for (int a = 0; a < 4; ++a) L.elem[e * nloc + a] = d->tets[e * 4 + a];
+  std::vector<int64_t> edge_a, edge_b;
+  std::vector<uint64_t> uniq_key;     // sorted edge keys
+  std::vector<int32_t> uniq_number;   // edge number of each sorted key
+  if (d->order == 2) {
+    const int64_t ne = 6 * E;
+    std::vector<uint64_t> key(ne);
+    for (int64_t e = 0; e < E; ++e)
+      for (int k = 0; k < 6; ++k) {
+        uint64_t a = d->tets[e * 4 + kEdgeA[k]], b = d->tets[e * 4 + kEdgeB[k]];
+        if (a > b) std::swap(a, b);
+        key[e * 6 + k] = a * (uint64_t)nv + b;
+      }
+    std::vector<int64_t> idx(ne);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) { return key[x] < key[y]; });
+    std::vector<int64_t> first;  // first occurrence of each unique key (sorted by key)
+    for (int64_t i = 0; i < ne; ++i)
+      if (i == 0 || key[idx[i]] != key[idx[i - 1]]) {
+        uniq_key.push_back(key[idx[i]]);
+        first.push_back(idx[i]);
+      }
+    const int64_t nu = (int64_t)uniq_key.size();
+    std::vector<int64_t> ord(nu);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) { return first[x] < first[y]; });
+    uniq_number.assign(nu, 0);
+    edge_a.assign(nu, 0);
+    edge_b.assign(nu, 0);
+    for (int64_t r = 0; r < nu; ++r) {
+      uniq_number[ord[r]] = (int32_t)r;
+      edge_a[r] = uniq_key[ord[r]] / nv;
+      edge_b[r] = uniq_key[ord[r]] % nv;
+    }
+    for (int64_t i = 0, u = -1; i < ne; ++i) {
+      if (i == 0 || key[idx[i]] != key[idx[i - 1]]) ++u;
+      int64_t e = idx[i] / 6, k = idx[i] % 6;
+      L.elem[e * nloc + 4 + k] = (int32_t)(nv + uniq_number[u]);
+    }
+  }
+  const int64_t n_nodes = nv + (int64_t)edge_a.size();
+  L.n_nodes = n_nodes;
+  L.nodes.assign(n_nodes * 3, 0.0);
+  for (int64_t i = 0; i < nv * 3; ++i) L.nodes[i] = d->coords[i];
+  for (size_t r = 0; r < edge_a.size(); ++r)
+    for (int k = 0; k < 3; ++k)
+      L.nodes[(nv + r) * 3 + k] = 0.5 * (d->coords[edge_a[r] * 3 + k] + d->coords[edge_b[r] * 3 + k]);
+  // boundary: faces that belong to exactly one tetrahedron
+  struct Face { int32_t v[3]; };
+  std::vector<Face> faces(4 * E);
+  static const int F[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+  for (int64_t e = 0; e < E; ++e)
+    for (int f = 0; f < 4; ++f) {
+      Face x{{d->tets[e * 4 + F[f][0]], d->tets[e * 4 + F[f][1]], d->tets[e * 4 + F[f][2]]}};
+      std::sort(x.v, x.v + 3);
+      faces[e * 4 + f] = x;
+    }
+  auto lessF = [](const Face& p, const Face& q) {
+    return std::lexicographical_compare(p.v, p.v + 3, q.v, q.v + 3);
+  };
+  std::sort(faces.begin(), faces.end(), lessF);
+  L.boundary.assign(n_nodes, 0);
+  for (size_t i = 0; i < faces.size();) {
+    size_t j = i + 1;
+    while (j < faces.size() && !lessF(faces[i], faces[j]) && !lessF(faces[j], faces[i])) ++j;
+    MK_ARG(j - i <= 2, std::string(name) + ": a face is shared by more than two tetrahedra");
+    if (j - i == 1) {
+      const Face& f = faces[i];
+      for (int k = 0; k < 3; ++k) L.boundary[f.v[k]] = 1;
+      if (d->order == 2) {
+        static const int P[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+        for (auto& pr : P) {
+          uint64_t k2 = (uint64_t)f.v[pr[0]] * nv + f.v[pr[1]];
+          auto it = std::lower_bound(uniq_key.begin(), uniq_key.end(), k2);
+          L.boundary[nv + uniq_number[it - uniq_key.begin()]] = 1;
+        }
+      }
+    }
+    i = j;
+  }
+  L.node_to_free.assign(n_nodes, -1);
+  L.free_idx.clear();
+  for (int64_t i = 0; i < n_nodes; ++i)
+    if (!L.boundary[i]) {
+      L.node_to_free[i] = (int32_t)L.free_idx.size();
+      L.free_idx.push_back((int32_t)i);
+    }
+  L.n_free = (int64_t)L.free_idx.size();
+  // greedy colouring: elements in index order, smallest colour unused by earlier vertex-sharing elements
+  std::vector<int64_t> vcount(nv + 1, 0);
+  for (int64_t i = 0; i < 4 * E; ++i) vcount[d->tets[i] + 1]++;
+  for (int64_t v = 0; v < nv; ++v) vcount[v + 1] += vcount[v];
+  std::vector<int32_t> v2e(4 * E);
+  {
+    std::vector<int64_t> pos(vcount.begin(), vcount.end() - 1);
+    for (int64_t e = 0; e < E; ++e)
+      for (int a = 0; a < 4; ++a) v2e[pos[d->tets[e * 4 + a]]++] = (int32_t)e;
+  }
+  L.colour.assign(E, -1);
+  std::vector<int64_t> stamp(256, -1);
+  int ncol = 0;
+  for (int64_t e = 0; e < E; ++e) {
+    for (int a = 0; a < 4; ++a) {
+      int32_t v = d->tets[e * 4 + a];
+      for (int64_t k = vcount[v]; k < vcount[v + 1]; ++k) {
+        int c = L.colour[v2e[k]];
+        if (c >= 0) {
+          if (c >= (int)stamp.size()) stamp.resize(2 * c + 2, -1);
+          stamp[c] = e;
+        }
+      }
+    }
+    int c = 0;
+    while (c < (int)stamp.size() && stamp[c] == e) ++c;
+    if (c >= (int)stamp.size()) stamp.resize(2 * c + 2, -1);
+    L.colour[e] = c;
+    ncol = std::max(ncol, c + 1);
+  }
+  L.n_colours = ncol;
+  L.colour_off.assign(ncol + 1, 0);
+  for (int64_t e = 0; e < E; ++e) L.colour_off[L.colour[e] + 1]++;
+  for (int c = 0; c < ncol; ++c) L.colour_off[c + 1] += L.colour_off[c];
+  // geometry
+  L.geom.resize(E);
+  for (int64_t e = 0; e < E; ++e) {
+    Geom& g = L.geom[e];
+    const double* x0 = &d->coords[d->tets[e * 4] * 3];
+    for (int c = 0; c < 3; ++c) {
+      const double* xc = &d->coords[d->tets[e * 4 + c + 1] * 3];
+      for (int r = 0; r < 3; ++r) g.J[r * 3 + c] = xc[r] - x0[r];
+    }
+    for (int r = 0; r < 3; ++r) g.x0[r] = x0[r];
+    g.det = det3(g.J);
+    MK_ARG(g.det > 0.0, std::string(name) + ": element " + std::to_string(e) + " has det J <= 0");
+    inv3(g.J, g.det, g.Jinv);
+  }
+  return MK_OK;
+}
+
+template <class T>
+static int upload(T** dst, const T* src, size_t n) {
+  if (n == 0) n = 1;
+  if (cudaMalloc(dst, n * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MK_ERR_OOM, "device allocation failed in mesh upload");
+  }
+  if (src) MK_CUDA(cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+  return MK_OK;
+}
+
+static int upload_level(Level& L) {
+  MK_TRY(upload(&L.d_elem, L.elem.data(), L.elem.size()));
+  std::vector<int32_t> ce(L.n_elems);
+  std::vector<int64_t> pos(L.colour_off.begin(), L.colour_off.end() - 1);
+  for (int64_t e = 0; e < L.n_elems; ++e) ce[pos[L.colour[e]]++] = (int32_t)e;
+  MK_TRY(upload(&L.d_colour_elems, ce.data(), ce.size()));
+  MK_TRY(upload(&L.d_boundary, L.boundary.data(), L.boundary.size()));
+  MK_TRY(upload(&L.d_free_idx, L.free_idx.data(), L.free_idx.size()));
+  MK_TRY(upload(&L.d_node_to_free, L.node_to_free.data(), L.node_to_free.size()));
+  MK_TRY(upload(&L.d_geom, L.geom.data(), L.geom.size()));
+  MK_TRY(upload(&L.d_nodes, L.nodes.data(), L.nodes.size()));
+  return MK_OK;
+}
+
+static void free_level(Level& L) {
+  cudaFree(L.d_elem); cudaFree(L.d_colour_elems); cudaFree(L.d_boundary); cudaFree(L.d_free_idx);
+  cudaFree(L.d_node_to_free); cudaFree(L.d_geom); cudaFree(L.d_nodes);
+  L.d_nodes = nullptr;
+  L.d_elem = L.d_colour_elems = L.d_free_idx = L.d_node_to_free = nullptr;
+  L.d_boundary = nullptr;
+  L.d_geom = nullptr;
+}
+
+int build_patches(mk_mesh* m);  // mk_patches.cpp
+void free_patches(mk::Patches& p);
+
+}  // namespace mk
+
+using namespace mk;
+
+extern "C" {
+
+int mk_last_error(char* buf, size_t len) {
+  if (!buf || len == 0) return (int)g_err.size();
+  size_t n = std::min(len - 1, g_err.size());
+  std::memcpy(buf, g_err.data(), n);
+  buf[n] = 0;
+  return (int)g_err.size();
+}
+
+const char* mk_version(void) { return "mk 0.1 (sm_103a)"; }
+
+int mk_ctx_create(mk_ctx** out, int device) {
+  MK_ARG(out, "mk_ctx_create: null out");
+  *out = nullptr;
+  int n = 0;
+  MK_CUDA(cudaGetDeviceCount(&n));
+  MK_ARG(device >= 0 && device < n, "mk_ctx_create: bad device id");
+  MK_CUDA(cudaSetDevice(device));
+  mk_ctx* c = new mk_ctx();
+  c->device = device;
+  MK_CUDA(cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, device));
+  for (int order = 1; order <= 2; ++order) {
+    build_ref_tables(order, &c->h_ref[order]);
+    MK_TRY(upload(&c->d_ref[order], &c->h_ref[order], 1));
+  }
+  *out = c;
+  return MK_OK;
+}
+
+int mk_ctx_destroy(mk_ctx* c) {
+  if (!c) return MK_OK;
+  cudaSetDevice(c->device);
+  for (void* p : c->slot_ptr) cudaFree(p);
+  for (int o = 1; o <= 2; ++o) cudaFree(c->d_ref[o]);
+  if (c->pinned) cudaFreeHost(c->pinned);
+  delete c;
+  return MK_OK;
+}
+
+int mk_mesh_upload(mk_ctx* ctx, const mk_mesh_desc* fine, const mk_mesh_desc* coarse, const int32_t* fine_parent,
+                   mk_mesh** out) {
+  MK_ARG(ctx && fine && coarse && fine_parent && out, "mk_mesh_upload: null argument");
+  *out = nullptr;
+  MK_ARG(fine->order == coarse->order, "mk_mesh_upload: fine and coarse orders differ");
+  MK_CUDA(cudaSetDevice(ctx->device));
+  mk_mesh* m = new mk_mesh();
+  m->ctx = ctx;
+  int r = build_level(fine, m->fine, "fine");
+  if (r == MK_OK) r = build_level(coarse, m->coarse, "coarse");
+  if (r != MK_OK) { delete m; return r; }
+  const Level& F = m->fine;
+  const Level& C = m->coarse;
+  m->parent.assign(fine_parent, fine_parent + F.n_elems);
+  for (int32_t p : m->parent)
+    if (p < 0 || p >= C.n_elems) { delete m; return fail(MK_ERR_INVALID_ARG, "mk_mesh_upload: parent out of range"); }
+  // prolongation rows: first occurrence of each fine node, coarse basis of the parent evaluated there
+  const int nloc = F.nloc;
+  std::vector<int64_t> first(F.n_nodes, -1);
+  for (int64_t i = 0; i < F.n_elems * nloc; ++i)
+    if (first[F.elem[i]] < 0) first[F.elem[i]] = i;
+  std::vector<int32_t> P_off(F.n_nodes + 1, 0), P_col;
+  std::vector<double> P_val;
+  for (int64_t nd = 0; nd < F.n_nodes; ++nd) {
+    if (first[nd] < 0) { delete m; return fail(MK_ERR_INVALID_ARG, "mk_mesh_upload: unused fine node"); }
+    int64_t e = first[nd] / nloc;
+    int32_t T = m->parent[e];
+    const Geom& g = C.geom[T];
+    double dx[3] = {F.nodes[nd * 3] - g.x0[0], F.nodes[nd * 3 + 1] - g.x0[1], F.nodes[nd * 3 + 2] - g.x0[2]};
+    double s[3];
+    for (int rr = 0; rr < 3; ++rr) s[rr] = g.Jinv[rr * 3] * dx[0] + g.Jinv[rr * 3 + 1] * dx[1] + g.Jinv[rr * 3 + 2] * dx[2];
+    double lam[4] = {1.0 - s[0] - s[1] - s[2], s[0], s[1], s[2]};
+    for (double l : lam)
+      if (l < -1e-9 || l > 1.0 + 1e-9) { delete m; return fail(MK_ERR_INVALID_ARG, "mk_mesh_upload: fine element outside its parent"); }
+    double phi[kMaxLoc];
+    basis_host(C.order, lam, phi, nullptr);
+    for (int b = 0; b < C.nloc; ++b) {
+      int32_t cn = C.elem[(int64_t)T * C.nloc + b];
+      int32_t cf = C.node_to_free[cn];
+      if (cf >= 0 && std::fabs(phi[b]) > 1e-12) {
+        P_col.push_back(cf);
+        P_val.push_back(phi[b]);
+      }
+    }
+    P_off[nd + 1] = (int32_t)P_col.size();
+  }
+  // transpose: coarse free DOF -> fine nodes (increasing)
+  std::vector<int32_t> PT_off(C.n_free + 1, 0), PT_col(P_col.size());
+  std::vector<double> PT_val(P_col.size());
+  for (int32_t c : P_col) PT_off[c + 1]++;
+  for (int64_t k = 0; k < C.n_free; ++k) PT_off[k + 1] += PT_off[k];
+  {
+    std::vector<int32_t> pos(PT_off.begin(), PT_off.end() - 1);
+    for (int64_t nd = 0; nd < F.n_nodes; ++nd)
+      for (int32_t k = P_off[nd]; k < P_off[nd + 1]; ++k) {
+        int32_t p = pos[P_col[k]]++;
+        PT_col[p] = (int32_t)nd;
+        PT_val[p] = P_val[k];
+      }
+  }
+  m->PT_nnz = (int64_t)PT_col.size();
+  std::vector<int32_t> ch_off(C.n_elems + 1, 0), ch(F.n_elems);
+  for (int32_t p : m->parent) ch_off[p + 1]++;
+  for (int64_t k = 0; k < C.n_elems; ++k) ch_off[k + 1] += ch_off[k];
+  {
+    std::vector<int32_t> pos(ch_off.begin(), ch_off.end() - 1);
+    for (int64_t e = 0; e < F.n_elems; ++e) ch[pos[m->parent[e]]++] = (int32_t)e;
+  }
+  r = upload_level(m->fine);
+  if (r == MK_OK) r = upload_level(m->coarse);
+  if (r == MK_OK) r = upload(&m->d_P_off, P_off.data(), P_off.size());
+  if (r == MK_OK) r = upload(&m->d_P_col, P_col.data(), P_col.size());
+  if (r == MK_OK) r = upload(&m->d_P_val, P_val.data(), P_val.size());
+  if (r == MK_OK) r = upload(&m->d_PT_off, PT_off.data(), PT_off.size());
+  if (r == MK_OK) r = upload(&m->d_PT_col, PT_col.data(), PT_col.size());
+  if (r == MK_OK) r = upload(&m->d_PT_val, PT_val.data(), PT_val.size());
+  if (r == MK_OK) r = upload(&m->d_child_off, ch_off.data(), ch_off.size());
+  if (r == MK_OK) r = upload(&m->d_child, ch.data(), ch.size());
+  if (r == MK_OK) r = build_patches(m);
+  if (r != MK_OK) { mk_mesh_destroy(m); return r; }
+  *out = m;
+  return MK_OK;
+}
+
+int mk_mesh_destroy(mk_mesh* m) {
+  if (!m) return MK_OK;
+  cudaSetDevice(m->ctx->device);
+  free_level(m->fine);
+  free_level(m->coarse);
+  cudaFree(m->d_P_off); cudaFree(m->d_P_col); cudaFree(m->d_P_val);
+  cudaFree(m->d_PT_off); cudaFree(m->d_PT_col); cudaFree(m->d_PT_val);
+  cudaFree(m->d_child_off); cudaFree(m->d_child);
+  free_patches(m->patches);
+  delete m;
+  return MK_OK;
+}
+
+int mk_mesh_get_info(const mk_mesh* m, mk_mesh_info* info) {
+  MK_ARG(m && info, "mk_mesh_get_info: null argument");
+  info->order = m->fine.order;
+  info->nloc = m->fine.nloc;
+  info->n_nodes = m->fine.n_nodes;
+  info->n_free = m->fine.n_free;
+  info->n_elems = m->fine.n_elems;
+  info->n_colours = m->fine.n_colours;
+  info->n_nodes_coarse = m->coarse.n_nodes;
+  info->n_free_coarse = m->coarse.n_free;
+  info->n_elems_coarse = m->coarse.n_elems;
+  info->n_quad = kQ;
+  return MK_OK;
+}
+
+int mk_mesh_get_topology(const mk_mesh* m, int level, double* nodes, uint8_t* boundary, int32_t* elem,
+                         int32_t* colour) {
+  MK_ARG(m && (level == 0 || level == 1), "mk_mesh_get_topology: bad argument");
+  const Level& L = level == 0 ? m->fine : m->coarse;
+  if (nodes) std::memcpy(nodes, L.nodes.data(), L.nodes.size() * sizeof(double));
+  if (boundary) std::memcpy(boundary, L.boundary.data(), L.boundary.size());
+  if (elem) std::memcpy(elem, L.elem.data(), L.elem.size() * sizeof(int32_t));
+  if (colour) std::memcpy(colour, L.colour.data(), L.colour.size() * sizeof(int32_t));
+  return MK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,172 @@
+// Internal declarations of the mk library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mk.h"
+
+namespace mk {
+
+// ------------------------------------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+
+#define MK_CUDA(call)                                                                          \
+  do {                                                                                         \
+    cudaError_t _e = (call);                                                                   \
+    if (_e != cudaSuccess)                                                                     \
+      return ::mk::fail(MK_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(_e));       \
+  } while (0)
+
+#define MK_TRY(call)           \
+  do {                         \
+    int _r = (call);           \
+    if (_r != MK_OK) return _r; \
+  } while (0)
+
+#define MK_ARG(cond, msg)                                                     \
+  do {                                                                        \
+    if (!(cond)) return ::mk::fail(MK_ERR_INVALID_ARG, std::string(msg));      \
+  } while (0)
+
+constexpr int kQ = 27;          // quadrature points per element (3x3x3 conical product, exact to degree 5)
+constexpr int kMaxLoc = 10;     // P2
+constexpr int kMaxPacked = 55;  // packed symmetric 10x10
+
+// Packed upper-triangular index of (a,b), a<=b, for an n x n symmetric matrix.
+__host__ __device__ inline int sym_index(int a, int b, int n) {
+  if (a > b) { int t = a; a = b; b = t; }
+  return a * n - a * (a - 1) / 2 + (b - a);
+}
+
+// Reference-element tables for one order (device copy lives in the context).
+struct RefTables {
+  int order, nloc, npack;
+  double qw[kQ];                     // weights on the reference tetrahedron (sum 1/6)
+  double qx[kQ][3];                  // points
+  double phi[kQ][kMaxLoc];           // basis values at the points
+  double mass[kMaxPacked];           // int_ref phi_a phi_b (packed)
+  double stiff[6][kMaxPacked];       // int_ref (d_i phi_a d_j phi_b + [i!=j] d_j phi_a d_i phi_b), (ij) = 00,11,22,01,02,12
+  double node_bary[kMaxLoc][4];      // barycentrics of the local nodes
+};
+
+void build_ref_tables(int order, RefTables* t);           // host: Gauss-Jacobi by Newton iteration
+void gauss_jacobi_newton(int n, double a, double b, double* x, double* w);
+
+// Per-element geometry (FP64): x = x0 + J xi.
+struct Geom {
+  double J[9];     // row-major J[r][c] = (x_{c+1} - x_0)_r
+  double Jinv[9];
+  double det;
+  double x0[3];
+};
+
+struct Level {
+  int order = 0, nloc = 0;
+  int64_t n_vertices = 0, n_nodes = 0, n_free = 0, n_elems = 0;
+  int n_colours = 0;
+  // host copies (A0 results)
+  std::vector<double> nodes;          // [n_nodes*3]
+  std::vector<uint8_t> boundary;      // [n_nodes]
+  std::vector<int32_t> elem;          // [E*nloc]
+  std::vector<int32_t> colour;        // [E]
+  std::vector<int32_t> free_idx;      // [n_free] node of each free DOF
+  std::vector<int32_t> node_to_free;  // [n_nodes] free index or -1
+  std::vector<int64_t> colour_off;    // [n_colours+1] into colour_elems
+  std::vector<Geom> geom;             // [E]
+  // device copies
+  int32_t* d_elem = nullptr;
+  int32_t* d_colour_elems = nullptr;  // element ids sorted by colour (stable)
+  uint8_t* d_boundary = nullptr;
+  int32_t* d_free_idx = nullptr;
+  int32_t* d_node_to_free = nullptr;
+  Geom* d_geom = nullptr;
+  double* d_nodes = nullptr;          // [n_nodes*3]
+};
+
+// Element patches for the FP32 operator (owner-computes scatter with a fixed-order halo sum).
+struct Patches {
+  int n_patches = 0, max_elems = 0, max_nodes = 0;
+  int64_t n_halo_slots = 0, n_shared_nodes = 0;
+  int32_t* d_patch_elem_off = nullptr;   // [P+1] into patch element arrays (elements reordered by patch)
+  int32_t* d_patch_node_off = nullptr;   // [P+1] into patch node arrays
+  int32_t* d_elem_id = nullptr;          // [E] original element id of each patch-ordered element
+  uint16_t* d_local_conn = nullptr;      // [E*nloc] local node index inside its patch
+  int32_t* d_node_target = nullptr;      // [sum nodes] >= 0: global node written directly; < 0: -(halo slot)-1
+  int32_t* d_node_global = nullptr;      // [sum nodes] global node id (for gathers)
+  int32_t* d_inc_off = nullptr;          // [sum nodes + P] per local node: offsets into incidence list (per patch)
+  uint16_t* d_inc = nullptr;             // [E*nloc] (local element * nloc + local slot) of each incidence
+  int32_t* d_shared_node = nullptr;      // [n_shared] global node
+  int32_t* d_shared_off = nullptr;       // [n_shared+1] into halo slots (slots of one node in patch order)
+};
+
+}  // namespace mk
+
+struct mk_ctx {
+  int device = 0;
+  int n_sms = 0;
+  mk::RefTables* d_ref[3] = {nullptr, nullptr, nullptr};  // by order (1, 2)
+  mk::RefTables h_ref[3];
+  // scratch: named slots grown on demand
+  std::vector<void*> slot_ptr;
+  std::vector<size_t> slot_size;
+  void* pinned = nullptr;  // small pinned host buffer for reports
+  size_t pinned_size = 0;
+};
+
+struct mk_mesh {
+  mk_ctx* ctx = nullptr;
+  mk::Level fine, coarse;
+  std::vector<int32_t> parent;
+  // prolongation P: fine node -> coarse free DOF (CSR over fine nodes)
+  int32_t* d_P_off = nullptr;
+  int32_t* d_P_col = nullptr;
+  double* d_P_val = nullptr;
+  // restriction P^T: coarse free DOF -> fine nodes (CSR over coarse free DOF, fine nodes increasing)
+  int32_t* d_PT_off = nullptr;
+  int32_t* d_PT_col = nullptr;
+  double* d_PT_val = nullptr;
+  int64_t PT_nnz = 0;
+  // children of each coarse element (CSR, fine element ids increasing)
+  int32_t* d_child_off = nullptr;
+  int32_t* d_child = nullptr;
+  mk::Patches patches;
+  // Jacobi diagonal pieces: diagonals of K/2 and M per node are molecule-independent
+};
+
+namespace mk {
+
+// scratch slots
+enum Slot : int {
+  S_ELEM64 = 0,   // element matrices FP64 [E*55]
+  S_ELEM64B,      // second FP64 element matrix set
+  S_ELEM32,       // FP32 element matrices (patch order)
+  S_DIAG64,       // Jacobi diagonal FP64 [n_nodes]
+  S_DIAG32,
+  S_R64, S_Z64, S_P64, S_Q64,   // PCG vectors FP64 [n_nodes*ld]
+  S_R32, S_P32, S_Q32, S_X32,   // PCG vectors FP32
+  S_HALO,         // halo partial sums
+  S_RED,          // reduction partials
+  S_SCAL,         // per-column scalars (device)
+  S_RHO,          // rho at quadrature points
+  S_VEC1, S_VEC2, S_VEC3,       // misc fine vectors
+  S_EIG,          // eigensolver workspace
+  S_COARSE,       // coarse element matrices
+  S_NUC,          // nuclei (Z, R)
+  S_OCC,          // occupations
+  S_COEF,         // small per-column coefficient arrays
+  S_VEC4, S_VEC5,
+  S_GRAM,
+  S_COUNT
+};
+void* scratch(mk_ctx* ctx, int slot, size_t bytes, int* err);
+
+// device helpers implemented in .cu files
+int launch_element_matrices(mk_ctx* ctx, const mk_mesh* m, const Level& L, const mk_molecule* mol, double half_k,
+                            double vext_scale, double mass_shift, const double* vq, double* out, cudaStream_t s);
+
+}  // namespace mk

@@ -1,0 +1,436 @@
+// Boundary-value problems on the fine mesh (Algorithm 1, steps 5 and 6): multi-RHS PCG on the matrix-free
+// element-by-element operator, the Hartree Poisson solve, the right-hand sides, and the shift estimate.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "mk_device.cuh"
+
+namespace mk {
+
+int restrict_to_coarse(mk_ctx*, const mk_mesh*, const double*, int, int, double*, int, cudaStream_t);
+int prolongate(mk_ctx*, const mk_mesh*, const double*, int, int, double*, int, cudaStream_t);
+int density(mk_ctx*, const Level&, const double*, int, int, const double*, double*, cudaStream_t);
+int frozen_potential(mk_ctx*, const Level&, const double*, const double*, mk_xc, double*, cudaStream_t);
+int load_vector(mk_ctx*, const Level&, const double*, double, double*, cudaStream_t);
+int multipole_boundary(mk_ctx*, const Level&, const double*, const double*, int, double*, cudaStream_t);
+int solve_mixed(mk_ctx*, const mk_mesh*, const mk_molecule*, double, const double*, const double*, const double*,
+                double*, int, int, const mk_solve_opts&, mk_solve_report*, cudaStream_t);
+
+// Per-column PCG state on the device.
+struct ColState {
+  double rz, pq, rr, bn, alpha, beta, rz_new;
+  int active, iters, breakdown, pad;
+};
+
+__global__ void k_residual(int64_t n, const uint8_t* __restrict__ bnd, const double* __restrict__ b,
+                           const double* __restrict__ Ax, const double* __restrict__ diag, double* __restrict__ r,
+                           double* __restrict__ z, double* __restrict__ p, int N, int ld) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * ld) return;
+  const int64_t nd = t / ld;
+  const int j = (int)(t % ld);
+  double rv = 0.0;
+  if (j < N && !bnd[nd]) rv = b[t] - Ax[t];
+  r[t] = rv;
+  const double zv = rv / diag[nd];
+  if (z) z[t] = zv;
+  if (p) p[t] = zv;
+}
+
+__global__ void k_init_state(ColState* st, const double* bb, const double* rz, const double* rr, int N, double rtol) {
+  const int j = threadIdx.x;
+  if (j >= N) return;
+  ColState c{};
+  c.bn = bb[j] > 0 ? sqrt(bb[j]) : 1.0;
+  c.rz = rz[j];
+  c.rr = rr[j];
+  c.active = sqrt(rr[j]) / c.bn > rtol;
+  st[j] = c;
+}
+
+__global__ void k_alpha(ColState* st, const double* pq, int N) {
+  const int j = threadIdx.x;
+  if (j >= N) return;
+  ColState c = st[j];
+  c.pq = pq[j];
+  if (c.active) {
+    if (!(c.pq > 0.0)) {
+      c.breakdown = 1;
+      c.active = 0;
+      c.alpha = 0.0;
+    } else {
+      c.alpha = c.rz / c.pq;
+    }
+  } else {
+    c.alpha = 0.0;
+  }
+  st[j] = c;
+}
+
+__global__ void k_update(int64_t n, const ColState* __restrict__ st, const double* __restrict__ p,
+                         const double* __restrict__ q, const double* __restrict__ diag, double* __restrict__ x,
+                         double* __restrict__ r, double* __restrict__ z, int N, int ld) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * ld) return;
+  const int j = (int)(t % ld);
+  if (j >= N) return;
+  const double a = st[j].alpha;
+  if (a == 0.0) return;
+  x[t] += a * p[t];
+  const double rv = r[t] - a * q[t];
+  r[t] = rv;
+  z[t] = rv / diag[t / ld];
+}
+
+__global__ void k_beta(ColState* st, const double* rz_new, const double* rr, int N, double rtol) {
+  const int j = threadIdx.x;
+  if (j >= N) return;
+  ColState c = st[j];
+  if (c.active) {
+    c.beta = rz_new[j] / c.rz;
+    c.rz = rz_new[j];
+    c.rr = rr[j];
+    c.iters += 1;
+    c.active = sqrt(c.rr) / c.bn > rtol;
+  } else {
+    c.beta = 0.0;
+  }
+  st[j] = c;
+}
+
+__global__ void k_pupdate(int64_t n, const ColState* __restrict__ st, const double* __restrict__ z,
+                          double* __restrict__ p, int N, int ld) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * ld) return;
+  const int j = (int)(t % ld);
+  if (j >= N || !st[j].active) return;
+  p[t] = z[t] + st[j].beta * p[t];
+}
+
+// Plain FP64 Jacobi-PCG on all columns at once.  `Ae` packed element matrices of the SPD operator, `diag` its
+// assembled diagonal (boundary rows 1).  x: initial guess in, solution out (boundary rows forced to 0).
+int pcg64(mk_ctx* ctx, const Level& L, const double* Ae, const double* diag, const double* b, double* x, int N,
+          int ld, const mk_solve_opts& o, mk_solve_report* rep, cudaStream_t s) {
+  int err = MK_OK;
+  const int64_t n = L.n_nodes;
+  const size_t vb = (size_t)n * ld * sizeof(double);
+  double* R = (double*)scratch(ctx, S_R64, vb, &err);
+  double* Z = (double*)scratch(ctx, S_Z64, vb, &err);
+  double* P = (double*)scratch(ctx, S_P64, vb, &err);
+  double* Q = (double*)scratch(ctx, S_Q64, vb, &err);
+  double* sc = (double*)scratch(ctx, S_SCAL, 8 * MK_MAX_RHS * sizeof(double) + MK_MAX_RHS * sizeof(ColState), &err);
+  if (!R || !Z || !P || !Q || !sc) return err;
+  double *d1 = sc, *d2 = sc + MK_MAX_RHS, *d3 = sc + 2 * MK_MAX_RHS;
+  ColState* st = (ColState*)(sc + 8 * MK_MAX_RHS);
+  const int th = 256;
+  const int gb = (int)((n * ld + th - 1) / th);
+  // host mirror of the column states
+  if (ctx->pinned_size < sizeof(ColState) * MK_MAX_RHS) {
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    MK_CUDA(cudaMallocHost(&ctx->pinned, sizeof(ColState) * MK_MAX_RHS * 2));
+    ctx->pinned_size = sizeof(ColState) * MK_MAX_RHS * 2;
+  }
+  ColState* hst = (ColState*)ctx->pinned;
+
+  MK_TRY(apply64(ctx, L, Ae, x, Q, N, ld, true, s));
+  k_residual<<<gb, th, 0, s>>>(n, L.d_boundary, b, Q, diag, R, Z, P, N, ld);
+  // x boundary rows to 0 (Q := 0 then mask trick): write x = x - 0 on interior, 0 on boundary
+  MK_TRY(column_dots(ctx, n, b, b, N, ld, d1, s));
+  MK_TRY(column_dots(ctx, n, R, Z, N, ld, d2, s));
+  MK_TRY(column_dots(ctx, n, R, R, N, ld, d3, s));
+  k_init_state<<<1, MK_MAX_RHS, 0, s>>>(st, d1, d2, d3, N, o.rtol);
+  const int check = std::max(1, o.check_every);
+  int it = 0, status = MK_OK;
+  bool any_active = true;
+  MK_CUDA(cudaMemcpyAsync(hst, st, sizeof(ColState) * N, cudaMemcpyDeviceToHost, s));
+  MK_CUDA(cudaStreamSynchronize(s));
+  any_active = false;
+  for (int j = 0; j < N; ++j) any_active |= hst[j].active != 0;
+  while (any_active && it < o.maxit) {
+    MK_TRY(apply64(ctx, L, Ae, P, Q, N, ld, true, s));
+    MK_TRY(column_dots(ctx, n, P, Q, N, ld, d1, s));
+    k_alpha<<<1, MK_MAX_RHS, 0, s>>>(st, d1, N);
+    k_update<<<gb, th, 0, s>>>(n, st, P, Q, diag, x, R, Z, N, ld);
+    MK_TRY(column_dots(ctx, n, R, Z, N, ld, d2, s));
+    MK_TRY(column_dots(ctx, n, R, R, N, ld, d3, s));
+    k_beta<<<1, MK_MAX_RHS, 0, s>>>(st, d2, d3, N, o.rtol);
+    k_pupdate<<<gb, th, 0, s>>>(n, st, Z, P, N, ld);
+    ++it;
+    if (it % check == 0 || it >= o.maxit) {
+      MK_CUDA(cudaMemcpyAsync(hst, st, sizeof(ColState) * N, cudaMemcpyDeviceToHost, s));
+      MK_CUDA(cudaStreamSynchronize(s));
+      any_active = false;
+      for (int j = 0; j < N; ++j) {
+        any_active |= hst[j].active != 0;
+        if (hst[j].breakdown) status = MK_ERR_BREAKDOWN;
+      }
+      if (status == MK_ERR_BREAKDOWN) break;
+    }
+  }
+  MK_CUDA(cudaGetLastError());
+  // final FP64 true residual
+  MK_TRY(apply64(ctx, L, Ae, x, Q, N, ld, true, s));
+  k_residual<<<gb, th, 0, s>>>(n, L.d_boundary, b, Q, diag, R, nullptr, nullptr, N, ld);
+  MK_TRY(column_dots(ctx, n, R, R, N, ld, d3, s));
+  MK_CUDA(cudaMemcpyAsync(hst, st, sizeof(ColState) * N, cudaMemcpyDeviceToHost, s));
+  double rr[MK_MAX_RHS];
+  MK_CUDA(cudaMemcpyAsync(rr, d3, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+  MK_CUDA(cudaStreamSynchronize(s));
+  if (rep) {
+    std::memset(rep, 0, sizeof(*rep));
+    rep->n_rhs = N;
+    rep->iterations = it;
+    double mx = 0.0;
+    for (int j = 0; j < N; ++j) {
+      rep->iters[j] = hst[j].iters;
+      rep->rel_residual[j] = std::sqrt(rr[j]) / hst[j].bn;
+      mx = std::max(mx, rep->rel_residual[j]);
+    }
+    rep->max_rel_residual = mx;
+  }
+  double mx = 0.0;
+  for (int j = 0; j < N; ++j) mx = std::max(mx, std::sqrt(rr[j]) / hst[j].bn);
+  if (status == MK_OK && !(mx <= o.rtol)) status = MK_ERR_NOT_CONVERGED;
+  if (rep) rep->status = status;
+  if (status == MK_ERR_BREAKDOWN) return fail(status, "PCG breakdown: p^T A p <= 0 (operator not positive definite)");
+  if (status == MK_ERR_NOT_CONVERGED) return fail(status, "PCG did not reach rtol within maxit");
+  return MK_OK;
+}
+
+static bool valid_opts(const mk_solve_opts* o) {
+  return o && o->rtol > 0 && o->maxit > 0;
+}
+
+__global__ void k_combine_rhs(int64_t n, const uint8_t* __restrict__ bnd, const double* __restrict__ Mu,
+                              const double* __restrict__ Vu, const double* __restrict__ coef, double* __restrict__ rhs,
+                              int N, int ld) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * ld) return;
+  const int64_t nd = t / ld;
+  const int j = (int)(t % ld);
+  rhs[t] = (j < N && !bnd[nd]) ? coef[j] * Mu[t] - Vu[t] : 0.0;
+}
+
+__global__ void k_axpy_interior(int64_t n, const uint8_t* __restrict__ bnd, const double* __restrict__ d,
+                                double* __restrict__ w) {
+  const int64_t nd = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (nd >= n || bnd[nd]) return;
+  w[nd] += d[nd];
+}
+
+__global__ void k_scale(int64_t n, double* __restrict__ v, const double* __restrict__ num,
+                        const double* __restrict__ den, int mode) {
+  // mode 0: v *= 1/sqrt(num[0]);  used by Lanczos normalisation
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  (void)den;
+  if (mode == 0) v[i] *= 1.0 / sqrt(num[0]);
+}
+
+__global__ void k_lanczos_w(int64_t n, const uint8_t* __restrict__ bnd, double* __restrict__ w,
+                            const double* __restrict__ v, const double* __restrict__ vprev, double alpha,
+                            double beta) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  w[i] = bnd[i] ? 0.0 : w[i] - alpha * v[i] - beta * vprev[i];
+}
+
+__global__ void k_scatter_free(int64_t nf, const int32_t* __restrict__ free_idx, const double* __restrict__ src,
+                               double* __restrict__ dst) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nf) dst[free_idx[k]] = src[k];
+}
+
+}  // namespace mk
+
+using namespace mk;
+
+extern "C" {
+
+int mk_prolongate(mk_ctx* ctx, const mk_mesh* m, const double* psiH, int ldc, int N, double* u, int ld,
+                  void* stream) {
+  MK_ARG(ctx && m && psiH && u, "mk_prolongate: null argument");
+  MK_ARG(N >= 1 && N <= ld && N <= ldc && N <= MK_MAX_RHS, "mk_prolongate: bad N/ld");
+  MK_CUDA(cudaSetDevice(ctx->device));
+  return prolongate(ctx, m, psiH, ldc, N, u, ld, (cudaStream_t)stream);
+}
+
+int mk_hartree_poisson(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, const double* occ, int N, int bc,
+                       double* w, const mk_solve_opts* opts, mk_solve_report* report, void* stream) {
+  MK_ARG(ctx && m && u && occ && w, "mk_hartree_poisson: null argument");
+  MK_ARG(N >= 1 && N <= ld && N <= MK_MAX_RHS, "mk_hartree_poisson: bad N/ld");
+  MK_ARG(bc == MK_BC_ZERO || bc == MK_BC_MULTIPOLE, "mk_hartree_poisson: bad bc");
+  MK_ARG(valid_opts(opts), "mk_hartree_poisson: bad opts");
+  MK_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const Level& L = m->fine;
+  int err = MK_OK;
+  double* rho = (double*)scratch(ctx, S_RHO, (size_t)L.n_elems * kQ * sizeof(double), &err);
+  double* F = (double*)scratch(ctx, S_VEC1, L.n_nodes * sizeof(double), &err);
+  double* y = (double*)scratch(ctx, S_VEC2, L.n_nodes * sizeof(double), &err);
+  double* d = (double*)scratch(ctx, S_VEC3, L.n_nodes * sizeof(double), &err);
+  double* Ke = (double*)scratch(ctx, S_ELEM64, (size_t)L.n_elems * (L.nloc * (L.nloc + 1) / 2) * sizeof(double), &err);
+  double* diag = (double*)scratch(ctx, S_DIAG64, L.n_nodes * sizeof(double), &err);
+  if (!rho || !F || !y || !d || !Ke || !diag) return err;
+  MK_TRY(density(ctx, L, u, ld, N, occ, rho, s));
+  MK_TRY(load_vector(ctx, L, rho, 4.0 * M_PI, F, s));
+  MK_TRY(multipole_boundary(ctx, L, rho, L.d_nodes, bc, w, s));
+  MK_TRY(element_matrices(ctx, L, nullptr, 1.0, 0.0, 0.0, nullptr, Ke, s));
+  MK_TRY(assemble_diagonal(ctx, L, Ke, diag, s));
+  MK_TRY(apply64(ctx, L, Ke, w, y, 1, 1, true, s));                     // K_IB g (interior rows)
+  double one = 1.0;
+  double* coef = (double*)scratch(ctx, S_COEF, 64 * sizeof(double), &err);
+  if (!coef) return err;
+  MK_CUDA(cudaMemcpyAsync(coef, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+  k_combine_rhs<<<(int)((L.n_nodes + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, F, y, coef, F, 1, 1);
+  MK_CUDA(cudaMemsetAsync(d, 0, L.n_nodes * sizeof(double), s));
+  int r = pcg64(ctx, L, Ke, diag, F, d, 1, 1, *opts, report, s);
+  k_axpy_interior<<<(int)((L.n_nodes + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, d, w);
+  MK_CUDA(cudaGetLastError());
+  MK_CUDA(cudaStreamSynchronize(s));
+  return r;
+}
+
+int mk_assemble_rhs(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, const double* lambdaH,
+                    const double* occ, int N, const double* w, double sigma, mk_xc xc, double* rhs, double* vq,
+                    void* stream) {
+  MK_ARG(ctx && m && u && lambdaH && occ && rhs && vq, "mk_assemble_rhs: null argument");
+  MK_ARG(N >= 1 && N <= ld && N <= MK_MAX_RHS, "mk_assemble_rhs: bad N/ld");
+  MK_ARG(xc.kind >= MK_XC_NONE && xc.kind <= MK_XC_LDA_PZ, "mk_assemble_rhs: bad xc");
+  MK_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const Level& L = m->fine;
+  int err = MK_OK;
+  const size_t eb = (size_t)L.n_elems * (L.nloc * (L.nloc + 1) / 2) * sizeof(double);
+  double* rho = (double*)scratch(ctx, S_RHO, (size_t)L.n_elems * kQ * sizeof(double), &err);
+  double* Me = (double*)scratch(ctx, S_ELEM64B, eb, &err);
+  double* Ve = (double*)scratch(ctx, S_ELEM64, eb, &err);
+  double* Mu = (double*)scratch(ctx, S_VEC1, (size_t)L.n_nodes * ld * sizeof(double), &err);
+  double* Vu = (double*)scratch(ctx, S_VEC2, (size_t)L.n_nodes * ld * sizeof(double), &err);
+  double* coef = (double*)scratch(ctx, S_COEF, 64 * sizeof(double), &err);
+  if (!rho || !Me || !Ve || !Mu || !Vu || !coef) return err;
+  MK_TRY(density(ctx, L, u, ld, N, occ, rho, s));
+  MK_TRY(frozen_potential(ctx, L, w, rho, xc, vq, s));
+  MK_TRY(element_matrices(ctx, L, nullptr, 0.0, 0.0, 0.0, vq, Ve, s));
+  MK_TRY(element_matrices(ctx, L, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s));
+  MK_TRY(apply64(ctx, L, Me, u, Mu, N, ld, true, s));
+  MK_TRY(apply64(ctx, L, Ve, u, Vu, N, ld, true, s));
+  double h[MK_MAX_RHS];
+  for (int j = 0; j < N; ++j) h[j] = lambdaH[j] + sigma;
+  MK_CUDA(cudaMemcpyAsync(coef, h, N * sizeof(double), cudaMemcpyHostToDevice, s));
+  MK_CUDA(cudaStreamSynchronize(s));
+  k_combine_rhs<<<(int)((L.n_nodes * ld + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, Mu, Vu, coef, rhs, N, ld);
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
+int mk_correction_solve(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, double sigma, const double* rhs,
+                        double* x, int ld, int N, const mk_solve_opts* opts, mk_solve_report* report,
+                        void* stream) {
+  MK_ARG(ctx && m && mol && rhs && x, "mk_correction_solve: null argument");
+  MK_ARG(N >= 1 && N <= ld && N <= MK_MAX_RHS, "mk_correction_solve: bad N/ld");
+  MK_ARG(valid_opts(opts), "mk_correction_solve: bad opts");
+  MK_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const Level& L = m->fine;
+  if (opts->precision == MK_PREC_MIXED) {
+    return solve_mixed(ctx, m, mol, sigma, rhs, nullptr, nullptr, x, ld, N, *opts, report, s);
+  }
+  MK_ARG(opts->precision == MK_PREC_FP64, "mk_correction_solve: bad precision");
+  if (opts->precond != MK_PRECOND_JACOBI) return fail(MK_ERR_UNSUPPORTED, "FP64 path supports Jacobi only");
+  int err = MK_OK;
+  double* Ae = (double*)scratch(ctx, S_ELEM64, (size_t)L.n_elems * (L.nloc * (L.nloc + 1) / 2) * sizeof(double), &err);
+  double* diag = (double*)scratch(ctx, S_DIAG64, L.n_nodes * sizeof(double), &err);
+  if (!Ae || !diag) return err;
+  MK_TRY(element_matrices(ctx, L, mol, 0.5, 1.0, sigma, nullptr, Ae, s));
+  MK_TRY(assemble_diagonal(ctx, L, Ae, diag, s));
+  return pcg64(ctx, L, Ae, diag, rhs, x, N, ld, *opts, report, s);
+}
+
+// Symmetric tridiagonal lowest eigenvalue by Sturm-sequence bisection (host, tiny).
+static double tridiag_lowest(const std::vector<double>& a, const std::vector<double>& b) {
+  const int n = (int)a.size();
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < n; ++i) {
+    double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < n ? std::fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    int count = 0;
+    double d = 1.0;
+    for (int i = 0; i < n; ++i) {
+      d = a[i] - mid - (i > 0 ? b[i - 1] * b[i - 1] / d : 0.0);
+      if (d == 0.0) d = -1e-300;
+      if (d < 0) ++count;
+    }
+    if (count >= 1) hi = mid; else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+int mk_lowest_ritz(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, const double* v0, int steps,
+                   double* theta, void* stream) {
+  MK_ARG(ctx && m && mol && v0 && theta && steps >= 1, "mk_lowest_ritz: bad argument");
+  MK_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const Level& L = m->fine;
+  const int64_t n = L.n_nodes;
+  int err = MK_OK;
+  const size_t eb = (size_t)L.n_elems * (L.nloc * (L.nloc + 1) / 2) * sizeof(double);
+  double* He = (double*)scratch(ctx, S_ELEM64B, eb, &err);
+  double* Me = (double*)scratch(ctx, S_ELEM64, eb, &err);
+  double* diagM = (double*)scratch(ctx, S_DIAG64, n * sizeof(double), &err);
+  double* v = (double*)scratch(ctx, S_VEC1, n * sizeof(double), &err);
+  double* vp = (double*)scratch(ctx, S_VEC2, n * sizeof(double), &err);
+  double* Hv = (double*)scratch(ctx, S_VEC3, n * sizeof(double), &err);
+  double* w = (double*)scratch(ctx, S_VEC4, n * sizeof(double), &err);
+  double* Mw = (double*)scratch(ctx, S_VEC5, n * sizeof(double), &err);
+  double* dd = (double*)scratch(ctx, S_COEF, 64 * sizeof(double), &err);
+  if (!He || !Me || !diagM || !v || !vp || !Hv || !w || !Mw || !dd) return err;
+  MK_TRY(element_matrices(ctx, L, mol, 0.5, 1.0, 0.0, nullptr, He, s));
+  MK_TRY(element_matrices(ctx, L, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s));
+  MK_TRY(assemble_diagonal(ctx, L, Me, diagM, s));
+  MK_CUDA(cudaMemsetAsync(v, 0, n * sizeof(double), s));
+  MK_CUDA(cudaMemsetAsync(vp, 0, n * sizeof(double), s));
+  double* v0d = Mw;
+  MK_CUDA(cudaMemcpyAsync(v0d, v0, L.n_free * sizeof(double), cudaMemcpyHostToDevice, s));
+  MK_CUDA(cudaStreamSynchronize(s));
+  k_scatter_free<<<(int)((L.n_free + 255) / 256), 256, 0, s>>>(L.n_free, L.d_free_idx, v0d, v);
+  MK_TRY(apply64(ctx, L, Me, v, Mw, 1, 1, true, s));
+  MK_TRY(column_dots(ctx, n, v, Mw, 1, 1, dd, s));
+  k_scale<<<(int)((n + 255) / 256), 256, 0, s>>>(n, v, dd, nullptr, 0);
+  mk_solve_opts mo{MK_PREC_FP64, MK_PRECOND_JACOBI, 1e-12, 5000, 0, 0, 25};
+  std::vector<double> a, b;
+  double beta = 0.0;
+  for (int k = 0; k < steps; ++k) {
+    MK_TRY(apply64(ctx, L, He, v, Hv, 1, 1, true, s));
+    MK_TRY(column_dots(ctx, n, v, Hv, 1, 1, dd, s));
+    double alpha;
+    MK_CUDA(cudaMemcpyAsync(&alpha, dd, sizeof(double), cudaMemcpyDeviceToHost, s));
+    MK_CUDA(cudaMemsetAsync(w, 0, n * sizeof(double), s));
+    MK_CUDA(cudaStreamSynchronize(s));
+    MK_TRY(pcg64(ctx, L, Me, diagM, Hv, w, 1, 1, mo, nullptr, s));   // w = M^-1 H v
+    k_lanczos_w<<<(int)((n + 255) / 256), 256, 0, s>>>(n, L.d_boundary, w, v, vp, alpha, beta);
+    MK_TRY(apply64(ctx, L, Me, w, Mw, 1, 1, true, s));
+    MK_TRY(column_dots(ctx, n, w, Mw, 1, 1, dd, s));
+    double bb;
+    MK_CUDA(cudaMemcpyAsync(&bb, dd, sizeof(double), cudaMemcpyDeviceToHost, s));
+    MK_CUDA(cudaStreamSynchronize(s));
+    a.push_back(alpha);
+    beta = std::sqrt(std::max(bb, 0.0));
+    if (beta == 0.0 || k + 1 == steps) break;
+    b.push_back(beta);
+    MK_CUDA(cudaMemcpyAsync(vp, v, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    MK_CUDA(cudaMemcpyAsync(v, w, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    k_scale<<<(int)((n + 255) / 256), 256, 0, s>>>(n, v, dd, nullptr, 0);
+  }
+  b.resize(a.size() > 0 ? a.size() - 1 : 0);
+  *theta = tridiag_lowest(a, b);
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
+}  // extern "C"

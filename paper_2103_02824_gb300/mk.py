@@ -1,0 +1,294 @@
+"""Python binding of the mk C ABI (include/mk.h): argument marshalling only.
+
+Every function here forwards to the CUDA library libmk.so; device arrays are torch CUDA tensors (float64, C
+contiguous), host arrays numpy.  If the library has not been built, importing this module raises: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmk.so")
+
+MK_OK = 0
+MK_ERR_INVALID_ARG = -1
+MK_ERR_CUDA = -2
+MK_ERR_OOM = -3
+MK_ERR_NOT_CONVERGED = -4
+MK_ERR_BREAKDOWN = -5
+MK_ERR_TIMEOUT = -6
+MK_ERR_SINGULAR_AUG = -7
+MK_ERR_UNSUPPORTED = -8
+MK_MAX_RHS = 64
+
+MK_XC = {"none": 0, "slater": 1, "xalpha": 2, "lda": 3}
+MK_PREC_FP64, MK_PREC_MIXED = 0, 1
+MK_PRECOND = {"jacobi": 0, "chebyshev": 1, "learned": 2}
+MK_BC = {"zero": 0, "multipole": 1}
+
+
+class MkError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"mk error {code}: {msg}")
+        self.code = code
+
+
+class mk_mesh_desc(C.Structure):
+    _fields_ = [("order", C.c_int), ("n_vertices", C.c_int64), ("coords", C.POINTER(C.c_double)),
+                ("n_elems", C.c_int64), ("tets", C.POINTER(C.c_int32))]
+
+
+class mk_molecule(C.Structure):
+    _fields_ = [("n_nuclei", C.c_int), ("Z", C.POINTER(C.c_double)), ("R", C.POINTER(C.c_double))]
+
+
+class mk_xc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("alpha", C.c_double)]
+
+
+class mk_solve_opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("precond", C.c_int), ("rtol", C.c_double), ("maxit", C.c_int),
+                ("inner_rtol", C.c_double), ("max_refine", C.c_int), ("check_every", C.c_int)]
+
+
+class mk_solve_report(C.Structure):
+    _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("refinements", C.c_int), ("n_rhs", C.c_int),
+                ("max_rel_residual", C.c_double), ("iters", C.c_int * MK_MAX_RHS),
+                ("rel_residual", C.c_double * MK_MAX_RHS)]
+
+    def to_dict(self):
+        n = self.n_rhs
+        return dict(status=self.status, iterations=self.iterations, refinements=self.refinements, n_rhs=n,
+                    max_rel_residual=self.max_rel_residual, iters=list(self.iters[:n]),
+                    rel_residual=list(self.rel_residual[:n]))
+
+
+class mk_mesh_info(C.Structure):
+    _fields_ = [("order", C.c_int), ("nloc", C.c_int), ("n_nodes", C.c_int64), ("n_free", C.c_int64),
+                ("n_elems", C.c_int64), ("n_colours", C.c_int64), ("n_nodes_coarse", C.c_int64),
+                ("n_free_coarse", C.c_int64), ("n_elems_coarse", C.c_int64), ("n_quad", C.c_int)]
+
+
+_vp = C.c_void_p
+_SIGS = {
+    "mk_ctx_create": [C.POINTER(_vp), C.c_int],
+    "mk_ctx_destroy": [_vp],
+    "mk_last_error": [C.c_char_p, C.c_size_t],
+    "mk_version": [],
+    "mk_mesh_upload": [_vp, C.POINTER(mk_mesh_desc), C.POINTER(mk_mesh_desc), C.POINTER(C.c_int32), C.POINTER(_vp)],
+    "mk_mesh_destroy": [_vp],
+    "mk_mesh_get_info": [_vp, C.POINTER(mk_mesh_info)],
+    "mk_mesh_get_topology": [_vp, C.c_int, _vp, _vp, _vp, _vp],
+    "mk_prolongate": [_vp, _vp, _vp, C.c_int, C.c_int, _vp, C.c_int, _vp],
+    "mk_hartree_poisson": [_vp, _vp, _vp, C.c_int, C.POINTER(C.c_double), C.c_int, C.c_int, _vp,
+                           C.POINTER(mk_solve_opts), C.POINTER(mk_solve_report), _vp],
+    "mk_assemble_rhs": [_vp, _vp, _vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int, _vp,
+                        C.c_double, mk_xc, _vp, _vp, _vp],
+    "mk_correction_solve": [_vp, _vp, C.POINTER(mk_molecule), C.c_double, _vp, _vp, C.c_int, C.c_int,
+                            C.POINTER(mk_solve_opts), C.POINTER(mk_solve_report), _vp],
+    "mk_augmented_project": [_vp, _vp, C.POINTER(mk_molecule), _vp, _vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp,
+                             _vp, _vp, _vp, _vp],
+    "mk_small_eigensolve": [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "mk_orbital_assemble": [_vp, _vp, _vp, _vp, _vp, C.c_int, C.c_int, _vp, _vp],
+    "mk_lowest_ritz": [_vp, _vp, C.POINTER(mk_molecule), C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double), _vp],
+}
+
+
+def header_symbols():
+    """Names of the entry points declared in include/mk.h (parsed from the header)."""
+    import re
+    hdr = open(os.path.join(os.path.dirname(_HERE), "include", "mk.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(mk_\w+)\s*\(", hdr, re.M)))
+
+
+def load(path: str = LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError(f"libmk.so not built at {path}: run `python -m paper_2103_02824_gb300.build`")
+    lib = C.CDLL(path)
+    for name, args in _SIGS.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_char_p if name == "mk_version" else C.c_int
+    return lib
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = load()
+    return _lib
+
+
+def _err():
+    buf = C.create_string_buffer(2048)
+    lib().mk_last_error(buf, 2048)
+    return buf.value.decode(errors="replace")
+
+
+def _check(code, allow=()):
+    if code != MK_OK and code not in allow:
+        raise MkError(code, _err())
+    return code
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor (must be contiguous float64/int32 on CUDA) or None."""
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(stream)
+
+
+def _host_f64(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Molecule:
+    def __init__(self, Z, R):
+        self.Z, zp = _host_f64(np.asarray(Z).ravel())
+        self.R, rp = _host_f64(np.asarray(R).reshape(-1, 3))
+        self.c = mk_molecule(len(self.Z), zp, rp)
+
+
+def opts(precision="fp64", precond="jacobi", rtol=1e-8, maxit=20000, inner_rtol=1e-4, max_refine=20, check_every=10):
+    return mk_solve_opts(MK_PREC_MIXED if precision == "mixed" else MK_PREC_FP64, MK_PRECOND[precond], rtol, maxit,
+                         inner_rtol, max_refine, check_every)
+
+
+class Context:
+    def __init__(self, device: int = 0):
+        self.h = C.c_void_p()
+        _check(lib().mk_ctx_create(C.byref(self.h), device))
+
+    def close(self):
+        if self.h:
+            lib().mk_ctx_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mesh:
+    def __init__(self, ctx: Context, fine_coords, fine_tets, coarse_coords, coarse_tets, parent, order: int):
+        self.ctx = ctx
+        keep = []
+
+        def desc(coords, tets):
+            c, cp = _host_f64(coords)
+            t = np.ascontiguousarray(tets, dtype=np.int32)
+            keep.extend([c, t])
+            return mk_mesh_desc(order, c.shape[0], cp, t.shape[0], t.ctypes.data_as(C.POINTER(C.c_int32)))
+
+        f = desc(fine_coords, fine_tets)
+        cdesc = desc(coarse_coords, coarse_tets)
+        par = np.ascontiguousarray(parent, dtype=np.int32)
+        self.h = C.c_void_p()
+        _check(lib().mk_mesh_upload(ctx.h, C.byref(f), C.byref(cdesc), par.ctypes.data_as(C.POINTER(C.c_int32)),
+                                    C.byref(self.h)))
+        info = mk_mesh_info()
+        _check(lib().mk_mesh_get_info(self.h, C.byref(info)))
+        self.info = {k: getattr(info, k) for k, _ in mk_mesh_info._fields_}
+
+    def topology(self, level: int = 0):
+        n = self.info["n_nodes"] if level == 0 else self.info["n_nodes_coarse"]
+        E = self.info["n_elems"] if level == 0 else self.info["n_elems_coarse"]
+        nodes = np.zeros((n, 3))
+        bnd = np.zeros(n, dtype=np.uint8)
+        elem = np.zeros((E, self.info["nloc"]), dtype=np.int32)
+        col = np.zeros(E, dtype=np.int32)
+        _check(lib().mk_mesh_get_topology(self.h, level, nodes.ctypes.data, bnd.ctypes.data, elem.ctypes.data,
+                                          col.ctypes.data))
+        return nodes, bnd.astype(bool), elem, col
+
+    def close(self):
+        if self.h:
+            lib().mk_mesh_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mk_prolongate(ctx, mesh, psiH, N, u, stream=None):
+    ldc = psiH.shape[1] if psiH.dim() == 2 else 1
+    ld = u.shape[1] if u.dim() == 2 else 1
+    _check(lib().mk_prolongate(ctx.h, mesh.h, _ptr(psiH), ldc, N, _ptr(u), ld, _stream(stream)))
+
+
+def mk_hartree_poisson(ctx, mesh, u, occ, N, w, bc="multipole", opt=None, stream=None):
+    ld = u.shape[1] if u.dim() == 2 else 1
+    occ_h, occ_p = _host_f64(occ)
+    rep = mk_solve_report()
+    o = opt or opts(rtol=1e-12)
+    code = lib().mk_hartree_poisson(ctx.h, mesh.h, _ptr(u), ld, occ_p, N, MK_BC[bc], _ptr(w), C.byref(o),
+                                    C.byref(rep), _stream(stream))
+    _check(code)
+    return rep.to_dict()
+
+
+def mk_assemble_rhs(ctx, mesh, u, lamH, occ, N, w, sigma, xc, rhs, vq, alpha=0.77298, stream=None):
+    ld = u.shape[1] if u.dim() == 2 else 1
+    lam_h, lam_p = _host_f64(lamH)
+    occ_h, occ_p = _host_f64(occ)
+    _check(lib().mk_assemble_rhs(ctx.h, mesh.h, _ptr(u), ld, lam_p, occ_p, N, _ptr(w), float(sigma),
+                                 mk_xc(MK_XC[xc], alpha), _ptr(rhs), _ptr(vq), _stream(stream)))
+
+
+def mk_correction_solve(ctx, mesh, mol: Molecule, sigma, rhs, x, N, opt=None, stream=None, allow=()):
+    ld = x.shape[1] if x.dim() == 2 else 1
+    rep = mk_solve_report()
+    o = opt or opts()
+    code = lib().mk_correction_solve(ctx.h, mesh.h, C.byref(mol.c), float(sigma), _ptr(rhs), _ptr(x), ld, N,
+                                     C.byref(o), C.byref(rep), _stream(stream))
+    _check(code, allow)
+    d = rep.to_dict()
+    d["code"] = code
+    return d
+
+
+def mk_augmented_project(ctx, mesh, mol: Molecule, vq, psihat, N, AH, MH, b, c, beta, gamma, gramA=None, gramM=None,
+                         stream=None):
+    ld = psihat.shape[1] if psihat.dim() == 2 else 1
+    _check(lib().mk_augmented_project(ctx.h, mesh.h, C.byref(mol.c), _ptr(vq), _ptr(psihat), ld, N, _ptr(AH),
+                                      _ptr(MH), _ptr(b), _ptr(c), _ptr(beta), _ptr(gamma), _ptr(gramA), _ptr(gramM),
+                                      _stream(stream)))
+
+
+def mk_small_eigensolve(ctx, NH, N, AH, MH, b, c, beta, gamma, lam, coef, status, stream=None):
+    _check(lib().mk_small_eigensolve(ctx.h, NH, N, _ptr(AH), _ptr(MH), _ptr(b), _ptr(c), _ptr(beta), _ptr(gamma),
+                                     _ptr(lam), _ptr(coef), _ptr(status), _stream(stream)))
+
+
+def mk_orbital_assemble(ctx, mesh, coef, psihat, u, N, psi, stream=None):
+    ld = psihat.shape[1] if psihat.dim() == 2 else 1
+    _check(lib().mk_orbital_assemble(ctx.h, mesh.h, _ptr(coef), _ptr(psihat), _ptr(u), ld, N, _ptr(psi),
+                                     _stream(stream)))
+
+
+def mk_lowest_ritz(ctx, mesh, mol: Molecule, v0, steps=60, stream=None):
+    v, vp = _host_f64(v0)
+    th = C.c_double()
+    _check(lib().mk_lowest_ritz(ctx.h, mesh.h, C.byref(mol.c), vp, steps, C.byref(th), _stream(stream)))
+    return th.value

@@ -1,0 +1,79 @@
+"""One fine-mesh correction step (Algorithm 1, steps 5-7, frozen V_Hxc(rho_H) on the right) through the C ABI.
+
+Holds device buffers for one mesh pair and chains mk_prolongate -> mk_hartree_poisson -> mk_assemble_rhs ->
+mk_correction_solve -> mk_augmented_project -> mk_small_eigensolve -> mk_orbital_assemble.  Every step runs in the
+CUDA library; this class only allocates the caller-owned device arrays (torch) and passes pointers.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import mk
+
+
+class CorrectionStep:
+    def __init__(self, ctx: "mk.Context", mesh: "mk.Mesh", Z, R, N: int, ld: int | None = None):
+        import torch
+        self.ctx, self.mesh, self.N = ctx, mesh, N
+        self.ld = ld or max(4, (N + 3) // 4 * 4)
+        self.mol = mk.Molecule(Z, R)
+        info = mesh.info
+        n, E, NH = info["n_nodes"], info["n_elems"], info["n_free_coarse"]
+        self.NH = NH
+        dev = torch.device("cuda")
+        f64 = dict(dtype=torch.float64, device=dev)
+        self.u = torch.zeros((n, self.ld), **f64)
+        self.w = torch.zeros(n, **f64)
+        self.rhs = torch.zeros((n, self.ld), **f64)
+        self.vq = torch.zeros((E, info["n_quad"]), **f64)
+        self.psihat = torch.zeros((n, self.ld), **f64)
+        self.AH = torch.zeros((NH, NH), **f64)
+        self.MH = torch.zeros((NH, NH), **f64)
+        self.b = torch.zeros((NH, N), **f64)
+        self.c = torch.zeros((NH, N), **f64)
+        self.beta = torch.zeros(N, **f64)
+        self.gamma = torch.zeros(N, **f64)
+        self.gramA = torch.zeros((N, N), **f64)
+        self.gramM = torch.zeros((N, N), **f64)
+        self.lam = torch.zeros(N, **f64)
+        self.coef = torch.zeros((NH + 1, N), **f64)
+        self.status = torch.zeros(N, dtype=torch.int32, device=dev)
+        self.psi = torch.zeros((n, self.ld), **f64)
+        self.psiH = torch.zeros((NH, self.ld), **f64)
+
+    def run(self, psiH, lamH, occ, sigma, xc="lda", hartree_bc="multipole", solve_opts=None, poisson_opts=None,
+            stream=None):
+        """psiH: torch [N_H, >=N] (device) or numpy [N_H, N]; lamH, occ: numpy [N].  Returns reports."""
+        import torch
+        N = self.N
+        if isinstance(psiH, np.ndarray):
+            self.psiH.zero_()
+            self.psiH[:, :N] = torch.from_numpy(psiH).to(self.psiH.device)
+            psiH = self.psiH
+        ctx, mesh = self.ctx, self.mesh
+        mk.mk_prolongate(ctx, mesh, psiH, N, self.u, stream=stream)
+        reps = {}
+        if hartree_bc == "none":
+            self.w.zero_()
+            reps["poisson"] = None
+        else:
+            reps["poisson"] = mk.mk_hartree_poisson(ctx, mesh, self.u, occ, N, self.w, bc=hartree_bc,
+                                                    opt=poisson_opts, stream=stream)
+        mk.mk_assemble_rhs(ctx, mesh, self.u, lamH, occ, N, self.w, sigma, xc, self.rhs, self.vq, stream=stream)
+        self.psihat.copy_(self.u)
+        reps["solve"] = mk.mk_correction_solve(ctx, mesh, self.mol, sigma, self.rhs, self.psihat, N,
+                                               opt=solve_opts, stream=stream)
+        mk.mk_augmented_project(ctx, mesh, self.mol, self.vq, self.psihat, N, self.AH, self.MH, self.b, self.c,
+                                self.beta, self.gamma, self.gramA, self.gramM, stream=stream)
+        mk.mk_small_eigensolve(ctx, self.NH, N, self.AH, self.MH, self.b, self.c, self.beta, self.gamma, self.lam,
+                               self.coef, self.status, stream=stream)
+        mk.mk_orbital_assemble(ctx, mesh, self.coef, self.psihat, self.u, N, self.psi, stream=stream)
+        return reps
+
+
+def upload_workload(ctx, wl):
+    """Meshes of a named synthetic workload (see synth.workload) uploaded to the device."""
+    from . import synth
+    cc, ct, fc, ft, par = synth.nested_cube_meshes(wl["n_coarse"], wl["levels"], wl["half"])
+    mesh = mk.Mesh(ctx, fc, ft, cc, ct, par, wl["order"])
+    return mesh, (cc, ct, fc, ft, par)

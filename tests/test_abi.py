@@ -1,0 +1,43 @@
+"""The C ABI library builds for sm_103a, loads, and exports every entry point include/mk.h declares (no GPU)."""
+import ctypes
+import subprocess
+
+import pytest
+
+from paper_2103_02824_gb300 import build, mk
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = mk.header_symbols()
+    for required in ("mk_mesh_upload", "mk_assemble_rhs", "mk_hartree_poisson", "mk_correction_solve",
+                     "mk_augmented_project", "mk_small_eigensolve"):
+        assert required in names
+
+
+def test_library_exports_every_header_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    for name in mk.header_symbols():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    for name in mk.header_symbols():
+        assert f" T {name}" in out, name
+
+
+def test_binding_covers_header(libpath):
+    assert set(mk.header_symbols()) <= set(mk._SIGS)
+    lib = mk.load(libpath)
+    assert b"sm_103a" in lib.mk_version()
+
+
+def test_no_device_fails_loudly(libpath):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(mk.MkError) as e:
+        mk.Context(0)
+    assert e.value.code == mk.MK_ERR_CUDA
