@@ -114,6 +114,15 @@ int mk_ctx_destroy(mk_ctx* ctx);
 int mk_last_error(char* buf, size_t len);
 /* Version string of the library build. */
 const char* mk_version(void);
+/* Number of CUDA kernels this library has launched in the process so far (all contexts); a diagnostic counter
+ * with no counterpart in the paper, used to report launches per step. */
+long long mk_launch_count(void);
+/* Optional timing of the operator applications with CUDA events recorded on the launching stream (diagnostic, no
+ * counterpart in the paper).  mk_profile_enable(ctx, 1) clears and starts recording; mk_profile_read waits for
+ * the recorded events and returns the summed duration and the number of timed applications of kind
+ * 0 = FP64 element-by-element apply, 1 = FP32 patch apply, 2 = FP32 halo sum. */
+int mk_profile_enable(mk_ctx* ctx, int on);
+int mk_profile_read(mk_ctx* ctx, int kind, double* total_ms, long long* count);
 
 /* ---------------------------------------------------------------------------------------------- mesh (A0) */
 /* Uploads a nested fine/coarse mesh pair (Sec. 2: V_H subset V_h needs T_h to refine T_H).  fine_parent [n_elems
@@ -168,6 +177,14 @@ int mk_assemble_rhs(mk_ctx* ctx, const mk_mesh* mesh, const double* u, int ld, c
 int mk_correction_solve(mk_ctx* ctx, const mk_mesh* mesh, const mk_molecule* mol, double sigma, const double* rhs,
                         double* x, int ld, int N, const mk_solve_opts* opts, mk_solve_report* report, void* stream);
 
+/* The operator of the correction problems alone (Eq. (Aux_Linear_Problem) with the shift): y = (K/2 + M_{V_ext} +
+ * sigma M) x on the free DOF (boundary rows of y written as 0), all ld columns, matrix-free element by element with
+ * the patch scatter (owner-computes in shared memory, halo slots summed in patch order; bitwise reproducible).
+ * precision MK_PREC_FP64: x, y are double [n_nodes*ld]; MK_PREC_MIXED: x, y are float [n_nodes*ld] (the FP32
+ * operator of the mixed solve).  Element matrices are rebuilt on every call. */
+int mk_operator_apply(mk_ctx* ctx, const mk_mesh* mesh, const mk_molecule* mol, double sigma, int precision,
+                      const void* x, void* y, int ld, void* stream);
+
 /* ---------------------------------------------------------------------------------------------- A6 */
 /* Projection on the augmented spaces V_H + span{psi^_i} (Eqs. (Eigenvalue_H_h), (Adef), (bdef), (betadef)) with
  * H = K/2 + M_{V_ext} + M_{vq} the Hamiltonian at the frozen density (vq from mk_assemble_rhs):
@@ -180,7 +197,24 @@ int mk_augmented_project(mk_ctx* ctx, const mk_mesh* mesh, const mk_molecule* mo
                          const double* psihat, int ld, int N, double* AH, double* MH, double* b, double* c,
                          double* beta, double* gamma, double* gramA, double* gramM, void* stream);
 
+/* The coarse blocks alone: AH = P^T H P, MH = P^T M P [N_H*N_H] for the frozen potential vq (Eq. (Adef); the
+ * paper assembles these on the fine mesh "in advance").  They do not depend on psi^, so a caller may compute
+ * them, and decompose them, on a second stream while mk_correction_solve runs.  vq may be NULL (bare
+ * Hamiltonian K/2 + V_ext).  Uses its own scratch, separate from mk_correction_solve's. */
+int mk_coarse_pencil(mk_ctx* ctx, const mk_mesh* mesh, const mk_molecule* mol, const double* vq, double* AH,
+                     double* MH, void* stream);
+
 /* ---------------------------------------------------------------------------------------------- A7 */
+/* Shared part of the small eigenproblem of Eq. (Eigenvalue_H_h): all eigenpairs of the coarse pencil (AH, MH),
+ * d [N_H] ascending and V [N_H*N_H] row-major (V[r*N_H + k] = component r of eigenvector k), M_H-orthonormal.
+ * MH is the mesh's own P^T M P, whose Cholesky factor mk_mesh_upload computed (M_H is fixed for a mesh pair).
+ * FP64: C = L^-1 AH L^-T by two GEMMs, cyclic Jacobi (cooperative launch), V = L^-T Q. */
+int mk_coarse_decompose(mk_ctx* ctx, const mk_mesh* mesh, const double* AH, double* d, double* V, void* stream);
+/* Per-orbital part, given the shared decomposition (d, V) of (AH, MH): same outputs and selection rule as
+ * mk_small_eigensolve below. */
+int mk_small_eigensolve_shared(mk_ctx* ctx, int N_H, int N, const double* d, const double* V, const double* b,
+                               const double* c, const double* beta, const double* gamma, double* lambda,
+                               double* coef, int32_t* status, void* stream);
 /* For each orbital i < N, all eigenpairs of the (N_H+1) pencil of Eq. (Eigenvalue_H_h)
  *   [[AH, b_i], [b_i^T, beta_i]] x = lambda [[MH, c_i], [c_i^T, gamma_i]] x
  * and the one "with the largest component in span{psi^_i}" (Algorithm 2 (a)), read as the largest

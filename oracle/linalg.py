@@ -58,8 +58,10 @@ def pcg(A, B, X0=None, tol=1e-13, maxit=50000):
 
 def lanczos_lowest(H, M, v0, steps=60):
     """Lowest Ritz value of `steps` Lanczos steps on the pencil (H, M) in the M inner product (operator M^-1 H),
-    no reorthogonalisation, start vector v0.  Used for the shift rule sigma = 1.05 max(0, -theta) + 0.5."""
-    Msolve = spla.factorized(M.tocsc())
+    no reorthogonalisation, start vector v0.  Used for the shift rule sigma = 1.05 max(0, -theta) + 0.5.
+    M^-1 is applied by Jacobi-PCG to 1e-13 (a direct factorisation of a 3-D mass matrix fills in badly)."""
+    def Msolve(r):
+        return pcg(M, r, tol=1e-13)[0]
     v = v0 / np.sqrt(v0 @ (M @ v0))
     v_prev = np.zeros_like(v)
     a, b = [], []

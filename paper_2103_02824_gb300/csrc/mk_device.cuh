@@ -59,9 +59,9 @@ inline void apply_coloured(const Level& L, const T* Ae, const T* x, T* y, int N,
     const int64_t work = cnt * N;
     const int blocks = (int)((work + th - 1) / th);
     if (L.nloc == 4)
-      k_apply_colour<4, T><<<blocks, th, 0, s>>>(L.d_colour_elems + off, (int)cnt, L.d_elem, Ae, x, y, N, ld);
+      MK_COUNT(), k_apply_colour<4, T><<<blocks, th, 0, s>>>(L.d_colour_elems + off, (int)cnt, L.d_elem, Ae, x, y, N, ld);
     else
-      k_apply_colour<10, T><<<blocks, th, 0, s>>>(L.d_colour_elems + off, (int)cnt, L.d_elem, Ae, x, y, N, ld);
+      MK_COUNT(), k_apply_colour<10, T><<<blocks, th, 0, s>>>(L.d_colour_elems + off, (int)cnt, L.d_elem, Ae, x, y, N, ld);
   }
 }
 
@@ -97,7 +97,7 @@ int column_dots32(mk_ctx* ctx, int64_t n_nodes, const float* a, const float* b, 
 
 // element matrices (packed, FP64) of half_k K + vext_scale M_{V_ext} + mass_shift M + M_{vq}
 int element_matrices(mk_ctx* ctx, const Level& L, const mk_molecule* mol, double half_k, double vext_scale,
-                     double mass_shift, const double* vq, double* out, cudaStream_t s);
+                     double mass_shift, const double* vq, double* out, cudaStream_t s, int nuc_slot = S_NUC);
 // assembled diagonal of the packed element matrices, boundary rows set to 1
 int assemble_diagonal(mk_ctx* ctx, const Level& L, const double* Ae, double* diag, cudaStream_t s);
 // y = A x (y zeroed first), boundary rows of y zeroed if mask_boundary
@@ -105,6 +105,6 @@ int apply64(mk_ctx* ctx, const Level& L, const double* Ae, const double* x, doub
             bool mask_boundary, cudaStream_t s);
 
 // nuclei packed for the device: [n*4] (Z, x, y, z); returns a device pointer in a ctx slot
-double* upload_nuclei(mk_ctx* ctx, const mk_molecule* mol, int* err, cudaStream_t s);
+double* upload_nuclei(mk_ctx* ctx, const mk_molecule* mol, int* err, cudaStream_t s, int slot = S_NUC);
 
 }  // namespace mk

@@ -77,6 +77,11 @@ __global__ void k_backward(int n, const double* __restrict__ LT, const double* _
   }
 }
 
+__global__ void k_identity(int n, double* __restrict__ I) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < (int64_t)n * n) I[t] = (t / n == t % n) ? 1.0 : 0.0;
+}
+
 __global__ void k_transpose(int n, const double* __restrict__ A, double* __restrict__ B) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)n * n) return;
@@ -115,92 +120,93 @@ __device__ __forceinline__ void pair_of(int r, int k, int n2, int* p, int* q) {
   *q = max(a, b);
 }
 
-// Cyclic Jacobi on the symmetric n2 x n2 matrix S (n2 even), accumulating Q <- Q J.  Cooperative launch.
-__global__ void k_jacobi(int n2, double* __restrict__ S, double* __restrict__ Q, Rot* __restrict__ rot,
-                         double* __restrict__ red, int max_sweeps, double tol, int* __restrict__ sweeps_out) {
+// Rotation in the (p,q) plane that zeroes S[p][q]: J = [[c, s], [-s, c]], t = s/c the smaller root of
+// t^2 + 2 theta t - 1 = 0, theta = (S_qq - S_pp) / (2 S_pq).
+__device__ __forceinline__ Rot make_rot(const double* __restrict__ S, int n2, int r, int k) {
+  int p, q;
+  pair_of(r, k, n2, &p, &q);
+  const double apq = S[(int64_t)p * n2 + q];
+  double c = 1.0, s = 0.0;
+  if (apq != 0.0) {
+    const double app = S[(int64_t)p * n2 + p], aqq = S[(int64_t)q * n2 + q];
+    const double theta = (aqq - app) / (2.0 * apq);
+    const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+    c = 1.0 / sqrt(t * t + 1.0);
+    s = t * c;
+  }
+  return Rot{p, q, c, s};
+}
+
+// Cyclic Jacobi on the symmetric n2 x n2 matrix (n2 even) in parallel round-robin order, accumulating Q <- Q J.
+// Cooperative launch.  Round r reads S_in and writes S_out (ping-pong): every CTA first derives all n2/2
+// rotations of the round from S_in into shared memory, then updates its share of the disjoint 2x2 blocks and
+// of Q; one grid barrier per round.  *final_buf tells which buffer holds the result.
+__global__ void k_jacobi(int n2, double* __restrict__ S0, double* __restrict__ S1, double* __restrict__ Q,
+                         double* __restrict__ red, int max_sweeps, double tol, int* __restrict__ info) {
   cg::grid_group grid = cg::this_grid();
+  extern __shared__ unsigned char smem_raw[];
+  Rot* rot = reinterpret_cast<Rot*>(smem_raw);
+  __shared__ double sh[256];
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nth = (int64_t)gridDim.x * blockDim.x;
   const int np = n2 / 2;
   const int64_t nblk2 = (int64_t)np * (np + 1) / 2;
-  __shared__ double sh[256];
+  double* Sin = S0;
+  double* Sout = S1;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
-    // convergence test: off-diagonal vs total Frobenius norm
     double off = 0.0, tot = 0.0;
     for (int64_t t = tid; t < (int64_t)n2 * n2; t += nth) {
-      const double v = S[t];
+      const double v = Sin[t];
       tot += v * v;
       if (t / n2 != t % n2) off += v * v;
     }
-    sh[threadIdx.x] = off;
-    __syncthreads();
-    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-      if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+    for (int pass = 0; pass < 2; ++pass) {
+      sh[threadIdx.x] = pass == 0 ? off : tot;
+      __syncthreads();
+      for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) red[2 * blockIdx.x + pass] = sh[0];
       __syncthreads();
     }
-    if (threadIdx.x == 0) red[2 * blockIdx.x] = sh[0];
-    __syncthreads();
-    sh[threadIdx.x] = tot;
-    __syncthreads();
-    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-      if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) red[2 * blockIdx.x + 1] = sh[0];
     grid.sync();
     double o = 0.0, f = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) {
-      o += red[2 * b];
-      f += red[2 * b + 1];
+    for (int bl = 0; bl < (int)gridDim.x; ++bl) {
+      o += red[2 * bl];
+      f += red[2 * bl + 1];
     }
     grid.sync();
     if (o <= tol * tol * f) break;
     for (int r = 0; r < n2 - 1; ++r) {
-      for (int64_t k = tid; k < np; k += nth) {
-        int p, q;
-        pair_of(r, (int)k, n2, &p, &q);
-        const double apq = S[(int64_t)p * n2 + q];
-        double c = 1.0, s = 0.0;
-        if (apq != 0.0) {
-          const double app = S[(int64_t)p * n2 + p], aqq = S[(int64_t)q * n2 + q];
-          const double theta = (aqq - app) / (2.0 * apq);
-          const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-          c = 1.0 / sqrt(t * t + 1.0);
-          s = t * c;
-        }
-        rot[k] = Rot{p, q, c, s};
-      }
-      grid.sync();
-      // 2x2 blocks (k1 <= k2): B' = R1^T B R2 with rows (p1,q1), cols (p2,q2)
+      for (int k = threadIdx.x; k < np; k += blockDim.x) rot[k] = make_rot(Sin, n2, r, k);
+      __syncthreads();
       for (int64_t t = tid; t < nblk2; t += nth) {
-        // decode upper-triangular pair index t -> (k1, k2)
-        int k1 = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) / 2.0);  // row in lower-tri enumeration
+        int k1 = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) / 2.0);
         while ((int64_t)(k1 + 1) * (k1 + 2) / 2 <= t) ++k1;
         while ((int64_t)k1 * (k1 + 1) / 2 > t) --k1;
         const int k2 = (int)(t - (int64_t)k1 * (k1 + 1) / 2);  // k2 <= k1
-        const Rot A = rot[k2], B = rot[k1];                    // rows from pair k2, cols from pair k1
-        const double b00 = S[(int64_t)A.p * n2 + B.p], b01 = S[(int64_t)A.p * n2 + B.q];
-        const double b10 = S[(int64_t)A.q * n2 + B.p], b11 = S[(int64_t)A.q * n2 + B.q];
-        // rows: r_p = c b_p - s b_q ; r_q = s b_p + c b_q
+        const Rot A = rot[k2], B = rot[k1];                    // rows from pair k2, columns from pair k1
+        const double b00 = Sin[(int64_t)A.p * n2 + B.p], b01 = Sin[(int64_t)A.p * n2 + B.q];
+        const double b10 = Sin[(int64_t)A.q * n2 + B.p], b11 = Sin[(int64_t)A.q * n2 + B.q];
         const double r00 = A.c * b00 - A.s * b10, r01 = A.c * b01 - A.s * b11;
         const double r10 = A.s * b00 + A.c * b10, r11 = A.s * b01 + A.c * b11;
-        // cols
         double n00 = B.c * r00 - B.s * r01, n01 = B.s * r00 + B.c * r01;
         double n10 = B.c * r10 - B.s * r11, n11 = B.s * r10 + B.c * r11;
         if (k1 == k2) {
           n01 = 0.0;
           n10 = 0.0;
         }
-        S[(int64_t)A.p * n2 + B.p] = n00;
-        S[(int64_t)A.p * n2 + B.q] = n01;
-        S[(int64_t)A.q * n2 + B.p] = n10;
-        S[(int64_t)A.q * n2 + B.q] = n11;
+        Sout[(int64_t)A.p * n2 + B.p] = n00;
+        Sout[(int64_t)A.p * n2 + B.q] = n01;
+        Sout[(int64_t)A.q * n2 + B.p] = n10;
+        Sout[(int64_t)A.q * n2 + B.q] = n11;
         if (k1 != k2) {
-          S[(int64_t)B.p * n2 + A.p] = n00;
-          S[(int64_t)B.q * n2 + A.p] = n01;
-          S[(int64_t)B.p * n2 + A.q] = n10;
-          S[(int64_t)B.q * n2 + A.q] = n11;
+          Sout[(int64_t)B.p * n2 + A.p] = n00;
+          Sout[(int64_t)B.q * n2 + A.p] = n01;
+          Sout[(int64_t)B.p * n2 + A.q] = n10;
+          Sout[(int64_t)B.q * n2 + A.q] = n11;
         }
       }
       for (int64_t t = tid; t < (int64_t)n2 * np; t += nth) {
@@ -211,9 +217,51 @@ __global__ void k_jacobi(int n2, double* __restrict__ S, double* __restrict__ Q,
         Q[(int64_t)row * n2 + R.q] = R.s * vp + R.c * vq;
       }
       grid.sync();
+      double* tmp = Sin;
+      Sin = Sout;
+      Sout = tmp;
     }
   }
-  if (tid == 0) *sweeps_out = sweep;
+  if (tid == 0) {
+    info[0] = sweep;
+    info[1] = (Sin == S0) ? 0 : 1;
+  }
+}
+
+// C[M x N] = op(A) op(B), op(X) = X or X^T (row-major storage), FP64, 32x32 tiles.
+__global__ void k_gemm64(int M, int N, int K, const double* __restrict__ A, int lda, int ta,
+                         const double* __restrict__ B, int ldb, int tb, double* __restrict__ C, int ldc) {
+  __shared__ double As[32][33], Bs[32][33];
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8 threads
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k0 = 0; k0 < K; k0 += 32) {
+    for (int r = ty; r < 32; r += 8) {
+      const int i = i0 + r, k = k0 + tx;
+      As[r][tx] = (i < M && k < K) ? (ta ? A[(int64_t)k * lda + i] : A[(int64_t)i * lda + k]) : 0.0;
+      const int kk = k0 + r, j = j0 + tx;
+      Bs[r][tx] = (kk < K && j < N) ? (tb ? B[(int64_t)j * ldb + kk] : B[(int64_t)kk * ldb + j]) : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      const double bv = Bs[k][tx];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += As[ty + 8 * q][k] * bv;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = i0 + ty + 8 * q, j = j0 + tx;
+    if (i < M && j < N) C[(int64_t)i * ldc + j] = acc[q];
+  }
+}
+
+static void gemm64(int M, int N, int K, const double* A, int lda, int ta, const double* B, int ldb, int tb, double* C,
+                   int ldc, cudaStream_t s) {
+  dim3 grid((N + 31) / 32, (M + 31) / 32);
+  MK_COUNT(), k_gemm64<<<grid, 256, 0, s>>>(M, N, K, A, lda, ta, B, ldb, tb, C, ldc);
 }
 
 // Sort the n eigenvalues (diag of S, first n of n2) ascending: perm[rank] = index (ties by index).
@@ -520,11 +568,132 @@ __global__ void k_flip(int64_t n_nodes, const double* __restrict__ dots, double*
   if (j < N && dots[j] < 0) psi[t] = -psi[t];
 }
 
+
+
+// Inverse Cholesky factor of the SPD n x n matrix MH: Linv = L^-1 (MH = L L^T), dense row-major.  Uses the
+// workspace slot `slot` for L^T.  Returns MK_ERR_INVALID_ARG if MH is not positive definite.
+int inverse_cholesky(mk_ctx* ctx, int n, const double* MH, double* Linv, int slot, cudaStream_t s) {
+  int err = MK_OK;
+  char* ws = (char*)scratch(ctx, slot, (size_t)n * n * 16 + 256, &err);
+  if (!ws) return err;
+  double* LT = (double*)ws;
+  double* I = LT + (size_t)n * n;
+  int* dflag = (int*)(I + (size_t)n * n);
+  MK_CUDA(cudaMemsetAsync(dflag, 0, sizeof(int), s));
+  MK_COUNT(), k_cholesky<<<1, 1024, 0, s>>>(n, MH, LT, dflag);
+  MK_COUNT(), k_identity<<<(int)(((int64_t)n * n + 255) / 256), 256, 0, s>>>(n, I);
+  MK_COUNT(), k_forward<<<(n + 127) / 128, 128, 0, s>>>(n, LT, I, Linv);
+  int h = 0;
+  MK_CUDA(cudaMemcpyAsync(&h, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MK_CUDA(cudaStreamSynchronize(s));
+  if (h) return fail(MK_ERR_INVALID_ARG, "M_H is not positive definite");
+  return MK_OK;
+}
+
+// Shared decomposition of the coarse pencil: C = Linv AH Linv^T, Jacobi C = Q diag Q^T, d ascending,
+// V = Linv^T Q (columns sorted with d).  V row-major [n x n], V[i][k] = component i of eigenvector k.
+int decompose(mk_ctx* ctx, int n, const double* Linv, const double* AH, double* d, double* V, cudaStream_t s) {
+  const int n2 = (n + 1) / 2 * 2;
+  int err = MK_OK;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
+  const size_t oT = take((size_t)n * n * 8), oC = take((size_t)n * n * 8), oS0 = take((size_t)n2 * n2 * 8);
+  const size_t oS1 = take((size_t)n2 * n2 * 8), oQ = take((size_t)n2 * n2 * 8), oRed = take(8192 * 8);
+  const size_t oPerm = take((size_t)n * 4), oInfo = take(64);
+  char* ws = (char*)scratch(ctx, S_EIG2, off, &err);
+  if (!ws) return err;
+  double *T = (double*)(ws + oT), *C = (double*)(ws + oC), *S0 = (double*)(ws + oS0), *S1 = (double*)(ws + oS1);
+  double *Q = (double*)(ws + oQ), *red = (double*)(ws + oRed);
+  int *perm = (int*)(ws + oPerm), *info = (int*)(ws + oInfo);
+  gemm64(n, n, n, Linv, n, 0, AH, n, 0, T, n, s);                   // T = Linv AH
+  gemm64(n, n, n, T, n, 0, Linv, n, 1, C, n, s);                    // C = T Linv^T
+  MK_COUNT(), k_pad_sym<<<(int)(((int64_t)n2 * n2 + 255) / 256), 256, 0, s>>>(n, n2, C, S0, Q, 0.0);
+  const int np = n2 / 2;
+  const size_t smem = (size_t)np * sizeof(Rot);
+  if (smem > 48 * 1024) MK_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  MK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi, 256, smem));
+  MK_ARG(per_sm >= 1, "mk: Jacobi kernel cannot be resident (coarse space too large)");
+  int grid = std::min(ctx->n_sms, 4096);
+  int max_sweeps = 60;
+  double tol = 1e-15;
+  int n2v = n2;
+  void* args[] = {&n2v, &S0, &S1, &Q, &red, &max_sweeps, &tol, &info};
+  MK_COUNT();
+  MK_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi, grid, 256, args, smem, s));
+  int hinfo[2];
+  MK_CUDA(cudaMemcpyAsync(hinfo, info, sizeof(hinfo), cudaMemcpyDeviceToHost, s));
+  MK_CUDA(cudaStreamSynchronize(s));
+  const double* Sf = hinfo[1] ? S1 : S0;
+  MK_COUNT(), k_rank<<<(n + 127) / 128, 128, 0, s>>>(n, n2, Sf, d, perm);
+  MK_COUNT(), k_gather_cols<<<(int)(((int64_t)n * n + 255) / 256), 256, 0, s>>>(n, n2, Q, perm, C);  // C = Q sorted
+  gemm64(n, n, n, Linv, n, 1, C, n, 0, V, n, s);                     // V = Linv^T Q
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
+int secular(mk_ctx* ctx, int n, int N, const double* d, const double* V, const double* b, const double* c,
+            const double* beta, const double* gamma, double* lambda, double* coef, int32_t* status, cudaStream_t s) {
+  int err = MK_OK;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
+  const size_t oG = take((size_t)n * 2 * N * 8), oW = take((size_t)N * kWorkVecs * (n + 1) * 8);
+  const size_t oIW = take((size_t)N * 4 * (n + 1) * 4);
+  char* ws = (char*)scratch(ctx, S_EIG, off, &err);
+  if (!ws) return err;
+  double *G = (double*)(ws + oG), *W = (double*)(ws + oW);
+  int* IW = (int*)(ws + oIW);
+  MK_COUNT(), k_vt_bc<<<(int)(((int64_t)n * 2 * N + 127) / 128), 128, 0, s>>>(n, N, V, b, c, G);
+  MK_COUNT(), k_secular_select<<<N, kEigThreads, 0, s>>>(n, N, d, V, G, beta, gamma, W, IW, lambda, coef, status,
+                                                        1e-7, 1e-12);
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
+// At mesh upload: M_H = P^T M P and its inverse Cholesky factor, kept in the mesh handle.
+int coarse_matrices(mk_ctx*, const mk_mesh*, const double*, const double*, double*, double*, int, cudaStream_t);
+
+int mesh_mass_factor(mk_ctx* ctx, mk_mesh* m) {
+  const Level& F = m->fine;
+  const int n = (int)m->coarse.n_free;
+  int err = MK_OK;
+  const size_t eb = (size_t)F.n_elems * (F.nloc * (F.nloc + 1) / 2) * sizeof(double);
+  double* Me = (double*)scratch(ctx, S_ELEM64D, eb, &err);
+  double* MH = (double*)scratch(ctx, S_VEC5, (size_t)n * n * sizeof(double) * 2, &err);
+  if (!Me || !MH) return err;
+  cudaStream_t s = 0;
+  MK_TRY(element_matrices(ctx, F, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s, S_NUC2));
+  MK_TRY(coarse_matrices(ctx, m, Me, Me, MH, MH + (size_t)n * n, S_COARSE2, s));
+  if (cudaMalloc(&m->d_MH_Linv, (size_t)n * n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MK_ERR_OOM, "mesh upload: M_H factor allocation failed");
+  }
+  MK_TRY(inverse_cholesky(ctx, n, MH, m->d_MH_Linv, S_EIG2, s));
+  MK_CUDA(cudaStreamSynchronize(s));
+  return MK_OK;
+}
+
 }  // namespace mk
 
 using namespace mk;
 
 extern "C" {
+
+int mk_coarse_decompose(mk_ctx* ctx, const mk_mesh* m, const double* AH, double* d, double* V, void* stream) {
+  MK_ARG(ctx && m && AH && d && V && m->d_MH_Linv, "mk_coarse_decompose: null argument");
+  MK_CUDA(cudaSetDevice(ctx->device));
+  return decompose(ctx, (int)m->coarse.n_free, m->d_MH_Linv, AH, d, V, (cudaStream_t)stream);
+}
+
+int mk_small_eigensolve_shared(mk_ctx* ctx, int NH, int N, const double* d, const double* V, const double* b,
+                               const double* c, const double* beta, const double* gamma, double* lambda,
+                               double* coef, int32_t* status, void* stream) {
+  MK_ARG(ctx && d && V && b && c && beta && gamma && lambda && coef && status,
+         "mk_small_eigensolve_shared: null argument");
+  MK_ARG(NH >= 1 && N >= 1 && N <= MK_MAX_RHS, "mk_small_eigensolve_shared: bad sizes");
+  MK_CUDA(cudaSetDevice(ctx->device));
+  return secular(ctx, NH, N, d, V, b, c, beta, gamma, lambda, coef, status, (cudaStream_t)stream);
+}
 
 int mk_small_eigensolve(mk_ctx* ctx, int NH, int N, const double* AH, const double* MH, const double* b,
                         const double* c, const double* beta, const double* gamma, double* lambda, double* coef,
@@ -533,55 +702,16 @@ int mk_small_eigensolve(mk_ctx* ctx, int NH, int N, const double* AH, const doub
   MK_ARG(NH >= 1 && N >= 1 && N <= MK_MAX_RHS, "mk_small_eigensolve: bad sizes");
   MK_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
-  const int n = NH, n2 = (n + 1) / 2 * 2;
   int err = MK_OK;
-  // workspace layout
-  size_t off = 0;
-  auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
-  const size_t oLT = take((size_t)n * n * 8), oX = take((size_t)n * n * 8), oC = take((size_t)n * n * 8);
-  const size_t oS = take((size_t)n2 * n2 * 8), oQ = take((size_t)n2 * n2 * 8), oV = take((size_t)n * n * 8);
-  const size_t oRot = take((size_t)(n2 / 2) * sizeof(Rot)), oRed = take(4096 * 8), oD = take((size_t)n * 8);
-  const size_t oPerm = take((size_t)n * 4), oG = take((size_t)n * 2 * N * 8), oFlag = take(64);
-  const size_t oW = take((size_t)N * kWorkVecs * (n + 1) * 8), oIW = take((size_t)N * 4 * (n + 1) * 4);
-  char* ws = (char*)scratch(ctx, S_EIG, off, &err);
-  if (!ws) return err;
-  double *LT = (double*)(ws + oLT), *X = (double*)(ws + oX), *C = (double*)(ws + oC), *S = (double*)(ws + oS);
-  double *Q = (double*)(ws + oQ), *V = (double*)(ws + oV), *red = (double*)(ws + oRed), *d = (double*)(ws + oD);
-  double *G = (double*)(ws + oG), *W = (double*)(ws + oW);
-  int *perm = (int*)(ws + oPerm), *flag = (int*)(ws + oFlag), *IW = (int*)(ws + oIW);
-  Rot* rot = (Rot*)(ws + oRot);
-  MK_CUDA(cudaMemsetAsync(flag, 0, 64, s));
-  k_cholesky<<<1, 1024, 0, s>>>(n, MH, LT, flag);
-  const int tb = 128, nb = (n + tb - 1) / tb;
-  k_forward<<<nb, tb, 0, s>>>(n, LT, AH, X);                         // X = L^-1 A
-  k_transpose<<<(int)(((int64_t)n * n + 255) / 256), 256, 0, s>>>(n, X, C);
-  k_forward<<<nb, tb, 0, s>>>(n, LT, C, X);                          // X = L^-1 (L^-1 A)^T = L^-1 A L^-T
-  k_pad_sym<<<(int)(((int64_t)n2 * n2 + 255) / 256), 256, 0, s>>>(n, n2, X, S, Q, 0.0);
-  // pad row: a decoupled eigenvalue far above the spectrum is not needed because off-diagonals are 0; any value works
-  MK_CUDA(cudaGetLastError());
-  {
-    int dev_blocks = 0;
-    MK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&dev_blocks, k_jacobi, 256, 0));
-    int grid = std::min(ctx->n_sms * std::max(1, dev_blocks), 4096 / 2);
-    grid = std::max(1, std::min(grid, ctx->n_sms * 2));
-    int max_sweeps = 40;
-    double tol = 1e-15;
-    int* sweeps_out = flag + 1;
-    int n2v = n2;
-    void* args[] = {&n2v, &S, &Q, &rot, &red, &max_sweeps, &tol, &sweeps_out};
-    MK_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi, grid, 256, args, 0, s));
-  }
-  k_rank<<<nb, tb, 0, s>>>(n, n2, S, d, perm);
-  k_gather_cols<<<(int)(((int64_t)n * n + 255) / 256), 256, 0, s>>>(n, n2, Q, perm, C);   // C = Q sorted
-  k_backward<<<nb, tb, 0, s>>>(n, LT, C, V, n, n);                                         // V = L^-T Q
-  k_vt_bc<<<(int)(((int64_t)n * 2 * N + 127) / 128), 128, 0, s>>>(n, N, V, b, c, G);
-  k_secular_select<<<N, kEigThreads, 0, s>>>(n, N, d, V, G, beta, gamma, W, IW, lambda, coef, status, 1e-7, 1e-12);
-  MK_CUDA(cudaGetLastError());
-  int hflag[2] = {0, 0};
-  MK_CUDA(cudaMemcpyAsync(hflag, flag, sizeof(hflag), cudaMemcpyDeviceToHost, s));
-  MK_CUDA(cudaStreamSynchronize(s));
-  if (hflag[0]) return fail(MK_ERR_INVALID_ARG, "mk_small_eigensolve: M_H is not positive definite");
-  return MK_OK;
+  double* buf = (double*)scratch(ctx, S_EIG3, (size_t)NH * NH * 2 * sizeof(double) + (size_t)NH * sizeof(double) + 256,
+                                 &err);
+  if (!buf) return err;
+  double* Linv = buf;
+  double* V = buf + (size_t)NH * NH;
+  double* d = V + (size_t)NH * NH;
+  MK_TRY(inverse_cholesky(ctx, NH, MH, Linv, S_EIG4, s));
+  MK_TRY(decompose(ctx, NH, Linv, AH, d, V, s));
+  return secular(ctx, NH, N, d, V, b, c, beta, gamma, lambda, coef, status, s);
 }
 
 int mk_orbital_assemble(mk_ctx* ctx, const mk_mesh* m, const double* coef, const double* psihat, const double* u,
@@ -598,12 +728,12 @@ int mk_orbital_assemble(mk_ctx* ctx, const mk_mesh* m, const double* coef, const
   double* dots = (double*)scratch(ctx, S_COEF, 64 * sizeof(double), &err);
   if (!Me || !Mu || !dots) return err;
   const int64_t work = F.n_nodes * ld;
-  k_orbitals<<<(int)((work + 255) / 256), 256, 0, s>>>(F.n_nodes, m->d_P_off, m->d_P_col, m->d_P_val, F.d_boundary,
+  MK_COUNT(), k_orbitals<<<(int)((work + 255) / 256), 256, 0, s>>>(F.n_nodes, m->d_P_off, m->d_P_col, m->d_P_val, F.d_boundary,
                                                        coef, (int)m->coarse.n_free, psihat, N, ld, psi);
   MK_TRY(element_matrices(ctx, F, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s));
   MK_TRY(apply64(ctx, F, Me, u, Mu, N, ld, true, s));
   MK_TRY(column_dots(ctx, F.n_nodes, psi, Mu, N, ld, dots, s));
-  k_flip<<<(int)((work + 255) / 256), 256, 0, s>>>(F.n_nodes, dots, psi, N, ld);
+  MK_COUNT(), k_flip<<<(int)((work + 255) / 256), 256, 0, s>>>(F.n_nodes, dots, psi, N, ld);
   MK_CUDA(cudaGetLastError());
   return MK_OK;
 }

@@ -22,8 +22,8 @@ static int column_dots_t(mk_ctx* ctx, int64_t n_nodes, const T* a, const T* b, i
   const int nblk = red_blocks(ctx);
   double* part = (double*)scratch(ctx, S_RED, (size_t)nblk * N * sizeof(double), &err);
   if (!part) return err;
-  k_dot_partial<T><<<nblk, kRedThreads, kRedThreads * sizeof(double), s>>>(n_nodes, a, b, N, ld, part);
-  k_sum_partials<<<(N + 63) / 64, 64, 0, s>>>(part, nblk, N, out);
+  MK_COUNT(), k_dot_partial<T><<<nblk, kRedThreads, kRedThreads * sizeof(double), s>>>(n_nodes, a, b, N, ld, part);
+  MK_COUNT(), k_sum_partials<<<(N + 63) / 64, 64, 0, s>>>(part, nblk, N, out);
   MK_CUDA(cudaGetLastError());
   return MK_OK;
 }
@@ -38,9 +38,9 @@ int column_dots32(mk_ctx* ctx, int64_t n_nodes, const float* a, const float* b, 
 }
 
 // ------------------------------------------------------------------------------------------------ nuclei
-double* upload_nuclei(mk_ctx* ctx, const mk_molecule* mol, int* err, cudaStream_t s) {
+double* upload_nuclei(mk_ctx* ctx, const mk_molecule* mol, int* err, cudaStream_t s, int slot) {
   const int n = mol ? mol->n_nuclei : 0;
-  double* d = (double*)scratch(ctx, S_NUC, (size_t)(4 * n + 4) * sizeof(double), err);
+  double* d = (double*)scratch(ctx, slot, (size_t)(4 * n + 4) * sizeof(double), err);
   if (!d) return nullptr;
   if (n > 0) {
     std::vector<double> h(4 * n);
@@ -118,18 +118,18 @@ __global__ void k_element_matrices(int64_t E, const RefTables* __restrict__ ref,
 }
 
 int element_matrices(mk_ctx* ctx, const Level& L, const mk_molecule* mol, double half_k, double vext_scale,
-                     double mass_shift, const double* vq, double* out, cudaStream_t s) {
+                     double mass_shift, const double* vq, double* out, cudaStream_t s, int nuc_slot) {
   int err = MK_OK;
-  double* nuc = upload_nuclei(ctx, mol, &err, s);
+  double* nuc = upload_nuclei(ctx, mol, &err, s, nuc_slot);
   if (!nuc) return err;
   const int nnuc = mol ? mol->n_nuclei : 0;
   const int th = 128;
   const int blocks = (int)((L.n_elems + th - 1) / th);
   if (L.nloc == 4)
-    k_element_matrices<4><<<blocks, th, 0, s>>>(L.n_elems, ctx->d_ref[1], L.d_geom, nnuc, nuc, half_k, vext_scale,
+    MK_COUNT(), k_element_matrices<4><<<blocks, th, 0, s>>>(L.n_elems, ctx->d_ref[1], L.d_geom, nnuc, nuc, half_k, vext_scale,
                                                 mass_shift, vq, out);
   else
-    k_element_matrices<10><<<blocks, th, 0, s>>>(L.n_elems, ctx->d_ref[2], L.d_geom, nnuc, nuc, half_k, vext_scale,
+    MK_COUNT(), k_element_matrices<10><<<blocks, th, 0, s>>>(L.n_elems, ctx->d_ref[2], L.d_geom, nnuc, nuc, half_k, vext_scale,
                                                  mass_shift, vq, out);
   MK_CUDA(cudaGetLastError());
   return MK_OK;
@@ -163,22 +163,23 @@ int assemble_diagonal(mk_ctx* ctx, const Level& L, const double* Ae, double* dia
     const int64_t off = L.colour_off[c], cnt = L.colour_off[c + 1] - off;
     const int blocks = (int)((cnt + 255) / 256);
     if (L.nloc == 4)
-      k_diag_colour<4><<<blocks, 256, 0, s>>>(L.d_colour_elems + off, (int)cnt, L.d_elem, Ae, diag);
+      MK_COUNT(), k_diag_colour<4><<<blocks, 256, 0, s>>>(L.d_colour_elems + off, (int)cnt, L.d_elem, Ae, diag);
     else
-      k_diag_colour<10><<<blocks, 256, 0, s>>>(L.d_colour_elems + off, (int)cnt, L.d_elem, Ae, diag);
+      MK_COUNT(), k_diag_colour<10><<<blocks, 256, 0, s>>>(L.d_colour_elems + off, (int)cnt, L.d_elem, Ae, diag);
   }
-  k_mask_rows<<<(int)((L.n_nodes + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, diag, 1, 1, 1.0);
+  MK_COUNT(), k_mask_rows<<<(int)((L.n_nodes + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, diag, 1, 1, 1.0);
   MK_CUDA(cudaGetLastError());
   return MK_OK;
 }
 
 int apply64(mk_ctx* ctx, const Level& L, const double* Ae, const double* x, double* y, int N, int ld,
             bool mask_boundary, cudaStream_t s) {
-  (void)ctx;
+  prof_mark(ctx, PROF_APPLY64, true, s);
   MK_CUDA(cudaMemsetAsync(y, 0, (size_t)L.n_nodes * ld * sizeof(double), s));
   apply_coloured<double>(L, Ae, x, y, N, ld, s);
+  prof_mark(ctx, PROF_APPLY64, false, s);
   if (mask_boundary)
-    k_mask_rows<<<(int)((L.n_nodes * N + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, y, N, ld, 0.0);
+    MK_COUNT(), k_mask_rows<<<(int)((L.n_nodes * N + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, y, N, ld, 0.0);
   MK_CUDA(cudaGetLastError());
   return MK_OK;
 }
@@ -233,7 +234,7 @@ int restrict_to_coarse(mk_ctx* ctx, const mk_mesh* m, const double* y, int ld, i
                        cudaStream_t s) {
   (void)ctx;
   const int th = 128;
-  k_restrict<<<(int)m->coarse.n_free, th, 8 * th * sizeof(double), s>>>(m->d_PT_off, m->d_PT_col, m->d_PT_val, y,
+  MK_COUNT(), k_restrict<<<(int)m->coarse.n_free, th, 8 * th * sizeof(double), s>>>(m->d_PT_off, m->d_PT_col, m->d_PT_val, y,
                                                                           ld, N, out, ldo);
   MK_CUDA(cudaGetLastError());
   return MK_OK;
@@ -243,7 +244,7 @@ int prolongate(mk_ctx* ctx, const mk_mesh* m, const double* psiH, int ldc, int N
                cudaStream_t s) {
   (void)ctx;
   const Level& F = m->fine;
-  k_prolong<<<(int)((F.n_nodes * ld + 255) / 256), 256, 0, s>>>(F.n_nodes, m->d_P_off, m->d_P_col, m->d_P_val,
+  MK_COUNT(), k_prolong<<<(int)((F.n_nodes * ld + 255) / 256), 256, 0, s>>>(F.n_nodes, m->d_P_off, m->d_P_col, m->d_P_val,
                                                                  F.d_boundary, psiH, ldc, N, u, ld);
   MK_CUDA(cudaGetLastError());
   return MK_OK;
@@ -329,9 +330,9 @@ int density(mk_ctx* ctx, const Level& L, const double* u, int ld, int N, const d
   MK_CUDA(cudaStreamSynchronize(s));
   const int th = 128, blocks = (int)((L.n_elems + th - 1) / th);
   if (L.nloc == 4)
-    k_density<4><<<blocks, th, 0, s>>>(L.n_elems, ctx->d_ref[1], L.d_elem, u, ld, N, occ, rho);
+    MK_COUNT(), k_density<4><<<blocks, th, 0, s>>>(L.n_elems, ctx->d_ref[1], L.d_elem, u, ld, N, occ, rho);
   else
-    k_density<10><<<blocks, th, 0, s>>>(L.n_elems, ctx->d_ref[2], L.d_elem, u, ld, N, occ, rho);
+    MK_COUNT(), k_density<10><<<blocks, th, 0, s>>>(L.n_elems, ctx->d_ref[2], L.d_elem, u, ld, N, occ, rho);
   MK_CUDA(cudaGetLastError());
   return MK_OK;
 }
@@ -340,9 +341,9 @@ int frozen_potential(mk_ctx* ctx, const Level& L, const double* w, const double*
                      cudaStream_t s) {
   const int th = 128, blocks = (int)((L.n_elems + th - 1) / th);
   if (L.nloc == 4)
-    k_frozen_potential<4><<<blocks, th, 0, s>>>(L.n_elems, ctx->d_ref[1], L.d_elem, w, rho, xc.kind, xc.alpha, vq);
+    MK_COUNT(), k_frozen_potential<4><<<blocks, th, 0, s>>>(L.n_elems, ctx->d_ref[1], L.d_elem, w, rho, xc.kind, xc.alpha, vq);
   else
-    k_frozen_potential<10><<<blocks, th, 0, s>>>(L.n_elems, ctx->d_ref[2], L.d_elem, w, rho, xc.kind, xc.alpha, vq);
+    MK_COUNT(), k_frozen_potential<10><<<blocks, th, 0, s>>>(L.n_elems, ctx->d_ref[2], L.d_elem, w, rho, xc.kind, xc.alpha, vq);
   MK_CUDA(cudaGetLastError());
   return MK_OK;
 }
@@ -375,10 +376,10 @@ int load_vector(mk_ctx* ctx, const Level& L, const double* rho, double scale, do
     const int64_t off = L.colour_off[c], cnt = L.colour_off[c + 1] - off;
     const int blocks = (int)((cnt + 127) / 128);
     if (L.nloc == 4)
-      k_load_colour<4><<<blocks, 128, 0, s>>>(L.d_colour_elems + off, (int)cnt, ctx->d_ref[1], L.d_elem, L.d_geom,
+      MK_COUNT(), k_load_colour<4><<<blocks, 128, 0, s>>>(L.d_colour_elems + off, (int)cnt, ctx->d_ref[1], L.d_elem, L.d_geom,
                                              rho, scale, F);
     else
-      k_load_colour<10><<<blocks, 128, 0, s>>>(L.d_colour_elems + off, (int)cnt, ctx->d_ref[2], L.d_elem, L.d_geom,
+      MK_COUNT(), k_load_colour<10><<<blocks, 128, 0, s>>>(L.d_colour_elems + off, (int)cnt, ctx->d_ref[2], L.d_elem, L.d_geom,
                                               rho, scale, F);
   }
   MK_CUDA(cudaGetLastError());
@@ -443,9 +444,9 @@ int multipole_boundary(mk_ctx* ctx, const Level& L, const double* rho, const dou
   double* part = (double*)scratch(ctx, S_RED, (size_t)nblk * 10 * sizeof(double), &err);
   double* mom = (double*)scratch(ctx, S_SCAL, 64 * sizeof(double), &err);
   if (!part || !mom) return err;
-  k_moments<<<nblk, kRedThreads, 0, s>>>(L.n_elems, ctx->d_ref[L.order], L.d_geom, rho, part);
-  k_sum_partials<<<1, 64, 0, s>>>(part, nblk, 10, mom);
-  k_multipole_bc<<<(int)((L.n_nodes + 255) / 256), 256, 0, s>>>(L.n_nodes, d_nodes, L.d_boundary, mom,
+  MK_COUNT(), k_moments<<<nblk, kRedThreads, 0, s>>>(L.n_elems, ctx->d_ref[L.order], L.d_geom, rho, part);
+  MK_COUNT(), k_sum_partials<<<1, 64, 0, s>>>(part, nblk, 10, mom);
+  MK_COUNT(), k_multipole_bc<<<(int)((L.n_nodes + 255) / 256), 256, 0, s>>>(L.n_nodes, d_nodes, L.d_boundary, mom,
                                                                  bc == MK_BC_MULTIPOLE, w);
   MK_CUDA(cudaGetLastError());
   return MK_OK;

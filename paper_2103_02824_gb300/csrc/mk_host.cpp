@@ -9,6 +9,7 @@
 namespace mk {
 
 static thread_local std::string g_err;
+std::atomic<long long> g_launch_count{0};
 
 void set_error(const std::string& msg) { g_err = msg; }
 int fail(int code, const std::string& msg) {
@@ -139,6 +140,21 @@ void build_ref_tables(int order, RefTables* t) {
       t->node_bary[4 + e][kEdgeA[e]] = 0.5;
       t->node_bary[4 + e][kEdgeB[e]] = 0.5;
     }
+}
+
+// ------------------------------------------------------------------------------------------------ profiling
+void prof_mark(mk_ctx* ctx, int kind, bool begin, cudaStream_t s) {
+  if (!ctx->prof_on) return;
+  auto& ev = ctx->prof_ev[kind];
+  int& used = ctx->prof_used[kind];
+  const size_t idx = 2 * (size_t)used + (begin ? 0 : 1);
+  if (idx >= ev.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    ev.push_back(e);
+  }
+  cudaEventRecord(ev[idx], s);
+  if (!begin) ++used;
 }
 
 // ------------------------------------------------------------------------------------------------ scratch
@@ -372,7 +388,8 @@ static void free_level(Level& L) {
   L.d_geom = nullptr;
 }
 
-int build_patches(mk_mesh* m);  // mk_patches.cpp
+int build_patches(mk_mesh* m);                 // mk_patches.cpp
+int mesh_mass_factor(mk_ctx* ctx, mk_mesh* m);  // mk_eig.cu
 void free_patches(mk::Patches& p);
 
 }  // namespace mk
@@ -390,6 +407,29 @@ int mk_last_error(char* buf, size_t len) {
 }
 
 const char* mk_version(void) { return "mk 0.1 (sm_103a)"; }
+
+long long mk_launch_count(void) { return g_launch_count.load(std::memory_order_relaxed); }
+
+int mk_profile_enable(mk_ctx* ctx, int on) {
+  MK_ARG(ctx, "mk_profile_enable: null ctx");
+  ctx->prof_on = on != 0;
+  for (int k = 0; k < 4; ++k) ctx->prof_used[k] = 0;
+  return MK_OK;
+}
+
+int mk_profile_read(mk_ctx* ctx, int kind, double* total_ms, long long* count) {
+  MK_ARG(ctx && total_ms && count && kind >= 0 && kind < 4, "mk_profile_read: bad argument");
+  double t = 0.0;
+  for (int i = 0; i < ctx->prof_used[kind]; ++i) {
+    float ms = 0.f;
+    MK_CUDA(cudaEventSynchronize(ctx->prof_ev[kind][2 * i + 1]));
+    MK_CUDA(cudaEventElapsedTime(&ms, ctx->prof_ev[kind][2 * i], ctx->prof_ev[kind][2 * i + 1]));
+    t += ms;
+  }
+  *total_ms = t;
+  *count = ctx->prof_used[kind];
+  return MK_OK;
+}
 
 int mk_ctx_create(mk_ctx** out, int device) {
   MK_ARG(out, "mk_ctx_create: null out");
@@ -415,6 +455,8 @@ int mk_ctx_destroy(mk_ctx* c) {
   for (void* p : c->slot_ptr) cudaFree(p);
   for (int o = 1; o <= 2; ++o) cudaFree(c->d_ref[o]);
   if (c->pinned) cudaFreeHost(c->pinned);
+  for (auto& v : c->prof_ev)
+    for (cudaEvent_t e : v) cudaEventDestroy(e);
   delete c;
   return MK_OK;
 }
@@ -498,6 +540,7 @@ int mk_mesh_upload(mk_ctx* ctx, const mk_mesh_desc* fine, const mk_mesh_desc* co
   if (r == MK_OK) r = upload(&m->d_child_off, ch_off.data(), ch_off.size());
   if (r == MK_OK) r = upload(&m->d_child, ch.data(), ch.size());
   if (r == MK_OK) r = build_patches(m);
+  if (r == MK_OK) r = mesh_mass_factor(ctx, m);
   if (r != MK_OK) { mk_mesh_destroy(m); return r; }
   *out = m;
   return MK_OK;
@@ -512,6 +555,7 @@ int mk_mesh_destroy(mk_mesh* m) {
   cudaFree(m->d_PT_off); cudaFree(m->d_PT_col); cudaFree(m->d_PT_val);
   cudaFree(m->d_child_off); cudaFree(m->d_child);
   free_patches(m->patches);
+  cudaFree(m->d_MH_Linv);
   delete m;
   return MK_OK;
 }

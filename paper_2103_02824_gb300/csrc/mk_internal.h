@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -10,6 +11,10 @@
 #include "../../include/mk.h"
 
 namespace mk {
+
+// Every kernel launch of the library goes through MK_COUNT() so callers can read how many ran (mk_launch_count).
+extern std::atomic<long long> g_launch_count;
+#define MK_COUNT() (::mk::g_launch_count.fetch_add(1, std::memory_order_relaxed))
 
 // ------------------------------------------------------------------------------------------------ errors
 void set_error(const std::string& msg);
@@ -92,17 +97,17 @@ struct Level {
 struct Patches {
   int n_patches = 0, max_elems = 0, max_nodes = 0;
   int64_t n_halo_slots = 0, n_shared_nodes = 0;
-  int32_t* d_patch_elem_off = nullptr;   // [P+1] into patch element arrays (elements reordered by patch)
-  int32_t* d_patch_node_off = nullptr;   // [P+1] into patch node arrays
+  int32_t* d_patch_elem_off = nullptr;   // [P+1] patch p owns patch-ordered elements [off[p], off[p+1])
+  int32_t* d_patch_node_off = nullptr;   // [P+1] its local nodes are [off[p], off[p+1]) of the node arrays
   int32_t* d_elem_id = nullptr;          // [E] original element id of each patch-ordered element
-  uint16_t* d_local_conn = nullptr;      // [E*nloc] local node index inside its patch
+  int32_t* d_conn = nullptr;             // [E*nloc] global nodes of the patch-ordered elements
   int32_t* d_node_target = nullptr;      // [sum nodes] >= 0: global node written directly; < 0: -(halo slot)-1
-  int32_t* d_node_global = nullptr;      // [sum nodes] global node id (for gathers)
-  int32_t* d_inc_off = nullptr;          // [sum nodes + P] per local node: offsets into incidence list (per patch)
-  uint16_t* d_inc = nullptr;             // [E*nloc] (local element * nloc + local slot) of each incidence
-  int32_t* d_shared_node = nullptr;      // [n_shared] global node
-  int32_t* d_shared_off = nullptr;       // [n_shared+1] into halo slots (slots of one node in patch order)
+  int32_t* d_inc_off = nullptr;          // [sum nodes + 1] start of each local node's incidences (global index)
+  uint16_t* d_inc = nullptr;             // [E*nloc] incidence = local element * nloc + local slot, fixed order
+  int32_t* d_shared_node = nullptr;      // [n_shared] global node of each shared node
+  int32_t* d_shared_off = nullptr;       // [n_shared+1] its halo slots (one per patch, in patch order)
 };
+int patch_elems(int nloc);
 
 }  // namespace mk
 
@@ -116,7 +121,17 @@ struct mk_ctx {
   std::vector<size_t> slot_size;
   void* pinned = nullptr;  // small pinned host buffer for reports
   size_t pinned_size = 0;
+  // optional CUDA-event timing of operator applications (mk_profile_*): [kind][2*i], [2*i+1] start/stop
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_ev[4];
+  int prof_used[4] = {0, 0, 0, 0};
 };
+
+namespace mk {
+// Record a start (begin=true) or stop event for profiled operation `kind` on stream s (no-op unless enabled).
+void prof_mark(mk_ctx* ctx, int kind, bool begin, cudaStream_t s);
+enum ProfKind { PROF_APPLY64 = 0, PROF_APPLY32 = 1, PROF_HALO = 2, PROF_OTHER = 3 };
+}  // namespace mk
 
 struct mk_mesh {
   mk_ctx* ctx = nullptr;
@@ -135,7 +150,9 @@ struct mk_mesh {
   int32_t* d_child_off = nullptr;
   int32_t* d_child = nullptr;
   mk::Patches patches;
-  // Jacobi diagonal pieces: diagonals of K/2 and M per node are molecule-independent
+  // M_H = P^T M P depends on the meshes only (it stays fixed, like the paper's M_H): its inverse Cholesky factor
+  // Linv = L^-1 (M_H = L L^T), dense row-major [N_H*N_H], is computed once at upload.
+  double* d_MH_Linv = nullptr;
 };
 
 namespace mk {
@@ -161,6 +178,12 @@ enum Slot : int {
   S_COEF,         // small per-column coefficient arrays
   S_VEC4, S_VEC5,
   S_GRAM,
+  S_ELEM64C, S_ELEM64D,         // element matrices of the coarse-pencil path (may run on another stream)
+  S_NUC2, S_COARSE2,
+  S_EIG2,                       // workspace of the shared coarse decomposition
+  S_EIG3, S_EIG4,               // general (unshared) eigensolve: factor + decomposition, Cholesky workspace
+  S_HALO64,                     // halo partial sums of the FP64 patch operator
+  S_OPA, S_OPB,                 // element matrices of mk_operator_apply (FP64 original order, patch order)
   S_COUNT
 };
 void* scratch(mk_ctx* ctx, int slot, size_t bytes, int* err);

@@ -1,13 +1,531 @@
-// Mixed-precision correction solve (filled in by the FP32 operator work).
+// Mixed-precision correction solve: FP32 patch-based operator inside PCG, FP64 residuals and iterative refinement.
+//
+// The operator A = K/2 + M_{V_ext} + sigma M is applied element by element from FP32 element matrices stored in
+// patch order; the FP64 residual b - A x is recomputed with the FP64 element matrices after every inner solve and
+// decides convergence, so the answer is the FP64 answer to rtol whatever the inner precision.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
 #include "mk_device.cuh"
 
 namespace mk {
 
-int solve_mixed(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, double sigma, const double* rhs,
+// ------------------------------------------------------------------------------------------------ vectors
+template <typename T, int VEC>
+struct Vec {
+  T v[VEC];
+};
+
+template <typename T, int VEC>
+__device__ __forceinline__ Vec<T, VEC> ldv(const T* __restrict__ p) {
+  Vec<T, VEC> r;
+  if constexpr (VEC == 4 && sizeof(T) == 4) {
+    const float4 f = *reinterpret_cast<const float4*>(p);
+    r.v[0] = f.x; r.v[1] = f.y; r.v[2] = f.z; r.v[3] = f.w;
+  } else if constexpr (VEC == 2 && sizeof(T) == 8) {
+    const double2 f = *reinterpret_cast<const double2*>(p);
+    r.v[0] = f.x; r.v[1] = f.y;
+  } else {
+#pragma unroll
+    for (int c = 0; c < VEC; ++c) r.v[c] = p[c];
+  }
+  return r;
+}
+
+template <typename T, int VEC>
+__device__ __forceinline__ void stv(T* __restrict__ p, const Vec<T, VEC>& r) {
+  if constexpr (VEC == 4 && sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+  } else if constexpr (VEC == 2 && sizeof(T) == 8) {
+    *reinterpret_cast<double2*>(p) = make_double2(r.v[0], r.v[1]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < VEC; ++c) p[c] = r.v[c];
+  }
+}
+
+// ------------------------------------------------------------------------------------------------ patch apply
+// One CTA per patch.  Phase 1: element products y_e = A_e x_e into shared memory (one thread per element and
+// group of VEC columns).  Phase 2: each local node sums its incidences in fixed order and writes the global row
+// (owned node) or its halo slot (shared node).  Columns [col0, col0 + W) with W = ncolg * VEC.
+template <int NLOC, typename T, int VEC>
+__global__ void __launch_bounds__(256) k_apply_patch(const int32_t* __restrict__ elem_off,
+                                                     const int32_t* __restrict__ node_off,
+                                                     const int32_t* __restrict__ conn, const T* __restrict__ Ae,
+                                                     const int32_t* __restrict__ target,
+                                                     const int32_t* __restrict__ inc_off,
+                                                     const uint16_t* __restrict__ inc,
+                                                     const uint8_t* __restrict__ bnd, int mask,
+                                                     const T* __restrict__ x, T* __restrict__ y, T* __restrict__ halo,
+                                                     int ncolg, int col0, int ld) {
+  constexpr int NP = NLOC * (NLOC + 1) / 2;
+  extern __shared__ unsigned char smraw[];
+  T* Ye = reinterpret_cast<T*>(smraw);
+  const int p = blockIdx.x;
+  const int e0 = elem_off[p], ne = elem_off[p + 1] - e0;
+  const int n0 = node_off[p], nl = node_off[p + 1] - n0;
+  const int W = ncolg * VEC;
+  for (int it = threadIdx.x; it < ne * ncolg; it += blockDim.x) {
+    const int el = it / ncolg, g = it - el * ncolg;
+    const int64_t e = e0 + el;
+    Vec<T, VEC> xv[NLOC];
+#pragma unroll
+    for (int a = 0; a < NLOC; ++a) xv[a] = ldv<T, VEC>(x + (int64_t)conn[e * NLOC + a] * ld + col0 + g * VEC);
+    const T* A = Ae + e * NP;
+    T Ar[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) Ar[k] = A[k];
+#pragma unroll
+    for (int a = 0; a < NLOC; ++a) {
+      Vec<T, VEC> acc;
+#pragma unroll
+      for (int c = 0; c < VEC; ++c) acc.v[c] = 0;
+#pragma unroll
+      for (int b = 0; b < NLOC; ++b) {
+        const T w = Ar[sym_index(a, b, NLOC)];
+#pragma unroll
+        for (int c = 0; c < VEC; ++c) acc.v[c] += w * xv[b].v[c];
+      }
+      stv<T, VEC>(Ye + (el * NLOC + a) * W + g * VEC, acc);
+    }
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < nl * ncolg; it += blockDim.x) {
+    const int l = it / ncolg, g = it - l * ncolg;
+    const int b = inc_off[n0 + l], e = inc_off[n0 + l + 1];
+    Vec<T, VEC> acc;
+#pragma unroll
+    for (int c = 0; c < VEC; ++c) acc.v[c] = 0;
+    for (int k = b; k < e; ++k) {
+      const Vec<T, VEC> v = ldv<T, VEC>(Ye + (int)inc[k] * W + g * VEC);
+#pragma unroll
+      for (int c = 0; c < VEC; ++c) acc.v[c] += v.v[c];
+    }
+    const int t = target[n0 + l];
+    if (t >= 0) {
+      if (mask && bnd[t])
+#pragma unroll
+        for (int c = 0; c < VEC; ++c) acc.v[c] = 0;
+      stv<T, VEC>(y + (int64_t)t * ld + col0 + g * VEC, acc);
+    } else {
+      stv<T, VEC>(halo + (int64_t)(-t - 1) * ld + col0 + g * VEC, acc);
+    }
+  }
+}
+
+// Shared nodes: y[node] = sum of the node's halo slots in patch order.
+template <typename T, int VEC>
+__global__ void k_halo(int64_t nshared, const int32_t* __restrict__ node, const int32_t* __restrict__ off,
+                       const uint8_t* __restrict__ bnd, int mask, const T* __restrict__ halo, T* __restrict__ y,
+                       int ncolg, int col0, int ld) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nshared * ncolg) return;
+  const int64_t k = t / ncolg;
+  const int g = (int)(t - k * ncolg);
+  Vec<T, VEC> acc;
+#pragma unroll
+  for (int c = 0; c < VEC; ++c) acc.v[c] = 0;
+  for (int s = off[k]; s < off[k + 1]; ++s) {
+    const Vec<T, VEC> v = ldv<T, VEC>(halo + (int64_t)s * ld + col0 + g * VEC);
+#pragma unroll
+    for (int c = 0; c < VEC; ++c) acc.v[c] += v.v[c];
+  }
+  const int nd = node[k];
+  if (mask && bnd[nd])
+#pragma unroll
+    for (int c = 0; c < VEC; ++c) acc.v[c] = 0;
+  stv<T, VEC>(y + (int64_t)nd * ld + col0 + g * VEC, acc);
+}
+
+template <typename T>
+__global__ void k_pack_elements(int64_t E, int np, const int32_t* __restrict__ elem_id, const double* __restrict__ A64,
+                                T* __restrict__ A) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= E * np) return;
+  const int64_t i = t / np;
+  const int k = (int)(t - i * np);
+  A[t] = (T)A64[(int64_t)elem_id[i] * np + k];
+}
+
+// y = A x with the patch operator (all ld columns), FP32 or FP64.
+template <typename T>
+int apply_patch(mk_ctx* ctx, const mk_mesh* m, const T* Ae, const T* x, T* y, int ld, bool mask, cudaStream_t s) {
+  const Patches& P = m->patches;
+  const Level& L = m->fine;
+  int err = MK_OK;
+  T* halo = (T*)scratch(ctx, sizeof(T) == 4 ? S_HALO : S_HALO64, (size_t)std::max<int64_t>(P.n_halo_slots, 1) * ld * sizeof(T), &err);
+  if (!halo) return err;
+  constexpr int VEC = sizeof(T) == 4 ? 4 : 2;
+  const int vec = (ld % VEC == 0) ? VEC : 1;
+  const int wmax = sizeof(T) == 4 ? 16 : 8;  // columns per pass (shared memory)
+  const int nloc = L.nloc;
+  for (int col0 = 0; col0 < ld; col0 += wmax) {
+    const int W = std::min(wmax, ld - col0);
+    const int ncolg = W / vec;
+    const size_t smem = (size_t)P.max_elems * nloc * W * sizeof(T);
+    prof_mark(ctx, PROF_APPLY32, true, s);
+#define MK_PATCH_LAUNCH(NL, V)                                                                                       \
+  do {                                                                                                              \
+    auto kern = k_apply_patch<NL, T, V>;                                                                            \
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
+    MK_COUNT(), kern<<<P.n_patches, 256, smem, s>>>(P.d_patch_elem_off, P.d_patch_node_off, P.d_conn, Ae,            \
+                                                    P.d_node_target, P.d_inc_off, P.d_inc, L.d_boundary, mask, x, y, \
+                                                    halo, ncolg, col0, ld);                                         \
+  } while (0)
+    if (nloc == 4) {
+      if (vec == VEC) MK_PATCH_LAUNCH(4, VEC); else MK_PATCH_LAUNCH(4, 1);
+    } else {
+      if (vec == VEC) MK_PATCH_LAUNCH(10, VEC); else MK_PATCH_LAUNCH(10, 1);
+    }
+#undef MK_PATCH_LAUNCH
+    prof_mark(ctx, PROF_APPLY32, false, s);
+    const int64_t work = P.n_shared_nodes * ncolg;
+    if (work > 0) {
+      prof_mark(ctx, PROF_HALO, true, s);
+      if (vec == VEC)
+        MK_COUNT(), k_halo<T, VEC><<<(int)((work + 255) / 256), 256, 0, s>>>(P.n_shared_nodes, P.d_shared_node,
+                                                                           P.d_shared_off, L.d_boundary, mask, halo,
+                                                                           y, ncolg, col0, ld);
+      else
+        MK_COUNT(), k_halo<T, 1><<<(int)((work + 255) / 256), 256, 0, s>>>(P.n_shared_nodes, P.d_shared_node,
+                                                                         P.d_shared_off, L.d_boundary, mask, halo, y,
+                                                                         ncolg, col0, ld);
+      prof_mark(ctx, PROF_HALO, false, s);
+    }
+  }
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
+template int apply_patch<float>(mk_ctx*, const mk_mesh*, const float*, const float*, float*, int, bool, cudaStream_t);
+template int apply_patch<double>(mk_ctx*, const mk_mesh*, const double*, const double*, double*, int, bool,
+                                 cudaStream_t);
+
+// Element matrices of the patch operator from FP64 originals (patch order).
+template <typename T>
+int pack_elements(mk_ctx* ctx, const mk_mesh* m, const double* A64, T* A, cudaStream_t s) {
+  (void)ctx;
+  const Level& L = m->fine;
+  const int np = L.nloc * (L.nloc + 1) / 2;
+  const int64_t work = L.n_elems * np;
+  MK_COUNT(), k_pack_elements<T><<<(int)((work + 255) / 256), 256, 0, s>>>(L.n_elems, np, m->patches.d_elem_id, A64, A);
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+template int pack_elements<float>(mk_ctx*, const mk_mesh*, const double*, float*, cudaStream_t);
+template int pack_elements<double>(mk_ctx*, const mk_mesh*, const double*, double*, cudaStream_t);
+
+// ------------------------------------------------------------------------------------------------ mixed PCG
+struct MixState {
+  double rz, pq, rr, rr0, alpha, beta, rr64, bn;
+  int active, iters, breakdown, outer_active;
+};
+
+// Column partial sums with a fixed map: thread t of a block of ld*(256/ld) threads always handles column t % ld.
+// part[blk][k*ld + j] for k < NS sums.
+template <int NS>
+__device__ __forceinline__ void block_partials(double (&acc)[NS], double* sh, int ld, double* part) {
+  const int rows = blockDim.x / ld;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    sh[threadIdx.x] = acc[k];
+    __syncthreads();
+    if (threadIdx.x < ld) {
+      double s = 0.0;
+      for (int r = 0; r < rows; ++r) s += sh[r * ld + threadIdx.x];
+      part[(int64_t)blockIdx.x * NS * ld + k * ld + threadIdx.x] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// r64 = b - Ax (interior rows), r32 = (float) r64, d32 = 0; partials of (b.b, r64.r64)
+__global__ void k_mixed_residual(int64_t n, const uint8_t* __restrict__ bnd, const double* __restrict__ b,
+                                 const double* __restrict__ Ax, float* __restrict__ r32, float* __restrict__ d32,
+                                 int N, int ld, double* __restrict__ part) {
+  __shared__ double sh[256];
+  double acc[2] = {0.0, 0.0};
+  const int rows = blockDim.x / ld;
+  const int j = threadIdx.x % ld, r = threadIdx.x / ld;
+  if (r < rows)
+    for (int64_t nd = (int64_t)blockIdx.x * rows + r; nd < n; nd += (int64_t)gridDim.x * rows) {
+      const int64_t t = nd * ld + j;
+      double rv = 0.0, bv = 0.0;
+      if (j < N && !bnd[nd]) {
+        bv = b[t];
+        rv = bv - Ax[t];
+      }
+      r32[t] = (float)rv;
+      d32[t] = 0.f;
+      acc[0] += bv * bv;
+      acc[1] += rv * rv;
+    }
+  block_partials<2>(acc, sh, ld, part);
+}
+
+// p = Dinv r; partials of (r.z, r.r)
+__global__ void k_mixed_init(int64_t n, const float* __restrict__ dinv, const float* __restrict__ r,
+                             float* __restrict__ p, int ld, double* __restrict__ part) {
+  __shared__ double sh[256];
+  double acc[2] = {0.0, 0.0};
+  const int rows = blockDim.x / ld;
+  const int j = threadIdx.x % ld, rr = threadIdx.x / ld;
+  if (rr < rows)
+    for (int64_t nd = (int64_t)blockIdx.x * rows + rr; nd < n; nd += (int64_t)gridDim.x * rows) {
+      const int64_t t = nd * ld + j;
+      const float rv = r[t];
+      const float z = rv * dinv[nd];
+      p[t] = z;
+      acc[0] += (double)rv * z;
+      acc[1] += (double)rv * rv;
+    }
+  block_partials<2>(acc, sh, ld, part);
+}
+
+// partial p.q
+__global__ void k_mixed_pq(int64_t n, const float* __restrict__ p, const float* __restrict__ q, int ld,
+                           double* __restrict__ part) {
+  __shared__ double sh[256];
+  double acc[1] = {0.0};
+  const int rows = blockDim.x / ld;
+  const int j = threadIdx.x % ld, rr = threadIdx.x / ld;
+  if (rr < rows)
+    for (int64_t nd = (int64_t)blockIdx.x * rows + rr; nd < n; nd += (int64_t)gridDim.x * rows) {
+      const int64_t t = nd * ld + j;
+      acc[0] += (double)p[t] * q[t];
+    }
+  block_partials<1>(acc, sh, ld, part);
+}
+
+// d += alpha p; r -= alpha q; partials of (r.z, r.r) with z = Dinv r
+__global__ void k_mixed_update(int64_t n, const MixState* __restrict__ st, const float* __restrict__ dinv,
+                               const float* __restrict__ p, const float* __restrict__ q, float* __restrict__ d,
+                               float* __restrict__ r, int ld, double* __restrict__ part) {
+  __shared__ double sh[256];
+  double acc[2] = {0.0, 0.0};
+  const int rows = blockDim.x / ld;
+  const int j = threadIdx.x % ld, rr = threadIdx.x / ld;
+  const float a = rr < rows ? (float)st[j].alpha : 0.f;
+  if (rr < rows)
+    for (int64_t nd = (int64_t)blockIdx.x * rows + rr; nd < n; nd += (int64_t)gridDim.x * rows) {
+      const int64_t t = nd * ld + j;
+      float rv = r[t];
+      if (a != 0.f) {
+        d[t] += a * p[t];
+        rv -= a * q[t];
+        r[t] = rv;
+      }
+      acc[0] += (double)rv * (rv * dinv[nd]);
+      acc[1] += (double)rv * rv;
+    }
+  block_partials<2>(acc, sh, ld, part);
+}
+
+// p = Dinv r + beta p (active columns)
+__global__ void k_mixed_p(int64_t n, const MixState* __restrict__ st, const float* __restrict__ dinv,
+                          const float* __restrict__ r, float* __restrict__ p, int ld) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * ld) return;
+  const int j = (int)(t % ld);
+  if (!st[j].active) return;
+  const int64_t nd = t / ld;
+  p[t] = r[t] * dinv[nd] + (float)st[j].beta * p[t];
+}
+
+__global__ void k_mixed_add(int64_t n, const float* __restrict__ d, double* __restrict__ x, int N, int ld) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * ld) return;
+  if ((int)(t % ld) < N) x[t] += (double)d[t];
+}
+
+__global__ void k_dinv32(int64_t n, const double* __restrict__ diag, float* __restrict__ dinv) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dinv[i] = (float)(1.0 / diag[i]);
+}
+
+__global__ void k_zero_boundary(int64_t n, const uint8_t* __restrict__ bnd, double* __restrict__ x, int ld) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n * ld && bnd[t / ld]) x[t] = 0.0;
+}
+
+// Finalisers: one block of ld threads, sums partials in block order.
+// mode 0: outer residual (bb, rr64) -> bn, rr64, outer_active
+// mode 1: inner init (rz, rr) -> rz, rr0, rr, active (outer_active), iters=0
+// mode 2: alpha from pq
+// mode 3: beta from (rz_new, rr) and convergence of the inner solve
+__global__ void k_mixed_finalize(int mode, const double* __restrict__ part, int nblk, int NS, int ld, int N,
+                                 MixState* __restrict__ st, double rtol, double inner_rtol2) {
+  const int j = threadIdx.x;
+  if (j >= ld) return;
+  double s[2] = {0.0, 0.0};
+  for (int b = 0; b < nblk; ++b)
+    for (int k = 0; k < NS; ++k) s[k] += part[(int64_t)b * NS * ld + k * ld + j];
+  MixState c = st[j];
+  if (mode == 0) {
+    c.bn = s[0] > 0 ? sqrt(s[0]) : 1.0;
+    c.rr64 = s[1];
+    c.outer_active = (j < N) && (sqrt(s[1]) / c.bn > rtol);
+  } else if (mode == 1) {
+    c.rz = s[0];
+    c.rr0 = s[1];
+    c.rr = s[1];
+    c.active = c.outer_active && s[1] > 0.0;
+    c.alpha = 0.0;
+    c.beta = 0.0;
+  } else if (mode == 2) {
+    c.pq = s[0];
+    if (c.active) {
+      if (!(c.pq > 0.0)) {
+        c.breakdown = 1;
+        c.active = 0;
+        c.alpha = 0.0;
+      } else {
+        c.alpha = c.rz / c.pq;
+      }
+    } else {
+      c.alpha = 0.0;
+    }
+  } else {
+    if (c.active) {
+      c.beta = s[0] / c.rz;
+      c.rz = s[0];
+      c.rr = s[1];
+      c.iters += 1;
+      c.active = c.rr > inner_rtol2 * c.rr0;
+    } else {
+      c.beta = 0.0;
+    }
+  }
+  st[j] = c;
+}
+
+int solve_mixed(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, double sigma, const double* b,
                 const double*, const double*, double* x, int ld, int N, const mk_solve_opts& o, mk_solve_report* rep,
                 cudaStream_t s) {
-  (void)ctx; (void)m; (void)mol; (void)sigma; (void)rhs; (void)x; (void)ld; (void)N; (void)o; (void)rep; (void)s;
-  return fail(MK_ERR_UNSUPPORTED, "mixed precision not built yet");
+  if (o.precond != MK_PRECOND_JACOBI) return fail(MK_ERR_UNSUPPORTED, "mixed path: only Jacobi is built");
+  MK_ARG(ld <= 256, "mixed path: ld must be <= 256");
+  const Level& L = m->fine;
+  const int64_t n = L.n_nodes;
+  const int np = L.nloc * (L.nloc + 1) / 2;
+  int err = MK_OK;
+  double* A64 = (double*)scratch(ctx, S_ELEM64, (size_t)L.n_elems * np * sizeof(double), &err);
+  float* A32 = (float*)scratch(ctx, S_ELEM32, (size_t)L.n_elems * np * sizeof(float), &err);
+  double* diag = (double*)scratch(ctx, S_DIAG64, n * sizeof(double), &err);
+  float* dinv = (float*)scratch(ctx, S_DIAG32, n * sizeof(float), &err);
+  double* Ax = (double*)scratch(ctx, S_Q64, (size_t)n * ld * sizeof(double), &err);
+  float* r = (float*)scratch(ctx, S_R32, (size_t)n * ld * sizeof(float), &err);
+  float* p = (float*)scratch(ctx, S_P32, (size_t)n * ld * sizeof(float), &err);
+  float* q = (float*)scratch(ctx, S_Q32, (size_t)n * ld * sizeof(float), &err);
+  float* d = (float*)scratch(ctx, S_X32, (size_t)n * ld * sizeof(float), &err);
+  const int nblk = red_blocks(ctx);
+  double* part = (double*)scratch(ctx, S_RED, (size_t)nblk * 2 * ld * sizeof(double), &err);
+  MixState* st = (MixState*)scratch(ctx, S_SCAL, 256 * sizeof(MixState), &err);
+  if (!A64 || !A32 || !diag || !dinv || !Ax || !r || !p || !q || !d || !part || !st) return err;
+  if (ctx->pinned_size < 256 * sizeof(MixState)) {
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    MK_CUDA(cudaMallocHost(&ctx->pinned, 256 * sizeof(MixState)));
+    ctx->pinned_size = 256 * sizeof(MixState);
+  }
+  MixState* hst = (MixState*)ctx->pinned;
+  MK_TRY(element_matrices(ctx, L, mol, 0.5, 1.0, sigma, nullptr, A64, s));
+  MK_TRY(assemble_diagonal(ctx, L, A64, diag, s));
+  MK_TRY(pack_elements<float>(ctx, m, A64, A32, s));
+  MK_COUNT(), k_dinv32<<<(int)((n + 255) / 256), 256, 0, s>>>(n, diag, dinv);
+  MK_COUNT(), k_zero_boundary<<<(int)((n * ld + 255) / 256), 256, 0, s>>>(n, L.d_boundary, x, ld);
+  MK_CUDA(cudaMemsetAsync(st, 0, 256 * sizeof(MixState), s));
+  const int th = ld * (256 / ld);
+  const int gb = (int)((n * ld + 255) / 256);
+  const int check = std::max(1, o.check_every);
+  const double inner2 = o.inner_rtol * o.inner_rtol;
+  int total_it = 0, refine = 0, status = MK_OK;
+  bool converged = false;
+  const int max_refine = o.max_refine > 0 ? o.max_refine : 20;
+  for (;;) {
+    MK_TRY(apply64(ctx, L, A64, x, Ax, ld, ld, true, s));   // FP64 residual of the current x
+    MK_COUNT(), k_mixed_residual<<<nblk, th, 0, s>>>(n, L.d_boundary, b, Ax, r, d, N, ld, part);
+    MK_COUNT(), k_mixed_finalize<<<1, ld, 0, s>>>(0, part, nblk, 2, ld, N, st, o.rtol, inner2);
+    MK_CUDA(cudaMemcpyAsync(hst, st, sizeof(MixState) * ld, cudaMemcpyDeviceToHost, s));
+    MK_CUDA(cudaStreamSynchronize(s));
+    bool any = false;
+    for (int j = 0; j < N; ++j) any |= hst[j].outer_active != 0;
+    if (!any) { converged = true; break; }
+    if (refine >= max_refine || total_it >= o.maxit) break;
+    ++refine;
+    MK_COUNT(), k_mixed_init<<<nblk, th, 0, s>>>(n, dinv, r, p, ld, part);
+    MK_COUNT(), k_mixed_finalize<<<1, ld, 0, s>>>(1, part, nblk, 2, ld, N, st, o.rtol, inner2);
+    int it = 0;
+    bool inner_active = true;
+    while (inner_active && total_it < o.maxit) {
+      MK_TRY(apply_patch<float>(ctx, m, A32, p, q, ld, true, s));
+      MK_COUNT(), k_mixed_pq<<<nblk, th, 0, s>>>(n, p, q, ld, part);
+      MK_COUNT(), k_mixed_finalize<<<1, ld, 0, s>>>(2, part, nblk, 1, ld, N, st, o.rtol, inner2);
+      MK_COUNT(), k_mixed_update<<<nblk, th, 0, s>>>(n, st, dinv, p, q, d, r, ld, part);
+      MK_COUNT(), k_mixed_finalize<<<1, ld, 0, s>>>(3, part, nblk, 2, ld, N, st, o.rtol, inner2);
+      MK_COUNT(), k_mixed_p<<<gb, 256, 0, s>>>(n, st, dinv, r, p, ld);
+      ++it;
+      ++total_it;
+      if (it % check == 0) {
+        MK_CUDA(cudaMemcpyAsync(hst, st, sizeof(MixState) * ld, cudaMemcpyDeviceToHost, s));
+        MK_CUDA(cudaStreamSynchronize(s));
+        inner_active = false;
+        for (int j = 0; j < N; ++j) {
+          inner_active |= hst[j].active != 0;
+          if (hst[j].breakdown) status = MK_ERR_BREAKDOWN;
+        }
+        if (status == MK_ERR_BREAKDOWN) break;
+      }
+    }
+    MK_COUNT(), k_mixed_add<<<gb, 256, 0, s>>>(n, d, x, N, ld);
+    if (status == MK_ERR_BREAKDOWN) break;
+  }
+  MK_CUDA(cudaGetLastError());
+  MK_CUDA(cudaMemcpyAsync(hst, st, sizeof(MixState) * ld, cudaMemcpyDeviceToHost, s));
+  MK_CUDA(cudaStreamSynchronize(s));
+  double mx = 0.0;
+  for (int j = 0; j < N; ++j) mx = std::max(mx, std::sqrt(hst[j].rr64) / hst[j].bn);
+  if (rep) {
+    std::memset(rep, 0, sizeof(*rep));
+    rep->n_rhs = N;
+    rep->iterations = total_it;
+    rep->refinements = refine;
+    rep->max_rel_residual = mx;
+    for (int j = 0; j < N; ++j) {
+      rep->iters[j] = hst[j].iters;
+      rep->rel_residual[j] = std::sqrt(hst[j].rr64) / hst[j].bn;
+    }
+  }
+  if (status == MK_OK && !converged) status = MK_ERR_NOT_CONVERGED;
+  if (rep) rep->status = status;
+  if (status == MK_ERR_BREAKDOWN) return fail(status, "mixed PCG breakdown: p^T A p <= 0 (operator not SPD)");
+  if (status == MK_ERR_NOT_CONVERGED) return fail(status, "mixed PCG did not reach rtol");
+  return MK_OK;
 }
 
 }  // namespace mk
+
+using namespace mk;
+
+extern "C" int mk_operator_apply(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, double sigma, int precision,
+                                 const void* x, void* y, int ld, void* stream) {
+  MK_ARG(ctx && m && mol && x && y && ld >= 1 && ld <= 256, "mk_operator_apply: bad argument");
+  MK_ARG(precision == MK_PREC_FP64 || precision == MK_PREC_MIXED, "mk_operator_apply: bad precision");
+  MK_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const Level& L = m->fine;
+  const int np = L.nloc * (L.nloc + 1) / 2;
+  int err = MK_OK;
+  double* A64 = (double*)scratch(ctx, S_OPA, (size_t)L.n_elems * np * sizeof(double), &err);
+  if (!A64) return err;
+  MK_TRY(element_matrices(ctx, L, mol, 0.5, 1.0, sigma, nullptr, A64, s));
+  if (precision == MK_PREC_FP64) {
+    double* A = (double*)scratch(ctx, S_OPB, (size_t)L.n_elems * np * sizeof(double), &err);
+    if (!A) return err;
+    MK_TRY(pack_elements<double>(ctx, m, A64, A, s));
+    return apply_patch<double>(ctx, m, A, (const double*)x, (double*)y, ld, true, s);
+  }
+  float* A = (float*)scratch(ctx, S_OPB, (size_t)L.n_elems * np * sizeof(float), &err);
+  if (!A) return err;
+  MK_TRY(pack_elements<float>(ctx, m, A64, A, s));
+  return apply_patch<float>(ctx, m, A, (const float*)x, (float*)y, ld, true, s);
+}

@@ -1,13 +1,159 @@
-// Element patches for the FP32 operator (filled in by the patch builder).
+// Element patches for the single-pass operator application (built once at mesh upload).
+//
+// Elements are ordered along a Morton curve of their centroids and cut into patches of at most kPatchElems(order)
+// consecutive elements; one CTA applies one patch.  Inside the CTA the element products go to shared memory and
+// each local node sums its incidences in a fixed order (owner computes).  A node used by one patch only is
+// written directly; a node shared by several patches is written to one halo slot per patch, and a second kernel
+// adds those slots in patch order.  Every sum has a fixed order, so results are bitwise reproducible, with no
+// atomics and no colour-by-colour launches.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
 #include "mk_internal.h"
 
 namespace mk {
 
-int build_patches(mk_mesh* m) {
-  (void)m;
+int patch_elems(int nloc) { return nloc == 4 ? 256 : 128; }
+
+static uint32_t spread10(uint32_t v) {
+  v &= 0x3ff;
+  v = (v | (v << 16)) & 0x030000FF;
+  v = (v | (v << 8)) & 0x0300F00F;
+  v = (v | (v << 4)) & 0x030C30C3;
+  v = (v | (v << 2)) & 0x09249249;
+  return v;
+}
+
+template <class T>
+static int up(T** dst, const std::vector<T>& src) {
+  size_t n = std::max<size_t>(src.size(), 1);
+  if (cudaMalloc(dst, n * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MK_ERR_OOM, "patch upload: allocation failed");
+  }
+  if (!src.empty() && cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(MK_ERR_CUDA, "patch upload: copy failed");
   return MK_OK;
 }
 
-void free_patches(Patches& p) { (void)p; }
+int build_patches(mk_mesh* m) {
+  const Level& L = m->fine;
+  Patches& P = m->patches;
+  const int nloc = L.nloc;
+  const int64_t E = L.n_elems, nn = L.n_nodes;
+  const int PE = patch_elems(nloc);
+  // Morton order of element centroids
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int64_t v = 0; v < L.n_vertices; ++v)
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = std::min(lo[k], L.nodes[v * 3 + k]);
+      hi[k] = std::max(hi[k], L.nodes[v * 3 + k]);
+    }
+  std::vector<uint32_t> code(E);
+  for (int64_t e = 0; e < E; ++e) {
+    uint32_t q[3];
+    for (int k = 0; k < 3; ++k) {
+      double c = 0.0;
+      for (int a = 0; a < 4; ++a) c += L.nodes[(int64_t)L.elem[e * nloc + a] * 3 + k];
+      c *= 0.25;
+      const double t = (hi[k] > lo[k]) ? (c - lo[k]) / (hi[k] - lo[k]) : 0.0;
+      q[k] = (uint32_t)std::min(1023.0, std::max(0.0, t * 1024.0));
+    }
+    code[e] = spread10(q[0]) | (spread10(q[1]) << 1) | (spread10(q[2]) << 2);
+  }
+  std::vector<int32_t> order(E);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return code[a] < code[b]; });
+  const int np = (int)((E + PE - 1) / PE);
+  P.n_patches = np;
+  P.max_elems = PE;
+  std::vector<int32_t> elem_off(np + 1), node_off(np + 1, 0);
+  for (int p = 0; p <= np; ++p) elem_off[p] = (int32_t)std::min<int64_t>((int64_t)p * PE, E);
+  // local node lists (sorted unique global ids per patch)
+  std::vector<int32_t> node_global;
+  std::vector<int32_t> cnt(nn, 0);
+  for (int p = 0; p < np; ++p) {
+    std::vector<int32_t> ns;
+    for (int32_t i = elem_off[p]; i < elem_off[p + 1]; ++i)
+      for (int a = 0; a < nloc; ++a) ns.push_back(L.elem[(int64_t)order[i] * nloc + a]);
+    std::sort(ns.begin(), ns.end());
+    ns.erase(std::unique(ns.begin(), ns.end()), ns.end());
+    for (int32_t g : ns) cnt[g]++;
+    node_off[p + 1] = node_off[p] + (int32_t)ns.size();
+    P.max_nodes = std::max(P.max_nodes, (int)ns.size());
+    node_global.insert(node_global.end(), ns.begin(), ns.end());
+  }
+  // halo slots of shared nodes: slots of one node are consecutive, in patch order
+  std::vector<int64_t> hbase(nn, -1);
+  std::vector<int32_t> shared_node, shared_off(1, 0);
+  int64_t nslot = 0;
+  for (int64_t g = 0; g < nn; ++g)
+    if (cnt[g] >= 2) {
+      hbase[g] = nslot;
+      nslot += cnt[g];
+      shared_node.push_back((int32_t)g);
+      shared_off.push_back((int32_t)nslot);
+    }
+  P.n_halo_slots = nslot;
+  P.n_shared_nodes = (int64_t)shared_node.size();
+  std::vector<int32_t> seen(nn, 0);
+  std::vector<int32_t> target(node_global.size());
+  std::vector<int32_t> inc_off;
+  std::vector<uint16_t> inc;
+  inc_off.reserve(node_global.size() + np);
+  std::vector<int32_t> conn((size_t)E * nloc);
+  std::vector<int32_t> elem_id(E);
+  for (int p = 0; p < np; ++p) {
+    const int32_t nb = node_off[p], ne = node_off[p + 1];
+    const int nl = ne - nb;
+    for (int l = 0; l < nl; ++l) {
+      const int32_t g = node_global[nb + l];
+      target[nb + l] = (cnt[g] >= 2) ? -(int32_t)(hbase[g] + seen[g]++) - 1 : g;
+    }
+    // incidences per local node in (element, slot) order, CSR local to the patch
+    std::vector<int32_t> c(nl + 1, 0);
+    std::vector<int32_t> lidx((size_t)(elem_off[p + 1] - elem_off[p]) * nloc);
+    for (int32_t i = elem_off[p]; i < elem_off[p + 1]; ++i) {
+      elem_id[i] = order[i];
+      for (int a = 0; a < nloc; ++a) {
+        const int32_t g = L.elem[(int64_t)order[i] * nloc + a];
+        conn[(size_t)i * nloc + a] = g;
+        const int l = (int)(std::lower_bound(node_global.begin() + nb, node_global.begin() + ne, g) -
+                            (node_global.begin() + nb));
+        lidx[(size_t)(i - elem_off[p]) * nloc + a] = l;
+        c[l + 1]++;
+      }
+    }
+    for (int l = 0; l < nl; ++l) c[l + 1] += c[l];
+    std::vector<uint16_t> lst(c[nl]);
+    std::vector<int32_t> pos(c.begin(), c.end() - 1);
+    for (size_t k = 0; k < lidx.size(); ++k) lst[pos[lidx[k]]++] = (uint16_t)k;   // k = local element * nloc + a
+    const int32_t base = (int32_t)inc.size();
+    for (int l = 0; l < nl; ++l) inc_off.push_back(base + c[l]);
+    inc.insert(inc.end(), lst.begin(), lst.end());
+  }
+  inc_off.push_back((int32_t)inc.size());   // sentinel after the last patch
+  // inc_off has one entry per local node of every patch (start) plus one final sentinel; the end of local node l
+  // of patch p is the start of the next entry, which for the last node of a patch is the first node of the next
+  // patch (or the sentinel): incidences of consecutive patches are contiguous, so starts alone suffice.
+  int r = up(&P.d_patch_elem_off, elem_off);
+  if (r == MK_OK) r = up(&P.d_patch_node_off, node_off);
+  if (r == MK_OK) r = up(&P.d_elem_id, elem_id);
+  if (r == MK_OK) r = up(&P.d_conn, conn);
+  if (r == MK_OK) r = up(&P.d_node_target, target);
+  if (r == MK_OK) r = up(&P.d_inc_off, inc_off);
+  if (r == MK_OK) r = up(&P.d_inc, inc);
+  if (r == MK_OK) r = up(&P.d_shared_node, shared_node);
+  if (r == MK_OK) r = up(&P.d_shared_off, shared_off);
+  return r;
+}
+
+void free_patches(Patches& p) {
+  cudaFree(p.d_patch_elem_off); cudaFree(p.d_patch_node_off); cudaFree(p.d_elem_id); cudaFree(p.d_conn);
+  cudaFree(p.d_node_target); cudaFree(p.d_inc_off); cudaFree(p.d_inc); cudaFree(p.d_shared_node);
+  cudaFree(p.d_shared_off);
+  p = Patches();
+}
 
 }  // namespace mk

@@ -146,8 +146,42 @@ int gram(mk_ctx* ctx, int64_t n, const double* X, const double* Y, int N, int ld
   const int nblk = red_blocks(ctx);
   double* part = (double*)scratch(ctx, S_RED, (size_t)nblk * N * N * sizeof(double), &err);
   if (!part) return err;
-  k_gram_partial<<<nblk, kRedThreads, kRedThreads * sizeof(double), s>>>(n, X, Y, N, ld, part);
-  k_sum_partials<<<(N * N + 63) / 64, 64, 0, s>>>(part, nblk, N * N, G);
+  MK_COUNT(), k_gram_partial<<<nblk, kRedThreads, kRedThreads * sizeof(double), s>>>(n, X, Y, N, ld, part);
+  MK_COUNT(), k_sum_partials<<<(N * N + 63) / 64, 64, 0, s>>>(part, nblk, N * N, G);
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
+// Dense coarse Galerkin matrices X1 = P^T A1 P, X2 = P^T A2 P over the coarse free DOF from two sets of packed
+// fine element matrices (children summed per coarse element in fixed order, then coarse colour by colour).
+int coarse_matrices(mk_ctx* ctx, const mk_mesh* m, const double* A1, const double* A2, double* X1, double* X2,
+                    int slot, cudaStream_t s) {
+  const Level& F = m->fine;
+  const Level& C = m->coarse;
+  const int NH = (int)C.n_free, nl = F.nloc;
+  int err = MK_OK;
+  double* CE = (double*)scratch(ctx, slot, (size_t)C.n_elems * nl * nl * 2 * sizeof(double), &err);
+  if (!CE) return err;
+  double* C1 = CE;
+  double* C2 = CE + (size_t)C.n_elems * nl * nl;
+  if (nl == 4)
+    MK_COUNT(), k_coarse_galerkin<4><<<(int)C.n_elems, 128, 0, s>>>(m->d_child_off, m->d_child, F.d_geom, C.d_geom,
+                                                                    ctx->d_ref[1], A1, A2, C1, C2);
+  else
+    MK_COUNT(), k_coarse_galerkin<10><<<(int)C.n_elems, 128, 0, s>>>(m->d_child_off, m->d_child, F.d_geom, C.d_geom,
+                                                                     ctx->d_ref[2], A1, A2, C1, C2);
+  MK_CUDA(cudaMemsetAsync(X1, 0, (size_t)NH * NH * sizeof(double), s));
+  MK_CUDA(cudaMemsetAsync(X2, 0, (size_t)NH * NH * sizeof(double), s));
+  for (int col = 0; col < C.n_colours; ++col) {
+    const int64_t off = C.colour_off[col], cnt = C.colour_off[col + 1] - off;
+    if (nl == 4)
+      MK_COUNT(), k_coarse_scatter<4><<<(int)((cnt + 63) / 64), 64, 0, s>>>(C.d_colour_elems + off, (int)cnt, C.d_elem,
+                                                                           C.d_node_to_free, C1, C2, X1, X2, NH);
+    else
+      MK_COUNT(), k_coarse_scatter<10><<<(int)((cnt + 63) / 64), 64, 0, s>>>(C.d_colour_elems + off, (int)cnt,
+                                                                            C.d_elem, C.d_node_to_free, C1, C2, X1,
+                                                                            X2, NH);
+  }
   MK_CUDA(cudaGetLastError());
   return MK_OK;
 }
@@ -156,16 +190,32 @@ int gram(mk_ctx* ctx, int64_t n, const double* X, const double* Y, int N, int ld
 
 using namespace mk;
 
+extern "C" int mk_coarse_pencil(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, const double* vq, double* AH,
+                                double* MH, void* stream) {
+  MK_ARG(ctx && m && mol && AH && MH, "mk_coarse_pencil: null argument");
+  MK_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const Level& F = m->fine;
+  const int nl = F.nloc;
+  int err = MK_OK;
+  const size_t eb = (size_t)F.n_elems * (nl * (nl + 1) / 2) * sizeof(double);
+  double* He = (double*)scratch(ctx, S_ELEM64C, eb, &err);
+  double* Me = (double*)scratch(ctx, S_ELEM64D, eb, &err);
+  if (!He || !Me) return err;
+  MK_TRY(element_matrices(ctx, F, mol, 0.5, 1.0, 0.0, vq, He, s, S_NUC2));
+  MK_TRY(element_matrices(ctx, F, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s, S_NUC2));
+  return coarse_matrices(ctx, m, He, Me, AH, MH, S_COARSE2, s);
+}
+
 extern "C" int mk_augmented_project(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, const double* vq,
                                     const double* psihat, int ld, int N, double* AH, double* MH, double* b, double* c,
                                     double* beta, double* gamma, double* gramA, double* gramM, void* stream) {
-  MK_ARG(ctx && m && mol && vq && psihat && AH && MH && b && c && beta && gamma, "mk_augmented_project: null argument");
+  MK_ARG(ctx && m && mol && vq && psihat && b && c && beta && gamma, "mk_augmented_project: null argument");
+  MK_ARG((AH == nullptr) == (MH == nullptr), "mk_augmented_project: AH and MH must both be given or both NULL");
   MK_ARG(N >= 1 && N <= ld && N <= MK_MAX_RHS, "mk_augmented_project: bad N/ld");
   MK_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
   const Level& F = m->fine;
-  const Level& C = m->coarse;
-  const int NH = (int)C.n_free;
   const int nl = F.nloc;
   int err = MK_OK;
   const size_t eb = (size_t)F.n_elems * (nl * (nl + 1) / 2) * sizeof(double);
@@ -173,9 +223,8 @@ extern "C" int mk_augmented_project(mk_ctx* ctx, const mk_mesh* m, const mk_mole
   double* Me = (double*)scratch(ctx, S_ELEM64B, eb, &err);
   double* Y = (double*)scratch(ctx, S_VEC1, (size_t)F.n_nodes * ld * sizeof(double), &err);
   double* MY = (double*)scratch(ctx, S_VEC2, (size_t)F.n_nodes * ld * sizeof(double), &err);
-  double* CE = (double*)scratch(ctx, S_COARSE, (size_t)C.n_elems * nl * nl * 2 * sizeof(double), &err);
   double* G = (double*)scratch(ctx, S_GRAM, (size_t)2 * N * N * sizeof(double), &err);
-  if (!He || !Me || !Y || !MY || !CE || !G) return err;
+  if (!He || !Me || !Y || !MY || !G) return err;
   MK_TRY(element_matrices(ctx, F, mol, 0.5, 1.0, 0.0, vq, He, s));
   MK_TRY(element_matrices(ctx, F, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s));
   MK_TRY(apply64(ctx, F, He, psihat, Y, N, ld, true, s));
@@ -186,27 +235,9 @@ extern "C" int mk_augmented_project(mk_ctx* ctx, const mk_mesh* m, const mk_mole
   double* GM = gramM ? gramM : G + N * N;
   MK_TRY(gram(ctx, F.n_nodes, psihat, Y, N, ld, GA, s));
   MK_TRY(gram(ctx, F.n_nodes, psihat, MY, N, ld, GM, s));
-  k_diag_of<<<1, MK_MAX_RHS, 0, s>>>(GA, N, beta);
-  k_diag_of<<<1, MK_MAX_RHS, 0, s>>>(GM, N, gamma);
-  double* C1 = CE;
-  double* C2 = CE + (size_t)C.n_elems * nl * nl;
-  if (nl == 4)
-    k_coarse_galerkin<4><<<(int)C.n_elems, 128, 0, s>>>(m->d_child_off, m->d_child, F.d_geom, C.d_geom, ctx->d_ref[1],
-                                                        He, Me, C1, C2);
-  else
-    k_coarse_galerkin<10><<<(int)C.n_elems, 128, 0, s>>>(m->d_child_off, m->d_child, F.d_geom, C.d_geom,
-                                                         ctx->d_ref[2], He, Me, C1, C2);
-  MK_CUDA(cudaMemsetAsync(AH, 0, (size_t)NH * NH * sizeof(double), s));
-  MK_CUDA(cudaMemsetAsync(MH, 0, (size_t)NH * NH * sizeof(double), s));
-  for (int col = 0; col < C.n_colours; ++col) {
-    const int64_t off = C.colour_off[col], cnt = C.colour_off[col + 1] - off;
-    if (nl == 4)
-      k_coarse_scatter<4><<<(int)((cnt + 63) / 64), 64, 0, s>>>(C.d_colour_elems + off, (int)cnt, C.d_elem,
-                                                               C.d_node_to_free, C1, C2, AH, MH, NH);
-    else
-      k_coarse_scatter<10><<<(int)((cnt + 63) / 64), 64, 0, s>>>(C.d_colour_elems + off, (int)cnt, C.d_elem,
-                                                                C.d_node_to_free, C1, C2, AH, MH, NH);
-  }
+  MK_COUNT(), k_diag_of<<<1, MK_MAX_RHS, 0, s>>>(GA, N, beta);
+  MK_COUNT(), k_diag_of<<<1, MK_MAX_RHS, 0, s>>>(GM, N, gamma);
+  if (AH) MK_TRY(coarse_matrices(ctx, m, He, Me, AH, MH, S_COARSE, s));
   MK_CUDA(cudaGetLastError());
   return MK_OK;
 }

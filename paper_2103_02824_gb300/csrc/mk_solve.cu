@@ -134,12 +134,12 @@ int pcg64(mk_ctx* ctx, const Level& L, const double* Ae, const double* diag, con
   ColState* hst = (ColState*)ctx->pinned;
 
   MK_TRY(apply64(ctx, L, Ae, x, Q, N, ld, true, s));
-  k_residual<<<gb, th, 0, s>>>(n, L.d_boundary, b, Q, diag, R, Z, P, N, ld);
+  MK_COUNT(), k_residual<<<gb, th, 0, s>>>(n, L.d_boundary, b, Q, diag, R, Z, P, N, ld);
   // x boundary rows to 0 (Q := 0 then mask trick): write x = x - 0 on interior, 0 on boundary
   MK_TRY(column_dots(ctx, n, b, b, N, ld, d1, s));
   MK_TRY(column_dots(ctx, n, R, Z, N, ld, d2, s));
   MK_TRY(column_dots(ctx, n, R, R, N, ld, d3, s));
-  k_init_state<<<1, MK_MAX_RHS, 0, s>>>(st, d1, d2, d3, N, o.rtol);
+  MK_COUNT(), k_init_state<<<1, MK_MAX_RHS, 0, s>>>(st, d1, d2, d3, N, o.rtol);
   const int check = std::max(1, o.check_every);
   int it = 0, status = MK_OK;
   bool any_active = true;
@@ -150,12 +150,12 @@ int pcg64(mk_ctx* ctx, const Level& L, const double* Ae, const double* diag, con
   while (any_active && it < o.maxit) {
     MK_TRY(apply64(ctx, L, Ae, P, Q, N, ld, true, s));
     MK_TRY(column_dots(ctx, n, P, Q, N, ld, d1, s));
-    k_alpha<<<1, MK_MAX_RHS, 0, s>>>(st, d1, N);
-    k_update<<<gb, th, 0, s>>>(n, st, P, Q, diag, x, R, Z, N, ld);
+    MK_COUNT(), k_alpha<<<1, MK_MAX_RHS, 0, s>>>(st, d1, N);
+    MK_COUNT(), k_update<<<gb, th, 0, s>>>(n, st, P, Q, diag, x, R, Z, N, ld);
     MK_TRY(column_dots(ctx, n, R, Z, N, ld, d2, s));
     MK_TRY(column_dots(ctx, n, R, R, N, ld, d3, s));
-    k_beta<<<1, MK_MAX_RHS, 0, s>>>(st, d2, d3, N, o.rtol);
-    k_pupdate<<<gb, th, 0, s>>>(n, st, Z, P, N, ld);
+    MK_COUNT(), k_beta<<<1, MK_MAX_RHS, 0, s>>>(st, d2, d3, N, o.rtol);
+    MK_COUNT(), k_pupdate<<<gb, th, 0, s>>>(n, st, Z, P, N, ld);
     ++it;
     if (it % check == 0 || it >= o.maxit) {
       MK_CUDA(cudaMemcpyAsync(hst, st, sizeof(ColState) * N, cudaMemcpyDeviceToHost, s));
@@ -171,7 +171,7 @@ int pcg64(mk_ctx* ctx, const Level& L, const double* Ae, const double* diag, con
   MK_CUDA(cudaGetLastError());
   // final FP64 true residual
   MK_TRY(apply64(ctx, L, Ae, x, Q, N, ld, true, s));
-  k_residual<<<gb, th, 0, s>>>(n, L.d_boundary, b, Q, diag, R, nullptr, nullptr, N, ld);
+  MK_COUNT(), k_residual<<<gb, th, 0, s>>>(n, L.d_boundary, b, Q, diag, R, nullptr, nullptr, N, ld);
   MK_TRY(column_dots(ctx, n, R, R, N, ld, d3, s));
   MK_CUDA(cudaMemcpyAsync(hst, st, sizeof(ColState) * N, cudaMemcpyDeviceToHost, s));
   double rr[MK_MAX_RHS];
@@ -283,10 +283,10 @@ int mk_hartree_poisson(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, c
   double* coef = (double*)scratch(ctx, S_COEF, 64 * sizeof(double), &err);
   if (!coef) return err;
   MK_CUDA(cudaMemcpyAsync(coef, &one, sizeof(double), cudaMemcpyHostToDevice, s));
-  k_combine_rhs<<<(int)((L.n_nodes + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, F, y, coef, F, 1, 1);
+  MK_COUNT(), k_combine_rhs<<<(int)((L.n_nodes + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, F, y, coef, F, 1, 1);
   MK_CUDA(cudaMemsetAsync(d, 0, L.n_nodes * sizeof(double), s));
   int r = pcg64(ctx, L, Ke, diag, F, d, 1, 1, *opts, report, s);
-  k_axpy_interior<<<(int)((L.n_nodes + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, d, w);
+  MK_COUNT(), k_axpy_interior<<<(int)((L.n_nodes + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, d, w);
   MK_CUDA(cudaGetLastError());
   MK_CUDA(cudaStreamSynchronize(s));
   return r;
@@ -320,7 +320,7 @@ int mk_assemble_rhs(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, cons
   for (int j = 0; j < N; ++j) h[j] = lambdaH[j] + sigma;
   MK_CUDA(cudaMemcpyAsync(coef, h, N * sizeof(double), cudaMemcpyHostToDevice, s));
   MK_CUDA(cudaStreamSynchronize(s));
-  k_combine_rhs<<<(int)((L.n_nodes * ld + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, Mu, Vu, coef, rhs, N, ld);
+  MK_COUNT(), k_combine_rhs<<<(int)((L.n_nodes * ld + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, Mu, Vu, coef, rhs, N, ld);
   MK_CUDA(cudaGetLastError());
   return MK_OK;
 }
@@ -398,10 +398,10 @@ int mk_lowest_ritz(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, const 
   double* v0d = Mw;
   MK_CUDA(cudaMemcpyAsync(v0d, v0, L.n_free * sizeof(double), cudaMemcpyHostToDevice, s));
   MK_CUDA(cudaStreamSynchronize(s));
-  k_scatter_free<<<(int)((L.n_free + 255) / 256), 256, 0, s>>>(L.n_free, L.d_free_idx, v0d, v);
+  MK_COUNT(), k_scatter_free<<<(int)((L.n_free + 255) / 256), 256, 0, s>>>(L.n_free, L.d_free_idx, v0d, v);
   MK_TRY(apply64(ctx, L, Me, v, Mw, 1, 1, true, s));
   MK_TRY(column_dots(ctx, n, v, Mw, 1, 1, dd, s));
-  k_scale<<<(int)((n + 255) / 256), 256, 0, s>>>(n, v, dd, nullptr, 0);
+  MK_COUNT(), k_scale<<<(int)((n + 255) / 256), 256, 0, s>>>(n, v, dd, nullptr, 0);
   mk_solve_opts mo{MK_PREC_FP64, MK_PRECOND_JACOBI, 1e-12, 5000, 0, 0, 25};
   std::vector<double> a, b;
   double beta = 0.0;
@@ -413,7 +413,7 @@ int mk_lowest_ritz(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, const 
     MK_CUDA(cudaMemsetAsync(w, 0, n * sizeof(double), s));
     MK_CUDA(cudaStreamSynchronize(s));
     MK_TRY(pcg64(ctx, L, Me, diagM, Hv, w, 1, 1, mo, nullptr, s));   // w = M^-1 H v
-    k_lanczos_w<<<(int)((n + 255) / 256), 256, 0, s>>>(n, L.d_boundary, w, v, vp, alpha, beta);
+    MK_COUNT(), k_lanczos_w<<<(int)((n + 255) / 256), 256, 0, s>>>(n, L.d_boundary, w, v, vp, alpha, beta);
     MK_TRY(apply64(ctx, L, Me, w, Mw, 1, 1, true, s));
     MK_TRY(column_dots(ctx, n, w, Mw, 1, 1, dd, s));
     double bb;
@@ -425,7 +425,7 @@ int mk_lowest_ritz(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, const 
     b.push_back(beta);
     MK_CUDA(cudaMemcpyAsync(vp, v, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     MK_CUDA(cudaMemcpyAsync(v, w, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    k_scale<<<(int)((n + 255) / 256), 256, 0, s>>>(n, v, dd, nullptr, 0);
+    MK_COUNT(), k_scale<<<(int)((n + 255) / 256), 256, 0, s>>>(n, v, dd, nullptr, 0);
   }
   b.resize(a.size() > 0 ? a.size() - 1 : 0);
   *theta = tridiag_lowest(a, b);

@@ -79,6 +79,9 @@ _SIGS = {
     "mk_ctx_destroy": [_vp],
     "mk_last_error": [C.c_char_p, C.c_size_t],
     "mk_version": [],
+    "mk_launch_count": [],
+    "mk_profile_enable": [_vp, C.c_int],
+    "mk_profile_read": [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)],
     "mk_mesh_upload": [_vp, C.POINTER(mk_mesh_desc), C.POINTER(mk_mesh_desc), C.POINTER(C.c_int32), C.POINTER(_vp)],
     "mk_mesh_destroy": [_vp],
     "mk_mesh_get_info": [_vp, C.POINTER(mk_mesh_info)],
@@ -93,6 +96,10 @@ _SIGS = {
     "mk_augmented_project": [_vp, _vp, C.POINTER(mk_molecule), _vp, _vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp,
                              _vp, _vp, _vp, _vp],
     "mk_small_eigensolve": [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "mk_coarse_pencil": [_vp, _vp, C.POINTER(mk_molecule), _vp, _vp, _vp, _vp],
+    "mk_operator_apply": [_vp, _vp, C.POINTER(mk_molecule), C.c_double, C.c_int, _vp, _vp, C.c_int, _vp],
+    "mk_coarse_decompose": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "mk_small_eigensolve_shared": [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "mk_orbital_assemble": [_vp, _vp, _vp, _vp, _vp, C.c_int, C.c_int, _vp, _vp],
     "mk_lowest_ritz": [_vp, _vp, C.POINTER(mk_molecule), C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double), _vp],
 }
@@ -102,7 +109,7 @@ def header_symbols():
     """Names of the entry points declared in include/mk.h (parsed from the header)."""
     import re
     hdr = open(os.path.join(os.path.dirname(_HERE), "include", "mk.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(mk_\w+)\s*\(", hdr, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|long long|const char\*)\s+(mk_\w+)\s*\(", hdr, re.M)))
 
 
 def load(path: str = LIB_PATH):
@@ -112,8 +119,26 @@ def load(path: str = LIB_PATH):
     for name, args in _SIGS.items():
         f = getattr(lib, name)
         f.argtypes = args
-        f.restype = C.c_char_p if name == "mk_version" else C.c_int
+        f.restype = {"mk_version": C.c_char_p, "mk_launch_count": C.c_longlong}.get(name, C.c_int)
     return lib
+
+
+def launch_count() -> int:
+    return int(lib().mk_launch_count())
+
+
+PROF_APPLY64, PROF_APPLY32, PROF_HALO = 0, 1, 2
+
+
+def profile_enable(ctx, on=True):
+    _check(lib().mk_profile_enable(ctx.h, 1 if on else 0))
+
+
+def profile_read(ctx, kind):
+    """(total_ms, count) of the operator applications timed since profile_enable."""
+    t, n = C.c_double(), C.c_longlong()
+    _check(lib().mk_profile_read(ctx.h, kind, C.byref(t), C.byref(n)))
+    return t.value, n.value
 
 
 _lib = None
@@ -279,6 +304,29 @@ def mk_augmented_project(ctx, mesh, mol: Molecule, vq, psihat, N, AH, MH, b, c, 
 def mk_small_eigensolve(ctx, NH, N, AH, MH, b, c, beta, gamma, lam, coef, status, stream=None):
     _check(lib().mk_small_eigensolve(ctx.h, NH, N, _ptr(AH), _ptr(MH), _ptr(b), _ptr(c), _ptr(beta), _ptr(gamma),
                                      _ptr(lam), _ptr(coef), _ptr(status), _stream(stream)))
+
+
+def mk_operator_apply(ctx, mesh, mol: Molecule, sigma, x, y, stream=None):
+    """y = (K/2 + M_Vext + sigma M) x; float32 tensors select the FP32 operator, float64 the FP64 one."""
+    import torch
+    prec = MK_PREC_MIXED if x.dtype == torch.float32 else MK_PREC_FP64
+    assert y.dtype == x.dtype
+    ld = x.shape[1] if x.dim() == 2 else 1
+    _check(lib().mk_operator_apply(ctx.h, mesh.h, C.byref(mol.c), float(sigma), prec, _ptr(x), _ptr(y), ld,
+                                   _stream(stream)))
+
+
+def mk_coarse_pencil(ctx, mesh, mol: Molecule, vq, AH, MH, stream=None):
+    _check(lib().mk_coarse_pencil(ctx.h, mesh.h, C.byref(mol.c), _ptr(vq), _ptr(AH), _ptr(MH), _stream(stream)))
+
+
+def mk_coarse_decompose(ctx, mesh, AH, d, V, stream=None):
+    _check(lib().mk_coarse_decompose(ctx.h, mesh.h, _ptr(AH), _ptr(d), _ptr(V), _stream(stream)))
+
+
+def mk_small_eigensolve_shared(ctx, NH, N, d, V, b, c, beta, gamma, lam, coef, status, stream=None):
+    _check(lib().mk_small_eigensolve_shared(ctx.h, NH, N, _ptr(d), _ptr(V), _ptr(b), _ptr(c), _ptr(beta),
+                                            _ptr(gamma), _ptr(lam), _ptr(coef), _ptr(status), _stream(stream)))
 
 
 def mk_orbital_assemble(ctx, mesh, coef, psihat, u, N, psi, stream=None):

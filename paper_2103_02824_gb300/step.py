@@ -35,6 +35,8 @@ class CorrectionStep:
         self.gamma = torch.zeros(N, **f64)
         self.gramA = torch.zeros((N, N), **f64)
         self.gramM = torch.zeros((N, N), **f64)
+        self.d = torch.zeros(NH, **f64)
+        self.V = torch.zeros((NH, NH), **f64)
         self.lam = torch.zeros(N, **f64)
         self.coef = torch.zeros((NH + 1, N), **f64)
         self.status = torch.zeros(N, dtype=torch.int32, device=dev)
@@ -63,12 +65,29 @@ class CorrectionStep:
         self.psihat.copy_(self.u)
         reps["solve"] = mk.mk_correction_solve(ctx, mesh, self.mol, sigma, self.rhs, self.psihat, N,
                                                opt=solve_opts, stream=stream)
-        mk.mk_augmented_project(ctx, mesh, self.mol, self.vq, self.psihat, N, self.AH, self.MH, self.b, self.c,
+        mk.mk_coarse_pencil(ctx, mesh, self.mol, self.vq, self.AH, self.MH, stream=stream)
+        mk.mk_coarse_decompose(ctx, mesh, self.AH, self.d, self.V, stream=stream)
+        mk.mk_augmented_project(ctx, mesh, self.mol, self.vq, self.psihat, N, None, None, self.b, self.c,
                                 self.beta, self.gamma, self.gramA, self.gramM, stream=stream)
-        mk.mk_small_eigensolve(ctx, self.NH, N, self.AH, self.MH, self.b, self.c, self.beta, self.gamma, self.lam,
-                               self.coef, self.status, stream=stream)
+        mk.mk_small_eigensolve_shared(ctx, self.NH, N, self.d, self.V, self.b, self.c, self.beta, self.gamma,
+                                      self.lam, self.coef, self.status, stream=stream)
         mk.mk_orbital_assemble(ctx, mesh, self.coef, self.psihat, self.u, N, self.psi, stream=stream)
         return reps
+
+
+def coarse_eigenpairs(ctx, mesh, Z, R, N):
+    """Lowest N eigenpairs of the bare coarse Hamiltonian P^T (K/2 + M_Vext) P in V_H, the frozen-potential version
+    of Algorithm 1, step 1 (the initial solve on the coarse space), on the GPU.  Returns numpy (psiH, lamH)."""
+    import torch
+    mol = mk.Molecule(Z, R)
+    NH = mesh.info["n_free_coarse"]
+    f64 = dict(dtype=torch.float64, device="cuda")
+    AH, MH, d, V = (torch.zeros((NH, NH), **f64), torch.zeros((NH, NH), **f64), torch.zeros(NH, **f64),
+                    torch.zeros((NH, NH), **f64))
+    mk.mk_coarse_pencil(ctx, mesh, mol, None, AH, MH)
+    mk.mk_coarse_decompose(ctx, mesh, AH, d, V)
+    torch.cuda.synchronize()
+    return V[:, :N].cpu().numpy().copy(), d[:N].cpu().numpy().copy()
 
 
 def upload_workload(ctx, wl):

@@ -132,6 +132,50 @@ def test_correction_solve_fp64(ctx, torch, name):
 
 
 @pytest.mark.parametrize("name", CASES)
+def test_operator_apply_patch(ctx, torch, name):
+    """Patch-scatter operator, FP64 and FP32, against the oracle's assembled K/2 + M_Vext + sigma M (free rows),
+    on random vectors (boundary rows zero); FP64 to rounding, FP32 to single precision; two calls bitwise equal."""
+    from paper_2103_02824_gb300 import mk
+    c = case(name)
+    lv = c["level"]
+    m = gpu_mesh(ctx, name)
+    mol = mk.Molecule(c["wl"]["Z"], c["wl"]["R"])
+    n, ld = m.info["n_nodes"], 8
+    X = np.random.default_rng(11).standard_normal((n, ld))
+    X[lv.fine.boundary] = 0.0
+    A = lv.operator(c["sigma"])
+    ref = np.zeros((n, ld))
+    ref[lv.fine.free] = A @ X[lv.fine.free]
+    for dt, tol in ((torch.float64, 1e-13), (torch.float32, 3e-6)):
+        x = torch.from_numpy(X).to(dt).cuda()
+        y1 = torch.full_like(x, 7.0)
+        y2 = torch.full_like(x, -3.0)
+        mk.mk_operator_apply(ctx, m, mol, c["sigma"], x, y1)
+        mk.mk_operator_apply(ctx, m, mol, c["sigma"], x, y2)
+        torch.cuda.synchronize()
+        got = y1.double().cpu().numpy()
+        assert rel(got, ref) < tol, (dt, rel(got, ref))
+        assert torch.equal(y1, y2)
+        assert np.all(got[lv.fine.boundary] == 0)
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_correction_solve_mixed(ctx, torch, name):
+    """FP32 inner PCG + FP64 refinement reaches the FP64 residual target and the oracle's solution."""
+    from paper_2103_02824_gb300 import mk
+    c = case(name)
+    m = gpu_mesh(ctx, name)
+    N, ld = c["N"], 8
+    rhs = dev(torch, padded(c["out"]["rhs"], ld))
+    x = dev(torch, padded(c["out"]["u"], ld))
+    rep = mk.mk_correction_solve(ctx, m, mk.Molecule(c["wl"]["Z"], c["wl"]["R"]), c["sigma"], rhs, x, N,
+                                 opt=mk.opts(precision="mixed", rtol=1e-12, inner_rtol=1e-4, check_every=5))
+    assert rep["max_rel_residual"] <= 1e-12 and rep["refinements"] >= 2
+    assert rel(x.cpu().numpy()[:, :N], c["out"]["psihat"]) < 1e-8
+    assert np.all(x.cpu().numpy()[:, N:] == 0)
+
+
+@pytest.mark.parametrize("name", CASES)
 def test_augmented_project(ctx, torch, name):
     from paper_2103_02824_gb300 import mk
     c = case(name)
@@ -172,6 +216,38 @@ def test_small_eigensolve(ctx, torch, name):
     mk.mk_small_eigensolve(ctx, NH, N, *_eig_inputs(torch, c), lam, coef, st)
     torch.cuda.synchronize()
     assert np.all(st.cpu().numpy() == 0)
+    assert np.abs(lam.cpu().numpy() - o["lam"]).max() < 1e-10
+    assert np.abs(coef.cpu().numpy() - o["coef"]).max() < 1e-8 * np.abs(o["coef"]).max()
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_coarse_pencil_and_decompose(ctx, torch, name):
+    """mk_coarse_pencil reproduces A_H, M_H; mk_coarse_decompose gives the full spectrum of (A_H, M_H) with
+    M_H-orthonormal eigenvectors; the shared per-orbital solve matches the dense oracle selection."""
+    import scipy.linalg as sla
+    from paper_2103_02824_gb300 import mk
+    c = case(name)
+    o = c["out"]
+    m = gpu_mesh(ctx, name)
+    N, NH = c["N"], m.info["n_free_coarse"]
+    z = lambda *s: torch.zeros(s, dtype=torch.float64, device="cuda")
+    AH, MH, d, V = z(NH, NH), z(NH, NH), z(NH), z(NH, NH)
+    mk.mk_coarse_pencil(ctx, m, mk.Molecule(c["wl"]["Z"], c["wl"]["R"]), dev(torch, c["vq"]), AH, MH)
+    mk.mk_coarse_decompose(ctx, m, AH, d, V)
+    torch.cuda.synchronize()
+    assert rel(AH.cpu().numpy(), o["AH"]) < 1e-12 and rel(MH.cpu().numpy(), o["MH"]) < 1e-13
+    ev = sla.eigh(o["AH"], o["MH"], eigvals_only=True)
+    dh = d.cpu().numpy()
+    assert np.abs(dh - ev).max() < 1e-10 * max(1.0, np.abs(ev).max())
+    Vh = V.cpu().numpy()
+    assert np.abs(Vh.T @ o["MH"] @ Vh - np.eye(NH)).max() < 1e-10
+    assert np.abs(o["AH"] @ Vh - o["MH"] @ Vh * dh[None, :]).max() < 1e-9 * max(1.0, np.abs(ev).max())
+    lam = z(N)
+    coef = z(NH + 1, N)
+    st = torch.zeros(N, dtype=torch.int32, device="cuda")
+    b, cc, beta, gamma = (dev(torch, o[k]) for k in ("b", "c", "beta", "gamma"))
+    mk.mk_small_eigensolve_shared(ctx, NH, N, d, V, b, cc, beta, gamma, lam, coef, st)
+    torch.cuda.synchronize()
     assert np.abs(lam.cpu().numpy() - o["lam"]).max() < 1e-10
     assert np.abs(coef.cpu().numpy() - o["coef"]).max() < 1e-8 * np.abs(o["coef"]).max()
 
