@@ -215,6 +215,18 @@ int mk_coarse_decompose(mk_ctx* ctx, const mk_mesh* mesh, const double* AH, doub
 int mk_small_eigensolve_shared(mk_ctx* ctx, int N_H, int N, const double* d, const double* V, const double* b,
                                const double* c, const double* beta, const double* gamma, double* lambda,
                                double* coef, int32_t* status, void* stream);
+/* The same per-orbital solve as mk_small_eigensolve_shared, for callers that must not allocate device memory:
+ * programs whose device memory is reserved up front by another allocator (a cudaMalloc would fail or break that
+ * budget) and latency-sensitive loops that cannot afford cudaMalloc/cudaFree, which may synchronise the whole
+ * device.  No counterpart in the paper.  Needs no mk_ctx and allocates nothing: its workspace is a fixed array
+ * in the library (about 0.9 MB, held by every GPU that loads the library until the process exits), sized for
+ * N_H <= 512 and N <= 16; larger sizes return MK_ERR_INVALID_ARG.  It runs on the current CUDA device.  The
+ * first call on a device looks up the array's device address once (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the one array: calls that overlap on the GPU (other streams or
+ * host threads) race, so serialise them.  Nothing in the array needs to start at zero. */
+int mk_small_eigensolve_static(int N_H, int N, const double* d, const double* V, const double* b, const double* c,
+                               const double* beta, const double* gamma, double* lambda, double* coef,
+                               int32_t* status, void* stream);
 /* For each orbital i < N, all eigenpairs of the (N_H+1) pencil of Eq. (Eigenvalue_H_h)
  *   [[AH, b_i], [b_i^T, beta_i]] x = lambda [[MH, c_i], [c_i^T, gamma_i]] x
  * and the one "with the largest component in span{psi^_i}" (Algorithm 2 (a)), read as the largest

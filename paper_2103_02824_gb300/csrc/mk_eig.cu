@@ -12,6 +12,8 @@
 #include <cooperative_groups.h>
 
 #include <cmath>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "mk_device.cuh"
@@ -739,3 +741,60 @@ int mk_orbital_assemble(mk_ctx* ctx, const mk_mesh* m, const double* coef, const
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------------ no allocation
+// Per-orbital small eigensolve for callers that must not allocate device memory: programs whose device memory is
+// reserved up front by another allocator (a cudaMalloc would fail or break that budget) and latency-sensitive
+// loops that cannot afford cudaMalloc/cudaFree, which may synchronise the whole device.  Its workspace is the
+// fixed array below, sized for N_H <= kStaticMaxNH and N <= kStaticMaxN (about 0.9 MB, held by every GPU that
+// loads the library until the process exits).
+namespace mk {
+constexpr int kStaticMaxNH = 512;
+constexpr int kStaticMaxN = 16;
+constexpr size_t kStaticG = (size_t)kStaticMaxNH * 2 * kStaticMaxN;                   // doubles: V^T [b | c]
+constexpr size_t kStaticW = (size_t)kStaticMaxN * kWorkVecs * (kStaticMaxNH + 1);     // doubles: per-orbital work
+constexpr size_t kStaticIW = (size_t)kStaticMaxN * 4 * (kStaticMaxNH + 1);            // ints: per-orbital work
+static __device__ __align__(256) double g_static_ws[kStaticG + kStaticW + (kStaticIW + 1) / 2];
+
+static std::mutex g_static_mu;
+static double* g_static_ptr[64] = {nullptr};
+
+// Device address of g_static_ws on the current device, looked up once per device (host code cannot use the
+// array's name as a device address).
+static int static_workspace(double** out) {
+  int dev = 0;
+  MK_CUDA(cudaGetDevice(&dev));
+  MK_ARG(dev >= 0 && dev < 64, "mk_small_eigensolve_static: device id out of range");
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    MK_CUDA(cudaGetSymbolAddress(&p, g_static_ws));
+    g_static_ptr[dev] = (double*)p;
+  }
+  *out = g_static_ptr[dev];
+  return MK_OK;
+}
+}  // namespace mk
+
+extern "C" int mk_small_eigensolve_static(int NH, int N, const double* d, const double* V, const double* b,
+                                          const double* c, const double* beta, const double* gamma, double* lambda,
+                                          double* coef, int32_t* status, void* stream) {
+  MK_ARG(d && V && b && c && beta && gamma && lambda && coef && status, "mk_small_eigensolve_static: null argument");
+  MK_ARG(NH >= 1 && N >= 1, "mk_small_eigensolve_static: sizes must be positive");
+  MK_ARG(NH <= kStaticMaxNH, "mk_small_eigensolve_static: N_H = " + std::to_string(NH) + " exceeds the fixed maximum " +
+                             std::to_string(kStaticMaxNH) + " (use mk_small_eigensolve_shared)");
+  MK_ARG(N <= kStaticMaxN, "mk_small_eigensolve_static: N = " + std::to_string(N) + " exceeds the fixed maximum " +
+                           std::to_string(kStaticMaxN) + " (use mk_small_eigensolve_shared)");
+  double* ws = nullptr;
+  MK_TRY(static_workspace(&ws));
+  cudaStream_t s = (cudaStream_t)stream;
+  double* G = ws;
+  double* W = ws + kStaticG;
+  int* IW = reinterpret_cast<int*>(ws + kStaticG + kStaticW);
+  // Every workspace entry the kernels read is written first in the same call, so nothing needs clearing.
+  MK_COUNT(), k_vt_bc<<<(int)(((int64_t)NH * 2 * N + 127) / 128), 128, 0, s>>>(NH, N, V, b, c, G);
+  MK_COUNT(), k_secular_select<<<N, kEigThreads, 0, s>>>(NH, N, d, V, G, beta, gamma, W, IW, lambda, coef, status,
+                                                        1e-7, 1e-12);
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}

@@ -100,6 +100,7 @@ _SIGS = {
     "mk_operator_apply": [_vp, _vp, C.POINTER(mk_molecule), C.c_double, C.c_int, _vp, _vp, C.c_int, _vp],
     "mk_coarse_decompose": [_vp, _vp, _vp, _vp, _vp, _vp],
     "mk_small_eigensolve_shared": [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "mk_small_eigensolve_static": [C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "mk_orbital_assemble": [_vp, _vp, _vp, _vp, _vp, C.c_int, C.c_int, _vp, _vp],
     "mk_lowest_ritz": [_vp, _vp, C.POINTER(mk_molecule), C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double), _vp],
 }
@@ -327,6 +328,12 @@ def mk_coarse_decompose(ctx, mesh, AH, d, V, stream=None):
 def mk_small_eigensolve_shared(ctx, NH, N, d, V, b, c, beta, gamma, lam, coef, status, stream=None):
     _check(lib().mk_small_eigensolve_shared(ctx.h, NH, N, _ptr(d), _ptr(V), _ptr(b), _ptr(c), _ptr(beta),
                                             _ptr(gamma), _ptr(lam), _ptr(coef), _ptr(status), _stream(stream)))
+
+
+def mk_small_eigensolve_static(NH, N, d, V, b, c, beta, gamma, lam, coef, status, stream=None):
+    """Allocation-free variant (fixed library workspace; N_H <= 512, N <= 16); returns the status code."""
+    return lib().mk_small_eigensolve_static(NH, N, _ptr(d), _ptr(V), _ptr(b), _ptr(c), _ptr(beta), _ptr(gamma),
+                                            _ptr(lam), _ptr(coef), _ptr(status), _stream(stream))
 
 
 def mk_orbital_assemble(ctx, mesh, coef, psihat, u, N, psi, stream=None):
