@@ -127,10 +127,10 @@ def main():
     mol = mk.Molecule(wl["Z"], wl["R"])
     theta = mk.mk_lowest_ritz(ctx, mesh, mol, synth.lanczos_start(n_free), steps=60)
     sigma = 1.05 * max(0.0, -theta) + 0.5
-    psiH, lamH = coarse_eigenpairs(ctx, mesh, wl["Z"], wl["R"], N)
-    st = CorrectionStep(ctx, mesh, wl["Z"], wl["R"], N)
+    psiH, lamH, basis = coarse_eigenpairs(ctx, mesh, wl["Z"], wl["R"], N, return_basis=True)
+    st = CorrectionStep(ctx, mesh, wl["Z"], wl["R"], N, basis=basis)
     sopts = mk.opts(precision=a.precision, rtol=1e-8, check_every=10)
-    popts = mk.opts(precision="fp64", rtol=1e-8, check_every=10)
+    popts = mk.opts(precision=a.precision, rtol=1e-8, check_every=10)
     psiH_dev = torch.zeros((NH, st.ld), dtype=torch.float64, device="cuda")
     psiH_dev[:, :N] = torch.from_numpy(psiH).cuda()
 

@@ -210,6 +210,12 @@ int mk_coarse_pencil(mk_ctx* ctx, const mk_mesh* mesh, const mk_molecule* mol, c
  * MH is the mesh's own P^T M P, whose Cholesky factor mk_mesh_upload computed (M_H is fixed for a mesh pair).
  * FP64: C = L^-1 AH L^-T by two GEMMs, cyclic Jacobi (cooperative launch), V = L^-T Q. */
 int mk_coarse_decompose(mk_ctx* ctx, const mk_mesh* mesh, const double* AH, double* d, double* V, void* stream);
+/* The same decomposition started from a known M_H-orthonormal basis V0 [N_H*N_H] (e.g. the eigenvectors of the
+ * density-independent pencil (P^T (K/2 + M_Vext) P, M_H), which stays fixed for a molecule as the paper's static
+ * blocks do): C = V0^T AH V0 is then close to diagonal and Jacobi needs fewer sweeps; V = V0 Q.  The result is
+ * the eigen-decomposition of (AH, M_H) to FP64 accuracy whatever V0 is, as long as V0^T M_H V0 = I. */
+int mk_coarse_decompose_warm(mk_ctx* ctx, int N_H, const double* AH, const double* V0, double* d, double* V,
+                             void* stream);
 /* Per-orbital part, given the shared decomposition (d, V) of (AH, MH): same outputs and selection rule as
  * mk_small_eigensolve below. */
 int mk_small_eigensolve_shared(mk_ctx* ctx, int N_H, int N, const double* d, const double* V, const double* b,

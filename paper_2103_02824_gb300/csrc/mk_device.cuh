@@ -12,13 +12,32 @@ constexpr int kRedThreads = 256;
 
 inline int red_blocks(const mk_ctx* ctx) { return ctx->n_sms * kRedBlocksPerSM; }
 
-__device__ __forceinline__ double nuclear_potential(const double* __restrict__ nuc, int nnuc, double x, double y,
-                                                    double z) {
+// Small per-call arrays travel as kernel parameters (no device allocation, no host synchronisation).
+constexpr int kMaxNuclei = 64;
+struct NucParams {
+  int n;
+  double v[4 * kMaxNuclei];  // (Z, x, y, z) per nucleus
+};
+struct ColParams {
+  double v[MK_MAX_RHS];
+};
+
+inline NucParams make_nuc(const mk_molecule* mol) {
+  NucParams p{};
+  p.n = mol ? mol->n_nuclei : 0;
+  for (int k = 0; k < p.n && k < kMaxNuclei; ++k) {
+    p.v[4 * k] = mol->Z[k];
+    for (int c = 0; c < 3; ++c) p.v[4 * k + 1 + c] = mol->R[3 * k + c];
+  }
+  return p;
+}
+
+__device__ __forceinline__ double nuclear_potential(const NucParams& P, double x, double y, double z) {
   double v = 0.0;
-  for (int k = 0; k < nnuc; ++k) {
-    double dx = x - nuc[4 * k + 1], dy = y - nuc[4 * k + 2], dz = z - nuc[4 * k + 3];
+  for (int k = 0; k < P.n; ++k) {
+    double dx = x - P.v[4 * k + 1], dy = y - P.v[4 * k + 2], dz = z - P.v[4 * k + 3];
     double r = sqrt(dx * dx + dy * dy + dz * dz);
-    v -= nuc[4 * k] / fmax(r, 1e-8);
+    v -= P.v[4 * k] / fmax(r, 1e-8);
   }
   return v;
 }
@@ -89,6 +108,7 @@ __global__ void k_dot_partial(int64_t n_nodes, const T* __restrict__ a, const T*
 
 // Sums partials in block order: out[j] = sum_blk part[blk*N + j].
 __global__ void k_sum_partials(const double* __restrict__ part, int nblk, int N, double* __restrict__ out);
+void sum_partials(const double* part, int nblk, int N, double* out, cudaStream_t s);
 
 int column_dots(mk_ctx* ctx, int64_t n_nodes, const double* a, const double* b, int N, int ld, double* out,
                 cudaStream_t s);
@@ -97,14 +117,12 @@ int column_dots32(mk_ctx* ctx, int64_t n_nodes, const float* a, const float* b, 
 
 // element matrices (packed, FP64) of half_k K + vext_scale M_{V_ext} + mass_shift M + M_{vq}
 int element_matrices(mk_ctx* ctx, const Level& L, const mk_molecule* mol, double half_k, double vext_scale,
-                     double mass_shift, const double* vq, double* out, cudaStream_t s, int nuc_slot = S_NUC);
+                     double mass_shift, const double* vq, double* out, cudaStream_t s);
 // assembled diagonal of the packed element matrices, boundary rows set to 1
 int assemble_diagonal(mk_ctx* ctx, const Level& L, const double* Ae, double* diag, cudaStream_t s);
 // y = A x (y zeroed first), boundary rows of y zeroed if mask_boundary
 int apply64(mk_ctx* ctx, const Level& L, const double* Ae, const double* x, double* y, int N, int ld,
             bool mask_boundary, cudaStream_t s);
 
-// nuclei packed for the device: [n*4] (Z, x, y, z); returns a device pointer in a ctx slot
-double* upload_nuclei(mk_ctx* ctx, const mk_molecule* mol, int* err, cudaStream_t s, int slot = S_NUC);
 
 }  // namespace mk

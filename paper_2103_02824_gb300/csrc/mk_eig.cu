@@ -12,6 +12,8 @@
 #include <cooperative_groups.h>
 
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -131,10 +133,38 @@ __device__ __forceinline__ Rot make_rot(const double* __restrict__ S, int n2, in
   double c = 1.0, s = 0.0;
   if (apq != 0.0) {
     const double app = S[(int64_t)p * n2 + p], aqq = S[(int64_t)q * n2 + q];
-    const double theta = (aqq - app) / (2.0 * apq);
-    const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-    c = 1.0 / sqrt(t * t + 1.0);
-    s = t * c;
+    // FP64 division and square root are slow here: FP32 seeds, then Newton steps that use FP64 FMAs only.  The
+    // FP32 seed needs |2 apq| well inside the FP32 range; outside it the exact FP64 division is used.
+    const double den = 2.0 * apq;
+    double theta;
+    if (fabs(den) > 1e-30 && fabs(den) < 1e30) {
+      double rd = (double)(1.0f / (float)den);
+      rd = rd * (2.0 - den * rd);
+      rd = rd * (2.0 - den * rd);
+      theta = (aqq - app) * rd;
+    } else {
+      theta = (aqq - app) / den;
+    }
+    double t;
+    if (!(fabs(theta) <= 1e15)) {
+      t = isfinite(theta) ? 0.5 / theta : 0.0;
+    } else {
+      const float tf = (float)theta;
+      t = (double)(copysignf(1.0f, tf) / (fabsf(tf) + sqrtf(tf * tf + 1.0f)));
+      for (int it = 0; it < 2; ++it) {  // root of t^2 + 2 theta t - 1 with |t| <= 1
+        const double f = t * t + 2.0 * theta * t - 1.0;
+        const double g = 2.0 * (t + theta);
+        double rg = (double)(1.0f / (float)g);
+        rg = rg * (2.0 - g * rg);
+        t -= f * rg;
+      }
+    }
+    const double x = 1.0 + t * t;
+    double r = (double)rsqrtf((float)x);
+    r = r * (1.5 - 0.5 * x * r * r);
+    r = r * (1.5 - 0.5 * x * r * r);
+    c = r;
+    s = t * r;
   }
   return Rot{p, q, c, s};
 }
@@ -267,14 +297,19 @@ static void gemm64(int M, int N, int K, const double* A, int lda, int ta, const 
 }
 
 // Sort the n eigenvalues (diag of S, first n of n2) ascending: perm[rank] = index (ties by index).
-__global__ void k_rank(int n, int n2, const double* __restrict__ S, double* __restrict__ d, int* __restrict__ perm) {
+__global__ void k_rank(int n, int n2, const double* __restrict__ S0, const double* __restrict__ S1,
+                       const int* __restrict__ info, double* __restrict__ d, int* __restrict__ perm) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const double* __restrict__ S = info[1] ? S1 : S0;  // buffer that holds the Jacobi result
+  // strict total order on (key, index) with NaN keyed as +inf: the ranks always form a permutation
+  auto key = [](double x) { return isnan(x) ? INFINITY : x; };
   const double v = S[(int64_t)i * n2 + i];
+  const double kv = key(v);
   int r = 0;
   for (int k = 0; k < n; ++k) {
-    const double w = S[(int64_t)k * n2 + k];
-    if (w < v || (w == v && k < i)) ++r;
+    const double kw = key(S[(int64_t)k * n2 + k]);
+    if (kw < kv || (kw == kv && k < i)) ++r;
   }
   d[r] = v;
   perm[r] = i;
@@ -286,7 +321,8 @@ __global__ void k_gather_cols(int n, int n2, const double* __restrict__ Q, const
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)n * n) return;
   const int i = (int)(t / n), r = (int)(t % n);
-  Qs[t] = Q[(int64_t)i * n2 + perm[r]];
+  const int c = perm[r];
+  Qs[t] = (c >= 0 && c < n) ? Q[(int64_t)i * n2 + c] : NAN;
 }
 
 // G[k][col] = sum_i V[i][k] B[i][col]  (V^T [b|c]); B has 2N columns: b (ld N) then c (ld N)
@@ -315,36 +351,49 @@ __device__ __forceinline__ double secular_f(int m, const double* __restrict__ dd
 
 constexpr int kEigThreads = 256;
 
-// One block per orbital.  Work arrays in global memory: per orbital kWorkVecs*(n+1) doubles, 4*(n+1) ints.
+// Per-orbital workspace: kWorkVecs vectors of n+1 doubles, a 16-double header, and 4 int vectors of n+1.
 constexpr int kWorkVecs = 10;
+__host__ __device__ constexpr int64_t sec_stride(int n) { return (int64_t)kWorkVecs * (n + 1) + 16; }
 
-__global__ void k_secular_select(int n, int N, const double* __restrict__ d, const double* __restrict__ V,
-                                 const double* __restrict__ G, const double* __restrict__ beta,
-                                 const double* __restrict__ gamma, double* __restrict__ work, int* __restrict__ iwork,
-                                 double* __restrict__ lambda, double* __restrict__ coef, int32_t* __restrict__ status,
-                                 double sing_rtol, double tie_rtol) {
+struct SecWork {
+  double *zs, *ps, *dk, *zk, *score, *eig, *yv, *rcos, *rsin, *ytmp, *hdr;
+  int *kind, *comp, *partner, *origin_idx;
+};
+
+__device__ __forceinline__ SecWork sec_work(double* work, int* iwork, int n, int i) {
+  const int64_t n1 = n + 1;
+  SecWork w;
+  w.zs = work + (int64_t)i * sec_stride(n);  // z in the (rotated) V basis
+  w.ps = w.zs + n1;                          // p = V^T c in the (rotated) V basis
+  w.dk = w.ps + n1;                          // poles kept in the secular equation
+  w.zk = w.dk + n1;                          // their z
+  w.score = w.zk + n1;                       // per candidate |(x, psi^)_M|
+  w.eig = w.score + n1;                      // per candidate eigenvalue
+  w.yv = w.eig + n1;                         // per root: offset delta from its origin pole
+  w.rcos = w.yv + n1;                        // deflation rotation of index k with its partner
+  w.rsin = w.rcos + n1;
+  w.ytmp = w.rsin + n1;                      // selected eigenvector
+  w.hdr = w.ytmp + n1;                       // alpha, ||u||, m, n_candidates, singular
+  w.kind = iwork + (int64_t)i * 4 * n1;      // candidate t: >= 0 root index, < 0 deflated -(k+1)
+  w.comp = w.kind + n1;                      // kept pole -> original index
+  w.partner = w.comp + n1;                   // rotation partner of k (-1 none)
+  w.origin_idx = w.partner + n1;             // per root: kept pole used as origin
+  return w;
+}
+
+// Phase 1, one block per orbital: p = V^T c, ||u||, z, alpha, deflation; the singular case is finished here.
+__global__ void k_sec_prepare(int n, int N, const double* __restrict__ d, const double* __restrict__ V,
+                              const double* __restrict__ G, const double* __restrict__ beta,
+                              const double* __restrict__ gamma, double* __restrict__ work, int* __restrict__ iwork,
+                              double* __restrict__ lambda, double* __restrict__ coef, int32_t* __restrict__ status,
+                              double sing_rtol, double tie_rtol) {
   const int i = blockIdx.x;
   if (i >= N) return;
-  const int64_t n1 = n + 1;
-  double* zs = work + (int64_t)i * kWorkVecs * n1;  // z in the (rotated) V basis
-  double* ps = zs + n1;                             // p = V^T c in the (rotated) V basis
-  double* dk = ps + n1;                             // poles kept in the secular equation
-  double* zk = dk + n1;                             // their z
-  double* score = zk + n1;                          // per candidate |(x, psi^)_M|
-  double* eig = score + n1;                         // per candidate eigenvalue
-  double* yv = eig + n1;                            // per root: offset delta; later the selected eigenvector
-  double* rcos = yv + n1;                           // deflation rotation of index k with its partner
-  double* rsin = rcos + n1;
-  double* ytmp = rsin + n1;
-  int* kind = iwork + (int64_t)i * 4 * n1;          // candidate t: >= 0 root index, < 0 deflated -(k+1)
-  int* comp = kind + n1;                            // kept pole -> original index
-  int* partner = comp + n1;                         // rotation partner of k (-1 none)
-  int* origin_idx = partner + n1;                   // per root: kept pole used as origin
-  __shared__ double s_alpha, s_un, s_norm, s_sign, s_ylast;
-  __shared__ int s_m, s_ncand, s_sel, s_singular;
+  SecWork w = sec_work(work, iwork, n, i);
   __shared__ double s_red[kEigThreads];
+  __shared__ double s_un;
+  __shared__ int s_singular, s_sel;
   const int tid = threadIdx.x;
-  // p = V^T c, g = V^T b;  ||u||^2 = gamma - |p|^2 (u = psi^ - Pi_H psi^, V is M_H-orthonormal)
   double pp = 0.0;
   for (int k = tid; k < n; k += blockDim.x) {
     const double pk = G[(int64_t)k * 2 * N + N + i];
@@ -360,6 +409,8 @@ __global__ void k_secular_select(int n, int N, const double* __restrict__ d, con
     const double u2 = gamma[i] - s_red[0];
     s_singular = !(u2 > sing_rtol * sing_rtol * gamma[i]);
     s_un = s_singular ? 0.0 : sqrt(u2);
+    w.hdr[1] = s_un;
+    w.hdr[4] = s_singular;
   }
   __syncthreads();
   if (s_singular) {  // psi^ in V_H: coarse Ritz pair with the largest |(v_k, Pi_H psi^)_M| = |p_k|
@@ -372,6 +423,7 @@ __global__ void k_secular_select(int n, int N, const double* __restrict__ d, con
       s_sel = sel;
       lambda[i] = d[sel];
       status[i] = MK_ERR_SINGULAR_AUG;
+      w.hdr[2] = -1.0;
     }
     __syncthreads();
     const double sgn = G[(int64_t)s_sel * 2 * N + N + i] < 0 ? -1.0 : 1.0;
@@ -383,9 +435,9 @@ __global__ void k_secular_select(int n, int N, const double* __restrict__ d, con
   double a2 = 0.0;
   for (int k = tid; k < n; k += blockDim.x) {
     const double gk = G[(int64_t)k * 2 * N + i], pk = G[(int64_t)k * 2 * N + N + i];
-    zs[k] = (gk - d[k] * pk) / s_un;
-    ps[k] = pk;
-    partner[k] = -1;
+    w.zs[k] = (gk - d[k] * pk) / s_un;
+    w.ps[k] = pk;
+    w.partner[k] = -1;
     a2 += -2.0 * pk * gk + pk * d[k] * pk;
   }
   s_red[tid] = a2;
@@ -395,155 +447,221 @@ __global__ void k_secular_select(int n, int N, const double* __restrict__ d, con
     __syncthreads();
   }
   if (tid == 0) {
-    s_alpha = (beta[i] + s_red[0]) / (s_un * s_un);
+    const double alpha = (beta[i] + s_red[0]) / (s_un * s_un);
     // deflation (sequential, O(n)): negligible z_k, then (nearly) equal poles merged by Givens rotations
-    double zn = 0.0, dmax = fabs(s_alpha);
+    double zn = 0.0, dmax = fabs(alpha);
     for (int k = 0; k < n; ++k) {
-      zn += zs[k] * zs[k];
+      zn += w.zs[k] * w.zs[k];
       dmax = fmax(dmax, fabs(d[k]));
     }
     zn = sqrt(zn);
     const double tol = 8.0 * 2.220446049250313e-16 * fmax(dmax, zn);
     int m = 0, nc = 0, last = -1;
     for (int k = 0; k < n; ++k) {
-      if (fabs(zs[k]) <= tol) {
-        kind[nc] = -(k + 1);
-        eig[nc] = d[k];
+      if (fabs(w.zs[k]) <= tol) {
+        w.kind[nc] = -(k + 1);
+        w.eig[nc] = d[k];
         ++nc;
         continue;
       }
       if (last >= 0 && fabs(d[k] - d[last]) <= tol) {
         // v_last' = c v_last + s v_k, v_k' = -s v_last + c v_k with z_k' = 0
-        const double r = hypot(zs[last], zs[k]);
-        const double c = zs[last] / r, sn = zs[k] / r;
-        const double pl = ps[last], pk = ps[k];
-        ps[last] = c * pl + sn * pk;
-        ps[k] = -sn * pl + c * pk;
-        zs[last] = r;
-        zs[k] = 0.0;
-        partner[k] = last;
-        rcos[k] = c;
-        rsin[k] = sn;
-        kind[nc] = -(k + 1);
-        eig[nc] = d[k];
+        const double r = hypot(w.zs[last], w.zs[k]);
+        const double c = w.zs[last] / r, sn = w.zs[k] / r;
+        const double pl = w.ps[last], pk = w.ps[k];
+        w.ps[last] = c * pl + sn * pk;
+        w.ps[k] = -sn * pl + c * pk;
+        w.zs[last] = r;
+        w.zs[k] = 0.0;
+        w.partner[k] = last;
+        w.rcos[k] = c;
+        w.rsin[k] = sn;
+        w.kind[nc] = -(k + 1);
+        w.eig[nc] = d[k];
         ++nc;
         continue;
       }
-      comp[m++] = k;
+      w.comp[m++] = k;
       last = k;
     }
     for (int t = 0; t < m; ++t) {
-      dk[t] = d[comp[t]];
-      zk[t] = zs[comp[t]];
+      w.dk[t] = d[w.comp[t]];
+      w.zk[t] = w.zs[w.comp[t]];
     }
-    for (int t = 0; t <= m; ++t) kind[nc + t] = t;
-    s_m = m;
-    s_ncand = nc + m + 1;
+    for (int t = 0; t <= m; ++t) w.kind[nc + t] = t;
+    for (int t = 0; t < nc; ++t) w.score[t] = fabs(w.ps[-w.kind[t] - 1]);
+    w.hdr[0] = alpha;
+    w.hdr[2] = m;
+    w.hdr[3] = nc + m + 1;
   }
-  __syncthreads();
-  const int m = s_m, nc0 = s_ncand - (m + 1);
-  const double alpha = s_alpha;
+}
+
+// Secular sum alpha - (origin + delta) + sum_t z_t^2 / ((origin - d_t) + delta), split over the 32 lanes and
+// folded with a fixed tree; every lane returns lane 0's value.
+__device__ __forceinline__ double warp_secular(int m, const double* __restrict__ dk, const double* __restrict__ zk,
+                                              double alpha, double origin, double delta, int lane) {
+  double f = 0.0;
+  for (int t = lane; t < m; t += 32) f += zk[t] * zk[t] / ((origin - dk[t]) + delta);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) f += __shfl_down_sync(0xffffffffu, f, off);
+  return __shfl_sync(0xffffffffu, f, 0) + (alpha - (origin + delta));
+}
+
+// Phase 2, one warp per root: bisection on the offset from the nearer pole, then the root's score.
+__global__ void k_sec_roots(int n, int N, double* __restrict__ work, int* __restrict__ iwork) {
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (gw >= (int64_t)N * (n + 1)) return;
+  const int i = (int)(gw / (n + 1)), r = (int)(gw % (n + 1));
+  SecWork w = sec_work(work, iwork, n, i);
+  if (w.hdr[4] != 0.0) return;
+  const int m = (int)w.hdr[2];
+  if (r > m) return;
+  const int nc0 = (int)w.hdr[3] - (m + 1);
+  const double alpha = w.hdr[0], un = w.hdr[1];
+  const double* dk = w.dk;
+  const double* zk = w.zk;
   double zn2 = 0.0;
-  for (int t = 0; t < m; ++t) zn2 += zk[t] * zk[t];
-  const double zn = sqrt(zn2);
-  // roots of alpha - mu + sum z_t^2/(mu - d_t): one in each of (-inf,d_0), (d_0,d_1), ..., (d_{m-1},inf)
-  for (int r = tid; r <= m; r += blockDim.x) {
-    double origin = alpha, lo = 0.0, hi = 0.0;
-    int oi = -1;
-    if (m > 0) {
-      if (r == 0) {
-        oi = 0; origin = dk[0];
-        lo = fmin(dk[0], alpha) - zn - 1.0 - origin; hi = 0.0;
-      } else if (r == m) {
-        oi = m - 1; origin = dk[m - 1];
-        lo = 0.0; hi = fmax(dk[m - 1], alpha) + zn + 1.0 - origin;
+  for (int t = lane; t < m; t += 32) zn2 += zk[t] * zk[t];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) zn2 += __shfl_down_sync(0xffffffffu, zn2, off);
+  const double zn = sqrt(__shfl_sync(0xffffffffu, zn2, 0));
+  double origin = alpha, lo = 0.0, hi = 0.0;
+  int oi = -1;
+  if (m > 0) {
+    if (r == 0) {
+      oi = 0; origin = dk[0];
+      lo = fmin(dk[0], alpha) - zn - 1.0 - origin; hi = 0.0;
+    } else if (r == m) {
+      oi = m - 1; origin = dk[m - 1];
+      lo = 0.0; hi = fmax(dk[m - 1], alpha) + zn + 1.0 - origin;
+    } else {
+      const double mid = 0.5 * (dk[r - 1] + dk[r]);
+      if (warp_secular(m, dk, zk, alpha, dk[r - 1], mid - dk[r - 1], lane) > 0) {
+        oi = r; origin = dk[r]; lo = mid - dk[r]; hi = 0.0;   // root in (mid, d_r)
       } else {
-        const double mid = 0.5 * (dk[r - 1] + dk[r]);
-        if (secular_f(m, dk, zk, alpha, dk[r - 1], mid - dk[r - 1]) > 0) {
-          oi = r; origin = dk[r]; lo = mid - dk[r]; hi = 0.0;   // root in (mid, d_r)
-        } else {
-          oi = r - 1; origin = dk[r - 1]; lo = 0.0; hi = mid - dk[r - 1];
-        }
+        oi = r - 1; origin = dk[r - 1]; lo = 0.0; hi = mid - dk[r - 1];
       }
     }
-    double delta = 0.5 * (lo + hi);
-    if (m > 0)
-      for (int it = 0; it < 2100; ++it) {  // bisection to adjacent doubles (bounded)
-        delta = 0.5 * (lo + hi);
-        if (delta == lo || delta == hi) break;
-        if (secular_f(m, dk, zk, alpha, origin, delta) > 0) lo = delta; else hi = delta;
-      }
-    origin_idx[r] = oi;
-    yv[r] = delta;
-    double yy = 1.0, yp = s_un;  // y_last = 1, p_last = ||u||
-    for (int t = 0; t < m; ++t) {
-      const double y = zk[t] / ((origin - dk[t]) + delta);
-      yy += y * y;
-      yp += y * ps[comp[t]];
-    }
-    score[nc0 + r] = fabs(yp) / sqrt(yy);
-    eig[nc0 + r] = origin + delta;
   }
-  for (int t = tid; t < nc0; t += blockDim.x) score[t] = fabs(ps[-kind[t] - 1]);
-  __syncthreads();
-  if (tid == 0) {  // largest score; ties within tie_rtol go to the lower eigenvalue
+  double delta = 0.5 * (lo + hi);
+  if (m > 0)
+    for (int it = 0; it < 2100; ++it) {  // bisection to adjacent doubles (bounded)
+      delta = 0.5 * (lo + hi);
+      if (delta == lo || delta == hi) break;
+      if (warp_secular(m, dk, zk, alpha, origin, delta, lane) > 0) lo = delta; else hi = delta;
+    }
+  // score of the eigenvector y_t = z_t/(mu - d_t), y_last = 1, against phi~ = (p, ||u||)
+  double yy = 0.0, yp = 0.0;
+  for (int t = lane; t < m; t += 32) {
+    const double y = zk[t] / ((origin - dk[t]) + delta);
+    yy += y * y;
+    yp += y * w.ps[w.comp[t]];
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    yy += __shfl_down_sync(0xffffffffu, yy, off);
+    yp += __shfl_down_sync(0xffffffffu, yp, off);
+  }
+  if (lane == 0) {
+    w.origin_idx[r] = oi;
+    w.yv[r] = delta;
+    w.score[nc0 + r] = fabs(yp + un) / sqrt(yy + 1.0);
+    w.eig[nc0 + r] = origin + delta;
+  }
+}
+
+// Phase 3, one block per orbital: selection (largest score; ties within tie_rtol to the lower eigenvalue), the
+// eigenvector back in the V basis and the coarse coefficients.
+__global__ void k_sec_select(int n, int N, const double* __restrict__ V, const double* __restrict__ G,
+                             double* __restrict__ work, int* __restrict__ iwork, double* __restrict__ lambda,
+                             double* __restrict__ coef, int32_t* __restrict__ status, double tie_rtol) {
+  const int i = blockIdx.x;
+  if (i >= N) return;
+  SecWork w = sec_work(work, iwork, n, i);
+  if (w.hdr[4] != 0.0) return;
+  __shared__ double s_norm, s_sign, s_ylast;
+  __shared__ int s_sel;
+  const int tid = threadIdx.x;
+  const int m = (int)w.hdr[2], ncand = (int)w.hdr[3];
+  const double alpha = w.hdr[0], un = w.hdr[1];
+  if (tid == 0) {
     double best = -1.0;
-    for (int t = 0; t < s_ncand; ++t) best = fmax(best, score[t]);
+    for (int t = 0; t < ncand; ++t) best = fmax(best, w.score[t]);
     int sel = -1;
-    for (int t = 0; t < s_ncand; ++t)
-      if (score[t] >= best * (1.0 - tie_rtol) && (sel < 0 || eig[t] < eig[sel])) sel = t;
+    for (int t = 0; t < ncand; ++t)
+      if (w.score[t] >= best * (1.0 - tie_rtol) && (sel < 0 || w.eig[t] < w.eig[sel])) sel = t;
     s_sel = sel;
-    lambda[i] = eig[sel];
-    status[i] = MK_OK;
+    if (sel >= 0) {
+      lambda[i] = w.eig[sel];
+      status[i] = MK_OK;
+    } else {  // no finite score (non-finite input): report and write nothing else
+      lambda[i] = NAN;
+      status[i] = MK_ERR_NOT_CONVERGED;
+    }
   }
+  for (int t = tid; t < n; t += blockDim.x) w.ytmp[t] = 0.0;
   __syncthreads();
+  if (s_sel < 0) {
+    for (int r = tid; r <= n; r += blockDim.x) coef[(int64_t)r * N + i] = 0.0;
+    return;
+  }
   const int sel = s_sel;
-  // selected eigenvector in the rotated V basis (ytmp) and its last component
-  for (int t = tid; t < n; t += blockDim.x) ytmp[t] = 0.0;
-  __syncthreads();
-  if (kind[sel] < 0) {
+  if (w.kind[sel] < 0) {
     if (tid == 0) {
-      ytmp[-kind[sel] - 1] = 1.0;
+      w.ytmp[-w.kind[sel] - 1] = 1.0;
       s_ylast = 0.0;
     }
   } else {
-    const int r = kind[sel];
-    const int oi = origin_idx[r];
-    const double origin = oi >= 0 ? dk[oi] : alpha;
-    const double delta = yv[r];
-    for (int t = tid; t < m; t += blockDim.x) ytmp[comp[t]] = zk[t] / ((origin - dk[t]) + delta);
+    const int r = w.kind[sel];
+    const int oi = w.origin_idx[r];
+    const double origin = oi >= 0 ? w.dk[oi] : alpha;
+    const double delta = w.yv[r];
+    for (int t = tid; t < m; t += blockDim.x) w.ytmp[w.comp[t]] = w.zk[t] / ((origin - w.dk[t]) + delta);
     if (tid == 0) s_ylast = 1.0;
   }
   __syncthreads();
   if (tid == 0) {
-    double nn = s_ylast * s_ylast, sp = s_ylast * s_un;
+    double nn = s_ylast * s_ylast, sp = s_ylast * un;
     for (int t = 0; t < n; ++t) {
-      nn += ytmp[t] * ytmp[t];
-      sp += ytmp[t] * ps[t];
+      nn += w.ytmp[t] * w.ytmp[t];
+      sp += w.ytmp[t] * w.ps[t];
     }
     s_norm = sqrt(nn);
     s_sign = sp < 0 ? -1.0 : 1.0;
     // back to the original V basis: undo the rotations in reverse order of creation
     for (int k = n - 1; k >= 0; --k) {
-      const int l = partner[k];
+      const int l = w.partner[k];
       if (l < 0) continue;
-      const double a = ytmp[l], b = ytmp[k];
-      ytmp[l] = a * rcos[k] - b * rsin[k];
-      ytmp[k] = a * rsin[k] + b * rcos[k];
+      const double a = w.ytmp[l], b = w.ytmp[k];
+      w.ytmp[l] = a * w.rcos[k] - b * w.rsin[k];
+      w.ytmp[k] = a * w.rsin[k] + b * w.rcos[k];
     }
   }
   __syncthreads();
   const double scale = s_sign / s_norm;
   const double yl = scale * s_ylast;
   // coarse part: phi_H = V (y - (y_last/||u||) p), theta_2 = y_last/||u||
-  for (int k = tid; k < n; k += blockDim.x) yv[k] = scale * ytmp[k] - (yl / s_un) * G[(int64_t)k * 2 * N + N + i];
+  for (int k = tid; k < n; k += blockDim.x) w.yv[k] = scale * w.ytmp[k] - (yl / un) * G[(int64_t)k * 2 * N + N + i];
   __syncthreads();
   for (int r = tid; r < n; r += blockDim.x) {
     double s = 0.0;
-    for (int k = 0; k < n; ++k) s += V[(int64_t)r * n + k] * yv[k];
+    for (int k = 0; k < n; ++k) s += V[(int64_t)r * n + k] * w.yv[k];
     coef[(int64_t)r * N + i] = s;
   }
-  if (tid == 0) coef[(int64_t)n * N + i] = yl / s_un;
+  if (tid == 0) coef[(int64_t)n * N + i] = yl / un;
+}
+
+// The three phases for all orbitals; work holds N * sec_stride(n) doubles, iwork N * 4 (n+1) ints.
+static void secular_launch(int n, int N, const double* d, const double* V, const double* G, const double* beta,
+                           const double* gamma, double* work, int* iwork, double* lambda, double* coef,
+                           int32_t* status, cudaStream_t s) {
+  const double sing_rtol = 1e-7, tie_rtol = 1e-12;
+  MK_COUNT(), k_sec_prepare<<<N, kEigThreads, 0, s>>>(n, N, d, V, G, beta, gamma, work, iwork, lambda, coef, status,
+                                                     sing_rtol, tie_rtol);
+  const int64_t warps = (int64_t)N * (n + 1);
+  MK_COUNT(), k_sec_roots<<<(int)((warps + 7) / 8), 256, 0, s>>>(n, N, work, iwork);
+  MK_COUNT(), k_sec_select<<<N, kEigThreads, 0, s>>>(n, N, V, G, work, iwork, lambda, coef, status, tie_rtol);
 }
 
 // ------------------------------------------------------------------------------------------------ A8
@@ -594,7 +712,12 @@ int inverse_cholesky(mk_ctx* ctx, int n, const double* MH, double* Linv, int slo
 
 // Shared decomposition of the coarse pencil: C = Linv AH Linv^T, Jacobi C = Q diag Q^T, d ascending,
 // V = Linv^T Q (columns sorted with d).  V row-major [n x n], V[i][k] = component i of eigenvector k.
-int decompose(mk_ctx* ctx, int n, const double* Linv, const double* AH, double* d, double* V, cudaStream_t s) {
+// In a basis W with W^T M_H W = I the pencil (AH, M_H) is the symmetric matrix C = W^T AH W; its Jacobi
+// eigenvectors Q give V = W Q (M_H-orthonormal), d ascending.  W = X when w_is_x (a previous eigenbasis: warm
+// start, C is then nearly diagonal), W = X^T when X = L^-1 (M_H = L L^T).  V row-major, V[i][k] = component i
+// of eigenvector k.
+int decompose(mk_ctx* ctx, int n, const double* X, bool w_is_x, const double* AH, double* d, double* V,
+              cudaStream_t s) {
   const int n2 = (n + 1) / 2 * 2;
   int err = MK_OK;
   size_t off = 0;
@@ -607,8 +730,9 @@ int decompose(mk_ctx* ctx, int n, const double* Linv, const double* AH, double* 
   double *T = (double*)(ws + oT), *C = (double*)(ws + oC), *S0 = (double*)(ws + oS0), *S1 = (double*)(ws + oS1);
   double *Q = (double*)(ws + oQ), *red = (double*)(ws + oRed);
   int *perm = (int*)(ws + oPerm), *info = (int*)(ws + oInfo);
-  gemm64(n, n, n, Linv, n, 0, AH, n, 0, T, n, s);                   // T = Linv AH
-  gemm64(n, n, n, T, n, 0, Linv, n, 1, C, n, s);                    // C = T Linv^T
+  const int tx = w_is_x ? 1 : 0;                                     // op for W^T
+  gemm64(n, n, n, X, n, tx, AH, n, 0, T, n, s);                      // T = W^T AH
+  gemm64(n, n, n, T, n, 0, X, n, 1 - tx, C, n, s);                   // C = T W
   MK_COUNT(), k_pad_sym<<<(int)(((int64_t)n2 * n2 + 255) / 256), 256, 0, s>>>(n, n2, C, S0, Q, 0.0);
   const int np = n2 / 2;
   const size_t smem = (size_t)np * sizeof(Rot);
@@ -618,18 +742,20 @@ int decompose(mk_ctx* ctx, int n, const double* Linv, const double* AH, double* 
   MK_ARG(per_sm >= 1, "mk: Jacobi kernel cannot be resident (coarse space too large)");
   int grid = std::min(ctx->n_sms, 4096);
   int max_sweeps = 60;
-  double tol = 1e-15;
+  double tol = 1e-14;
   int n2v = n2;
   void* args[] = {&n2v, &S0, &S1, &Q, &red, &max_sweeps, &tol, &info};
   MK_COUNT();
   MK_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi, grid, 256, args, smem, s));
-  int hinfo[2];
-  MK_CUDA(cudaMemcpyAsync(hinfo, info, sizeof(hinfo), cudaMemcpyDeviceToHost, s));
-  MK_CUDA(cudaStreamSynchronize(s));
-  const double* Sf = hinfo[1] ? S1 : S0;
-  MK_COUNT(), k_rank<<<(n + 127) / 128, 128, 0, s>>>(n, n2, Sf, d, perm);
+  if (std::getenv("MK_DEBUG")) {
+    int h[2];
+    cudaMemcpyAsync(h, info, sizeof(h), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    std::fprintf(stderr, "mk: Jacobi n=%d sweeps=%d (%s)\n", n, h[0], w_is_x ? "warm" : "cholesky");
+  }
+  MK_COUNT(), k_rank<<<(n + 127) / 128, 128, 0, s>>>(n, n2, S0, S1, info, d, perm);
   MK_COUNT(), k_gather_cols<<<(int)(((int64_t)n * n + 255) / 256), 256, 0, s>>>(n, n2, Q, perm, C);  // C = Q sorted
-  gemm64(n, n, n, Linv, n, 1, C, n, 0, V, n, s);                     // V = Linv^T Q
+  gemm64(n, n, n, X, n, 1 - tx, C, n, 0, V, n, s);                   // V = W Q
   MK_CUDA(cudaGetLastError());
   return MK_OK;
 }
@@ -639,15 +765,14 @@ int secular(mk_ctx* ctx, int n, int N, const double* d, const double* V, const d
   int err = MK_OK;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
-  const size_t oG = take((size_t)n * 2 * N * 8), oW = take((size_t)N * kWorkVecs * (n + 1) * 8);
+  const size_t oG = take((size_t)n * 2 * N * 8), oW = take((size_t)N * sec_stride(n) * 8);
   const size_t oIW = take((size_t)N * 4 * (n + 1) * 4);
   char* ws = (char*)scratch(ctx, S_EIG, off, &err);
   if (!ws) return err;
   double *G = (double*)(ws + oG), *W = (double*)(ws + oW);
   int* IW = (int*)(ws + oIW);
   MK_COUNT(), k_vt_bc<<<(int)(((int64_t)n * 2 * N + 127) / 128), 128, 0, s>>>(n, N, V, b, c, G);
-  MK_COUNT(), k_secular_select<<<N, kEigThreads, 0, s>>>(n, N, d, V, G, beta, gamma, W, IW, lambda, coef, status,
-                                                        1e-7, 1e-12);
+  secular_launch(n, N, d, V, G, beta, gamma, W, IW, lambda, coef, status, s);
   MK_CUDA(cudaGetLastError());
   return MK_OK;
 }
@@ -664,7 +789,7 @@ int mesh_mass_factor(mk_ctx* ctx, mk_mesh* m) {
   double* MH = (double*)scratch(ctx, S_VEC5, (size_t)n * n * sizeof(double) * 2, &err);
   if (!Me || !MH) return err;
   cudaStream_t s = 0;
-  MK_TRY(element_matrices(ctx, F, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s, S_NUC2));
+  MK_TRY(element_matrices(ctx, F, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s));
   MK_TRY(coarse_matrices(ctx, m, Me, Me, MH, MH + (size_t)n * n, S_COARSE2, s));
   if (cudaMalloc(&m->d_MH_Linv, (size_t)n * n * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
@@ -684,7 +809,15 @@ extern "C" {
 int mk_coarse_decompose(mk_ctx* ctx, const mk_mesh* m, const double* AH, double* d, double* V, void* stream) {
   MK_ARG(ctx && m && AH && d && V && m->d_MH_Linv, "mk_coarse_decompose: null argument");
   MK_CUDA(cudaSetDevice(ctx->device));
-  return decompose(ctx, (int)m->coarse.n_free, m->d_MH_Linv, AH, d, V, (cudaStream_t)stream);
+  return decompose(ctx, (int)m->coarse.n_free, m->d_MH_Linv, false, AH, d, V, (cudaStream_t)stream);
+}
+
+int mk_coarse_decompose_warm(mk_ctx* ctx, int NH, const double* AH, const double* V0, double* d, double* V,
+                             void* stream) {
+  MK_ARG(ctx && AH && V0 && d && V && NH >= 1, "mk_coarse_decompose_warm: bad argument");
+  MK_ARG(V0 != V, "mk_coarse_decompose_warm: V0 and V must not alias");
+  MK_CUDA(cudaSetDevice(ctx->device));
+  return decompose(ctx, NH, V0, true, AH, d, V, (cudaStream_t)stream);
 }
 
 int mk_small_eigensolve_shared(mk_ctx* ctx, int NH, int N, const double* d, const double* V, const double* b,
@@ -712,7 +845,7 @@ int mk_small_eigensolve(mk_ctx* ctx, int NH, int N, const double* AH, const doub
   double* V = buf + (size_t)NH * NH;
   double* d = V + (size_t)NH * NH;
   MK_TRY(inverse_cholesky(ctx, NH, MH, Linv, S_EIG4, s));
-  MK_TRY(decompose(ctx, NH, Linv, AH, d, V, s));
+  MK_TRY(decompose(ctx, NH, Linv, false, AH, d, V, s));
   return secular(ctx, NH, N, d, V, b, c, beta, gamma, lambda, coef, status, s);
 }
 
@@ -752,7 +885,7 @@ namespace mk {
 constexpr int kStaticMaxNH = 512;
 constexpr int kStaticMaxN = 16;
 constexpr size_t kStaticG = (size_t)kStaticMaxNH * 2 * kStaticMaxN;                   // doubles: V^T [b | c]
-constexpr size_t kStaticW = (size_t)kStaticMaxN * kWorkVecs * (kStaticMaxNH + 1);     // doubles: per-orbital work
+constexpr size_t kStaticW = (size_t)kStaticMaxN * sec_stride(kStaticMaxNH);          // doubles: per-orbital work
 constexpr size_t kStaticIW = (size_t)kStaticMaxN * 4 * (kStaticMaxNH + 1);            // ints: per-orbital work
 static __device__ __align__(256) double g_static_ws[kStaticG + kStaticW + (kStaticIW + 1) / 2];
 
@@ -793,8 +926,7 @@ extern "C" int mk_small_eigensolve_static(int NH, int N, const double* d, const 
   int* IW = reinterpret_cast<int*>(ws + kStaticG + kStaticW);
   // Every workspace entry the kernels read is written first in the same call, so nothing needs clearing.
   MK_COUNT(), k_vt_bc<<<(int)(((int64_t)NH * 2 * N + 127) / 128), 128, 0, s>>>(NH, N, V, b, c, G);
-  MK_COUNT(), k_secular_select<<<N, kEigThreads, 0, s>>>(NH, N, d, V, G, beta, gamma, W, IW, lambda, coef, status,
-                                                        1e-7, 1e-12);
+  secular_launch(NH, N, d, V, G, beta, gamma, W, IW, lambda, coef, status, s);
   MK_CUDA(cudaGetLastError());
   return MK_OK;
 }

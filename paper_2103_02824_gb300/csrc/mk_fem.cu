@@ -7,12 +7,20 @@
 namespace mk {
 
 // ------------------------------------------------------------------------------------------------ reductions
+// One warp per output: lanes add the block partials lane-strided, then a fixed shuffle tree (deterministic).
 __global__ void k_sum_partials(const double* __restrict__ part, int nblk, int N, double* __restrict__ out) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (j >= N) return;
   double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * N + j];
-  out[j] = s;
+  for (int b = lane; b < nblk; b += 32) s += part[(int64_t)b * N + j];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if (lane == 0) out[j] = s;
+}
+
+void sum_partials(const double* part, int nblk, int N, double* out, cudaStream_t s) {
+  MK_COUNT(), k_sum_partials<<<(N + 7) / 8, 256, 0, s>>>(part, nblk, N, out);
 }
 
 template <typename T>
@@ -23,7 +31,7 @@ static int column_dots_t(mk_ctx* ctx, int64_t n_nodes, const T* a, const T* b, i
   double* part = (double*)scratch(ctx, S_RED, (size_t)nblk * N * sizeof(double), &err);
   if (!part) return err;
   MK_COUNT(), k_dot_partial<T><<<nblk, kRedThreads, kRedThreads * sizeof(double), s>>>(n_nodes, a, b, N, ld, part);
-  MK_COUNT(), k_sum_partials<<<(N + 63) / 64, 64, 0, s>>>(part, nblk, N, out);
+  sum_partials(part, nblk, N, out, s);
   MK_CUDA(cudaGetLastError());
   return MK_OK;
 }
@@ -37,38 +45,14 @@ int column_dots32(mk_ctx* ctx, int64_t n_nodes, const float* a, const float* b, 
   return column_dots_t<float>(ctx, n_nodes, a, b, N, ld, out, s);
 }
 
-// ------------------------------------------------------------------------------------------------ nuclei
-double* upload_nuclei(mk_ctx* ctx, const mk_molecule* mol, int* err, cudaStream_t s, int slot) {
-  const int n = mol ? mol->n_nuclei : 0;
-  double* d = (double*)scratch(ctx, slot, (size_t)(4 * n + 4) * sizeof(double), err);
-  if (!d) return nullptr;
-  if (n > 0) {
-    std::vector<double> h(4 * n);
-    for (int k = 0; k < n; ++k) {
-      h[4 * k] = mol->Z[k];
-      for (int c = 0; c < 3; ++c) h[4 * k + 1 + c] = mol->R[3 * k + c];
-    }
-    if (cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess) {
-      *err = fail(MK_ERR_CUDA, "upload_nuclei: copy failed");
-      return nullptr;
-    }
-    // pageable source: make sure the copy has consumed it before h goes out of scope
-    if (cudaStreamSynchronize(s) != cudaSuccess) {
-      *err = fail(MK_ERR_CUDA, "upload_nuclei: sync failed");
-      return nullptr;
-    }
-  }
-  return d;
-}
-
 // ------------------------------------------------------------------------------------------------ element matrices
 // out_e = half_k K_e + vext_scale M_{V_ext,e} + mass_shift M_e + M_{vq,e}, packed upper triangle, FP64.
 // K_e = |det J| sum_{i<=j} (J^-1 J^-T)_{ij} S^{ij} with the reference tensors S^{ij}; the mass-type terms by the
-// 27-point rule at the physical points x_q = x0 + J xi_q.
+// 27-point rule at the physical points x_q = x0 + J xi_q (a constant coefficient uses the exact reference mass).
 template <int NLOC>
 __global__ void k_element_matrices(int64_t E, const RefTables* __restrict__ ref, const Geom* __restrict__ geom,
-                                   int nnuc, const double* __restrict__ nuc, double half_k, double vext_scale,
-                                   double mass_shift, const double* __restrict__ vq, double* __restrict__ out) {
+                                   const NucParams nucp, double half_k, double vext_scale, double mass_shift,
+                                   const double* __restrict__ vq, double* __restrict__ out) {
   constexpr int NP = NLOC * (NLOC + 1) / 2;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
@@ -77,16 +61,16 @@ __global__ void k_element_matrices(int64_t E, const RefTables* __restrict__ ref,
   double acc[NP];
 #pragma unroll
   for (int p = 0; p < NP; ++p) acc[p] = 0.0;
-  const bool any_mass = (vext_scale != 0.0 && nnuc > 0) || mass_shift != 0.0 || vq != nullptr;
-  if (any_mass) {
+  const bool vext = vext_scale != 0.0 && nucp.n > 0;
+  if (vext || vq != nullptr) {
     for (int q = 0; q < kQ; ++q) {
       const double xi = ref->qx[q][0], et = ref->qx[q][1], ze = ref->qx[q][2];
       double c = mass_shift;
-      if (vext_scale != 0.0 && nnuc > 0) {
+      if (vext) {
         const double x = g.x0[0] + g.J[0] * xi + g.J[1] * et + g.J[2] * ze;
         const double y = g.x0[1] + g.J[3] * xi + g.J[4] * et + g.J[5] * ze;
         const double z = g.x0[2] + g.J[6] * xi + g.J[7] * et + g.J[8] * ze;
-        c += vext_scale * nuclear_potential(nuc, nnuc, x, y, z);
+        c += vext_scale * nuclear_potential(nucp, x, y, z);
       }
       if (vq) c += vq[e * kQ + q];
       c *= ref->qw[q] * det;
@@ -98,6 +82,10 @@ __global__ void k_element_matrices(int64_t E, const RefTables* __restrict__ ref,
 #pragma unroll
         for (int b = a; b < NLOC; ++b) acc[sym_index(a, b, NLOC)] += c * ph[a] * ph[b];
     }
+  } else if (mass_shift != 0.0) {
+    const double f = mass_shift * det;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) acc[p] = f * ref->mass[p];
   }
   if (half_k != 0.0) {
     const double* Ji = g.Jinv;
@@ -118,19 +106,17 @@ __global__ void k_element_matrices(int64_t E, const RefTables* __restrict__ ref,
 }
 
 int element_matrices(mk_ctx* ctx, const Level& L, const mk_molecule* mol, double half_k, double vext_scale,
-                     double mass_shift, const double* vq, double* out, cudaStream_t s, int nuc_slot) {
-  int err = MK_OK;
-  double* nuc = upload_nuclei(ctx, mol, &err, s, nuc_slot);
-  if (!nuc) return err;
-  const int nnuc = mol ? mol->n_nuclei : 0;
+                     double mass_shift, const double* vq, double* out, cudaStream_t s) {
+  MK_ARG(!mol || mol->n_nuclei <= kMaxNuclei, "at most 64 nuclei are supported");
+  const NucParams nucp = make_nuc(mol);
   const int th = 128;
   const int blocks = (int)((L.n_elems + th - 1) / th);
   if (L.nloc == 4)
-    MK_COUNT(), k_element_matrices<4><<<blocks, th, 0, s>>>(L.n_elems, ctx->d_ref[1], L.d_geom, nnuc, nuc, half_k, vext_scale,
-                                                mass_shift, vq, out);
+    MK_COUNT(), k_element_matrices<4><<<blocks, th, 0, s>>>(L.n_elems, ctx->d_ref[1], L.d_geom, nucp, half_k,
+                                                            vext_scale, mass_shift, vq, out);
   else
-    MK_COUNT(), k_element_matrices<10><<<blocks, th, 0, s>>>(L.n_elems, ctx->d_ref[2], L.d_geom, nnuc, nuc, half_k, vext_scale,
-                                                 mass_shift, vq, out);
+    MK_COUNT(), k_element_matrices<10><<<blocks, th, 0, s>>>(L.n_elems, ctx->d_ref[2], L.d_geom, nucp, half_k,
+                                                             vext_scale, mass_shift, vq, out);
   MK_CUDA(cudaGetLastError());
   return MK_OK;
 }
@@ -254,7 +240,7 @@ int prolongate(mk_ctx* ctx, const mk_mesh* m, const double* psiH, int ldc, int N
 // rho[e*Q+q] = sum_j occ[j] u_j(x_q)^2
 template <int NLOC>
 __global__ void k_density(int64_t E, const RefTables* __restrict__ ref, const int32_t* __restrict__ elem,
-                          const double* __restrict__ u, int ld, int N, const double* __restrict__ occ,
+                          const double* __restrict__ u, int ld, int N, const ColParams occ,
                           double* __restrict__ rho) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
@@ -268,7 +254,7 @@ __global__ void k_density(int64_t E, const RefTables* __restrict__ ref, const in
     double ua[NLOC];
 #pragma unroll
     for (int a = 0; a < NLOC; ++a) ua[a] = u[(int64_t)nd[a] * ld + j];
-    const double f = occ[j];
+    const double f = occ.v[j];
 #pragma unroll
     for (int q = 0; q < kQ; ++q) {
       double v = 0.0;
@@ -323,11 +309,8 @@ __global__ void k_frozen_potential(int64_t E, const RefTables* __restrict__ ref,
 
 int density(mk_ctx* ctx, const Level& L, const double* u, int ld, int N, const double* occ_host, double* rho,
             cudaStream_t s) {
-  int err = MK_OK;
-  double* occ = (double*)scratch(ctx, S_OCC, (size_t)(N + 1) * sizeof(double), &err);
-  if (!occ) return err;
-  MK_CUDA(cudaMemcpyAsync(occ, occ_host, N * sizeof(double), cudaMemcpyHostToDevice, s));
-  MK_CUDA(cudaStreamSynchronize(s));
+  ColParams occ{};
+  for (int j = 0; j < N && j < MK_MAX_RHS; ++j) occ.v[j] = occ_host[j];
   const int th = 128, blocks = (int)((L.n_elems + th - 1) / th);
   if (L.nloc == 4)
     MK_COUNT(), k_density<4><<<blocks, th, 0, s>>>(L.n_elems, ctx->d_ref[1], L.d_elem, u, ld, N, occ, rho);
@@ -445,7 +428,7 @@ int multipole_boundary(mk_ctx* ctx, const Level& L, const double* rho, const dou
   double* mom = (double*)scratch(ctx, S_SCAL, 64 * sizeof(double), &err);
   if (!part || !mom) return err;
   MK_COUNT(), k_moments<<<nblk, kRedThreads, 0, s>>>(L.n_elems, ctx->d_ref[L.order], L.d_geom, rho, part);
-  MK_COUNT(), k_sum_partials<<<1, 64, 0, s>>>(part, nblk, 10, mom);
+  sum_partials(part, nblk, 10, mom, s);
   MK_COUNT(), k_multipole_bc<<<(int)((L.n_nodes + 255) / 256), 256, 0, s>>>(L.n_nodes, d_nodes, L.d_boundary, mom,
                                                                  bc == MK_BC_MULTIPOLE, w);
   MK_CUDA(cudaGetLastError());

@@ -1,6 +1,7 @@
 // Host side of the mk library: errors, context, scratch, reference-element tables and mesh preprocessing (A0).
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 
@@ -143,8 +144,49 @@ void build_ref_tables(int order, RefTables* t) {
 }
 
 // ------------------------------------------------------------------------------------------------ profiling
+void prof_capture(mk_ctx* ctx, bool on) {
+  ctx->capturing = on;
+  if (on)
+    for (int k = 0; k < 4; ++k) {
+      ctx->cap_state[k] = 0;
+      ctx->gev_valid[k] = false;
+    }
+}
+
+// Events used to time applications inside a graph; created before any capture starts.
+void prof_prepare_capture(mk_ctx* ctx) {
+  if (!ctx->prof_on) return;
+  for (auto& pr : ctx->gev)
+    for (cudaEvent_t& e : pr)
+      if (!e) cudaEventCreate(&e);
+}
+
+void prof_harvest(mk_ctx* ctx) {
+  if (!ctx->prof_on) return;
+  for (int k = 0; k < 4; ++k) {
+    if (!ctx->gev_valid[k]) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->gev[k][0], ctx->gev[k][1]) == cudaSuccess) {
+      ctx->acc_ms[k] += ms;
+      ctx->acc_n[k] += 1;
+    } else {
+      cudaGetLastError();
+    }
+  }
+}
+
 void prof_mark(mk_ctx* ctx, int kind, bool begin, cudaStream_t s) {
   if (!ctx->prof_on) return;
+  if (ctx->capturing) {
+    int& st = ctx->cap_state[kind];
+    if ((begin && st != 0) || (!begin && st != 1)) return;
+    cudaEvent_t& e = ctx->gev[kind][begin ? 0 : 1];
+    if (!e) return;
+    cudaEventRecord(e, s);
+    st = begin ? 1 : 2;
+    if (!begin) ctx->gev_valid[kind] = true;
+    return;
+  }
   auto& ev = ctx->prof_ev[kind];
   int& used = ctx->prof_used[kind];
   const size_t idx = 2 * (size_t)used + (begin ? 0 : 1);
@@ -413,7 +455,11 @@ long long mk_launch_count(void) { return g_launch_count.load(std::memory_order_r
 int mk_profile_enable(mk_ctx* ctx, int on) {
   MK_ARG(ctx, "mk_profile_enable: null ctx");
   ctx->prof_on = on != 0;
-  for (int k = 0; k < 4; ++k) ctx->prof_used[k] = 0;
+  for (int k = 0; k < 4; ++k) {
+    ctx->prof_used[k] = 0;
+    ctx->acc_ms[k] = 0.0;
+    ctx->acc_n[k] = 0;
+  }
   return MK_OK;
 }
 
@@ -426,8 +472,8 @@ int mk_profile_read(mk_ctx* ctx, int kind, double* total_ms, long long* count) {
     MK_CUDA(cudaEventElapsedTime(&ms, ctx->prof_ev[kind][2 * i], ctx->prof_ev[kind][2 * i + 1]));
     t += ms;
   }
-  *total_ms = t;
-  *count = ctx->prof_used[kind];
+  *total_ms = t + ctx->acc_ms[kind];
+  *count = ctx->prof_used[kind] + ctx->acc_n[kind];
   return MK_OK;
 }
 
@@ -441,6 +487,10 @@ int mk_ctx_create(mk_ctx** out, int device) {
   mk_ctx* c = new mk_ctx();
   c->device = device;
   MK_CUDA(cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, device));
+  const char* ng = std::getenv("MK_NO_GRAPHS");
+  c->no_graphs = ng && ng[0] == '1';
+  MK_CUDA(cudaStreamCreateWithFlags(&c->solve_stream, cudaStreamNonBlocking));
+  for (cudaEvent_t& e : c->solve_ev) MK_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   for (int order = 1; order <= 2; ++order) {
     build_ref_tables(order, &c->h_ref[order]);
     MK_TRY(upload(&c->d_ref[order], &c->h_ref[order], 1));
@@ -457,6 +507,12 @@ int mk_ctx_destroy(mk_ctx* c) {
   if (c->pinned) cudaFreeHost(c->pinned);
   for (auto& v : c->prof_ev)
     for (cudaEvent_t e : v) cudaEventDestroy(e);
+  for (auto& pr : c->gev)
+    for (cudaEvent_t e : pr)
+      if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->solve_ev)
+    if (e) cudaEventDestroy(e);
+  if (c->solve_stream) cudaStreamDestroy(c->solve_stream);
   delete c;
   return MK_OK;
 }

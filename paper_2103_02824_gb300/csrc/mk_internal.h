@@ -125,11 +125,27 @@ struct mk_ctx {
   bool prof_on = false;
   std::vector<cudaEvent_t> prof_ev[4];
   int prof_used[4] = {0, 0, 0, 0};
+  // inside a CUDA-graph capture only the first application of each kind is timed, with one event pair that
+  // every replay re-records; prof_harvest adds it after each replay
+  bool capturing = false;
+  int cap_state[4] = {0, 0, 0, 0};
+  bool gev_valid[4] = {false, false, false, false};
+  cudaEvent_t gev[4][2] = {};
+  double acc_ms[4] = {0, 0, 0, 0};
+  long long acc_n[4] = {0, 0, 0, 0};
+  bool no_graphs = false;  // environment MK_NO_GRAPHS=1 disables graph replay of the inner PCG iterations
+  // the inner PCG runs on this stream (graphs cannot be captured on the legacy default stream), ordered against
+  // the caller's stream by two events
+  cudaStream_t solve_stream = nullptr;
+  cudaEvent_t solve_ev[2] = {nullptr, nullptr};
 };
 
 namespace mk {
 // Record a start (begin=true) or stop event for profiled operation `kind` on stream s (no-op unless enabled).
 void prof_mark(mk_ctx* ctx, int kind, bool begin, cudaStream_t s);
+void prof_capture(mk_ctx* ctx, bool on);
+void prof_prepare_capture(mk_ctx* ctx);
+void prof_harvest(mk_ctx* ctx);
 enum ProfKind { PROF_APPLY64 = 0, PROF_APPLY32 = 1, PROF_HALO = 2, PROF_OTHER = 3 };
 }  // namespace mk
 

@@ -354,13 +354,26 @@ __global__ void k_zero_boundary(int64_t n, const uint8_t* __restrict__ bnd, doub
 // mode 1: inner init (rz, rr) -> rz, rr0, rr, active (outer_active), iters=0
 // mode 2: alpha from pq
 // mode 3: beta from (rz_new, rr) and convergence of the inner solve
-__global__ void k_mixed_finalize(int mode, const double* __restrict__ part, int nblk, int NS, int ld, int N,
-                                 MixState* __restrict__ st, double rtol, double inner_rtol2) {
+// Launched with kFinThreads threads: one warp per (sum, column) pair adds the block partials lane-strided and
+// folds them with a fixed shuffle tree (deterministic), then one thread per column updates its state.
+constexpr int kFinThreads = 1024;
+__global__ void __launch_bounds__(kFinThreads) k_mixed_finalize(int mode, const double* __restrict__ part, int nblk,
+                                                               int NS, int ld, int N, MixState* __restrict__ st,
+                                                               double rtol, double inner_rtol2) {
+  __shared__ double sums[2 * 256];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int pr = warp; pr < NS * ld; pr += nw) {
+    const int k = pr / ld, jj = pr - k * ld;
+    double v = 0.0;
+    for (int b = lane; b < nblk; b += 32) v += part[(int64_t)b * NS * ld + k * ld + jj];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) sums[k * ld + jj] = v;
+  }
+  __syncthreads();
   const int j = threadIdx.x;
   if (j >= ld) return;
-  double s[2] = {0.0, 0.0};
-  for (int b = 0; b < nblk; ++b)
-    for (int k = 0; k < NS; ++k) s[k] += part[(int64_t)b * NS * ld + k * ld + j];
+  double s[2] = {sums[j], NS > 1 ? sums[ld + j] : 0.0};
   MixState c = st[j];
   if (mode == 0) {
     c.bn = s[0] > 0 ? sqrt(s[0]) : 1.0;
@@ -400,16 +413,46 @@ __global__ void k_mixed_finalize(int mode, const double* __restrict__ part, int 
   st[j] = c;
 }
 
+int pcg_mixed(mk_ctx* ctx, const mk_mesh* m, const double* A64, const double* b, double* x, int ld, int N,
+              const mk_solve_opts& o, mk_solve_report* rep, cudaStream_t s);
+
 int solve_mixed(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, double sigma, const double* b,
                 const double*, const double*, double* x, int ld, int N, const mk_solve_opts& o, mk_solve_report* rep,
                 cudaStream_t s) {
   if (o.precond != MK_PRECOND_JACOBI) return fail(MK_ERR_UNSUPPORTED, "mixed path: only Jacobi is built");
+  const Level& L = m->fine;
+  const int np = L.nloc * (L.nloc + 1) / 2;
+  int err = MK_OK;
+  double* A64 = (double*)scratch(ctx, S_ELEM64, (size_t)L.n_elems * np * sizeof(double), &err);
+  if (!A64) return err;
+  MK_TRY(element_matrices(ctx, L, mol, 0.5, 1.0, sigma, nullptr, A64, s));
+  return pcg_mixed(ctx, m, A64, b, x, ld, N, o, rep, s);
+}
+
+// FP32 inner Jacobi-PCG on the patch operator built from the FP64 element matrices A64 (element order), FP64
+// residual b - A x and iterative refinement of x until every column meets o.rtol.
+static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const double* b, double* x, int ld, int N,
+                        const mk_solve_opts& o, mk_solve_report* rep, cudaStream_t s);
+
+// Runs the solve on the context's own stream (CUDA graphs cannot be captured on the legacy default stream), after
+// everything already queued on the caller's stream and before anything queued there afterwards.
+int pcg_mixed(mk_ctx* ctx, const mk_mesh* m, const double* A64, const double* b, double* x, int ld, int N,
+              const mk_solve_opts& o, mk_solve_report* rep, cudaStream_t caller) {
+  MK_CUDA(cudaEventRecord(ctx->solve_ev[0], caller));
+  MK_CUDA(cudaStreamWaitEvent(ctx->solve_stream, ctx->solve_ev[0], 0));
+  const int r = pcg_mixed_on(ctx, m, A64, b, x, ld, N, o, rep, ctx->solve_stream);
+  MK_CUDA(cudaEventRecord(ctx->solve_ev[1], ctx->solve_stream));
+  MK_CUDA(cudaStreamWaitEvent(caller, ctx->solve_ev[1], 0));
+  return r;
+}
+
+static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const double* b, double* x, int ld, int N,
+                        const mk_solve_opts& o, mk_solve_report* rep, cudaStream_t s) {
   MK_ARG(ld <= 256, "mixed path: ld must be <= 256");
   const Level& L = m->fine;
   const int64_t n = L.n_nodes;
   const int np = L.nloc * (L.nloc + 1) / 2;
   int err = MK_OK;
-  double* A64 = (double*)scratch(ctx, S_ELEM64, (size_t)L.n_elems * np * sizeof(double), &err);
   float* A32 = (float*)scratch(ctx, S_ELEM32, (size_t)L.n_elems * np * sizeof(float), &err);
   double* diag = (double*)scratch(ctx, S_DIAG64, n * sizeof(double), &err);
   float* dinv = (float*)scratch(ctx, S_DIAG32, n * sizeof(float), &err);
@@ -421,14 +464,13 @@ int solve_mixed(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, double si
   const int nblk = red_blocks(ctx);
   double* part = (double*)scratch(ctx, S_RED, (size_t)nblk * 2 * ld * sizeof(double), &err);
   MixState* st = (MixState*)scratch(ctx, S_SCAL, 256 * sizeof(MixState), &err);
-  if (!A64 || !A32 || !diag || !dinv || !Ax || !r || !p || !q || !d || !part || !st) return err;
+  if (!A32 || !diag || !dinv || !Ax || !r || !p || !q || !d || !part || !st) return err;
   if (ctx->pinned_size < 256 * sizeof(MixState)) {
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
     MK_CUDA(cudaMallocHost(&ctx->pinned, 256 * sizeof(MixState)));
     ctx->pinned_size = 256 * sizeof(MixState);
   }
   MixState* hst = (MixState*)ctx->pinned;
-  MK_TRY(element_matrices(ctx, L, mol, 0.5, 1.0, sigma, nullptr, A64, s));
   MK_TRY(assemble_diagonal(ctx, L, A64, diag, s));
   MK_TRY(pack_elements<float>(ctx, m, A64, A32, s));
   MK_COUNT(), k_dinv32<<<(int)((n + 255) / 256), 256, 0, s>>>(n, diag, dinv);
@@ -441,10 +483,16 @@ int solve_mixed(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, double si
   int total_it = 0, refine = 0, status = MK_OK;
   bool converged = false;
   const int max_refine = o.max_refine > 0 ? o.max_refine : 20;
+  cudaGraphExec_t exec = nullptr;
+  long long graph_kernels = 0;
+  const bool use_graph = !ctx->no_graphs;
+  // the operator's halo buffer must exist before a capture starts (nothing may allocate inside a capture)
+  if (!scratch(ctx, S_HALO, (size_t)std::max<int64_t>(m->patches.n_halo_slots, 1) * ld * sizeof(float), &err))
+    return err;
   for (;;) {
     MK_TRY(apply64(ctx, L, A64, x, Ax, ld, ld, true, s));   // FP64 residual of the current x
     MK_COUNT(), k_mixed_residual<<<nblk, th, 0, s>>>(n, L.d_boundary, b, Ax, r, d, N, ld, part);
-    MK_COUNT(), k_mixed_finalize<<<1, ld, 0, s>>>(0, part, nblk, 2, ld, N, st, o.rtol, inner2);
+    MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(0, part, nblk, 2, ld, N, st, o.rtol, inner2);
     MK_CUDA(cudaMemcpyAsync(hst, st, sizeof(MixState) * ld, cudaMemcpyDeviceToHost, s));
     MK_CUDA(cudaStreamSynchronize(s));
     bool any = false;
@@ -453,32 +501,62 @@ int solve_mixed(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, double si
     if (refine >= max_refine || total_it >= o.maxit) break;
     ++refine;
     MK_COUNT(), k_mixed_init<<<nblk, th, 0, s>>>(n, dinv, r, p, ld, part);
-    MK_COUNT(), k_mixed_finalize<<<1, ld, 0, s>>>(1, part, nblk, 2, ld, N, st, o.rtol, inner2);
+    MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(1, part, nblk, 2, ld, N, st, o.rtol, inner2);
     int it = 0;
     bool inner_active = true;
-    while (inner_active && total_it < o.maxit) {
+    // one PCG iteration; every scalar it needs lives on the device, so `check` of them can be replayed as a graph
+    auto iteration = [&]() -> int {
       MK_TRY(apply_patch<float>(ctx, m, A32, p, q, ld, true, s));
       MK_COUNT(), k_mixed_pq<<<nblk, th, 0, s>>>(n, p, q, ld, part);
-      MK_COUNT(), k_mixed_finalize<<<1, ld, 0, s>>>(2, part, nblk, 1, ld, N, st, o.rtol, inner2);
+      MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(2, part, nblk, 1, ld, N, st, o.rtol, inner2);
       MK_COUNT(), k_mixed_update<<<nblk, th, 0, s>>>(n, st, dinv, p, q, d, r, ld, part);
-      MK_COUNT(), k_mixed_finalize<<<1, ld, 0, s>>>(3, part, nblk, 2, ld, N, st, o.rtol, inner2);
+      MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(3, part, nblk, 2, ld, N, st, o.rtol, inner2);
       MK_COUNT(), k_mixed_p<<<gb, 256, 0, s>>>(n, st, dinv, r, p, ld);
-      ++it;
-      ++total_it;
-      if (it % check == 0) {
-        MK_CUDA(cudaMemcpyAsync(hst, st, sizeof(MixState) * ld, cudaMemcpyDeviceToHost, s));
-        MK_CUDA(cudaStreamSynchronize(s));
-        inner_active = false;
-        for (int j = 0; j < N; ++j) {
-          inner_active |= hst[j].active != 0;
-          if (hst[j].breakdown) status = MK_ERR_BREAKDOWN;
+      return MK_OK;
+    };
+    while (inner_active && total_it < o.maxit) {
+      const int k = std::min(check, o.maxit - total_it);
+      // with profiling on, the first chunk of every inner solve runs eagerly so each operator application is
+      // timed by its own event pair on this stream
+      if (use_graph && k == check && !(ctx->prof_on && it == 0)) {
+        if (!exec) {
+          const long long c0 = g_launch_count.load();
+          prof_prepare_capture(ctx);
+          MK_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+          prof_capture(ctx, true);
+          int rc = MK_OK;
+          for (int c = 0; c < check && rc == MK_OK; ++c) rc = iteration();
+          prof_capture(ctx, false);
+          cudaGraph_t graph = nullptr;
+          const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+          if (rc != MK_OK) return rc;
+          if (ce != cudaSuccess) return fail(MK_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+          MK_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+          cudaGraphDestroy(graph);
+          graph_kernels = g_launch_count.load() - c0;
+          g_launch_count.fetch_sub(graph_kernels);   // counted when replayed, below
         }
-        if (status == MK_ERR_BREAKDOWN) break;
+        MK_CUDA(cudaGraphLaunch(exec, s));
+        g_launch_count.fetch_add(graph_kernels);
+      } else {
+        for (int c = 0; c < k; ++c) MK_TRY(iteration());
       }
+      it += k;
+      total_it += k;
+      MK_CUDA(cudaMemcpyAsync(hst, st, sizeof(MixState) * ld, cudaMemcpyDeviceToHost, s));
+      MK_CUDA(cudaStreamSynchronize(s));
+      prof_harvest(ctx);
+      inner_active = false;
+      for (int j = 0; j < N; ++j) {
+        inner_active |= hst[j].active != 0;
+        if (hst[j].breakdown) status = MK_ERR_BREAKDOWN;
+      }
+      if (status == MK_ERR_BREAKDOWN) break;
     }
     MK_COUNT(), k_mixed_add<<<gb, 256, 0, s>>>(n, d, x, N, ld);
     if (status == MK_ERR_BREAKDOWN) break;
   }
+  if (exec) cudaGraphExecDestroy(exec);
   MK_CUDA(cudaGetLastError());
   MK_CUDA(cudaMemcpyAsync(hst, st, sizeof(MixState) * ld, cudaMemcpyDeviceToHost, s));
   MK_CUDA(cudaStreamSynchronize(s));

@@ -147,7 +147,7 @@ int gram(mk_ctx* ctx, int64_t n, const double* X, const double* Y, int N, int ld
   double* part = (double*)scratch(ctx, S_RED, (size_t)nblk * N * N * sizeof(double), &err);
   if (!part) return err;
   MK_COUNT(), k_gram_partial<<<nblk, kRedThreads, kRedThreads * sizeof(double), s>>>(n, X, Y, N, ld, part);
-  MK_COUNT(), k_sum_partials<<<(N * N + 63) / 64, 64, 0, s>>>(part, nblk, N * N, G);
+  sum_partials(part, nblk, N * N, G, s);
   MK_CUDA(cudaGetLastError());
   return MK_OK;
 }
@@ -202,8 +202,8 @@ extern "C" int mk_coarse_pencil(mk_ctx* ctx, const mk_mesh* m, const mk_molecule
   double* He = (double*)scratch(ctx, S_ELEM64C, eb, &err);
   double* Me = (double*)scratch(ctx, S_ELEM64D, eb, &err);
   if (!He || !Me) return err;
-  MK_TRY(element_matrices(ctx, F, mol, 0.5, 1.0, 0.0, vq, He, s, S_NUC2));
-  MK_TRY(element_matrices(ctx, F, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s, S_NUC2));
+  MK_TRY(element_matrices(ctx, F, mol, 0.5, 1.0, 0.0, vq, He, s));
+  MK_TRY(element_matrices(ctx, F, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s));
   return coarse_matrices(ctx, m, He, Me, AH, MH, S_COARSE2, s);
 }
 

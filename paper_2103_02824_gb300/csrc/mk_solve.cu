@@ -16,6 +16,8 @@ int load_vector(mk_ctx*, const Level&, const double*, double, double*, cudaStrea
 int multipole_boundary(mk_ctx*, const Level&, const double*, const double*, int, double*, cudaStream_t);
 int solve_mixed(mk_ctx*, const mk_mesh*, const mk_molecule*, double, const double*, const double*, const double*,
                 double*, int, int, const mk_solve_opts&, mk_solve_report*, cudaStream_t);
+int pcg_mixed(mk_ctx*, const mk_mesh*, const double*, const double*, double*, int, int, const mk_solve_opts&,
+              mk_solve_report*, cudaStream_t);
 
 // Per-column PCG state on the device.
 struct ColState {
@@ -203,13 +205,13 @@ static bool valid_opts(const mk_solve_opts* o) {
 }
 
 __global__ void k_combine_rhs(int64_t n, const uint8_t* __restrict__ bnd, const double* __restrict__ Mu,
-                              const double* __restrict__ Vu, const double* __restrict__ coef, double* __restrict__ rhs,
+                              const double* __restrict__ Vu, const ColParams coef, double* __restrict__ rhs,
                               int N, int ld) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * ld) return;
   const int64_t nd = t / ld;
   const int j = (int)(t % ld);
-  rhs[t] = (j < N && !bnd[nd]) ? coef[j] * Mu[t] - Vu[t] : 0.0;
+  rhs[t] = (j < N && !bnd[nd]) ? coef.v[j] * Mu[t] - Vu[t] : 0.0;
 }
 
 __global__ void k_axpy_interior(int64_t n, const uint8_t* __restrict__ bnd, const double* __restrict__ d,
@@ -279,13 +281,12 @@ int mk_hartree_poisson(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, c
   MK_TRY(element_matrices(ctx, L, nullptr, 1.0, 0.0, 0.0, nullptr, Ke, s));
   MK_TRY(assemble_diagonal(ctx, L, Ke, diag, s));
   MK_TRY(apply64(ctx, L, Ke, w, y, 1, 1, true, s));                     // K_IB g (interior rows)
-  double one = 1.0;
-  double* coef = (double*)scratch(ctx, S_COEF, 64 * sizeof(double), &err);
-  if (!coef) return err;
-  MK_CUDA(cudaMemcpyAsync(coef, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+  ColParams coef{};
+  coef.v[0] = 1.0;
   MK_COUNT(), k_combine_rhs<<<(int)((L.n_nodes + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, F, y, coef, F, 1, 1);
   MK_CUDA(cudaMemsetAsync(d, 0, L.n_nodes * sizeof(double), s));
-  int r = pcg64(ctx, L, Ke, diag, F, d, 1, 1, *opts, report, s);
+  int r = opts->precision == MK_PREC_MIXED ? pcg_mixed(ctx, m, Ke, F, d, 1, 1, *opts, report, s)
+                                           : pcg64(ctx, L, Ke, diag, F, d, 1, 1, *opts, report, s);
   MK_COUNT(), k_axpy_interior<<<(int)((L.n_nodes + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, d, w);
   MK_CUDA(cudaGetLastError());
   MK_CUDA(cudaStreamSynchronize(s));
@@ -308,18 +309,15 @@ int mk_assemble_rhs(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, cons
   double* Ve = (double*)scratch(ctx, S_ELEM64, eb, &err);
   double* Mu = (double*)scratch(ctx, S_VEC1, (size_t)L.n_nodes * ld * sizeof(double), &err);
   double* Vu = (double*)scratch(ctx, S_VEC2, (size_t)L.n_nodes * ld * sizeof(double), &err);
-  double* coef = (double*)scratch(ctx, S_COEF, 64 * sizeof(double), &err);
-  if (!rho || !Me || !Ve || !Mu || !Vu || !coef) return err;
+  if (!rho || !Me || !Ve || !Mu || !Vu) return err;
   MK_TRY(density(ctx, L, u, ld, N, occ, rho, s));
   MK_TRY(frozen_potential(ctx, L, w, rho, xc, vq, s));
   MK_TRY(element_matrices(ctx, L, nullptr, 0.0, 0.0, 0.0, vq, Ve, s));
   MK_TRY(element_matrices(ctx, L, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s));
   MK_TRY(apply64(ctx, L, Me, u, Mu, N, ld, true, s));
   MK_TRY(apply64(ctx, L, Ve, u, Vu, N, ld, true, s));
-  double h[MK_MAX_RHS];
-  for (int j = 0; j < N; ++j) h[j] = lambdaH[j] + sigma;
-  MK_CUDA(cudaMemcpyAsync(coef, h, N * sizeof(double), cudaMemcpyHostToDevice, s));
-  MK_CUDA(cudaStreamSynchronize(s));
+  ColParams coef{};
+  for (int j = 0; j < N; ++j) coef.v[j] = lambdaH[j] + sigma;
   MK_COUNT(), k_combine_rhs<<<(int)((L.n_nodes * ld + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, Mu, Vu, coef, rhs, N, ld);
   MK_CUDA(cudaGetLastError());
   return MK_OK;

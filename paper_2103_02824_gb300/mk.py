@@ -99,6 +99,7 @@ _SIGS = {
     "mk_coarse_pencil": [_vp, _vp, C.POINTER(mk_molecule), _vp, _vp, _vp, _vp],
     "mk_operator_apply": [_vp, _vp, C.POINTER(mk_molecule), C.c_double, C.c_int, _vp, _vp, C.c_int, _vp],
     "mk_coarse_decompose": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "mk_coarse_decompose_warm": [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp],
     "mk_small_eigensolve_shared": [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "mk_small_eigensolve_static": [C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "mk_orbital_assemble": [_vp, _vp, _vp, _vp, _vp, C.c_int, C.c_int, _vp, _vp],
@@ -323,6 +324,10 @@ def mk_coarse_pencil(ctx, mesh, mol: Molecule, vq, AH, MH, stream=None):
 
 def mk_coarse_decompose(ctx, mesh, AH, d, V, stream=None):
     _check(lib().mk_coarse_decompose(ctx.h, mesh.h, _ptr(AH), _ptr(d), _ptr(V), _stream(stream)))
+
+
+def mk_coarse_decompose_warm(ctx, NH, AH, V0, d, V, stream=None):
+    _check(lib().mk_coarse_decompose_warm(ctx.h, NH, _ptr(AH), _ptr(V0), _ptr(d), _ptr(V), _stream(stream)))
 
 
 def mk_small_eigensolve_shared(ctx, NH, N, d, V, b, c, beta, gamma, lam, coef, status, stream=None):

@@ -12,9 +12,18 @@ from . import mk
 
 
 class CorrectionStep:
-    def __init__(self, ctx: "mk.Context", mesh: "mk.Mesh", Z, R, N: int, ld: int | None = None):
+    def __init__(self, ctx: "mk.Context", mesh: "mk.Mesh", Z, R, N: int, ld: int | None = None,
+                 overlap: bool = True, basis=None):
+        """basis: optional M_H-orthonormal device matrix [N_H, N_H] (eigenvectors of the density-independent
+        coarse pencil) from which the coarse decomposition is warm-started."""
         import torch
         self.ctx, self.mesh, self.N = ctx, mesh, N
+        self.overlap = overlap
+        self.basis = basis
+        if overlap:
+            self._side = torch.cuda.Stream()
+            self._ev_rhs = torch.cuda.Event()
+            self._ev_dec = torch.cuda.Event()
         self.ld = ld or max(4, (N + 3) // 4 * 4)
         self.mol = mk.Molecule(Z, R)
         info = mesh.info
@@ -43,6 +52,12 @@ class CorrectionStep:
         self.psi = torch.zeros((n, self.ld), **f64)
         self.psiH = torch.zeros((NH, self.ld), **f64)
 
+    def _decompose(self, stream):
+        if self.basis is not None:
+            mk.mk_coarse_decompose_warm(self.ctx, self.NH, self.AH, self.basis, self.d, self.V, stream=stream)
+        else:
+            mk.mk_coarse_decompose(self.ctx, self.mesh, self.AH, self.d, self.V, stream=stream)
+
     def run(self, psiH, lamH, occ, sigma, xc="lda", hartree_bc="multipole", solve_opts=None, poisson_opts=None,
             stream=None):
         """psiH: torch [N_H, >=N] (device) or numpy [N_H, N]; lamH, occ: numpy [N].  Returns reports."""
@@ -62,22 +77,35 @@ class CorrectionStep:
             reps["poisson"] = mk.mk_hartree_poisson(ctx, mesh, self.u, occ, N, self.w, bc=hartree_bc,
                                                     opt=poisson_opts, stream=stream)
         mk.mk_assemble_rhs(ctx, mesh, self.u, lamH, occ, N, self.w, sigma, xc, self.rhs, self.vq, stream=stream)
+        main = torch.cuda.current_stream() if stream is None else torch.cuda.ExternalStream(stream)
+        if self.overlap:
+            # the coarse pencil and its decomposition need only vq, not psi^: run them beside the fine solve
+            self._ev_rhs.record(main)
+            self._side.wait_event(self._ev_rhs)
+            mk.mk_coarse_pencil(ctx, mesh, self.mol, self.vq, self.AH, self.MH, stream=self._side.cuda_stream)
+            self._decompose(self._side.cuda_stream)
+            self._ev_dec.record(self._side)
         self.psihat.copy_(self.u)
         reps["solve"] = mk.mk_correction_solve(ctx, mesh, self.mol, sigma, self.rhs, self.psihat, N,
                                                opt=solve_opts, stream=stream)
-        mk.mk_coarse_pencil(ctx, mesh, self.mol, self.vq, self.AH, self.MH, stream=stream)
-        mk.mk_coarse_decompose(ctx, mesh, self.AH, self.d, self.V, stream=stream)
+        if not self.overlap:
+            mk.mk_coarse_pencil(ctx, mesh, self.mol, self.vq, self.AH, self.MH, stream=stream)
+            self._decompose(stream)
         mk.mk_augmented_project(ctx, mesh, self.mol, self.vq, self.psihat, N, None, None, self.b, self.c,
                                 self.beta, self.gamma, self.gramA, self.gramM, stream=stream)
+        if self.overlap:
+            main.wait_event(self._ev_dec)
         mk.mk_small_eigensolve_shared(ctx, self.NH, N, self.d, self.V, self.b, self.c, self.beta, self.gamma,
                                       self.lam, self.coef, self.status, stream=stream)
         mk.mk_orbital_assemble(ctx, mesh, self.coef, self.psihat, self.u, N, self.psi, stream=stream)
         return reps
 
 
-def coarse_eigenpairs(ctx, mesh, Z, R, N):
+def coarse_eigenpairs(ctx, mesh, Z, R, N, return_basis=False):
     """Lowest N eigenpairs of the bare coarse Hamiltonian P^T (K/2 + M_Vext) P in V_H, the frozen-potential version
-    of Algorithm 1, step 1 (the initial solve on the coarse space), on the GPU.  Returns numpy (psiH, lamH)."""
+    of Algorithm 1, step 1 (the initial solve on the coarse space), on the GPU.  Returns numpy (psiH, lamH), and
+    with return_basis also the full M_H-orthonormal eigenbasis as a device tensor (a warm start for the step's
+    coarse decomposition)."""
     import torch
     mol = mk.Molecule(Z, R)
     NH = mesh.info["n_free_coarse"]
@@ -87,7 +115,8 @@ def coarse_eigenpairs(ctx, mesh, Z, R, N):
     mk.mk_coarse_pencil(ctx, mesh, mol, None, AH, MH)
     mk.mk_coarse_decompose(ctx, mesh, AH, d, V)
     torch.cuda.synchronize()
-    return V[:, :N].cpu().numpy().copy(), d[:N].cpu().numpy().copy()
+    out = (V[:, :N].cpu().numpy().copy(), d[:N].cpu().numpy().copy())
+    return out + (V,) if return_basis else out
 
 
 def upload_workload(ctx, wl):

@@ -85,15 +85,17 @@ def test_prolongate(ctx, torch, name):
     assert np.all(got[:, N:] == 0)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("name", CASES)
-def test_hartree_poisson(ctx, torch, name):
+def test_hartree_poisson(ctx, torch, name, precision):
     from paper_2103_02824_gb300 import mk
     c = case(name)
     m = gpu_mesh(ctx, name)
     N, ld = c["N"], 8
     u = dev(torch, padded(c["out"]["u"], ld))
     w = torch.zeros(m.info["n_nodes"], dtype=torch.float64, device="cuda")
-    rep = mk.mk_hartree_poisson(ctx, m, u, c["occ"], N, w, bc="multipole", opt=mk.opts(rtol=1e-13))
+    rep = mk.mk_hartree_poisson(ctx, m, u, c["occ"], N, w, bc="multipole",
+                                opt=mk.opts(precision=precision, rtol=1e-13, check_every=5))
     ref = c["out"]["w"]
     assert rep["max_rel_residual"] <= 1e-13
     assert rel(w.cpu().numpy(), ref) < 1e-10
@@ -252,6 +254,27 @@ def test_coarse_pencil_and_decompose(ctx, torch, name):
     assert np.abs(coef.cpu().numpy() - o["coef"]).max() < 1e-8 * np.abs(o["coef"]).max()
 
 
+@pytest.mark.parametrize("name", CASES)
+def test_coarse_decompose_warm(ctx, torch, name):
+    """Warm start from the eigenbasis of the density-independent pencil gives the same decomposition."""
+    import scipy.linalg as sla
+    from paper_2103_02824_gb300 import mk
+    c = case(name)
+    o, lv = c["out"], c["level"]
+    NH = o["AH"].shape[0]
+    A0 = (lv.Pf.T @ ((0.5 * lv.Kff + lv.MVff) @ lv.Pf)).toarray()
+    _, V0 = sla.eigh(A0, o["MH"])
+    d = torch.zeros(NH, dtype=torch.float64, device="cuda")
+    V = torch.zeros((NH, NH), dtype=torch.float64, device="cuda")
+    mk.mk_coarse_decompose_warm(ctx, NH, dev(torch, o["AH"]), dev(torch, V0), d, V)
+    torch.cuda.synchronize()
+    ev = sla.eigh(o["AH"], o["MH"], eigvals_only=True)
+    dh, Vh = d.cpu().numpy(), V.cpu().numpy()
+    assert np.abs(dh - ev).max() < 1e-10 * max(1.0, np.abs(ev).max())
+    assert np.abs(Vh.T @ o["MH"] @ Vh - np.eye(NH)).max() < 1e-10
+    assert np.abs(o["AH"] @ Vh - o["MH"] @ Vh * dh[None, :]).max() < 1e-9 * max(1.0, np.abs(ev).max())
+
+
 def test_small_eigensolve_singular(ctx, torch):
     """psi^ in V_H: status MK_ERR_SINGULAR_AUG and the coarse Ritz pair best aligned with it."""
     from oracle import linalg as olin
@@ -288,9 +311,11 @@ def test_orbital_assemble(ctx, torch, name):
     assert rel(psi.cpu().numpy()[:, :N], o["psi"]) < 1e-12
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("name", CASES)
-def test_full_step(ctx, torch, name):
-    """A1-A8 chained on the GPU (FP64) vs the oracle: eigenvalues within 1e-6 Ha, orbitals within 1e-6."""
+def test_full_step(ctx, torch, name, precision):
+    """A1-A8 chained on the GPU vs the oracle (coarse decomposition overlapped on a second stream): eigenvalues
+    within 1e-6 Ha, orbitals within 1e-6 relative L2."""
     from paper_2103_02824_gb300 import mk
     from paper_2103_02824_gb300.step import CorrectionStep
     c = case(name)
@@ -298,7 +323,8 @@ def test_full_step(ctx, torch, name):
     m = gpu_mesh(ctx, name)
     st = CorrectionStep(ctx, m, c["wl"]["Z"], c["wl"]["R"], c["N"], ld=8)
     st.run(c["psiH"], c["lamH"], c["occ"], c["sigma"], xc=c["xc"], hartree_bc="multipole",
-           solve_opts=mk.opts(rtol=1e-13), poisson_opts=mk.opts(rtol=1e-13))
+           solve_opts=mk.opts(precision=precision, rtol=1e-13, check_every=5),
+           poisson_opts=mk.opts(precision=precision, rtol=1e-13, check_every=5))
     torch.cuda.synchronize()
     lam = st.lam.cpu().numpy()
     assert np.abs(lam - o["lam"]).max() < 1e-6
