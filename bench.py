@@ -38,7 +38,45 @@ def parse():
     ap.add_argument("--workload", default="mol4_p2")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="step", choices=["step", "apply"],
+                    help="apply: time the FP32 element-by-element operator alone (kernel-level roofline)")
     return ap.parse_args()
+
+
+def apply_mode(a):
+    """Times mk_operator_apply's FP32 patch operator (y = A x, all orbital columns) on the workload's mesh."""
+    import torch
+    from paper_2103_02824_gb300 import build, mk, synth
+    from paper_2103_02824_gb300.step import upload_workload
+    build.build()
+    wl = synth.workload(a.workload)
+    ctx = mk.Context(0)
+    mesh, _ = upload_workload(ctx, wl)
+    info = mesh.info
+    N = synth.n_orbitals(wl["Z"])
+    ld = max(4, (N + 3) // 4 * 4)
+    mol = mk.Molecule(wl["Z"], wl["R"])
+    g = torch.Generator(device="cuda").manual_seed(5)
+    x = torch.randn((info["n_nodes"], ld), generator=g, device="cuda", dtype=torch.float32)
+    y = torch.empty_like(x)
+    for _ in range(a.warmup):
+        mk.mk_operator_apply(ctx, mesh, mol, 18.0, x, y)
+    mk.profile_enable(ctx, True)
+    torch.cuda.synchronize()
+    for _ in range(a.steps):
+        mk.mk_operator_apply(ctx, mesh, mol, 18.0, x, y)
+    torch.cuda.synchronize()
+    ms, n = mk.profile_read(ctx, mk.PROF_APPLY32)
+    hms, hn = mk.profile_read(ctx, mk.PROF_HALO)
+    nloc, E = info["nloc"], info["n_elems"]
+    npack = nloc * (nloc + 1) // 2
+    nbytes = 2.0 * info["n_nodes"] * ld * 4 + E * (npack * 4 + nloc * 4 + 2 * nloc)
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6780.7) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6780.7
+    gbs = nbytes / (ms / n * 1e-3) / 1e9
+    print(json.dumps({"mode": "apply", "workload": a.workload, "ld": ld, "applications": n,
+                      "patch_ms": ms / n, "halo_ms": hms / max(hn, 1), "bytes_per_application": nbytes,
+                      "achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak}))
 
 
 def workload_config(wl, N, n_free, NH, E):
@@ -108,6 +146,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if a.impl == "reference":
         return reference(a, rank, world)
+    if a.mode == "apply":
+        return apply_mode(a)
     import numpy as np
     import torch
     torch.cuda.set_device(local)
@@ -149,12 +189,14 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     t0 = time.perf_counter()
     e0.record()
     for _ in range(a.steps):
         reps = step()
     e1.record()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     wall = time.perf_counter() - t0
     if dist:
         dist.barrier()

@@ -99,11 +99,13 @@ __global__ void k_dot_partial(int64_t n_nodes, const T* __restrict__ a, const T*
   }
   sh[threadIdx.x] = (r < rows) ? acc : 0.0;
   __syncthreads();
-  if (threadIdx.x < N) {
-    double s = 0.0;
-    for (int k = 0; k < rows; ++k) s += sh[k * N + threadIdx.x];
-    part[(int64_t)blockIdx.x * N + threadIdx.x] = s;
+  int top = 1;
+  while (top < rows) top <<= 1;
+  for (int st = top >> 1; st > 0; st >>= 1) {  // fixed pairwise tree over the rows of each column
+    if (r < st && r + st < rows) sh[threadIdx.x] += sh[threadIdx.x + st * N];
+    __syncthreads();
   }
+  if (threadIdx.x < N) part[(int64_t)blockIdx.x * N + threadIdx.x] = sh[threadIdx.x];
 }
 
 // Sums partials in block order: out[j] = sum_blk part[blk*N + j].
@@ -117,7 +119,10 @@ int column_dots32(mk_ctx* ctx, int64_t n_nodes, const float* a, const float* b, 
 
 // element matrices (packed, FP64) of half_k K + vext_scale M_{V_ext} + mass_shift M + M_{vq}
 int element_matrices(mk_ctx* ctx, const Level& L, const mk_molecule* mol, double half_k, double vext_scale,
-                     double mass_shift, const double* vq, double* out, cudaStream_t s);
+                     double mass_shift, const double* vq, double* out, cudaStream_t s,
+                     const double* base = nullptr);
+// cached K/2 + M_{V_ext} element matrices of the fine mesh for a molecule (nullptr and *err set on failure)
+const double* static_matrices(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, cudaStream_t s, int* err);
 // assembled diagonal of the packed element matrices, boundary rows set to 1
 int assemble_diagonal(mk_ctx* ctx, const Level& L, const double* Ae, double* diag, cudaStream_t s);
 // y = A x (y zeroed first), boundary rows of y zeroed if mask_boundary

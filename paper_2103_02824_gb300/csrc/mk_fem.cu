@@ -46,13 +46,15 @@ int column_dots32(mk_ctx* ctx, int64_t n_nodes, const float* a, const float* b, 
 }
 
 // ------------------------------------------------------------------------------------------------ element matrices
-// out_e = half_k K_e + vext_scale M_{V_ext,e} + mass_shift M_e + M_{vq,e}, packed upper triangle, FP64.
+// out_e = base_e + half_k K_e + vext_scale M_{V_ext,e} + mass_shift M_e + M_{vq,e}, packed upper triangle, FP64
+// (base optional: a precomputed set of element matrices in the same layout).
 // K_e = |det J| sum_{i<=j} (J^-1 J^-T)_{ij} S^{ij} with the reference tensors S^{ij}; the mass-type terms by the
 // 27-point rule at the physical points x_q = x0 + J xi_q (a constant coefficient uses the exact reference mass).
 template <int NLOC>
 __global__ void k_element_matrices(int64_t E, const RefTables* __restrict__ ref, const Geom* __restrict__ geom,
                                    const NucParams nucp, double half_k, double vext_scale, double mass_shift,
-                                   const double* __restrict__ vq, double* __restrict__ out) {
+                                   const double* __restrict__ vq, const double* __restrict__ base,
+                                   double* __restrict__ out) {
   constexpr int NP = NLOC * (NLOC + 1) / 2;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
@@ -60,7 +62,7 @@ __global__ void k_element_matrices(int64_t E, const RefTables* __restrict__ ref,
   const double det = fabs(g.det);
   double acc[NP];
 #pragma unroll
-  for (int p = 0; p < NP; ++p) acc[p] = 0.0;
+  for (int p = 0; p < NP; ++p) acc[p] = base ? base[e * NP + p] : 0.0;
   const bool vext = vext_scale != 0.0 && nucp.n > 0;
   if (vext || vq != nullptr) {
     for (int q = 0; q < kQ; ++q) {
@@ -85,7 +87,7 @@ __global__ void k_element_matrices(int64_t E, const RefTables* __restrict__ ref,
   } else if (mass_shift != 0.0) {
     const double f = mass_shift * det;
 #pragma unroll
-    for (int p = 0; p < NP; ++p) acc[p] = f * ref->mass[p];
+    for (int p = 0; p < NP; ++p) acc[p] += f * ref->mass[p];
   }
   if (half_k != 0.0) {
     const double* Ji = g.Jinv;
@@ -106,19 +108,73 @@ __global__ void k_element_matrices(int64_t E, const RefTables* __restrict__ ref,
 }
 
 int element_matrices(mk_ctx* ctx, const Level& L, const mk_molecule* mol, double half_k, double vext_scale,
-                     double mass_shift, const double* vq, double* out, cudaStream_t s) {
+                     double mass_shift, const double* vq, double* out, cudaStream_t s, const double* base) {
   MK_ARG(!mol || mol->n_nuclei <= kMaxNuclei, "at most 64 nuclei are supported");
   const NucParams nucp = make_nuc(mol);
   const int th = 128;
   const int blocks = (int)((L.n_elems + th - 1) / th);
   if (L.nloc == 4)
     MK_COUNT(), k_element_matrices<4><<<blocks, th, 0, s>>>(L.n_elems, ctx->d_ref[1], L.d_geom, nucp, half_k,
-                                                            vext_scale, mass_shift, vq, out);
+                                                            vext_scale, mass_shift, vq, base, out);
   else
     MK_COUNT(), k_element_matrices<10><<<blocks, th, 0, s>>>(L.n_elems, ctx->d_ref[2], L.d_geom, nucp, half_k,
-                                                             vext_scale, mass_shift, vq, out);
+                                                             vext_scale, mass_shift, vq, base, out);
   MK_CUDA(cudaGetLastError());
   return MK_OK;
+}
+
+// K/2 + M_{V_ext} element matrices of the fine mesh for `mol`, computed once per (mesh, molecule) and kept in the
+// mesh handle: they depend on neither the density nor the shift (the paper's static blocks, assembled in
+// advance).  The molecule is compared by value; a different one replaces the cached set.
+const double* static_matrices(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, cudaStream_t s, int* err) {
+  const Level& L = m->fine;
+  std::vector<double> key;
+  const int n = mol ? mol->n_nuclei : 0;
+  key.push_back(n);
+  for (int k = 0; k < n; ++k) {
+    key.push_back(mol->Z[k]);
+    for (int c = 0; c < 3; ++c) key.push_back(mol->R[3 * k + c]);
+  }
+  if (!m->static_ev && cudaEventCreateWithFlags(&m->static_ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    m->static_ev = nullptr;
+    *err = fail(MK_ERR_CUDA, "static element matrices: event creation failed");
+    return nullptr;
+  }
+  if (m->d_static && m->static_key == key) {
+    // the set may have been written on another stream: order this one after it
+    if (cudaStreamWaitEvent(s, m->static_ev, 0) != cudaSuccess) {
+      *err = fail(MK_ERR_CUDA, "static element matrices: cudaStreamWaitEvent failed");
+      return nullptr;
+    }
+    return m->d_static;
+  }
+  if (m->d_static) {
+    // another molecule: earlier readers of the old set, on any stream, finish first
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+      *err = fail(MK_ERR_CUDA, "static element matrices: cudaDeviceSynchronize failed");
+      return nullptr;
+    }
+  } else {
+    const size_t bytes = (size_t)L.n_elems * (L.nloc * (L.nloc + 1) / 2) * sizeof(double);
+    if (cudaMalloc(&m->d_static, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      m->d_static = nullptr;
+      *err = fail(MK_ERR_OOM, "static element matrices: allocation failed");
+      return nullptr;
+    }
+  }
+  const int r = element_matrices(ctx, L, mol, 0.5, 1.0, 0.0, nullptr, m->d_static, s);
+  if (r != MK_OK) {
+    *err = r;
+    return nullptr;
+  }
+  if (cudaEventRecord(m->static_ev, s) != cudaSuccess) {
+    *err = fail(MK_ERR_CUDA, "static element matrices: cudaEventRecord failed");
+    return nullptr;
+  }
+  m->static_key = key;
+  return m->d_static;
 }
 
 // ------------------------------------------------------------------------------------------------ diagonal

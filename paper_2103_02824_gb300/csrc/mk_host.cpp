@@ -612,6 +612,8 @@ int mk_mesh_destroy(mk_mesh* m) {
   cudaFree(m->d_child_off); cudaFree(m->d_child);
   free_patches(m->patches);
   cudaFree(m->d_MH_Linv);
+  cudaFree(m->d_static);
+  if (m->static_ev) cudaEventDestroy(m->static_ev);
   delete m;
   return MK_OK;
 }

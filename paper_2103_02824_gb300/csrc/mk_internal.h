@@ -103,7 +103,7 @@ struct Patches {
   int32_t* d_conn = nullptr;             // [E*nloc] global nodes of the patch-ordered elements
   int32_t* d_node_target = nullptr;      // [sum nodes] >= 0: global node written directly; < 0: -(halo slot)-1
   int32_t* d_inc_off = nullptr;          // [sum nodes + 1] start of each local node's incidences (global index)
-  uint16_t* d_inc = nullptr;             // [E*nloc] incidence = local element * nloc + local slot, fixed order
+  uint16_t* d_inc = nullptr;             // [E*nloc] incidence = local slot * max_elems + local element, fixed order
   int32_t* d_shared_node = nullptr;      // [n_shared] global node of each shared node
   int32_t* d_shared_off = nullptr;       // [n_shared+1] its halo slots (one per patch, in patch order)
 };
@@ -169,6 +169,10 @@ struct mk_mesh {
   // M_H = P^T M P depends on the meshes only (it stays fixed, like the paper's M_H): its inverse Cholesky factor
   // Linv = L^-1 (M_H = L L^T), dense row-major [N_H*N_H], is computed once at upload.
   double* d_MH_Linv = nullptr;
+  // K/2 + M_{V_ext} element matrices (FP64, element order) for the molecule in static_key (see static_matrices)
+  mutable double* d_static = nullptr;
+  mutable std::vector<double> static_key;
+  mutable cudaEvent_t static_ev = nullptr;  // recorded after the set was written
 };
 
 namespace mk {
@@ -203,9 +207,5 @@ enum Slot : int {
   S_COUNT
 };
 void* scratch(mk_ctx* ctx, int slot, size_t bytes, int* err);
-
-// device helpers implemented in .cu files
-int launch_element_matrices(mk_ctx* ctx, const mk_mesh* m, const Level& L, const mk_molecule* mol, double half_k,
-                            double vext_scale, double mass_shift, const double* vq, double* out, cudaStream_t s);
 
 }  // namespace mk

@@ -46,8 +46,64 @@ __device__ __forceinline__ void stv(T* __restrict__ p, const Vec<T, VEC>& r) {
 }
 
 // ------------------------------------------------------------------------------------------------ patch apply
-// One CTA per patch.  Phase 1: element products y_e = A_e x_e into shared memory (one thread per element and
-// group of VEC columns).  Phase 2: each local node sums its incidences in fixed order and writes the global row
+// Asynchronous global -> shared copies (cp.async): every copy of a CTA is in flight at once, so staging a patch
+// costs one memory latency instead of one per loop trip.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Block-cooperative copy of nbytes (a multiple of 4) from the 4-byte aligned global address src into the 16-byte
+// aligned shared region (nbytes + 16 bytes long).  The data land at region + (src mod 16), so the aligned body
+// moves in 16-byte copies and only the head and tail in 4-byte ones; returns where src[0] landed.
+template <typename U>
+__device__ __forceinline__ const U* stage_async(unsigned char* region, const U* src, int nbytes) {
+  const unsigned char* g = reinterpret_cast<const unsigned char*>(src);
+  const int mis = (int)(reinterpret_cast<uintptr_t>(g) & 15);
+  unsigned char* d = region + mis;
+  const int head = min((16 - mis) & 15, nbytes);
+  const int body = (nbytes - head) & ~15;
+  const int tail = nbytes - head - body;
+  for (int k = threadIdx.x; k < head / 4; k += blockDim.x) cp_async4(d + 4 * k, g + 4 * k);
+  for (int k = threadIdx.x; k < body / 16; k += blockDim.x) cp_async16(d + head + 16 * k, g + head + 16 * k);
+  for (int k = threadIdx.x; k < tail / 4; k += blockDim.x) cp_async4(d + head + body + 4 * k, g + head + body + 4 * k);
+  return reinterpret_cast<const U*>(d);
+}
+
+// Row length of one packed element matrix of the patch operator, padded so that every row starts on a 16-byte
+// boundary (55 -> 56 for P2 in FP32 or FP64, 10 -> 12 for P1 in FP32): rows load as whole 16-byte vectors.
+__host__ __device__ constexpr int padded_np(int nloc, int tsize) {
+  return (nloc * (nloc + 1) / 2 + 16 / tsize - 1) / (16 / tsize) * (16 / tsize);
+}
+
+// Shared-memory layout of one patch-apply CTA (byte offsets, each region 16-byte aligned).
+struct PatchSmem {
+  size_t ye, as, conn, inc, ioff, tgt, total;
+};
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+__host__ __device__ inline PatchSmem patch_smem(int nloc, int pe, int max_nodes, int W, int tsize) {
+  PatchSmem L;
+  L.ye = 0;
+  L.as = L.ye + align16((size_t)nloc * pe * W * tsize);
+  L.conn = L.as + align16((size_t)pe * padded_np(nloc, tsize) * tsize + 16);
+  L.inc = L.conn + align16((size_t)pe * nloc * 4 + 16);
+  L.ioff = L.inc + align16((size_t)pe * nloc * 2 + 16);
+  L.tgt = L.ioff + align16((size_t)(max_nodes + 1) * 4 + 16);
+  L.total = L.tgt + align16((size_t)max_nodes * 4 + 16);
+  return L;
+}
+
+// y = A x for one patch per CTA: owner-computes scatter, fixed summation order, no atomics.
+// Staging: the patch's element matrices, connectivity, incidence lists and node targets are copied into shared
+// memory asynchronously, all at once.  Phase 1: element products y_e = A_e x_e (x gathered from global, mostly L2
+// hits) into shared memory laid out [slot][element][column]; one thread per element and group of VEC columns.
+// Each element matrix is read from shared memory once (packed order), with all output rows held in registers.
+// Phase 2: each local node sums its incidences in fixed order (shared memory only) and writes the global row
 // (owned node) or its halo slot (shared node).  Columns [col0, col0 + W) with W = ncolg * VEC.
 template <int NLOC, typename T, int VEC>
 __global__ void __launch_bounds__(256) k_apply_patch(const int32_t* __restrict__ elem_off,
@@ -58,51 +114,72 @@ __global__ void __launch_bounds__(256) k_apply_patch(const int32_t* __restrict__
                                                      const uint16_t* __restrict__ inc,
                                                      const uint8_t* __restrict__ bnd, int mask,
                                                      const T* __restrict__ x, T* __restrict__ y, T* __restrict__ halo,
-                                                     int ncolg, int col0, int ld) {
-  constexpr int NP = NLOC * (NLOC + 1) / 2;
-  extern __shared__ unsigned char smraw[];
-  T* Ye = reinterpret_cast<T*>(smraw);
+                                                     int ncolg, int col0, int ld, int pe, int max_nodes) {
+  constexpr int NPS = padded_np(NLOC, (int)sizeof(T));
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int W = ncolg * VEC;
+  const PatchSmem lay = patch_smem(NLOC, pe, max_nodes, W, (int)sizeof(T));
+  T* Ye = reinterpret_cast<T*>(smraw + lay.ye);  // [NLOC][pe][W]
   const int p = blockIdx.x;
   const int e0 = elem_off[p], ne = elem_off[p + 1] - e0;
   const int n0 = node_off[p], nl = node_off[p + 1] - n0;
-  const int W = ncolg * VEC;
+  const int ibase = e0 * NLOC;  // the patch's incidences are inc[ibase, ibase + ne * NLOC)
+  const T* As = stage_async(smraw + lay.as, Ae + (int64_t)e0 * NPS, ne * NPS * (int)sizeof(T));
+  const int32_t* cs = stage_async(smraw + lay.conn, conn + ibase, ne * NLOC * 4);
+  const uint16_t* is = stage_async(smraw + lay.inc, inc + ibase, ne * NLOC * 2);
+  const int32_t* os = stage_async(smraw + lay.ioff, inc_off + n0, (nl + 1) * 4);
+  const int32_t* ts = stage_async(smraw + lay.tgt, target + n0, nl * 4);
+  cp_async_wait_all();
+  __syncthreads();
   for (int it = threadIdx.x; it < ne * ncolg; it += blockDim.x) {
     const int el = it / ncolg, g = it - el * ncolg;
-    const int64_t e = e0 + el;
     Vec<T, VEC> xv[NLOC];
 #pragma unroll
-    for (int a = 0; a < NLOC; ++a) xv[a] = ldv<T, VEC>(x + (int64_t)conn[e * NLOC + a] * ld + col0 + g * VEC);
-    const T* A = Ae + e * NP;
-    T Ar[NP];
+    for (int a = 0; a < NLOC; ++a) xv[a] = ldv<T, VEC>(x + (int64_t)cs[el * NLOC + a] * ld + col0 + g * VEC);
+    // one pass over the packed upper triangle: each entry is read once and feeds rows a and b; nothing is
+    // stored until every row is complete
+    const T* A = As + el * NPS;
+    Vec<T, VEC> acc[NLOC];
 #pragma unroll
-    for (int k = 0; k < NP; ++k) Ar[k] = A[k];
+    for (int a = 0; a < NLOC; ++a)
 #pragma unroll
-    for (int a = 0; a < NLOC; ++a) {
-      Vec<T, VEC> acc;
+      for (int c = 0; c < VEC; ++c) acc[a].v[c] = 0;
 #pragma unroll
-      for (int c = 0; c < VEC; ++c) acc.v[c] = 0;
+    for (int a = 0; a < NLOC; ++a)
 #pragma unroll
-      for (int b = 0; b < NLOC; ++b) {
-        const T w = Ar[sym_index(a, b, NLOC)];
+      for (int b = a; b < NLOC; ++b) {
+        const T w = A[sym_index(a, b, NLOC)];
 #pragma unroll
-        for (int c = 0; c < VEC; ++c) acc.v[c] += w * xv[b].v[c];
+        for (int c = 0; c < VEC; ++c) {
+          acc[a].v[c] += w * xv[b].v[c];
+          if (b != a) acc[b].v[c] += w * xv[a].v[c];
+        }
       }
-      stv<T, VEC>(Ye + (el * NLOC + a) * W + g * VEC, acc);
-    }
+#pragma unroll
+    for (int a = 0; a < NLOC; ++a) stv<T, VEC>(Ye + ((size_t)a * pe + el) * W + g * VEC, acc[a]);
   }
   __syncthreads();
   for (int it = threadIdx.x; it < nl * ncolg; it += blockDim.x) {
     const int l = it / ncolg, g = it - l * ncolg;
-    const int b = inc_off[n0 + l], e = inc_off[n0 + l + 1];
+    const int b = os[l] - ibase, e = os[l + 1] - ibase;
     Vec<T, VEC> acc;
 #pragma unroll
     for (int c = 0; c < VEC; ++c) acc.v[c] = 0;
-    for (int k = b; k < e; ++k) {
-      const Vec<T, VEC> v = ldv<T, VEC>(Ye + (int)inc[k] * W + g * VEC);
+    auto ye = [&](int k) {  // product of incidence k (slot * pe + local element)
+      return ldv<T, VEC>(Ye + (size_t)is[k] * W + g * VEC);
+    };
+    int k = b;
+    for (; k + 4 <= e; k += 4) {  // four independent loads, then the sums in list order
+      const Vec<T, VEC> v0 = ye(k), v1 = ye(k + 1), v2 = ye(k + 2), v3 = ye(k + 3);
+#pragma unroll
+      for (int c = 0; c < VEC; ++c) acc.v[c] = (((acc.v[c] + v0.v[c]) + v1.v[c]) + v2.v[c]) + v3.v[c];
+    }
+    for (; k < e; ++k) {
+      const Vec<T, VEC> v = ye(k);
 #pragma unroll
       for (int c = 0; c < VEC; ++c) acc.v[c] += v.v[c];
     }
-    const int t = target[n0 + l];
+    const int t = ts[l];
     if (t >= 0) {
       if (mask && bnd[t])
 #pragma unroll
@@ -139,13 +216,13 @@ __global__ void k_halo(int64_t nshared, const int32_t* __restrict__ node, const 
 }
 
 template <typename T>
-__global__ void k_pack_elements(int64_t E, int np, const int32_t* __restrict__ elem_id, const double* __restrict__ A64,
-                                T* __restrict__ A) {
+__global__ void k_pack_elements(int64_t E, int np, int nps, const int32_t* __restrict__ elem_id,
+                                const double* __restrict__ A64, T* __restrict__ A) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= E * np) return;
-  const int64_t i = t / np;
-  const int k = (int)(t - i * np);
-  A[t] = (T)A64[(int64_t)elem_id[i] * np + k];
+  if (t >= E * nps) return;
+  const int64_t i = t / nps;
+  const int k = (int)(t - i * nps);
+  A[t] = k < np ? (T)A64[(int64_t)elem_id[i] * np + k] : (T)0;
 }
 
 // y = A x with the patch operator (all ld columns), FP32 or FP64.
@@ -158,20 +235,22 @@ int apply_patch(mk_ctx* ctx, const mk_mesh* m, const T* Ae, const T* x, T* y, in
   if (!halo) return err;
   constexpr int VEC = sizeof(T) == 4 ? 4 : 2;
   const int vec = (ld % VEC == 0) ? VEC : 1;
-  const int wmax = sizeof(T) == 4 ? 16 : 8;  // columns per pass (shared memory)
+  const int wmax = sizeof(T) == 4 ? 16 : 4;  // columns per pass (shared memory)
   const int nloc = L.nloc;
   for (int col0 = 0; col0 < ld; col0 += wmax) {
     const int W = std::min(wmax, ld - col0);
     const int ncolg = W / vec;
-    const size_t smem = (size_t)P.max_elems * nloc * W * sizeof(T);
+    const size_t smem = patch_smem(nloc, P.max_elems, P.max_nodes, W, (int)sizeof(T)).total;
+    if (smem > 227 * 1024) return fail(MK_ERR_UNSUPPORTED, "patch operator: patch too large for shared memory");
+    const int th = std::min(256, (P.max_elems * ncolg + 31) / 32 * 32);  // one phase-1 item per thread
     prof_mark(ctx, PROF_APPLY32, true, s);
 #define MK_PATCH_LAUNCH(NL, V)                                                                                       \
   do {                                                                                                              \
     auto kern = k_apply_patch<NL, T, V>;                                                                            \
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
-    MK_COUNT(), kern<<<P.n_patches, 256, smem, s>>>(P.d_patch_elem_off, P.d_patch_node_off, P.d_conn, Ae,            \
+    MK_COUNT(), kern<<<P.n_patches, th, smem, s>>>(P.d_patch_elem_off, P.d_patch_node_off, P.d_conn, Ae,            \
                                                     P.d_node_target, P.d_inc_off, P.d_inc, L.d_boundary, mask, x, y, \
-                                                    halo, ncolg, col0, ld);                                         \
+                                                    halo, ncolg, col0, ld, P.max_elems, P.max_nodes);               \
   } while (0)
     if (nloc == 4) {
       if (vec == VEC) MK_PATCH_LAUNCH(4, VEC); else MK_PATCH_LAUNCH(4, 1);
@@ -208,8 +287,10 @@ int pack_elements(mk_ctx* ctx, const mk_mesh* m, const double* A64, T* A, cudaSt
   (void)ctx;
   const Level& L = m->fine;
   const int np = L.nloc * (L.nloc + 1) / 2;
-  const int64_t work = L.n_elems * np;
-  MK_COUNT(), k_pack_elements<T><<<(int)((work + 255) / 256), 256, 0, s>>>(L.n_elems, np, m->patches.d_elem_id, A64, A);
+  const int nps = padded_np(L.nloc, (int)sizeof(T));
+  const int64_t work = L.n_elems * nps;
+  MK_COUNT(), k_pack_elements<T><<<(int)((work + 255) / 256), 256, 0, s>>>(L.n_elems, np, nps, m->patches.d_elem_id,
+                                                                           A64, A);
   MK_CUDA(cudaGetLastError());
   return MK_OK;
 }
@@ -227,15 +308,18 @@ struct MixState {
 template <int NS>
 __device__ __forceinline__ void block_partials(double (&acc)[NS], double* sh, int ld, double* part) {
   const int rows = blockDim.x / ld;
+  const int r = threadIdx.x / ld;
+  int top = 1;
+  while (top < rows) top <<= 1;
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
     sh[threadIdx.x] = acc[k];
     __syncthreads();
-    if (threadIdx.x < ld) {
-      double s = 0.0;
-      for (int r = 0; r < rows; ++r) s += sh[r * ld + threadIdx.x];
-      part[(int64_t)blockIdx.x * NS * ld + k * ld + threadIdx.x] = s;
+    for (int st = top >> 1; st > 0; st >>= 1) {  // fixed pairwise tree over the rows of each column
+      if (r < st && r + st < rows) sh[threadIdx.x] += sh[threadIdx.x + st * ld];
+      __syncthreads();
     }
+    if (threadIdx.x < ld) part[(int64_t)blockIdx.x * NS * ld + k * ld + threadIdx.x] = sh[threadIdx.x];
     __syncthreads();
   }
 }
@@ -425,7 +509,9 @@ int solve_mixed(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, double si
   int err = MK_OK;
   double* A64 = (double*)scratch(ctx, S_ELEM64, (size_t)L.n_elems * np * sizeof(double), &err);
   if (!A64) return err;
-  MK_TRY(element_matrices(ctx, L, mol, 0.5, 1.0, sigma, nullptr, A64, s));
+  const double* H0 = static_matrices(ctx, m, mol, s, &err);
+  if (!H0) return err;
+  MK_TRY(element_matrices(ctx, L, nullptr, 0.0, 0.0, sigma, nullptr, A64, s, H0));
   return pcg_mixed(ctx, m, A64, b, x, ld, N, o, rep, s);
 }
 
@@ -453,7 +539,7 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
   const int64_t n = L.n_nodes;
   const int np = L.nloc * (L.nloc + 1) / 2;
   int err = MK_OK;
-  float* A32 = (float*)scratch(ctx, S_ELEM32, (size_t)L.n_elems * np * sizeof(float), &err);
+  float* A32 = (float*)scratch(ctx, S_ELEM32, (size_t)L.n_elems * padded_np(L.nloc, 4) * sizeof(float), &err);
   double* diag = (double*)scratch(ctx, S_DIAG64, n * sizeof(double), &err);
   float* dinv = (float*)scratch(ctx, S_DIAG32, n * sizeof(float), &err);
   double* Ax = (double*)scratch(ctx, S_Q64, (size_t)n * ld * sizeof(double), &err);
@@ -595,14 +681,16 @@ extern "C" int mk_operator_apply(mk_ctx* ctx, const mk_mesh* m, const mk_molecul
   int err = MK_OK;
   double* A64 = (double*)scratch(ctx, S_OPA, (size_t)L.n_elems * np * sizeof(double), &err);
   if (!A64) return err;
-  MK_TRY(element_matrices(ctx, L, mol, 0.5, 1.0, sigma, nullptr, A64, s));
+  const double* H0 = static_matrices(ctx, m, mol, s, &err);
+  if (!H0) return err;
+  MK_TRY(element_matrices(ctx, L, nullptr, 0.0, 0.0, sigma, nullptr, A64, s, H0));
   if (precision == MK_PREC_FP64) {
-    double* A = (double*)scratch(ctx, S_OPB, (size_t)L.n_elems * np * sizeof(double), &err);
+    double* A = (double*)scratch(ctx, S_OPB, (size_t)L.n_elems * padded_np(L.nloc, 8) * sizeof(double), &err);
     if (!A) return err;
     MK_TRY(pack_elements<double>(ctx, m, A64, A, s));
     return apply_patch<double>(ctx, m, A, (const double*)x, (double*)y, ld, true, s);
   }
-  float* A = (float*)scratch(ctx, S_OPB, (size_t)L.n_elems * np * sizeof(float), &err);
+  float* A = (float*)scratch(ctx, S_OPB, (size_t)L.n_elems * padded_np(L.nloc, 4) * sizeof(float), &err);
   if (!A) return err;
   MK_TRY(pack_elements<float>(ctx, m, A64, A, s));
   return apply_patch<float>(ctx, m, A, (const float*)x, (float*)y, ld, true, s);

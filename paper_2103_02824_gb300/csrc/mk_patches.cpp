@@ -7,6 +7,7 @@
 // adds those slots in patch order.  Every sum has a fixed order, so results are bitwise reproducible, with no
 // atomics and no colour-by-colour launches.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 
@@ -14,7 +15,15 @@
 
 namespace mk {
 
-int patch_elems(int nloc) { return nloc == 4 ? 256 : 128; }
+// Elements per patch: 256 (P1) or 128 (P2); the environment variable MK_PATCH_ELEMS (a multiple of 32 in
+// [32, 512]) overrides it for tuning.  It is read when a mesh is uploaded.
+int patch_elems(int nloc) {
+  if (const char* e = std::getenv("MK_PATCH_ELEMS")) {
+    const int v = std::atoi(e);
+    if (v >= 32 && v <= 512 && v % 32 == 0) return v;
+  }
+  return nloc == 4 ? 256 : 128;
+}
 
 static uint32_t spread10(uint32_t v) {
   v &= 0x3ff;
@@ -78,7 +87,18 @@ int build_patches(mk_mesh* m) {
     for (int32_t i = elem_off[p]; i < elem_off[p + 1]; ++i)
       for (int a = 0; a < nloc; ++a) ns.push_back(L.elem[(int64_t)order[i] * nloc + a]);
     std::sort(ns.begin(), ns.end());
-    ns.erase(std::unique(ns.begin(), ns.end()), ns.end());
+    // incidences of each distinct node inside the patch; local nodes are numbered by decreasing count (ties by
+    // global id) so that the threads of a warp, which take consecutive local nodes, sum lists of similar length
+    std::vector<std::pair<int32_t, int32_t>> by_count;  // (-count, global id)
+    for (size_t i = 0; i < ns.size();) {
+      size_t j = i;
+      while (j < ns.size() && ns[j] == ns[i]) ++j;
+      by_count.push_back({-(int32_t)(j - i), ns[i]});
+      i = j;
+    }
+    std::sort(by_count.begin(), by_count.end());
+    ns.clear();
+    for (const auto& bc : by_count) ns.push_back(bc.second);
     for (int32_t g : ns) cnt[g]++;
     node_off[p + 1] = node_off[p] + (int32_t)ns.size();
     P.max_nodes = std::max(P.max_nodes, (int)ns.size());
@@ -111,6 +131,10 @@ int build_patches(mk_mesh* m) {
       const int32_t g = node_global[nb + l];
       target[nb + l] = (cnt[g] >= 2) ? -(int32_t)(hbase[g] + seen[g]++) - 1 : g;
     }
+    // local index of each global node of the patch (node_global[nb, ne) is in count order, not sorted)
+    std::vector<std::pair<int32_t, int32_t>> lookup(nl);  // (global id, local index), sorted by global id
+    for (int l = 0; l < nl; ++l) lookup[l] = {node_global[nb + l], l};
+    std::sort(lookup.begin(), lookup.end());
     // incidences per local node in (element, slot) order, CSR local to the patch
     std::vector<int32_t> c(nl + 1, 0);
     std::vector<int32_t> lidx((size_t)(elem_off[p + 1] - elem_off[p]) * nloc);
@@ -119,8 +143,7 @@ int build_patches(mk_mesh* m) {
       for (int a = 0; a < nloc; ++a) {
         const int32_t g = L.elem[(int64_t)order[i] * nloc + a];
         conn[(size_t)i * nloc + a] = g;
-        const int l = (int)(std::lower_bound(node_global.begin() + nb, node_global.begin() + ne, g) -
-                            (node_global.begin() + nb));
+        const int l = std::lower_bound(lookup.begin(), lookup.end(), std::make_pair(g, (int32_t)-1))->second;
         lidx[(size_t)(i - elem_off[p]) * nloc + a] = l;
         c[l + 1]++;
       }
@@ -128,7 +151,10 @@ int build_patches(mk_mesh* m) {
     for (int l = 0; l < nl; ++l) c[l + 1] += c[l];
     std::vector<uint16_t> lst(c[nl]);
     std::vector<int32_t> pos(c.begin(), c.end() - 1);
-    for (size_t k = 0; k < lidx.size(); ++k) lst[pos[lidx[k]]++] = (uint16_t)k;   // k = local element * nloc + a
+    for (size_t k = 0; k < lidx.size(); ++k) {  // k = local element * nloc + slot; stored as slot * PE + element
+      const int el = (int)(k / nloc), a = (int)(k % nloc);
+      lst[pos[lidx[k]]++] = (uint16_t)(a * PE + el);
+    }
     const int32_t base = (int32_t)inc.size();
     for (int l = 0; l < nl; ++l) inc_off.push_back(base + c[l]);
     inc.insert(inc.end(), lst.begin(), lst.end());

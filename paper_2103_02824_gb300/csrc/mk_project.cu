@@ -85,20 +85,16 @@ __global__ void k_coarse_scatter(const int32_t* __restrict__ celems, int count, 
                                  const int32_t* __restrict__ node_to_free, const double* __restrict__ C1,
                                  const double* __restrict__ C2, double* __restrict__ AH, double* __restrict__ MH,
                                  int NH) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= count) return;
+  // one thread per (element, a, b): elements of one colour share no node, so every (f_a, f_b) is written once
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)count * NLOC * NLOC) return;
+  const int i = (int)(t / (NLOC * NLOC)), ab = (int)(t % (NLOC * NLOC));
+  const int a = ab / NLOC, b = ab % NLOC;
   const int T = celems[i];
-  int f[NLOC];
-#pragma unroll
-  for (int a = 0; a < NLOC; ++a) f[a] = node_to_free[elem[(int64_t)T * NLOC + a]];
-  for (int a = 0; a < NLOC; ++a) {
-    if (f[a] < 0) continue;
-    for (int b = 0; b < NLOC; ++b) {
-      if (f[b] < 0) continue;
-      AH[(int64_t)f[a] * NH + f[b]] += C1[(int64_t)T * NLOC * NLOC + a * NLOC + b];
-      MH[(int64_t)f[a] * NH + f[b]] += C2[(int64_t)T * NLOC * NLOC + a * NLOC + b];
-    }
-  }
+  const int fa = node_to_free[elem[(int64_t)T * NLOC + a]], fb = node_to_free[elem[(int64_t)T * NLOC + b]];
+  if (fa < 0 || fb < 0) return;
+  AH[(int64_t)fa * NH + fb] += C1[(int64_t)T * NLOC * NLOC + ab];
+  MH[(int64_t)fa * NH + fb] += C2[(int64_t)T * NLOC * NLOC + ab];
 }
 
 // Gram partials: part[blk][j*N+k] = sum over nodes of X[n][j] Y[n][k]
@@ -175,10 +171,10 @@ int coarse_matrices(mk_ctx* ctx, const mk_mesh* m, const double* A1, const doubl
   for (int col = 0; col < C.n_colours; ++col) {
     const int64_t off = C.colour_off[col], cnt = C.colour_off[col + 1] - off;
     if (nl == 4)
-      MK_COUNT(), k_coarse_scatter<4><<<(int)((cnt + 63) / 64), 64, 0, s>>>(C.d_colour_elems + off, (int)cnt, C.d_elem,
+      MK_COUNT(), k_coarse_scatter<4><<<(int)((cnt * 16 + 255) / 256), 256, 0, s>>>(C.d_colour_elems + off, (int)cnt, C.d_elem,
                                                                            C.d_node_to_free, C1, C2, X1, X2, NH);
     else
-      MK_COUNT(), k_coarse_scatter<10><<<(int)((cnt + 63) / 64), 64, 0, s>>>(C.d_colour_elems + off, (int)cnt,
+      MK_COUNT(), k_coarse_scatter<10><<<(int)((cnt * 100 + 255) / 256), 256, 0, s>>>(C.d_colour_elems + off, (int)cnt,
                                                                             C.d_elem, C.d_node_to_free, C1, C2, X1,
                                                                             X2, NH);
   }
@@ -202,7 +198,9 @@ extern "C" int mk_coarse_pencil(mk_ctx* ctx, const mk_mesh* m, const mk_molecule
   double* He = (double*)scratch(ctx, S_ELEM64C, eb, &err);
   double* Me = (double*)scratch(ctx, S_ELEM64D, eb, &err);
   if (!He || !Me) return err;
-  MK_TRY(element_matrices(ctx, F, mol, 0.5, 1.0, 0.0, vq, He, s));
+  const double* H0 = static_matrices(ctx, m, mol, s, &err);
+  if (!H0) return err;
+  MK_TRY(element_matrices(ctx, F, nullptr, 0.0, 0.0, 0.0, vq, He, s, H0));
   MK_TRY(element_matrices(ctx, F, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s));
   return coarse_matrices(ctx, m, He, Me, AH, MH, S_COARSE2, s);
 }
@@ -225,7 +223,9 @@ extern "C" int mk_augmented_project(mk_ctx* ctx, const mk_mesh* m, const mk_mole
   double* MY = (double*)scratch(ctx, S_VEC2, (size_t)F.n_nodes * ld * sizeof(double), &err);
   double* G = (double*)scratch(ctx, S_GRAM, (size_t)2 * N * N * sizeof(double), &err);
   if (!He || !Me || !Y || !MY || !G) return err;
-  MK_TRY(element_matrices(ctx, F, mol, 0.5, 1.0, 0.0, vq, He, s));
+  const double* H0 = static_matrices(ctx, m, mol, s, &err);
+  if (!H0) return err;
+  MK_TRY(element_matrices(ctx, F, nullptr, 0.0, 0.0, 0.0, vq, He, s, H0));
   MK_TRY(element_matrices(ctx, F, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s));
   MK_TRY(apply64(ctx, F, He, psihat, Y, N, ld, true, s));
   MK_TRY(apply64(ctx, F, Me, psihat, MY, N, ld, true, s));

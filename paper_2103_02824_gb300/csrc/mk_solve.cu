@@ -341,7 +341,9 @@ int mk_correction_solve(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, d
   double* Ae = (double*)scratch(ctx, S_ELEM64, (size_t)L.n_elems * (L.nloc * (L.nloc + 1) / 2) * sizeof(double), &err);
   double* diag = (double*)scratch(ctx, S_DIAG64, L.n_nodes * sizeof(double), &err);
   if (!Ae || !diag) return err;
-  MK_TRY(element_matrices(ctx, L, mol, 0.5, 1.0, sigma, nullptr, Ae, s));
+  const double* H0 = static_matrices(ctx, m, mol, s, &err);
+  if (!H0) return err;
+  MK_TRY(element_matrices(ctx, L, nullptr, 0.0, 0.0, sigma, nullptr, Ae, s, H0));
   MK_TRY(assemble_diagonal(ctx, L, Ae, diag, s));
   return pcg64(ctx, L, Ae, diag, rhs, x, N, ld, *opts, report, s);
 }
