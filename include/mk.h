@@ -79,14 +79,24 @@ enum { MK_PREC_FP64 = 0, MK_PREC_MIXED = 1 };
 enum { MK_PRECOND_JACOBI = 0, MK_PRECOND_CHEBYSHEV = 1, MK_PRECOND_LEARNED = 2 };
 enum { MK_BC_ZERO = 0, MK_BC_MULTIPOLE = 1 };
 
+typedef struct mk_mlp mk_mlp;
+
 typedef struct {
   int precision;     /* MK_PREC_FP64: plain FP64 PCG.  MK_PREC_MIXED: FP32 inner PCG + FP64 residual refinement */
-  int precond;       /* MK_PRECOND_* */
+  int precond;       /* MK_PRECOND_*.  LEARNED (MIXED only): FCG(1) inner solve with mk_learned_precond */
   double rtol;       /* stop when ||b_i - A x_i||_2 / ||b_i||_2 <= rtol for every column (FP64, free DOF) */
   int maxit;         /* cap on PCG iterations (inner iterations summed for MIXED) */
   double inner_rtol; /* MIXED: relative reduction asked of each FP32 inner solve */
   int max_refine;    /* MIXED: cap on FP64 refinement cycles */
   int check_every;   /* iterations between host convergence checks (>= 1) */
+  const mk_mlp* mlp; /* LEARNED: the network (NULL otherwise) */
+  int mlp_precision; /* LEARNED: MK_MLP_BF16 (tensor cores) or MK_MLP_FP32 */
+  /* FP64 path only: every trace_every-th iterate x_k and recursive residual r_k (k = 0, trace_every, ...) is
+   * copied to trace_x / trace_r, device double [trace_cap][n_nodes*ld], until trace_cap are taken (0 = off);
+   * the report's n_traced says how many.  These pairs are the training data of the learned preconditioner. */
+  int trace_every, trace_cap;
+  double* trace_x;
+  double* trace_r;
 } mk_solve_opts;
 
 typedef struct {
@@ -97,6 +107,7 @@ typedef struct {
   double max_rel_residual;              /* max over columns of the final FP64 relative residual */
   int iters[MK_MAX_RHS];                /* per column: iterations until it met rtol */
   double rel_residual[MK_MAX_RHS];      /* per column: final FP64 ||b - A x|| / ||b|| */
+  int n_traced;                         /* iterates copied to mk_solve_opts.trace_x / trace_r */
 } mk_solve_report;
 
 typedef struct {
@@ -258,6 +269,55 @@ int mk_orbital_assemble(mk_ctx* ctx, const mk_mesh* mesh, const double* coef, co
  * sigma = 1.05 max(0, -theta) + 0.5 that keeps the correction operator positive definite. */
 int mk_lowest_ritz(mk_ctx* ctx, const mk_mesh* mesh, const mk_molecule* mol, const double* v0, int steps,
                    double* theta, void* stream);
+
+/* ---------------------------------------------------------------------------------------------------------
+ * Learned element-patch preconditioner (this library's addition; the paper solves its boundary-value problems
+ * with standard solvers).  Definitions, for element e and orbital column j:
+ *   input   x = [r_e / s, (v_k - centroid_e) / h_e (k = 0..3)]    r_e: residual at the element's n_loc nodes,
+ *           s = ||r_e||_2 (x's first part 0 when s = 0), h_e = |det J_e|^(1/3); n_in = n_loc + 12
+ *   network y = W3 relu(W2 relu(W1 x + b1) + b2) + b3, hidden width MK_MLP_HIDDEN, n_out = n_loc
+ *   precond z(node) = r(node)/A(node,node) + (sum over the node's (element, slot) incidences of y[slot] s/h_e)
+ *                     / (number of incidences); boundary rows 0
+ *   training sample (x, u, e): u = s/h_e, e = (x* - x_k) at the element's nodes for an iterate x_k of a solve
+ *            with residual r_k and converged solution x*; loss L = sum_s ||u_s y_s - e_s||^2 / sum_s u_s^2
+ *            (the network predicts the error normalised like its input), Adam updates.
+ * Parameters are FP32, flattened in the order W1 [H][n_in], b1 [H], W2 [H][H], b2 [H], W3 [n_out][H],
+ * b3 [n_out], row-major.  Inference in BF16 (weights and activations rounded to BF16, FP32 accumulation, warp
+ * tensor-core MMA) or FP32; training in FP32 with deterministic (fixed-order) gradient sums.
+ * --------------------------------------------------------------------------------------------------------- */
+#define MK_MLP_HIDDEN 64
+enum { MK_MLP_FP32 = 0, MK_MLP_BF16 = 1 };
+
+typedef struct {
+  double lr, beta1, beta2, eps; /* Adam (Kingma & Ba); lr = 0: gradient only, no update */
+} mk_adam;
+
+/* Number of parameters for elements with n_loc nodes (4 or 10). */
+int64_t mk_mlp_param_count(int nloc);
+/* Create a network for n_loc-node elements from `params` (host, mk_mlp_param_count(nloc) floats).  Adam moments
+ * start at zero.  The handle owns its device memory (freed by mk_mlp_destroy). */
+int mk_mlp_create(mk_ctx* ctx, int nloc, const float* params, mk_mlp** out);
+int mk_mlp_destroy(mk_mlp* mlp);
+/* Copy the FP32 parameters to host `params` (save) or from host `params` into the network (load; resets Adam). */
+int mk_mlp_save(const mk_mlp* mlp, float* params);
+int mk_mlp_load(mk_mlp* mlp, const float* params);
+/* Y[s] = network(X[s]) for S rows: X device float [S][n_in], Y device float [S][n_out]; precision MK_MLP_*. */
+int mk_mlp_forward(mk_ctx* ctx, const mk_mlp* mlp, const float* X, int64_t S, float* Y, int precision, void* stream);
+/* One training step on S samples (rows idx[0..S) of X [.][n_in], U [.], E [.][n_out], all device float; idx
+ * device int32 or NULL for rows 0..S-1): loss and gradient of L over the batch (FP32 products, FP64 sums over
+ * blocks in fixed order), then an Adam update unless opt is NULL or opt->lr == 0.  *loss (host) and, if given,
+ * grad (device float [param_count]) receive the values before the update.  Synchronises the stream. */
+int mk_mlp_train_step(mk_ctx* ctx, mk_mlp* mlp, const float* X, const float* U, const float* E,
+                      const int32_t* idx, int64_t S, const mk_adam* opt, double* loss, float* grad, void* stream);
+/* Training samples from one iterate of a solve on the fine mesh: for every element e (original order) and
+ * column j < N, row e*N + j of X [E*N][n_in], U [E*N], E [E*N][n_out] (device float).  Rk, Xk, Xstar: device
+ * double [n_nodes*ld] (residual and iterate at step k, converged solution). */
+int mk_mlp_harvest(mk_ctx* ctx, const mk_mesh* mesh, const double* Rk, const double* Xk, const double* Xstar, int ld,
+                   int N, float* X, float* U, float* E, void* stream);
+/* z = learned preconditioner applied to r for the operator K/2 + M_{V_ext} + sigma M of `mol` (its diagonal
+ * gives the Jacobi part): r, z device float [n_nodes*ld], columns j < N (others of z untouched). */
+int mk_learned_precond(mk_ctx* ctx, const mk_mesh* mesh, const mk_mlp* mlp, const mk_molecule* mol, double sigma,
+                       const float* r, float* z, int ld, int N, int precision, void* stream);
 
 #ifdef __cplusplus
 }

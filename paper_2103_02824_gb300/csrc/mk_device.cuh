@@ -129,5 +129,10 @@ int assemble_diagonal(mk_ctx* ctx, const Level& L, const double* Ae, double* dia
 int apply64(mk_ctx* ctx, const Level& L, const double* Ae, const double* x, double* y, int N, int ld,
             bool mask_boundary, cudaStream_t s);
 
+// dinv = (float)(1 / diag)
+int diag_inverse32(int64_t n, const double* diag, float* dinv, cudaStream_t s);
+// z = learned preconditioner of r (FP32, columns < N); dinv: FP32 inverse diagonal of the operator
+int learned_apply(mk_ctx* ctx, const mk_mesh* m, const mk_mlp* mlp, const float* dinv, const float* r, float* z,
+                  int ld, int N, int precision, cudaStream_t s);
 
 }  // namespace mk

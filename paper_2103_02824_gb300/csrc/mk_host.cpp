@@ -525,6 +525,7 @@ int mk_mesh_upload(mk_ctx* ctx, const mk_mesh_desc* fine, const mk_mesh_desc* co
   MK_CUDA(cudaSetDevice(ctx->device));
   mk_mesh* m = new mk_mesh();
   m->ctx = ctx;
+  m->device = ctx->device;
   int r = build_level(fine, m->fine, "fine");
   if (r == MK_OK) r = build_level(coarse, m->coarse, "coarse");
   if (r != MK_OK) { delete m; return r; }
@@ -604,7 +605,7 @@ int mk_mesh_upload(mk_ctx* ctx, const mk_mesh_desc* fine, const mk_mesh_desc* co
 
 int mk_mesh_destroy(mk_mesh* m) {
   if (!m) return MK_OK;
-  cudaSetDevice(m->ctx->device);
+  cudaSetDevice(m->device);
   free_level(m->fine);
   free_level(m->coarse);
   cudaFree(m->d_P_off); cudaFree(m->d_P_col); cudaFree(m->d_P_val);

@@ -106,6 +106,10 @@ struct Patches {
   uint16_t* d_inc = nullptr;             // [E*nloc] incidence = local slot * max_elems + local element, fixed order
   int32_t* d_shared_node = nullptr;      // [n_shared] global node of each shared node
   int32_t* d_shared_off = nullptr;       // [n_shared+1] its halo slots (one per patch, in patch order)
+  // learned preconditioner inputs: per patch-ordered element (h_e, (v_k - centroid)/h_e for k = 0..3, 0, 0, 0)
+  // with h_e = |det J|^(1/3); per node 1 / (number of (element, slot) incidences)
+  float* d_geomf = nullptr;              // [E*16]
+  float* d_inv_mult = nullptr;           // [n_nodes]
 };
 int patch_elems(int nloc);
 
@@ -140,6 +144,22 @@ struct mk_ctx {
   cudaEvent_t solve_ev[2] = {nullptr, nullptr};
 };
 
+// Learned preconditioner network: FP32 master parameters (flattened W1,b1,W2,b2,W3,b3), Adam moments, and the
+// BF16 copy in the padded layout of the tensor-core kernels (W1 [64][40], W2 [64][72], W3 [16][72] halves,
+// zero padded) with FP32 biases [64 + 64 + 16].
+struct mk_mlp {
+  mk_ctx* ctx = nullptr;
+  int device = 0;  // kept here so that the handle can be destroyed after its context
+  int nloc = 0, nin = 0, nout = 0;
+  int64_t count = 0;
+  float* d_w = nullptr;
+  float* d_m = nullptr;
+  float* d_v = nullptr;
+  void* d_wb = nullptr;
+  float* d_bias = nullptr;
+  long long t = 0;  // Adam steps taken
+};
+
 namespace mk {
 // Record a start (begin=true) or stop event for profiled operation `kind` on stream s (no-op unless enabled).
 void prof_mark(mk_ctx* ctx, int kind, bool begin, cudaStream_t s);
@@ -151,6 +171,7 @@ enum ProfKind { PROF_APPLY64 = 0, PROF_APPLY32 = 1, PROF_HALO = 2, PROF_OTHER = 
 
 struct mk_mesh {
   mk_ctx* ctx = nullptr;
+  int device = 0;  // kept here so that the handle can be destroyed after its context
   mk::Level fine, coarse;
   std::vector<int32_t> parent;
   // prolongation P: fine node -> coarse free DOF (CSR over fine nodes)
@@ -204,6 +225,10 @@ enum Slot : int {
   S_EIG3, S_EIG4,               // general (unshared) eigensolve: factor + decomposition, Cholesky workspace
   S_HALO64,                     // halo partial sums of the FP64 patch operator
   S_OPA, S_OPB,                 // element matrices of mk_operator_apply (FP64 original order, patch order)
+  S_Z32,                        // FCG preconditioned residual (FP32)
+  S_LHALO,                      // halo partial sums of the learned preconditioner
+  S_MLPPART, S_MLPGRAD,         // training: per-block gradient partials, reduced gradient
+  S_LDINV,                      // mk_learned_precond: FP64 diagonal, FP32 inverse
   S_COUNT
 };
 void* scratch(mk_ctx* ctx, int slot, size_t bytes, int* err);

@@ -8,95 +8,9 @@
 #include <cstring>
 
 #include "mk_device.cuh"
+#include "mk_patch.cuh"
 
 namespace mk {
-
-// ------------------------------------------------------------------------------------------------ vectors
-template <typename T, int VEC>
-struct Vec {
-  T v[VEC];
-};
-
-template <typename T, int VEC>
-__device__ __forceinline__ Vec<T, VEC> ldv(const T* __restrict__ p) {
-  Vec<T, VEC> r;
-  if constexpr (VEC == 4 && sizeof(T) == 4) {
-    const float4 f = *reinterpret_cast<const float4*>(p);
-    r.v[0] = f.x; r.v[1] = f.y; r.v[2] = f.z; r.v[3] = f.w;
-  } else if constexpr (VEC == 2 && sizeof(T) == 8) {
-    const double2 f = *reinterpret_cast<const double2*>(p);
-    r.v[0] = f.x; r.v[1] = f.y;
-  } else {
-#pragma unroll
-    for (int c = 0; c < VEC; ++c) r.v[c] = p[c];
-  }
-  return r;
-}
-
-template <typename T, int VEC>
-__device__ __forceinline__ void stv(T* __restrict__ p, const Vec<T, VEC>& r) {
-  if constexpr (VEC == 4 && sizeof(T) == 4) {
-    *reinterpret_cast<float4*>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
-  } else if constexpr (VEC == 2 && sizeof(T) == 8) {
-    *reinterpret_cast<double2*>(p) = make_double2(r.v[0], r.v[1]);
-  } else {
-#pragma unroll
-    for (int c = 0; c < VEC; ++c) p[c] = r.v[c];
-  }
-}
-
-// ------------------------------------------------------------------------------------------------ patch apply
-// Asynchronous global -> shared copies (cp.async): every copy of a CTA is in flight at once, so staging a patch
-// costs one memory latency instead of one per loop trip.
-__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
-// Block-cooperative copy of nbytes (a multiple of 4) from the 4-byte aligned global address src into the 16-byte
-// aligned shared region (nbytes + 16 bytes long).  The data land at region + (src mod 16), so the aligned body
-// moves in 16-byte copies and only the head and tail in 4-byte ones; returns where src[0] landed.
-template <typename U>
-__device__ __forceinline__ const U* stage_async(unsigned char* region, const U* src, int nbytes) {
-  const unsigned char* g = reinterpret_cast<const unsigned char*>(src);
-  const int mis = (int)(reinterpret_cast<uintptr_t>(g) & 15);
-  unsigned char* d = region + mis;
-  const int head = min((16 - mis) & 15, nbytes);
-  const int body = (nbytes - head) & ~15;
-  const int tail = nbytes - head - body;
-  for (int k = threadIdx.x; k < head / 4; k += blockDim.x) cp_async4(d + 4 * k, g + 4 * k);
-  for (int k = threadIdx.x; k < body / 16; k += blockDim.x) cp_async16(d + head + 16 * k, g + head + 16 * k);
-  for (int k = threadIdx.x; k < tail / 4; k += blockDim.x) cp_async4(d + head + body + 4 * k, g + head + body + 4 * k);
-  return reinterpret_cast<const U*>(d);
-}
-
-// Row length of one packed element matrix of the patch operator, padded so that every row starts on a 16-byte
-// boundary (55 -> 56 for P2 in FP32 or FP64, 10 -> 12 for P1 in FP32): rows load as whole 16-byte vectors.
-__host__ __device__ constexpr int padded_np(int nloc, int tsize) {
-  return (nloc * (nloc + 1) / 2 + 16 / tsize - 1) / (16 / tsize) * (16 / tsize);
-}
-
-// Shared-memory layout of one patch-apply CTA (byte offsets, each region 16-byte aligned).
-struct PatchSmem {
-  size_t ye, as, conn, inc, ioff, tgt, total;
-};
-__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
-__host__ __device__ inline PatchSmem patch_smem(int nloc, int pe, int max_nodes, int W, int tsize) {
-  PatchSmem L;
-  L.ye = 0;
-  L.as = L.ye + align16((size_t)nloc * pe * W * tsize);
-  L.conn = L.as + align16((size_t)pe * padded_np(nloc, tsize) * tsize + 16);
-  L.inc = L.conn + align16((size_t)pe * nloc * 4 + 16);
-  L.ioff = L.inc + align16((size_t)pe * nloc * 2 + 16);
-  L.tgt = L.ioff + align16((size_t)(max_nodes + 1) * 4 + 16);
-  L.total = L.tgt + align16((size_t)max_nodes * 4 + 16);
-  return L;
-}
 
 // y = A x for one patch per CTA: owner-computes scatter, fixed summation order, no atomics.
 // Staging: the patch's element matrices, connectivity, incidence lists and node targets are copied into shared
@@ -417,6 +331,55 @@ __global__ void k_mixed_p(int64_t n, const MixState* __restrict__ st, const floa
   p[t] = r[t] * dinv[nd] + (float)st[j].beta * p[t];
 }
 
+// FCG(1): partials of (p.q, p.r)
+__global__ void k_fcg_pq(int64_t n, const float* __restrict__ p, const float* __restrict__ q,
+                         const float* __restrict__ r, int ld, double* __restrict__ part) {
+  __shared__ double sh[256];
+  double acc[2] = {0.0, 0.0};
+  const int rows = blockDim.x / ld;
+  const int j = threadIdx.x % ld, rr = threadIdx.x / ld;
+  if (rr < rows)
+    for (int64_t nd = (int64_t)blockIdx.x * rows + rr; nd < n; nd += (int64_t)gridDim.x * rows) {
+      const int64_t t = nd * ld + j;
+      acc[0] += (double)p[t] * q[t];
+      acc[1] += (double)p[t] * r[t];
+    }
+  block_partials<2>(acc, sh, ld, part);
+}
+
+// FCG(1): d += alpha p; r -= alpha q; partial r.r
+__global__ void k_fcg_update(int64_t n, const MixState* __restrict__ st, const float* __restrict__ p,
+                             const float* __restrict__ q, float* __restrict__ d, float* __restrict__ r, int ld,
+                             double* __restrict__ part) {
+  __shared__ double sh[256];
+  double acc[1] = {0.0};
+  const int rows = blockDim.x / ld;
+  const int j = threadIdx.x % ld, rr = threadIdx.x / ld;
+  const float a = rr < rows ? (float)st[j].alpha : 0.f;
+  if (rr < rows)
+    for (int64_t nd = (int64_t)blockIdx.x * rows + rr; nd < n; nd += (int64_t)gridDim.x * rows) {
+      const int64_t t = nd * ld + j;
+      float rv = r[t];
+      if (a != 0.f) {
+        d[t] += a * p[t];
+        rv -= a * q[t];
+        r[t] = rv;
+      }
+      acc[0] += (double)rv * rv;
+    }
+  block_partials<1>(acc, sh, ld, part);
+}
+
+// FCG(1): p = z + beta p (active columns)
+__global__ void k_fcg_p(int64_t n, const MixState* __restrict__ st, const float* __restrict__ z,
+                        float* __restrict__ p, int ld) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * ld) return;
+  const int j = (int)(t % ld);
+  if (!st[j].active) return;
+  p[t] = z[t] + (float)st[j].beta * p[t];
+}
+
 __global__ void k_mixed_add(int64_t n, const float* __restrict__ d, double* __restrict__ x, int N, int ld) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * ld) return;
@@ -426,6 +389,12 @@ __global__ void k_mixed_add(int64_t n, const float* __restrict__ d, double* __re
 __global__ void k_dinv32(int64_t n, const double* __restrict__ diag, float* __restrict__ dinv) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) dinv[i] = (float)(1.0 / diag[i]);
+}
+
+int diag_inverse32(int64_t n, const double* diag, float* dinv, cudaStream_t s) {
+  MK_COUNT(), k_dinv32<<<(int)((n + 255) / 256), 256, 0, s>>>(n, diag, dinv);
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
 }
 
 __global__ void k_zero_boundary(int64_t n, const uint8_t* __restrict__ bnd, double* __restrict__ x, int ld) {
@@ -438,6 +407,8 @@ __global__ void k_zero_boundary(int64_t n, const uint8_t* __restrict__ bnd, doub
 // mode 1: inner init (rz, rr) -> rz, rr0, rr, active (outer_active), iters=0
 // mode 2: alpha from pq
 // mode 3: beta from (rz_new, rr) and convergence of the inner solve
+// FCG(1) (flexible CG, the learned preconditioner): mode 4: alpha = (p.r)/(p.q); mode 5: rr and convergence;
+// mode 6: beta = -(z.q)/(p.q); mode 7: inner init from r.r
 // Launched with kFinThreads threads: one warp per (sum, column) pair adds the block partials lane-strided and
 // folds them with a fixed shuffle tree (deterministic), then one thread per column updates its state.
 constexpr int kFinThreads = 1024;
@@ -483,7 +454,7 @@ __global__ void __launch_bounds__(kFinThreads) k_mixed_finalize(int mode, const 
     } else {
       c.alpha = 0.0;
     }
-  } else {
+  } else if (mode == 3) {
     if (c.active) {
       c.beta = s[0] / c.rz;
       c.rz = s[0];
@@ -493,6 +464,33 @@ __global__ void __launch_bounds__(kFinThreads) k_mixed_finalize(int mode, const 
     } else {
       c.beta = 0.0;
     }
+  } else if (mode == 4) {
+    c.pq = s[0];
+    if (c.active) {
+      if (!(c.pq > 0.0)) {
+        c.breakdown = 1;
+        c.active = 0;
+        c.alpha = 0.0;
+      } else {
+        c.alpha = s[1] / c.pq;
+      }
+    } else {
+      c.alpha = 0.0;
+    }
+  } else if (mode == 5) {
+    if (c.active) {
+      c.rr = s[0];
+      c.iters += 1;
+      c.active = c.rr > inner_rtol2 * c.rr0;
+    }
+  } else if (mode == 6) {
+    c.beta = c.active ? -s[0] / c.pq : 0.0;
+  } else {
+    c.rr0 = s[0];
+    c.rr = s[0];
+    c.active = c.outer_active && s[0] > 0.0;
+    c.alpha = 0.0;
+    c.beta = 0.0;
   }
   st[j] = c;
 }
@@ -503,7 +501,9 @@ int pcg_mixed(mk_ctx* ctx, const mk_mesh* m, const double* A64, const double* b,
 int solve_mixed(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, double sigma, const double* b,
                 const double*, const double*, double* x, int ld, int N, const mk_solve_opts& o, mk_solve_report* rep,
                 cudaStream_t s) {
-  if (o.precond != MK_PRECOND_JACOBI) return fail(MK_ERR_UNSUPPORTED, "mixed path: only Jacobi is built");
+  if (o.precond != MK_PRECOND_JACOBI && o.precond != MK_PRECOND_LEARNED)
+    return fail(MK_ERR_UNSUPPORTED, "mixed path: Jacobi or learned preconditioner");
+  if (o.precond == MK_PRECOND_LEARNED && !o.mlp) return fail(MK_ERR_INVALID_ARG, "learned preconditioner: no network");
   const Level& L = m->fine;
   const int np = L.nloc * (L.nloc + 1) / 2;
   int err = MK_OK;
@@ -547,6 +547,9 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
   float* p = (float*)scratch(ctx, S_P32, (size_t)n * ld * sizeof(float), &err);
   float* q = (float*)scratch(ctx, S_Q32, (size_t)n * ld * sizeof(float), &err);
   float* d = (float*)scratch(ctx, S_X32, (size_t)n * ld * sizeof(float), &err);
+  const bool fcg = o.precond == MK_PRECOND_LEARNED && o.mlp;
+  float* zb = fcg ? (float*)scratch(ctx, S_Z32, (size_t)n * ld * sizeof(float), &err) : nullptr;
+  if (fcg && !zb) return err;
   const int nblk = red_blocks(ctx);
   double* part = (double*)scratch(ctx, S_RED, (size_t)nblk * 2 * ld * sizeof(double), &err);
   MixState* st = (MixState*)scratch(ctx, S_SCAL, 256 * sizeof(MixState), &err);
@@ -575,6 +578,11 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
   // the operator's halo buffer must exist before a capture starts (nothing may allocate inside a capture)
   if (!scratch(ctx, S_HALO, (size_t)std::max<int64_t>(m->patches.n_halo_slots, 1) * ld * sizeof(float), &err))
     return err;
+  if (fcg) {
+    if (!scratch(ctx, S_LHALO, (size_t)std::max<int64_t>(m->patches.n_halo_slots, 1) * ld * sizeof(float), &err))
+      return err;
+    MK_CUDA(cudaMemsetAsync(zb, 0, (size_t)n * ld * sizeof(float), s));  // columns >= N stay zero
+  }
   for (;;) {
     MK_TRY(apply64(ctx, L, A64, x, Ax, ld, ld, true, s));   // FP64 residual of the current x
     MK_COUNT(), k_mixed_residual<<<nblk, th, 0, s>>>(n, L.d_boundary, b, Ax, r, d, N, ld, part);
@@ -586,13 +594,32 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
     if (!any) { converged = true; break; }
     if (refine >= max_refine || total_it >= o.maxit) break;
     ++refine;
-    MK_COUNT(), k_mixed_init<<<nblk, th, 0, s>>>(n, dinv, r, p, ld, part);
-    MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(1, part, nblk, 2, ld, N, st, o.rtol, inner2);
+    if (fcg) {
+      MK_TRY(learned_apply(ctx, m, o.mlp, dinv, r, zb, ld, N, o.mlp_precision, s));
+      MK_CUDA(cudaMemcpyAsync(p, zb, (size_t)n * ld * sizeof(float), cudaMemcpyDeviceToDevice, s));
+      MK_COUNT(), k_mixed_pq<<<nblk, th, 0, s>>>(n, r, r, ld, part);
+      MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(7, part, nblk, 1, ld, N, st, o.rtol, inner2);
+    } else {
+      MK_COUNT(), k_mixed_init<<<nblk, th, 0, s>>>(n, dinv, r, p, ld, part);
+      MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(1, part, nblk, 2, ld, N, st, o.rtol, inner2);
+    }
     int it = 0;
     bool inner_active = true;
-    // one PCG iteration; every scalar it needs lives on the device, so `check` of them can be replayed as a graph
+    // one PCG (or FCG(1)) iteration; every scalar it needs lives on the device, so `check` of them can be
+    // replayed as a graph
     auto iteration = [&]() -> int {
       MK_TRY(apply_patch<float>(ctx, m, A32, p, q, ld, true, s));
+      if (fcg) {
+        MK_COUNT(), k_fcg_pq<<<nblk, th, 0, s>>>(n, p, q, r, ld, part);
+        MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(4, part, nblk, 2, ld, N, st, o.rtol, inner2);
+        MK_COUNT(), k_fcg_update<<<nblk, th, 0, s>>>(n, st, p, q, d, r, ld, part);
+        MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(5, part, nblk, 1, ld, N, st, o.rtol, inner2);
+        MK_TRY(learned_apply(ctx, m, o.mlp, dinv, r, zb, ld, N, o.mlp_precision, s));
+        MK_COUNT(), k_mixed_pq<<<nblk, th, 0, s>>>(n, zb, q, ld, part);
+        MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(6, part, nblk, 1, ld, N, st, o.rtol, inner2);
+        MK_COUNT(), k_fcg_p<<<gb, 256, 0, s>>>(n, st, zb, p, ld);
+        return MK_OK;
+      }
       MK_COUNT(), k_mixed_pq<<<nblk, th, 0, s>>>(n, p, q, ld, part);
       MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(2, part, nblk, 1, ld, N, st, o.rtol, inner2);
       MK_COUNT(), k_mixed_update<<<nblk, th, 0, s>>>(n, st, dinv, p, q, d, r, ld, part);

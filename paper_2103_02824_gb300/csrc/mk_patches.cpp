@@ -7,6 +7,7 @@
 // adds those slots in patch order.  Every sum has a fixed order, so results are bitwise reproducible, with no
 // atomics and no colour-by-colour launches.
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <numeric>
@@ -163,7 +164,29 @@ int build_patches(mk_mesh* m) {
   // inc_off has one entry per local node of every patch (start) plus one final sentinel; the end of local node l
   // of patch p is the start of the next entry, which for the last node of a patch is the first node of the next
   // patch (or the sentinel): incidences of consecutive patches are contiguous, so starts alone suffice.
+  // learned-preconditioner geometry (patch order) and node multiplicities
+  std::vector<float> geomf((size_t)E * 16, 0.f);
+  for (int64_t i = 0; i < E; ++i) {
+    const Geom& G = L.geom[elem_id[i]];
+    const double h = std::cbrt(std::fabs(G.det));
+    double v[4][3];
+    for (int c = 0; c < 3; ++c) {
+      v[0][c] = G.x0[c];
+      for (int k = 1; k < 4; ++k) v[k][c] = G.x0[c] + G.J[c * 3 + (k - 1)];
+    }
+    double cen[3];
+    for (int c = 0; c < 3; ++c) cen[c] = 0.25 * (v[0][c] + v[1][c] + v[2][c] + v[3][c]);
+    geomf[i * 16] = (float)h;
+    for (int k = 0; k < 4; ++k)
+      for (int c = 0; c < 3; ++c) geomf[i * 16 + 1 + 3 * k + c] = (float)((v[k][c] - cen[c]) / h);
+  }
+  std::vector<int32_t> mult(nn, 0);
+  for (int64_t i = 0; i < E * nloc; ++i) mult[L.elem[i]]++;
+  std::vector<float> inv_mult(nn);
+  for (int64_t g = 0; g < nn; ++g) inv_mult[g] = mult[g] > 0 ? (float)(1.0 / mult[g]) : 0.f;
   int r = up(&P.d_patch_elem_off, elem_off);
+  if (r == MK_OK) r = up(&P.d_geomf, geomf);
+  if (r == MK_OK) r = up(&P.d_inv_mult, inv_mult);
   if (r == MK_OK) r = up(&P.d_patch_node_off, node_off);
   if (r == MK_OK) r = up(&P.d_elem_id, elem_id);
   if (r == MK_OK) r = up(&P.d_conn, conn);
@@ -178,6 +201,7 @@ int build_patches(mk_mesh* m) {
 void free_patches(Patches& p) {
   cudaFree(p.d_patch_elem_off); cudaFree(p.d_patch_node_off); cudaFree(p.d_elem_id); cudaFree(p.d_conn);
   cudaFree(p.d_node_target); cudaFree(p.d_inc_off); cudaFree(p.d_inc); cudaFree(p.d_shared_node);
+  cudaFree(p.d_geomf); cudaFree(p.d_inv_mult);
   cudaFree(p.d_shared_off);
   p = Patches();
 }

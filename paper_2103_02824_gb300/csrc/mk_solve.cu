@@ -149,7 +149,14 @@ int pcg64(mk_ctx* ctx, const Level& L, const double* Ae, const double* diag, con
   MK_CUDA(cudaStreamSynchronize(s));
   any_active = false;
   for (int j = 0; j < N; ++j) any_active |= hst[j].active != 0;
+  int ntr = 0;
+  const bool trace = o.trace_cap > 0 && o.trace_every > 0 && o.trace_x && o.trace_r;
   while (any_active && it < o.maxit) {
+    if (trace && it % o.trace_every == 0 && ntr < o.trace_cap) {  // training data of the learned preconditioner
+      MK_CUDA(cudaMemcpyAsync(o.trace_x + (size_t)ntr * n * ld, x, vb, cudaMemcpyDeviceToDevice, s));
+      MK_CUDA(cudaMemcpyAsync(o.trace_r + (size_t)ntr * n * ld, R, vb, cudaMemcpyDeviceToDevice, s));
+      ++ntr;
+    }
     MK_TRY(apply64(ctx, L, Ae, P, Q, N, ld, true, s));
     MK_TRY(column_dots(ctx, n, P, Q, N, ld, d1, s));
     MK_COUNT(), k_alpha<<<1, MK_MAX_RHS, 0, s>>>(st, d1, N);
@@ -190,6 +197,7 @@ int pcg64(mk_ctx* ctx, const Level& L, const double* Ae, const double* diag, con
       mx = std::max(mx, rep->rel_residual[j]);
     }
     rep->max_rel_residual = mx;
+    rep->n_traced = ntr;
   }
   double mx = 0.0;
   for (int j = 0; j < N; ++j) mx = std::max(mx, std::sqrt(rr[j]) / hst[j].bn);
@@ -201,7 +209,11 @@ int pcg64(mk_ctx* ctx, const Level& L, const double* Ae, const double* diag, con
 }
 
 static bool valid_opts(const mk_solve_opts* o) {
-  return o && o->rtol > 0 && o->maxit > 0;
+  if (!o || !(o->rtol > 0) || o->maxit <= 0) return false;
+  if (o->precond == MK_PRECOND_LEARNED)
+    return o->precision == MK_PREC_MIXED && o->mlp != nullptr &&
+           (o->mlp_precision == MK_MLP_FP32 || o->mlp_precision == MK_MLP_BF16);
+  return o->precond == MK_PRECOND_JACOBI;
 }
 
 __global__ void k_combine_rhs(int64_t n, const uint8_t* __restrict__ bnd, const double* __restrict__ Mu,

@@ -52,19 +52,25 @@ class mk_xc(C.Structure):
 
 class mk_solve_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("precond", C.c_int), ("rtol", C.c_double), ("maxit", C.c_int),
-                ("inner_rtol", C.c_double), ("max_refine", C.c_int), ("check_every", C.c_int)]
+                ("inner_rtol", C.c_double), ("max_refine", C.c_int), ("check_every", C.c_int),
+                ("mlp", C.c_void_p), ("mlp_precision", C.c_int), ("trace_every", C.c_int), ("trace_cap", C.c_int),
+                ("trace_x", C.c_void_p), ("trace_r", C.c_void_p)]
 
 
 class mk_solve_report(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("refinements", C.c_int), ("n_rhs", C.c_int),
                 ("max_rel_residual", C.c_double), ("iters", C.c_int * MK_MAX_RHS),
-                ("rel_residual", C.c_double * MK_MAX_RHS)]
+                ("rel_residual", C.c_double * MK_MAX_RHS), ("n_traced", C.c_int)]
 
     def to_dict(self):
         n = self.n_rhs
         return dict(status=self.status, iterations=self.iterations, refinements=self.refinements, n_rhs=n,
                     max_rel_residual=self.max_rel_residual, iters=list(self.iters[:n]),
-                    rel_residual=list(self.rel_residual[:n]))
+                    rel_residual=list(self.rel_residual[:n]), n_traced=self.n_traced)
+
+
+class mk_adam(C.Structure):
+    _fields_ = [("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double)]
 
 
 class mk_mesh_info(C.Structure):
@@ -104,6 +110,17 @@ _SIGS = {
     "mk_small_eigensolve_static": [C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "mk_orbital_assemble": [_vp, _vp, _vp, _vp, _vp, C.c_int, C.c_int, _vp, _vp],
     "mk_lowest_ritz": [_vp, _vp, C.POINTER(mk_molecule), C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double), _vp],
+    "mk_mlp_param_count": [C.c_int],
+    "mk_mlp_create": [_vp, C.c_int, C.POINTER(C.c_float), C.POINTER(_vp)],
+    "mk_mlp_destroy": [_vp],
+    "mk_mlp_save": [_vp, C.POINTER(C.c_float)],
+    "mk_mlp_load": [_vp, C.POINTER(C.c_float)],
+    "mk_mlp_forward": [_vp, _vp, _vp, C.c_int64, _vp, C.c_int, _vp],
+    "mk_mlp_train_step": [_vp, _vp, _vp, _vp, _vp, _vp, C.c_int64, C.POINTER(mk_adam), C.POINTER(C.c_double), _vp,
+                          _vp],
+    "mk_mlp_harvest": [_vp, _vp, _vp, _vp, _vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp],
+    "mk_learned_precond": [_vp, _vp, _vp, C.POINTER(mk_molecule), C.c_double, _vp, _vp, C.c_int, C.c_int, C.c_int,
+                           _vp],
 }
 
 
@@ -111,7 +128,7 @@ def header_symbols():
     """Names of the entry points declared in include/mk.h (parsed from the header)."""
     import re
     hdr = open(os.path.join(os.path.dirname(_HERE), "include", "mk.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:int|long long|const char\*)\s+(mk_\w+)\s*\(", hdr, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|int64_t|long long|const char\*)\s+(mk_\w+)\s*\(", hdr, re.M)))
 
 
 def load(path: str = LIB_PATH):
@@ -121,7 +138,8 @@ def load(path: str = LIB_PATH):
     for name, args in _SIGS.items():
         f = getattr(lib, name)
         f.argtypes = args
-        f.restype = {"mk_version": C.c_char_p, "mk_launch_count": C.c_longlong}.get(name, C.c_int)
+        f.restype = {"mk_version": C.c_char_p, "mk_launch_count": C.c_longlong,
+                     "mk_mlp_param_count": C.c_int64}.get(name, C.c_int)
     return lib
 
 
@@ -192,9 +210,85 @@ class Molecule:
         self.c = mk_molecule(len(self.Z), zp, rp)
 
 
-def opts(precision="fp64", precond="jacobi", rtol=1e-8, maxit=20000, inner_rtol=1e-4, max_refine=20, check_every=10):
-    return mk_solve_opts(MK_PREC_MIXED if precision == "mixed" else MK_PREC_FP64, MK_PRECOND[precond], rtol, maxit,
-                         inner_rtol, max_refine, check_every)
+MK_MLP_FP32, MK_MLP_BF16 = 0, 1
+
+
+def opts(precision="fp64", precond="jacobi", rtol=1e-8, maxit=20000, inner_rtol=1e-4, max_refine=20, check_every=10,
+         mlp=None, mlp_precision="bf16", trace=None):
+    """Solver options.  mlp: an Mlp (precond='learned'); trace: (every, x_buf, r_buf) device float64 tensors of
+    shape [cap, n_nodes, ld] receiving iterates and residuals of the FP64 PCG."""
+    o = mk_solve_opts(MK_PREC_MIXED if precision == "mixed" else MK_PREC_FP64, MK_PRECOND[precond], rtol, maxit,
+                      inner_rtol, max_refine, check_every)
+    if mlp is not None:
+        o.mlp = mlp.h.value
+        o.mlp_precision = MK_MLP_BF16 if mlp_precision == "bf16" else MK_MLP_FP32
+    if trace is not None:
+        every, xb, rb = trace
+        o.trace_every, o.trace_cap = int(every), int(xb.shape[0])
+        o.trace_x, o.trace_r = _ptr(xb).value, _ptr(rb).value
+        o._keep = (xb, rb)
+    return o
+
+
+class Mlp:
+    """The learned preconditioner's network (device-resident FP32 weights, Adam state, BF16 copy)."""
+
+    def __init__(self, ctx, nloc, params):
+        self.ctx, self.nloc = ctx, nloc
+        self.count = int(lib().mk_mlp_param_count(nloc))
+        p = np.ascontiguousarray(params, dtype=np.float32).ravel()
+        assert p.size == self.count, (p.size, self.count)
+        self.h = _vp()
+        _check(lib().mk_mlp_create(ctx.h, nloc, p.ctypes.data_as(C.POINTER(C.c_float)), C.byref(self.h)))
+
+    def save(self):
+        out = np.zeros(self.count, dtype=np.float32)
+        _check(lib().mk_mlp_save(self.h, out.ctypes.data_as(C.POINTER(C.c_float))))
+        return out
+
+    def load(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32).ravel()
+        assert p.size == self.count
+        _check(lib().mk_mlp_load(self.h, p.ctypes.data_as(C.POINTER(C.c_float))))
+
+    def close(self):
+        if self.h:
+            lib().mk_mlp_destroy(self.h)
+            self.h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mk_mlp_forward(ctx, mlp: Mlp, X, Y, precision="fp32", stream=None):
+    _check(lib().mk_mlp_forward(ctx.h, mlp.h, _ptr(X), X.shape[0], _ptr(Y),
+                                MK_MLP_BF16 if precision == "bf16" else MK_MLP_FP32, _stream(stream)))
+
+
+def mk_mlp_train_step(ctx, mlp: Mlp, X, U, E, idx=None, S=None, lr=0.0, beta1=0.9, beta2=0.999, eps=1e-8, grad=None,
+                      stream=None):
+    """Loss (before the update) of one training step; Adam update when lr > 0."""
+    S = int(S if S is not None else (idx.shape[0] if idx is not None else X.shape[0]))
+    loss = C.c_double()
+    a = mk_adam(lr, beta1, beta2, eps)
+    _check(lib().mk_mlp_train_step(ctx.h, mlp.h, _ptr(X), _ptr(U), _ptr(E), _ptr(idx), S, C.byref(a),
+                                   C.byref(loss), _ptr(grad), _stream(stream)))
+    return loss.value
+
+
+def mk_mlp_harvest(ctx, mesh, Rk, Xk, Xstar, N, X, U, E, stream=None):
+    ld = Rk.shape[1] if Rk.dim() == 2 else 1
+    _check(lib().mk_mlp_harvest(ctx.h, mesh.h, _ptr(Rk), _ptr(Xk), _ptr(Xstar), ld, N, _ptr(X), _ptr(U), _ptr(E),
+                                _stream(stream)))
+
+
+def mk_learned_precond(ctx, mesh, mlp: Mlp, mol: Molecule, sigma, r, z, N, precision="bf16", stream=None):
+    ld = r.shape[1] if r.dim() == 2 else 1
+    _check(lib().mk_learned_precond(ctx.h, mesh.h, mlp.h, C.byref(mol.c), float(sigma), _ptr(r), _ptr(z), ld, N,
+                                    MK_MLP_BF16 if precision == "bf16" else MK_MLP_FP32, _stream(stream)))
 
 
 class Context:

@@ -143,6 +143,19 @@ def lanczos_start(n: int, seed: int = 7) -> np.ndarray:
     return np.random.default_rng(seed).standard_normal(n)
 
 
+def mlp_init(nloc: int, seed: int, nh: int = 64, out_scale: float = 0.1) -> np.ndarray:
+    """Seeded initial parameters of the learned preconditioner's network, float32, flattened in the order
+    W1 [nh][nloc+12], b1 [nh], W2 [nh][nh], b2 [nh], W3 [nloc][nh], b3 [nloc] (row-major): He-normal weights,
+    zero biases, the last layer scaled by out_scale so that the untrained correction is small."""
+    rng = np.random.default_rng(seed)
+    nin, nout = nloc + 12, nloc
+    W1 = rng.standard_normal((nh, nin)) * np.sqrt(2.0 / nin)
+    W2 = rng.standard_normal((nh, nh)) * np.sqrt(2.0 / nh)
+    W3 = rng.standard_normal((nout, nh)) * np.sqrt(2.0 / nh) * out_scale
+    parts = [W1.ravel(), np.zeros(nh), W2.ravel(), np.zeros(nh), W3.ravel(), np.zeros(nout)]
+    return np.concatenate(parts).astype(np.float32)
+
+
 def workload(name: str):
     """Named workloads of the paper's kind, with their sizes.
 

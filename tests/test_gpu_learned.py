@@ -1,0 +1,250 @@
+"""GPU parity of the learned element-patch preconditioner against the FP64 oracle (oracle/learned.py), and what
+the trained network gains inside flexible CG.
+
+Tolerances: the FP32 forward / gradient / preconditioner paths accumulate in FP32 (unit roundoff 6e-8) over at
+most a few hundred terms per sum, so 1e-5 relative to the result's scale.  The BF16 tensor-core path rounds
+weights and the input of each of the three layers to BF16 (relative rounding 2^-9 per value); through 22 + 64
++ 64-term sums with random signs the relative error of the output stays near 1e-2, so 3e-2 relative to the
+output scale.  Adam runs in FP32: 1e-6 relative to the step size.
+"""
+import numpy as np
+import pytest
+
+from oracle import learned as LO
+from tests._cases import case, rel
+
+pytestmark = pytest.mark.gpu
+
+NAME = "mol4_p2_small"
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+@pytest.fixture(scope="module")
+def ctx(torch):
+    from paper_2103_02824_gb300 import build, mk
+    build.build()
+    c = mk.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def gmesh(ctx):
+    from paper_2103_02824_gb300 import mk
+    c = case(NAME)
+    cc, ct, fc, ft, par = c["meshes"]
+    m = mk.Mesh(ctx, fc, ft, cc, ct, par, c["wl"]["order"])
+    yield m
+    m.close()
+
+
+def _params(nloc, seed=3):
+    from paper_2103_02824_gb300 import synth
+    p = synth.mlp_init(nloc, seed, out_scale=1.0).copy()
+    rng = np.random.default_rng(seed)
+    nin = nloc + 12
+    o1 = 64 * nin
+    o2 = o1 + 64 + 64 * 64
+    o3 = o2 + 64 + nloc * 64
+    p[o1:o1 + 64] = 0.1 * rng.standard_normal(64)        # nonzero biases
+    p[o2:o2 + 64] = 0.1 * rng.standard_normal(64)
+    p[o3:o3 + nloc] = 0.1 * rng.standard_normal(nloc)
+    return p.astype(np.float32)
+
+
+def _oracle_params(p32, nloc):
+    nin, nh, _, nout = LO.sizes(nloc)
+    return LO.unflatten(p32.astype(np.float64), nin, nh, nout)
+
+
+def _bf16(a):
+    """Round float32 values to the nearest BF16 (ties to even), returned as float64."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("nloc", [4, 10])
+def test_forward_fp32_and_bf16(ctx, torch, nloc):
+    from paper_2103_02824_gb300 import mk
+    p = _params(nloc)
+    mlp = mk.Mlp(ctx, nloc, p)
+    rng = np.random.default_rng(1)
+    S = 1000  # several tiles and a ragged tail
+    X = rng.standard_normal((S, nloc + 12)).astype(np.float32)
+    Xd = torch.from_numpy(X).cuda()
+    Y = torch.zeros((S, nloc), dtype=torch.float32, device="cuda")
+    ref, _ = LO.forward(_oracle_params(p, nloc), X.astype(np.float64))
+    scale = np.abs(ref).max()
+    mk.mk_mlp_forward(ctx, mlp, Xd, Y, "fp32")
+    torch.cuda.synchronize()
+    assert np.abs(Y.cpu().numpy() - ref).max() <= 1e-5 * scale
+    mk.mk_mlp_forward(ctx, mlp, Xd, Y, "bf16")
+    torch.cuda.synchronize()
+    assert np.abs(Y.cpu().numpy() - ref).max() <= 3e-2 * scale
+    # with BF16-representable weights and inputs the first layer is exact up to FP32 accumulation: the remaining
+    # difference comes from rounding the two hidden layers, far below the bound above
+    pb = _bf16(p)
+    mlp.load(pb.astype(np.float32))
+    Xb = _bf16(X)
+    Yb = torch.zeros_like(Y)
+    mk.mk_mlp_forward(ctx, mlp, torch.from_numpy(Xb.astype(np.float32)).cuda(), Yb, "bf16")
+    torch.cuda.synchronize()
+    refb, _ = LO.forward(_oracle_params(pb.astype(np.float32), nloc), Xb)
+    assert np.abs(Yb.cpu().numpy() - refb).max() <= 2e-2 * np.abs(refb).max()
+    mlp.close()
+
+
+def test_gradient_and_adam(ctx, torch):
+    from paper_2103_02824_gb300 import mk
+    nloc = 10
+    p = _params(nloc, seed=4)
+    mlp = mk.Mlp(ctx, nloc, p)
+    rng = np.random.default_rng(2)
+    S = 777
+    X = rng.standard_normal((S, nloc + 12)).astype(np.float32)
+    U = (np.abs(rng.standard_normal(S)) + 0.05).astype(np.float32)
+    E = rng.standard_normal((S, nloc)).astype(np.float32)
+    d = lambda a: torch.from_numpy(a).cuda()
+    grad = torch.zeros(mlp.count, dtype=torch.float32, device="cuda")
+    loss = mk.mk_mlp_train_step(ctx, mlp, d(X), d(U), d(E), lr=0.0, grad=grad)
+    po = _oracle_params(p, nloc)
+    lref, gref = LO.loss_and_grad(po, X.astype(np.float64), U.astype(np.float64), E.astype(np.float64))
+    assert loss == pytest.approx(lref, rel=1e-5)
+    gv = LO.flatten(gref)
+    assert np.abs(grad.cpu().numpy() - gv).max() <= 1e-5 * np.abs(gv).max()
+    # a minibatch through idx equals the same rows passed directly
+    idx = rng.integers(0, S, 300).astype(np.int32)
+    l2 = mk.mk_mlp_train_step(ctx, mlp, d(X), d(U), d(E), idx=d(idx), lr=0.0, grad=grad)
+    lsub, gsub = LO.loss_and_grad(po, X[idx].astype(np.float64), U[idx].astype(np.float64), E[idx].astype(np.float64))
+    assert l2 == pytest.approx(lsub, rel=1e-5)
+    assert np.abs(grad.cpu().numpy() - LO.flatten(gsub)).max() <= 1e-5 * np.abs(LO.flatten(gsub)).max()
+    # one Adam step from zero moments against the oracle's, from the same gradient
+    mk.mk_mlp_train_step(ctx, mlp, d(X), d(U), d(E), lr=1e-3, grad=grad)
+    g64 = LO.unflatten(grad.cpu().numpy().astype(np.float64), nloc + 12, 64, nloc)
+    new = LO.flatten(LO.adam_step(po, g64, {}, 1e-3))
+    got = mlp.save().astype(np.float64)
+    assert np.abs(got - new).max() <= 1e-6 * 1e-3 + 1e-7 * np.abs(new).max()
+    # determinism: the same step twice gives bit-identical gradients
+    mlp.load(p)
+    g1 = torch.zeros_like(grad)
+    g2 = torch.zeros_like(grad)
+    mk.mk_mlp_train_step(ctx, mlp, d(X), d(U), d(E), lr=0.0, grad=g1)
+    mk.mk_mlp_train_step(ctx, mlp, d(X), d(U), d(E), lr=0.0, grad=g2)
+    assert torch.equal(g1, g2)
+    mlp.close()
+
+
+def test_harvest(ctx, torch, gmesh):
+    from paper_2103_02824_gb300 import mk
+    c = case(NAME)
+    f = c["level"].fine
+    N, ld = 3, 4
+    rng = np.random.default_rng(3)
+    Rk, Xk, Xs = (rng.standard_normal((f.n_nodes, ld)) for _ in range(3))
+    for a in (Rk, Xk, Xs):
+        a[f.boundary] = 0
+    E = f.n_elems
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    X = torch.zeros((E * N, 22), dtype=torch.float32, device="cuda")
+    U = torch.zeros(E * N, dtype=torch.float32, device="cuda")
+    Er = torch.zeros((E * N, 10), dtype=torch.float32, device="cuda")
+    mk.mk_mlp_harvest(ctx, gmesh, d(Rk), d(Xk), d(Xs), N, X, U, Er)
+    torch.cuda.synchronize()
+    Xo, Uo, Eo = LO.harvest(f, Rk[:, :N], Xk[:, :N], Xs[:, :N])
+    assert np.abs(X.cpu().numpy() - Xo).max() <= 1e-6
+    assert rel(U.cpu().numpy(), Uo) <= 1e-6
+    assert np.abs(Er.cpu().numpy() - Eo).max() <= 1e-6 * np.abs(Eo).max()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("bf16", 3e-2)])
+def test_learned_precond(ctx, torch, gmesh, precision, tol):
+    """z = D^-1 r + assembled network correction, per node, against the oracle (ragged N over two passes)."""
+    from paper_2103_02824_gb300 import mk
+    c = case(NAME)
+    lv, f = c["level"], c["level"].fine
+    p = _params(10, seed=6)
+    mlp = mk.Mlp(ctx, 10, p)
+    N, ld = 11, 12  # two column passes of the patch kernel, the second ragged
+    rng = np.random.default_rng(4)
+    R = rng.standard_normal((f.n_nodes, ld)).astype(np.float32)
+    R[f.boundary] = 0
+    R[:, N:] = 0
+    sigma = c["sigma"]
+    A = lv.operator(sigma)
+    diag = np.ones(f.n_nodes)
+    diag[f.free] = A.diagonal()
+    Zr = LO.precond(f, _oracle_params(p, 10), diag, R[:, :N].astype(np.float64))
+    z = torch.full((f.n_nodes, ld), 7.0, dtype=torch.float32, device="cuda")
+    mk.mk_learned_precond(ctx, gmesh, mlp, mk.Molecule(c["wl"]["Z"], c["wl"]["R"]), sigma,
+                          torch.from_numpy(R).cuda(), z, N, precision)
+    torch.cuda.synchronize()
+    got = z.cpu().numpy()
+    assert np.all(got[:, N:] == 7.0)                 # columns >= N untouched
+    assert np.all(got[f.boundary, :N] == 0)
+    err = np.abs(got[:, :N] - Zr).max()
+    corr = Zr - np.where(f.boundary[:, None], 0.0, R[:, :N] / diag[:, None])
+    assert err <= tol * np.abs(corr).max() + 1e-6 * np.abs(Zr).max(), (err, np.abs(corr).max())
+    mlp.close()
+
+
+def test_fcg_learned_solve_matches_oracle(ctx, torch, gmesh):
+    """Mixed-precision FCG(1) with the (untrained) learned preconditioner reaches the FP64 residual target and
+    the oracle's solution of the correction problem."""
+    from paper_2103_02824_gb300 import mk, synth
+    c = case(NAME)
+    mlp = mk.Mlp(ctx, 10, synth.mlp_init(10, 0))
+    N, ld = c["N"], 8
+    rhs = np.zeros((c["level"].fine.n_nodes, ld))
+    rhs[:, :N] = c["out"]["rhs"]
+    x0 = np.zeros_like(rhs)
+    x0[:, :N] = c["out"]["u"]
+    rhs_d, x = torch.from_numpy(rhs).cuda(), torch.from_numpy(x0).cuda()
+    for prec in ("bf16", "fp32"):
+        xx = x.clone()
+        rep = mk.mk_correction_solve(ctx, gmesh, mk.Molecule(c["wl"]["Z"], c["wl"]["R"]), c["sigma"], rhs_d, xx, N,
+                                     opt=mk.opts(precision="mixed", precond="learned", mlp=mlp, mlp_precision=prec,
+                                                 rtol=1e-12, inner_rtol=1e-4, check_every=5))
+        assert rep["max_rel_residual"] <= 1e-12
+        assert rel(xx.cpu().numpy()[:, :N], c["out"]["psihat"]) < 1e-8
+    mlp.close()
+
+
+def test_learned_gain_on_unseen_molecule(ctx, torch, gmesh):
+    """Train on correction solves of four seeded molecules, evaluate FCG iterations on an unseen one against the
+    same solver with the network off (Jacobi) and with the untrained network.  The numbers are reported; the
+    assertions are that training lowers the loss and that every variant converges to the same FP64 answer."""
+    from paper_2103_02824_gb300 import learned, mk, synth
+    probs = [learned.Problem(ctx, gmesh, *synth.molecule(s, 4)) for s in (3, 4, 5, 6)]
+    data = [learned.harvest(p, every=2, cap=10) for p in probs]
+    X = torch.cat([d[0] for d in data])
+    U = torch.cat([d[1] for d in data])
+    E = torch.cat([d[2] for d in data])
+    p0 = synth.mlp_init(10, 0)
+    mlp = mk.Mlp(ctx, 10, p0)
+    untrained = mk.Mlp(ctx, 10, p0)
+    hist = learned.train(ctx, mlp, X, U, E, steps=600, batch=4096, lr=1e-3, seed=1)
+    assert np.mean(hist[-50:]) < np.mean(hist[:50])
+    test = learned.Problem(ctx, gmesh, *synth.molecule(11, 4))
+    its = {}
+    ref = None
+    for label, pc, net in (("jacobi", "jacobi", None), ("untrained", "learned", untrained),
+                           ("trained", "learned", mlp)):
+        x, rep = test.solve(mk.opts(precision="mixed", precond=pc, mlp=net, rtol=1e-8, inner_rtol=1e-4,
+                                    check_every=1))
+        assert rep["max_rel_residual"] <= 1e-8
+        its[label] = rep["iterations"]
+        xs = x.cpu().numpy()[:, : test.N]
+        ref = xs if ref is None else ref
+        assert rel(xs, ref) < 1e-6
+    print("\nlearned preconditioner, inner iterations to 1e-8 on an unseen molecule:", its,
+          "loss first/last", float(np.mean(hist[:50])), float(np.mean(hist[-50:])))
+    mlp.close()
+    untrained.close()
