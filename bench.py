@@ -1,11 +1,16 @@
 """Benchmark of the fine-mesh correction step (all hot-path rows A1-A8) on the GB300.
 
-python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mk|reference] [--workload mol4_p2] [--precision mixed|fp64]
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mk|reference] [--workload mol4_p2]
+                [--precision mixed|fp64] [--precond learned|jacobi]
 
 Metric: fine-mesh DOF x orbitals solved per second at 1e-8 FP64 relative residual, i.e. n_free * N per step time,
 where one step = prolongation, Hartree Poisson solve, RHS, correction solve, coarse pencil + decomposition,
 augmented projection, small eigensolves and orbital assembly, with inputs resident in HBM.  The working set of a
 step (fine-mesh element matrices and vectors, several hundred MB) is larger than the 129 MB L2.
+
+The headline `value` is the learned-preconditioned mixed-precision form (FP32 operator, BF16 network, FCG(1),
+FP64 refinement); `compare` times the same step with mixed-precision Jacobi PCG and with plain FP64 PCG.  The
+network is trained before any timing on correction solves of other seeded molecules.
 
 --gpus N > 1 (torchrun): replicas only -- each rank solves its own copy of the workload, no collective on the data
 path; value = all ranks' units / max over ranks of the timed region.
@@ -26,6 +31,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "fine-mesh DOF×orbitals solved/s at 1e-8 rel. residual; learned vs plain PCG"
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_apply_patch launch from an ncu capture of the same kernel
+# build on the same workload (None until such a capture exists for the current kernel)
+TRAFFIC = {}
 UNIT = "DOF*orbitals/s"
 
 
@@ -37,6 +45,8 @@ def parse():
     ap.add_argument("--impl", default="mk", choices=["mk", "reference"])
     ap.add_argument("--workload", default="mol4_p2")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precond", default="learned", choices=["learned", "jacobi"],
+                    help="inner preconditioner of the mixed-precision correction solve (learned: FCG(1))")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="step", choices=["step", "apply"],
                     help="apply: time the FP32 element-by-element operator alone (kernel-level roofline)")
@@ -139,6 +149,29 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": reasons, "samples": len(rows)}
 
 
+def train_network(ctx, order, seeds=(3, 4, 5, 6), steps=600, batch=8192):
+    """The learned preconditioner's network, trained before any timing on correction solves of other seeded
+    molecules (never the benchmark molecule) on the mid-size mesh of the same kind (the inputs are
+    resolution-free)."""
+    import numpy as np
+    from paper_2103_02824_gb300 import learned, mk, synth
+    from paper_2103_02824_gb300.step import upload_workload
+    t0 = time.perf_counter()
+    wl = synth.workload("mol4_p2_mid")
+    mesh, _ = upload_workload(ctx, wl)
+    data = [learned.harvest(learned.Problem(ctx, mesh, *synth.molecule(s, 4)), every=2, cap=10) for s in seeds]
+    import torch
+    X, U, E = (torch.cat([d[k] for d in data]) for k in range(3))
+    mlp = mk.Mlp(ctx, 10 if order == 2 else 4, synth.mlp_init(10 if order == 2 else 4, 0))
+    hist = learned.train(ctx, mlp, X, U, E, steps=steps, batch=batch, lr=1e-3, seed=1)
+    del X, U, E, data
+    mesh.close()
+    return mlp, {"molecules": f"synth.molecule(seed, 4), seeds {list(seeds)}, on mol4_p2_mid (fine 16^3 cubes)",
+                 "samples_from": "FP64 PCG iterates 0, 2, ..., 18 of each correction solve",
+                 "steps": steps, "batch": batch, "loss_first50": float(np.mean(hist[:50])),
+                 "loss_last50": float(np.mean(hist[-50:])), "train_s": time.perf_counter() - t0}
+
+
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -160,6 +193,10 @@ def main():
     build.build()
     wl = synth.workload(a.workload)
     ctx = mk.Context(local)
+    precond = "jacobi" if a.precision == "fp64" else a.precond
+    mlp, train_info = (None, None)
+    if precond == "learned":
+        mlp, train_info = train_network(ctx, wl["order"])
     mesh, _ = upload_workload(ctx, wl)
     info = mesh.info
     N, occ = synth.n_orbitals(wl["Z"]), synth.occupations(wl["Z"])
@@ -169,41 +206,44 @@ def main():
     sigma = 1.05 * max(0.0, -theta) + 0.5
     psiH, lamH, basis = coarse_eigenpairs(ctx, mesh, wl["Z"], wl["R"], N, return_basis=True)
     st = CorrectionStep(ctx, mesh, wl["Z"], wl["R"], N, basis=basis)
-    sopts = mk.opts(precision=a.precision, rtol=1e-8, check_every=10)
-    popts = mk.opts(precision=a.precision, rtol=1e-8, check_every=10)
     psiH_dev = torch.zeros((NH, st.ld), dtype=torch.float64, device="cuda")
     psiH_dev[:, :N] = torch.from_numpy(psiH).cuda()
 
-    def step():
-        return st.run(psiH_dev, lamH, occ, sigma, xc=wl["xc"], hartree_bc="multipole", solve_opts=sopts,
-                      poisson_opts=popts)
+    def arm_opts(kind):
+        prec = "fp64" if kind == "fp64" else "mixed"
+        pc = "learned" if kind == "learned" else "jacobi"
+        so = mk.opts(precision=prec, precond=pc, mlp=mlp if pc == "learned" else None, rtol=1e-8, check_every=10)
+        po = mk.opts(precision=prec, rtol=1e-8, check_every=10)
+        return so, po
 
+    def make_step(kind):
+        so, po = arm_opts(kind)
+        return lambda: st.run(psiH_dev, lamH, occ, sigma, xc=wl["xc"], hartree_bc="multipole", solve_opts=so,
+                              poisson_opts=po)
+
+    head_kind = "fp64" if a.precision == "fp64" else precond
+    step = make_step(head_kind)
     for _ in range(a.warmup):
         reps = step()
     torch.cuda.synchronize()
     clocks = Clocks(local)
     clocks.start()
-    mk.profile_enable(ctx, True)
     launches0 = mk.launch_count()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.nvtx.range_push("timed")
-    t0 = time.perf_counter()
     e0.record()
     for _ in range(a.steps):
         reps = step()
     e1.record()
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
-    wall = time.perf_counter() - t0
     if dist:
         dist.barrier()
     launches = mk.launch_count() - launches0
     ms_total = e0.elapsed_time(e1)
-    prof = {k: mk.profile_read(ctx, k) for k in (mk.PROF_APPLY64, mk.PROF_APPLY32, mk.PROF_HALO)}
-    mk.profile_enable(ctx, False)
     clk = clocks.stop()
     t_max = ms_total
     if dist:
@@ -212,6 +252,16 @@ def main():
         t_max = float(tt.item())
     units = float(n_free) * N * a.steps * world
     value = units / (t_max * 1e-3)
+    lam_head = st.lam.cpu().numpy().copy()
+
+    # the dominant kernel's duration, from CUDA events around each application on the launching stream, over a
+    # second pass of the same steps (the events are kept out of the timed region above)
+    mk.profile_enable(ctx, True)
+    for _ in range(a.steps):
+        step()
+    torch.cuda.synchronize()
+    prof = {k: mk.profile_read(ctx, k) for k in (mk.PROF_APPLY64, mk.PROF_APPLY32, mk.PROF_HALO)}
+    mk.profile_enable(ctx, False)
 
     # end to end through the C ABI with host buffers: pinned psi_H in, eigenvalues, coefficients, orbitals out
     h_psiH = torch.zeros((NH, st.ld), dtype=torch.float64).pin_memory()
@@ -232,6 +282,28 @@ def main():
     h2d = h_psiH.numel() * 8
     d2h = (h_lam.numel() + h_coef.numel() + h_psi.numel()) * 8
 
+    # the other forms of the same step on the same GPU: mixed precision with Jacobi, and plain FP64 PCG
+    compare = {}
+    for kind in ("learned", "jacobi", "fp64"):
+        if kind == head_kind or (kind == "learned" and mlp is None):
+            continue
+        stp = make_step(kind)
+        for _ in range(max(1, a.warmup)):
+            r = stp()
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record()
+        for _ in range(a.steps):
+            r = stp()
+        c1.record()
+        torch.cuda.synchronize()
+        ms = c0.elapsed_time(c1) / a.steps
+        lam_k = st.lam.cpu().numpy()
+        compare[kind] = {"value": float(n_free) * N / (ms * 1e-3), "ms_per_step": ms,
+                         "solve_iterations": r["solve"]["iterations"],
+                         "poisson_iterations": r["poisson"]["iterations"] if r["poisson"] else None,
+                         "max_abs_lambda_diff_vs_headline_Ha": float(np.abs(lam_k - lam_head).max())}
+
     # roofline of the dominant kernel (the element-by-element operator application)
     kind = mk.PROF_APPLY32 if prof[mk.PROF_APPLY32][1] > 0 else mk.PROF_APPLY64
     ms_k, n_k = prof[kind]
@@ -244,7 +316,6 @@ def main():
     npack = nloc * (nloc + 1) // 2
     ld = st.ld
     if kind == mk.PROF_APPLY64:
-        # FP64 coloured apply: ALU-bound on GB300's FP64 units; algorithmic flops = 2 * npack-symmetric matvec
         flops = 2.0 * nloc * nloc * E * N
         achieved = flops / (ms_k / n_k * 1e-3) / 1e12 if n_k else None
         peak = 1.196  # measured FP64 FMA throughput (TFLOP/s) of this machine's GB300
@@ -257,9 +328,10 @@ def main():
         achieved = nbytes / (ms_k / n_k * 1e-3) / 1e9 if n_k else None
         peak = peaks.get("hbm_gbs", 6780.7)
         roof = {"kernel": "k_apply_patch (FP32 element-by-element operator)", "bound": "hbm", "achieved": achieved,
-                "peak": peak, "unit": "GB/s", "frac": achieved / peak if achieved else None, "traffic": None,
+                "peak": peak, "unit": "GB/s", "frac": achieved / peak if achieved else None,
+                "traffic": TRAFFIC.get((a.workload, ld)),
                 "applications": n_k, "ms_per_application": ms_k / n_k if n_k else None,
-                "bytes_per_application": nbytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst)"}
+                "bytes_per_application": nbytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst), of measured"}
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -278,17 +350,20 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": t_max / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64" if a.precision == "mixed" else "f64", "data": "synthetic",
-            "config": dict(workload_config(wl, N, n_free, NH, E), precision=a.precision, precond="jacobi",
+            "dtype": "f32+bf16+f64" if head_kind == "learned" else ("f32+f64" if head_kind == "jacobi" else "f64"),
+            "data": "synthetic",
+            "config": dict(workload_config(wl, N, n_free, NH, E), precision=a.precision,
+                           precond="learned (FCG(1))" if head_kind == "learned" else "jacobi",
                            rtol=1e-8, sigma=sigma, l2="working set > L2 (no flush needed)",
                            parallelism="replicas" if world > 1 else "single GPU"),
             "e2e": {"value": float(n_free) * N * a.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "gpu_launches_per_step": launches / a.steps,
             "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
+            "compare": compare, "training": train_info,
             "solve_iterations": solve["iterations"], "solve_max_rel_residual": solve["max_rel_residual"],
             "poisson_iterations": reps["poisson"]["iterations"] if reps["poisson"] else None,
-            "lambda": [float(x) for x in st.lam.cpu().numpy()],
+            "lambda": [float(x) for x in lam_head],
         }
         print(json.dumps(line))
     if dist:
