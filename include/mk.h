@@ -97,6 +97,10 @@ typedef struct {
   int trace_every, trace_cap;
   double* trace_x;
   double* trace_r;
+  /* MIXED only: add the exact coarse-space correction P A_H^-1 P^T r to the preconditioner (two-level additive:
+   * Jacobi or learned fine part plus the Galerkin coarse operator A_H = P^T A P on V_H, inverted densely once
+   * per mesh for the Poisson operator and once per (molecule, sigma) for the correction operator) */
+  int coarse;
 } mk_solve_opts;
 
 typedef struct {

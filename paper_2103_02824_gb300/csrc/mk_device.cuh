@@ -129,6 +129,14 @@ int assemble_diagonal(mk_ctx* ctx, const Level& L, const double* Ae, double* dia
 int apply64(mk_ctx* ctx, const Level& L, const double* Ae, const double* x, double* y, int N, int ld,
             bool mask_boundary, cudaStream_t s);
 
+// out = (float) (P^T A P)^-1, the dense inverse of the Galerkin coarse operator of the fine element matrices A64
+// (synchronises s: the Cholesky factorisation reports a matrix that is not positive definite)
+int coarse_inverse32(mk_ctx* ctx, const mk_mesh* m, const double* A64, float* out, cudaStream_t s);
+// FP32 values of P and P^T for the two-level preconditioner (once per mesh)
+int tl_prepare(const mk_mesh* m, cudaStream_t s);
+// cached FP32 coarse inverse (P^T A P)^-1: key NULL = the mesh's Poisson operator, else (sigma, molecule)
+const float* coarse_inverse_cached(mk_ctx* ctx, const mk_mesh* m, const double* A64, const std::vector<double>* key,
+                                   cudaStream_t s, int* err);
 // dinv = (float)(1 / diag)
 int diag_inverse32(int64_t n, const double* diag, float* dinv, cudaStream_t s);
 // z = learned preconditioner of r (FP32, columns < N); dinv: FP32 inverse diagonal of the operator

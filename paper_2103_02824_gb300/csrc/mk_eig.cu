@@ -16,6 +16,7 @@
 #include <cstdlib>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "mk_device.cuh"
@@ -126,13 +127,9 @@ __device__ __forceinline__ void pair_of(int r, int k, int n2, int* p, int* q) {
 
 // Rotation in the (p,q) plane that zeroes S[p][q]: J = [[c, s], [-s, c]], t = s/c the smaller root of
 // t^2 + 2 theta t - 1 = 0, theta = (S_qq - S_pp) / (2 S_pq).
-__device__ __forceinline__ Rot make_rot(const double* __restrict__ S, int n2, int r, int k) {
-  int p, q;
-  pair_of(r, k, n2, &p, &q);
-  const double apq = S[(int64_t)p * n2 + q];
+__device__ __forceinline__ Rot rot_from(int p, int q, double app, double aqq, double apq) {
   double c = 1.0, s = 0.0;
   if (apq != 0.0) {
-    const double app = S[(int64_t)p * n2 + p], aqq = S[(int64_t)q * n2 + q];
     // FP64 division and square root are slow here: FP32 seeds, then Newton steps that use FP64 FMAs only.  The
     // FP32 seed needs |2 apq| well inside the FP32 range; outside it the exact FP64 division is used.
     const double den = 2.0 * apq;
@@ -167,6 +164,14 @@ __device__ __forceinline__ Rot make_rot(const double* __restrict__ S, int n2, in
     s = t * r;
   }
   return Rot{p, q, c, s};
+}
+
+__device__ __forceinline__ Rot make_rot(const double* __restrict__ S, int n2, int r, int k) {
+  int p, q;
+  pair_of(r, k, n2, &p, &q);
+  const double apq = S[(int64_t)p * n2 + q];
+  if (apq == 0.0) return Rot{p, q, 1.0, 0.0};
+  return rot_from(p, q, S[(int64_t)p * n2 + p], S[(int64_t)q * n2 + q], apq);
 }
 
 // Cyclic Jacobi on the symmetric n2 x n2 matrix (n2 even) in parallel round-robin order, accumulating Q <- Q J.
@@ -706,7 +711,29 @@ int inverse_cholesky(mk_ctx* ctx, int n, const double* MH, double* Linv, int slo
   int h = 0;
   MK_CUDA(cudaMemcpyAsync(&h, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
   MK_CUDA(cudaStreamSynchronize(s));
-  if (h) return fail(MK_ERR_INVALID_ARG, "M_H is not positive definite");
+  if (h) return fail(MK_ERR_INVALID_ARG, "coarse matrix is not positive definite");
+  return MK_OK;
+}
+
+__global__ void k_to_float(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+int coarse_matrices(mk_ctx*, const mk_mesh*, const double*, const double*, double*, double*, int, cudaStream_t);
+
+int coarse_inverse32(mk_ctx* ctx, const mk_mesh* m, const double* A64, float* out, cudaStream_t s) {
+  const int n = (int)m->coarse.n_free;
+  int err = MK_OK;
+  double* X = (double*)scratch(ctx, S_TLX, (size_t)n * n * 3 * sizeof(double), &err);
+  if (!X) return err;
+  double* X2 = X + (size_t)n * n;
+  double* Li = X2 + (size_t)n * n;
+  MK_TRY(coarse_matrices(ctx, m, A64, A64, X, X2, S_TLC, s));        // A_H = P^T A P (twice: one is spare)
+  MK_TRY(inverse_cholesky(ctx, n, X, Li, S_TLW, s));                 // A_H = L L^T, Li = L^-1
+  gemm64(n, n, n, Li, n, 1, Li, n, 0, X2, n, s);                     // A_H^-1 = L^-T L^-1
+  MK_COUNT(), k_to_float<<<(int)(((int64_t)n * n + 255) / 256), 256, 0, s>>>((int64_t)n * n, X2, out);
+  MK_CUDA(cudaGetLastError());
   return MK_OK;
 }
 
@@ -778,7 +805,6 @@ int secular(mk_ctx* ctx, int n, int N, const double* d, const double* V, const d
 }
 
 // At mesh upload: M_H = P^T M P and its inverse Cholesky factor, kept in the mesh handle.
-int coarse_matrices(mk_ctx*, const mk_mesh*, const double*, const double*, double*, double*, int, cudaStream_t);
 
 int mesh_mass_factor(mk_ctx* ctx, mk_mesh* m) {
   const Level& F = m->fine;

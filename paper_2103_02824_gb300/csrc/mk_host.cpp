@@ -614,6 +614,10 @@ int mk_mesh_destroy(mk_mesh* m) {
   free_patches(m->patches);
   cudaFree(m->d_MH_Linv);
   cudaFree(m->d_static);
+  cudaFree(m->d_P_val32);
+  cudaFree(m->d_PT_val32);
+  cudaFree(m->d_cinv_poisson);
+  cudaFree(m->d_cinv_corr);
   if (m->static_ev) cudaEventDestroy(m->static_ev);
   delete m;
   return MK_OK;

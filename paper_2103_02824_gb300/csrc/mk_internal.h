@@ -194,6 +194,13 @@ struct mk_mesh {
   mutable double* d_static = nullptr;
   mutable std::vector<double> static_key;
   mutable cudaEvent_t static_ev = nullptr;  // recorded after the set was written
+  // two-level preconditioner (built on first use): FP32 values of P and P^T, and FP32 dense inverses of the
+  // Galerkin coarse operators P^T K P (Poisson) and P^T (K/2 + M_Vext + sigma M) P (the key: molecule, sigma)
+  mutable float* d_P_val32 = nullptr;
+  mutable float* d_PT_val32 = nullptr;
+  mutable float* d_cinv_poisson = nullptr;
+  mutable float* d_cinv_corr = nullptr;
+  mutable std::vector<double> cinv_corr_key;
 };
 
 namespace mk {
@@ -229,6 +236,8 @@ enum Slot : int {
   S_LHALO,                      // halo partial sums of the learned preconditioner
   S_MLPPART, S_MLPGRAD,         // training: per-block gradient partials, reduced gradient
   S_LDINV,                      // mk_learned_precond: FP64 diagonal, FP32 inverse
+  S_TLC, S_TLX, S_TLW,          // two-level setup: coarse element products, coarse matrices, Cholesky workspace
+  S_TLT,                        // two-level apply: restricted residual and coarse solution (FP32)
   S_COUNT
 };
 void* scratch(mk_ctx* ctx, int slot, size_t bytes, int* err);

@@ -211,6 +211,174 @@ int pack_elements(mk_ctx* ctx, const mk_mesh* m, const double* A64, T* A, cudaSt
 template int pack_elements<float>(mk_ctx*, const mk_mesh*, const double*, float*, cudaStream_t);
 template int pack_elements<double>(mk_ctx*, const mk_mesh*, const double*, double*, cudaStream_t);
 
+// ------------------------------------------------------------------------------------------------ two-level
+// Coarse-space correction of the preconditioner (two-level additive, the coarse space V_H of the method):
+// t = P^T r restricted to the coarse free DOF, y = A_H^-1 t with the dense inverse of the Galerkin coarse operator
+// A_H = P^T A P, then z = (Jacobi or learned part) + P y.  FP32; every sum has a fixed order.
+constexpr int kTLC = 8;  // orbital columns per pass
+
+constexpr int kTLS = 8;  // segments (CTAs) per coarse DOF in the restriction
+
+// tp[k][seg][j] = sum over segment seg of the support of coarse DOF k of P^T[k][i] r[i][j]; one CTA per
+// (coarse DOF, segment), so that every SM has rows to stream.
+__global__ void __launch_bounds__(256) k_tl_restrict(const int32_t* __restrict__ off, const int32_t* __restrict__ col,
+                                                    const float* __restrict__ val, const float* __restrict__ r,
+                                                    int ld, int N, float* __restrict__ tp) {
+  __shared__ float sh[kTLC][8];
+  const int k = blockIdx.x / kTLS, seg = blockIdx.x % kTLS;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int b0 = off[k], len = off[k + 1] - b0;
+  const int b = b0 + (int)((int64_t)len * seg / kTLS), e = b0 + (int)((int64_t)len * (seg + 1) / kTLS);
+  for (int c0 = 0; c0 < N; c0 += kTLC) {
+    const int nc = min(kTLC, N - c0);
+    float acc[kTLC];
+#pragma unroll
+    for (int c = 0; c < kTLC; ++c) acc[c] = 0.f;
+#pragma unroll 4
+    for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
+      const float w = val[i];
+      const float* ri = r + (int64_t)col[i] * ld + c0;
+#pragma unroll
+      for (int c = 0; c < kTLC; ++c)
+        if (c < nc) acc[c] = fmaf(w, ri[c], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < kTLC; ++c) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], o);
+      if (lane == 0) sh[c][warp] = acc[c];
+    }
+    __syncthreads();
+    if (threadIdx.x < nc) {
+      float v = 0.f;
+      for (int w = 0; w < nw; ++w) v += sh[threadIdx.x][w];
+      tp[((int64_t)k * kTLS + seg) * ld + c0 + threadIdx.x] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// y[k][j] = sum_l Ainv[k][l] t[l][j] with t[l][j] = sum over segments of tp[l][seg][j] (in order); one warp per
+// coarse DOF k.
+__global__ void k_tl_coarse(int nH, const float* __restrict__ Ainv, const float* __restrict__ tp, int ld, int N,
+                            float* __restrict__ y) {
+  const int k = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (k >= nH) return;
+  for (int c0 = 0; c0 < N; c0 += kTLC) {
+    const int nc = min(kTLC, N - c0);
+    float acc[kTLC];
+#pragma unroll
+    for (int c = 0; c < kTLC; ++c) acc[c] = 0.f;
+    for (int l = lane; l < nH; l += 32) {
+      const float a = Ainv[(int64_t)k * nH + l];
+#pragma unroll
+      for (int c = 0; c < kTLC; ++c)
+        if (c < nc) {
+          float t = 0.f;
+#pragma unroll
+          for (int sg = 0; sg < kTLS; ++sg) t += tp[((int64_t)l * kTLS + sg) * ld + c0 + c];
+          acc[c] = fmaf(a, t, acc[c]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < kTLC; ++c) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], o);
+    }
+    if (lane == 0)
+#pragma unroll
+      for (int c = 0; c < kTLC; ++c)
+        if (c < nc) y[(int64_t)k * ld + c0 + c] = acc[c];
+  }
+}
+
+// z[i][j] = (add ? z[i][j] : r[i][j] / diag[i]) + sum_q P[i][q] y[q][j] for j < N; boundary rows 0.
+__global__ void k_tl_prolong(int64_t n, const int32_t* __restrict__ off, const int32_t* __restrict__ col,
+                             const float* __restrict__ val, const float* __restrict__ y,
+                             const float* __restrict__ dinv, const uint8_t* __restrict__ bnd,
+                             const float* __restrict__ r, float* __restrict__ z, int ld, int N, int add) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * N) return;
+  const int64_t i = t / N;
+  const int j = (int)(t - i * N);
+  const int64_t idx = i * ld + j;
+  if (bnd[i]) {
+    z[idx] = 0.f;
+    return;
+  }
+  float acc = add ? z[idx] : dinv[i] * r[idx];
+  for (int q = off[i]; q < off[i + 1]; ++q) acc = fmaf(val[q], y[(int64_t)col[q] * ld + j], acc);
+  z[idx] = acc;
+}
+
+__global__ void k_f64_to_f32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+// FP32 copies of the values of P and P^T (built once per mesh, before any graph capture uses them).
+int tl_prepare(const mk_mesh* m, cudaStream_t s) {
+  if (m->d_P_val32) return MK_OK;
+  const int64_t nP = m->PT_nnz;  // P and P^T hold the same entries
+  float *a = nullptr, *b = nullptr;
+  if (cudaMalloc(&a, (size_t)std::max<int64_t>(nP, 1) * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&b, (size_t)std::max<int64_t>(nP, 1) * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(a);
+    return fail(MK_ERR_OOM, "two-level preconditioner: allocation failed");
+  }
+  MK_COUNT(), k_f64_to_f32<<<(int)((nP + 255) / 256), 256, 0, s>>>(nP, m->d_P_val, a);
+  MK_COUNT(), k_f64_to_f32<<<(int)((nP + 255) / 256), 256, 0, s>>>(nP, m->d_PT_val, b);
+  MK_CUDA(cudaGetLastError());
+  m->d_P_val32 = a;
+  m->d_PT_val32 = b;
+  return MK_OK;
+}
+
+// Cached FP32 coarse inverse for the operator of A64: the mesh's Poisson operator (key empty) or the correction
+// operator of a molecule and shift (key = Z, R, sigma).  Built on first use.
+const float* coarse_inverse_cached(mk_ctx* ctx, const mk_mesh* m, const double* A64, const std::vector<double>* key,
+                                   cudaStream_t s, int* err) {
+  const int64_t nH = m->coarse.n_free;
+  float** slot = key ? &m->d_cinv_corr : &m->d_cinv_poisson;
+  if (*slot && (!key || m->cinv_corr_key == *key)) return *slot;
+  if (*slot && key && cudaDeviceSynchronize() != cudaSuccess) {  // earlier users of the old inverse finish first
+    *err = fail(MK_ERR_CUDA, "two-level preconditioner: cudaDeviceSynchronize failed");
+    return nullptr;
+  }
+  if (!*slot && cudaMalloc(slot, (size_t)nH * nH * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    *slot = nullptr;
+    *err = fail(MK_ERR_OOM, "two-level preconditioner: allocation failed");
+    return nullptr;
+  }
+  const int r = coarse_inverse32(ctx, m, A64, *slot, s);
+  if (r != MK_OK) {
+    *err = r;
+    if (key) m->cinv_corr_key.clear();
+    return nullptr;
+  }
+  if (key) m->cinv_corr_key = *key;
+  return *slot;
+}
+
+// z = (add ? z : D^-1 r) + P A_H^-1 P^T r for columns < N.
+static int twolevel_apply(mk_ctx* ctx, const mk_mesh* m, const float* cinv, const float* dinv, const float* r,
+                          float* z, int ld, int N, bool add, cudaStream_t s) {
+  const Level& L = m->fine;
+  const int nH = (int)m->coarse.n_free;
+  int err = MK_OK;
+  float* t = (float*)scratch(ctx, S_TLT, (size_t)(kTLS + 1) * nH * ld * sizeof(float), &err);
+  if (!t) return err;
+  float* y = t + (size_t)kTLS * nH * ld;
+  MK_COUNT(), k_tl_restrict<<<nH * kTLS, 256, 0, s>>>(m->d_PT_off, m->d_PT_col, m->d_PT_val32, r, ld, N, t);
+  MK_COUNT(), k_tl_coarse<<<(nH * 32 + 255) / 256, 256, 0, s>>>(nH, cinv, t, ld, N, y);
+  MK_COUNT(), k_tl_prolong<<<(int)((L.n_nodes * N + 255) / 256), 256, 0, s>>>(
+      L.n_nodes, m->d_P_off, m->d_P_col, m->d_P_val32, y, dinv, L.d_boundary, r, z, ld, N, add ? 1 : 0);
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
 // ------------------------------------------------------------------------------------------------ mixed PCG
 struct MixState {
   double rz, pq, rr, rr0, alpha, beta, rr64, bn;
@@ -496,7 +664,7 @@ __global__ void __launch_bounds__(kFinThreads) k_mixed_finalize(int mode, const 
 }
 
 int pcg_mixed(mk_ctx* ctx, const mk_mesh* m, const double* A64, const double* b, double* x, int ld, int N,
-              const mk_solve_opts& o, mk_solve_report* rep, cudaStream_t s);
+              const mk_solve_opts& o, mk_solve_report* rep, cudaStream_t s, const float* cinv);
 
 int solve_mixed(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, double sigma, const double* b,
                 const double*, const double*, double* x, int ld, int N, const mk_solve_opts& o, mk_solve_report* rep,
@@ -512,28 +680,40 @@ int solve_mixed(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, double si
   const double* H0 = static_matrices(ctx, m, mol, s, &err);
   if (!H0) return err;
   MK_TRY(element_matrices(ctx, L, nullptr, 0.0, 0.0, sigma, nullptr, A64, s, H0));
-  return pcg_mixed(ctx, m, A64, b, x, ld, N, o, rep, s);
+  const float* cinv = nullptr;
+  if (o.coarse) {  // two-level: the coarse inverse of this molecule's shifted operator (cached)
+    std::vector<double> key;
+    key.push_back(sigma);
+    for (int k = 0; k < mol->n_nuclei; ++k) {
+      key.push_back(mol->Z[k]);
+      for (int c = 0; c < 3; ++c) key.push_back(mol->R[3 * k + c]);
+    }
+    MK_TRY(tl_prepare(m, s));
+    cinv = coarse_inverse_cached(ctx, m, A64, &key, s, &err);
+    if (!cinv) return err;
+  }
+  return pcg_mixed(ctx, m, A64, b, x, ld, N, o, rep, s, cinv);
 }
 
 // FP32 inner Jacobi-PCG on the patch operator built from the FP64 element matrices A64 (element order), FP64
 // residual b - A x and iterative refinement of x until every column meets o.rtol.
 static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const double* b, double* x, int ld, int N,
-                        const mk_solve_opts& o, mk_solve_report* rep, cudaStream_t s);
+                        const mk_solve_opts& o, mk_solve_report* rep, cudaStream_t s, const float* cinv);
 
 // Runs the solve on the context's own stream (CUDA graphs cannot be captured on the legacy default stream), after
 // everything already queued on the caller's stream and before anything queued there afterwards.
 int pcg_mixed(mk_ctx* ctx, const mk_mesh* m, const double* A64, const double* b, double* x, int ld, int N,
-              const mk_solve_opts& o, mk_solve_report* rep, cudaStream_t caller) {
+              const mk_solve_opts& o, mk_solve_report* rep, cudaStream_t caller, const float* cinv) {
   MK_CUDA(cudaEventRecord(ctx->solve_ev[0], caller));
   MK_CUDA(cudaStreamWaitEvent(ctx->solve_stream, ctx->solve_ev[0], 0));
-  const int r = pcg_mixed_on(ctx, m, A64, b, x, ld, N, o, rep, ctx->solve_stream);
+  const int r = pcg_mixed_on(ctx, m, A64, b, x, ld, N, o, rep, ctx->solve_stream, cinv);
   MK_CUDA(cudaEventRecord(ctx->solve_ev[1], ctx->solve_stream));
   MK_CUDA(cudaStreamWaitEvent(caller, ctx->solve_ev[1], 0));
   return r;
 }
 
 static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const double* b, double* x, int ld, int N,
-                        const mk_solve_opts& o, mk_solve_report* rep, cudaStream_t s) {
+                        const mk_solve_opts& o, mk_solve_report* rep, cudaStream_t s, const float* cinv) {
   MK_ARG(ld <= 256, "mixed path: ld must be <= 256");
   const Level& L = m->fine;
   const int64_t n = L.n_nodes;
@@ -547,7 +727,10 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
   float* p = (float*)scratch(ctx, S_P32, (size_t)n * ld * sizeof(float), &err);
   float* q = (float*)scratch(ctx, S_Q32, (size_t)n * ld * sizeof(float), &err);
   float* d = (float*)scratch(ctx, S_X32, (size_t)n * ld * sizeof(float), &err);
-  const bool fcg = o.precond == MK_PRECOND_LEARNED && o.mlp;
+  const bool learned = o.precond == MK_PRECOND_LEARNED && o.mlp;
+  // an explicit preconditioned residual z (FCG(1), which is PCG for a fixed SPD preconditioner) whenever the
+  // preconditioner is more than the diagonal: learned, two-level, or both
+  const bool fcg = learned || cinv != nullptr;
   float* zb = fcg ? (float*)scratch(ctx, S_Z32, (size_t)n * ld * sizeof(float), &err) : nullptr;
   if (fcg && !zb) return err;
   const int nblk = red_blocks(ctx);
@@ -578,6 +761,7 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
   // the operator's halo buffer must exist before a capture starts (nothing may allocate inside a capture)
   if (!scratch(ctx, S_HALO, (size_t)std::max<int64_t>(m->patches.n_halo_slots, 1) * ld * sizeof(float), &err))
     return err;
+  if (cinv && !scratch(ctx, S_TLT, (size_t)(kTLS + 1) * m->coarse.n_free * ld * sizeof(float), &err)) return err;
   if (fcg) {
     if (!scratch(ctx, S_LHALO, (size_t)std::max<int64_t>(m->patches.n_halo_slots, 1) * ld * sizeof(float), &err))
       return err;
@@ -594,8 +778,16 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
     if (!any) { converged = true; break; }
     if (refine >= max_refine || total_it >= o.maxit) break;
     ++refine;
+    auto precond = [&]() -> int {  // zb = M(r)
+      if (learned) {
+        MK_TRY(learned_apply(ctx, m, o.mlp, dinv, r, zb, ld, N, o.mlp_precision, s));
+        if (cinv) MK_TRY(twolevel_apply(ctx, m, cinv, dinv, r, zb, ld, N, true, s));
+        return MK_OK;
+      }
+      return twolevel_apply(ctx, m, cinv, dinv, r, zb, ld, N, false, s);
+    };
     if (fcg) {
-      MK_TRY(learned_apply(ctx, m, o.mlp, dinv, r, zb, ld, N, o.mlp_precision, s));
+      MK_TRY(precond());
       MK_CUDA(cudaMemcpyAsync(p, zb, (size_t)n * ld * sizeof(float), cudaMemcpyDeviceToDevice, s));
       MK_COUNT(), k_mixed_pq<<<nblk, th, 0, s>>>(n, r, r, ld, part);
       MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(7, part, nblk, 1, ld, N, st, o.rtol, inner2);
@@ -614,7 +806,7 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
         MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(4, part, nblk, 2, ld, N, st, o.rtol, inner2);
         MK_COUNT(), k_fcg_update<<<nblk, th, 0, s>>>(n, st, p, q, d, r, ld, part);
         MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(5, part, nblk, 1, ld, N, st, o.rtol, inner2);
-        MK_TRY(learned_apply(ctx, m, o.mlp, dinv, r, zb, ld, N, o.mlp_precision, s));
+        MK_TRY(precond());
         MK_COUNT(), k_mixed_pq<<<nblk, th, 0, s>>>(n, zb, q, ld, part);
         MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(6, part, nblk, 1, ld, N, st, o.rtol, inner2);
         MK_COUNT(), k_fcg_p<<<gb, 256, 0, s>>>(n, st, zb, p, ld);

@@ -17,7 +17,7 @@ int multipole_boundary(mk_ctx*, const Level&, const double*, const double*, int,
 int solve_mixed(mk_ctx*, const mk_mesh*, const mk_molecule*, double, const double*, const double*, const double*,
                 double*, int, int, const mk_solve_opts&, mk_solve_report*, cudaStream_t);
 int pcg_mixed(mk_ctx*, const mk_mesh*, const double*, const double*, double*, int, int, const mk_solve_opts&,
-              mk_solve_report*, cudaStream_t);
+              mk_solve_report*, cudaStream_t, const float* cinv = nullptr);
 
 // Per-column PCG state on the device.
 struct ColState {
@@ -210,6 +210,7 @@ int pcg64(mk_ctx* ctx, const Level& L, const double* Ae, const double* diag, con
 
 static bool valid_opts(const mk_solve_opts* o) {
   if (!o || !(o->rtol > 0) || o->maxit <= 0) return false;
+  if (o->coarse && o->precision != MK_PREC_MIXED) return false;
   if (o->precond == MK_PRECOND_LEARNED)
     return o->precision == MK_PREC_MIXED && o->mlp != nullptr &&
            (o->mlp_precision == MK_MLP_FP32 || o->mlp_precision == MK_MLP_BF16);
@@ -297,7 +298,13 @@ int mk_hartree_poisson(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, c
   coef.v[0] = 1.0;
   MK_COUNT(), k_combine_rhs<<<(int)((L.n_nodes + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, F, y, coef, F, 1, 1);
   MK_CUDA(cudaMemsetAsync(d, 0, L.n_nodes * sizeof(double), s));
-  int r = opts->precision == MK_PREC_MIXED ? pcg_mixed(ctx, m, Ke, F, d, 1, 1, *opts, report, s)
+  const float* cinv = nullptr;
+  if (opts->precision == MK_PREC_MIXED && opts->coarse) {  // two-level: the coarse inverse of P^T K P (cached)
+    MK_TRY(tl_prepare(m, s));
+    cinv = coarse_inverse_cached(ctx, m, Ke, nullptr, s, &err);
+    if (!cinv) return err;
+  }
+  int r = opts->precision == MK_PREC_MIXED ? pcg_mixed(ctx, m, Ke, F, d, 1, 1, *opts, report, s, cinv)
                                            : pcg64(ctx, L, Ke, diag, F, d, 1, 1, *opts, report, s);
   MK_COUNT(), k_axpy_interior<<<(int)((L.n_nodes + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, d, w);
   MK_CUDA(cudaGetLastError());

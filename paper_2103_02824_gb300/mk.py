@@ -54,7 +54,7 @@ class mk_solve_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("precond", C.c_int), ("rtol", C.c_double), ("maxit", C.c_int),
                 ("inner_rtol", C.c_double), ("max_refine", C.c_int), ("check_every", C.c_int),
                 ("mlp", C.c_void_p), ("mlp_precision", C.c_int), ("trace_every", C.c_int), ("trace_cap", C.c_int),
-                ("trace_x", C.c_void_p), ("trace_r", C.c_void_p)]
+                ("trace_x", C.c_void_p), ("trace_r", C.c_void_p), ("coarse", C.c_int)]
 
 
 class mk_solve_report(C.Structure):
@@ -214,11 +214,13 @@ MK_MLP_FP32, MK_MLP_BF16 = 0, 1
 
 
 def opts(precision="fp64", precond="jacobi", rtol=1e-8, maxit=20000, inner_rtol=1e-4, max_refine=20, check_every=10,
-         mlp=None, mlp_precision="bf16", trace=None):
+         mlp=None, mlp_precision="bf16", trace=None, coarse=False):
     """Solver options.  mlp: an Mlp (precond='learned'); trace: (every, x_buf, r_buf) device float64 tensors of
-    shape [cap, n_nodes, ld] receiving iterates and residuals of the FP64 PCG."""
+    shape [cap, n_nodes, ld] receiving iterates and residuals of the FP64 PCG; coarse: add the two-level coarse
+    correction (mixed precision)."""
     o = mk_solve_opts(MK_PREC_MIXED if precision == "mixed" else MK_PREC_FP64, MK_PRECOND[precond], rtol, maxit,
                       inner_rtol, max_refine, check_every)
+    o.coarse = 1 if coarse else 0
     if mlp is not None:
         o.mlp = mlp.h.value
         o.mlp_precision = MK_MLP_BF16 if mlp_precision == "bf16" else MK_MLP_FP32

@@ -369,3 +369,40 @@ def test_breakdown_and_not_converged(ctx, torch):
                                  allow=(mk.MK_ERR_NOT_CONVERGED,))
     assert rep["code"] == mk.MK_ERR_NOT_CONVERGED and rep["iterations"] == 2
     assert rep["max_rel_residual"] > 1e-12
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_twolevel_solves(ctx, torch, name):
+    """Mixed-precision solves with the two-level coarse correction (Jacobi or learned fine part) reach the FP64
+    targets and the oracle's solutions."""
+    from paper_2103_02824_gb300 import mk, synth
+    c = case(name)
+    m = gpu_mesh(ctx, name)
+    N, ld = c["N"], 8
+    mol = mk.Molecule(c["wl"]["Z"], c["wl"]["R"])
+    rhs = dev(torch, padded(c["out"]["rhs"], ld))
+    x0 = dev(torch, padded(c["out"]["u"], ld))
+    its = {}
+    for label, kw in (("jacobi", {}), ("twolevel", {"coarse": True})):
+        x = x0.clone()
+        rep = mk.mk_correction_solve(ctx, m, mol, c["sigma"], rhs, x, N,
+                                     opt=mk.opts(precision="mixed", rtol=1e-12, inner_rtol=1e-4, check_every=5, **kw))
+        assert rep["max_rel_residual"] <= 1e-12
+        assert rel(x.cpu().numpy()[:, :N], c["out"]["psihat"]) < 1e-8
+        its[label] = rep["iterations"]
+    print("\ninner iterations", name, its)
+    mlp = mk.Mlp(ctx, c["wl"]["order"] == 2 and 10 or 4, synth.mlp_init(10 if c["wl"]["order"] == 2 else 4, 0))
+    x = x0.clone()
+    rep = mk.mk_correction_solve(ctx, m, mol, c["sigma"], rhs, x, N,
+                                 opt=mk.opts(precision="mixed", precond="learned", mlp=mlp, coarse=True, rtol=1e-12,
+                                             inner_rtol=1e-4, check_every=5))
+    assert rep["max_rel_residual"] <= 1e-12
+    assert rel(x.cpu().numpy()[:, :N], c["out"]["psihat"]) < 1e-8
+    mlp.close()
+    # Poisson with the two-level preconditioner against the oracle's Hartree potential
+    u = dev(torch, padded(c["out"]["u"], ld))
+    w = torch.zeros(c["level"].fine.n_nodes, dtype=torch.float64, device="cuda")
+    rp = mk.mk_hartree_poisson(ctx, m, u, c["occ"], N, w,
+                               opt=mk.opts(precision="mixed", rtol=1e-12, check_every=5, coarse=True))
+    assert rp["max_rel_residual"] <= 1e-12
+    assert rel(w.cpu().numpy(), c["out"]["w"]) < 1e-9
