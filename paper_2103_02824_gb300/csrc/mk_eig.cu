@@ -125,37 +125,20 @@ __device__ __forceinline__ void pair_of(int r, int k, int n2, int* p, int* q) {
   *q = max(a, b);
 }
 
-// Rotation in the (p,q) plane that zeroes S[p][q]: J = [[c, s], [-s, c]], t = s/c the smaller root of
-// t^2 + 2 theta t - 1 = 0, theta = (S_qq - S_pp) / (2 S_pq).
+// Rotation in the (p,q) plane that (nearly) zeroes S[p][q]: J = [[c, s], [-s, c]] with t = s/c the smaller root of
+// t^2 + 2 theta t - 1 = 0, theta = (S_qq - S_pp) / (2 S_pq).  Only the angle is taken in FP32 (GB300's FP64 rate
+// is low and every CTA derives every rotation of a round); c = (1 + t^2)^-1/2 and s = t c are formed from that t in
+// FP64 (FP32 seed, two Newton steps), so the rotation is orthogonal to FP64 precision.  The slightly inexact angle
+// leaves about 6e-8 |S_pq| behind, which the updates keep exactly and the next sweep removes.
 __device__ __forceinline__ Rot rot_from(int p, int q, double app, double aqq, double apq) {
   double c = 1.0, s = 0.0;
-  if (apq != 0.0) {
-    // FP64 division and square root are slow here: FP32 seeds, then Newton steps that use FP64 FMAs only.  The
-    // FP32 seed needs |2 apq| well inside the FP32 range; outside it the exact FP64 division is used.
-    const double den = 2.0 * apq;
-    double theta;
-    if (fabs(den) > 1e-30 && fabs(den) < 1e30) {
-      double rd = (double)(1.0f / (float)den);
-      rd = rd * (2.0 - den * rd);
-      rd = rd * (2.0 - den * rd);
-      theta = (aqq - app) * rd;
-    } else {
-      theta = (aqq - app) / den;
-    }
-    double t;
-    if (!(fabs(theta) <= 1e15)) {
-      t = isfinite(theta) ? 0.5 / theta : 0.0;
-    } else {
-      const float tf = (float)theta;
-      t = (double)(copysignf(1.0f, tf) / (fabsf(tf) + sqrtf(tf * tf + 1.0f)));
-      for (int it = 0; it < 2; ++it) {  // root of t^2 + 2 theta t - 1 with |t| <= 1
-        const double f = t * t + 2.0 * theta * t - 1.0;
-        const double g = 2.0 * (t + theta);
-        double rg = (double)(1.0f / (float)g);
-        rg = rg * (2.0 - g * rg);
-        t -= f * rg;
-      }
-    }
+  const float fa = (float)apq;
+  if (fa != 0.0f) {
+    const float theta = (float)(aqq - app) / (2.0f * fa);
+    float tf;
+    if (!(fabsf(theta) <= 1e18f)) tf = isfinite(theta) ? 0.5f / theta : 0.0f;  // theta^2 would overflow
+    else tf = copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.0f));
+    const double t = (double)tf;
     const double x = 1.0 + t * t;
     double r = (double)rsqrtf((float)x);
     r = r * (1.5 - 0.5 * x * r * r);
@@ -178,12 +161,13 @@ __device__ __forceinline__ Rot make_rot(const double* __restrict__ S, int n2, in
 // Cooperative launch.  Round r reads S_in and writes S_out (ping-pong): every CTA first derives all n2/2
 // rotations of the round from S_in into shared memory, then updates its share of the disjoint 2x2 blocks and
 // of Q; one grid barrier per round.  *final_buf tells which buffer holds the result.
-__global__ void k_jacobi(int n2, double* __restrict__ S0, double* __restrict__ S1, double* __restrict__ Q,
+constexpr int kJacobiThreads = 512;  // half an SM: the solve kernels of the other stream still fit beside it
+__global__ void __launch_bounds__(kJacobiThreads) k_jacobi(int n2, double* __restrict__ S0, double* __restrict__ S1, double* __restrict__ Q,
                          double* __restrict__ red, int max_sweeps, double tol, int* __restrict__ info) {
   cg::grid_group grid = cg::this_grid();
   extern __shared__ unsigned char smem_raw[];
   Rot* rot = reinterpret_cast<Rot*>(smem_raw);
-  __shared__ double sh[256];
+  __shared__ double sh[kJacobiThreads];
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nth = (int64_t)gridDim.x * blockDim.x;
   const int np = n2 / 2;
@@ -219,8 +203,20 @@ __global__ void k_jacobi(int n2, double* __restrict__ S0, double* __restrict__ S
     for (int r = 0; r < n2 - 1; ++r) {
       for (int k = threadIdx.x; k < np; k += blockDim.x) rot[k] = make_rot(Sin, n2, r, k);
       __syncthreads();
-      for (int64_t t = tid; t < nblk2; t += nth) {
-        int k1 = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) / 2.0);
+      // one index space for the 2x2 block updates of S and the column-pair updates of Q, so that every
+      // thread issues its loads at once (one memory latency per round instead of two)
+      for (int64_t t = tid; t < nblk2 + (int64_t)n2 * np; t += nth) {
+        if (t >= nblk2) {
+          const int64_t u = t - nblk2;
+          const int row = (int)(u / np), k = (int)(u % np);
+          const Rot R = rot[k];
+          const double vp = Q[(int64_t)row * n2 + R.p], vq = Q[(int64_t)row * n2 + R.q];
+          Q[(int64_t)row * n2 + R.p] = R.c * vp - R.s * vq;
+          Q[(int64_t)row * n2 + R.q] = R.s * vp + R.c * vq;
+          continue;
+        }
+        // (k1, k2), k2 <= k1, from t = k1 (k1 + 1) / 2 + k2: an FP32 estimate, corrected exactly in integers
+        int k1 = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
         while ((int64_t)(k1 + 1) * (k1 + 2) / 2 <= t) ++k1;
         while ((int64_t)k1 * (k1 + 1) / 2 > t) --k1;
         const int k2 = (int)(t - (int64_t)k1 * (k1 + 1) / 2);  // k2 <= k1
@@ -229,12 +225,10 @@ __global__ void k_jacobi(int n2, double* __restrict__ S0, double* __restrict__ S
         const double b10 = Sin[(int64_t)A.q * n2 + B.p], b11 = Sin[(int64_t)A.q * n2 + B.q];
         const double r00 = A.c * b00 - A.s * b10, r01 = A.c * b01 - A.s * b11;
         const double r10 = A.s * b00 + A.c * b10, r11 = A.s * b01 + A.c * b11;
-        double n00 = B.c * r00 - B.s * r01, n01 = B.s * r00 + B.c * r01;
-        double n10 = B.c * r10 - B.s * r11, n11 = B.s * r10 + B.c * r11;
-        if (k1 == k2) {
-          n01 = 0.0;
-          n10 = 0.0;
-        }
+        const double n00 = B.c * r00 - B.s * r01, n01 = B.s * r00 + B.c * r01;
+        double n10 = B.c * r10 - B.s * r11;
+        const double n11 = B.s * r10 + B.c * r11;
+        if (k1 == k2) n10 = n01;  // the diagonal block stays exactly symmetric
         Sout[(int64_t)A.p * n2 + B.p] = n00;
         Sout[(int64_t)A.p * n2 + B.q] = n01;
         Sout[(int64_t)A.q * n2 + B.p] = n10;
@@ -245,13 +239,6 @@ __global__ void k_jacobi(int n2, double* __restrict__ S0, double* __restrict__ S
           Sout[(int64_t)B.p * n2 + A.q] = n10;
           Sout[(int64_t)B.q * n2 + A.q] = n11;
         }
-      }
-      for (int64_t t = tid; t < (int64_t)n2 * np; t += nth) {
-        const int row = (int)(t / np), k = (int)(t % np);
-        const Rot R = rot[k];
-        const double vp = Q[(int64_t)row * n2 + R.p], vq = Q[(int64_t)row * n2 + R.q];
-        Q[(int64_t)row * n2 + R.p] = R.c * vp - R.s * vq;
-        Q[(int64_t)row * n2 + R.q] = R.s * vp + R.c * vq;
       }
       grid.sync();
       double* tmp = Sin;
@@ -765,7 +752,7 @@ int decompose(mk_ctx* ctx, int n, const double* X, bool w_is_x, const double* AH
   const size_t smem = (size_t)np * sizeof(Rot);
   if (smem > 48 * 1024) MK_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  MK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi, 256, smem));
+  MK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi, kJacobiThreads, smem));
   MK_ARG(per_sm >= 1, "mk: Jacobi kernel cannot be resident (coarse space too large)");
   int grid = std::min(ctx->n_sms, 4096);
   int max_sweeps = 60;
@@ -773,7 +760,7 @@ int decompose(mk_ctx* ctx, int n, const double* X, bool w_is_x, const double* AH
   int n2v = n2;
   void* args[] = {&n2v, &S0, &S1, &Q, &red, &max_sweeps, &tol, &info};
   MK_COUNT();
-  MK_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi, grid, 256, args, smem, s));
+  MK_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi, grid, kJacobiThreads, args, smem, s));
   if (std::getenv("MK_DEBUG")) {
     int h[2];
     cudaMemcpyAsync(h, info, sizeof(h), cudaMemcpyDeviceToHost, s);
