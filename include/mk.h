@@ -213,9 +213,10 @@ int mk_augmented_project(mk_ctx* ctx, const mk_mesh* mesh, const mk_molecule* mo
                          double* beta, double* gamma, double* gramA, double* gramM, void* stream);
 
 /* The coarse blocks alone: AH = P^T H P, MH = P^T M P [N_H*N_H] for the frozen potential vq (Eq. (Adef); the
- * paper assembles these on the fine mesh "in advance").  They do not depend on psi^, so a caller may compute
- * them, and decompose them, on a second stream while mk_correction_solve runs.  vq may be NULL (bare
- * Hamiltonian K/2 + V_ext).  Uses its own scratch, separate from mk_correction_solve's. */
+ * coarse blocks are assembled on the fine mesh, ahead of the augmented solve).  They do not depend on psi^, so a
+ * caller may compute them, and decompose them, on a second stream while mk_correction_solve runs.  vq may be NULL
+ * (bare Hamiltonian K/2 + V_ext).  MH may be NULL: M_H does not depend on the density, and the decomposition uses
+ * the factor of M_H kept by the mesh handle.  Uses its own scratch, separate from mk_correction_solve's. */
 int mk_coarse_pencil(mk_ctx* ctx, const mk_mesh* mesh, const mk_molecule* mol, const double* vq, double* AH,
                      double* MH, void* stream);
 

@@ -125,9 +125,15 @@ int element_matrices(mk_ctx* ctx, const Level& L, const mk_molecule* mol, double
 const double* static_matrices(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, cudaStream_t s, int* err);
 // assembled diagonal of the packed element matrices, boundary rows set to 1
 int assemble_diagonal(mk_ctx* ctx, const Level& L, const double* Ae, double* diag, cudaStream_t s);
-// y = A x (y zeroed first), boundary rows of y zeroed if mask_boundary
-int apply64(mk_ctx* ctx, const Level& L, const double* Ae, const double* x, double* y, int N, int ld,
+// y = A x on the fine mesh (all ld columns) with the FP64 patch operator, from element matrices Ae in element
+// order; boundary rows of y zeroed if mask_boundary
+int apply64(mk_ctx* ctx, const mk_mesh* m, const double* Ae, const double* x, double* y, int N, int ld,
             bool mask_boundary, cudaStream_t s);
+// the patch operator (mk_mixed.cu): element matrices packed in patch order, then y = A x
+template <typename T>
+int pack_elements(mk_ctx* ctx, const mk_mesh* m, const double* A64, T* A, cudaStream_t s);
+template <typename T>
+int apply_patch(mk_ctx* ctx, const mk_mesh* m, const T* Ae, const T* x, T* y, int ld, bool mask, cudaStream_t s);
 
 // out = (float) (P^T A P)^-1, the dense inverse of the Galerkin coarse operator of the fine element matrices A64
 // (synchronises s: the Cholesky factorisation reports a matrix that is not positive definite)

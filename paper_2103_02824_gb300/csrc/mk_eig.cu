@@ -716,7 +716,7 @@ int coarse_inverse32(mk_ctx* ctx, const mk_mesh* m, const double* A64, float* ou
   if (!X) return err;
   double* X2 = X + (size_t)n * n;
   double* Li = X2 + (size_t)n * n;
-  MK_TRY(coarse_matrices(ctx, m, A64, A64, X, X2, S_TLC, s));        // A_H = P^T A P (twice: one is spare)
+  MK_TRY(coarse_matrices(ctx, m, A64, nullptr, X, nullptr, S_TLC, s));  // A_H = P^T A P
   MK_TRY(inverse_cholesky(ctx, n, X, Li, S_TLW, s));                 // A_H = L L^T, Li = L^-1
   gemm64(n, n, n, Li, n, 1, Li, n, 0, X2, n, s);                     // A_H^-1 = L^-T L^-1
   MK_COUNT(), k_to_float<<<(int)(((int64_t)n * n + 255) / 256), 256, 0, s>>>((int64_t)n * n, X2, out);
@@ -803,7 +803,7 @@ int mesh_mass_factor(mk_ctx* ctx, mk_mesh* m) {
   if (!Me || !MH) return err;
   cudaStream_t s = 0;
   MK_TRY(element_matrices(ctx, F, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s));
-  MK_TRY(coarse_matrices(ctx, m, Me, Me, MH, MH + (size_t)n * n, S_COARSE2, s));
+  MK_TRY(coarse_matrices(ctx, m, Me, nullptr, MH, nullptr, S_COARSE2, s));
   if (cudaMalloc(&m->d_MH_Linv, (size_t)n * n * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return fail(MK_ERR_OOM, "mesh upload: M_H factor allocation failed");
@@ -879,7 +879,7 @@ int mk_orbital_assemble(mk_ctx* ctx, const mk_mesh* m, const double* coef, const
   MK_COUNT(), k_orbitals<<<(int)((work + 255) / 256), 256, 0, s>>>(F.n_nodes, m->d_P_off, m->d_P_col, m->d_P_val, F.d_boundary,
                                                        coef, (int)m->coarse.n_free, psihat, N, ld, psi);
   MK_TRY(element_matrices(ctx, F, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s));
-  MK_TRY(apply64(ctx, F, Me, u, Mu, N, ld, true, s));
+  MK_TRY(apply64(ctx, m, Me, u, Mu, N, ld, true, s));
   MK_TRY(column_dots(ctx, F.n_nodes, psi, Mu, N, ld, dots, s));
   MK_COUNT(), k_flip<<<(int)((work + 255) / 256), 256, 0, s>>>(F.n_nodes, dots, psi, N, ld);
   MK_CUDA(cudaGetLastError());

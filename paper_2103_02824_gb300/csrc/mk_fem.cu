@@ -3,6 +3,7 @@
 #include <cmath>
 
 #include "mk_device.cuh"
+#include "mk_patch.cuh"
 
 namespace mk {
 
@@ -214,16 +215,15 @@ int assemble_diagonal(mk_ctx* ctx, const Level& L, const double* Ae, double* dia
   return MK_OK;
 }
 
-int apply64(mk_ctx* ctx, const Level& L, const double* Ae, const double* x, double* y, int N, int ld,
+int apply64(mk_ctx* ctx, const mk_mesh* m, const double* Ae, const double* x, double* y, int N, int ld,
             bool mask_boundary, cudaStream_t s) {
-  prof_mark(ctx, PROF_APPLY64, true, s);
-  MK_CUDA(cudaMemsetAsync(y, 0, (size_t)L.n_nodes * ld * sizeof(double), s));
-  apply_coloured<double>(L, Ae, x, y, N, ld, s);
-  prof_mark(ctx, PROF_APPLY64, false, s);
-  if (mask_boundary)
-    MK_COUNT(), k_mask_rows<<<(int)((L.n_nodes * N + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, y, N, ld, 0.0);
-  MK_CUDA(cudaGetLastError());
-  return MK_OK;
+  (void)N;  // the patch operator writes every row of all ld columns
+  const Level& L = m->fine;
+  int err = MK_OK;
+  double* A = (double*)scratch(ctx, S_ELEMP64, (size_t)L.n_elems * padded_np(L.nloc, 8) * sizeof(double), &err);
+  if (!A) return err;
+  MK_TRY(pack_elements<double>(ctx, m, Ae, A, s));
+  return apply_patch<double>(ctx, m, A, x, y, ld, mask_boundary, s);
 }
 
 // ------------------------------------------------------------------------------------------------ A1, restriction

@@ -238,6 +238,7 @@ enum Slot : int {
   S_LDINV,                      // mk_learned_precond: FP64 diagonal, FP32 inverse
   S_TLC, S_TLX, S_TLW,          // two-level setup: coarse element products, coarse matrices, Cholesky workspace
   S_TLT,                        // two-level apply: restricted residual and coarse solution (FP32)
+  S_ELEMP64,                    // FP64 element matrices in patch order (apply64)
   S_COUNT
 };
 void* scratch(mk_ctx* ctx, int slot, size_t bytes, int* err);

@@ -157,7 +157,7 @@ int apply_patch(mk_ctx* ctx, const mk_mesh* m, const T* Ae, const T* x, T* y, in
     const size_t smem = patch_smem(nloc, P.max_elems, P.max_nodes, W, (int)sizeof(T)).total;
     if (smem > 227 * 1024) return fail(MK_ERR_UNSUPPORTED, "patch operator: patch too large for shared memory");
     const int th = std::min(256, (P.max_elems * ncolg + 31) / 32 * 32);  // one phase-1 item per thread
-    prof_mark(ctx, PROF_APPLY32, true, s);
+    prof_mark(ctx, sizeof(T) == 4 ? PROF_APPLY32 : PROF_APPLY64, true, s);
 #define MK_PATCH_LAUNCH(NL, V)                                                                                       \
   do {                                                                                                              \
     auto kern = k_apply_patch<NL, T, V>;                                                                            \
@@ -172,7 +172,7 @@ int apply_patch(mk_ctx* ctx, const mk_mesh* m, const T* Ae, const T* x, T* y, in
       if (vec == VEC) MK_PATCH_LAUNCH(10, VEC); else MK_PATCH_LAUNCH(10, 1);
     }
 #undef MK_PATCH_LAUNCH
-    prof_mark(ctx, PROF_APPLY32, false, s);
+    prof_mark(ctx, sizeof(T) == 4 ? PROF_APPLY32 : PROF_APPLY64, false, s);
     const int64_t work = P.n_shared_nodes * ncolg;
     if (work > 0) {
       prof_mark(ctx, PROF_HALO, true, s);
@@ -768,7 +768,7 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
     MK_CUDA(cudaMemsetAsync(zb, 0, (size_t)n * ld * sizeof(float), s));  // columns >= N stay zero
   }
   for (;;) {
-    MK_TRY(apply64(ctx, L, A64, x, Ax, ld, ld, true, s));   // FP64 residual of the current x
+    MK_TRY(apply64(ctx, m, A64, x, Ax, ld, ld, true, s));   // FP64 residual of the current x
     MK_COUNT(), k_mixed_residual<<<nblk, th, 0, s>>>(n, L.d_boundary, b, Ax, r, d, N, ld, part);
     MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(0, part, nblk, 2, ld, N, st, o.rtol, inner2);
     MK_CUDA(cudaMemcpyAsync(hst, st, sizeof(MixState) * ld, cudaMemcpyDeviceToHost, s));

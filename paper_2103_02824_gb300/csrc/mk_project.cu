@@ -14,31 +14,37 @@ template <int NLOC>
 __global__ void k_coarse_galerkin(const int32_t* __restrict__ child_off, const int32_t* __restrict__ child,
                                   const Geom* __restrict__ fgeom, const Geom* __restrict__ cgeom,
                                   const RefTables* __restrict__ ref, const double* __restrict__ A1,
-                                  const double* __restrict__ A2, double* __restrict__ out1, double* __restrict__ out2) {
+                                  const double* __restrict__ A2, int nchunk, double* __restrict__ part1,
+                                  double* __restrict__ part2) {
   constexpr int NP = NLOC * (NLOC + 1) / 2;
   __shared__ double R[NLOC][NLOC];
   __shared__ double S1[NLOC][NLOC], S2[NLOC][NLOC];
   __shared__ double T1[NLOC][NLOC], T2[NLOC][NLOC];
-  const int T = blockIdx.x;
+  // block = (coarse element T, chunk ch of its children): the children of one coarse element are spread over
+  // nchunk CTAs, whose partial sums k_coarse_reduce adds in chunk order
+  const int T = blockIdx.x / nchunk, ch = blockIdx.x % nchunk;
   const Geom cg = cgeom[T];
   const int tid = threadIdx.x;
   const int a = tid / NLOC, b = tid % NLOC;
+  const bool two = A2 != nullptr;
+  const int c0 = child_off[T], len = child_off[T + 1] - c0;
+  const int kb = c0 + (int)((int64_t)len * ch / nchunk), ke = c0 + (int)((int64_t)len * (ch + 1) / nchunk);
   double acc1 = 0.0, acc2 = 0.0;
-  for (int k = child_off[T]; k < child_off[T + 1]; ++k) {
+  for (int k = kb; k < ke; ++k) {
     const int e = child[k];
     if (tid < NLOC * NLOC) {
       const Geom g = fgeom[e];
       // fine local node a: reference coords from barycentrics, physical point, barycentrics in the parent
       const double* lb = ref->node_bary[a];
       const double xi[3] = {lb[1], lb[2], lb[3]};
-      double x[3], s[3];
+      double x[3], sv[3];
 #pragma unroll
       for (int r = 0; r < 3; ++r) x[r] = g.x0[r] + g.J[r * 3] * xi[0] + g.J[r * 3 + 1] * xi[1] + g.J[r * 3 + 2] * xi[2];
 #pragma unroll
       for (int r = 0; r < 3; ++r)
-        s[r] = cg.Jinv[r * 3] * (x[0] - cg.x0[0]) + cg.Jinv[r * 3 + 1] * (x[1] - cg.x0[1]) +
-               cg.Jinv[r * 3 + 2] * (x[2] - cg.x0[2]);
-      const double lam[4] = {1.0 - s[0] - s[1] - s[2], s[0], s[1], s[2]};
+        sv[r] = cg.Jinv[r * 3] * (x[0] - cg.x0[0]) + cg.Jinv[r * 3 + 1] * (x[1] - cg.x0[1]) +
+                cg.Jinv[r * 3 + 2] * (x[2] - cg.x0[2]);
+      const double lam[4] = {1.0 - sv[0] - sv[1] - sv[2], sv[0], sv[1], sv[2]};
       double v;
       if (NLOC == 4) {
         v = lam[b];
@@ -50,7 +56,7 @@ __global__ void k_coarse_galerkin(const int32_t* __restrict__ child_off, const i
       }
       R[a][b] = v;
       S1[a][b] = A1[(int64_t)e * NP + sym_index(a, b, NLOC)];
-      S2[a][b] = A2[(int64_t)e * NP + sym_index(a, b, NLOC)];
+      if (two) S2[a][b] = A2[(int64_t)e * NP + sym_index(a, b, NLOC)];
     }
     __syncthreads();
     if (tid < NLOC * NLOC) {  // T = A R  (row a, col b)
@@ -58,25 +64,37 @@ __global__ void k_coarse_galerkin(const int32_t* __restrict__ child_off, const i
 #pragma unroll
       for (int d = 0; d < NLOC; ++d) {
         t1 += S1[a][d] * R[d][b];
-        t2 += S2[a][d] * R[d][b];
+        if (two) t2 += S2[a][d] * R[d][b];
       }
       T1[a][b] = t1;
-      T2[a][b] = t2;
+      if (two) T2[a][b] = t2;
     }
     __syncthreads();
     if (tid < NLOC * NLOC) {  // acc += (R^T T)[a][b]
 #pragma unroll
       for (int c = 0; c < NLOC; ++c) {
         acc1 += R[c][a] * T1[c][b];
-        acc2 += R[c][a] * T2[c][b];
+        if (two) acc2 += R[c][a] * T2[c][b];
       }
     }
     __syncthreads();
   }
   if (tid < NLOC * NLOC) {
-    out1[(int64_t)T * NLOC * NLOC + tid] = acc1;
-    out2[(int64_t)T * NLOC * NLOC + tid] = acc2;
+    part1[(int64_t)blockIdx.x * NLOC * NLOC + tid] = acc1;
+    if (two) part2[(int64_t)blockIdx.x * NLOC * NLOC + tid] = acc2;
   }
+}
+
+// out[T][i] = sum over chunks, in order, of part[T][chunk][i]
+__global__ void k_coarse_reduce(int64_t ne, int nn, int nchunk, const double* __restrict__ part,
+                                double* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ne * nn) return;
+  const int64_t T = t / nn;
+  const int i = (int)(t - T * nn);
+  double v = 0.0;
+  for (int c = 0; c < nchunk; ++c) v += part[(T * nchunk + c) * nn + i];
+  out[t] = v;
 }
 
 // Dense coarse matrices over the coarse free DOF, one colour of coarse elements at a time.
@@ -94,7 +112,7 @@ __global__ void k_coarse_scatter(const int32_t* __restrict__ celems, int count, 
   const int fa = node_to_free[elem[(int64_t)T * NLOC + a]], fb = node_to_free[elem[(int64_t)T * NLOC + b]];
   if (fa < 0 || fb < 0) return;
   AH[(int64_t)fa * NH + fb] += C1[(int64_t)T * NLOC * NLOC + ab];
-  MH[(int64_t)fa * NH + fb] += C2[(int64_t)T * NLOC * NLOC + ab];
+  if (MH) MH[(int64_t)fa * NH + fb] += C2[(int64_t)T * NLOC * NLOC + ab];
 }
 
 // Gram partials: part[blk][j*N+k] = sum over nodes of X[n][j] Y[n][k]
@@ -152,31 +170,41 @@ int gram(mk_ctx* ctx, int64_t n, const double* X, const double* Y, int N, int ld
 // fine element matrices (children summed per coarse element in fixed order, then coarse colour by colour).
 int coarse_matrices(mk_ctx* ctx, const mk_mesh* m, const double* A1, const double* A2, double* X1, double* X2,
                     int slot, cudaStream_t s) {
+  // X1 = P^T A1 P and, when A2 and X2 are given, X2 = P^T A2 P (dense over the coarse free DOF)
   const Level& F = m->fine;
   const Level& C = m->coarse;
   const int NH = (int)C.n_free, nl = F.nloc;
+  const bool two = A2 && X2;
+  constexpr int kChunks = 16;
   int err = MK_OK;
-  double* CE = (double*)scratch(ctx, slot, (size_t)C.n_elems * nl * nl * 2 * sizeof(double), &err);
+  const size_t per = (size_t)C.n_elems * nl * nl;
+  double* CE = (double*)scratch(ctx, slot, per * 2 * (kChunks + 1) * sizeof(double), &err);
   if (!CE) return err;
   double* C1 = CE;
-  double* C2 = CE + (size_t)C.n_elems * nl * nl;
+  double* C2 = CE + per;
+  double* P1 = CE + 2 * per;
+  double* P2 = P1 + per * kChunks;
+  const int blocks = (int)C.n_elems * kChunks;
   if (nl == 4)
-    MK_COUNT(), k_coarse_galerkin<4><<<(int)C.n_elems, 128, 0, s>>>(m->d_child_off, m->d_child, F.d_geom, C.d_geom,
-                                                                    ctx->d_ref[1], A1, A2, C1, C2);
+    MK_COUNT(), k_coarse_galerkin<4><<<blocks, 128, 0, s>>>(m->d_child_off, m->d_child, F.d_geom, C.d_geom,
+                                                           ctx->d_ref[1], A1, two ? A2 : nullptr, kChunks, P1, P2);
   else
-    MK_COUNT(), k_coarse_galerkin<10><<<(int)C.n_elems, 128, 0, s>>>(m->d_child_off, m->d_child, F.d_geom, C.d_geom,
-                                                                     ctx->d_ref[2], A1, A2, C1, C2);
+    MK_COUNT(), k_coarse_galerkin<10><<<blocks, 128, 0, s>>>(m->d_child_off, m->d_child, F.d_geom, C.d_geom,
+                                                            ctx->d_ref[2], A1, two ? A2 : nullptr, kChunks, P1, P2);
+  const int64_t work = (int64_t)per;
+  MK_COUNT(), k_coarse_reduce<<<(int)((work + 255) / 256), 256, 0, s>>>(C.n_elems, nl * nl, kChunks, P1, C1);
+  if (two) MK_COUNT(), k_coarse_reduce<<<(int)((work + 255) / 256), 256, 0, s>>>(C.n_elems, nl * nl, kChunks, P2, C2);
   MK_CUDA(cudaMemsetAsync(X1, 0, (size_t)NH * NH * sizeof(double), s));
-  MK_CUDA(cudaMemsetAsync(X2, 0, (size_t)NH * NH * sizeof(double), s));
+  if (two) MK_CUDA(cudaMemsetAsync(X2, 0, (size_t)NH * NH * sizeof(double), s));
   for (int col = 0; col < C.n_colours; ++col) {
     const int64_t off = C.colour_off[col], cnt = C.colour_off[col + 1] - off;
     if (nl == 4)
       MK_COUNT(), k_coarse_scatter<4><<<(int)((cnt * 16 + 255) / 256), 256, 0, s>>>(C.d_colour_elems + off, (int)cnt, C.d_elem,
-                                                                           C.d_node_to_free, C1, C2, X1, X2, NH);
+                                                                           C.d_node_to_free, C1, C2, X1, two ? X2 : nullptr, NH);
     else
       MK_COUNT(), k_coarse_scatter<10><<<(int)((cnt * 100 + 255) / 256), 256, 0, s>>>(C.d_colour_elems + off, (int)cnt,
                                                                             C.d_elem, C.d_node_to_free, C1, C2, X1,
-                                                                            X2, NH);
+                                                                            two ? X2 : nullptr, NH);
   }
   MK_CUDA(cudaGetLastError());
   return MK_OK;
@@ -188,7 +216,7 @@ using namespace mk;
 
 extern "C" int mk_coarse_pencil(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, const double* vq, double* AH,
                                 double* MH, void* stream) {
-  MK_ARG(ctx && m && mol && AH && MH, "mk_coarse_pencil: null argument");
+  MK_ARG(ctx && m && mol && AH, "mk_coarse_pencil: null argument");
   MK_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
   const Level& F = m->fine;
@@ -196,12 +224,12 @@ extern "C" int mk_coarse_pencil(mk_ctx* ctx, const mk_mesh* m, const mk_molecule
   int err = MK_OK;
   const size_t eb = (size_t)F.n_elems * (nl * (nl + 1) / 2) * sizeof(double);
   double* He = (double*)scratch(ctx, S_ELEM64C, eb, &err);
-  double* Me = (double*)scratch(ctx, S_ELEM64D, eb, &err);
-  if (!He || !Me) return err;
+  double* Me = MH ? (double*)scratch(ctx, S_ELEM64D, eb, &err) : nullptr;
+  if (!He || (MH && !Me)) return err;
   const double* H0 = static_matrices(ctx, m, mol, s, &err);
   if (!H0) return err;
   MK_TRY(element_matrices(ctx, F, nullptr, 0.0, 0.0, 0.0, vq, He, s, H0));
-  MK_TRY(element_matrices(ctx, F, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s));
+  if (MH) MK_TRY(element_matrices(ctx, F, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s));
   return coarse_matrices(ctx, m, He, Me, AH, MH, S_COARSE2, s);
 }
 
@@ -227,8 +255,8 @@ extern "C" int mk_augmented_project(mk_ctx* ctx, const mk_mesh* m, const mk_mole
   if (!H0) return err;
   MK_TRY(element_matrices(ctx, F, nullptr, 0.0, 0.0, 0.0, vq, He, s, H0));
   MK_TRY(element_matrices(ctx, F, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s));
-  MK_TRY(apply64(ctx, F, He, psihat, Y, N, ld, true, s));
-  MK_TRY(apply64(ctx, F, Me, psihat, MY, N, ld, true, s));
+  MK_TRY(apply64(ctx, m, He, psihat, Y, N, ld, true, s));
+  MK_TRY(apply64(ctx, m, Me, psihat, MY, N, ld, true, s));
   MK_TRY(restrict_to_coarse(ctx, m, Y, ld, N, b, N, s));
   MK_TRY(restrict_to_coarse(ctx, m, MY, ld, N, c, N, s));
   double* GA = gramA ? gramA : G;

@@ -5,6 +5,7 @@
 #include <cstring>
 
 #include "mk_device.cuh"
+#include "mk_patch.cuh"
 
 namespace mk {
 
@@ -112,10 +113,15 @@ __global__ void k_pupdate(int64_t n, const ColState* __restrict__ st, const doub
 
 // Plain FP64 Jacobi-PCG on all columns at once.  `Ae` packed element matrices of the SPD operator, `diag` its
 // assembled diagonal (boundary rows 1).  x: initial guess in, solution out (boundary rows forced to 0).
-int pcg64(mk_ctx* ctx, const Level& L, const double* Ae, const double* diag, const double* b, double* x, int N,
+int pcg64(mk_ctx* ctx, const mk_mesh* m, const double* Ae, const double* diag, const double* b, double* x, int N,
           int ld, const mk_solve_opts& o, mk_solve_report* rep, cudaStream_t s) {
+  const Level& L = m->fine;
   int err = MK_OK;
   const int64_t n = L.n_nodes;
+  // the FP64 patch operator: element matrices packed in patch order once per solve
+  double* Ap = (double*)scratch(ctx, S_ELEMP64, (size_t)L.n_elems * padded_np(L.nloc, 8) * sizeof(double), &err);
+  if (!Ap) return err;
+  MK_TRY(pack_elements<double>(ctx, m, Ae, Ap, s));
   const size_t vb = (size_t)n * ld * sizeof(double);
   double* R = (double*)scratch(ctx, S_R64, vb, &err);
   double* Z = (double*)scratch(ctx, S_Z64, vb, &err);
@@ -135,7 +141,7 @@ int pcg64(mk_ctx* ctx, const Level& L, const double* Ae, const double* diag, con
   }
   ColState* hst = (ColState*)ctx->pinned;
 
-  MK_TRY(apply64(ctx, L, Ae, x, Q, N, ld, true, s));
+  MK_TRY(apply_patch<double>(ctx, m, Ap, x, Q, ld, true, s));
   MK_COUNT(), k_residual<<<gb, th, 0, s>>>(n, L.d_boundary, b, Q, diag, R, Z, P, N, ld);
   // x boundary rows to 0 (Q := 0 then mask trick): write x = x - 0 on interior, 0 on boundary
   MK_TRY(column_dots(ctx, n, b, b, N, ld, d1, s));
@@ -157,7 +163,7 @@ int pcg64(mk_ctx* ctx, const Level& L, const double* Ae, const double* diag, con
       MK_CUDA(cudaMemcpyAsync(o.trace_r + (size_t)ntr * n * ld, R, vb, cudaMemcpyDeviceToDevice, s));
       ++ntr;
     }
-    MK_TRY(apply64(ctx, L, Ae, P, Q, N, ld, true, s));
+    MK_TRY(apply_patch<double>(ctx, m, Ap, P, Q, ld, true, s));
     MK_TRY(column_dots(ctx, n, P, Q, N, ld, d1, s));
     MK_COUNT(), k_alpha<<<1, MK_MAX_RHS, 0, s>>>(st, d1, N);
     MK_COUNT(), k_update<<<gb, th, 0, s>>>(n, st, P, Q, diag, x, R, Z, N, ld);
@@ -179,7 +185,7 @@ int pcg64(mk_ctx* ctx, const Level& L, const double* Ae, const double* diag, con
   }
   MK_CUDA(cudaGetLastError());
   // final FP64 true residual
-  MK_TRY(apply64(ctx, L, Ae, x, Q, N, ld, true, s));
+  MK_TRY(apply_patch<double>(ctx, m, Ap, x, Q, ld, true, s));
   MK_COUNT(), k_residual<<<gb, th, 0, s>>>(n, L.d_boundary, b, Q, diag, R, nullptr, nullptr, N, ld);
   MK_TRY(column_dots(ctx, n, R, R, N, ld, d3, s));
   MK_CUDA(cudaMemcpyAsync(hst, st, sizeof(ColState) * N, cudaMemcpyDeviceToHost, s));
@@ -293,7 +299,7 @@ int mk_hartree_poisson(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, c
   MK_TRY(multipole_boundary(ctx, L, rho, L.d_nodes, bc, w, s));
   MK_TRY(element_matrices(ctx, L, nullptr, 1.0, 0.0, 0.0, nullptr, Ke, s));
   MK_TRY(assemble_diagonal(ctx, L, Ke, diag, s));
-  MK_TRY(apply64(ctx, L, Ke, w, y, 1, 1, true, s));                     // K_IB g (interior rows)
+  MK_TRY(apply64(ctx, m, Ke, w, y, 1, 1, true, s));                     // K_IB g (interior rows)
   ColParams coef{};
   coef.v[0] = 1.0;
   MK_COUNT(), k_combine_rhs<<<(int)((L.n_nodes + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, F, y, coef, F, 1, 1);
@@ -305,7 +311,7 @@ int mk_hartree_poisson(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, c
     if (!cinv) return err;
   }
   int r = opts->precision == MK_PREC_MIXED ? pcg_mixed(ctx, m, Ke, F, d, 1, 1, *opts, report, s, cinv)
-                                           : pcg64(ctx, L, Ke, diag, F, d, 1, 1, *opts, report, s);
+                                           : pcg64(ctx, m, Ke, diag, F, d, 1, 1, *opts, report, s);
   MK_COUNT(), k_axpy_interior<<<(int)((L.n_nodes + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, d, w);
   MK_CUDA(cudaGetLastError());
   MK_CUDA(cudaStreamSynchronize(s));
@@ -333,8 +339,8 @@ int mk_assemble_rhs(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, cons
   MK_TRY(frozen_potential(ctx, L, w, rho, xc, vq, s));
   MK_TRY(element_matrices(ctx, L, nullptr, 0.0, 0.0, 0.0, vq, Ve, s));
   MK_TRY(element_matrices(ctx, L, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s));
-  MK_TRY(apply64(ctx, L, Me, u, Mu, N, ld, true, s));
-  MK_TRY(apply64(ctx, L, Ve, u, Vu, N, ld, true, s));
+  MK_TRY(apply64(ctx, m, Me, u, Mu, N, ld, true, s));
+  MK_TRY(apply64(ctx, m, Ve, u, Vu, N, ld, true, s));
   ColParams coef{};
   for (int j = 0; j < N; ++j) coef.v[j] = lambdaH[j] + sigma;
   MK_COUNT(), k_combine_rhs<<<(int)((L.n_nodes * ld + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, Mu, Vu, coef, rhs, N, ld);
@@ -364,7 +370,7 @@ int mk_correction_solve(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, d
   if (!H0) return err;
   MK_TRY(element_matrices(ctx, L, nullptr, 0.0, 0.0, sigma, nullptr, Ae, s, H0));
   MK_TRY(assemble_diagonal(ctx, L, Ae, diag, s));
-  return pcg64(ctx, L, Ae, diag, rhs, x, N, ld, *opts, report, s);
+  return pcg64(ctx, m, Ae, diag, rhs, x, N, ld, *opts, report, s);
 }
 
 // Symmetric tridiagonal lowest eigenvalue by Sturm-sequence bisection (host, tiny).
@@ -418,22 +424,22 @@ int mk_lowest_ritz(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, const 
   MK_CUDA(cudaMemcpyAsync(v0d, v0, L.n_free * sizeof(double), cudaMemcpyHostToDevice, s));
   MK_CUDA(cudaStreamSynchronize(s));
   MK_COUNT(), k_scatter_free<<<(int)((L.n_free + 255) / 256), 256, 0, s>>>(L.n_free, L.d_free_idx, v0d, v);
-  MK_TRY(apply64(ctx, L, Me, v, Mw, 1, 1, true, s));
+  MK_TRY(apply64(ctx, m, Me, v, Mw, 1, 1, true, s));
   MK_TRY(column_dots(ctx, n, v, Mw, 1, 1, dd, s));
   MK_COUNT(), k_scale<<<(int)((n + 255) / 256), 256, 0, s>>>(n, v, dd, nullptr, 0);
   mk_solve_opts mo{MK_PREC_FP64, MK_PRECOND_JACOBI, 1e-12, 5000, 0, 0, 25};
   std::vector<double> a, b;
   double beta = 0.0;
   for (int k = 0; k < steps; ++k) {
-    MK_TRY(apply64(ctx, L, He, v, Hv, 1, 1, true, s));
+    MK_TRY(apply64(ctx, m, He, v, Hv, 1, 1, true, s));
     MK_TRY(column_dots(ctx, n, v, Hv, 1, 1, dd, s));
     double alpha;
     MK_CUDA(cudaMemcpyAsync(&alpha, dd, sizeof(double), cudaMemcpyDeviceToHost, s));
     MK_CUDA(cudaMemsetAsync(w, 0, n * sizeof(double), s));
     MK_CUDA(cudaStreamSynchronize(s));
-    MK_TRY(pcg64(ctx, L, Me, diagM, Hv, w, 1, 1, mo, nullptr, s));   // w = M^-1 H v
+    MK_TRY(pcg64(ctx, m, Me, diagM, Hv, w, 1, 1, mo, nullptr, s));   // w = M^-1 H v
     MK_COUNT(), k_lanczos_w<<<(int)((n + 255) / 256), 256, 0, s>>>(n, L.d_boundary, w, v, vp, alpha, beta);
-    MK_TRY(apply64(ctx, L, Me, w, Mw, 1, 1, true, s));
+    MK_TRY(apply64(ctx, m, Me, w, Mw, 1, 1, true, s));
     MK_TRY(column_dots(ctx, n, w, Mw, 1, 1, dd, s));
     double bb;
     MK_CUDA(cudaMemcpyAsync(&bb, dd, sizeof(double), cudaMemcpyDeviceToHost, s));

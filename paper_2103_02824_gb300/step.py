@@ -82,14 +82,14 @@ class CorrectionStep:
             # the coarse pencil and its decomposition need only vq, not psi^: run them beside the fine solve
             self._ev_rhs.record(main)
             self._side.wait_event(self._ev_rhs)
-            mk.mk_coarse_pencil(ctx, mesh, self.mol, self.vq, self.AH, self.MH, stream=self._side.cuda_stream)
+            mk.mk_coarse_pencil(ctx, mesh, self.mol, self.vq, self.AH, None, stream=self._side.cuda_stream)
             self._decompose(self._side.cuda_stream)
             self._ev_dec.record(self._side)
         self.psihat.copy_(self.u)
         reps["solve"] = mk.mk_correction_solve(ctx, mesh, self.mol, sigma, self.rhs, self.psihat, N,
                                                opt=solve_opts, stream=stream)
         if not self.overlap:
-            mk.mk_coarse_pencil(ctx, mesh, self.mol, self.vq, self.AH, self.MH, stream=stream)
+            mk.mk_coarse_pencil(ctx, mesh, self.mol, self.vq, self.AH, None, stream=stream)
             self._decompose(stream)
         mk.mk_augmented_project(ctx, mesh, self.mol, self.vq, self.psihat, N, None, None, self.b, self.c,
                                 self.beta, self.gamma, self.gramA, self.gramM, stream=stream)
