@@ -305,6 +305,23 @@ def main():
                          "poisson_iterations": r["poisson"]["iterations"] if r["poisson"] else None,
                          "max_abs_lambda_diff_vs_headline_Ha": float(np.abs(lam_k - lam_head).max())}
 
+    # the same operator kernel timed alone (no concurrent stream), for comparison with its in-step duration
+    iso_ms = None
+    if a.precision == "mixed":
+        g = torch.Generator(device="cuda").manual_seed(5)
+        xa = torch.randn((info["n_nodes"], st.ld), generator=g, device="cuda", dtype=torch.float32)
+        ya = torch.empty_like(xa)
+        for _ in range(3):
+            mk.mk_operator_apply(ctx, mesh, mol, sigma, xa, ya)
+        torch.cuda.synchronize()
+        mk.profile_enable(ctx, True)
+        for _ in range(20):
+            mk.mk_operator_apply(ctx, mesh, mol, sigma, xa, ya)
+        torch.cuda.synchronize()
+        ims, inn = mk.profile_read(ctx, mk.PROF_APPLY32)
+        mk.profile_enable(ctx, False)
+        iso_ms = ims / inn if inn else None
+
     # roofline of the dominant kernel (the element-by-element operator application)
     kind = mk.PROF_APPLY32 if prof[mk.PROF_APPLY32][1] > 0 else mk.PROF_APPLY64
     ms_k, n_k = prof[kind]
@@ -332,7 +349,12 @@ def main():
                 "peak": peak, "unit": "GB/s", "frac": achieved / peak if achieved else None,
                 "traffic": TRAFFIC.get((a.workload, ld)),
                 "applications": n_k, "ms_per_application": ms_k / n_k if n_k else None,
-                "bytes_per_application": nbytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst), of measured"}
+                "bytes_per_application": nbytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst), of measured",
+                "measured": "CUDA events around every application inside the steps (concurrent with the coarse "
+                            "decomposition on the other stream)",
+                "isolated": None if iso_ms is None else {
+                    "ms_per_application": iso_ms, "achieved": nbytes / (iso_ms * 1e-3) / 1e9,
+                    "frac": nbytes / (iso_ms * 1e-3) / 1e9 / peak, "applications": 20}}
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
