@@ -276,6 +276,31 @@ int mk_lowest_ritz(mk_ctx* ctx, const mk_mesh* mesh, const mk_molecule* mol, con
                    double* theta, void* stream);
 
 /* ---------------------------------------------------------------------------------------------------------
+ * Batching: many molecules (uneven meshes, uneven orbital counts) in shared launches, and autotuned patch sizes
+ * --------------------------------------------------------------------------------------------------------- */
+/* Solves the correction problems (Eq. (Aux_Linear_Problem)) of K molecules together: problem k is (meshes[k],
+ * mols[k], sigmas[k]) with right-hand side rhs[k] and initial guess / result x[k] (device double
+ * [n_nodes_k * ld[k]], columns < N[k]), as mk_correction_solve with *opts (MK_PREC_MIXED, Jacobi, no coarse
+ * correction).  The FP64 residual refinement runs per problem; every inner FP32 PCG iteration runs as seven kernel
+ * launches for the whole batch (one grid over the element patches of all meshes, the halo sums, the dot products
+ * and updates of all problems), replayed from one CUDA graph per chunk of opts->check_every iterations.  All meshes
+ * must use the same element order; ld[k] in {4, 8, 16}; K <= MK_MAX_BATCH.  reports[k] (host) is filled for every
+ * problem.  Each problem's result is bit-identical to mk_correction_solve's with the same options (same kernels,
+ * same summation orders; a converged problem idles while others iterate).  Returns MK_ERR_NOT_CONVERGED or
+ * MK_ERR_BREAKDOWN if any problem did (see the reports).  Synchronises the stream. */
+#define MK_MAX_BATCH 256
+int mk_batch_correction_solve(mk_ctx* ctx, int K, const mk_mesh* const* meshes, const mk_molecule* mols,
+                              const double* sigmas, const double* const* rhs, double* const* x, const int* ld,
+                              const int* N, const mk_solve_opts* opts, mk_solve_report* reports, void* stream);
+/* Rebuilds the mesh's element patches with pe elements each (pe a multiple of 32 in [32, 512]; the patch
+ * kernels' shared memory must fit).  Synchronises the device. */
+int mk_mesh_set_patch_elems(mk_mesh* mesh, int pe);
+/* Autotuner of the patch size: times the FP32 operator on this mesh for ld columns with each candidate (64, 96,
+ * 128, 192 elements per patch for P2; 128, 192, 256, 384 for P1), leaves the mesh with the fastest and returns it
+ * in *best_pe; ms (host, 4 entries, may be NULL) receives each candidate's time per application. */
+int mk_autotune_patches(mk_ctx* ctx, mk_mesh* mesh, int ld, int* best_pe, double* ms);
+
+/* ---------------------------------------------------------------------------------------------------------
  * Learned element-patch preconditioner (this library's addition; the paper solves its boundary-value problems
  * with standard solvers).  Definitions, for element e and orbital column j:
  *   input   x = [r_e / s, (v_k - centroid_e) / h_e (k = 0..3)]    r_e: residual at the element's n_loc nodes,

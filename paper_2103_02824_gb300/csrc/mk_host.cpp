@@ -430,9 +430,7 @@ static void free_level(Level& L) {
   L.d_geom = nullptr;
 }
 
-int build_patches(mk_mesh* m);                 // mk_patches.cpp
 int mesh_mass_factor(mk_ctx* ctx, mk_mesh* m);  // mk_eig.cu
-void free_patches(mk::Patches& p);
 
 }  // namespace mk
 

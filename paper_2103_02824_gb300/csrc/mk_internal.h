@@ -239,8 +239,12 @@ enum Slot : int {
   S_TLC, S_TLX, S_TLW,          // two-level setup: coarse element products, coarse matrices, Cholesky workspace
   S_TLT,                        // two-level apply: restricted residual and coarse solution (FP32)
   S_ELEMP64,                    // FP64 element matrices in patch order (apply64)
+  S_BATCH,                      // batched solve: per-problem buffers
   S_COUNT
 };
 void* scratch(mk_ctx* ctx, int slot, size_t bytes, int* err);
+// element patches of the fine mesh (mk_patches.cpp): pe elements per patch, 0 = the default for the order
+int build_patches(mk_mesh* m, int pe = 0);
+void free_patches(Patches& p);
 
 }  // namespace mk

@@ -12,13 +12,7 @@
 
 namespace mk {
 
-// y = A x for one patch per CTA: owner-computes scatter, fixed summation order, no atomics.
-// Staging: the patch's element matrices, connectivity, incidence lists and node targets are copied into shared
-// memory asynchronously, all at once.  Phase 1: element products y_e = A_e x_e (x gathered from global, mostly L2
-// hits) into shared memory laid out [slot][element][column]; one thread per element and group of VEC columns.
-// Each element matrix is read from shared memory once (packed order), with all output rows held in registers.
-// Phase 2: each local node sums its incidences in fixed order (shared memory only) and writes the global row
-// (owned node) or its halo slot (shared node).  Columns [col0, col0 + W) with W = ncolg * VEC.
+// y = A x for one patch per CTA (see patch_apply).
 template <int NLOC, typename T, int VEC>
 __global__ void __launch_bounds__(256) k_apply_patch(const int32_t* __restrict__ elem_off,
                                                      const int32_t* __restrict__ node_off,
@@ -29,104 +23,17 @@ __global__ void __launch_bounds__(256) k_apply_patch(const int32_t* __restrict__
                                                      const uint8_t* __restrict__ bnd, int mask,
                                                      const T* __restrict__ x, T* __restrict__ y, T* __restrict__ halo,
                                                      int ncolg, int col0, int ld, int pe, int max_nodes) {
-  constexpr int NPS = padded_np(NLOC, (int)sizeof(T));
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int W = ncolg * VEC;
-  const PatchSmem lay = patch_smem(NLOC, pe, max_nodes, W, (int)sizeof(T));
-  T* Ye = reinterpret_cast<T*>(smraw + lay.ye);  // [NLOC][pe][W]
-  const int p = blockIdx.x;
-  const int e0 = elem_off[p], ne = elem_off[p + 1] - e0;
-  const int n0 = node_off[p], nl = node_off[p + 1] - n0;
-  const int ibase = e0 * NLOC;  // the patch's incidences are inc[ibase, ibase + ne * NLOC)
-  const T* As = stage_async(smraw + lay.as, Ae + (int64_t)e0 * NPS, ne * NPS * (int)sizeof(T));
-  const int32_t* cs = stage_async(smraw + lay.conn, conn + ibase, ne * NLOC * 4);
-  const uint16_t* is = stage_async(smraw + lay.inc, inc + ibase, ne * NLOC * 2);
-  const int32_t* os = stage_async(smraw + lay.ioff, inc_off + n0, (nl + 1) * 4);
-  const int32_t* ts = stage_async(smraw + lay.tgt, target + n0, nl * 4);
-  cp_async_wait_all();
-  __syncthreads();
-  for (int it = threadIdx.x; it < ne * ncolg; it += blockDim.x) {
-    const int el = it / ncolg, g = it - el * ncolg;
-    Vec<T, VEC> xv[NLOC];
-#pragma unroll
-    for (int a = 0; a < NLOC; ++a) xv[a] = ldv<T, VEC>(x + (int64_t)cs[el * NLOC + a] * ld + col0 + g * VEC);
-    // one pass over the packed upper triangle: each entry is read once and feeds rows a and b; nothing is
-    // stored until every row is complete
-    const T* A = As + el * NPS;
-    Vec<T, VEC> acc[NLOC];
-#pragma unroll
-    for (int a = 0; a < NLOC; ++a)
-#pragma unroll
-      for (int c = 0; c < VEC; ++c) acc[a].v[c] = 0;
-#pragma unroll
-    for (int a = 0; a < NLOC; ++a)
-#pragma unroll
-      for (int b = a; b < NLOC; ++b) {
-        const T w = A[sym_index(a, b, NLOC)];
-#pragma unroll
-        for (int c = 0; c < VEC; ++c) {
-          acc[a].v[c] += w * xv[b].v[c];
-          if (b != a) acc[b].v[c] += w * xv[a].v[c];
-        }
-      }
-#pragma unroll
-    for (int a = 0; a < NLOC; ++a) stv<T, VEC>(Ye + ((size_t)a * pe + el) * W + g * VEC, acc[a]);
-  }
-  __syncthreads();
-  for (int it = threadIdx.x; it < nl * ncolg; it += blockDim.x) {
-    const int l = it / ncolg, g = it - l * ncolg;
-    const int b = os[l] - ibase, e = os[l + 1] - ibase;
-    Vec<T, VEC> acc;
-#pragma unroll
-    for (int c = 0; c < VEC; ++c) acc.v[c] = 0;
-    auto ye = [&](int k) {  // product of incidence k (slot * pe + local element)
-      return ldv<T, VEC>(Ye + (size_t)is[k] * W + g * VEC);
-    };
-    int k = b;
-    for (; k + 4 <= e; k += 4) {  // four independent loads, then the sums in list order
-      const Vec<T, VEC> v0 = ye(k), v1 = ye(k + 1), v2 = ye(k + 2), v3 = ye(k + 3);
-#pragma unroll
-      for (int c = 0; c < VEC; ++c) acc.v[c] = (((acc.v[c] + v0.v[c]) + v1.v[c]) + v2.v[c]) + v3.v[c];
-    }
-    for (; k < e; ++k) {
-      const Vec<T, VEC> v = ye(k);
-#pragma unroll
-      for (int c = 0; c < VEC; ++c) acc.v[c] += v.v[c];
-    }
-    const int t = ts[l];
-    if (t >= 0) {
-      if (mask && bnd[t])
-#pragma unroll
-        for (int c = 0; c < VEC; ++c) acc.v[c] = 0;
-      stv<T, VEC>(y + (int64_t)t * ld + col0 + g * VEC, acc);
-    } else {
-      stv<T, VEC>(halo + (int64_t)(-t - 1) * ld + col0 + g * VEC, acc);
-    }
-  }
+  patch_apply<NLOC, T, VEC>(blockIdx.x, elem_off, node_off, conn, Ae, target, inc_off, inc, bnd, mask, x, y, halo,
+                            ncolg, col0, ld, pe, max_nodes, smraw);
 }
 
-// Shared nodes: y[node] = sum of the node's halo slots in patch order.
 template <typename T, int VEC>
 __global__ void k_halo(int64_t nshared, const int32_t* __restrict__ node, const int32_t* __restrict__ off,
                        const uint8_t* __restrict__ bnd, int mask, const T* __restrict__ halo, T* __restrict__ y,
                        int ncolg, int col0, int ld) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nshared * ncolg) return;
-  const int64_t k = t / ncolg;
-  const int g = (int)(t - k * ncolg);
-  Vec<T, VEC> acc;
-#pragma unroll
-  for (int c = 0; c < VEC; ++c) acc.v[c] = 0;
-  for (int s = off[k]; s < off[k + 1]; ++s) {
-    const Vec<T, VEC> v = ldv<T, VEC>(halo + (int64_t)s * ld + col0 + g * VEC);
-#pragma unroll
-    for (int c = 0; c < VEC; ++c) acc.v[c] += v.v[c];
-  }
-  const int nd = node[k];
-  if (mask && bnd[nd])
-#pragma unroll
-    for (int c = 0; c < VEC; ++c) acc.v[c] = 0;
-  stv<T, VEC>(y + (int64_t)nd * ld + col0 + g * VEC, acc);
+  halo_sum<T, VEC>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, nshared, node, off, bnd, mask, halo, y, ncolg,
+                   col0, ld);
 }
 
 template <typename T>
@@ -388,7 +295,7 @@ struct MixState {
 // Column partial sums with a fixed map: thread t of a block of ld*(256/ld) threads always handles column t % ld.
 // part[blk][k*ld + j] for k < NS sums.
 template <int NS>
-__device__ __forceinline__ void block_partials(double (&acc)[NS], double* sh, int ld, double* part) {
+__device__ __forceinline__ void block_partials(double (&acc)[NS], double* sh, int ld, double* part, int bx) {
   const int rows = blockDim.x / ld;
   const int r = threadIdx.x / ld;
   int top = 1;
@@ -401,7 +308,7 @@ __device__ __forceinline__ void block_partials(double (&acc)[NS], double* sh, in
       if (r < st && r + st < rows) sh[threadIdx.x] += sh[threadIdx.x + st * ld];
       __syncthreads();
     }
-    if (threadIdx.x < ld) part[(int64_t)blockIdx.x * NS * ld + k * ld + threadIdx.x] = sh[threadIdx.x];
+    if (threadIdx.x < ld) part[(int64_t)bx * NS * ld + k * ld + threadIdx.x] = sh[threadIdx.x];
     __syncthreads();
   }
 }
@@ -427,7 +334,7 @@ __global__ void k_mixed_residual(int64_t n, const uint8_t* __restrict__ bnd, con
       acc[0] += bv * bv;
       acc[1] += rv * rv;
     }
-  block_partials<2>(acc, sh, ld, part);
+  block_partials<2>(acc, sh, ld, part, blockIdx.x);
 }
 
 // p = Dinv r; partials of (r.z, r.r)
@@ -446,35 +353,40 @@ __global__ void k_mixed_init(int64_t n, const float* __restrict__ dinv, const fl
       acc[0] += (double)rv * z;
       acc[1] += (double)rv * rv;
     }
-  block_partials<2>(acc, sh, ld, part);
+  block_partials<2>(acc, sh, ld, part, blockIdx.x);
 }
 
-// partial p.q
-__global__ void k_mixed_pq(int64_t n, const float* __restrict__ p, const float* __restrict__ q, int ld,
-                           double* __restrict__ part) {
+// partial p.q (block bx of gx)
+__device__ __forceinline__ void mixed_pq_body(int bx, int gx, int64_t n, const float* __restrict__ p,
+                                              const float* __restrict__ q, int ld, double* __restrict__ part) {
   __shared__ double sh[256];
   double acc[1] = {0.0};
   const int rows = blockDim.x / ld;
   const int j = threadIdx.x % ld, rr = threadIdx.x / ld;
   if (rr < rows)
-    for (int64_t nd = (int64_t)blockIdx.x * rows + rr; nd < n; nd += (int64_t)gridDim.x * rows) {
+    for (int64_t nd = (int64_t)bx * rows + rr; nd < n; nd += (int64_t)gx * rows) {
       const int64_t t = nd * ld + j;
       acc[0] += (double)p[t] * q[t];
     }
-  block_partials<1>(acc, sh, ld, part);
+  block_partials<1>(acc, sh, ld, part, bx);
+}
+__global__ void k_mixed_pq(int64_t n, const float* __restrict__ p, const float* __restrict__ q, int ld,
+                           double* __restrict__ part) {
+  mixed_pq_body(blockIdx.x, gridDim.x, n, p, q, ld, part);
 }
 
-// d += alpha p; r -= alpha q; partials of (r.z, r.r) with z = Dinv r
-__global__ void k_mixed_update(int64_t n, const MixState* __restrict__ st, const float* __restrict__ dinv,
-                               const float* __restrict__ p, const float* __restrict__ q, float* __restrict__ d,
-                               float* __restrict__ r, int ld, double* __restrict__ part) {
+// d += alpha p; r -= alpha q; partials of (r.z, r.r) with z = Dinv r (block bx of gx)
+__device__ __forceinline__ void mixed_update_body(int bx, int gx, int64_t n, const MixState* __restrict__ st,
+                                                  const float* __restrict__ dinv, const float* __restrict__ p,
+                                                  const float* __restrict__ q, float* __restrict__ d,
+                                                  float* __restrict__ r, int ld, double* __restrict__ part) {
   __shared__ double sh[256];
   double acc[2] = {0.0, 0.0};
   const int rows = blockDim.x / ld;
   const int j = threadIdx.x % ld, rr = threadIdx.x / ld;
   const float a = rr < rows ? (float)st[j].alpha : 0.f;
   if (rr < rows)
-    for (int64_t nd = (int64_t)blockIdx.x * rows + rr; nd < n; nd += (int64_t)gridDim.x * rows) {
+    for (int64_t nd = (int64_t)bx * rows + rr; nd < n; nd += (int64_t)gx * rows) {
       const int64_t t = nd * ld + j;
       float rv = r[t];
       if (a != 0.f) {
@@ -485,18 +397,27 @@ __global__ void k_mixed_update(int64_t n, const MixState* __restrict__ st, const
       acc[0] += (double)rv * (rv * dinv[nd]);
       acc[1] += (double)rv * rv;
     }
-  block_partials<2>(acc, sh, ld, part);
+  block_partials<2>(acc, sh, ld, part, bx);
+}
+__global__ void k_mixed_update(int64_t n, const MixState* __restrict__ st, const float* __restrict__ dinv,
+                               const float* __restrict__ p, const float* __restrict__ q, float* __restrict__ d,
+                               float* __restrict__ r, int ld, double* __restrict__ part) {
+  mixed_update_body(blockIdx.x, gridDim.x, n, st, dinv, p, q, d, r, ld, part);
 }
 
-// p = Dinv r + beta p (active columns)
-__global__ void k_mixed_p(int64_t n, const MixState* __restrict__ st, const float* __restrict__ dinv,
-                          const float* __restrict__ r, float* __restrict__ p, int ld) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// p = Dinv r + beta p (active columns); item t = node * ld + column
+__device__ __forceinline__ void mixed_p_body(int64_t t, int64_t n, const MixState* __restrict__ st,
+                                             const float* __restrict__ dinv, const float* __restrict__ r,
+                                             float* __restrict__ p, int ld) {
   if (t >= n * ld) return;
   const int j = (int)(t % ld);
   if (!st[j].active) return;
   const int64_t nd = t / ld;
   p[t] = r[t] * dinv[nd] + (float)st[j].beta * p[t];
+}
+__global__ void k_mixed_p(int64_t n, const MixState* __restrict__ st, const float* __restrict__ dinv,
+                          const float* __restrict__ r, float* __restrict__ p, int ld) {
+  mixed_p_body((int64_t)blockIdx.x * blockDim.x + threadIdx.x, n, st, dinv, r, p, ld);
 }
 
 // FCG(1): partials of (p.q, p.r)
@@ -512,7 +433,7 @@ __global__ void k_fcg_pq(int64_t n, const float* __restrict__ p, const float* __
       acc[0] += (double)p[t] * q[t];
       acc[1] += (double)p[t] * r[t];
     }
-  block_partials<2>(acc, sh, ld, part);
+  block_partials<2>(acc, sh, ld, part, blockIdx.x);
 }
 
 // FCG(1): d += alpha p; r -= alpha q; partial r.r
@@ -535,7 +456,7 @@ __global__ void k_fcg_update(int64_t n, const MixState* __restrict__ st, const f
       }
       acc[0] += (double)rv * rv;
     }
-  block_partials<1>(acc, sh, ld, part);
+  block_partials<1>(acc, sh, ld, part, blockIdx.x);
 }
 
 // FCG(1): p = z + beta p (active columns)
@@ -580,9 +501,8 @@ __global__ void k_zero_boundary(int64_t n, const uint8_t* __restrict__ bnd, doub
 // Launched with kFinThreads threads: one warp per (sum, column) pair adds the block partials lane-strided and
 // folds them with a fixed shuffle tree (deterministic), then one thread per column updates its state.
 constexpr int kFinThreads = 1024;
-__global__ void __launch_bounds__(kFinThreads) k_mixed_finalize(int mode, const double* __restrict__ part, int nblk,
-                                                               int NS, int ld, int N, MixState* __restrict__ st,
-                                                               double rtol, double inner_rtol2) {
+__device__ __forceinline__ void finalize_body(int mode, const double* __restrict__ part, int nblk, int NS, int ld,
+                                              int N, MixState* __restrict__ st, double rtol, double inner_rtol2) {
   __shared__ double sums[2 * 256];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int pr = warp; pr < NS * ld; pr += nw) {
@@ -661,6 +581,11 @@ __global__ void __launch_bounds__(kFinThreads) k_mixed_finalize(int mode, const 
     c.beta = 0.0;
   }
   st[j] = c;
+}
+__global__ void __launch_bounds__(kFinThreads) k_mixed_finalize(int mode, const double* __restrict__ part, int nblk,
+                                                               int NS, int ld, int N, MixState* __restrict__ st,
+                                                               double rtol, double inner_rtol2) {
+  finalize_body(mode, part, nblk, NS, ld, N, st, rtol, inner_rtol2);
 }
 
 int pcg_mixed(mk_ctx* ctx, const mk_mesh* m, const double* A64, const double* b, double* x, int ld, int N,
@@ -913,4 +838,386 @@ extern "C" int mk_operator_apply(mk_ctx* ctx, const mk_mesh* m, const mk_molecul
   if (!A) return err;
   MK_TRY(pack_elements<float>(ctx, m, A64, A, s));
   return apply_patch<float>(ctx, m, A, (const float*)x, (float*)y, ld, true, s);
+}
+
+// ------------------------------------------------------------------------------------------------ batched solve
+// Many correction problems (different meshes, molecules, orbital counts) share every launch of the inner FP32
+// PCG iteration.  A device table describes each problem; the operator grid spans the patches of all meshes (block
+// -> problem through blk_prob), the other kernels take the problem from blockIdx.y or from item offsets.  Every
+// kernel body is the single-problem one, so each problem's arithmetic is exactly that of its own solve.
+namespace mk {
+
+struct BatchProb {
+  // patch operator
+  const int32_t *elem_off, *node_off, *conn, *target, *inc_off, *shared_node, *shared_off;
+  const uint16_t* inc;
+  const uint8_t* bnd;
+  const float* A32;
+  float* halo;
+  int64_t n_shared, n;
+  int pe, max_nodes, first_block, ld, N;
+  // PCG state
+  const float* dinv;
+  float *r, *p, *q, *d;
+  MixState* st;
+  double* part;
+};
+
+__device__ __forceinline__ int batch_find(const int64_t* __restrict__ off, int K, int64_t t) {
+  int lo = 0, hi = K;  // largest k with off[k] <= t
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+template <int NLOC>
+__global__ void __launch_bounds__(256) k_bapply(const BatchProb* __restrict__ probs, const int32_t* __restrict__ blk_prob) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int b = blk_prob[blockIdx.x];
+  const BatchProb& P = probs[b];
+  patch_apply<NLOC, float, 4>((int)blockIdx.x - P.first_block, P.elem_off, P.node_off, P.conn, P.A32, P.target,
+                              P.inc_off, P.inc, P.bnd, 1, P.p, P.q, P.halo, P.ld / 4, 0, P.ld, P.pe, P.max_nodes, smraw);
+}
+
+__global__ void k_bhalo(const BatchProb* __restrict__ probs, int K, const int64_t* __restrict__ off) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= off[K]) return;
+  const int b = batch_find(off, K, t);
+  const BatchProb& P = probs[b];
+  halo_sum<float, 4>(t - off[b], P.n_shared, P.shared_node, P.shared_off, P.bnd, 1, P.halo, P.q, P.ld / 4, 0, P.ld);
+}
+
+__global__ void k_bpq(const BatchProb* __restrict__ probs) {
+  const BatchProb& P = probs[blockIdx.y];
+  mixed_pq_body(blockIdx.x, gridDim.x, P.n, P.p, P.q, P.ld, P.part);
+}
+
+__global__ void k_bupdate(const BatchProb* __restrict__ probs) {
+  const BatchProb& P = probs[blockIdx.y];
+  mixed_update_body(blockIdx.x, gridDim.x, P.n, P.st, P.dinv, P.p, P.q, P.d, P.r, P.ld, P.part);
+}
+
+__global__ void k_bp(const BatchProb* __restrict__ probs, int K, const int64_t* __restrict__ off) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= off[K]) return;
+  const int b = batch_find(off, K, t);
+  const BatchProb& P = probs[b];
+  mixed_p_body(t - off[b], P.n, P.st, P.dinv, P.r, P.p, P.ld);
+}
+
+__global__ void __launch_bounds__(kFinThreads) k_bfinalize(int mode, const BatchProb* __restrict__ probs, int nblk,
+                                                          int NS, double rtol, double inner_rtol2) {
+  const BatchProb& P = probs[blockIdx.x];
+  finalize_body(mode, P.part, nblk, NS, P.ld, P.N, P.st, rtol, inner_rtol2);
+}
+
+}  // namespace mk
+
+extern "C" int mk_batch_correction_solve(mk_ctx* ctx, int K, const mk_mesh* const* meshes, const mk_molecule* mols,
+                                         const double* sigmas, const double* const* rhs, double* const* x,
+                                         const int* ld, const int* N, const mk_solve_opts* opts,
+                                         mk_solve_report* reports, void* stream) {
+  MK_ARG(ctx && meshes && mols && sigmas && rhs && x && ld && N && opts && reports,
+         "mk_batch_correction_solve: null argument");
+  MK_ARG(K >= 1 && K <= MK_MAX_BATCH, "mk_batch_correction_solve: bad K");
+  MK_ARG(opts->precision == MK_PREC_MIXED && opts->precond == MK_PRECOND_JACOBI && !opts->coarse &&
+             opts->rtol > 0 && opts->maxit > 0,
+         "mk_batch_correction_solve: mixed precision with Jacobi only");
+  MK_ARG(meshes[0], "mk_batch_correction_solve: null mesh");
+  const int nloc = meshes[0]->fine.nloc;
+  for (int k = 0; k < K; ++k) {
+    MK_ARG(meshes[k] && rhs[k] && x[k], "mk_batch_correction_solve: null problem");
+    MK_ARG(meshes[k]->fine.nloc == nloc, "mk_batch_correction_solve: all meshes must use one element order");
+    MK_ARG(ld[k] == 4 || ld[k] == 8 || ld[k] == 16, "mk_batch_correction_solve: ld must be 4, 8 or 16");
+    MK_ARG(N[k] >= 1 && N[k] <= ld[k], "mk_batch_correction_solve: bad N");
+  }
+  MK_CUDA(cudaSetDevice(ctx->device));
+  const mk_solve_opts& o = *opts;
+  cudaStream_t caller = (cudaStream_t)stream;
+  MK_CUDA(cudaEventRecord(ctx->solve_ev[0], caller));
+  MK_CUDA(cudaStreamWaitEvent(ctx->solve_stream, ctx->solve_ev[0], 0));
+  cudaStream_t s = ctx->solve_stream;
+  const int nblk = red_blocks(ctx);
+  const int np = nloc * (nloc + 1) / 2, nps = padded_np(nloc, 4);
+  // one scratch region: per-problem buffers, then the device tables
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o2 = off; off += (bytes + 255) / 256 * 256; return o2; };
+  std::vector<size_t> oA64(K), oA32(K), oDiag(K), oDinv(K), oAx(K), oR(K), oP(K), oQ(K), oD(K), oH(K), oPart(K);
+  int64_t nblocks = 0, hitems = 0, pitems = 0;
+  size_t smem = 0;
+  for (int k = 0; k < K; ++k) {
+    const Level& L = meshes[k]->fine;
+    const Patches& P = meshes[k]->patches;
+    const size_t n = (size_t)L.n_nodes, v32 = n * ld[k] * sizeof(float);
+    oA64[k] = take((size_t)L.n_elems * np * 8);
+    oA32[k] = take((size_t)L.n_elems * nps * 4);
+    oDiag[k] = take(n * 8);
+    oDinv[k] = take(n * 4);
+    oAx[k] = take(n * ld[k] * 8);
+    oR[k] = take(v32);
+    oP[k] = take(v32);
+    oQ[k] = take(v32);
+    oD[k] = take(v32);
+    oH[k] = take((size_t)std::max<int64_t>(P.n_halo_slots, 1) * ld[k] * 4);
+    oPart[k] = take((size_t)nblk * 2 * ld[k] * 8);
+    nblocks += P.n_patches;
+    hitems += P.n_shared_nodes * (ld[k] / 4);
+    pitems += (int64_t)n * ld[k];
+    smem = std::max(smem, patch_smem(nloc, P.max_elems, P.max_nodes, ld[k], 4).total);
+  }
+  MK_ARG(smem <= 227 * 1024, "mk_batch_correction_solve: patch too large for shared memory");
+  const size_t oSt = take((size_t)K * 16 * sizeof(MixState)), oProbs = take((size_t)K * sizeof(BatchProb));
+  const size_t oBlk = take((size_t)nblocks * 4), oHoff = take((size_t)(K + 1) * 8), oPoff = take((size_t)(K + 1) * 8);
+  int err = MK_OK;
+  char* ws = (char*)scratch(ctx, S_BATCH, off, &err);
+  if (!ws) return err;
+  if (ctx->pinned_size < (size_t)K * 16 * sizeof(MixState)) {
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    ctx->pinned = nullptr;
+    ctx->pinned_size = 0;
+    MK_CUDA(cudaMallocHost(&ctx->pinned, (size_t)K * 16 * sizeof(MixState)));
+    ctx->pinned_size = (size_t)K * 16 * sizeof(MixState);
+  }
+  MixState* hst = (MixState*)ctx->pinned;
+  MixState* dst = (MixState*)(ws + oSt);
+  std::vector<BatchProb> hp(K);
+  std::vector<int32_t> blk(nblocks);
+  std::vector<int64_t> hoff(K + 1, 0), poff(K + 1, 0);
+  int64_t b0 = 0;
+  for (int k = 0; k < K; ++k) {
+    const mk_mesh* m = meshes[k];
+    const Level& L = m->fine;
+    const Patches& P = m->patches;
+    BatchProb& B = hp[k];
+    B.elem_off = P.d_patch_elem_off;
+    B.node_off = P.d_patch_node_off;
+    B.conn = P.d_conn;
+    B.target = P.d_node_target;
+    B.inc_off = P.d_inc_off;
+    B.shared_node = P.d_shared_node;
+    B.shared_off = P.d_shared_off;
+    B.inc = P.d_inc;
+    B.bnd = L.d_boundary;
+    B.A32 = (const float*)(ws + oA32[k]);
+    B.halo = (float*)(ws + oH[k]);
+    B.n_shared = P.n_shared_nodes;
+    B.n = L.n_nodes;
+    B.pe = P.max_elems;
+    B.max_nodes = P.max_nodes;
+    B.first_block = (int)b0;
+    B.ld = ld[k];
+    B.N = N[k];
+    B.dinv = (const float*)(ws + oDinv[k]);
+    B.r = (float*)(ws + oR[k]);
+    B.p = (float*)(ws + oP[k]);
+    B.q = (float*)(ws + oQ[k]);
+    B.d = (float*)(ws + oD[k]);
+    B.st = dst + (size_t)k * 16;
+    B.part = (double*)(ws + oPart[k]);
+    for (int i = 0; i < P.n_patches; ++i) blk[b0 + i] = k;
+    b0 += P.n_patches;
+    hoff[k + 1] = hoff[k] + P.n_shared_nodes * (ld[k] / 4);
+    poff[k + 1] = poff[k] + L.n_nodes * ld[k];
+  }
+  BatchProb* dprobs = (BatchProb*)(ws + oProbs);
+  int32_t* dblk = (int32_t*)(ws + oBlk);
+  int64_t* dhoff = (int64_t*)(ws + oHoff);
+  int64_t* dpoff = (int64_t*)(ws + oPoff);
+  MK_CUDA(cudaMemcpyAsync(dprobs, hp.data(), (size_t)K * sizeof(BatchProb), cudaMemcpyHostToDevice, s));
+  MK_CUDA(cudaMemcpyAsync(dblk, blk.data(), (size_t)nblocks * 4, cudaMemcpyHostToDevice, s));
+  MK_CUDA(cudaMemcpyAsync(dhoff, hoff.data(), (size_t)(K + 1) * 8, cudaMemcpyHostToDevice, s));
+  MK_CUDA(cudaMemcpyAsync(dpoff, poff.data(), (size_t)(K + 1) * 8, cudaMemcpyHostToDevice, s));
+  MK_CUDA(cudaMemsetAsync(dst, 0, (size_t)K * 16 * sizeof(MixState), s));
+  MK_CUDA(cudaStreamSynchronize(s));  // the host tables above may go out of scope only after the copies
+  // per problem: operator K/2 + M_Vext + sigma M (FP64 element matrices, FP32 patch copy), Jacobi diagonal
+  for (int k = 0; k < K; ++k) {
+    const mk_mesh* m = meshes[k];
+    const Level& L = m->fine;
+    double* A64 = (double*)(ws + oA64[k]);
+    const double* H0 = static_matrices(ctx, m, &mols[k], s, &err);
+    if (!H0) return err;
+    MK_TRY(element_matrices(ctx, L, nullptr, 0.0, 0.0, sigmas[k], nullptr, A64, s, H0));
+    MK_TRY(assemble_diagonal(ctx, L, A64, (double*)(ws + oDiag[k]), s));
+    MK_TRY(pack_elements<float>(ctx, m, A64, (float*)(ws + oA32[k]), s));
+    MK_COUNT(), k_dinv32<<<(int)((L.n_nodes + 255) / 256), 256, 0, s>>>(L.n_nodes, (const double*)(ws + oDiag[k]),
+                                                                         (float*)(ws + oDinv[k]));
+    MK_COUNT(), k_zero_boundary<<<(int)((L.n_nodes * ld[k] + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, x[k],
+                                                                                         ld[k]);
+  }
+  if (nloc == 4) MK_CUDA(cudaFuncSetAttribute(k_bapply<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  else MK_CUDA(cudaFuncSetAttribute(k_bapply<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int check = std::max(1, o.check_every);
+  const double inner2 = o.inner_rtol * o.inner_rtol;
+  const int max_refine = o.max_refine > 0 ? o.max_refine : 20;
+  auto iteration = [&]() -> int {  // one inner PCG iteration of every problem
+    if (nloc == 4) MK_COUNT(), k_bapply<4><<<(int)nblocks, 256, smem, s>>>(dprobs, dblk);
+    else MK_COUNT(), k_bapply<10><<<(int)nblocks, 256, smem, s>>>(dprobs, dblk);
+    if (hitems > 0) MK_COUNT(), k_bhalo<<<(int)((hitems + 255) / 256), 256, 0, s>>>(dprobs, K, dhoff);
+    MK_COUNT(), k_bpq<<<dim3(nblk, K), 256, 0, s>>>(dprobs);
+    MK_COUNT(), k_bfinalize<<<K, kFinThreads, 0, s>>>(2, dprobs, nblk, 1, o.rtol, inner2);
+    MK_COUNT(), k_bupdate<<<dim3(nblk, K), 256, 0, s>>>(dprobs);
+    MK_COUNT(), k_bfinalize<<<K, kFinThreads, 0, s>>>(3, dprobs, nblk, 2, o.rtol, inner2);
+    MK_COUNT(), k_bp<<<(int)((pitems + 255) / 256), 256, 0, s>>>(dprobs, K, dpoff);
+    return MK_OK;
+  };
+  std::vector<int> refines(K, 0);
+  std::vector<char> conv(K, 0);
+  int total_it = 0, status = MK_OK;
+  cudaGraphExec_t exec = nullptr;
+  long long graph_kernels = 0;
+  for (int refine = 0;; ++refine) {
+    for (int k = 0; k < K; ++k) {  // FP64 residual of every problem
+      const BatchProb& B = hp[k];
+      MK_TRY(apply64(ctx, meshes[k], (const double*)(ws + oA64[k]), x[k], (double*)(ws + oAx[k]), ld[k], ld[k], true,
+                     s));
+      MK_COUNT(), k_mixed_residual<<<nblk, 256, 0, s>>>(B.n, B.bnd, rhs[k], (const double*)(ws + oAx[k]), B.r, B.d,
+                                                         N[k], ld[k], B.part);
+      MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(0, B.part, nblk, 2, ld[k], N[k], B.st, o.rtol, inner2);
+    }
+    MK_CUDA(cudaMemcpyAsync(hst, dst, (size_t)K * 16 * sizeof(MixState), cudaMemcpyDeviceToHost, s));
+    MK_CUDA(cudaStreamSynchronize(s));
+    bool any = false;
+    for (int k = 0; k < K; ++k) {
+      bool a = false;
+      for (int j = 0; j < N[k]; ++j) a |= hst[k * 16 + j].outer_active != 0;
+      conv[k] = !a;
+      any |= a;
+    }
+    if (!any || refine >= max_refine || total_it >= o.maxit) break;
+    for (int k = 0; k < K; ++k) {
+      const BatchProb& B = hp[k];
+      if (!conv[k]) refines[k] += 1;
+      MK_COUNT(), k_mixed_init<<<nblk, 256, 0, s>>>(B.n, B.dinv, B.r, B.p, ld[k], B.part);
+      MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(1, B.part, nblk, 2, ld[k], N[k], B.st, o.rtol, inner2);
+    }
+    bool inner_active = true;
+    while (inner_active && total_it < o.maxit) {
+      const int kk = std::min(check, o.maxit - total_it);
+      if (!ctx->no_graphs && kk == check) {
+        if (!exec) {  // one graph of `check` iterations of the whole batch, replayed for the rest of the solve
+          const long long c0 = g_launch_count.load();
+          MK_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+          int rc = MK_OK;
+          for (int c = 0; c < check && rc == MK_OK; ++c) rc = iteration();
+          cudaGraph_t graph = nullptr;
+          const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+          if (rc != MK_OK) return rc;
+          if (ce != cudaSuccess) return fail(MK_ERR_CUDA, std::string("batch graph capture: ") + cudaGetErrorString(ce));
+          MK_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+          cudaGraphDestroy(graph);
+          graph_kernels = g_launch_count.load() - c0;
+          g_launch_count.fetch_sub(graph_kernels);
+        }
+        MK_CUDA(cudaGraphLaunch(exec, s));
+        g_launch_count.fetch_add(graph_kernels);
+      } else {
+        for (int c = 0; c < kk; ++c) MK_TRY(iteration());
+      }
+      total_it += kk;
+      MK_CUDA(cudaMemcpyAsync(hst, dst, (size_t)K * 16 * sizeof(MixState), cudaMemcpyDeviceToHost, s));
+      MK_CUDA(cudaStreamSynchronize(s));
+      inner_active = false;
+      for (int k = 0; k < K; ++k)
+        for (int j = 0; j < N[k]; ++j) {
+          inner_active |= hst[k * 16 + j].active != 0;
+          if (hst[k * 16 + j].breakdown) status = MK_ERR_BREAKDOWN;
+        }
+      if (status == MK_ERR_BREAKDOWN) break;
+    }
+    for (int k = 0; k < K; ++k) {
+      const BatchProb& B = hp[k];
+      MK_COUNT(), k_mixed_add<<<(int)((B.n * ld[k] + 255) / 256), 256, 0, s>>>(B.n, B.d, x[k], N[k], ld[k]);
+    }
+    if (status == MK_ERR_BREAKDOWN) break;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  MK_CUDA(cudaGetLastError());
+  // reports from the last FP64 residual (taken at the top of the final pass of the refinement loop)
+  int worst = status;
+  for (int k = 0; k < K; ++k) {
+    mk_solve_report& R = reports[k];
+    std::memset(&R, 0, sizeof(R));
+    R.n_rhs = N[k];
+    R.refinements = refines[k];
+    double mx = 0.0;
+    int its = 0;
+    for (int j = 0; j < N[k]; ++j) {
+      const MixState& c = hst[k * 16 + j];
+      R.iters[j] = c.iters;
+      R.rel_residual[j] = std::sqrt(c.rr64) / c.bn;
+      mx = std::max(mx, R.rel_residual[j]);
+      its = std::max(its, c.iters);
+      if (c.breakdown) R.status = MK_ERR_BREAKDOWN;
+    }
+    R.iterations = its;
+    R.max_rel_residual = mx;
+    if (R.status == MK_OK && !conv[k]) R.status = MK_ERR_NOT_CONVERGED;
+    if (R.status != MK_OK && worst == MK_OK) worst = R.status;
+  }
+  MK_CUDA(cudaEventRecord(ctx->solve_ev[1], s));
+  MK_CUDA(cudaStreamWaitEvent(caller, ctx->solve_ev[1], 0));
+  if (worst == MK_ERR_BREAKDOWN) return fail(worst, "batched PCG breakdown: p^T A p <= 0 in some problem");
+  if (worst == MK_ERR_NOT_CONVERGED) return fail(worst, "batched PCG: some problem did not reach rtol");
+  return MK_OK;
+}
+
+extern "C" int mk_mesh_set_patch_elems(mk_mesh* m, int pe) {
+  MK_ARG(m, "mk_mesh_set_patch_elems: null mesh");
+  MK_ARG(pe >= 32 && pe <= 512 && pe % 32 == 0, "mk_mesh_set_patch_elems: pe must be a multiple of 32 in [32, 512]");
+  MK_CUDA(cudaSetDevice(m->device));
+  MK_CUDA(cudaDeviceSynchronize());  // no kernel may still read the old patches
+  free_patches(m->patches);
+  return build_patches(m, pe);
+}
+
+extern "C" int mk_autotune_patches(mk_ctx* ctx, mk_mesh* m, int ld, int* best_pe, double* ms_out) {
+  MK_ARG(ctx && m && best_pe, "mk_autotune_patches: null argument");
+  MK_ARG(ld >= 1 && ld <= 256, "mk_autotune_patches: bad ld");
+  MK_CUDA(cudaSetDevice(ctx->device));
+  const Level& L = m->fine;
+  const int cand2[4] = {64, 96, 128, 192}, cand1[4] = {128, 192, 256, 384};
+  const int* cand = L.nloc == 10 ? cand2 : cand1;
+  const int np = L.nloc * (L.nloc + 1) / 2;
+  int err = MK_OK;
+  double* A64 = (double*)scratch(ctx, S_OPA, (size_t)L.n_elems * np * sizeof(double), &err);
+  float* A = (float*)scratch(ctx, S_OPB, (size_t)L.n_elems * padded_np(L.nloc, 4) * sizeof(float), &err);
+  float* xy = (float*)scratch(ctx, S_VEC4, (size_t)L.n_nodes * ld * 2 * sizeof(float), &err);
+  if (!A64 || !A || !xy) return err;
+  cudaStream_t s = ctx->solve_stream;
+  MK_TRY(element_matrices(ctx, L, nullptr, 0.5, 0.0, 1.0, nullptr, A64, s));  // K/2 + M: timing stand-in
+  MK_CUDA(cudaMemsetAsync(xy, 0, (size_t)L.n_nodes * ld * 2 * sizeof(float), s));
+  cudaEvent_t e0, e1;
+  MK_CUDA(cudaEventCreate(&e0));
+  MK_CUDA(cudaEventCreate(&e1));
+  double best = 1e300;
+  int bpe = cand[0];
+  for (int c = 0; c < 4; ++c) {
+    int r = mk_mesh_set_patch_elems(m, cand[c]);
+    if (r == MK_OK) r = pack_elements<float>(ctx, m, A64, A, s);
+    for (int w = 0; w < 3 && r == MK_OK; ++w) r = apply_patch<float>(ctx, m, A, xy, xy + L.n_nodes * ld, ld, true, s);
+    double ms = 1e300;
+    if (r == MK_OK) {
+      cudaEventRecord(e0, s);
+      for (int it = 0; it < 10 && r == MK_OK; ++it)
+        r = apply_patch<float>(ctx, m, A, xy, xy + L.n_nodes * ld, ld, true, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      ms = t / 10.0;
+    } else {
+      cudaGetLastError();  // a candidate whose shared memory does not fit is skipped
+    }
+    if (ms_out) ms_out[c] = r == MK_OK ? ms : -1.0;
+    if (r == MK_OK && ms < best) {
+      best = ms;
+      bpe = cand[c];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *best_pe = bpe;
+  return mk_mesh_set_patch_elems(m, bpe);
 }

@@ -95,4 +95,119 @@ __host__ __device__ inline PatchSmem patch_smem(int nloc, int pe, int max_nodes,
   return L;
 }
 
+// y = A x for one patch per CTA: owner-computes scatter, fixed summation order, no atomics.
+// Staging: the patch's element matrices, connectivity, incidence lists and node targets are copied into shared
+// memory asynchronously, all at once.  Phase 1: element products y_e = A_e x_e (x gathered from global, mostly L2
+// hits) into shared memory laid out [slot][element][column]; one thread per element and group of VEC columns.
+// Each element matrix is read from shared memory once (packed order), with all output rows held in registers.
+// Phase 2: each local node sums its incidences in fixed order (shared memory only) and writes the global row
+// (owned node) or its halo slot (shared node).  Columns [col0, col0 + W) with W = ncolg * VEC.
+template <int NLOC, typename T, int VEC>
+__device__ __forceinline__ void patch_apply(int p, const int32_t* __restrict__ elem_off,
+                                                     const int32_t* __restrict__ node_off,
+                                                     const int32_t* __restrict__ conn, const T* __restrict__ Ae,
+                                                     const int32_t* __restrict__ target,
+                                                     const int32_t* __restrict__ inc_off,
+                                                     const uint16_t* __restrict__ inc,
+                                                     const uint8_t* __restrict__ bnd, int mask,
+                                                     const T* __restrict__ x, T* __restrict__ y, T* __restrict__ halo,
+                                                     int ncolg, int col0, int ld, int pe, int max_nodes,
+                                                     unsigned char* smraw) {
+  constexpr int NPS = padded_np(NLOC, (int)sizeof(T));
+  const int W = ncolg * VEC;
+  const PatchSmem lay = patch_smem(NLOC, pe, max_nodes, W, (int)sizeof(T));
+  T* Ye = reinterpret_cast<T*>(smraw + lay.ye);  // [NLOC][pe][W]
+  const int e0 = elem_off[p], ne = elem_off[p + 1] - e0;
+  const int n0 = node_off[p], nl = node_off[p + 1] - n0;
+  const int ibase = e0 * NLOC;  // the patch's incidences are inc[ibase, ibase + ne * NLOC)
+  const T* As = stage_async(smraw + lay.as, Ae + (int64_t)e0 * NPS, ne * NPS * (int)sizeof(T));
+  const int32_t* cs = stage_async(smraw + lay.conn, conn + ibase, ne * NLOC * 4);
+  const uint16_t* is = stage_async(smraw + lay.inc, inc + ibase, ne * NLOC * 2);
+  const int32_t* os = stage_async(smraw + lay.ioff, inc_off + n0, (nl + 1) * 4);
+  const int32_t* ts = stage_async(smraw + lay.tgt, target + n0, nl * 4);
+  cp_async_wait_all();
+  __syncthreads();
+  for (int it = threadIdx.x; it < ne * ncolg; it += blockDim.x) {
+    const int el = it / ncolg, g = it - el * ncolg;
+    Vec<T, VEC> xv[NLOC];
+#pragma unroll
+    for (int a = 0; a < NLOC; ++a) xv[a] = ldv<T, VEC>(x + (int64_t)cs[el * NLOC + a] * ld + col0 + g * VEC);
+    // one pass over the packed upper triangle: each entry is read once and feeds rows a and b; nothing is
+    // stored until every row is complete
+    const T* A = As + el * NPS;
+    Vec<T, VEC> acc[NLOC];
+#pragma unroll
+    for (int a = 0; a < NLOC; ++a)
+#pragma unroll
+      for (int c = 0; c < VEC; ++c) acc[a].v[c] = 0;
+#pragma unroll
+    for (int a = 0; a < NLOC; ++a)
+#pragma unroll
+      for (int b = a; b < NLOC; ++b) {
+        const T w = A[sym_index(a, b, NLOC)];
+#pragma unroll
+        for (int c = 0; c < VEC; ++c) {
+          acc[a].v[c] += w * xv[b].v[c];
+          if (b != a) acc[b].v[c] += w * xv[a].v[c];
+        }
+      }
+#pragma unroll
+    for (int a = 0; a < NLOC; ++a) stv<T, VEC>(Ye + ((size_t)a * pe + el) * W + g * VEC, acc[a]);
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < nl * ncolg; it += blockDim.x) {
+    const int l = it / ncolg, g = it - l * ncolg;
+    const int b = os[l] - ibase, e = os[l + 1] - ibase;
+    Vec<T, VEC> acc;
+#pragma unroll
+    for (int c = 0; c < VEC; ++c) acc.v[c] = 0;
+    auto ye = [&](int k) {  // product of incidence k (slot * pe + local element)
+      return ldv<T, VEC>(Ye + (size_t)is[k] * W + g * VEC);
+    };
+    int k = b;
+    for (; k + 4 <= e; k += 4) {  // four independent loads, then the sums in list order
+      const Vec<T, VEC> v0 = ye(k), v1 = ye(k + 1), v2 = ye(k + 2), v3 = ye(k + 3);
+#pragma unroll
+      for (int c = 0; c < VEC; ++c) acc.v[c] = (((acc.v[c] + v0.v[c]) + v1.v[c]) + v2.v[c]) + v3.v[c];
+    }
+    for (; k < e; ++k) {
+      const Vec<T, VEC> v = ye(k);
+#pragma unroll
+      for (int c = 0; c < VEC; ++c) acc.v[c] += v.v[c];
+    }
+    const int t = ts[l];
+    if (t >= 0) {
+      if (mask && bnd[t])
+#pragma unroll
+        for (int c = 0; c < VEC; ++c) acc.v[c] = 0;
+      stv<T, VEC>(y + (int64_t)t * ld + col0 + g * VEC, acc);
+    } else {
+      stv<T, VEC>(halo + (int64_t)(-t - 1) * ld + col0 + g * VEC, acc);
+    }
+  }
+}
+
+// Shared nodes: y[node] = sum of the node's halo slots in patch order; item t = (shared node, column group).
+template <typename T, int VEC>
+__device__ __forceinline__ void halo_sum(int64_t t, int64_t nshared, const int32_t* __restrict__ node,
+                                         const int32_t* __restrict__ off, const uint8_t* __restrict__ bnd, int mask,
+                                         const T* __restrict__ halo, T* __restrict__ y, int ncolg, int col0, int ld) {
+  if (t >= nshared * ncolg) return;
+  const int64_t k = t / ncolg;
+  const int g = (int)(t - k * ncolg);
+  Vec<T, VEC> acc;
+#pragma unroll
+  for (int c = 0; c < VEC; ++c) acc.v[c] = 0;
+  for (int s = off[k]; s < off[k + 1]; ++s) {
+    const Vec<T, VEC> v = ldv<T, VEC>(halo + (int64_t)s * ld + col0 + g * VEC);
+#pragma unroll
+    for (int c = 0; c < VEC; ++c) acc.v[c] += v.v[c];
+  }
+  const int nd = node[k];
+  if (mask && bnd[nd])
+#pragma unroll
+    for (int c = 0; c < VEC; ++c) acc.v[c] = 0;
+  stv<T, VEC>(y + (int64_t)nd * ld + col0 + g * VEC, acc);
+}
+
 }  // namespace mk

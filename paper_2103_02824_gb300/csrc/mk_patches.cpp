@@ -47,12 +47,12 @@ static int up(T** dst, const std::vector<T>& src) {
   return MK_OK;
 }
 
-int build_patches(mk_mesh* m) {
+int build_patches(mk_mesh* m, int pe) {
   const Level& L = m->fine;
   Patches& P = m->patches;
   const int nloc = L.nloc;
   const int64_t E = L.n_elems, nn = L.n_nodes;
-  const int PE = patch_elems(nloc);
+  const int PE = pe > 0 ? pe : patch_elems(nloc);
   // Morton order of element centroids
   double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
   for (int64_t v = 0; v < L.n_vertices; ++v)

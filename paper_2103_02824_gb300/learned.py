@@ -23,7 +23,7 @@ class Problem:
         self.ctx, self.mesh, self.Z, self.R = ctx, mesh, np.asarray(Z, float), np.asarray(R, float)
         info = mesh.info
         self.N = synth.n_orbitals(self.Z)
-        self.ld = max(4, (self.N + 3) // 4 * 4)
+        self.ld = 4 if self.N <= 4 else 8 if self.N <= 8 else 16 if self.N <= 16 else (self.N + 3) // 4 * 4
         self.mol = mk.Molecule(self.Z, self.R)
         occ = synth.occupations(self.Z)
         theta = mk.mk_lowest_ritz(ctx, mesh, self.mol, synth.lanczos_start(info["n_free"], lanczos_seed), steps=60)

@@ -110,6 +110,11 @@ _SIGS = {
     "mk_small_eigensolve_static": [C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "mk_orbital_assemble": [_vp, _vp, _vp, _vp, _vp, C.c_int, C.c_int, _vp, _vp],
     "mk_lowest_ritz": [_vp, _vp, C.POINTER(mk_molecule), C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double), _vp],
+    "mk_batch_correction_solve": [_vp, C.c_int, C.POINTER(_vp), C.POINTER(mk_molecule), C.POINTER(C.c_double),
+                                  C.POINTER(_vp), C.POINTER(_vp), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                  C.POINTER(mk_solve_opts), C.POINTER(mk_solve_report), _vp],
+    "mk_mesh_set_patch_elems": [_vp, C.c_int],
+    "mk_autotune_patches": [_vp, _vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "mk_mlp_param_count": [C.c_int],
     "mk_mlp_create": [_vp, C.c_int, C.POINTER(C.c_float), C.POINTER(_vp)],
     "mk_mlp_destroy": [_vp],
@@ -389,6 +394,38 @@ def mk_correction_solve(ctx, mesh, mol: Molecule, sigma, rhs, x, N, opt=None, st
     d = rep.to_dict()
     d["code"] = code
     return d
+
+
+def mk_batch_correction_solve(ctx, meshes, mols, sigmas, rhs_list, x_list, Ns, opt=None, stream=None, allow=()):
+    """Correction solves of K molecules in shared launches (see include/mk.h); returns K report dicts."""
+    K = len(meshes)
+    mh = (_vp * K)(*[m.h.value for m in meshes])
+    ml = (mk_molecule * K)(*[mo.c for mo in mols])
+    sg = (C.c_double * K)(*[float(v) for v in sigmas])
+    rp = (_vp * K)(*[_ptr(r).value for r in rhs_list])
+    xp = (_vp * K)(*[_ptr(x).value for x in x_list])
+    lds = (C.c_int * K)(*[int(x.shape[1]) for x in x_list])
+    ns = (C.c_int * K)(*[int(n) for n in Ns])
+    reps = (mk_solve_report * K)()
+    o = opt or opts(precision="mixed")
+    code = lib().mk_batch_correction_solve(ctx.h, K, mh, ml, sg, rp, xp, lds, ns, C.byref(o), reps, _stream(stream))
+    _check(code, allow)
+    out = [r.to_dict() for r in reps]
+    for d in out:
+        d["code"] = code
+    return out
+
+
+def mk_mesh_set_patch_elems(mesh, pe):
+    _check(lib().mk_mesh_set_patch_elems(mesh.h, int(pe)))
+
+
+def mk_autotune_patches(ctx, mesh, ld):
+    """(best elements per patch, [ms per application of each candidate])"""
+    best = C.c_int()
+    ms = (C.c_double * 4)()
+    _check(lib().mk_autotune_patches(ctx.h, mesh.h, int(ld), C.byref(best), ms))
+    return best.value, list(ms)
 
 
 def mk_augmented_project(ctx, mesh, mol: Molecule, vq, psihat, N, AH, MH, b, c, beta, gamma, gramA=None, gramM=None,
