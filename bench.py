@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--precond", default="learned", choices=["learned", "jacobi"],
                     help="inner preconditioner of the mixed-precision correction solve (learned: FCG(1))")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve measurement")
     ap.add_argument("--mode", default="step", choices=["step", "apply"],
                     help="apply: time the FP32 element-by-element operator alone (kernel-level roofline)")
     return ap.parse_args()
@@ -322,6 +323,45 @@ def main():
         mk.profile_enable(ctx, False)
         iso_ms = ims / inn if inn else None
 
+    # batching: the correction solves of 8 other seeded molecules on mid-size meshes, batched (shared launches)
+    # against one after the other, same options
+    batch = None
+    if a.precision == "mixed" and world == 1 and not a.no_batch:
+        from paper_2103_02824_gb300 import learned
+        bw = synth.workload("mol4_p2_mid")
+        bmeshes = [upload_workload(ctx, bw)[0] for _ in range(8)]
+        bprobs = [learned.Problem(ctx, bm, *synth.molecule(sd, 4)) for bm, sd in zip(bmeshes, range(20, 28))]
+        bopt = mk.opts(precision="mixed", rtol=1e-8, check_every=10)
+        units_b = sum(float(bm.info["n_free"]) * bp.N for bm, bp in zip(bmeshes, bprobs))
+        for _ in range(2):  # warm-up of both forms
+            for bp in bprobs:
+                bp.solve(bopt)
+            mk.mk_batch_correction_solve(ctx, bmeshes, [bp.mol for bp in bprobs], [bp.sigma for bp in bprobs],
+                                         [bp.rhs for bp in bprobs], [bp.u.clone() for bp in bprobs],
+                                         [bp.N for bp in bprobs], opt=bopt)
+        torch.cuda.synchronize()
+        xs = [bp.u.clone() for bp in bprobs]
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record()
+        for bp in bprobs:
+            bp.solve(bopt)
+        c1.record()
+        torch.cuda.synchronize()
+        seq_ms = c0.elapsed_time(c1)
+        c0.record()
+        breps = mk.mk_batch_correction_solve(ctx, bmeshes, [bp.mol for bp in bprobs], [bp.sigma for bp in bprobs],
+                                             [bp.rhs for bp in bprobs], xs, [bp.N for bp in bprobs], opt=bopt)
+        c1.record()
+        torch.cuda.synchronize()
+        bat_ms = c0.elapsed_time(c1)
+        batch = {"molecules": "synth.molecule(seed, 4), seeds 20-27, each on its own mol4_p2_mid mesh (24,576 P2 tets)",
+                 "orbitals": [bp.N for bp in bprobs], "correction_solves_ms_batched": bat_ms,
+                 "correction_solves_ms_sequential": seq_ms,
+                 "value_batched": units_b / (bat_ms * 1e-3), "value_sequential": units_b / (seq_ms * 1e-3),
+                 "unit": UNIT, "max_rel_residual": max(r["max_rel_residual"] for r in breps)}
+        for bm in bmeshes:
+            bm.close()
+
     # roofline of the dominant kernel (the element-by-element operator application)
     kind = mk.PROF_APPLY32 if prof[mk.PROF_APPLY32][1] > 0 else mk.PROF_APPLY64
     ms_k, n_k = prof[kind]
@@ -383,7 +423,7 @@ def main():
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "gpu_launches_per_step": launches / a.steps,
             "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
-            "compare": compare, "training": train_info,
+            "compare": compare, "training": train_info, "batch": batch,
             "solve_iterations": solve["iterations"], "solve_max_rel_residual": solve["max_rel_residual"],
             "poisson_iterations": reps["poisson"]["iterations"] if reps["poisson"] else None,
             "lambda": [float(x) for x in lam_head],
