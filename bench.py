@@ -49,8 +49,9 @@ def parse():
                     help="inner preconditioner of the mixed-precision correction solve (learned: FCG(1))")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve measurement")
-    ap.add_argument("--mode", default="step", choices=["step", "apply"],
-                    help="apply: time the FP32 element-by-element operator alone (kernel-level roofline)")
+    ap.add_argument("--mode", default="step", choices=["step", "apply", "learned"],
+                    help="apply: time the FP32 element-by-element operator alone (kernel-level roofline); "
+                         "learned: time the learned preconditioner (BF16 network) alone")
     return ap.parse_args()
 
 
@@ -88,6 +89,40 @@ def apply_mode(a):
     print(json.dumps({"mode": "apply", "workload": a.workload, "ld": ld, "applications": n,
                       "patch_ms": ms / n, "halo_ms": hms / max(hn, 1), "bytes_per_application": nbytes,
                       "achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak}))
+
+
+def learned_mode(a):
+    """Times mk_learned_precond (BF16 tensor-core network, untrained seeded weights) on the workload's mesh."""
+    import torch
+    from paper_2103_02824_gb300 import build, mk, synth
+    from paper_2103_02824_gb300.step import upload_workload
+    build.build()
+    wl = synth.workload(a.workload)
+    ctx = mk.Context(0)
+    mesh, _ = upload_workload(ctx, wl)
+    info = mesh.info
+    N = synth.n_orbitals(wl["Z"])
+    ld = max(4, (N + 3) // 4 * 4)
+    mol = mk.Molecule(wl["Z"], wl["R"])
+    mlp = mk.Mlp(ctx, info["nloc"], synth.mlp_init(info["nloc"], 0))
+    g = torch.Generator(device="cuda").manual_seed(5)
+    r = torch.randn((info["n_nodes"], ld), generator=g, device="cuda", dtype=torch.float32)
+    z = torch.empty_like(r)
+    for _ in range(a.warmup):
+        mk.mk_learned_precond(ctx, mesh, mlp, mol, 18.0, r, z, N)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        mk.mk_learned_precond(ctx, mesh, mlp, mol, 18.0, r, z, N)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.steps
+    rows = info["n_elems"] * N
+    flops = 2.0 * (22 * 64 + 64 * 64 + 64 * 10) * rows if info["nloc"] == 10 else 2.0 * (16 * 64 + 64 * 64 + 64 * 4) * rows
+    print(json.dumps({"mode": "learned", "workload": a.workload, "N": N, "ms_per_application": ms,
+                      "note": "includes the operator diagonal (element matrices + assembly) recomputed per call",
+                      "network_tflops": flops / (ms * 1e-3) / 1e12}))
 
 
 def workload_config(wl, N, n_free, NH, E):
@@ -182,6 +217,8 @@ def main():
         return reference(a, rank, world)
     if a.mode == "apply":
         return apply_mode(a)
+    if a.mode == "learned":
+        return learned_mode(a)
     import numpy as np
     import torch
     torch.cuda.set_device(local)

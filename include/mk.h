@@ -181,6 +181,13 @@ int mk_hartree_poisson(mk_ctx* ctx, const mk_mesh* mesh, const double* u, int ld
 int mk_assemble_rhs(mk_ctx* ctx, const mk_mesh* mesh, const double* u, int ld, const double* lambdaH,
                     const double* occ, int N, const double* w, double sigma, mk_xc xc, double* rhs, double* vq,
                     void* stream);
+/* The two halves of mk_assemble_rhs, so that the coarse pencil (which needs vq, not rhs) can start on another
+ * stream as soon as vq exists.  mk_frozen_potential: rho_H = sum_i occ[i] u_i^2 and vq = w + V_xc(rho_H) at the
+ * quadrature points [n_elems * n_quad].  mk_assemble_rhs_from_vq: rhs from u and that vq (as mk_assemble_rhs). */
+int mk_frozen_potential(mk_ctx* ctx, const mk_mesh* mesh, const double* u, int ld, const double* occ, int N,
+                        const double* w, mk_xc xc, double* vq, void* stream);
+int mk_assemble_rhs_from_vq(mk_ctx* ctx, const mk_mesh* mesh, const double* u, int ld, const double* lambdaH, int N,
+                            const double* vq, double sigma, double* rhs, void* stream);
 
 /* ---------------------------------------------------------------------------------------------- A4 */
 /* Solves (K/2 + M_{V_ext} + sigma M) x_i = rhs_i on the free fine DOF for i < N at once (Eq. (Aux_Linear_Problem),

@@ -101,7 +101,8 @@ struct Patches {
   int32_t* d_patch_node_off = nullptr;   // [P+1] its local nodes are [off[p], off[p+1]) of the node arrays
   int32_t* d_elem_id = nullptr;          // [E] original element id of each patch-ordered element
   int32_t* d_conn = nullptr;             // [E*nloc] global nodes of the patch-ordered elements
-  int32_t* d_node_target = nullptr;      // [sum nodes] >= 0: global node written directly; < 0: -(halo slot)-1
+  int32_t* d_node_target = nullptr;      // [sum nodes] >= 0: global node written directly (bit 30 set for a boundary
+                                         // node); < 0: -(halo slot)-1
   int32_t* d_inc_off = nullptr;          // [sum nodes + 1] start of each local node's incidences (global index)
   uint16_t* d_inc = nullptr;             // [E*nloc] incidence = local slot * max_elems + local element, fixed order
   int32_t* d_shared_node = nullptr;      // [n_shared] global node of each shared node
@@ -110,6 +111,8 @@ struct Patches {
   // with h_e = |det J|^(1/3); per node 1 / (number of (element, slot) incidences)
   float* d_geomf = nullptr;              // [E*16]
   float* d_inv_mult = nullptr;           // [n_nodes]
+  int32_t* d_node_gid = nullptr;         // [sum nodes] global node of each local node
+  uint16_t* d_lconn = nullptr;           // [E*nloc] local node index of each (patch-ordered element, slot)
 };
 int patch_elems(int nloc);
 

@@ -222,13 +222,14 @@ __global__ void k_mlp_pack(const float* __restrict__ w, int nin, int nout, __nv_
 
 // ------------------------------------------------------------------------------------------------ preconditioner
 struct LearnSmem {
-  size_t ye, conn, inc, ioff, tgt, geo, w, xt, sc, total;
+  size_t ye, rs, conn, inc, ioff, tgt, geo, w, xt, sc, total;
 };
 __host__ __device__ inline LearnSmem learn_smem(int nloc, int pe, int max_nodes, bool tc, int64_t count, int nwarps) {
   LearnSmem L;
   L.ye = 0;
-  L.conn = L.ye + align16((size_t)nloc * pe * kLW * 4);
-  L.inc = L.conn + align16((size_t)pe * nloc * 4 + 16);
+  L.rs = L.ye + align16((size_t)nloc * pe * kLW * 4);                 // residual rows of the local nodes
+  L.conn = L.rs + align16((size_t)max_nodes * kLW * 4);              // local node of each element slot (uint16)
+  L.inc = L.conn + align16((size_t)pe * nloc * 2 + 16);
   L.ioff = L.inc + align16((size_t)pe * nloc * 2 + 16);
   L.tgt = L.ioff + align16((size_t)(max_nodes + 1) * 4 + 16);
   L.geo = L.tgt + align16((size_t)max_nodes * 4 + 16);
@@ -247,8 +248,9 @@ __host__ __device__ inline LearnSmem learn_smem(int nloc, int pe, int max_nodes,
 // slot (shared nodes, finished by k_learned_halo).  Columns [col0, col0 + Nw), Nw = min(kLW, N - col0).
 template <int NLOC, bool TC>
 __global__ void __launch_bounds__(256) k_learned_patch(
-    const int32_t* __restrict__ elem_off, const int32_t* __restrict__ node_off, const int32_t* __restrict__ conn,
-    const int32_t* __restrict__ target, const int32_t* __restrict__ inc_off, const uint16_t* __restrict__ inc,
+    const int32_t* __restrict__ elem_off, const int32_t* __restrict__ node_off, const uint16_t* __restrict__ lconn,
+    const int32_t* __restrict__ node_gid, const int32_t* __restrict__ target, const int32_t* __restrict__ inc_off,
+    const uint16_t* __restrict__ inc,
     const float* __restrict__ geomf, const void* __restrict__ wsrc, const float* __restrict__ bias, int64_t count,
     const float* __restrict__ dinv, const float* __restrict__ inv_mult, const uint8_t* __restrict__ bnd,
     const float* __restrict__ r, float* __restrict__ z, float* __restrict__ halo, int N, int col0, int ld, int pe,
@@ -262,7 +264,14 @@ __global__ void __launch_bounds__(256) k_learned_patch(
   const int n0 = node_off[p], nl = node_off[p + 1] - n0;
   const int ibase = e0 * NLOC;
   const int Nw = min(kLW, N - col0);
-  const int32_t* cs = stage_async(smraw + lay.conn, conn + ibase, ne * NLOC * 4);
+  const uint16_t* cs = stage_async(smraw + lay.conn, lconn + ibase, ne * NLOC * 2);
+  // the residual rows of the patch's local nodes, columns [col0, col0 + 8) (16-byte copies; ld % 4 == 0)
+  float* rs = reinterpret_cast<float*>(smraw + lay.rs);
+  const int nvec = min(kLW, ld - col0) / 4;
+  for (int l = threadIdx.x; l < nl; l += blockDim.x) {
+    const float* src = r + (int64_t)node_gid[n0 + l] * ld + col0;
+    for (int v = 0; v < nvec; ++v) cp_async16(rs + l * kLW + 4 * v, src + 4 * v);
+  }
   const uint16_t* is = stage_async(smraw + lay.inc, inc + ibase, ne * NLOC * 2);
   const int32_t* os = stage_async(smraw + lay.ioff, inc_off + n0, (nl + 1) * 4);
   const int32_t* ts = stage_async(smraw + lay.tgt, target + n0, nl * 4);
@@ -294,7 +303,7 @@ __global__ void __launch_bounds__(256) k_learned_patch(
         float rv[NLOC], ss = 0.f;
 #pragma unroll
         for (int a = 0; a < NLOC; ++a) {
-          rv[a] = valid ? r[(int64_t)cs[el * NLOC + a] * ld + col0 + jj] : 0.f;
+          rv[a] = valid ? rs[cs[el * NLOC + a] * kLW + jj] : 0.f;
           ss = fmaf(rv[a], rv[a], ss);
         }
         const float s = sqrtf(ss);
@@ -337,7 +346,7 @@ __global__ void __launch_bounds__(256) k_learned_patch(
       float x[NLOC + 12], y[NLOC], ss = 0.f;
 #pragma unroll
       for (int a = 0; a < NLOC; ++a) {
-        x[a] = r[(int64_t)cs[el * NLOC + a] * ld + col0 + jj];
+        x[a] = rs[cs[el * NLOC + a] * kLW + jj];
         ss = fmaf(x[a], x[a], ss);
       }
       const float s = sqrtf(ss);
@@ -360,8 +369,9 @@ __global__ void __launch_bounds__(256) k_learned_patch(
     for (int k = b; k < e; ++k) acc += Ye[(size_t)is[k] * kLW + jj];
     const int tg = ts[l];
     if (tg >= 0) {
-      const int64_t t = (int64_t)tg * ld + col0 + jj;
-      z[t] = bnd[tg] ? 0.f : fmaf(acc, inv_mult[tg], dinv[tg] * r[t]);
+      const int nd = tg & (kOwnedBoundary - 1);
+      const int64_t t = (int64_t)nd * ld + col0 + jj;
+      z[t] = (tg & kOwnedBoundary) ? 0.f : fmaf(acc, inv_mult[nd], dinv[nd] * r[t]);
     } else {
       halo[(int64_t)(-tg - 1) * ld + col0 + jj] = acc;
     }
@@ -390,6 +400,7 @@ int learned_apply(mk_ctx* ctx, const mk_mesh* m, const mk_mlp* mlp, const float*
   const Level& L = m->fine;
   MK_ARG(mlp->nloc == L.nloc, "learned preconditioner: network built for another element order");
   MK_ARG(precision == MK_MLP_FP32 || precision == MK_MLP_BF16, "learned preconditioner: bad precision");
+  MK_ARG(ld % 4 == 0, "learned preconditioner: ld must be a multiple of 4");
   int err = MK_OK;
   float* halo = (float*)scratch(ctx, S_LHALO, (size_t)std::max<int64_t>(P.n_halo_slots, 1) * ld * sizeof(float), &err);
   if (!halo) return err;
@@ -404,8 +415,9 @@ int learned_apply(mk_ctx* ctx, const mk_mesh* m, const mk_mlp* mlp, const float*
   do {                                                                                                            \
     auto kern = k_learned_patch<NL, TCV>;                                                                         \
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);                     \
-    MK_COUNT(), kern<<<P.n_patches, th, lay.total, s>>>(P.d_patch_elem_off, P.d_patch_node_off, P.d_conn,         \
-                                                        P.d_node_target, P.d_inc_off, P.d_inc, P.d_geomf, wsrc,    \
+    MK_COUNT(), kern<<<P.n_patches, th, lay.total, s>>>(P.d_patch_elem_off, P.d_patch_node_off, P.d_lconn,        \
+                                                        P.d_node_gid, P.d_node_target, P.d_inc_off, P.d_inc,      \
+                                                        P.d_geomf, wsrc,                                          \
                                                         mlp->d_bias, mlp->count, dinv, P.d_inv_mult, L.d_boundary, \
                                                         r, z, halo, N, col0, ld, P.max_elems, P.max_nodes);       \
   } while (0)

@@ -12,8 +12,8 @@
 
 namespace mk {
 
-// y = A x for one patch per CTA (see patch_apply).
-template <int NLOC, typename T, int VEC>
+// y = A x for one patch per CTA (see patch_apply); NCG > 0: the number of column groups fixed at compile time.
+template <int NLOC, typename T, int VEC, int NCG>
 __global__ void __launch_bounds__(256) k_apply_patch(const int32_t* __restrict__ elem_off,
                                                      const int32_t* __restrict__ node_off,
                                                      const int32_t* __restrict__ conn, const T* __restrict__ Ae,
@@ -24,8 +24,8 @@ __global__ void __launch_bounds__(256) k_apply_patch(const int32_t* __restrict__
                                                      const T* __restrict__ x, T* __restrict__ y, T* __restrict__ halo,
                                                      int ncolg, int col0, int ld, int pe, int max_nodes) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  patch_apply<NLOC, T, VEC>(blockIdx.x, elem_off, node_off, conn, Ae, target, inc_off, inc, bnd, mask, x, y, halo,
-                            ncolg, col0, ld, pe, max_nodes, smraw);
+  patch_apply<NLOC, T, VEC, NCG>(blockIdx.x, elem_off, node_off, conn, Ae, target, inc_off, inc, bnd, mask, x, y,
+                                 halo, ncolg, col0, ld, pe, max_nodes, smraw);
 }
 
 template <typename T, int VEC>
@@ -65,19 +65,29 @@ int apply_patch(mk_ctx* ctx, const mk_mesh* m, const T* Ae, const T* x, T* y, in
     if (smem > 227 * 1024) return fail(MK_ERR_UNSUPPORTED, "patch operator: patch too large for shared memory");
     const int th = std::min(256, (P.max_elems * ncolg + 31) / 32 * 32);  // one phase-1 item per thread
     prof_mark(ctx, sizeof(T) == 4 ? PROF_APPLY32 : PROF_APPLY64, true, s);
-#define MK_PATCH_LAUNCH(NL, V)                                                                                       \
+#define MK_PATCH_LAUNCH(NL, V, G)                                                                                    \
   do {                                                                                                              \
-    auto kern = k_apply_patch<NL, T, V>;                                                                            \
+    auto kern = k_apply_patch<NL, T, V, G>;                                                                         \
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
     MK_COUNT(), kern<<<P.n_patches, th, smem, s>>>(P.d_patch_elem_off, P.d_patch_node_off, P.d_conn, Ae,            \
                                                     P.d_node_target, P.d_inc_off, P.d_inc, L.d_boundary, mask, x, y, \
                                                     halo, ncolg, col0, ld, P.max_elems, P.max_nodes);               \
   } while (0)
-    if (nloc == 4) {
-      if (vec == VEC) MK_PATCH_LAUNCH(4, VEC); else MK_PATCH_LAUNCH(4, 1);
-    } else {
-      if (vec == VEC) MK_PATCH_LAUNCH(10, VEC); else MK_PATCH_LAUNCH(10, 1);
-    }
+#define MK_PATCH_DISPATCH(NL)                                      \
+  do {                                                             \
+    if (vec == VEC) {                                              \
+      if (ncolg == 1) MK_PATCH_LAUNCH(NL, VEC, 1);                 \
+      else if (ncolg == 2) MK_PATCH_LAUNCH(NL, VEC, 2);            \
+      else if (ncolg == 4) MK_PATCH_LAUNCH(NL, VEC, 4);            \
+      else MK_PATCH_LAUNCH(NL, VEC, 0);                            \
+    } else {                                                       \
+      if (ncolg == 1) MK_PATCH_LAUNCH(NL, 1, 1);                   \
+      else MK_PATCH_LAUNCH(NL, 1, 0);                              \
+    }                                                              \
+  } while (0)
+    if (nloc == 4) MK_PATCH_DISPATCH(4);
+    else MK_PATCH_DISPATCH(10);
+#undef MK_PATCH_DISPATCH
 #undef MK_PATCH_LAUNCH
     prof_mark(ctx, sizeof(T) == 4 ? PROF_APPLY32 : PROF_APPLY64, false, s);
     const int64_t work = P.n_shared_nodes * ncolg;

@@ -102,7 +102,11 @@ __host__ __device__ inline PatchSmem patch_smem(int nloc, int pe, int max_nodes,
 // Each element matrix is read from shared memory once (packed order), with all output rows held in registers.
 // Phase 2: each local node sums its incidences in fixed order (shared memory only) and writes the global row
 // (owned node) or its halo slot (shared node).  Columns [col0, col0 + W) with W = ncolg * VEC.
-template <int NLOC, typename T, int VEC>
+// Node targets of the patches: >= 0 a node written directly, with kOwnedBoundary set when it is a boundary node (its
+// row is zeroed when the operator masks the boundary); < 0 a halo slot -(slot)-1.
+constexpr int32_t kOwnedBoundary = 1 << 30;
+
+template <int NLOC, typename T, int VEC, int NCG = 0>
 __device__ __forceinline__ void patch_apply(int p, const int32_t* __restrict__ elem_off,
                                                      const int32_t* __restrict__ node_off,
                                                      const int32_t* __restrict__ conn, const T* __restrict__ Ae,
@@ -114,7 +118,8 @@ __device__ __forceinline__ void patch_apply(int p, const int32_t* __restrict__ e
                                                      int ncolg, int col0, int ld, int pe, int max_nodes,
                                                      unsigned char* smraw) {
   constexpr int NPS = padded_np(NLOC, (int)sizeof(T));
-  const int W = ncolg * VEC;
+  const int ncg = NCG > 0 ? NCG : ncolg;  // column groups: a compile-time constant in the hot instances
+  const int W = ncg * VEC;
   const PatchSmem lay = patch_smem(NLOC, pe, max_nodes, W, (int)sizeof(T));
   T* Ye = reinterpret_cast<T*>(smraw + lay.ye);  // [NLOC][pe][W]
   const int e0 = elem_off[p], ne = elem_off[p + 1] - e0;
@@ -127,11 +132,12 @@ __device__ __forceinline__ void patch_apply(int p, const int32_t* __restrict__ e
   const int32_t* ts = stage_async(smraw + lay.tgt, target + n0, nl * 4);
   cp_async_wait_all();
   __syncthreads();
-  for (int it = threadIdx.x; it < ne * ncolg; it += blockDim.x) {
-    const int el = it / ncolg, g = it - el * ncolg;
+  for (int it = threadIdx.x; it < ne * ncg; it += blockDim.x) {
+    const int el = it / ncg, g = it - el * ncg;
+    const T* xg = x + col0 + g * VEC;
     Vec<T, VEC> xv[NLOC];
 #pragma unroll
-    for (int a = 0; a < NLOC; ++a) xv[a] = ldv<T, VEC>(x + (int64_t)cs[el * NLOC + a] * ld + col0 + g * VEC);
+    for (int a = 0; a < NLOC; ++a) xv[a] = ldv<T, VEC>(xg + cs[el * NLOC + a] * ld);
     // one pass over the packed upper triangle: each entry is read once and feeds rows a and b; nothing is
     // stored until every row is complete
     const T* A = As + el * NPS;
@@ -155,8 +161,8 @@ __device__ __forceinline__ void patch_apply(int p, const int32_t* __restrict__ e
     for (int a = 0; a < NLOC; ++a) stv<T, VEC>(Ye + ((size_t)a * pe + el) * W + g * VEC, acc[a]);
   }
   __syncthreads();
-  for (int it = threadIdx.x; it < nl * ncolg; it += blockDim.x) {
-    const int l = it / ncolg, g = it - l * ncolg;
+  for (int it = threadIdx.x; it < nl * ncg; it += blockDim.x) {
+    const int l = it / ncg, g = it - l * ncg;
     const int b = os[l] - ibase, e = os[l + 1] - ibase;
     Vec<T, VEC> acc;
 #pragma unroll
@@ -177,10 +183,10 @@ __device__ __forceinline__ void patch_apply(int p, const int32_t* __restrict__ e
     }
     const int t = ts[l];
     if (t >= 0) {
-      if (mask && bnd[t])
+      if (mask && (t & kOwnedBoundary))
 #pragma unroll
         for (int c = 0; c < VEC; ++c) acc.v[c] = 0;
-      stv<T, VEC>(y + (int64_t)t * ld + col0 + g * VEC, acc);
+      stv<T, VEC>(y + (int64_t)(t & (kOwnedBoundary - 1)) * ld + col0 + g * VEC, acc);
     } else {
       stv<T, VEC>(halo + (int64_t)(-t - 1) * ld + col0 + g * VEC, acc);
     }

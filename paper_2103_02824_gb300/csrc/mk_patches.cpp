@@ -47,11 +47,15 @@ static int up(T** dst, const std::vector<T>& src) {
   return MK_OK;
 }
 
+// matches kOwnedBoundary of the patch kernels: an owned boundary node's target carries this bit
+constexpr int32_t kOwnedBoundaryTarget = 1 << 30;
+
 int build_patches(mk_mesh* m, int pe) {
   const Level& L = m->fine;
   Patches& P = m->patches;
   const int nloc = L.nloc;
   const int64_t E = L.n_elems, nn = L.n_nodes;
+  if (nn >= kOwnedBoundaryTarget) return fail(MK_ERR_UNSUPPORTED, "patches: more than 2^30 fine nodes");
   const int PE = pe > 0 ? pe : patch_elems(nloc);
   // Morton order of element centroids
   double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
@@ -124,13 +128,15 @@ int build_patches(mk_mesh* m, int pe) {
   std::vector<uint16_t> inc;
   inc_off.reserve(node_global.size() + np);
   std::vector<int32_t> conn((size_t)E * nloc);
+  std::vector<uint16_t> lconn((size_t)E * nloc);
   std::vector<int32_t> elem_id(E);
   for (int p = 0; p < np; ++p) {
     const int32_t nb = node_off[p], ne = node_off[p + 1];
     const int nl = ne - nb;
     for (int l = 0; l < nl; ++l) {
       const int32_t g = node_global[nb + l];
-      target[nb + l] = (cnt[g] >= 2) ? -(int32_t)(hbase[g] + seen[g]++) - 1 : g;
+      target[nb + l] = (cnt[g] >= 2) ? -(int32_t)(hbase[g] + seen[g]++) - 1
+                                     : (L.boundary[g] ? (g | kOwnedBoundaryTarget) : g);
     }
     // local index of each global node of the patch (node_global[nb, ne) is in count order, not sorted)
     std::vector<std::pair<int32_t, int32_t>> lookup(nl);  // (global id, local index), sorted by global id
@@ -146,6 +152,7 @@ int build_patches(mk_mesh* m, int pe) {
         conn[(size_t)i * nloc + a] = g;
         const int l = std::lower_bound(lookup.begin(), lookup.end(), std::make_pair(g, (int32_t)-1))->second;
         lidx[(size_t)(i - elem_off[p]) * nloc + a] = l;
+        lconn[(size_t)i * nloc + a] = (uint16_t)l;
         c[l + 1]++;
       }
     }
@@ -187,6 +194,8 @@ int build_patches(mk_mesh* m, int pe) {
   int r = up(&P.d_patch_elem_off, elem_off);
   if (r == MK_OK) r = up(&P.d_geomf, geomf);
   if (r == MK_OK) r = up(&P.d_inv_mult, inv_mult);
+  if (r == MK_OK) r = up(&P.d_node_gid, node_global);
+  if (r == MK_OK) r = up(&P.d_lconn, lconn);
   if (r == MK_OK) r = up(&P.d_patch_node_off, node_off);
   if (r == MK_OK) r = up(&P.d_elem_id, elem_id);
   if (r == MK_OK) r = up(&P.d_conn, conn);
@@ -201,7 +210,7 @@ int build_patches(mk_mesh* m, int pe) {
 void free_patches(Patches& p) {
   cudaFree(p.d_patch_elem_off); cudaFree(p.d_patch_node_off); cudaFree(p.d_elem_id); cudaFree(p.d_conn);
   cudaFree(p.d_node_target); cudaFree(p.d_inc_off); cudaFree(p.d_inc); cudaFree(p.d_shared_node);
-  cudaFree(p.d_geomf); cudaFree(p.d_inv_mult);
+  cudaFree(p.d_geomf); cudaFree(p.d_inv_mult); cudaFree(p.d_node_gid); cudaFree(p.d_lconn);
   cudaFree(p.d_shared_off);
   p = Patches();
 }

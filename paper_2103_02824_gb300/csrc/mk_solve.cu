@@ -318,25 +318,37 @@ int mk_hartree_poisson(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, c
   return r;
 }
 
-int mk_assemble_rhs(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, const double* lambdaH,
-                    const double* occ, int N, const double* w, double sigma, mk_xc xc, double* rhs, double* vq,
-                    void* stream) {
-  MK_ARG(ctx && m && u && lambdaH && occ && rhs && vq, "mk_assemble_rhs: null argument");
-  MK_ARG(N >= 1 && N <= ld && N <= MK_MAX_RHS, "mk_assemble_rhs: bad N/ld");
-  MK_ARG(xc.kind >= MK_XC_NONE && xc.kind <= MK_XC_LDA_PZ, "mk_assemble_rhs: bad xc");
+int mk_frozen_potential(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, const double* occ, int N,
+                        const double* w, mk_xc xc, double* vq, void* stream) {
+  MK_ARG(ctx && m && u && occ && w && vq, "mk_frozen_potential: null argument");
+  MK_ARG(N >= 1 && N <= ld && N <= MK_MAX_RHS, "mk_frozen_potential: bad N/ld");
+  MK_ARG(xc.kind >= MK_XC_NONE && xc.kind <= MK_XC_LDA_PZ, "mk_frozen_potential: bad xc");
+  MK_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const Level& L = m->fine;
+  int err = MK_OK;
+  double* rho = (double*)scratch(ctx, S_RHO, (size_t)L.n_elems * kQ * sizeof(double), &err);
+  if (!rho) return err;
+  MK_TRY(density(ctx, L, u, ld, N, occ, rho, s));
+  MK_TRY(frozen_potential(ctx, L, w, rho, xc, vq, s));
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
+int mk_assemble_rhs_from_vq(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, const double* lambdaH, int N,
+                            const double* vq, double sigma, double* rhs, void* stream) {
+  MK_ARG(ctx && m && u && lambdaH && vq && rhs, "mk_assemble_rhs_from_vq: null argument");
+  MK_ARG(N >= 1 && N <= ld && N <= MK_MAX_RHS, "mk_assemble_rhs_from_vq: bad N/ld");
   MK_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
   const Level& L = m->fine;
   int err = MK_OK;
   const size_t eb = (size_t)L.n_elems * (L.nloc * (L.nloc + 1) / 2) * sizeof(double);
-  double* rho = (double*)scratch(ctx, S_RHO, (size_t)L.n_elems * kQ * sizeof(double), &err);
   double* Me = (double*)scratch(ctx, S_ELEM64B, eb, &err);
   double* Ve = (double*)scratch(ctx, S_ELEM64, eb, &err);
   double* Mu = (double*)scratch(ctx, S_VEC1, (size_t)L.n_nodes * ld * sizeof(double), &err);
   double* Vu = (double*)scratch(ctx, S_VEC2, (size_t)L.n_nodes * ld * sizeof(double), &err);
-  if (!rho || !Me || !Ve || !Mu || !Vu) return err;
-  MK_TRY(density(ctx, L, u, ld, N, occ, rho, s));
-  MK_TRY(frozen_potential(ctx, L, w, rho, xc, vq, s));
+  if (!Me || !Ve || !Mu || !Vu) return err;
   MK_TRY(element_matrices(ctx, L, nullptr, 0.0, 0.0, 0.0, vq, Ve, s));
   MK_TRY(element_matrices(ctx, L, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s));
   MK_TRY(apply64(ctx, m, Me, u, Mu, N, ld, true, s));
@@ -346,6 +358,14 @@ int mk_assemble_rhs(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, cons
   MK_COUNT(), k_combine_rhs<<<(int)((L.n_nodes * ld + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, Mu, Vu, coef, rhs, N, ld);
   MK_CUDA(cudaGetLastError());
   return MK_OK;
+}
+
+int mk_assemble_rhs(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, const double* lambdaH,
+                    const double* occ, int N, const double* w, double sigma, mk_xc xc, double* rhs, double* vq,
+                    void* stream) {
+  MK_ARG(ctx && m && u && lambdaH && occ && rhs && vq, "mk_assemble_rhs: null argument");
+  MK_TRY(mk_frozen_potential(ctx, m, u, ld, occ, N, w, xc, vq, stream));
+  return mk_assemble_rhs_from_vq(ctx, m, u, ld, lambdaH, N, vq, sigma, rhs, stream);
 }
 
 int mk_correction_solve(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, double sigma, const double* rhs,

@@ -115,6 +115,8 @@ _SIGS = {
                                   C.POINTER(mk_solve_opts), C.POINTER(mk_solve_report), _vp],
     "mk_mesh_set_patch_elems": [_vp, C.c_int],
     "mk_autotune_patches": [_vp, _vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)],
+    "mk_frozen_potential": [_vp, _vp, _vp, C.c_int, C.POINTER(C.c_double), C.c_int, _vp, mk_xc, _vp, _vp],
+    "mk_assemble_rhs_from_vq": [_vp, _vp, _vp, C.c_int, C.POINTER(C.c_double), C.c_int, _vp, C.c_double, _vp, _vp],
     "mk_mlp_param_count": [C.c_int],
     "mk_mlp_create": [_vp, C.c_int, C.POINTER(C.c_float), C.POINTER(_vp)],
     "mk_mlp_destroy": [_vp],
@@ -382,6 +384,20 @@ def mk_assemble_rhs(ctx, mesh, u, lamH, occ, N, w, sigma, xc, rhs, vq, alpha=0.7
     occ_h, occ_p = _host_f64(occ)
     _check(lib().mk_assemble_rhs(ctx.h, mesh.h, _ptr(u), ld, lam_p, occ_p, N, _ptr(w), float(sigma),
                                  mk_xc(MK_XC[xc], alpha), _ptr(rhs), _ptr(vq), _stream(stream)))
+
+
+def mk_frozen_potential(ctx, mesh, u, occ, N, w, xc, vq, alpha=0.77298, stream=None):
+    ld = u.shape[1] if u.dim() == 2 else 1
+    occ_h, occ_p = _host_f64(occ)
+    _check(lib().mk_frozen_potential(ctx.h, mesh.h, _ptr(u), ld, occ_p, N, _ptr(w), mk_xc(MK_XC[xc], alpha), _ptr(vq),
+                                     _stream(stream)))
+
+
+def mk_assemble_rhs_from_vq(ctx, mesh, u, lamH, N, vq, sigma, rhs, stream=None):
+    ld = u.shape[1] if u.dim() == 2 else 1
+    lam_h, lam_p = _host_f64(lamH)
+    _check(lib().mk_assemble_rhs_from_vq(ctx.h, mesh.h, _ptr(u), ld, lam_p, N, _ptr(vq), float(sigma), _ptr(rhs),
+                                         _stream(stream)))
 
 
 def mk_correction_solve(ctx, mesh, mol: Molecule, sigma, rhs, x, N, opt=None, stream=None, allow=()):

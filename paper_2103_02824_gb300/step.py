@@ -76,15 +76,17 @@ class CorrectionStep:
         else:
             reps["poisson"] = mk.mk_hartree_poisson(ctx, mesh, self.u, occ, N, self.w, bc=hartree_bc,
                                                     opt=poisson_opts, stream=stream)
-        mk.mk_assemble_rhs(ctx, mesh, self.u, lamH, occ, N, self.w, sigma, xc, self.rhs, self.vq, stream=stream)
+        # A3 in two halves: the frozen potential vq first, so that the coarse pencil and its decomposition (which
+        # need vq, not rhs or psi^) start on the side stream while the right-hand sides and the fine solve run
+        mk.mk_frozen_potential(ctx, mesh, self.u, occ, N, self.w, xc, self.vq, stream=stream)
         main = torch.cuda.current_stream() if stream is None else torch.cuda.ExternalStream(stream)
         if self.overlap:
-            # the coarse pencil and its decomposition need only vq, not psi^: run them beside the fine solve
             self._ev_rhs.record(main)
             self._side.wait_event(self._ev_rhs)
             mk.mk_coarse_pencil(ctx, mesh, self.mol, self.vq, self.AH, None, stream=self._side.cuda_stream)
             self._decompose(self._side.cuda_stream)
             self._ev_dec.record(self._side)
+        mk.mk_assemble_rhs_from_vq(ctx, mesh, self.u, lamH, N, self.vq, sigma, self.rhs, stream=stream)
         self.psihat.copy_(self.u)
         reps["solve"] = mk.mk_correction_solve(ctx, mesh, self.mol, sigma, self.rhs, self.psihat, N,
                                                opt=solve_opts, stream=stream)

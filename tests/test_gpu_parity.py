@@ -406,3 +406,25 @@ def test_twolevel_solves(ctx, torch, name):
                                opt=mk.opts(precision="mixed", rtol=1e-12, check_every=5, coarse=True))
     assert rp["max_rel_residual"] <= 1e-12
     assert rel(w.cpu().numpy(), c["out"]["w"]) < 1e-9
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_assemble_rhs_in_two_halves(ctx, torch, name):
+    """mk_frozen_potential + mk_assemble_rhs_from_vq reproduce mk_assemble_rhs exactly."""
+    from paper_2103_02824_gb300 import mk
+    c = case(name)
+    m = gpu_mesh(ctx, name)
+    N, ld = c["N"], 8
+    u = dev(torch, padded(c["out"]["u"], ld))
+    w = dev(torch, c["out"]["w"])
+    info = m.info
+    rhs1 = torch.zeros((info["n_nodes"], ld), dtype=torch.float64, device="cuda")
+    rhs2 = torch.zeros_like(rhs1)
+    vq1 = torch.zeros((info["n_elems"], info["n_quad"]), dtype=torch.float64, device="cuda")
+    vq2 = torch.zeros_like(vq1)
+    mk.mk_assemble_rhs(ctx, m, u, c["lamH"], c["occ"], N, w, c["sigma"], c["xc"], rhs1, vq1)
+    mk.mk_frozen_potential(ctx, m, u, c["occ"], N, w, c["xc"], vq2)
+    mk.mk_assemble_rhs_from_vq(ctx, m, u, c["lamH"], N, vq2, c["sigma"], rhs2)
+    torch.cuda.synchronize()
+    assert torch.equal(vq1, vq2) and torch.equal(rhs1, rhs2)
+    assert rel(rhs2.cpu().numpy()[:, :N], c["out"]["rhs"]) < 1e-10
