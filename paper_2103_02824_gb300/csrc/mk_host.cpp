@@ -18,6 +18,14 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
+int check_fault(mk_ctx* c, cudaStream_t s) {
+  int f = 0;
+  MK_CUDA(cudaMemcpyAsync(&f, c->d_fault, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MK_CUDA(cudaStreamSynchronize(s));
+  if (f) return fail(MK_ERR_TIMEOUT, "a bounded device-side wait gave up (fault word " + std::to_string(f) + ")");
+  return MK_OK;
+}
+
 // ------------------------------------------------------------------------------------------------ quadrature
 // Jacobi polynomial P_n^{(a,b)}(x) and its derivative by the three-term recurrence.
 static void jacobi_eval(int n, double a, double b, double x, double* p, double* dp) {
@@ -487,6 +495,8 @@ int mk_ctx_create(mk_ctx** out, int device) {
   MK_CUDA(cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, device));
   const char* ng = std::getenv("MK_NO_GRAPHS");
   c->no_graphs = ng && ng[0] == '1';
+  MK_CUDA(cudaMalloc(&c->d_fault, sizeof(int)));
+  MK_CUDA(cudaMemset(c->d_fault, 0, sizeof(int)));
   MK_CUDA(cudaStreamCreateWithFlags(&c->solve_stream, cudaStreamNonBlocking));
   for (cudaEvent_t& e : c->solve_ev) MK_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   for (int order = 1; order <= 2; ++order) {
@@ -511,9 +521,20 @@ int mk_ctx_destroy(mk_ctx* c) {
   for (cudaEvent_t e : c->solve_ev)
     if (e) cudaEventDestroy(e);
   if (c->solve_stream) cudaStreamDestroy(c->solve_stream);
+  cudaFree(c->d_fault);
   delete c;
   return MK_OK;
 }
+
+int mk_ctx_fault(mk_ctx* c, int* fault) {
+  MK_ARG(c && fault, "mk_ctx_fault: null argument");
+  MK_CUDA(cudaSetDevice(c->device));
+  MK_CUDA(cudaDeviceSynchronize());
+  MK_CUDA(cudaMemcpy(fault, c->d_fault, sizeof(int), cudaMemcpyDeviceToHost));
+  MK_CUDA(cudaMemset(c->d_fault, 0, sizeof(int)));
+  return MK_OK;
+}
+
 
 int mk_mesh_upload(mk_ctx* ctx, const mk_mesh_desc* fine, const mk_mesh_desc* coarse, const int32_t* fine_parent,
                    mk_mesh** out) {

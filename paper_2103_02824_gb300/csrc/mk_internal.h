@@ -19,6 +19,8 @@ extern std::atomic<long long> g_launch_count;
 // ------------------------------------------------------------------------------------------------ errors
 void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);
+// MK_ERR_TIMEOUT if a kernel on stream s set the context's device fault word (synchronises s).
+int check_fault(mk_ctx* c, cudaStream_t s);
 
 #define MK_CUDA(call)                                                                          \
   do {                                                                                         \
@@ -113,7 +115,17 @@ struct Patches {
   float* d_inv_mult = nullptr;           // [n_nodes]
   int32_t* d_node_gid = nullptr;         // [sum nodes] global node of each local node
   uint16_t* d_lconn = nullptr;           // [E*nloc] local node index of each (patch-ordered element, slot)
+  // one record per patch for the pipelined operator kernel (bulk-copied into shared memory in one piece), at byte
+  // offset rec_off[p] (a multiple of 16): int32 header {e0, ne, n0, nl, off_pos, off_ioff, off_tgt, off_gid}, then
+  // the local connectivity (uint16 [ne*nloc], at byte 32), the place of each (element, slot) incidence in the
+  // patch's node-sorted incidence list (uint16 [ne*nloc]), the start of each local node's run in that list
+  // (uint16 [nl+1]), the node targets (int32 [nl]) and the global ids of the local nodes (int32 [nl]); every
+  // section starts on a 16-byte boundary
+  unsigned char* d_rec = nullptr;
+  int64_t* d_rec_off = nullptr;          // [P+1]
+  int max_rec_bytes = 0;
 };
+constexpr int kRecHeader = 32;
 int patch_elems(int nloc);
 
 }  // namespace mk
@@ -121,6 +133,7 @@ int patch_elems(int nloc);
 struct mk_ctx {
   int device = 0;
   int n_sms = 0;
+  int* d_fault = nullptr;  // device word: MK_FAULT_* bits set by kernels whose bounded waits gave up
   mk::RefTables* d_ref[3] = {nullptr, nullptr, nullptr};  // by order (1, 2)
   mk::RefTables h_ref[3];
   // scratch: named slots grown on demand

@@ -5,6 +5,7 @@
 // decides convergence, so the answer is the FP64 answer to rtol whatever the inner precision.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "mk_device.cuh"
@@ -28,6 +29,21 @@ __global__ void __launch_bounds__(256) k_apply_patch(const int32_t* __restrict__
                                  halo, ncolg, col0, ld, pe, max_nodes, smraw);
 }
 
+// y = A x over a persistent grid of CTAs, each looping over its patches with the next patch's bulk copies in
+// flight (see patch_apply_pipelined).
+template <int NLOC, typename T, int VEC, int NCG>
+__global__ void __launch_bounds__(512, 1) k_apply_stream(const unsigned char* __restrict__ rec,
+                                                          const int64_t* __restrict__ rec_off,
+                                                          const T* __restrict__ Ae, int mask,
+                                                          const T* __restrict__ x, T* __restrict__ y,
+                                                          T* __restrict__ halo, int col0, int ld, int pe,
+                                                          int max_nodes, int max_rec, int n_patches, int64_t n_nodes,
+                                                          int64_t n_elems, int* __restrict__ fault) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  patch_apply_pipelined<NLOC, T, VEC, NCG>(rec, rec_off, Ae, mask, x, y, halo, col0, ld, pe, max_nodes, max_rec,
+                                           n_patches, n_nodes, n_elems, fault, smraw);
+}
+
 template <typename T, int VEC>
 __global__ void k_halo(int64_t nshared, const int32_t* __restrict__ node, const int32_t* __restrict__ off,
                        const uint8_t* __restrict__ bnd, int mask, const T* __restrict__ halo, T* __restrict__ y,
@@ -46,6 +62,87 @@ __global__ void k_pack_elements(int64_t E, int np, int nps, const int32_t* __res
   A[t] = k < np ? (T)A64[(int64_t)elem_id[i] * np + k] : (T)0;
 }
 
+// The shared nodes' rows of y from their halo slots, columns [col0, col0 + ncolg * vec).
+template <typename T>
+static int halo_pass(mk_ctx* ctx, const mk_mesh* m, const T* halo, T* y, bool mask, int ncolg, int vec, int col0,
+                     int ld, cudaStream_t s) {
+  const Patches& P = m->patches;
+  const Level& L = m->fine;
+  constexpr int VEC = sizeof(T) == 4 ? 4 : 2;
+  const int64_t work = P.n_shared_nodes * ncolg;
+  if (work == 0) return MK_OK;
+  prof_mark(ctx, PROF_HALO, true, s);
+  if (vec == VEC)
+    MK_COUNT(), k_halo<T, VEC><<<(int)((work + 255) / 256), 256, 0, s>>>(P.n_shared_nodes, P.d_shared_node,
+                                                                       P.d_shared_off, L.d_boundary, mask, halo, y,
+                                                                       ncolg, col0, ld);
+  else
+    MK_COUNT(), k_halo<T, 1><<<(int)((work + 255) / 256), 256, 0, s>>>(P.n_shared_nodes, P.d_shared_node,
+                                                                     P.d_shared_off, L.d_boundary, mask, halo, y,
+                                                                     ncolg, col0, ld);
+  prof_mark(ctx, PROF_HALO, false, s);
+  return MK_OK;
+}
+
+template <int NL, typename T, int PV, int G>
+static int launch_stream_kernel(mk_ctx* ctx, const mk_mesh* m, const T* Ae, const T* x, T* y, T* halo, int col0,
+                                int ld, bool mask, size_t ssm, int th, cudaStream_t s) {
+  const Patches& P = m->patches;
+  const Level& L = m->fine;
+  auto kern = k_apply_stream<NL, T, PV, G>;
+  MK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
+  int bps = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, th, ssm) != cudaSuccess || bps < 1) bps = 1;
+  const int grid = (int)std::min<int64_t>(P.n_patches, (int64_t)ctx->n_sms * bps);
+  MK_COUNT(), kern<<<grid, th, ssm, s>>>(P.d_rec, P.d_rec_off, Ae, mask, x, y, halo, col0, ld, P.max_elems,
+                                         P.max_nodes, P.max_rec_bytes, P.n_patches, L.n_nodes, L.n_elems,
+                                         ctx->d_fault);
+  return MK_OK;
+}
+
+// The pipelined patch kernel for columns [col0, col0 + W), if its shared memory fits and an instance exists for
+// this column width (*launched = 1); product items take 4 FP32 columns (2 with MK_PATCH_VEC=2) or 2 FP64 ones.
+template <typename T>
+static int launch_stream(mk_ctx* ctx, const mk_mesh* m, const T* Ae, const T* x, T* y, T* halo, int col0, int W,
+                         int ld, bool mask, cudaStream_t s, int* launched) {
+  const Patches& P = m->patches;
+  const int nloc = m->fine.nloc;
+  *launched = 0;
+  const size_t ssm = stream_smem(nloc, P.max_elems, P.max_nodes, P.max_rec_bytes, W, (int)sizeof(T)).total;
+  if (ssm > 227 * 1024) return MK_OK;
+  const char* ve = std::getenv("MK_PATCH_VEC");
+  const int pv = sizeof(T) == 8 ? 2 : (ve && ve[0] == '2') ? 2 : 4;
+  if (W % pv) return MK_OK;
+  const int th = kStreamThreads;
+  const int kind = sizeof(T) == 4 ? PROF_APPLY32 : PROF_APPLY64;
+  int r = MK_OK;
+  prof_mark(ctx, kind, true, s);
+#define MK_SL(NL, PVV, G) (r = launch_stream_kernel<NL, T, PVV, G>(ctx, m, Ae, x, y, halo, col0, ld, mask, ssm, th, s), *launched = 1)
+#define MK_SD(NL)                                                        \
+  do {                                                                   \
+    if constexpr (sizeof(T) == 8) {                                      \
+      if (W == 2) MK_SL(NL, 2, 1);                                       \
+      else if (W == 4) MK_SL(NL, 2, 2);                                  \
+    } else if (pv == 4) {                                                \
+      if (W == 4) MK_SL(NL, 4, 1);                                       \
+      else if (W == 8) MK_SL(NL, 4, 2);                                  \
+      else if (W == 12) MK_SL(NL, 4, 3);                                 \
+      else if (W == 16) MK_SL(NL, 4, 4);                                 \
+    } else {                                                             \
+      if (W == 4) MK_SL(NL, 2, 2);                                       \
+      else if (W == 8) MK_SL(NL, 2, 4);                                  \
+      else if (W == 12) MK_SL(NL, 2, 6);                                 \
+      else if (W == 16) MK_SL(NL, 2, 8);                                 \
+    }                                                                    \
+  } while (0)
+  if (nloc == 4) MK_SD(4);
+  else MK_SD(10);
+#undef MK_SD
+#undef MK_SL
+  prof_mark(ctx, kind, false, s);
+  return r;
+}
+
 // y = A x with the patch operator (all ld columns), FP32 or FP64.
 template <typename T>
 int apply_patch(mk_ctx* ctx, const mk_mesh* m, const T* Ae, const T* x, T* y, int ld, bool mask, cudaStream_t s) {
@@ -56,11 +153,30 @@ int apply_patch(mk_ctx* ctx, const mk_mesh* m, const T* Ae, const T* x, T* y, in
   if (!halo) return err;
   constexpr int VEC = sizeof(T) == 4 ? 4 : 2;
   const int vec = (ld % VEC == 0) ? VEC : 1;
-  const int wmax = sizeof(T) == 4 ? 16 : 4;  // columns per pass (shared memory)
   const int nloc = L.nloc;
+  // the pipelined kernel stages x rows in 16-byte copies: x aligned, ld a multiple of 16 bytes
+  const char* pipe_env = std::getenv("MK_PATCH_PIPELINE");
+  const bool pipe_ok = !(pipe_env && pipe_env[0] == '0') && ld % (16 / (int)sizeof(T)) == 0 &&
+                       (reinterpret_cast<uintptr_t>(x) & 15) == 0 && (reinterpret_cast<uintptr_t>(y) & 15) == 0 &&
+                       (reinterpret_cast<uintptr_t>(halo) & 15) == 0 && (reinterpret_cast<uintptr_t>(Ae) & 15) == 0 &&
+                       P.d_rec != nullptr;
+  // columns per pass: the shared memory of one patch bounds them (16 FP32 / 4 FP64); the pipelined kernel, which
+  // holds two patches' products, takes 8 FP32 columns per pass when 16 do not fit
+  int wmax = sizeof(T) == 4 ? 16 : 4;
+  if (pipe_ok && sizeof(T) == 4 && ld > 8 &&
+      stream_smem(nloc, P.max_elems, P.max_nodes, P.max_rec_bytes, std::min(ld, 16), 4).total > 227 * 1024)
+    wmax = 8;
   for (int col0 = 0; col0 < ld; col0 += wmax) {
     const int W = std::min(wmax, ld - col0);
     const int ncolg = W / vec;
+    if (pipe_ok) {
+      int launched = 0;
+      MK_TRY(launch_stream<T>(ctx, m, Ae, x, y, halo, col0, W, ld, mask, s, &launched));
+      if (launched) {
+        MK_TRY(halo_pass<T>(ctx, m, halo, y, mask, W / (16 / (int)sizeof(T)), 16 / (int)sizeof(T), col0, ld, s));
+        continue;
+      }
+    }
     const size_t smem = patch_smem(nloc, P.max_elems, P.max_nodes, W, (int)sizeof(T)).total;
     if (smem > 227 * 1024) return fail(MK_ERR_UNSUPPORTED, "patch operator: patch too large for shared memory");
     const int th = std::min(256, (P.max_elems * ncolg + 31) / 32 * 32);  // one phase-1 item per thread
@@ -90,19 +206,7 @@ int apply_patch(mk_ctx* ctx, const mk_mesh* m, const T* Ae, const T* x, T* y, in
 #undef MK_PATCH_DISPATCH
 #undef MK_PATCH_LAUNCH
     prof_mark(ctx, sizeof(T) == 4 ? PROF_APPLY32 : PROF_APPLY64, false, s);
-    const int64_t work = P.n_shared_nodes * ncolg;
-    if (work > 0) {
-      prof_mark(ctx, PROF_HALO, true, s);
-      if (vec == VEC)
-        MK_COUNT(), k_halo<T, VEC><<<(int)((work + 255) / 256), 256, 0, s>>>(P.n_shared_nodes, P.d_shared_node,
-                                                                           P.d_shared_off, L.d_boundary, mask, halo,
-                                                                           y, ncolg, col0, ld);
-      else
-        MK_COUNT(), k_halo<T, 1><<<(int)((work + 255) / 256), 256, 0, s>>>(P.n_shared_nodes, P.d_shared_node,
-                                                                         P.d_shared_off, L.d_boundary, mask, halo, y,
-                                                                         ncolg, col0, ld);
-      prof_mark(ctx, PROF_HALO, false, s);
-    }
+    MK_TRY(halo_pass<T>(ctx, m, halo, y, mask, ncolg, vec, col0, ld, s));
   }
   MK_CUDA(cudaGetLastError());
   return MK_OK;
@@ -652,7 +756,6 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
   MK_ARG(ld <= 256, "mixed path: ld must be <= 256");
   const Level& L = m->fine;
   const int64_t n = L.n_nodes;
-  const int np = L.nloc * (L.nloc + 1) / 2;
   int err = MK_OK;
   float* A32 = (float*)scratch(ctx, S_ELEM32, (size_t)L.n_elems * padded_np(L.nloc, 4) * sizeof(float), &err);
   double* diag = (double*)scratch(ctx, S_DIAG64, n * sizeof(double), &err);
@@ -800,6 +903,7 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
   MK_CUDA(cudaGetLastError());
   MK_CUDA(cudaMemcpyAsync(hst, st, sizeof(MixState) * ld, cudaMemcpyDeviceToHost, s));
   MK_CUDA(cudaStreamSynchronize(s));
+  MK_TRY(check_fault(ctx, s));
   double mx = 0.0;
   for (int j = 0; j < N; ++j) mx = std::max(mx, std::sqrt(hst[j].rr64) / hst[j].bn);
   if (rep) {
@@ -1168,6 +1272,7 @@ extern "C" int mk_batch_correction_solve(mk_ctx* ctx, int K, const mk_mesh* cons
   }
   MK_CUDA(cudaEventRecord(ctx->solve_ev[1], s));
   MK_CUDA(cudaStreamWaitEvent(caller, ctx->solve_ev[1], 0));
+  MK_TRY(check_fault(ctx, s));
   if (worst == MK_ERR_BREAKDOWN) return fail(worst, "batched PCG breakdown: p^T A p <= 0 in some problem");
   if (worst == MK_ERR_NOT_CONVERGED) return fail(worst, "batched PCG: some problem did not reach rtol");
   return MK_OK;

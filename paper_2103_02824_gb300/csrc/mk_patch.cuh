@@ -23,6 +23,9 @@ __device__ __forceinline__ Vec<T, VEC> ldv(const T* __restrict__ p) {
   } else if constexpr (VEC == 2 && sizeof(T) == 8) {
     const double2 f = *reinterpret_cast<const double2*>(p);
     r.v[0] = f.x; r.v[1] = f.y;
+  } else if constexpr (VEC == 2 && sizeof(T) == 4) {
+    const float2 f = *reinterpret_cast<const float2*>(p);
+    r.v[0] = f.x; r.v[1] = f.y;
   } else {
 #pragma unroll
     for (int c = 0; c < VEC; ++c) r.v[c] = p[c];
@@ -36,6 +39,8 @@ __device__ __forceinline__ void stv(T* __restrict__ p, const Vec<T, VEC>& r) {
     *reinterpret_cast<float4*>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
   } else if constexpr (VEC == 2 && sizeof(T) == 8) {
     *reinterpret_cast<double2*>(p) = make_double2(r.v[0], r.v[1]);
+  } else if constexpr (VEC == 2 && sizeof(T) == 4) {
+    *reinterpret_cast<float2*>(p) = make_float2(r.v[0], r.v[1]);
   } else {
 #pragma unroll
     for (int c = 0; c < VEC; ++c) p[c] = r.v[c];
@@ -190,6 +195,299 @@ __device__ __forceinline__ void patch_apply(int p, const int32_t* __restrict__ e
     } else {
       stv<T, VEC>(halo + (int64_t)(-t - 1) * ld + col0 + g * VEC, acc);
     }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------ pipelined apply
+// ------------------------------------------------------------------------------------------------ bulk copies
+// mbarrier and bulk (TMA, non-tensor) copy primitives.  Every wait is bounded: kWaitLimit polls of
+// mbarrier.try_wait (each suspending the thread for at most about kSuspendNs), then the caller is told.
+constexpr int kWaitLimit = 1 << 20;
+constexpr unsigned kSuspendNs = 1000;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+// one arrival that also announces `bytes` more bytes of transactions for the current phase
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// waits for the phase of the given parity, suspending up to about kSuspendNs per call
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
+      : "memory");
+  return ok != 0;
+}
+// the barrier's current phase also waits for every cp.async this thread issued before (an arrival counted in
+// the barrier's initial count)
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  for (int i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// global -> shared bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned), completing on bar
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Shared-memory layout of the pipelined patch kernel: mbarriers, kRecBufs patch-record buffers, kAStages buffers
+// of element matrices, two of local-node x rows, and two product buffers Ye [incidence][W].
+constexpr int kAStages = 2;   // element matrices are fetched kAStages - 1 steps ahead
+constexpr int kRecAhead = 3;  // records are fetched kRecAhead steps ahead
+constexpr int kRecBufs = kRecAhead + 2;
+struct StreamSmem {
+  size_t bar, rec, rec_stride, as, as_stride, xs, xs_stride, ye, ye_stride, total;
+};
+__host__ __device__ inline StreamSmem stream_smem(int nloc, int pe, int max_nodes, int max_rec, int W, int tsize) {
+  StreamSmem L;
+  L.bar = 0;
+  L.rec = 256;
+  L.rec_stride = align16((size_t)max_rec);
+  L.as = L.rec + kRecBufs * L.rec_stride;
+  L.as_stride = align16((size_t)pe * padded_np(nloc, tsize) * tsize);
+  L.xs = L.as + kAStages * L.as_stride;
+  L.xs_stride = align16((size_t)max_nodes * W * tsize);
+  L.ye = L.xs + 2 * L.xs_stride;
+  L.ye_stride = align16((size_t)nloc * pe * W * tsize);
+  L.total = L.ye + 2 * L.ye_stride;
+  return L;
+}
+constexpr int kStreamThreads = 512;  // 16 warps: warps 0-7 compute element products, warps 8-15 sum and copy
+constexpr int kStreamP1 = 256;
+
+// y = A x (columns [col0, col0 + W)) over the patches blockIdx.x, blockIdx.x + gridDim.x, ... of one CTA,
+// pipelined across two warp groups.  In step t the product group (threads [0, kStreamP1)) computes the element
+// products of patch t, while the sum group (the other threads) sums the incidences of patch t - 1 and starts the
+// copies for later patches: the element matrices of patch t + 1 (one bulk copy; they depend on the patch index
+// only), the x rows of the local nodes of patch t + 1 (cp.async; their ids come with the patch's record, which
+// arrived kRecAhead - 1 steps of slack earlier) and the record of patch t + kRecAhead (one bulk copy).  One CTA
+// barrier ends the step.  So the two phases of the method overlap, and no copy waits on another within a step.
+// Products: one item per (element, group of VEC columns); product row a of element e goes to the place of
+// incidence (e, a) in the patch's node-sorted incidence list, so that a local node's incidences are consecutive
+// rows.  Sums: one item per (local node, V2 columns), the node's rows in list order, written to its row of y
+// (owned node) or to its halo slot (shared node).  Every sum has the terms and order of patch_apply, so both
+// kernels give bitwise identical results.  The lanes that read one element matrix are neighbours (NCG >= 2), so
+// its 16-byte loads are conflict-free at the packed row stride.
+// Requires blockDim.x == kStreamThreads; patches of pe consecutive elements (the last one shorter); Ae, x
+// 16-byte aligned; ld and col0 multiples of 16 / sizeof(T).  A record whose header is out of range, or a wait
+// that gives up, sets a bit of *fault and ends the CTA after a bounded wait for its copies.
+template <int NLOC, typename T, int VEC, int NCG>
+__device__ __forceinline__ void patch_apply_pipelined(const unsigned char* __restrict__ rec,
+                                                      const int64_t* __restrict__ rec_off, const T* __restrict__ Ae,
+                                                      int mask, const T* __restrict__ x, T* __restrict__ y,
+                                                      T* __restrict__ halo, int col0, int ld, int pe, int max_nodes,
+                                                      int max_rec, int n_patches, int64_t n_nodes, int64_t n_elems,
+                                                      int* __restrict__ fault, unsigned char* smraw) {
+  constexpr int NPS = padded_np(NLOC, (int)sizeof(T));
+  constexpr int V2 = 16 / (int)sizeof(T);  // columns per sum item (one 16-byte vector)
+  constexpr int W = NCG * VEC;
+  constexpr int XCH = W / V2;              // 16-byte chunks per x row
+  constexpr int NG2 = W / V2;
+  constexpr int NSUM = kStreamThreads - kStreamP1;
+  const StreamSmem lay = stream_smem(NLOC, pe, max_nodes, max_rec, W, (int)sizeof(T));
+  uint64_t* barR = reinterpret_cast<uint64_t*>(smraw + lay.bar);  // [kRecBufs] records
+  uint64_t* barM = barR + kRecBufs;                                // [kAStages] element matrices
+  uint64_t* barX = barM + kAStages;                                // [2] x rows
+  const int tid = threadIdx.x;
+  const bool prod = tid < kStreamP1;
+  const int gt = prod ? tid : tid - kStreamP1;  // thread index within its group
+  const bool elected = tid == kStreamP1;        // issues the bulk copies
+  const int np_mine = n_patches > (int)blockIdx.x ? (n_patches - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  if (np_mine == 0) return;
+  auto patch_of = [&](int i) { return (int)blockIdx.x + i * (int)gridDim.x; };
+  auto recbuf = [&](int i) { return smraw + lay.rec + (size_t)(i % kRecBufs) * lay.rec_stride; };
+  auto hdr = [&](int i) { return reinterpret_cast<const int32_t*>(recbuf(i)); };
+  // phases issued, and record phases seen complete, by this thread (for the drain after a failure)
+  int rec_issued = 0, rec_waited = 0, mat_issued = 0, x_issued = 0;
+  bool ok = true;
+  auto issue_rec = [&](int i) {  // elected thread: the record of patch i
+    if (elected) {
+      const int64_t o = rec_off[patch_of(i)];
+      const int64_t bytes = rec_off[patch_of(i) + 1] - o;
+      if (bytes <= 0 || bytes > max_rec || (bytes & 15) || (o & 15)) {
+        atomicOr(fault, MK_FAULT_PATCH_RECORD);
+        *reinterpret_cast<int32_t*>(recbuf(i) + 4) = 0;  // ne = 0: the header check rejects the record
+        mbar_arrive_expect(&barR[i % kRecBufs], 0);      // completes the phase with nothing copied
+      } else {
+        fence_proxy_async();
+        mbar_arrive_expect(&barR[i % kRecBufs], (unsigned)bytes);
+        bulk_g2s(recbuf(i), rec + o, (unsigned)bytes, &barR[i % kRecBufs]);
+      }
+    }
+    ++rec_issued;
+  };
+  auto issue_mat = [&](int i) {  // elected thread: the element matrices of patch i (elements [p*pe, p*pe + ne))
+    if (elected) {
+      const int64_t e0 = (int64_t)patch_of(i) * pe;
+      const int ne = (int)(n_elems - e0 < (int64_t)pe ? n_elems - e0 : (int64_t)pe);
+      uint64_t* bar = &barM[i % kAStages];
+      fence_proxy_async();
+      const unsigned bytes = (unsigned)(ne * NPS * (int)sizeof(T));
+      mbar_arrive_expect(bar, bytes);
+      bulk_g2s(smraw + lay.as + (size_t)(i % kAStages) * lay.as_stride, Ae + e0 * NPS, bytes, bar);
+    }
+    ++mat_issued;
+  };
+  // waits for the record of patch i and checks its header (sizes within the launch's bounds; the elements those
+  // of the patch index); both groups wait on it themselves (its buffer is rewritten only after patch i's sums)
+  auto wait_rec = [&](int i) {
+    const bool w = mbar_wait(&barR[i % kRecBufs], (unsigned)((i / kRecBufs) & 1));
+    rec_waited += w;
+    ok = ok && w;
+    if (ok) {
+      const int32_t* h = hdr(i);
+      const bool sane = h[1] >= 1 && h[1] <= pe && h[3] >= 1 && h[3] <= max_nodes &&
+                        (int64_t)h[0] == (int64_t)patch_of(i) * pe && (int64_t)h[0] + h[1] <= n_elems &&
+                        h[4] >= kRecHeader && h[5] > h[4] && h[6] > h[5] && h[7] > h[6] && h[7] + 4 * h[3] <= max_rec;
+      if (!sane) {
+        if (elected) atomicOr(fault, MK_FAULT_PATCH_RECORD);
+        ok = false;
+      }
+    }
+  };
+  // sum group: x rows of patch i (cp.async; each thread then arrives once its own copies land).  After a failed
+  // wait the copies are skipped but the arrivals still happen, so the phase completes and the step's barrier
+  // reports the failure.
+  auto issue_x = [&](int i) {
+    uint64_t* bar = &barX[i & 1];
+    if (ok) {
+      const int32_t* h = hdr(i);
+      const int nl = h[3];
+      const int32_t* gid = reinterpret_cast<const int32_t*>(recbuf(i) + h[7]);
+      unsigned char* xs = smraw + lay.xs + (size_t)(i & 1) * lay.xs_stride;
+      for (int k = gt; k < nl * XCH; k += NSUM) {
+        const int l = k / XCH, j = k - l * XCH;
+        int64_t g = gid[l];
+        if (g < 0 || g >= n_nodes) {  // a bad id: record it and copy row 0 instead
+          atomicOr(fault, MK_FAULT_PATCH_RECORD);
+          g = 0;
+        }
+        cp_async16(xs + ((size_t)l * W + j * V2) * sizeof(T), x + g * ld + col0 + j * V2);
+      }
+    }
+    cp_async_arrive(bar);
+    ++x_issued;
+  };
+  // after a failure detected at the end of step t: the sum group, which issued every copy, waits (bounded) for the
+  // record phases it has not seen complete and for the element-matrix and x phases of patches t onwards
+  auto drain = [&](int t) {
+    if (tid == 0) atomicOr(fault, MK_FAULT_PATCH_WAIT);
+    if (prod) return;
+    for (int k = rec_waited; k < rec_issued; ++k) mbar_wait(&barR[k % kRecBufs], (unsigned)((k / kRecBufs) & 1));
+    for (int k = t; k < mat_issued; ++k) mbar_wait(&barM[k % kAStages], (unsigned)((k / kAStages) & 1));
+    for (int k = t; k < x_issued; ++k) mbar_wait(&barX[k & 1], (unsigned)((k >> 1) & 1));
+  };
+  if (tid == 0) {
+    for (int k = 0; k < kRecBufs; ++k) mbar_init(&barR[k], 1);
+    for (int k = 0; k < kAStages; ++k) mbar_init(&barM[k], 1);
+    for (int k = 0; k < 2; ++k) mbar_init(&barX[k], (unsigned)NSUM);  // the sum group's cp.async arrivals
+    mbar_fence_init();
+  }
+  __syncthreads();
+  for (int k = 0; k < kAStages - 1 && k < np_mine; ++k) issue_mat(k);
+  for (int k = 0; k < kRecAhead && k < np_mine; ++k) issue_rec(k);
+  if (!prod) {
+    wait_rec(0);
+    issue_x(0);
+  }
+  for (int t = 0; t <= np_mine; ++t) {
+    if (!prod) {
+      if (t + 1 < np_mine) {
+        wait_rec(t + 1);
+        issue_x(t + 1);
+      }
+      if (t + kAStages - 1 < np_mine) issue_mat(t + kAStages - 1);  // into the buffer of patch t - 1
+      if (t + kRecAhead < np_mine) issue_rec(t + kRecAhead);  // into the buffer of record t - 2, read in step t - 1
+      if (t >= 1 && ok) {                     // sums of patch t - 1
+        const int i = t - 1;
+        const int32_t* h = hdr(i);
+        const int nl = h[3];
+        const unsigned char* rb = recbuf(i);
+        const uint16_t* os = reinterpret_cast<const uint16_t*>(rb + h[5]);
+        const int32_t* ts = reinterpret_cast<const int32_t*>(rb + h[6]);
+        const T* Ye = reinterpret_cast<const T*>(smraw + lay.ye + (size_t)(i & 1) * lay.ye_stride);
+        for (int it = gt; it < nl * NG2; it += NSUM) {
+          const int l = it / NG2, g = it - l * NG2;
+          const int e = os[l + 1];
+          Vec<T, V2> acc;
+#pragma unroll
+          for (int c = 0; c < V2; ++c) acc.v[c] = 0;
+          const T* yr = Ye + g * V2;
+          int k = os[l];
+          for (; k + 4 <= e; k += 4) {
+            const Vec<T, V2> v0 = ldv<T, V2>(yr + (size_t)k * W), v1 = ldv<T, V2>(yr + (size_t)(k + 1) * W),
+                             v2 = ldv<T, V2>(yr + (size_t)(k + 2) * W), v3 = ldv<T, V2>(yr + (size_t)(k + 3) * W);
+#pragma unroll
+            for (int c = 0; c < V2; ++c) acc.v[c] = (((acc.v[c] + v0.v[c]) + v1.v[c]) + v2.v[c]) + v3.v[c];
+          }
+          for (; k < e; ++k) {
+            const Vec<T, V2> v = ldv<T, V2>(yr + (size_t)k * W);
+#pragma unroll
+            for (int c = 0; c < V2; ++c) acc.v[c] += v.v[c];
+          }
+          const int tg = ts[l];
+          if (tg >= 0) {
+            if (mask && (tg & kOwnedBoundary))
+#pragma unroll
+              for (int c = 0; c < V2; ++c) acc.v[c] = 0;
+            stv<T, V2>(y + (int64_t)(tg & (kOwnedBoundary - 1)) * ld + col0 + g * V2, acc);
+          } else {
+            stv<T, V2>(halo + (int64_t)(-tg - 1) * ld + col0 + g * V2, acc);
+          }
+        }
+      }
+    } else if (t < np_mine) {  // products of patch t
+      wait_rec(t);
+      ok = ok && mbar_wait(&barM[t % kAStages], (unsigned)((t / kAStages) & 1));
+      ok = ok && mbar_wait(&barX[t & 1], (unsigned)((t >> 1) & 1));
+      const int32_t* h = hdr(t);
+      const int ne = h[1];
+      const unsigned char* rb = recbuf(t);
+      const uint16_t* cs = reinterpret_cast<const uint16_t*>(rb + kRecHeader);
+      const uint16_t* yp = reinterpret_cast<const uint16_t*>(rb + h[4]);
+      const T* As = reinterpret_cast<const T*>(smraw + lay.as + (size_t)(t % kAStages) * lay.as_stride);
+      const T* Xs = reinterpret_cast<const T*>(smraw + lay.xs + (size_t)(t & 1) * lay.xs_stride);
+      T* Ye = reinterpret_cast<T*>(smraw + lay.ye + (size_t)(t & 1) * lay.ye_stride);
+      for (int it = gt; ok && it < ne * NCG; it += kStreamP1) {
+        const int el = it / NCG, g = it - el * NCG;
+        Vec<T, VEC> xv[NLOC];
+#pragma unroll
+        for (int a = 0; a < NLOC; ++a) xv[a] = ldv<T, VEC>(Xs + (int)cs[el * NLOC + a] * W + g * VEC);
+        const T* A = As + el * NPS;
+        Vec<T, VEC> acc[NLOC];
+#pragma unroll
+        for (int a = 0; a < NLOC; ++a)
+#pragma unroll
+          for (int c = 0; c < VEC; ++c) acc[a].v[c] = 0;
+#pragma unroll
+        for (int a = 0; a < NLOC; ++a)
+#pragma unroll
+          for (int b = a; b < NLOC; ++b) {
+            const T wv = A[sym_index(a, b, NLOC)];
+#pragma unroll
+            for (int c = 0; c < VEC; ++c) {
+              acc[a].v[c] += wv * xv[b].v[c];
+              if (b != a) acc[b].v[c] += wv * xv[a].v[c];
+            }
+          }
+#pragma unroll
+        for (int a = 0; a < NLOC; ++a) stv<T, VEC>(Ye + (size_t)yp[el * NLOC + a] * W + g * VEC, acc[a]);
+      }
+    }
+    if (__syncthreads_or(!ok)) { drain(t); return; }
   }
 }
 

@@ -129,6 +129,7 @@ int build_patches(mk_mesh* m, int pe) {
   inc_off.reserve(node_global.size() + np);
   std::vector<int32_t> conn((size_t)E * nloc);
   std::vector<uint16_t> lconn((size_t)E * nloc);
+  std::vector<uint16_t> ypos((size_t)E * nloc);
   std::vector<int32_t> elem_id(E);
   for (int p = 0; p < np; ++p) {
     const int32_t nb = node_off[p], ne = node_off[p + 1];
@@ -161,6 +162,7 @@ int build_patches(mk_mesh* m, int pe) {
     std::vector<int32_t> pos(c.begin(), c.end() - 1);
     for (size_t k = 0; k < lidx.size(); ++k) {  // k = local element * nloc + slot; stored as slot * PE + element
       const int el = (int)(k / nloc), a = (int)(k % nloc);
+      ypos[(size_t)elem_off[p] * nloc + k] = (uint16_t)pos[lidx[k]];  // its place in the node-sorted list
       lst[pos[lidx[k]]++] = (uint16_t)(a * PE + el);
     }
     const int32_t base = (int32_t)inc.size();
@@ -187,6 +189,44 @@ int build_patches(mk_mesh* m, int pe) {
     for (int k = 0; k < 4; ++k)
       for (int c = 0; c < 3; ++c) geomf[i * 16 + 1 + 3 * k + c] = (float)((v[k][c] - cen[c]) / h);
   }
+  // patch records (layout in Patches)
+  auto a16 = [](int64_t b) { return (b + 15) / 16 * 16; };
+  std::vector<int64_t> rec_off(np + 1, 0);
+  for (int p = 0; p < np; ++p) {
+    const int64_t ne = elem_off[p + 1] - elem_off[p], nl = node_off[p + 1] - node_off[p];
+    const int64_t bytes = kRecHeader + 2 * a16(ne * nloc * 2) + a16((nl + 1) * 2) + 2 * a16(nl * 4);
+    rec_off[p + 1] = rec_off[p] + bytes;
+    P.max_rec_bytes = std::max<int>(P.max_rec_bytes, (int)bytes);
+  }
+  std::vector<unsigned char> rec((size_t)rec_off[np], 0);
+  for (int p = 0; p < np; ++p) {
+    const int32_t e0 = elem_off[p], ne = elem_off[p + 1] - e0, n0 = node_off[p], nl = node_off[p + 1] - n0;
+    unsigned char* r = rec.data() + rec_off[p];
+    const int32_t o_inc = kRecHeader + (int32_t)a16((int64_t)ne * nloc * 2);
+    const int32_t o_io = o_inc + (int32_t)a16((int64_t)ne * nloc * 2);
+    const int32_t o_tg = o_io + (int32_t)a16((int64_t)(nl + 1) * 2);
+    const int32_t o_gd = o_tg + (int32_t)a16((int64_t)nl * 4);
+    const int32_t hdr[8] = {e0, ne, n0, nl, o_inc, o_io, o_tg, o_gd};
+    std::memcpy(r, hdr, sizeof(hdr));
+    std::memcpy(r + kRecHeader, lconn.data() + (size_t)e0 * nloc, (size_t)ne * nloc * 2);
+    std::memcpy(r + o_inc, ypos.data() + (size_t)e0 * nloc, (size_t)ne * nloc * 2);
+    const int32_t ibase = e0 * nloc;
+    for (int l = 0; l <= nl; ++l) {
+      const int32_t v = inc_off[n0 + l] - ibase;  // the entry after a patch's last node starts the next patch
+      const uint16_t u = (uint16_t)v;
+      std::memcpy(r + o_io + 2 * l, &u, 2);
+    }
+    std::memcpy(r + o_tg, target.data() + n0, (size_t)nl * 4);
+    std::memcpy(r + o_gd, node_global.data() + n0, (size_t)nl * 4);
+    // the invariants the kernels index by, checked once here: local nodes, incidences and offsets in range
+    for (int64_t k = 0; k < (int64_t)ne * nloc; ++k)
+      if (lconn[(size_t)e0 * nloc + k] >= nl || ypos[(size_t)e0 * nloc + k] >= ne * nloc ||
+          inc[(size_t)e0 * nloc + k] >= nloc * PE)
+        return fail(MK_ERR_INVALID_ARG, "patches: local index out of range");
+    for (int l = 0; l < nl; ++l)
+      if (inc_off[n0 + l + 1] < inc_off[n0 + l] || inc_off[n0 + l + 1] - ibase > ne * nloc)
+        return fail(MK_ERR_INVALID_ARG, "patches: incidence offsets out of range");
+  }
   std::vector<int32_t> mult(nn, 0);
   for (int64_t i = 0; i < E * nloc; ++i) mult[L.elem[i]]++;
   std::vector<float> inv_mult(nn);
@@ -204,6 +244,8 @@ int build_patches(mk_mesh* m, int pe) {
   if (r == MK_OK) r = up(&P.d_inc, inc);
   if (r == MK_OK) r = up(&P.d_shared_node, shared_node);
   if (r == MK_OK) r = up(&P.d_shared_off, shared_off);
+  if (r == MK_OK) r = up(&P.d_rec, rec);
+  if (r == MK_OK) r = up(&P.d_rec_off, rec_off);
   return r;
 }
 
@@ -211,7 +253,7 @@ void free_patches(Patches& p) {
   cudaFree(p.d_patch_elem_off); cudaFree(p.d_patch_node_off); cudaFree(p.d_elem_id); cudaFree(p.d_conn);
   cudaFree(p.d_node_target); cudaFree(p.d_inc_off); cudaFree(p.d_inc); cudaFree(p.d_shared_node);
   cudaFree(p.d_geomf); cudaFree(p.d_inv_mult); cudaFree(p.d_node_gid); cudaFree(p.d_lconn);
-  cudaFree(p.d_shared_off);
+  cudaFree(p.d_shared_off); cudaFree(p.d_rec); cudaFree(p.d_rec_off);
   p = Patches();
 }
 

@@ -192,6 +192,7 @@ int pcg64(mk_ctx* ctx, const mk_mesh* m, const double* Ae, const double* diag, c
   double rr[MK_MAX_RHS];
   MK_CUDA(cudaMemcpyAsync(rr, d3, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
   MK_CUDA(cudaStreamSynchronize(s));
+  MK_TRY(check_fault(ctx, s));
   if (rep) {
     std::memset(rep, 0, sizeof(*rep));
     rep->n_rhs = N;

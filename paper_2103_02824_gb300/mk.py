@@ -84,6 +84,7 @@ _SIGS = {
     "mk_ctx_create": [C.POINTER(_vp), C.c_int],
     "mk_ctx_destroy": [_vp],
     "mk_last_error": [C.c_char_p, C.c_size_t],
+    "mk_ctx_fault": [_vp, C.POINTER(C.c_int)],
     "mk_version": [],
     "mk_launch_count": [],
     "mk_profile_enable": [_vp, C.c_int],
@@ -152,6 +153,14 @@ def load(path: str = LIB_PATH):
 
 def launch_count() -> int:
     return int(lib().mk_launch_count())
+
+
+def ctx_fault(ctx) -> int:
+    """The context's device fault word (0 = none; MK_FAULT_* bits), read after waiting for the device, then
+    cleared."""
+    f = C.c_int()
+    _check(lib().mk_ctx_fault(ctx.h, C.byref(f)))
+    return int(f.value)
 
 
 PROF_APPLY64, PROF_APPLY32, PROF_HALO = 0, 1, 2

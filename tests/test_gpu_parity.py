@@ -428,3 +428,45 @@ def test_assemble_rhs_in_two_halves(ctx, torch, name):
     torch.cuda.synchronize()
     assert torch.equal(vq1, vq2) and torch.equal(rhs1, rhs2)
     assert rel(rhs2.cpu().numpy()[:, :N], c["out"]["rhs"]) < 1e-10
+
+
+@pytest.mark.parametrize("name,pe", [("mol4_p2_mid", 32), ("mol4_p2_mid", 128), ("h_p1", 32)])
+def test_pipelined_patch_kernel_matches_single_patch_kernel(ctx, torch, name, pe):
+    """The persistent pipelined patch kernel (several patches per CTA, the next patch's copies in flight) and the
+    one-patch-per-CTA kernel sum in the same order, so they agree bitwise, FP32 and FP64, for every column
+    width; an ld that is not a multiple of 16 bytes takes the single-patch kernel, still against the oracle.
+    Meshes with more patches than resident CTAs, so that CTAs loop over several patches."""
+    import os
+    from oracle.correction import Level
+    from paper_2103_02824_gb300 import mk, synth
+    wl = synth.workload(name)
+    cc, ct, fc, ft, par = synth.nested_cube_meshes(wl["n_coarse"], wl["levels"], wl["half"])
+    lv = Level(cc, ct, fc, ft, par, wl["order"], wl["Z"], wl["R"])
+    sigma = 2.0
+    m = mk.Mesh(ctx, fc, ft, cc, ct, par, wl["order"])
+    try:
+        mk.mk_mesh_set_patch_elems(m, pe)
+        mol = mk.Molecule(wl["Z"], wl["R"])
+        n = m.info["n_nodes"]
+        A = lv.operator(sigma)
+        for ld in (4, 8, 12, 16, 6):
+            X = np.random.default_rng(ld).standard_normal((n, ld))
+            X[lv.fine.boundary] = 0.0
+            ref = np.zeros((n, ld))
+            ref[lv.fine.free] = A @ X[lv.fine.free]
+            for dt, tol in ((torch.float64, 1e-13), (torch.float32, 3e-6)):
+                x = torch.from_numpy(X).to(dt).cuda()
+                outs = []
+                for pipe in ("1", "0"):
+                    os.environ["MK_PATCH_PIPELINE"] = pipe
+                    y = torch.full_like(x, 5.0)
+                    mk.mk_operator_apply(ctx, m, mol, sigma, x, y)
+                    torch.cuda.synchronize()
+                    outs.append(y)
+                os.environ.pop("MK_PATCH_PIPELINE", None)
+                assert torch.equal(outs[0], outs[1]), (ld, dt)
+                assert rel(outs[0].double().cpu().numpy(), ref) < tol, (ld, dt)
+        assert mk.ctx_fault(ctx) == 0  # no bounded wait gave up, no record failed its checks
+    finally:
+        os.environ.pop("MK_PATCH_PIPELINE", None)
+        m.close()
