@@ -252,6 +252,226 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(int n2, double* __res
   }
 }
 
+// ------------------------------------------------------------------------------------------------ block Jacobi
+// Cyclic block Jacobi on the symmetric n2 x n2 matrix (n2 a multiple of 2 kBW), accumulating Q <- Q U.
+// The indices are cut into blocks of kBW; a sweep pairs the blocks round-robin (nb - 1 rounds of nb / 2 disjoint
+// block pairs).  In a round, each block pair's 2kBW x 2kBW diagonal sub-block is (nearly) diagonalised by an
+// orthogonal U (phase P, one CTA per pair), then S <- U^T S U and Q <- Q U are applied with all the round's U at once
+// (phase A, all CTAs, FP64).  Phase P runs one cyclic Jacobi sweep on the sub-block in FP32 (each angle from the
+// initial FP64 difference of the two diagonal entries, rounded once, plus the FP32 changes of the diagonal since: two
+// nearly equal entries still give the right angle), then makes U orthogonal to FP64 precision with two Newton-Schulz
+// steps U <- U (3I - U^T U) / 2 (GB300 executes FP64 at a small fraction of its FP32 rate, so FP64 is kept to
+// these and to phase A).  So
+// every applied transform is orthogonal in FP64 and the FP64 matrix stays similar to the input; an inexact angle only
+// leaves a small residue that later sweeps remove.  Compared with the scalar cyclic Jacobi this takes kBW times fewer
+// grid barriers per sweep, which is what bounds the scalar version on this GPU.  Two grid barriers per round;
+// *info = {sweeps, buffer holding the result}.
+constexpr int kBW = 8;
+constexpr int kBP = 2 * kBW;
+constexpr int kBJThreads = 256;  // one thread per entry of a kBP x kBP block
+
+__device__ __forceinline__ int bj_index(int I, int J, int k) { return k < kBW ? I * kBW + k : J * kBW + (k - kBW); }
+
+__global__ void __launch_bounds__(kBJThreads) k_bjacobi(int n2, double* __restrict__ S0, double* __restrict__ S1,
+                                                       double* __restrict__ Q, double* __restrict__ Ug,
+                                                       double* __restrict__ red, int max_sweeps, double tol,
+                                                       int* __restrict__ info) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double sa[kBP * kBP], sb[kBP * kBP], sc[kBP * kBP], sd[kBP * kBP];
+  __shared__ float fa[2][kBP * kBP], fu[2][kBP * kBP];
+  __shared__ double dg[kBP];
+  __shared__ float dd[kBP * kBP], dl[kBP];  // FP32 initial diagonal differences, changes of the diagonal
+  __shared__ float rcs[kBP][2];  // per index: its coefficients (self, partner) in the current inner round
+  __shared__ int prt[kBP];       // per index: its partner in the current inner round
+  __shared__ double sh[kBJThreads];
+  const int tid = threadIdx.x;
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + tid;
+  const int64_t gnth = (int64_t)gridDim.x * blockDim.x;
+  const int nb = n2 / kBW, npr = nb / 2;
+  const int ti = tid / kBP, tj = tid % kBP;  // this thread's entry of a block
+  double* Sin = S0;
+  double* Sout = S1;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int64_t t = gtid; t < (int64_t)n2 * n2; t += gnth) {
+      const double v = Sin[t];
+      tot += v * v;
+      if (t / n2 != t % n2) off += v * v;
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+      sh[tid] = pass == 0 ? off : tot;
+      __syncthreads();
+      for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (tid < st) sh[tid] += sh[tid + st];
+        __syncthreads();
+      }
+      if (tid == 0) red[2 * blockIdx.x + pass] = sh[0];
+      __syncthreads();
+    }
+    grid.sync();
+    double o = 0.0, f = 0.0;
+    for (int bl = 0; bl < (int)gridDim.x; ++bl) {
+      o += red[2 * bl];
+      f += red[2 * bl + 1];
+    }
+    grid.sync();
+    if (o <= tol * tol * f) break;
+    for (int r = 0; r < nb - 1; ++r) {
+      // phase P: the orthogonal U of every block pair of the round
+      for (int c = blockIdx.x; c < npr; c += gridDim.x) {
+        int I, J;
+        pair_of(r, c, nb, &I, &J);
+        const double v = Sin[(int64_t)bj_index(I, J, ti) * n2 + bj_index(I, J, tj)];
+        if (ti == tj) dg[ti] = v;
+        fa[0][tid] = ti == tj ? 0.0f : (float)v;
+        fu[0][tid] = ti == tj ? 1.0f : 0.0f;
+        if (tid < kBP) dl[tid] = 0.0f;
+        __syncthreads();
+        dd[tid] = (float)(dg[tj] - dg[ti]);  // the FP64 difference of two diagonal entries, rounded once
+        __syncthreads();
+        int cur = 0;
+        for (int k = 0; k < kBP - 1; ++k) {  // one inner sweep
+          if (tid < kBP / 2) {  // rotation tid of inner round k, all in FP32
+            int p, q;
+            pair_of(k, tid, kBP, &p, &q);
+            const float apq = fa[cur][p * kBP + q];
+            float cc = 1.0f, ss = 0.0f;
+            if (apq != 0.0f) {
+              // a_qq - a_pp = (initial difference) + (the changes since), each part accurate in FP32
+              const float theta = (dd[p * kBP + q] + (dl[q] - dl[p])) / (2.0f * apq);
+              float t;
+              if (!(fabsf(theta) <= 1e18f)) t = isfinite(theta) ? 0.5f / theta : 0.0f;
+              else t = copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.0f));
+              cc = rsqrtf(1.0f + t * t);
+              ss = t * cc;
+              dl[p] -= t * apq;
+              dl[q] += t * apq;
+            }
+            // index p: row' = c row_p - s row_q; index q: row' = s row_p + c row_q (columns alike)
+            rcs[p][0] = cc; rcs[p][1] = -ss; prt[p] = q;
+            rcs[q][0] = cc; rcs[q][1] = ss; prt[q] = p;
+          }
+          __syncthreads();
+          {  // A <- J^T A J and U <- U J with J = [[c, s], [-s, c]] in every (p, q) plane of the round
+            const int yi = prt[ti], yj = prt[tj];
+            const float ri = rcs[ti][0], ro = rcs[ti][1], cs_ = rcs[tj][0], co = rcs[tj][1];
+            const float* A = fa[cur];
+            float nv = 0.0f;  // the diagonal is tracked in dl; a pair's own entry is annihilated
+            if (ti != tj && yi != tj) {
+              const float row0 = ri * A[ti * kBP + tj] + ro * A[yi * kBP + tj];  // (J^T A)[ti][tj]
+              const float row1 = ri * A[ti * kBP + yj] + ro * A[yi * kBP + yj];  // (J^T A)[ti][yj]
+              nv = cs_ * row0 + co * row1;
+            }
+            fa[cur ^ 1][tid] = nv;
+            const float* U = fu[cur];
+            fu[cur ^ 1][tid] = cs_ * U[ti * kBP + tj] + co * U[ti * kBP + yj];
+          }
+          __syncthreads();
+          cur ^= 1;
+        }
+        // U in FP64, two Newton-Schulz steps U <- U + U E / 2 with E = I - U^T U: E (symmetric) in FP64, the small
+        // correction U E in FP32.  The FP32 U is orthogonal to ~1e-6; the steps take that to ~1e-12, then to
+        // FP64 rounding.
+        sa[tid] = (double)fu[cur][tid];
+        __syncthreads();
+        for (int step = 0; step < 2; ++step) {
+          if (ti <= tj) {
+            double g = 0.0;
+            for (int m = 0; m < kBP; ++m) g += sa[m * kBP + ti] * sa[m * kBP + tj];
+            const float e = (float)((ti == tj ? 1.0 : 0.0) - g);
+            fa[cur ^ 1][ti * kBP + tj] = e;
+            fa[cur ^ 1][tj * kBP + ti] = e;
+          }
+          fu[cur][tid] = (float)sa[tid];
+          __syncthreads();
+          float corr = 0.0f;
+          for (int m = 0; m < kBP; ++m) corr = fmaf(fu[cur][ti * kBP + m], fa[cur ^ 1][m * kBP + tj], corr);
+          const double un = sa[tid] + 0.5 * (double)corr;
+          __syncthreads();
+          sa[tid] = un;
+          __syncthreads();
+        }
+        Ug[(int64_t)c * kBP * kBP + tid] = sa[tid];
+        __syncthreads();
+      }
+      grid.sync();
+      // phase A: S_out = U^T S_in U block by block (pairs a >= b, the transpose written too) and Q <- Q U in place.
+      // The operands of a CTA's next item are loaded into registers while the current one is computed.
+      const int nS = npr * (npr + 1) / 2, nQ = (n2 / kBP) * npr;
+      struct Item {
+        int a, b;           // S item: row pair a, column pair b; Q item: a = -1 - row tile, b = column pair
+        int64_t at, at2;    // this thread's entry (and its transposed place for S items)
+        double x, ua, ub;   // S or Q entry, U_a entry, U_b entry
+      };
+      auto load_item = [&](int item, Item& it) {
+        if (item < nS) {
+          int a = (int)((sqrtf(8.0f * (float)item + 1.0f) - 1.0f) * 0.5f);  // item = a (a + 1) / 2 + b, b <= a
+          while ((a + 1) * (a + 2) / 2 <= item) ++a;
+          while (a * (a + 1) / 2 > item) --a;
+          const int b = item - a * (a + 1) / 2;
+          int Ia, Ja, Ib, Jb;
+          pair_of(r, a, nb, &Ia, &Ja);
+          pair_of(r, b, nb, &Ib, &Jb);
+          const int row = bj_index(Ia, Ja, ti), col = bj_index(Ib, Jb, tj);
+          it.a = a; it.b = b;
+          it.at = (int64_t)row * n2 + col;
+          it.at2 = (int64_t)col * n2 + row;
+          it.x = Sin[it.at];
+          it.ua = Ug[(int64_t)a * kBP * kBP + tid];
+          it.ub = Ug[(int64_t)b * kBP * kBP + tid];
+        } else {
+          const int u = item - nS, rt = u / npr, b = u % npr;
+          int Ib, Jb;
+          pair_of(r, b, nb, &Ib, &Jb);
+          it.a = -1 - rt; it.b = b;
+          it.at = (int64_t)(rt * kBP + ti) * n2 + bj_index(Ib, Jb, tj);
+          it.x = Q[it.at];
+          it.ub = Ug[(int64_t)b * kBP * kBP + tid];
+        }
+      };
+      Item cur{}, nxt{};
+      if ((int)blockIdx.x < nS + nQ) load_item(blockIdx.x, cur);
+      for (int item = blockIdx.x; item < nS + nQ; item += gridDim.x) {
+        sa[tid] = cur.x;
+        if (cur.a >= 0) sb[tid] = cur.ua;
+        sc[tid] = cur.ub;
+        __syncthreads();
+        if (item + (int)gridDim.x < nS + nQ) load_item(item + gridDim.x, nxt);
+        if (cur.a >= 0) {
+          double t = 0.0;  // (S U_b)[ti][tj]
+          for (int m = 0; m < kBP; ++m) t += sa[ti * kBP + m] * sc[m * kBP + tj];
+          sd[tid] = t;
+          __syncthreads();
+          double o = 0.0;  // (U_a^T S U_b)[ti][tj]
+          for (int m = 0; m < kBP; ++m) o += sb[m * kBP + ti] * sd[m * kBP + tj];
+          if (cur.a == cur.b) {  // the diagonal block stays exactly symmetric
+            sa[tid] = o;
+            __syncthreads();
+            o = ti <= tj ? sa[tid] : sa[tj * kBP + ti];
+          }
+          Sout[cur.at] = o;
+          if (cur.a != cur.b) Sout[cur.at2] = o;
+        } else {
+          double o = 0.0;
+          for (int m = 0; m < kBP; ++m) o += sa[ti * kBP + m] * sc[m * kBP + tj];
+          Q[cur.at] = o;
+        }
+        __syncthreads();
+        cur = nxt;
+      }
+      grid.sync();
+      double* tmp = Sin;
+      Sin = Sout;
+      Sout = tmp;
+    }
+  }
+  if (gtid == 0) {
+    info[0] = sweep;
+    info[1] = (Sin == S0) ? 0 : 1;
+  }
+}
+
 // C[M x N] = op(A) op(B), op(X) = X or X^T (row-major storage), FP64, 32x32 tiles.
 __global__ void k_gemm64(int M, int N, int K, const double* __restrict__ A, int lda, int ta,
                          const double* __restrict__ B, int ldb, int tb, double* __restrict__ C, int ldc) {
@@ -732,22 +952,38 @@ int coarse_inverse32(mk_ctx* ctx, const mk_mesh* m, const double* A64, float* ou
 // of eigenvector k.
 int decompose(mk_ctx* ctx, int n, const double* X, bool w_is_x, const double* AH, double* d, double* V,
               cudaStream_t s) {
-  const int n2 = (n + 1) / 2 * 2;
+  // block Jacobi (default) on n padded to a multiple of 2 kBW; MK_SCALAR_JACOBI=1 selects the scalar cyclic Jacobi
+  const char* sj = std::getenv("MK_SCALAR_JACOBI");
+  const bool block = !(sj && sj[0] == '1');
+  const int n2 = block ? (n + kBP - 1) / kBP * kBP : (n + 1) / 2 * 2;
   int err = MK_OK;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
   const size_t oT = take((size_t)n * n * 8), oC = take((size_t)n * n * 8), oS0 = take((size_t)n2 * n2 * 8);
   const size_t oS1 = take((size_t)n2 * n2 * 8), oQ = take((size_t)n2 * n2 * 8), oRed = take(8192 * 8);
-  const size_t oPerm = take((size_t)n * 4), oInfo = take(64);
+  const size_t oPerm = take((size_t)n * 4), oInfo = take(64), oU = take((size_t)(n2 / kBP) * kBP * kBP * 8);
   char* ws = (char*)scratch(ctx, S_EIG2, off, &err);
   if (!ws) return err;
   double *T = (double*)(ws + oT), *C = (double*)(ws + oC), *S0 = (double*)(ws + oS0), *S1 = (double*)(ws + oS1);
   double *Q = (double*)(ws + oQ), *red = (double*)(ws + oRed);
   int *perm = (int*)(ws + oPerm), *info = (int*)(ws + oInfo);
+  double* Ug = (double*)(ws + oU);
   const int tx = w_is_x ? 1 : 0;                                     // op for W^T
   gemm64(n, n, n, X, n, tx, AH, n, 0, T, n, s);                      // T = W^T AH
   gemm64(n, n, n, T, n, 0, X, n, 1 - tx, C, n, s);                   // C = T W
   MK_COUNT(), k_pad_sym<<<(int)(((int64_t)n2 * n2 + 255) / 256), 256, 0, s>>>(n, n2, C, S0, Q, 0.0);
+  int max_sweeps = 60;
+  double tol = 1e-14;
+  int n2v = n2;
+  if (block) {
+    int per_sm = 0;
+    MK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bjacobi, kBJThreads, 0));
+    MK_ARG(per_sm >= 1, "mk: block Jacobi kernel cannot be resident");
+    int grid = std::min(ctx->n_sms, 4096);
+    void* args[] = {&n2v, &S0, &S1, &Q, &Ug, &red, &max_sweeps, &tol, &info};
+    MK_COUNT();
+    MK_CUDA(cudaLaunchCooperativeKernel((void*)k_bjacobi, grid, kBJThreads, args, 0, s));
+  } else {
   const int np = n2 / 2;
   const size_t smem = (size_t)np * sizeof(Rot);
   if (smem > 48 * 1024) MK_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -755,17 +991,16 @@ int decompose(mk_ctx* ctx, int n, const double* X, bool w_is_x, const double* AH
   MK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi, kJacobiThreads, smem));
   MK_ARG(per_sm >= 1, "mk: Jacobi kernel cannot be resident (coarse space too large)");
   int grid = std::min(ctx->n_sms, 4096);
-  int max_sweeps = 60;
-  double tol = 1e-14;
-  int n2v = n2;
   void* args[] = {&n2v, &S0, &S1, &Q, &red, &max_sweeps, &tol, &info};
   MK_COUNT();
   MK_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi, grid, kJacobiThreads, args, smem, s));
+  }
   if (std::getenv("MK_DEBUG")) {
     int h[2];
     cudaMemcpyAsync(h, info, sizeof(h), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
-    std::fprintf(stderr, "mk: Jacobi n=%d sweeps=%d (%s)\n", n, h[0], w_is_x ? "warm" : "cholesky");
+    std::fprintf(stderr, "mk: %s Jacobi n=%d sweeps=%d (%s)\n", block ? "block" : "scalar", n, h[0],
+                 w_is_x ? "warm" : "cholesky");
   }
   MK_COUNT(), k_rank<<<(n + 127) / 128, 128, 0, s>>>(n, n2, S0, S1, info, d, perm);
   MK_COUNT(), k_gather_cols<<<(int)(((int64_t)n * n + 255) / 256), 256, 0, s>>>(n, n2, Q, perm, C);  // C = Q sorted
