@@ -256,15 +256,16 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(int n2, double* __res
 // Cyclic block Jacobi on the symmetric n2 x n2 matrix (n2 a multiple of 2 kBW), accumulating Q <- Q U.
 // The indices are cut into blocks of kBW; a sweep pairs the blocks round-robin (nb - 1 rounds of nb / 2 disjoint
 // block pairs).  In a round, each block pair's 2kBW x 2kBW diagonal sub-block is (nearly) diagonalised by an
-// orthogonal U (phase P, one CTA per pair), then S <- U^T S U and Q <- Q U are applied with all the round's U at once
-// (phase A, all CTAs, FP64).  Phase P runs one cyclic Jacobi sweep on the sub-block in FP32 (each angle from the
-// initial FP64 difference of the two diagonal entries, rounded once, plus the FP32 changes of the diagonal since: two
-// nearly equal entries still give the right angle), then makes U orthogonal to FP64 precision with two Newton-Schulz
-// steps U <- U (3I - U^T U) / 2 (GB300 executes FP64 at a small fraction of its FP32 rate, so FP64 is kept to
-// these and to phase A).  So
-// every applied transform is orthogonal in FP64 and the FP64 matrix stays similar to the input; an inexact angle only
-// leaves a small residue that later sweeps remove.  Compared with the scalar cyclic Jacobi this takes kBW times fewer
-// grid barriers per sweep, which is what bounds the scalar version on this GPU.  Two grid barriers per round;
+// orthogonal U, and S <- U^T S U, Q <- Q U are applied with all the round's U at once in FP64.  The sub-problem runs
+// one cyclic Jacobi sweep in FP32 (each angle from the FP64 difference of the two diagonal entries, rounded once, plus
+// the FP32 changes of the diagonal since: nearly equal entries still give the right angle), then U is made
+// orthogonal to FP64 precision by two Newton-Schulz steps U <- U (3I - U^T U) / 2.  So every applied transform is
+// orthogonal in FP64 and the FP64 matrix stays similar to the input; an inexact angle only leaves a small residue
+// that later sweeps remove.  GB300 executes FP64 at a small fraction of its FP32 rate, so FP64 is kept to the
+// Newton-Schulz steps and the block application.
+// Overlap: in round r, CTAs [0, nb/2) compute the U of round r + 1 — the sub-block they need, of S after round r,
+// formed directly from S before round r and the round's U — while the other CTAs apply round r.  One grid barrier
+// per round (kBW times fewer than the scalar cyclic Jacobi, whose barriers bound it on this GPU).
 // *info = {sweeps, buffer holding the result}.
 constexpr int kBW = 8;
 constexpr int kBP = 2 * kBW;
@@ -272,23 +273,169 @@ constexpr int kBJThreads = 256;  // one thread per entry of a kBP x kBP block
 
 __device__ __forceinline__ int bj_index(int I, int J, int k) { return k < kBW ? I * kBW + k : J * kBW + (k - kBW); }
 
-__global__ void __launch_bounds__(kBJThreads) k_bjacobi(int n2, double* __restrict__ S0, double* __restrict__ S1,
+struct BJSmem {
+  double sa[kBP * kBP], sb[kBP * kBP], sc[kBP * kBP], sd[kBP * kBP];
+  float fa[2][kBP * kBP], fu[2][kBP * kBP];
+  double dg[kBP];
+  float dd[kBP * kBP], dl[kBP];  // FP32 initial diagonal differences, changes of the diagonal since
+  float rcs[kBP][2];             // per index: its coefficients (self, partner) in the current inner round
+  int prt[kBP];                  // per index: its partner in the current inner round
+  double sh[kBJThreads];
+  double bb[3 * kBW * kBW];      // the three kBW x kBW blocks of the next round's sub-block
+};
+
+// The orthogonal U that nearly diagonalises the symmetric kBP x kBP block whose entry (ti, tj) = (tid / kBP,
+// tid % kBP) this thread passes in v; written to Uout [kBP * kBP].  Called by all threads of the CTA.
+__device__ void bj_pair_solve(BJSmem& S, double v, double* __restrict__ Uout) {
+  const int tid = threadIdx.x, ti = tid / kBP, tj = tid % kBP;
+  if (ti == tj) S.dg[ti] = v;
+  S.fa[0][tid] = ti == tj ? 0.0f : (float)v;
+  S.fu[0][tid] = ti == tj ? 1.0f : 0.0f;
+  if (tid < kBP) S.dl[tid] = 0.0f;
+  __syncthreads();
+  S.dd[tid] = (float)(S.dg[tj] - S.dg[ti]);  // the FP64 difference of two diagonal entries, rounded once
+  __syncthreads();
+  int cur = 0;
+  for (int k = 0; k < kBP - 1; ++k) {  // one inner sweep
+    if (tid < kBP / 2) {                // rotation tid of inner round k, all in FP32
+      int p, q;
+      pair_of(k, tid, kBP, &p, &q);
+      const float apq = S.fa[cur][p * kBP + q];
+      float cc = 1.0f, ss = 0.0f;
+      if (apq != 0.0f) {
+        // a_qq - a_pp = (initial difference) + (the changes since), each part accurate in FP32
+        const float theta = (S.dd[p * kBP + q] + (S.dl[q] - S.dl[p])) / (2.0f * apq);
+        float t;
+        if (!(fabsf(theta) <= 1e18f)) t = isfinite(theta) ? 0.5f / theta : 0.0f;
+        else t = copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.0f));
+        cc = rsqrtf(1.0f + t * t);
+        ss = t * cc;
+        S.dl[p] -= t * apq;
+        S.dl[q] += t * apq;
+      }
+      // index p: row' = c row_p - s row_q; index q: row' = s row_p + c row_q (columns alike)
+      S.rcs[p][0] = cc; S.rcs[p][1] = -ss; S.prt[p] = q;
+      S.rcs[q][0] = cc; S.rcs[q][1] = ss; S.prt[q] = p;
+    }
+    __syncthreads();
+    {  // A <- J^T A J and U <- U J with J = [[c, s], [-s, c]] in every (p, q) plane of the round
+      const int yi = S.prt[ti], yj = S.prt[tj];
+      const float ri = S.rcs[ti][0], ro = S.rcs[ti][1], cs_ = S.rcs[tj][0], co = S.rcs[tj][1];
+      const float* A = S.fa[cur];
+      float nv = 0.0f;  // the diagonal is tracked in dl; a pair's own entry is annihilated
+      if (ti != tj && yi != tj) {
+        const float row0 = ri * A[ti * kBP + tj] + ro * A[yi * kBP + tj];  // (J^T A)[ti][tj]
+        const float row1 = ri * A[ti * kBP + yj] + ro * A[yi * kBP + yj];  // (J^T A)[ti][yj]
+        nv = cs_ * row0 + co * row1;
+      }
+      S.fa[cur ^ 1][tid] = nv;
+      const float* U = S.fu[cur];
+      S.fu[cur ^ 1][tid] = cs_ * U[ti * kBP + tj] + co * U[ti * kBP + yj];
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  // U in FP64, two Newton-Schulz steps U <- U + U E / 2 with E = I - U^T U: E (symmetric) in FP64, the small
+  // correction U E in FP32.  The FP32 U is orthogonal to ~1e-6; the steps take that to ~1e-12, then to FP64 rounding.
+  S.sa[tid] = (double)S.fu[cur][tid];
+  __syncthreads();
+  for (int step = 0; step < 2; ++step) {
+    if (ti <= tj) {
+      double g = 0.0;
+      for (int m = 0; m < kBP; ++m) g += S.sa[m * kBP + ti] * S.sa[m * kBP + tj];
+      const float e = (float)((ti == tj ? 1.0 : 0.0) - g);
+      S.fa[cur ^ 1][ti * kBP + tj] = e;
+      S.fa[cur ^ 1][tj * kBP + ti] = e;
+    }
+    S.fu[cur][tid] = (float)S.sa[tid];
+    __syncthreads();
+    float corr = 0.0f;
+    for (int m = 0; m < kBP; ++m) corr = fmaf(S.fu[cur][ti * kBP + m], S.fa[cur ^ 1][m * kBP + tj], corr);
+    const double un = S.sa[tid] + 0.5 * (double)corr;
+    __syncthreads();
+    S.sa[tid] = un;
+    __syncthreads();
+  }
+  Uout[tid] = S.sa[tid];
+  __syncthreads();
+}
+
+// The round-r pair holding block K, and whether K is its second block.
+__device__ __forceinline__ void bj_pair_of_block(int r, int K, int nb, int* pair, int* half) {
+  for (int m = 0; m < nb / 2; ++m) {
+    int a, b;
+    pair_of(r, m, nb, &a, &b);
+    if (a == K || b == K) {
+      *pair = m;
+      *half = (b == K) ? 1 : 0;
+      return;
+    }
+  }
+  *pair = 0;
+  *half = 0;
+}
+
+// This thread's entry (tid / kBP, tid % kBP) of the sub-block [I', J'] x [I', J'] of S after round r, i.e. of
+// Ubar^T Sin Ubar with Ubar the round's block-diagonal transform (U of pair m at Ur + m kBP^2): for blocks K, L
+// in round-r pairs x, y, S'[K, L] = U_x[:, half K]^T Sin[x, y] U_y[:, half L] (8 x 16 x 16 x 8 products).
+__device__ double bj_next_block(BJSmem& S, const double* __restrict__ Sin, const double* __restrict__ Ur, int n2,
+                                int nb, int r, int Ip, int Jp) {
+  const int tid = threadIdx.x, ti = tid / kBP, tj = tid % kBP;
+  int x, hx, y, hy;
+  bj_pair_of_block(r, Ip, nb, &x, &hx);
+  bj_pair_of_block(r, Jp, nb, &y, &hy);
+  int Ix, Jx, Iy, Jy;
+  pair_of(r, x, nb, &Ix, &Jx);
+  pair_of(r, y, nb, &Iy, &Jy);
+  // the three 16 x 16 blocks of Sin: [x, x], [x, y], [y, y]
+  const double t1 = Sin[(int64_t)bj_index(Ix, Jx, ti) * n2 + bj_index(Ix, Jx, tj)];
+  const double t2 = Sin[(int64_t)bj_index(Ix, Jx, ti) * n2 + bj_index(Iy, Jy, tj)];
+  const double t3 = Sin[(int64_t)bj_index(Iy, Jy, ti) * n2 + bj_index(Iy, Jy, tj)];
+  S.sb[tid] = Ur[(int64_t)x * kBP * kBP + tid];
+  S.sc[tid] = Ur[(int64_t)y * kBP * kBP + tid];
+  for (int part = 0; part < 3; ++part) {  // S'[I', I'], S'[I', J'], S'[J', J'] into bb
+    S.sa[tid] = part == 0 ? t1 : part == 1 ? t2 : t3;
+    const double* Ul = part == 2 ? S.sc : S.sb;   // left factor: U_x for [x, x] and [x, y], U_y for [y, y]
+    const double* Urt = part == 0 ? S.sb : S.sc;  // right factor
+    const int hl = part == 2 ? hy : hx, hr = part == 0 ? hx : hy;
+    __syncthreads();
+    if (tid < kBP * kBW) {  // W = T U_right[:, half] (16 x 8)
+      const int i = tid / kBW, j = tid % kBW;
+      double w = 0.0;
+      for (int m = 0; m < kBP; ++m) w += S.sa[i * kBP + m] * Urt[m * kBP + hr * kBW + j];
+      S.sd[tid] = w;
+    }
+    __syncthreads();
+    if (tid < kBW * kBW) {  // B = U_left[:, half]^T W (8 x 8)
+      const int i = tid / kBW, j = tid % kBW;
+      double o = 0.0;
+      for (int m = 0; m < kBP; ++m) o += Ul[m * kBP + hl * kBW + i] * S.sd[m * kBW + j];
+      S.bb[part * kBW * kBW + tid] = o;
+    }
+    __syncthreads();
+  }
+  double v;
+  if (ti < kBW && tj < kBW) v = S.bb[ti * kBW + tj];
+  else if (ti < kBW) v = S.bb[kBW * kBW + ti * kBW + (tj - kBW)];
+  else if (tj < kBW) v = S.bb[kBW * kBW + tj * kBW + (ti - kBW)];
+  else v = S.bb[2 * kBW * kBW + (ti - kBW) * kBW + (tj - kBW)];
+  __syncthreads();
+  return v;
+}
+
+__global__ void __launch_bounds__(kBJThreads, 1) k_bjacobi(int n2, double* __restrict__ S0, double* __restrict__ S1,
                                                        double* __restrict__ Q, double* __restrict__ Ug,
                                                        double* __restrict__ red, int max_sweeps, double tol,
                                                        int* __restrict__ info) {
   cg::grid_group grid = cg::this_grid();
-  __shared__ double sa[kBP * kBP], sb[kBP * kBP], sc[kBP * kBP], sd[kBP * kBP];
-  __shared__ float fa[2][kBP * kBP], fu[2][kBP * kBP];
-  __shared__ double dg[kBP];
-  __shared__ float dd[kBP * kBP], dl[kBP];  // FP32 initial diagonal differences, changes of the diagonal
-  __shared__ float rcs[kBP][2];  // per index: its coefficients (self, partner) in the current inner round
-  __shared__ int prt[kBP];       // per index: its partner in the current inner round
-  __shared__ double sh[kBJThreads];
+  __shared__ BJSmem S;
   const int tid = threadIdx.x;
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + tid;
   const int64_t gnth = (int64_t)gridDim.x * blockDim.x;
   const int nb = n2 / kBW, npr = nb / 2;
   const int ti = tid / kBP, tj = tid % kBP;  // this thread's entry of a block
+  const bool solver = (int)blockIdx.x < npr;  // computes the next round's U; the others apply the current round
+  const int na = (int)gridDim.x - npr;       // applying CTAs
   double* Sin = S0;
   double* Sout = S1;
   int sweep = 0;
@@ -300,13 +447,13 @@ __global__ void __launch_bounds__(kBJThreads) k_bjacobi(int n2, double* __restri
       if (t / n2 != t % n2) off += v * v;
     }
     for (int pass = 0; pass < 2; ++pass) {
-      sh[tid] = pass == 0 ? off : tot;
+      S.sh[tid] = pass == 0 ? off : tot;
       __syncthreads();
       for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-        if (tid < st) sh[tid] += sh[tid + st];
+        if (tid < st) S.sh[tid] += S.sh[tid + st];
         __syncthreads();
       }
-      if (tid == 0) red[2 * blockIdx.x + pass] = sh[0];
+      if (tid == 0) red[2 * blockIdx.x + pass] = S.sh[0];
       __syncthreads();
     }
     grid.sync();
@@ -317,148 +464,88 @@ __global__ void __launch_bounds__(kBJThreads) k_bjacobi(int n2, double* __restri
     }
     grid.sync();
     if (o <= tol * tol * f) break;
+    if (solver) {  // the U of round 0, from Sin itself
+      int I, J;
+      pair_of(0, blockIdx.x, nb, &I, &J);
+      bj_pair_solve(S, Sin[(int64_t)bj_index(I, J, ti) * n2 + bj_index(I, J, tj)],
+                    Ug + (int64_t)blockIdx.x * kBP * kBP);
+    }
+    grid.sync();
     for (int r = 0; r < nb - 1; ++r) {
-      // phase P: the orthogonal U of every block pair of the round
-      for (int c = blockIdx.x; c < npr; c += gridDim.x) {
-        int I, J;
-        pair_of(r, c, nb, &I, &J);
-        const double v = Sin[(int64_t)bj_index(I, J, ti) * n2 + bj_index(I, J, tj)];
-        if (ti == tj) dg[ti] = v;
-        fa[0][tid] = ti == tj ? 0.0f : (float)v;
-        fu[0][tid] = ti == tj ? 1.0f : 0.0f;
-        if (tid < kBP) dl[tid] = 0.0f;
-        __syncthreads();
-        dd[tid] = (float)(dg[tj] - dg[ti]);  // the FP64 difference of two diagonal entries, rounded once
-        __syncthreads();
-        int cur = 0;
-        for (int k = 0; k < kBP - 1; ++k) {  // one inner sweep
-          if (tid < kBP / 2) {  // rotation tid of inner round k, all in FP32
-            int p, q;
-            pair_of(k, tid, kBP, &p, &q);
-            const float apq = fa[cur][p * kBP + q];
-            float cc = 1.0f, ss = 0.0f;
-            if (apq != 0.0f) {
-              // a_qq - a_pp = (initial difference) + (the changes since), each part accurate in FP32
-              const float theta = (dd[p * kBP + q] + (dl[q] - dl[p])) / (2.0f * apq);
-              float t;
-              if (!(fabsf(theta) <= 1e18f)) t = isfinite(theta) ? 0.5f / theta : 0.0f;
-              else t = copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.0f));
-              cc = rsqrtf(1.0f + t * t);
-              ss = t * cc;
-              dl[p] -= t * apq;
-              dl[q] += t * apq;
-            }
-            // index p: row' = c row_p - s row_q; index q: row' = s row_p + c row_q (columns alike)
-            rcs[p][0] = cc; rcs[p][1] = -ss; prt[p] = q;
-            rcs[q][0] = cc; rcs[q][1] = ss; prt[q] = p;
-          }
-          __syncthreads();
-          {  // A <- J^T A J and U <- U J with J = [[c, s], [-s, c]] in every (p, q) plane of the round
-            const int yi = prt[ti], yj = prt[tj];
-            const float ri = rcs[ti][0], ro = rcs[ti][1], cs_ = rcs[tj][0], co = rcs[tj][1];
-            const float* A = fa[cur];
-            float nv = 0.0f;  // the diagonal is tracked in dl; a pair's own entry is annihilated
-            if (ti != tj && yi != tj) {
-              const float row0 = ri * A[ti * kBP + tj] + ro * A[yi * kBP + tj];  // (J^T A)[ti][tj]
-              const float row1 = ri * A[ti * kBP + yj] + ro * A[yi * kBP + yj];  // (J^T A)[ti][yj]
-              nv = cs_ * row0 + co * row1;
-            }
-            fa[cur ^ 1][tid] = nv;
-            const float* U = fu[cur];
-            fu[cur ^ 1][tid] = cs_ * U[ti * kBP + tj] + co * U[ti * kBP + yj];
-          }
-          __syncthreads();
-          cur ^= 1;
+      const double* Ur = Ug + (int64_t)(r & 1) * npr * kBP * kBP;
+      if (solver) {
+        if (r + 1 < nb - 1) {
+          int Ip, Jp;
+          pair_of(r + 1, blockIdx.x, nb, &Ip, &Jp);
+          const double v = bj_next_block(S, Sin, Ur, n2, nb, r, Ip, Jp);
+          bj_pair_solve(S, v, Ug + ((int64_t)((r + 1) & 1) * npr + blockIdx.x) * kBP * kBP);
         }
-        // U in FP64, two Newton-Schulz steps U <- U + U E / 2 with E = I - U^T U: E (symmetric) in FP64, the small
-        // correction U E in FP32.  The FP32 U is orthogonal to ~1e-6; the steps take that to ~1e-12, then to
-        // FP64 rounding.
-        sa[tid] = (double)fu[cur][tid];
-        __syncthreads();
-        for (int step = 0; step < 2; ++step) {
-          if (ti <= tj) {
-            double g = 0.0;
-            for (int m = 0; m < kBP; ++m) g += sa[m * kBP + ti] * sa[m * kBP + tj];
-            const float e = (float)((ti == tj ? 1.0 : 0.0) - g);
-            fa[cur ^ 1][ti * kBP + tj] = e;
-            fa[cur ^ 1][tj * kBP + ti] = e;
+      } else {
+        // S_out = U^T S_in U block by block (pairs a >= b, the transpose written too) and Q <- Q U in place; the
+        // operands of a CTA's next item are loaded into registers while the current one is computed
+        const int nS = npr * (npr + 1) / 2, nQ = (n2 / kBP) * npr;
+        struct Item {
+          int a, b;          // S item: row pair a, column pair b; Q item: a = -1 - row tile, b = column pair
+          int64_t at, at2;   // this thread's entry (and its transposed place for S items)
+          double x, ua, ub;  // S or Q entry, U_a entry, U_b entry
+        };
+        auto load_item = [&](int item, Item& it) {
+          if (item < nS) {
+            int a = (int)((sqrtf(8.0f * (float)item + 1.0f) - 1.0f) * 0.5f);  // item = a (a + 1) / 2 + b, b <= a
+            while ((a + 1) * (a + 2) / 2 <= item) ++a;
+            while (a * (a + 1) / 2 > item) --a;
+            const int b = item - a * (a + 1) / 2;
+            int Ia, Ja, Ib, Jb;
+            pair_of(r, a, nb, &Ia, &Ja);
+            pair_of(r, b, nb, &Ib, &Jb);
+            const int row = bj_index(Ia, Ja, ti), col = bj_index(Ib, Jb, tj);
+            it.a = a; it.b = b;
+            it.at = (int64_t)row * n2 + col;
+            it.at2 = (int64_t)col * n2 + row;
+            it.x = Sin[it.at];
+            it.ua = Ur[(int64_t)a * kBP * kBP + tid];
+            it.ub = Ur[(int64_t)b * kBP * kBP + tid];
+          } else {
+            const int u = item - nS, rt = u / npr, b = u % npr;
+            int Ib, Jb;
+            pair_of(r, b, nb, &Ib, &Jb);
+            it.a = -1 - rt; it.b = b;
+            it.at = (int64_t)(rt * kBP + ti) * n2 + bj_index(Ib, Jb, tj);
+            it.x = Q[it.at];
+            it.ub = Ur[(int64_t)b * kBP * kBP + tid];
           }
-          fu[cur][tid] = (float)sa[tid];
+        };
+        const int first = (int)blockIdx.x - npr;
+        Item cur{}, nxt{};
+        if (first < nS + nQ) load_item(first, cur);
+        for (int item = first; item < nS + nQ; item += na) {
+          S.sa[tid] = cur.x;
+          if (cur.a >= 0) S.sb[tid] = cur.ua;
+          S.sc[tid] = cur.ub;
           __syncthreads();
-          float corr = 0.0f;
-          for (int m = 0; m < kBP; ++m) corr = fmaf(fu[cur][ti * kBP + m], fa[cur ^ 1][m * kBP + tj], corr);
-          const double un = sa[tid] + 0.5 * (double)corr;
-          __syncthreads();
-          sa[tid] = un;
-          __syncthreads();
-        }
-        Ug[(int64_t)c * kBP * kBP + tid] = sa[tid];
-        __syncthreads();
-      }
-      grid.sync();
-      // phase A: S_out = U^T S_in U block by block (pairs a >= b, the transpose written too) and Q <- Q U in place.
-      // The operands of a CTA's next item are loaded into registers while the current one is computed.
-      const int nS = npr * (npr + 1) / 2, nQ = (n2 / kBP) * npr;
-      struct Item {
-        int a, b;           // S item: row pair a, column pair b; Q item: a = -1 - row tile, b = column pair
-        int64_t at, at2;    // this thread's entry (and its transposed place for S items)
-        double x, ua, ub;   // S or Q entry, U_a entry, U_b entry
-      };
-      auto load_item = [&](int item, Item& it) {
-        if (item < nS) {
-          int a = (int)((sqrtf(8.0f * (float)item + 1.0f) - 1.0f) * 0.5f);  // item = a (a + 1) / 2 + b, b <= a
-          while ((a + 1) * (a + 2) / 2 <= item) ++a;
-          while (a * (a + 1) / 2 > item) --a;
-          const int b = item - a * (a + 1) / 2;
-          int Ia, Ja, Ib, Jb;
-          pair_of(r, a, nb, &Ia, &Ja);
-          pair_of(r, b, nb, &Ib, &Jb);
-          const int row = bj_index(Ia, Ja, ti), col = bj_index(Ib, Jb, tj);
-          it.a = a; it.b = b;
-          it.at = (int64_t)row * n2 + col;
-          it.at2 = (int64_t)col * n2 + row;
-          it.x = Sin[it.at];
-          it.ua = Ug[(int64_t)a * kBP * kBP + tid];
-          it.ub = Ug[(int64_t)b * kBP * kBP + tid];
-        } else {
-          const int u = item - nS, rt = u / npr, b = u % npr;
-          int Ib, Jb;
-          pair_of(r, b, nb, &Ib, &Jb);
-          it.a = -1 - rt; it.b = b;
-          it.at = (int64_t)(rt * kBP + ti) * n2 + bj_index(Ib, Jb, tj);
-          it.x = Q[it.at];
-          it.ub = Ug[(int64_t)b * kBP * kBP + tid];
-        }
-      };
-      Item cur{}, nxt{};
-      if ((int)blockIdx.x < nS + nQ) load_item(blockIdx.x, cur);
-      for (int item = blockIdx.x; item < nS + nQ; item += gridDim.x) {
-        sa[tid] = cur.x;
-        if (cur.a >= 0) sb[tid] = cur.ua;
-        sc[tid] = cur.ub;
-        __syncthreads();
-        if (item + (int)gridDim.x < nS + nQ) load_item(item + gridDim.x, nxt);
-        if (cur.a >= 0) {
-          double t = 0.0;  // (S U_b)[ti][tj]
-          for (int m = 0; m < kBP; ++m) t += sa[ti * kBP + m] * sc[m * kBP + tj];
-          sd[tid] = t;
-          __syncthreads();
-          double o = 0.0;  // (U_a^T S U_b)[ti][tj]
-          for (int m = 0; m < kBP; ++m) o += sb[m * kBP + ti] * sd[m * kBP + tj];
-          if (cur.a == cur.b) {  // the diagonal block stays exactly symmetric
-            sa[tid] = o;
+          if (item + na < nS + nQ) load_item(item + na, nxt);
+          if (cur.a >= 0) {
+            double t = 0.0;  // (S U_b)[ti][tj]
+            for (int m = 0; m < kBP; ++m) t += S.sa[ti * kBP + m] * S.sc[m * kBP + tj];
+            S.sd[tid] = t;
             __syncthreads();
-            o = ti <= tj ? sa[tid] : sa[tj * kBP + ti];
+            double ov = 0.0;  // (U_a^T S U_b)[ti][tj]
+            for (int m = 0; m < kBP; ++m) ov += S.sb[m * kBP + ti] * S.sd[m * kBP + tj];
+            if (cur.a == cur.b) {  // the diagonal block stays exactly symmetric
+              S.sa[tid] = ov;
+              __syncthreads();
+              ov = ti <= tj ? S.sa[tid] : S.sa[tj * kBP + ti];
+            }
+            Sout[cur.at] = ov;
+            if (cur.a != cur.b) Sout[cur.at2] = ov;
+          } else {
+            double ov = 0.0;
+            for (int m = 0; m < kBP; ++m) ov += S.sa[ti * kBP + m] * S.sc[m * kBP + tj];
+            Q[cur.at] = ov;
           }
-          Sout[cur.at] = o;
-          if (cur.a != cur.b) Sout[cur.at2] = o;
-        } else {
-          double o = 0.0;
-          for (int m = 0; m < kBP; ++m) o += sa[ti * kBP + m] * sc[m * kBP + tj];
-          Q[cur.at] = o;
+          __syncthreads();
+          cur = nxt;
         }
-        __syncthreads();
-        cur = nxt;
       }
       grid.sync();
       double* tmp = Sin;
@@ -961,7 +1048,7 @@ int decompose(mk_ctx* ctx, int n, const double* X, bool w_is_x, const double* AH
   auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
   const size_t oT = take((size_t)n * n * 8), oC = take((size_t)n * n * 8), oS0 = take((size_t)n2 * n2 * 8);
   const size_t oS1 = take((size_t)n2 * n2 * 8), oQ = take((size_t)n2 * n2 * 8), oRed = take(8192 * 8);
-  const size_t oPerm = take((size_t)n * 4), oInfo = take(64), oU = take((size_t)(n2 / kBP) * kBP * kBP * 8);
+  const size_t oPerm = take((size_t)n * 4), oInfo = take(64), oU = take((size_t)2 * (n2 / kBP) * kBP * kBP * 8);
   char* ws = (char*)scratch(ctx, S_EIG2, off, &err);
   if (!ws) return err;
   double *T = (double*)(ws + oT), *C = (double*)(ws + oC), *S0 = (double*)(ws + oS0), *S1 = (double*)(ws + oS1);
@@ -979,7 +1066,8 @@ int decompose(mk_ctx* ctx, int n, const double* X, bool w_is_x, const double* AH
     int per_sm = 0;
     MK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bjacobi, kBJThreads, 0));
     MK_ARG(per_sm >= 1, "mk: block Jacobi kernel cannot be resident");
-    int grid = std::min(ctx->n_sms, 4096);
+    int grid = std::min(ctx->n_sms * per_sm, 4096);
+    MK_ARG(grid > n2 / kBP, "mk: block Jacobi needs more CTAs than block pairs (coarse space too large)");
     void* args[] = {&n2v, &S0, &S1, &Q, &Ug, &red, &max_sweeps, &tol, &info};
     MK_COUNT();
     MK_CUDA(cudaLaunchCooperativeKernel((void*)k_bjacobi, grid, kBJThreads, args, 0, s));
