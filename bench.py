@@ -31,9 +31,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "fine-mesh DOF×orbitals solved/s at 1e-8 rel. residual; learned vs plain PCG"
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_apply_patch launch from an ncu capture of the same kernel
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_apply_stream launch from an ncu capture of the same kernel
 # build on the same workload (None until such a capture exists for the current kernel)
-TRAFFIC = {("mol4_p2", 8): 71.64e6}  # ncu: 68.81 MB read + 2.83 MB written by one launch on mol4_p2
+TRAFFIC = {("mol4_p2", 8): 67.72e6}  # ncu: 65.67 MB read + 2.05 MB written by one launch on mol4_p2
 UNIT = "DOF*orbitals/s"
 
 
@@ -414,7 +414,7 @@ def main():
         flops = 2.0 * nloc * nloc * E * N
         achieved = flops / (ms_k / n_k * 1e-3) / 1e12 if n_k else None
         peak = 1.196  # measured FP64 FMA throughput (TFLOP/s) of this machine's GB300
-        roof = {"kernel": "k_apply_colour<10,double> (one colour sweep = 1 application)", "bound": "alu",
+        roof = {"kernel": "k_apply_patch<10,double> (FP64 element-by-element operator)", "bound": "alu",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,
                 "traffic": None, "applications": n_k, "ms_per_application": ms_k / n_k if n_k else None,
                 "peak_source": "measured FP64 FMA probe, 1.196 TFLOP/s"}
@@ -422,13 +422,13 @@ def main():
         nbytes = 2.0 * info["n_nodes"] * ld * 4 + E * (npack * 4 + nloc * 4 + 2 * nloc)
         achieved = nbytes / (ms_k / n_k * 1e-3) / 1e9 if n_k else None
         peak = peaks.get("hbm_gbs", 6780.7)
-        roof = {"kernel": "k_apply_patch (FP32 element-by-element operator)", "bound": "hbm", "achieved": achieved,
+        roof = {"kernel": "k_apply_stream (FP32 element-by-element operator, persistent pipelined)", "bound": "hbm",
+                "achieved": achieved,
                 "peak": peak, "unit": "GB/s", "frac": achieved / peak if achieved else None,
                 "traffic": TRAFFIC.get((a.workload, ld)),
                 "applications": n_k, "ms_per_application": ms_k / n_k if n_k else None,
                 "bytes_per_application": nbytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst), of measured",
-                "measured": "CUDA events around every application inside the steps (concurrent with the coarse "
-                            "decomposition on the other stream)",
+                "measured": "CUDA events around every application inside the steps",
                 "isolated": None if iso_ms is None else {
                     "ms_per_application": iso_ms, "achieved": nbytes / (iso_ms * 1e-3) / 1e9,
                     "frac": nbytes / (iso_ms * 1e-3) / 1e9 / peak, "applications": 20}}
