@@ -423,7 +423,7 @@ __device__ double bj_next_block(BJSmem& S, const double* __restrict__ Sin, const
   return v;
 }
 
-__global__ void __launch_bounds__(kBJThreads, 1) k_bjacobi(int n2, double* __restrict__ S0, double* __restrict__ S1,
+__global__ void __launch_bounds__(kBJThreads, 2) k_bjacobi(int n2, double* __restrict__ S0, double* __restrict__ S1,
                                                        double* __restrict__ Q, double* __restrict__ Ug,
                                                        double* __restrict__ red, int max_sweeps, double tol,
                                                        int* __restrict__ info) {
@@ -1066,10 +1066,14 @@ int decompose(mk_ctx* ctx, int n, const double* X, bool w_is_x, const double* AH
     int per_sm = 0;
     MK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bjacobi, kBJThreads, 0));
     MK_ARG(per_sm >= 1, "mk: block Jacobi kernel cannot be resident");
-    int grid = std::min(ctx->n_sms * per_sm, 4096);
+    // one CTA per SM (half its registers): the fine solve's kernels on the other stream run beside it
+    int grid = std::min(ctx->n_sms, 4096);
     MK_ARG(grid > n2 / kBP, "mk: block Jacobi needs more CTAs than block pairs (coarse space too large)");
     void* args[] = {&n2v, &S0, &S1, &Q, &Ug, &red, &max_sweeps, &tol, &info};
     MK_COUNT();
+    // the largest shared-memory carveout, so that an SM running this CTA can also take the fine solve's CTAs
+    MK_CUDA(cudaFuncSetAttribute(k_bjacobi, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared));
     MK_CUDA(cudaLaunchCooperativeKernel((void*)k_bjacobi, grid, kBJThreads, args, 0, s));
   } else {
   const int np = n2 / 2;

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(256) k_apply_patch(const int32_t* __restrict__
 // y = A x over a persistent grid of CTAs, each looping over its patches with the next patch's bulk copies in
 // flight (see patch_apply_pipelined).
 template <int NLOC, typename T, int VEC, int NCG>
-__global__ void __launch_bounds__(512, 1) k_apply_stream(const unsigned char* __restrict__ rec,
+__global__ void __launch_bounds__(kStreamThreads, 2) k_apply_stream(const unsigned char* __restrict__ rec,
                                                           const int64_t* __restrict__ rec_off,
                                                           const T* __restrict__ Ae, int mask,
                                                           const T* __restrict__ x, T* __restrict__ y,

@@ -265,8 +265,10 @@ __host__ __device__ inline StreamSmem stream_smem(int nloc, int pe, int max_node
   L.total = L.ye + 2 * L.ye_stride;
   return L;
 }
-constexpr int kStreamThreads = 512;  // 16 warps: warps 0-7 compute element products, warps 8-15 sum and copy
-constexpr int kStreamP1 = 256;
+// 8 warps: warps 0-3 compute element products, warps 4-7 sum and copy.  With at most 128 registers a thread the CTA
+// takes half an SM's registers, so a CTA of the coarse decomposition (run on another stream) fits beside it.
+constexpr int kStreamThreads = 256;
+constexpr int kStreamP1 = 128;
 
 // y = A x (columns [col0, col0 + W)) over the patches blockIdx.x, blockIdx.x + gridDim.x, ... of one CTA,
 // pipelined across two warp groups.  In step t the product group (threads [0, kStreamP1)) computes the element

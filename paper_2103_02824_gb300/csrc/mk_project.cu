@@ -185,12 +185,18 @@ int coarse_matrices(mk_ctx* ctx, const mk_mesh* m, const double* A1, const doubl
   double* P1 = CE + 2 * per;
   double* P2 = P1 + per * kChunks;
   const int blocks = (int)C.n_elems * kChunks;
-  if (nl == 4)
+  // the largest shared-memory carveout: room for the fine solve's CTAs (other stream) beside this kernel's
+  if (nl == 4) {
+    cudaFuncSetAttribute(k_coarse_galerkin<4>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
     MK_COUNT(), k_coarse_galerkin<4><<<blocks, 128, 0, s>>>(m->d_child_off, m->d_child, F.d_geom, C.d_geom,
                                                            ctx->d_ref[1], A1, two ? A2 : nullptr, kChunks, P1, P2);
-  else
+  } else {
+    cudaFuncSetAttribute(k_coarse_galerkin<10>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
     MK_COUNT(), k_coarse_galerkin<10><<<blocks, 128, 0, s>>>(m->d_child_off, m->d_child, F.d_geom, C.d_geom,
                                                             ctx->d_ref[2], A1, two ? A2 : nullptr, kChunks, P1, P2);
+  }
   const int64_t work = (int64_t)per;
   MK_COUNT(), k_coarse_reduce<<<(int)((work + 255) / 256), 256, 0, s>>>(C.n_elems, nl * nl, kChunks, P1, C1);
   if (two) MK_COUNT(), k_coarse_reduce<<<(int)((work + 255) / 256), 256, 0, s>>>(C.n_elems, nl * nl, kChunks, P2, C2);
