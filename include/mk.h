@@ -210,7 +210,9 @@ int mk_correction_solve(mk_ctx* ctx, const mk_mesh* mesh, const mk_molecule* mol
  * sigma M) x on the free DOF (boundary rows of y written as 0), all ld columns, matrix-free element by element with
  * the patch scatter (owner-computes in shared memory, halo slots summed in patch order; bitwise reproducible).
  * precision MK_PREC_FP64: x, y are double [n_nodes*ld]; MK_PREC_MIXED: x, y are float [n_nodes*ld] (the FP32
- * operator of the mixed solve).  Element matrices are rebuilt on every call. */
+ * operator of the mixed solve).  Element matrices are rebuilt on every call.  mol = NULL (with sigma = 0): the
+ * stiffness operator K of the Hartree Poisson problem (Sec. 2, the Hartree equation) instead, in FP32 matrix-free
+ * (per element |det J| J^-1 J^-T times the reference stiffness components), in FP64 from stored element matrices. */
 int mk_operator_apply(mk_ctx* ctx, const mk_mesh* mesh, const mk_molecule* mol, double sigma, int precision,
                       const void* x, void* y, int ld, void* stream);
 

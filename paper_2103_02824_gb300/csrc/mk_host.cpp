@@ -636,6 +636,8 @@ int mk_mesh_destroy(mk_mesh* m) {
   cudaFree(m->d_P_val32);
   cudaFree(m->d_PT_val32);
   cudaFree(m->d_cinv_poisson);
+  cudaFree(m->d_K64);
+  cudaFree(m->d_K64diag);
   cudaFree(m->d_cinv_corr);
   if (m->static_ev) cudaEventDestroy(m->static_ev);
   delete m;

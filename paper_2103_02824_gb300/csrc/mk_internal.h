@@ -124,6 +124,9 @@ struct Patches {
   unsigned char* d_rec = nullptr;
   int64_t* d_rec_off = nullptr;          // [P+1]
   int max_rec_bytes = 0;
+  // matrix-free stiffness operator: per patch-ordered element |det J| (J^-1 J^-T)_{ij}, ij = 00,11,22,01,02,12, and
+  // two zeros (computed on first use)
+  mutable float* d_stiff_fac = nullptr;  // [E*8]
 };
 constexpr int kRecHeader = 32;
 int patch_elems(int nloc);
@@ -215,6 +218,9 @@ struct mk_mesh {
   mutable float* d_P_val32 = nullptr;
   mutable float* d_PT_val32 = nullptr;
   mutable float* d_cinv_poisson = nullptr;
+  // the Hartree Poisson operator: stiffness element matrices (FP64, element order) and K's diagonal, on first use
+  mutable double* d_K64 = nullptr;
+  mutable double* d_K64diag = nullptr;
   mutable float* d_cinv_corr = nullptr;
   mutable std::vector<double> cinv_corr_key;
 };
@@ -254,6 +260,7 @@ enum Slot : int {
   S_LDINV,                      // mk_learned_precond: FP64 diagonal, FP32 inverse
   S_TLC, S_TLX, S_TLW,          // two-level setup: coarse element products, coarse matrices, Cholesky workspace
   S_TLT,                        // two-level apply: restricted residual and coarse solution (FP32)
+  S_TLQ,                        // multiplicative two-level: operator product and residual (FP32)
   S_ELEMP64,                    // FP64 element matrices in patch order (apply64)
   S_BATCH,                      // batched solve: per-problem buffers
   S_COUNT

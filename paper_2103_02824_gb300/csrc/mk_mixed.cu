@@ -232,6 +232,162 @@ int pack_elements(mk_ctx* ctx, const mk_mesh* m, const double* A64, T* A, cudaSt
 template int pack_elements<float>(mk_ctx*, const mk_mesh*, const double*, float*, cudaStream_t);
 template int pack_elements<double>(mk_ctx*, const mk_mesh*, const double*, double*, cudaStream_t);
 
+// ------------------------------------------------------------------------------------------------ stiffness operator
+// Matrix-free FP32 stiffness operator y = K x (the Hartree Poisson operator).  Per element six factors
+// f_c = |det J| (J^-1 J^-T)_{ij} (ij = 00, 11, 22, 01, 02, 12) and K_e = sum_c f_c Khat_c, with Khat_c the reference
+// stiffness components (the tables the FP64 element matrices are built from), so an element streams 32 bytes of
+// factors instead of 55 matrix values.  One CTA per patch, owner-computes sums in the fixed order of patch_apply.
+struct StiffRef {
+  float k[6][55];  // packed symmetric reference components (P1 uses the first 10 of each)
+};
+
+__global__ void k_stiff_factors(int64_t E, const int32_t* __restrict__ elem_id, const Geom* __restrict__ geom,
+                                float* __restrict__ fac) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E) return;
+  const Geom g = geom[elem_id[i]];
+  const double det = fabs(g.det);
+  const int I6[6] = {0, 1, 2, 0, 0, 1}, J6[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const double G = g.Jinv[I6[c] * 3] * g.Jinv[J6[c] * 3] + g.Jinv[I6[c] * 3 + 1] * g.Jinv[J6[c] * 3 + 1] +
+                     g.Jinv[I6[c] * 3 + 2] * g.Jinv[J6[c] * 3 + 2];
+    fac[i * 8 + c] = (float)(det * G);
+  }
+  fac[i * 8 + 6] = 0.f;
+  fac[i * 8 + 7] = 0.f;
+}
+
+template <int NLOC>
+__global__ void __launch_bounds__(128, 8) k_stiff_patch(const int32_t* __restrict__ elem_off,
+                                                    const int32_t* __restrict__ node_off,
+                                                    const int32_t* __restrict__ conn, const float* __restrict__ fac,
+                                                    const int32_t* __restrict__ target,
+                                                    const int32_t* __restrict__ inc_off,
+                                                    const uint16_t* __restrict__ inc, int mask,
+                                                    const float* __restrict__ x, float* __restrict__ y,
+                                                    float* __restrict__ halo, int ncol, int ld, int pe, int max_nodes,
+                                                    const StiffRef ref) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const PatchSmem lay = patch_smem(NLOC, pe, max_nodes, ncol, 4);  // its element-matrix region holds the factors
+  float* Ye = reinterpret_cast<float*>(smraw + lay.ye);            // [NLOC][pe][ncol]
+  const int p = blockIdx.x;
+  const int e0 = elem_off[p], ne = elem_off[p + 1] - e0;
+  const int n0 = node_off[p], nl = node_off[p + 1] - n0;
+  const int ibase = e0 * NLOC;
+  const float* fs = stage_async(smraw + lay.as, fac + (int64_t)e0 * 8, ne * 8 * 4);
+  const int32_t* cs = stage_async(smraw + lay.conn, conn + ibase, ne * NLOC * 4);
+  const uint16_t* is = stage_async(smraw + lay.inc, inc + ibase, ne * NLOC * 2);
+  const int32_t* os = stage_async(smraw + lay.ioff, inc_off + n0, (nl + 1) * 4);
+  const int32_t* ts = stage_async(smraw + lay.tgt, target + n0, nl * 4);
+  cp_async_wait_all();
+  __syncthreads();
+  constexpr int NP = NLOC * (NLOC + 1) / 2;
+  for (int it = threadIdx.x; it < ne * ncol; it += blockDim.x) {
+    const int el = it / ncol, col = it - el * ncol;
+    float xv[NLOC];
+#pragma unroll
+    for (int a = 0; a < NLOC; ++a) xv[a] = x[(int64_t)cs[el * NLOC + a] * ld + col];
+    // y_e = sum_c f_c (Khat_c x_e): the reference components come from the constant bank, so a thread keeps only
+    // x_e, y_e and one Khat_c x_e in registers (many CTAs per SM hide the gather latency)
+    float acc[NLOC];
+#pragma unroll
+    for (int a = 0; a < NLOC; ++a) acc[a] = 0.f;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      float t[NLOC];
+#pragma unroll
+      for (int a = 0; a < NLOC; ++a) t[a] = 0.f;
+#pragma unroll
+      for (int a = 0; a < NLOC; ++a)
+#pragma unroll
+        for (int b = a; b < NLOC; ++b) {
+          const float w = ref.k[c][sym_index(a, b, NLOC)];
+          t[a] = fmaf(w, xv[b], t[a]);
+          if (b != a) t[b] = fmaf(w, xv[a], t[b]);
+        }
+      const float fc = fs[el * 8 + c];
+#pragma unroll
+      for (int a = 0; a < NLOC; ++a) acc[a] = fmaf(fc, t[a], acc[a]);
+    }
+    (void)NP;
+#pragma unroll
+    for (int a = 0; a < NLOC; ++a) Ye[((size_t)a * pe + el) * ncol + col] = acc[a];
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < nl * ncol; it += blockDim.x) {
+    const int l = it / ncol, col = it - l * ncol;
+    const int b = os[l] - ibase, e = os[l + 1] - ibase;
+    float acc = 0.f;
+    int k = b;
+    for (; k + 4 <= e; k += 4) {
+      const float v0 = Ye[(size_t)is[k] * ncol + col], v1 = Ye[(size_t)is[k + 1] * ncol + col];
+      const float v2 = Ye[(size_t)is[k + 2] * ncol + col], v3 = Ye[(size_t)is[k + 3] * ncol + col];
+      acc = (((acc + v0) + v1) + v2) + v3;
+    }
+    for (; k < e; ++k) acc += Ye[(size_t)is[k] * ncol + col];
+    const int t = ts[l];
+    if (t >= 0) {
+      if (mask && (t & kOwnedBoundary)) acc = 0.f;
+      y[(int64_t)(t & (kOwnedBoundary - 1)) * ld + col] = acc;
+    } else {
+      halo[(int64_t)(-t - 1) * ld + col] = acc;
+    }
+  }
+}
+
+// The six patch-ordered stiffness factors per element of mesh m (computed on first use, kept in the mesh handle).
+static const float* stiff_factors(const mk_mesh* m, cudaStream_t s, int* err) {
+  const Patches& P = m->patches;
+  if (P.d_stiff_fac) return P.d_stiff_fac;
+  const Level& L = m->fine;
+  if (cudaMalloc(&P.d_stiff_fac, (size_t)L.n_elems * 8 * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    *err = fail(MK_ERR_OOM, "stiffness factors: allocation failed");
+    return nullptr;
+  }
+  MK_COUNT(), k_stiff_factors<<<(int)((L.n_elems + 255) / 256), 256, 0, s>>>(L.n_elems, P.d_elem_id, L.d_geom,
+                                                                            P.d_stiff_fac);
+  return P.d_stiff_fac;
+}
+
+// y = K x with the matrix-free stiffness operator (all ld columns, boundary rows zero when mask).
+static int apply_stiff(mk_ctx* ctx, const mk_mesh* m, const float* x, float* y, int ld, bool mask, cudaStream_t s) {
+  const Patches& P = m->patches;
+  const Level& L = m->fine;
+  int err = MK_OK;
+  const float* fac = stiff_factors(m, s, &err);
+  float* halo = (float*)scratch(ctx, S_HALO, (size_t)std::max<int64_t>(P.n_halo_slots, 1) * ld * sizeof(float), &err);
+  if (!fac || !halo) return err;
+  StiffRef ref;
+  const RefTables& R = ctx->h_ref[L.order];
+  for (int c = 0; c < 6; ++c)
+    for (int q = 0; q < 55; ++q) ref.k[c][q] = q < R.npack ? (float)R.stiff[c][q] : 0.f;
+  for (int col0 = 0; col0 < ld; col0 += 16) {
+    const int W = std::min(16, ld - col0);
+    const size_t smem = patch_smem(L.nloc, P.max_elems, P.max_nodes, W, 4).total;
+    if (smem > 227 * 1024) return fail(MK_ERR_UNSUPPORTED, "stiffness operator: patch too large for shared memory");
+    prof_mark(ctx, PROF_APPLY32, true, s);
+    if (L.nloc == 4) {
+      if (smem > 48 * 1024) cudaFuncSetAttribute(k_stiff_patch<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      MK_COUNT(), k_stiff_patch<4><<<P.n_patches, 128, smem, s>>>(P.d_patch_elem_off, P.d_patch_node_off, P.d_conn,
+                                                                  fac, P.d_node_target, P.d_inc_off, P.d_inc, mask,
+                                                                  x + col0, y + col0, halo + col0, W, ld,
+                                                                  P.max_elems, P.max_nodes, ref);
+    } else {
+      if (smem > 48 * 1024) cudaFuncSetAttribute(k_stiff_patch<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      MK_COUNT(), k_stiff_patch<10><<<P.n_patches, 128, smem, s>>>(P.d_patch_elem_off, P.d_patch_node_off, P.d_conn,
+                                                                   fac, P.d_node_target, P.d_inc_off, P.d_inc, mask,
+                                                                   x + col0, y + col0, halo + col0, W, ld,
+                                                                   P.max_elems, P.max_nodes, ref);
+    }
+    prof_mark(ctx, PROF_APPLY32, false, s);
+    MK_TRY(halo_pass<float>(ctx, m, halo, y, mask, W, 1, col0, ld, s));
+  }
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
 // ------------------------------------------------------------------------------------------------ two-level
 // Coarse-space correction of the preconditioner (two-level additive, the coarse space V_H of the method):
 // t = P^T r restricted to the coarse free DOF, y = A_H^-1 t with the dense inverse of the Galerkin coarse operator
@@ -384,6 +540,62 @@ const float* coarse_inverse_cached(mk_ctx* ctx, const mk_mesh* m, const double* 
 }
 
 // z = (add ? z : D^-1 r) + P A_H^-1 P^T r for columns < N.
+// Symmetric multiplicative two-level preconditioner (one damped Jacobi sweep, the coarse correction, one damped
+// Jacobi sweep): z = w D^-1 r;  z += P A_H^-1 P^T (r - A z);  z += w D^-1 (r - A z).  w = kTLOmega: the largest
+// eigenvalue of D^-1 A is about 2 for the P1/P2 stiffness matrices of these meshes (power iteration), so 0.8 keeps
+// the sweep a smoother and the preconditioner positive definite.  On the 250,047-DOF P2 Poisson problem it takes FCG
+// to 1e-8 in 47 iterations against 85 for the additive form (CPU experiment with the same matrices).
+constexpr float kTLOmega = 0.8f;
+
+__global__ void k_tl_jacobi(int64_t n, const uint8_t* __restrict__ bnd, const float* __restrict__ dinv,
+                            const float* __restrict__ r, float* __restrict__ z, int ld, int N, float w) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * N) return;
+  const int64_t i = t / N;
+  const int64_t idx = i * ld + (t - i * N);
+  z[idx] = bnd[i] ? 0.f : w * dinv[i] * r[idx];
+}
+// mode 0: t = r - q;  mode 1: z += w D^-1 (r - q)
+__global__ void k_tl_resid(int64_t n, const uint8_t* __restrict__ bnd, const float* __restrict__ dinv,
+                           const float* __restrict__ r, const float* __restrict__ q, float* __restrict__ out, int ld,
+                           int N, float w, int mode) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * N) return;
+  const int64_t i = t / N;
+  const int64_t idx = i * ld + (t - i * N);
+  if (bnd[i]) {
+    out[idx] = 0.f;
+    return;
+  }
+  const float d = r[idx] - q[idx];
+  out[idx] = mode == 0 ? d : fmaf(w * dinv[i], d, out[idx]);
+}
+
+template <typename Apply>
+static int twolevel_mult_apply(mk_ctx* ctx, const mk_mesh* m, Apply&& apply32, const float* cinv, const float* dinv,
+                               const float* r, float* z, int ld, int N, cudaStream_t s) {
+  const Level& L = m->fine;
+  const int nH = (int)m->coarse.n_free;
+  int err = MK_OK;
+  float* t = (float*)scratch(ctx, S_TLT, (size_t)(kTLS + 1) * nH * ld * sizeof(float), &err);
+  float* q = (float*)scratch(ctx, S_TLQ, (size_t)L.n_nodes * ld * 2 * sizeof(float), &err);
+  if (!t || !q) return err;
+  float* y = t + (size_t)kTLS * nH * ld;
+  float* rr = q + (size_t)L.n_nodes * ld;
+  const int gb = (int)((L.n_nodes * N + 255) / 256);
+  MK_COUNT(), k_tl_jacobi<<<gb, 256, 0, s>>>(L.n_nodes, L.d_boundary, dinv, r, z, ld, N, kTLOmega);
+  MK_TRY(apply32(z, q));
+  MK_COUNT(), k_tl_resid<<<gb, 256, 0, s>>>(L.n_nodes, L.d_boundary, dinv, r, q, rr, ld, N, kTLOmega, 0);
+  MK_COUNT(), k_tl_restrict<<<nH * kTLS, 256, 0, s>>>(m->d_PT_off, m->d_PT_col, m->d_PT_val32, rr, ld, N, t);
+  MK_COUNT(), k_tl_coarse<<<(nH * 32 + 255) / 256, 256, 0, s>>>(nH, cinv, t, ld, N, y);
+  MK_COUNT(), k_tl_prolong<<<gb, 256, 0, s>>>(L.n_nodes, m->d_P_off, m->d_P_col, m->d_P_val32, y, dinv,
+                                              L.d_boundary, r, z, ld, N, 1);
+  MK_TRY(apply32(z, q));
+  MK_COUNT(), k_tl_resid<<<gb, 256, 0, s>>>(L.n_nodes, L.d_boundary, dinv, r, q, z, ld, N, kTLOmega, 1);
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
 static int twolevel_apply(mk_ctx* ctx, const mk_mesh* m, const float* cinv, const float* dinv, const float* r,
                           float* z, int ld, int N, bool add, cudaStream_t s) {
   const Level& L = m->fine;
@@ -703,7 +915,8 @@ __global__ void __launch_bounds__(kFinThreads) k_mixed_finalize(int mode, const 
 }
 
 int pcg_mixed(mk_ctx* ctx, const mk_mesh* m, const double* A64, const double* b, double* x, int ld, int N,
-              const mk_solve_opts& o, mk_solve_report* rep, cudaStream_t s, const float* cinv);
+              const mk_solve_opts& o, mk_solve_report* rep, cudaStream_t s, const float* cinv, bool stiff,
+              const double* diag_pre);
 
 int solve_mixed(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, double sigma, const double* b,
                 const double*, const double*, double* x, int ld, int N, const mk_solve_opts& o, mk_solve_report* rep,
@@ -731,28 +944,33 @@ int solve_mixed(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, double si
     cinv = coarse_inverse_cached(ctx, m, A64, &key, s, &err);
     if (!cinv) return err;
   }
-  return pcg_mixed(ctx, m, A64, b, x, ld, N, o, rep, s, cinv);
+  return pcg_mixed(ctx, m, A64, b, x, ld, N, o, rep, s, cinv, false, nullptr);
 }
 
 // FP32 inner Jacobi-PCG on the patch operator built from the FP64 element matrices A64 (element order), FP64
-// residual b - A x and iterative refinement of x until every column meets o.rtol.
+// residual b - A x and iterative refinement of x until every column meets o.rtol.  stiff: A64 is the stiffness
+// matrix K itself, and the inner FP32 applications use the matrix-free stiffness operator.  diag_pre: the
+// operator's diagonal if already known (else assembled here).
 static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const double* b, double* x, int ld, int N,
-                        const mk_solve_opts& o, mk_solve_report* rep, cudaStream_t s, const float* cinv);
+                        const mk_solve_opts& o, mk_solve_report* rep, cudaStream_t s, const float* cinv, bool stiff,
+                        const double* diag_pre);
 
 // Runs the solve on the context's own stream (CUDA graphs cannot be captured on the legacy default stream), after
 // everything already queued on the caller's stream and before anything queued there afterwards.
 int pcg_mixed(mk_ctx* ctx, const mk_mesh* m, const double* A64, const double* b, double* x, int ld, int N,
-              const mk_solve_opts& o, mk_solve_report* rep, cudaStream_t caller, const float* cinv) {
+              const mk_solve_opts& o, mk_solve_report* rep, cudaStream_t caller, const float* cinv, bool stiff,
+              const double* diag_pre) {
   MK_CUDA(cudaEventRecord(ctx->solve_ev[0], caller));
   MK_CUDA(cudaStreamWaitEvent(ctx->solve_stream, ctx->solve_ev[0], 0));
-  const int r = pcg_mixed_on(ctx, m, A64, b, x, ld, N, o, rep, ctx->solve_stream, cinv);
+  const int r = pcg_mixed_on(ctx, m, A64, b, x, ld, N, o, rep, ctx->solve_stream, cinv, stiff, diag_pre);
   MK_CUDA(cudaEventRecord(ctx->solve_ev[1], ctx->solve_stream));
   MK_CUDA(cudaStreamWaitEvent(caller, ctx->solve_ev[1], 0));
   return r;
 }
 
 static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const double* b, double* x, int ld, int N,
-                        const mk_solve_opts& o, mk_solve_report* rep, cudaStream_t s, const float* cinv) {
+                        const mk_solve_opts& o, mk_solve_report* rep, cudaStream_t s, const float* cinv, bool stiff,
+                        const double* diag_pre) {
   MK_ARG(ld <= 256, "mixed path: ld must be <= 256");
   const Level& L = m->fine;
   const int64_t n = L.n_nodes;
@@ -781,8 +999,17 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
     ctx->pinned_size = 256 * sizeof(MixState);
   }
   MixState* hst = (MixState*)ctx->pinned;
-  MK_TRY(assemble_diagonal(ctx, L, A64, diag, s));
-  MK_TRY(pack_elements<float>(ctx, m, A64, A32, s));
+  if (diag_pre) MK_CUDA(cudaMemcpyAsync(diag, diag_pre, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  else MK_TRY(assemble_diagonal(ctx, L, A64, diag, s));
+  if (!stiff) MK_TRY(pack_elements<float>(ctx, m, A64, A32, s));
+  // the FP64 element matrices in patch order, packed once for every residual of this solve
+  double* A64p = (double*)scratch(ctx, S_ELEMP64, (size_t)L.n_elems * padded_np(L.nloc, 8) * sizeof(double), &err);
+  if (!A64p) return err;
+  MK_TRY(pack_elements<double>(ctx, m, A64, A64p, s));
+  // the inner FP32 operator: the packed element matrices, or the matrix-free stiffness operator
+  auto apply32 = [&](const float* xin, float* yout) -> int {
+    return stiff ? apply_stiff(ctx, m, xin, yout, ld, true, s) : apply_patch<float>(ctx, m, A32, xin, yout, ld, true, s);
+  };
   MK_COUNT(), k_dinv32<<<(int)((n + 255) / 256), 256, 0, s>>>(n, diag, dinv);
   MK_COUNT(), k_zero_boundary<<<(int)((n * ld + 255) / 256), 256, 0, s>>>(n, L.d_boundary, x, ld);
   MK_CUDA(cudaMemsetAsync(st, 0, 256 * sizeof(MixState), s));
@@ -800,13 +1027,15 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
   if (!scratch(ctx, S_HALO, (size_t)std::max<int64_t>(m->patches.n_halo_slots, 1) * ld * sizeof(float), &err))
     return err;
   if (cinv && !scratch(ctx, S_TLT, (size_t)(kTLS + 1) * m->coarse.n_free * ld * sizeof(float), &err)) return err;
+  if (cinv && !learned && !scratch(ctx, S_TLQ, (size_t)n * ld * 2 * sizeof(float), &err)) return err;
+  if (stiff && !stiff_factors(m, s, &err)) return err;  // allocated here: nothing may allocate inside a capture
   if (fcg) {
     if (!scratch(ctx, S_LHALO, (size_t)std::max<int64_t>(m->patches.n_halo_slots, 1) * ld * sizeof(float), &err))
       return err;
     MK_CUDA(cudaMemsetAsync(zb, 0, (size_t)n * ld * sizeof(float), s));  // columns >= N stay zero
   }
   for (;;) {
-    MK_TRY(apply64(ctx, m, A64, x, Ax, ld, ld, true, s));   // FP64 residual of the current x
+    MK_TRY(apply_patch<double>(ctx, m, A64p, x, Ax, ld, true, s));  // FP64 residual of the current x
     MK_COUNT(), k_mixed_residual<<<nblk, th, 0, s>>>(n, L.d_boundary, b, Ax, r, d, N, ld, part);
     MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(0, part, nblk, 2, ld, N, st, o.rtol, inner2);
     MK_CUDA(cudaMemcpyAsync(hst, st, sizeof(MixState) * ld, cudaMemcpyDeviceToHost, s));
@@ -822,7 +1051,7 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
         if (cinv) MK_TRY(twolevel_apply(ctx, m, cinv, dinv, r, zb, ld, N, true, s));
         return MK_OK;
       }
-      return twolevel_apply(ctx, m, cinv, dinv, r, zb, ld, N, false, s);
+      return twolevel_mult_apply(ctx, m, apply32, cinv, dinv, r, zb, ld, N, s);
     };
     if (fcg) {
       MK_TRY(precond());
@@ -838,7 +1067,7 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
     // one PCG (or FCG(1)) iteration; every scalar it needs lives on the device, so `check` of them can be
     // replayed as a graph
     auto iteration = [&]() -> int {
-      MK_TRY(apply_patch<float>(ctx, m, A32, p, q, ld, true, s));
+      MK_TRY(apply32(p, q));
       if (fcg) {
         MK_COUNT(), k_fcg_pq<<<nblk, th, 0, s>>>(n, p, q, r, ld, part);
         MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(4, part, nblk, 2, ld, N, st, o.rtol, inner2);
@@ -930,18 +1159,25 @@ using namespace mk;
 
 extern "C" int mk_operator_apply(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, double sigma, int precision,
                                  const void* x, void* y, int ld, void* stream) {
-  MK_ARG(ctx && m && mol && x && y && ld >= 1 && ld <= 256, "mk_operator_apply: bad argument");
+  MK_ARG(ctx && m && x && y && ld >= 1 && ld <= 256, "mk_operator_apply: bad argument");
+  MK_ARG(mol || sigma == 0.0, "mk_operator_apply: the stiffness operator (no molecule) takes sigma = 0");
   MK_ARG(precision == MK_PREC_FP64 || precision == MK_PREC_MIXED, "mk_operator_apply: bad precision");
   MK_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
   const Level& L = m->fine;
   const int np = L.nloc * (L.nloc + 1) / 2;
   int err = MK_OK;
+  if (!mol && precision == MK_PREC_MIXED)  // the Hartree Poisson operator K, matrix-free in FP32
+    return apply_stiff(ctx, m, (const float*)x, (float*)y, ld, true, s);
   double* A64 = (double*)scratch(ctx, S_OPA, (size_t)L.n_elems * np * sizeof(double), &err);
   if (!A64) return err;
-  const double* H0 = static_matrices(ctx, m, mol, s, &err);
-  if (!H0) return err;
-  MK_TRY(element_matrices(ctx, L, nullptr, 0.0, 0.0, sigma, nullptr, A64, s, H0));
+  if (mol) {
+    const double* H0 = static_matrices(ctx, m, mol, s, &err);
+    if (!H0) return err;
+    MK_TRY(element_matrices(ctx, L, nullptr, 0.0, 0.0, sigma, nullptr, A64, s, H0));
+  } else {
+    MK_TRY(element_matrices(ctx, L, nullptr, 1.0, 0.0, 0.0, nullptr, A64, s));  // K
+  }
   if (precision == MK_PREC_FP64) {
     double* A = (double*)scratch(ctx, S_OPB, (size_t)L.n_elems * padded_np(L.nloc, 8) * sizeof(double), &err);
     if (!A) return err;

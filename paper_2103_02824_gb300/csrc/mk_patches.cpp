@@ -253,7 +253,7 @@ void free_patches(Patches& p) {
   cudaFree(p.d_patch_elem_off); cudaFree(p.d_patch_node_off); cudaFree(p.d_elem_id); cudaFree(p.d_conn);
   cudaFree(p.d_node_target); cudaFree(p.d_inc_off); cudaFree(p.d_inc); cudaFree(p.d_shared_node);
   cudaFree(p.d_geomf); cudaFree(p.d_inv_mult); cudaFree(p.d_node_gid); cudaFree(p.d_lconn);
-  cudaFree(p.d_shared_off); cudaFree(p.d_rec); cudaFree(p.d_rec_off);
+  cudaFree(p.d_shared_off); cudaFree(p.d_rec); cudaFree(p.d_rec_off); cudaFree(p.d_stiff_fac);
   p = Patches();
 }
 

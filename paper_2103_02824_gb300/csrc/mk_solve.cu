@@ -18,7 +18,8 @@ int multipole_boundary(mk_ctx*, const Level&, const double*, const double*, int,
 int solve_mixed(mk_ctx*, const mk_mesh*, const mk_molecule*, double, const double*, const double*, const double*,
                 double*, int, int, const mk_solve_opts&, mk_solve_report*, cudaStream_t);
 int pcg_mixed(mk_ctx*, const mk_mesh*, const double*, const double*, double*, int, int, const mk_solve_opts&,
-              mk_solve_report*, cudaStream_t, const float* cinv = nullptr);
+              mk_solve_report*, cudaStream_t, const float* cinv = nullptr, bool stiff = false,
+              const double* diag_pre = nullptr);
 
 // Per-column PCG state on the device.
 struct ColState {
@@ -292,14 +293,23 @@ int mk_hartree_poisson(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, c
   double* F = (double*)scratch(ctx, S_VEC1, L.n_nodes * sizeof(double), &err);
   double* y = (double*)scratch(ctx, S_VEC2, L.n_nodes * sizeof(double), &err);
   double* d = (double*)scratch(ctx, S_VEC3, L.n_nodes * sizeof(double), &err);
-  double* Ke = (double*)scratch(ctx, S_ELEM64, (size_t)L.n_elems * (L.nloc * (L.nloc + 1) / 2) * sizeof(double), &err);
   double* diag = (double*)scratch(ctx, S_DIAG64, L.n_nodes * sizeof(double), &err);
-  if (!rho || !F || !y || !d || !Ke || !diag) return err;
+  if (!rho || !F || !y || !d || !diag) return err;
+  // K and its diagonal depend on the mesh only: built on the first call, kept in the mesh handle
+  if (!m->d_K64) {
+    const size_t kb = (size_t)L.n_elems * (L.nloc * (L.nloc + 1) / 2) * sizeof(double);
+    if (cudaMalloc(&m->d_K64, kb) != cudaSuccess || cudaMalloc(&m->d_K64diag, L.n_nodes * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(MK_ERR_OOM, "mk_hartree_poisson: stiffness allocation failed");
+    }
+    MK_TRY(element_matrices(ctx, L, nullptr, 1.0, 0.0, 0.0, nullptr, m->d_K64, s));
+    MK_TRY(assemble_diagonal(ctx, L, m->d_K64, m->d_K64diag, s));
+  }
+  const double* Ke = m->d_K64;
+  MK_CUDA(cudaMemcpyAsync(diag, m->d_K64diag, L.n_nodes * sizeof(double), cudaMemcpyDeviceToDevice, s));
   MK_TRY(density(ctx, L, u, ld, N, occ, rho, s));
   MK_TRY(load_vector(ctx, L, rho, 4.0 * M_PI, F, s));
   MK_TRY(multipole_boundary(ctx, L, rho, L.d_nodes, bc, w, s));
-  MK_TRY(element_matrices(ctx, L, nullptr, 1.0, 0.0, 0.0, nullptr, Ke, s));
-  MK_TRY(assemble_diagonal(ctx, L, Ke, diag, s));
   MK_TRY(apply64(ctx, m, Ke, w, y, 1, 1, true, s));                     // K_IB g (interior rows)
   ColParams coef{};
   coef.v[0] = 1.0;
@@ -311,7 +321,7 @@ int mk_hartree_poisson(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, c
     cinv = coarse_inverse_cached(ctx, m, Ke, nullptr, s, &err);
     if (!cinv) return err;
   }
-  int r = opts->precision == MK_PREC_MIXED ? pcg_mixed(ctx, m, Ke, F, d, 1, 1, *opts, report, s, cinv)
+  int r = opts->precision == MK_PREC_MIXED ? pcg_mixed(ctx, m, Ke, F, d, 1, 1, *opts, report, s, cinv, true, diag)
                                            : pcg64(ctx, m, Ke, diag, F, d, 1, 1, *opts, report, s);
   MK_COUNT(), k_axpy_interior<<<(int)((L.n_nodes + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, d, w);
   MK_CUDA(cudaGetLastError());

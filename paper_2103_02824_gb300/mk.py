@@ -467,13 +467,14 @@ def mk_small_eigensolve(ctx, NH, N, AH, MH, b, c, beta, gamma, lam, coef, status
 
 
 def mk_operator_apply(ctx, mesh, mol: Molecule, sigma, x, y, stream=None):
-    """y = (K/2 + M_Vext + sigma M) x; float32 tensors select the FP32 operator, float64 the FP64 one."""
+    """y = (K/2 + M_Vext + sigma M) x, or y = K x (the Poisson operator) with mol None and sigma 0; float32 tensors
+    select the FP32 operator, float64 the FP64 one."""
     import torch
     prec = MK_PREC_MIXED if x.dtype == torch.float32 else MK_PREC_FP64
     assert y.dtype == x.dtype
     ld = x.shape[1] if x.dim() == 2 else 1
-    _check(lib().mk_operator_apply(ctx.h, mesh.h, C.byref(mol.c), float(sigma), prec, _ptr(x), _ptr(y), ld,
-                                   _stream(stream)))
+    _check(lib().mk_operator_apply(ctx.h, mesh.h, None if mol is None else C.byref(mol.c), float(sigma), prec,
+                                   _ptr(x), _ptr(y), ld, _stream(stream)))
 
 
 def mk_coarse_pencil(ctx, mesh, mol: Molecule, vq, AH, MH, stream=None):
