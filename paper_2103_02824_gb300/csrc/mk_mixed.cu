@@ -435,41 +435,49 @@ __global__ void __launch_bounds__(256) k_tl_restrict(const int32_t* __restrict__
   }
 }
 
-// y[k][j] = sum_l Ainv[k][l] t[l][j] with t[l][j] = sum over segments of tp[l][seg][j] (in order); one warp per
-// coarse DOF k.
-__global__ void k_tl_coarse(int nH, const float* __restrict__ Ainv, const float* __restrict__ tp, int ld, int N,
-                            float* __restrict__ y) {
-  const int k = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-  if (k >= nH) return;
+// y[k][j] = sum_l Ainv[k][l] t[l][j] with t[l][j] = sum over segments of tp[l][seg][j] (in order); a CTA first
+// forms t for its column chunk in shared memory, then each of its warps takes one coarse DOF k.
+constexpr int kTLRows = 8;  // coarse DOF per CTA (one per warp)
+__global__ void __launch_bounds__(kTLRows * 32) k_tl_coarse(int nH, const float* __restrict__ Ainv,
+                                                           const float* __restrict__ tp, int ld, int N,
+                                                           float* __restrict__ y) {
+  extern __shared__ float tsh[];  // [nH][kTLC]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x * kTLRows + warp;
   for (int c0 = 0; c0 < N; c0 += kTLC) {
     const int nc = min(kTLC, N - c0);
-    float acc[kTLC];
+    for (int i = threadIdx.x; i < nH * nc; i += blockDim.x) {
+      const int l = i / nc, c = i - l * nc;
+      float t = 0.f;
 #pragma unroll
-    for (int c = 0; c < kTLC; ++c) acc[c] = 0.f;
-    for (int l = lane; l < nH; l += 32) {
-      const float a = Ainv[(int64_t)k * nH + l];
-#pragma unroll
-      for (int c = 0; c < kTLC; ++c)
-        if (c < nc) {
-          float t = 0.f;
-#pragma unroll
-          for (int sg = 0; sg < kTLS; ++sg) t += tp[((int64_t)l * kTLS + sg) * ld + c0 + c];
-          acc[c] = fmaf(a, t, acc[c]);
-        }
+      for (int sg = 0; sg < kTLS; ++sg) t += tp[((int64_t)l * kTLS + sg) * ld + c0 + c];
+      tsh[l * kTLC + c] = t;
     }
+    __syncthreads();
+    if (k < nH) {
+      float acc[kTLC];
 #pragma unroll
-    for (int c = 0; c < kTLC; ++c) {
+      for (int c = 0; c < kTLC; ++c) acc[c] = 0.f;
+      for (int l = lane; l < nH; l += 32) {
+        const float a = Ainv[(int64_t)k * nH + l];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], o);
+        for (int c = 0; c < kTLC; ++c)
+          if (c < nc) acc[c] = fmaf(a, tsh[l * kTLC + c], acc[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < kTLC; ++c) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], o);
+      }
+      if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < kTLC; ++c)
+          if (c < nc) y[(int64_t)k * ld + c0 + c] = acc[c];
     }
-    if (lane == 0)
-#pragma unroll
-      for (int c = 0; c < kTLC; ++c)
-        if (c < nc) y[(int64_t)k * ld + c0 + c] = acc[c];
+    __syncthreads();
   }
 }
 
-// z[i][j] = (add ? z[i][j] : r[i][j] / diag[i]) + sum_q P[i][q] y[q][j] for j < N; boundary rows 0.
 __global__ void k_tl_prolong(int64_t n, const int32_t* __restrict__ off, const int32_t* __restrict__ col,
                              const float* __restrict__ val, const float* __restrict__ y,
                              const float* __restrict__ dinv, const uint8_t* __restrict__ bnd,
@@ -587,7 +595,8 @@ static int twolevel_mult_apply(mk_ctx* ctx, const mk_mesh* m, Apply&& apply32, c
   MK_TRY(apply32(z, q));
   MK_COUNT(), k_tl_resid<<<gb, 256, 0, s>>>(L.n_nodes, L.d_boundary, dinv, r, q, rr, ld, N, kTLOmega, 0);
   MK_COUNT(), k_tl_restrict<<<nH * kTLS, 256, 0, s>>>(m->d_PT_off, m->d_PT_col, m->d_PT_val32, rr, ld, N, t);
-  MK_COUNT(), k_tl_coarse<<<(nH * 32 + 255) / 256, 256, 0, s>>>(nH, cinv, t, ld, N, y);
+  MK_COUNT(), k_tl_coarse<<<(nH + kTLRows - 1) / kTLRows, kTLRows * 32, (size_t)nH * kTLC * sizeof(float), s>>>(
+      nH, cinv, t, ld, N, y);
   MK_COUNT(), k_tl_prolong<<<gb, 256, 0, s>>>(L.n_nodes, m->d_P_off, m->d_P_col, m->d_P_val32, y, dinv,
                                               L.d_boundary, r, z, ld, N, 1);
   MK_TRY(apply32(z, q));
@@ -605,7 +614,8 @@ static int twolevel_apply(mk_ctx* ctx, const mk_mesh* m, const float* cinv, cons
   if (!t) return err;
   float* y = t + (size_t)kTLS * nH * ld;
   MK_COUNT(), k_tl_restrict<<<nH * kTLS, 256, 0, s>>>(m->d_PT_off, m->d_PT_col, m->d_PT_val32, r, ld, N, t);
-  MK_COUNT(), k_tl_coarse<<<(nH * 32 + 255) / 256, 256, 0, s>>>(nH, cinv, t, ld, N, y);
+  MK_COUNT(), k_tl_coarse<<<(nH + kTLRows - 1) / kTLRows, kTLRows * 32, (size_t)nH * kTLC * sizeof(float), s>>>(
+      nH, cinv, t, ld, N, y);
   MK_COUNT(), k_tl_prolong<<<(int)((L.n_nodes * N + 255) / 256), 256, 0, s>>>(
       L.n_nodes, m->d_P_off, m->d_P_col, m->d_P_val32, y, dinv, L.d_boundary, r, z, ld, N, add ? 1 : 0);
   MK_CUDA(cudaGetLastError());
@@ -639,184 +649,6 @@ __device__ __forceinline__ void block_partials(double (&acc)[NS], double* sh, in
   }
 }
 
-// r64 = b - Ax (interior rows), r32 = (float) r64, d32 = 0; partials of (b.b, r64.r64)
-__global__ void k_mixed_residual(int64_t n, const uint8_t* __restrict__ bnd, const double* __restrict__ b,
-                                 const double* __restrict__ Ax, float* __restrict__ r32, float* __restrict__ d32,
-                                 int N, int ld, double* __restrict__ part) {
-  __shared__ double sh[256];
-  double acc[2] = {0.0, 0.0};
-  const int rows = blockDim.x / ld;
-  const int j = threadIdx.x % ld, r = threadIdx.x / ld;
-  if (r < rows)
-    for (int64_t nd = (int64_t)blockIdx.x * rows + r; nd < n; nd += (int64_t)gridDim.x * rows) {
-      const int64_t t = nd * ld + j;
-      double rv = 0.0, bv = 0.0;
-      if (j < N && !bnd[nd]) {
-        bv = b[t];
-        rv = bv - Ax[t];
-      }
-      r32[t] = (float)rv;
-      d32[t] = 0.f;
-      acc[0] += bv * bv;
-      acc[1] += rv * rv;
-    }
-  block_partials<2>(acc, sh, ld, part, blockIdx.x);
-}
-
-// p = Dinv r; partials of (r.z, r.r)
-__global__ void k_mixed_init(int64_t n, const float* __restrict__ dinv, const float* __restrict__ r,
-                             float* __restrict__ p, int ld, double* __restrict__ part) {
-  __shared__ double sh[256];
-  double acc[2] = {0.0, 0.0};
-  const int rows = blockDim.x / ld;
-  const int j = threadIdx.x % ld, rr = threadIdx.x / ld;
-  if (rr < rows)
-    for (int64_t nd = (int64_t)blockIdx.x * rows + rr; nd < n; nd += (int64_t)gridDim.x * rows) {
-      const int64_t t = nd * ld + j;
-      const float rv = r[t];
-      const float z = rv * dinv[nd];
-      p[t] = z;
-      acc[0] += (double)rv * z;
-      acc[1] += (double)rv * rv;
-    }
-  block_partials<2>(acc, sh, ld, part, blockIdx.x);
-}
-
-// partial p.q (block bx of gx)
-__device__ __forceinline__ void mixed_pq_body(int bx, int gx, int64_t n, const float* __restrict__ p,
-                                              const float* __restrict__ q, int ld, double* __restrict__ part) {
-  __shared__ double sh[256];
-  double acc[1] = {0.0};
-  const int rows = blockDim.x / ld;
-  const int j = threadIdx.x % ld, rr = threadIdx.x / ld;
-  if (rr < rows)
-    for (int64_t nd = (int64_t)bx * rows + rr; nd < n; nd += (int64_t)gx * rows) {
-      const int64_t t = nd * ld + j;
-      acc[0] += (double)p[t] * q[t];
-    }
-  block_partials<1>(acc, sh, ld, part, bx);
-}
-__global__ void k_mixed_pq(int64_t n, const float* __restrict__ p, const float* __restrict__ q, int ld,
-                           double* __restrict__ part) {
-  mixed_pq_body(blockIdx.x, gridDim.x, n, p, q, ld, part);
-}
-
-// d += alpha p; r -= alpha q; partials of (r.z, r.r) with z = Dinv r (block bx of gx)
-__device__ __forceinline__ void mixed_update_body(int bx, int gx, int64_t n, const MixState* __restrict__ st,
-                                                  const float* __restrict__ dinv, const float* __restrict__ p,
-                                                  const float* __restrict__ q, float* __restrict__ d,
-                                                  float* __restrict__ r, int ld, double* __restrict__ part) {
-  __shared__ double sh[256];
-  double acc[2] = {0.0, 0.0};
-  const int rows = blockDim.x / ld;
-  const int j = threadIdx.x % ld, rr = threadIdx.x / ld;
-  const float a = rr < rows ? (float)st[j].alpha : 0.f;
-  if (rr < rows)
-    for (int64_t nd = (int64_t)bx * rows + rr; nd < n; nd += (int64_t)gx * rows) {
-      const int64_t t = nd * ld + j;
-      float rv = r[t];
-      if (a != 0.f) {
-        d[t] += a * p[t];
-        rv -= a * q[t];
-        r[t] = rv;
-      }
-      acc[0] += (double)rv * (rv * dinv[nd]);
-      acc[1] += (double)rv * rv;
-    }
-  block_partials<2>(acc, sh, ld, part, bx);
-}
-__global__ void k_mixed_update(int64_t n, const MixState* __restrict__ st, const float* __restrict__ dinv,
-                               const float* __restrict__ p, const float* __restrict__ q, float* __restrict__ d,
-                               float* __restrict__ r, int ld, double* __restrict__ part) {
-  mixed_update_body(blockIdx.x, gridDim.x, n, st, dinv, p, q, d, r, ld, part);
-}
-
-// p = Dinv r + beta p (active columns); item t = node * ld + column
-__device__ __forceinline__ void mixed_p_body(int64_t t, int64_t n, const MixState* __restrict__ st,
-                                             const float* __restrict__ dinv, const float* __restrict__ r,
-                                             float* __restrict__ p, int ld) {
-  if (t >= n * ld) return;
-  const int j = (int)(t % ld);
-  if (!st[j].active) return;
-  const int64_t nd = t / ld;
-  p[t] = r[t] * dinv[nd] + (float)st[j].beta * p[t];
-}
-__global__ void k_mixed_p(int64_t n, const MixState* __restrict__ st, const float* __restrict__ dinv,
-                          const float* __restrict__ r, float* __restrict__ p, int ld) {
-  mixed_p_body((int64_t)blockIdx.x * blockDim.x + threadIdx.x, n, st, dinv, r, p, ld);
-}
-
-// FCG(1): partials of (p.q, p.r)
-__global__ void k_fcg_pq(int64_t n, const float* __restrict__ p, const float* __restrict__ q,
-                         const float* __restrict__ r, int ld, double* __restrict__ part) {
-  __shared__ double sh[256];
-  double acc[2] = {0.0, 0.0};
-  const int rows = blockDim.x / ld;
-  const int j = threadIdx.x % ld, rr = threadIdx.x / ld;
-  if (rr < rows)
-    for (int64_t nd = (int64_t)blockIdx.x * rows + rr; nd < n; nd += (int64_t)gridDim.x * rows) {
-      const int64_t t = nd * ld + j;
-      acc[0] += (double)p[t] * q[t];
-      acc[1] += (double)p[t] * r[t];
-    }
-  block_partials<2>(acc, sh, ld, part, blockIdx.x);
-}
-
-// FCG(1): d += alpha p; r -= alpha q; partial r.r
-__global__ void k_fcg_update(int64_t n, const MixState* __restrict__ st, const float* __restrict__ p,
-                             const float* __restrict__ q, float* __restrict__ d, float* __restrict__ r, int ld,
-                             double* __restrict__ part) {
-  __shared__ double sh[256];
-  double acc[1] = {0.0};
-  const int rows = blockDim.x / ld;
-  const int j = threadIdx.x % ld, rr = threadIdx.x / ld;
-  const float a = rr < rows ? (float)st[j].alpha : 0.f;
-  if (rr < rows)
-    for (int64_t nd = (int64_t)blockIdx.x * rows + rr; nd < n; nd += (int64_t)gridDim.x * rows) {
-      const int64_t t = nd * ld + j;
-      float rv = r[t];
-      if (a != 0.f) {
-        d[t] += a * p[t];
-        rv -= a * q[t];
-        r[t] = rv;
-      }
-      acc[0] += (double)rv * rv;
-    }
-  block_partials<1>(acc, sh, ld, part, blockIdx.x);
-}
-
-// FCG(1): p = z + beta p (active columns)
-__global__ void k_fcg_p(int64_t n, const MixState* __restrict__ st, const float* __restrict__ z,
-                        float* __restrict__ p, int ld) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n * ld) return;
-  const int j = (int)(t % ld);
-  if (!st[j].active) return;
-  p[t] = z[t] + (float)st[j].beta * p[t];
-}
-
-__global__ void k_mixed_add(int64_t n, const float* __restrict__ d, double* __restrict__ x, int N, int ld) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n * ld) return;
-  if ((int)(t % ld) < N) x[t] += (double)d[t];
-}
-
-__global__ void k_dinv32(int64_t n, const double* __restrict__ diag, float* __restrict__ dinv) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dinv[i] = (float)(1.0 / diag[i]);
-}
-
-int diag_inverse32(int64_t n, const double* diag, float* dinv, cudaStream_t s) {
-  MK_COUNT(), k_dinv32<<<(int)((n + 255) / 256), 256, 0, s>>>(n, diag, dinv);
-  MK_CUDA(cudaGetLastError());
-  return MK_OK;
-}
-
-__global__ void k_zero_boundary(int64_t n, const uint8_t* __restrict__ bnd, double* __restrict__ x, int ld) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n * ld && bnd[t / ld]) x[t] = 0.0;
-}
-
 // Finalisers: one block of ld threads, sums partials in block order.
 // mode 0: outer residual (bb, rr64) -> bn, rr64, outer_active
 // mode 1: inner init (rz, rr) -> rz, rr0, rr, active (outer_active), iters=0
@@ -834,7 +666,7 @@ __device__ __forceinline__ void finalize_body(int mode, const double* __restrict
   for (int pr = warp; pr < NS * ld; pr += nw) {
     const int k = pr / ld, jj = pr - k * ld;
     double v = 0.0;
-    for (int b = lane; b < nblk; b += 32) v += part[(int64_t)b * NS * ld + k * ld + jj];
+    for (int b = lane; b < nblk; b += 32) v += __ldcg(&part[(int64_t)b * NS * ld + k * ld + jj]);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
     if (lane == 0) sums[k * ld + jj] = v;
@@ -912,6 +744,212 @@ __global__ void __launch_bounds__(kFinThreads) k_mixed_finalize(int mode, const 
                                                                int NS, int ld, int N, MixState* __restrict__ st,
                                                                double rtol, double inner_rtol2) {
   finalize_body(mode, part, nblk, NS, ld, N, st, rtol, inner_rtol2);
+}
+
+
+// Finalisation fused into the kernel that produced the partials: each block publishes its partials, then the last
+// block of the grid to arrive (an atomic counter) folds them in block order exactly as k_mixed_finalize would and
+// resets the counter for the next launch.  ctr == nullptr: no finalisation here (a separate launch does it).
+struct FinArgs {
+  int* ctr;
+  int mode, NS, N;
+  MixState* st;
+  double rtol, inner2;
+};
+__device__ __forceinline__ void finalize_if_last(const FinArgs& f, const double* __restrict__ part, int ld) {
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(f.ctr, 1) == (int)gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x == 0) *f.ctr = 0;
+  finalize_body(f.mode, part, (int)gridDim.x, f.NS, ld, f.N, f.st, f.rtol, f.inner2);
+}
+
+// r64 = b - Ax (interior rows), r32 = (float) r64, d32 = 0; partials of (b.b, r64.r64)
+__global__ void k_mixed_residual(int64_t n, const uint8_t* __restrict__ bnd, const double* __restrict__ b,
+                                 const double* __restrict__ Ax, float* __restrict__ r32, float* __restrict__ d32,
+                                 int N, int ld, double* __restrict__ part, FinArgs fin) {
+  __shared__ double sh[256];
+  double acc[2] = {0.0, 0.0};
+  const int rows = blockDim.x / ld;
+  const int j = threadIdx.x % ld, r = threadIdx.x / ld;
+  if (r < rows)
+    for (int64_t nd = (int64_t)blockIdx.x * rows + r; nd < n; nd += (int64_t)gridDim.x * rows) {
+      const int64_t t = nd * ld + j;
+      double rv = 0.0, bv = 0.0;
+      if (j < N && !bnd[nd]) {
+        bv = b[t];
+        rv = bv - Ax[t];
+      }
+      r32[t] = (float)rv;
+      d32[t] = 0.f;
+      acc[0] += bv * bv;
+      acc[1] += rv * rv;
+    }
+  block_partials<2>(acc, sh, ld, part, blockIdx.x);
+  if (fin.ctr) finalize_if_last(fin, part, ld);
+}
+
+// p = Dinv r; partials of (r.z, r.r)
+__global__ void k_mixed_init(int64_t n, const float* __restrict__ dinv, const float* __restrict__ r,
+                             float* __restrict__ p, int ld, double* __restrict__ part, FinArgs fin) {
+  __shared__ double sh[256];
+  double acc[2] = {0.0, 0.0};
+  const int rows = blockDim.x / ld;
+  const int j = threadIdx.x % ld, rr = threadIdx.x / ld;
+  if (rr < rows)
+    for (int64_t nd = (int64_t)blockIdx.x * rows + rr; nd < n; nd += (int64_t)gridDim.x * rows) {
+      const int64_t t = nd * ld + j;
+      const float rv = r[t];
+      const float z = rv * dinv[nd];
+      p[t] = z;
+      acc[0] += (double)rv * z;
+      acc[1] += (double)rv * rv;
+    }
+  block_partials<2>(acc, sh, ld, part, blockIdx.x);
+  if (fin.ctr) finalize_if_last(fin, part, ld);
+}
+
+// partial p.q (block bx of gx)
+__device__ __forceinline__ void mixed_pq_body(int bx, int gx, int64_t n, const float* __restrict__ p,
+                                              const float* __restrict__ q, int ld, double* __restrict__ part) {
+  __shared__ double sh[256];
+  double acc[1] = {0.0};
+  const int rows = blockDim.x / ld;
+  const int j = threadIdx.x % ld, rr = threadIdx.x / ld;
+  if (rr < rows)
+    for (int64_t nd = (int64_t)bx * rows + rr; nd < n; nd += (int64_t)gx * rows) {
+      const int64_t t = nd * ld + j;
+      acc[0] += (double)p[t] * q[t];
+    }
+  block_partials<1>(acc, sh, ld, part, bx);
+}
+__global__ void k_mixed_pq(int64_t n, const float* __restrict__ p, const float* __restrict__ q, int ld,
+                           double* __restrict__ part, FinArgs fin) {
+  mixed_pq_body(blockIdx.x, gridDim.x, n, p, q, ld, part);
+  if (fin.ctr) finalize_if_last(fin, part, ld);
+}
+
+// d += alpha p; r -= alpha q; partials of (r.z, r.r) with z = Dinv r (block bx of gx)
+__device__ __forceinline__ void mixed_update_body(int bx, int gx, int64_t n, const MixState* __restrict__ st,
+                                                  const float* __restrict__ dinv, const float* __restrict__ p,
+                                                  const float* __restrict__ q, float* __restrict__ d,
+                                                  float* __restrict__ r, int ld, double* __restrict__ part) {
+  __shared__ double sh[256];
+  double acc[2] = {0.0, 0.0};
+  const int rows = blockDim.x / ld;
+  const int j = threadIdx.x % ld, rr = threadIdx.x / ld;
+  const float a = rr < rows ? (float)st[j].alpha : 0.f;
+  if (rr < rows)
+    for (int64_t nd = (int64_t)bx * rows + rr; nd < n; nd += (int64_t)gx * rows) {
+      const int64_t t = nd * ld + j;
+      float rv = r[t];
+      if (a != 0.f) {
+        d[t] += a * p[t];
+        rv -= a * q[t];
+        r[t] = rv;
+      }
+      acc[0] += (double)rv * (rv * dinv[nd]);
+      acc[1] += (double)rv * rv;
+    }
+  block_partials<2>(acc, sh, ld, part, bx);
+}
+__global__ void k_mixed_update(int64_t n, const MixState* __restrict__ st, const float* __restrict__ dinv,
+                               const float* __restrict__ p, const float* __restrict__ q, float* __restrict__ d,
+                               float* __restrict__ r, int ld, double* __restrict__ part, FinArgs fin) {
+  mixed_update_body(blockIdx.x, gridDim.x, n, st, dinv, p, q, d, r, ld, part);
+  if (fin.ctr) finalize_if_last(fin, part, ld);
+}
+
+// p = Dinv r + beta p (active columns); item t = node * ld + column
+__device__ __forceinline__ void mixed_p_body(int64_t t, int64_t n, const MixState* __restrict__ st,
+                                             const float* __restrict__ dinv, const float* __restrict__ r,
+                                             float* __restrict__ p, int ld) {
+  if (t >= n * ld) return;
+  const int j = (int)(t % ld);
+  if (!st[j].active) return;
+  const int64_t nd = t / ld;
+  p[t] = r[t] * dinv[nd] + (float)st[j].beta * p[t];
+}
+__global__ void k_mixed_p(int64_t n, const MixState* __restrict__ st, const float* __restrict__ dinv,
+                          const float* __restrict__ r, float* __restrict__ p, int ld) {
+  mixed_p_body((int64_t)blockIdx.x * blockDim.x + threadIdx.x, n, st, dinv, r, p, ld);
+}
+
+// FCG(1): partials of (p.q, p.r)
+__global__ void k_fcg_pq(int64_t n, const float* __restrict__ p, const float* __restrict__ q,
+                         const float* __restrict__ r, int ld, double* __restrict__ part, FinArgs fin) {
+  __shared__ double sh[256];
+  double acc[2] = {0.0, 0.0};
+  const int rows = blockDim.x / ld;
+  const int j = threadIdx.x % ld, rr = threadIdx.x / ld;
+  if (rr < rows)
+    for (int64_t nd = (int64_t)blockIdx.x * rows + rr; nd < n; nd += (int64_t)gridDim.x * rows) {
+      const int64_t t = nd * ld + j;
+      acc[0] += (double)p[t] * q[t];
+      acc[1] += (double)p[t] * r[t];
+    }
+  block_partials<2>(acc, sh, ld, part, blockIdx.x);
+  if (fin.ctr) finalize_if_last(fin, part, ld);
+}
+
+// FCG(1): d += alpha p; r -= alpha q; partial r.r
+__global__ void k_fcg_update(int64_t n, const MixState* __restrict__ st, const float* __restrict__ p,
+                             const float* __restrict__ q, float* __restrict__ d, float* __restrict__ r, int ld,
+                             double* __restrict__ part, FinArgs fin) {
+  __shared__ double sh[256];
+  double acc[1] = {0.0};
+  const int rows = blockDim.x / ld;
+  const int j = threadIdx.x % ld, rr = threadIdx.x / ld;
+  const float a = rr < rows ? (float)st[j].alpha : 0.f;
+  if (rr < rows)
+    for (int64_t nd = (int64_t)blockIdx.x * rows + rr; nd < n; nd += (int64_t)gridDim.x * rows) {
+      const int64_t t = nd * ld + j;
+      float rv = r[t];
+      if (a != 0.f) {
+        d[t] += a * p[t];
+        rv -= a * q[t];
+        r[t] = rv;
+      }
+      acc[0] += (double)rv * rv;
+    }
+  block_partials<1>(acc, sh, ld, part, blockIdx.x);
+  if (fin.ctr) finalize_if_last(fin, part, ld);
+}
+
+// FCG(1): p = z + beta p (active columns)
+__global__ void k_fcg_p(int64_t n, const MixState* __restrict__ st, const float* __restrict__ z,
+                        float* __restrict__ p, int ld) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * ld) return;
+  const int j = (int)(t % ld);
+  if (!st[j].active) return;
+  p[t] = z[t] + (float)st[j].beta * p[t];
+}
+
+__global__ void k_mixed_add(int64_t n, const float* __restrict__ d, double* __restrict__ x, int N, int ld) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * ld) return;
+  if ((int)(t % ld) < N) x[t] += (double)d[t];
+}
+
+__global__ void k_dinv32(int64_t n, const double* __restrict__ diag, float* __restrict__ dinv) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dinv[i] = (float)(1.0 / diag[i]);
+}
+
+int diag_inverse32(int64_t n, const double* diag, float* dinv, cudaStream_t s) {
+  MK_COUNT(), k_dinv32<<<(int)((n + 255) / 256), 256, 0, s>>>(n, diag, dinv);
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
+__global__ void k_zero_boundary(int64_t n, const uint8_t* __restrict__ bnd, double* __restrict__ x, int ld) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n * ld && bnd[t / ld]) x[t] = 0.0;
 }
 
 int pcg_mixed(mk_ctx* ctx, const mk_mesh* m, const double* A64, const double* b, double* x, int ld, int N,
@@ -1017,6 +1055,11 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
   const int gb = (int)((n * ld + 255) / 256);
   const int check = std::max(1, o.check_every);
   const double inner2 = o.inner_rtol * o.inner_rtol;
+  // the finalisation of each reduction runs in the last block of the kernel that produced the partials
+  int* fin_ctr = (int*)scratch(ctx, S_FINCTR, 64, &err);
+  if (!fin_ctr) return err;
+  MK_CUDA(cudaMemsetAsync(fin_ctr, 0, sizeof(int), s));
+  auto fin = [&](int mode, int NS) { return FinArgs{fin_ctr, mode, NS, N, st, o.rtol, inner2}; };
   int total_it = 0, refine = 0, status = MK_OK;
   bool converged = false;
   const int max_refine = o.max_refine > 0 ? o.max_refine : 20;
@@ -1036,8 +1079,7 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
   }
   for (;;) {
     MK_TRY(apply_patch<double>(ctx, m, A64p, x, Ax, ld, true, s));  // FP64 residual of the current x
-    MK_COUNT(), k_mixed_residual<<<nblk, th, 0, s>>>(n, L.d_boundary, b, Ax, r, d, N, ld, part);
-    MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(0, part, nblk, 2, ld, N, st, o.rtol, inner2);
+    MK_COUNT(), k_mixed_residual<<<nblk, th, 0, s>>>(n, L.d_boundary, b, Ax, r, d, N, ld, part, fin(0, 2));
     MK_CUDA(cudaMemcpyAsync(hst, st, sizeof(MixState) * ld, cudaMemcpyDeviceToHost, s));
     MK_CUDA(cudaStreamSynchronize(s));
     bool any = false;
@@ -1056,11 +1098,9 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
     if (fcg) {
       MK_TRY(precond());
       MK_CUDA(cudaMemcpyAsync(p, zb, (size_t)n * ld * sizeof(float), cudaMemcpyDeviceToDevice, s));
-      MK_COUNT(), k_mixed_pq<<<nblk, th, 0, s>>>(n, r, r, ld, part);
-      MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(7, part, nblk, 1, ld, N, st, o.rtol, inner2);
+      MK_COUNT(), k_mixed_pq<<<nblk, th, 0, s>>>(n, r, r, ld, part, fin(7, 1));
     } else {
-      MK_COUNT(), k_mixed_init<<<nblk, th, 0, s>>>(n, dinv, r, p, ld, part);
-      MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(1, part, nblk, 2, ld, N, st, o.rtol, inner2);
+      MK_COUNT(), k_mixed_init<<<nblk, th, 0, s>>>(n, dinv, r, p, ld, part, fin(1, 2));
     }
     int it = 0;
     bool inner_active = true;
@@ -1069,20 +1109,15 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
     auto iteration = [&]() -> int {
       MK_TRY(apply32(p, q));
       if (fcg) {
-        MK_COUNT(), k_fcg_pq<<<nblk, th, 0, s>>>(n, p, q, r, ld, part);
-        MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(4, part, nblk, 2, ld, N, st, o.rtol, inner2);
-        MK_COUNT(), k_fcg_update<<<nblk, th, 0, s>>>(n, st, p, q, d, r, ld, part);
-        MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(5, part, nblk, 1, ld, N, st, o.rtol, inner2);
+        MK_COUNT(), k_fcg_pq<<<nblk, th, 0, s>>>(n, p, q, r, ld, part, fin(4, 2));
+        MK_COUNT(), k_fcg_update<<<nblk, th, 0, s>>>(n, st, p, q, d, r, ld, part, fin(5, 1));
         MK_TRY(precond());
-        MK_COUNT(), k_mixed_pq<<<nblk, th, 0, s>>>(n, zb, q, ld, part);
-        MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(6, part, nblk, 1, ld, N, st, o.rtol, inner2);
+        MK_COUNT(), k_mixed_pq<<<nblk, th, 0, s>>>(n, zb, q, ld, part, fin(6, 1));
         MK_COUNT(), k_fcg_p<<<gb, 256, 0, s>>>(n, st, zb, p, ld);
         return MK_OK;
       }
-      MK_COUNT(), k_mixed_pq<<<nblk, th, 0, s>>>(n, p, q, ld, part);
-      MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(2, part, nblk, 1, ld, N, st, o.rtol, inner2);
-      MK_COUNT(), k_mixed_update<<<nblk, th, 0, s>>>(n, st, dinv, p, q, d, r, ld, part);
-      MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(3, part, nblk, 2, ld, N, st, o.rtol, inner2);
+      MK_COUNT(), k_mixed_pq<<<nblk, th, 0, s>>>(n, p, q, ld, part, fin(2, 1));
+      MK_COUNT(), k_mixed_update<<<nblk, th, 0, s>>>(n, st, dinv, p, q, d, r, ld, part, fin(3, 2));
       MK_COUNT(), k_mixed_p<<<gb, 256, 0, s>>>(n, st, dinv, r, p, ld);
       return MK_OK;
     };
@@ -1423,7 +1458,7 @@ extern "C" int mk_batch_correction_solve(mk_ctx* ctx, int K, const mk_mesh* cons
       MK_TRY(apply64(ctx, meshes[k], (const double*)(ws + oA64[k]), x[k], (double*)(ws + oAx[k]), ld[k], ld[k], true,
                      s));
       MK_COUNT(), k_mixed_residual<<<nblk, 256, 0, s>>>(B.n, B.bnd, rhs[k], (const double*)(ws + oAx[k]), B.r, B.d,
-                                                         N[k], ld[k], B.part);
+                                                         N[k], ld[k], B.part, FinArgs{});
       MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(0, B.part, nblk, 2, ld[k], N[k], B.st, o.rtol, inner2);
     }
     MK_CUDA(cudaMemcpyAsync(hst, dst, (size_t)K * 16 * sizeof(MixState), cudaMemcpyDeviceToHost, s));
@@ -1439,7 +1474,7 @@ extern "C" int mk_batch_correction_solve(mk_ctx* ctx, int K, const mk_mesh* cons
     for (int k = 0; k < K; ++k) {
       const BatchProb& B = hp[k];
       if (!conv[k]) refines[k] += 1;
-      MK_COUNT(), k_mixed_init<<<nblk, 256, 0, s>>>(B.n, B.dinv, B.r, B.p, ld[k], B.part);
+      MK_COUNT(), k_mixed_init<<<nblk, 256, 0, s>>>(B.n, B.dinv, B.r, B.p, ld[k], B.part, FinArgs{});
       MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(1, B.part, nblk, 2, ld[k], N[k], B.st, o.rtol, inner2);
     }
     bool inner_active = true;
