@@ -79,58 +79,64 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// Four 8 x 8 BF16 matrices from shared memory (ldmatrix): lanes 8m .. 8m + 7 give the row addresses of matrix m,
+// and register m of lane l receives row l / 4, columns 2 (l % 4) and + 1 of matrix m.
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const __nv_bfloat16* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_u32(p)));
+}
+
 // The network on 16 rows by one warp.  Xs: 16 x kS1 BF16 inputs (columns >= n_in zero); W1b/W2b/W3b: BF16
-// weights [out][in] with row strides kS1/kS2/kS2 halves; bias: FP32 b1 | b2 | b3 (zero padded to 16).
+// weights [out][in] with row strides kS1/kS2/kS2 halves (16-byte rows: every ldmatrix row address is aligned, and
+// the strides put the eight rows of a matrix in distinct bank groups); bias: FP32 b1 | b2 | b3 (zero padded to 16).
 // Fragment layout of m16n8k16 (g = lane / 4, t = lane % 4): A holds (row g | g+8, cols 2t, 2t+1 | 2t+8, 2t+9),
-// B holds (k = 2t, 2t+1 | 2t+8, 2t+9; n = g), C holds (row g | g+8, cols 2t, 2t+1).  The C tiles of two
-// neighbouring n-blocks are exactly the A fragment of the next layer's k-block, so hidden activations stay in
-// registers.  out[nt][0..1]: row g, outputs nt*8 + 2t + {0,1}; out[nt][2..3]: row g + 8.
+// B holds (k = 2t, 2t+1 | 2t+8, 2t+9; n = g), C holds (row g | g+8, cols 2t, 2t+1).  A comes from the input tile by
+// ldmatrix (matrices: rows 0-7 / 8-15 x k 0-7 / 8-15 of a k-step), B from the weights by ldmatrix (rows n of an
+// n-tile x consecutive 8-wide k blocks).  The C tiles of two neighbouring n-blocks are exactly the A fragment of
+// the next layer's k-block, so hidden activations stay in registers.  out[nt][0..1]: row g, outputs
+// nt*8 + 2t + {0,1}; out[nt][2..3]: row g + 8.
 __device__ __forceinline__ void mlp_tile_bf16(const __nv_bfloat16* __restrict__ Xs,
                                               const __nv_bfloat16* __restrict__ W1b,
                                               const __nv_bfloat16* __restrict__ W2b,
                                               const __nv_bfloat16* __restrict__ W3b,
                                               const float* __restrict__ bias, float (&out)[2][4]) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  constexpr int s1 = kS1 / 2, s2 = kS2 / 2;  // strides in 32-bit words
-  const uint32_t* X32 = reinterpret_cast<const uint32_t*>(Xs);
-  const uint32_t* W1w = reinterpret_cast<const uint32_t*>(W1b);
-  const uint32_t* W2w = reinterpret_cast<const uint32_t*>(W2b);
-  const uint32_t* W3w = reinterpret_cast<const uint32_t*>(W3b);
+  const int lane = threadIdx.x & 31, r8 = lane & 7, mm = lane >> 3, t = lane & 3;
   uint32_t a1[2][4];
 #pragma unroll
-  for (int ks = 0; ks < 2; ++ks) {
-    a1[ks][0] = X32[g * s1 + ks * 8 + t];
-    a1[ks][1] = X32[(g + 8) * s1 + ks * 8 + t];
-    a1[ks][2] = X32[g * s1 + ks * 8 + 4 + t];
-    a1[ks][3] = X32[(g + 8) * s1 + ks * 8 + 4 + t];
-  }
+  for (int ks = 0; ks < 2; ++ks) ldsm_x4(a1[ks], Xs + (r8 + 8 * (mm & 1)) * kS1 + 16 * ks + 8 * (mm >> 1));
   uint32_t h1[4][4], h2[4][4];
 #pragma unroll
   for (int nt = 0; nt < 8; ++nt) {
+    uint32_t b[4];
+    ldsm_x4(b, W1b + (nt * 8 + r8) * kS1 + 8 * mm);  // k blocks 0, 8, 16, 24
     float c[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int ks = 0; ks < 2; ++ks)
-      mma_bf16(c, a1[ks], W1w[(nt * 8 + g) * s1 + ks * 8 + t], W1w[(nt * 8 + g) * s1 + ks * 8 + 4 + t]);
+    mma_bf16(c, a1[0], b[0], b[1]);
+    mma_bf16(c, a1[1], b[2], b[3]);
     const float b0 = bias[nt * 8 + 2 * t], b1 = bias[nt * 8 + 2 * t + 1];
     h1[nt >> 1][(nt & 1) * 2 + 0] = pack_bf16(fmaxf(c[0] + b0, 0.f), fmaxf(c[1] + b1, 0.f));
     h1[nt >> 1][(nt & 1) * 2 + 1] = pack_bf16(fmaxf(c[2] + b0, 0.f), fmaxf(c[3] + b1, 0.f));
   }
 #pragma unroll
   for (int nt = 0; nt < 8; ++nt) {
+    uint32_t b[2][4];
+    ldsm_x4(b[0], W2b + (nt * 8 + r8) * kS2 + 8 * mm);       // k blocks 0, 8, 16, 24
+    ldsm_x4(b[1], W2b + (nt * 8 + r8) * kS2 + 32 + 8 * mm);  // k blocks 32, 40, 48, 56
     float c[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int kk = 0; kk < 4; ++kk)
-      mma_bf16(c, h1[kk], W2w[(nt * 8 + g) * s2 + kk * 8 + t], W2w[(nt * 8 + g) * s2 + kk * 8 + 4 + t]);
+    for (int kk = 0; kk < 4; ++kk) mma_bf16(c, h1[kk], b[kk >> 1][(kk & 1) * 2], b[kk >> 1][(kk & 1) * 2 + 1]);
     const float b0 = bias[kNH + nt * 8 + 2 * t], b1 = bias[kNH + nt * 8 + 2 * t + 1];
     h2[nt >> 1][(nt & 1) * 2 + 0] = pack_bf16(fmaxf(c[0] + b0, 0.f), fmaxf(c[1] + b1, 0.f));
     h2[nt >> 1][(nt & 1) * 2 + 1] = pack_bf16(fmaxf(c[2] + b0, 0.f), fmaxf(c[3] + b1, 0.f));
   }
 #pragma unroll
   for (int nt = 0; nt < 2; ++nt) {
+    uint32_t b[2][4];
+    ldsm_x4(b[0], W3b + (nt * 8 + r8) * kS2 + 8 * mm);
+    ldsm_x4(b[1], W3b + (nt * 8 + r8) * kS2 + 32 + 8 * mm);
     float c[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int kk = 0; kk < 4; ++kk)
-      mma_bf16(c, h2[kk], W3w[(nt * 8 + g) * s2 + kk * 8 + t], W3w[(nt * 8 + g) * s2 + kk * 8 + 4 + t]);
+    for (int kk = 0; kk < 4; ++kk) mma_bf16(c, h2[kk], b[kk >> 1][(kk & 1) * 2], b[kk >> 1][(kk & 1) * 2 + 1]);
     const float b0 = bias[2 * kNH + nt * 8 + 2 * t], b1 = bias[2 * kNH + nt * 8 + 2 * t + 1];
     out[nt][0] = c[0] + b0;
     out[nt][1] = c[1] + b1;
@@ -247,7 +253,7 @@ __host__ __device__ inline LearnSmem learn_smem(int nloc, int pe, int max_nodes,
 // in fixed order, then z = sum / multiplicity + r / diag (owned nodes) or the partial sum to the node's halo
 // slot (shared nodes, finished by k_learned_halo).  Columns [col0, col0 + Nw), Nw = min(kLW, N - col0).
 template <int NLOC, bool TC>
-__global__ void __launch_bounds__(256) k_learned_patch(
+__global__ void __launch_bounds__(256, 2) k_learned_patch(
     const int32_t* __restrict__ elem_off, const int32_t* __restrict__ node_off, const uint16_t* __restrict__ lconn,
     const int32_t* __restrict__ node_gid, const int32_t* __restrict__ target, const int32_t* __restrict__ inc_off,
     const uint16_t* __restrict__ inc,
