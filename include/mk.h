@@ -174,10 +174,17 @@ int mk_prolongate(mk_ctx* ctx, const mk_mesh* mesh, const double* psiH, int ldc,
  * 4 pi (rho_H, v) for all free v with rho_H(x) = sum_i occ[i] u_i(x)^2 evaluated at the quadrature points.
  * bc = MK_BC_MULTIPOLE: boundary values from the multipole expansion of int rho(y)/|x-y| dy about the origin
  * through l = 2 (Remark after Algorithm 3); MK_BC_ZERO: w = 0 on the boundary.
- * u [n_nodes*ld] device, occ [N] host, w [n_nodes] device output (boundary values included).  The report is
+ * u [n_nodes*ld] device, occ [N] host, w [n_nodes] device output (boundary values included).  rho_q: rho_H at
+ * the quadrature points as mk_density writes it for the same u and occ, or NULL (computed here).  The report is
  * filled (stream synchronised).  Errors: MK_ERR_NOT_CONVERGED, MK_ERR_BREAKDOWN, MK_ERR_INVALID_ARG. */
-int mk_hartree_poisson(mk_ctx* ctx, const mk_mesh* mesh, const double* u, int ld, const double* occ, int N, int bc,
-                       double* w, const mk_solve_opts* opts, mk_solve_report* report, void* stream);
+int mk_hartree_poisson(mk_ctx* ctx, const mk_mesh* mesh, const double* u, int ld, const double* occ, int N,
+                       const double* rho_q, int bc, double* w, const mk_solve_opts* opts, mk_solve_report* report,
+                       void* stream);
+/* rho_H = sum_i occ[i] u_i^2 at the quadrature points of every fine element, rho_q [n_elems * n_quad] device
+ * (element order of the upload; n_quad from mk_mesh_info), FP64; u [n_nodes*ld] device, occ [N] host.  Computed
+ * once per step, it serves mk_hartree_poisson and mk_frozen_potential (both evaluate the same rho_H). */
+int mk_density(mk_ctx* ctx, const mk_mesh* mesh, const double* u, int ld, const double* occ, int N, double* rho_q,
+               void* stream);
 
 /* ---------------------------------------------------------------------------------------------- A3 */
 /* Right-hand sides of the correction problems (Eq. (Aux_Linear_Problem) with V_Hxc(rho_H) moved to the right):
@@ -190,9 +197,10 @@ int mk_assemble_rhs(mk_ctx* ctx, const mk_mesh* mesh, const double* u, int ld, c
                     void* stream);
 /* The two halves of mk_assemble_rhs, so that the coarse pencil (which needs vq, not rhs) can start on another
  * stream as soon as vq exists.  mk_frozen_potential: rho_H = sum_i occ[i] u_i^2 and vq = w + V_xc(rho_H) at the
- * quadrature points [n_elems * n_quad].  mk_assemble_rhs_from_vq: rhs from u and that vq (as mk_assemble_rhs). */
+ * quadrature points [n_elems * n_quad] (rho_q as for mk_hartree_poisson, or NULL).  mk_assemble_rhs_from_vq: rhs
+ * from u and that vq (as mk_assemble_rhs). */
 int mk_frozen_potential(mk_ctx* ctx, const mk_mesh* mesh, const double* u, int ld, const double* occ, int N,
-                        const double* w, mk_xc xc, double* vq, void* stream);
+                        const double* rho_q, const double* w, mk_xc xc, double* vq, void* stream);
 int mk_assemble_rhs_from_vq(mk_ctx* ctx, const mk_mesh* mesh, const double* u, int ld, const double* lambdaH, int N,
                             const double* vq, double sigma, double* rhs, void* stream);
 

@@ -279,8 +279,19 @@ int mk_prolongate(mk_ctx* ctx, const mk_mesh* m, const double* psiH, int ldc, in
   return prolongate(ctx, m, psiH, ldc, N, u, ld, (cudaStream_t)stream);
 }
 
-int mk_hartree_poisson(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, const double* occ, int N, int bc,
-                       double* w, const mk_solve_opts* opts, mk_solve_report* report, void* stream) {
+int mk_density(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, const double* occ, int N, double* rho_q,
+               void* stream) {
+  MK_ARG(ctx && m && u && occ && rho_q, "mk_density: null argument");
+  MK_ARG(N >= 1 && N <= ld && N <= MK_MAX_RHS, "mk_density: bad N/ld");
+  MK_CUDA(cudaSetDevice(ctx->device));
+  MK_TRY(density(ctx, m->fine, u, ld, N, occ, rho_q, (cudaStream_t)stream));
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
+int mk_hartree_poisson(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, const double* occ, int N,
+                       const double* rho_q, int bc, double* w, const mk_solve_opts* opts, mk_solve_report* report,
+                       void* stream) {
   MK_ARG(ctx && m && u && occ && w, "mk_hartree_poisson: null argument");
   MK_ARG(N >= 1 && N <= ld && N <= MK_MAX_RHS, "mk_hartree_poisson: bad N/ld");
   MK_ARG(bc == MK_BC_ZERO || bc == MK_BC_MULTIPOLE, "mk_hartree_poisson: bad bc");
@@ -289,7 +300,8 @@ int mk_hartree_poisson(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, c
   cudaStream_t s = (cudaStream_t)stream;
   const Level& L = m->fine;
   int err = MK_OK;
-  double* rho = (double*)scratch(ctx, S_RHO, (size_t)L.n_elems * kQ * sizeof(double), &err);
+  double* rho_own = rho_q ? nullptr : (double*)scratch(ctx, S_RHO, (size_t)L.n_elems * kQ * sizeof(double), &err);
+  const double* rho = rho_q ? rho_q : rho_own;
   double* F = (double*)scratch(ctx, S_VEC1, L.n_nodes * sizeof(double), &err);
   double* y = (double*)scratch(ctx, S_VEC2, L.n_nodes * sizeof(double), &err);
   double* d = (double*)scratch(ctx, S_VEC3, L.n_nodes * sizeof(double), &err);
@@ -307,7 +319,7 @@ int mk_hartree_poisson(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, c
   }
   const double* Ke = m->d_K64;
   MK_CUDA(cudaMemcpyAsync(diag, m->d_K64diag, L.n_nodes * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  MK_TRY(density(ctx, L, u, ld, N, occ, rho, s));
+  if (!rho_q) MK_TRY(density(ctx, L, u, ld, N, occ, rho_own, s));
   MK_TRY(load_vector(ctx, L, rho, 4.0 * M_PI, F, s));
   MK_TRY(multipole_boundary(ctx, L, rho, L.d_nodes, bc, w, s));
   MK_TRY(apply64(ctx, m, Ke, w, y, 1, 1, true, s));                     // K_IB g (interior rows)
@@ -330,7 +342,7 @@ int mk_hartree_poisson(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, c
 }
 
 int mk_frozen_potential(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, const double* occ, int N,
-                        const double* w, mk_xc xc, double* vq, void* stream) {
+                        const double* rho_q, const double* w, mk_xc xc, double* vq, void* stream) {
   MK_ARG(ctx && m && u && occ && w && vq, "mk_frozen_potential: null argument");
   MK_ARG(N >= 1 && N <= ld && N <= MK_MAX_RHS, "mk_frozen_potential: bad N/ld");
   MK_ARG(xc.kind >= MK_XC_NONE && xc.kind <= MK_XC_LDA_PZ, "mk_frozen_potential: bad xc");
@@ -338,9 +350,13 @@ int mk_frozen_potential(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, 
   cudaStream_t s = (cudaStream_t)stream;
   const Level& L = m->fine;
   int err = MK_OK;
-  double* rho = (double*)scratch(ctx, S_RHO, (size_t)L.n_elems * kQ * sizeof(double), &err);
-  if (!rho) return err;
-  MK_TRY(density(ctx, L, u, ld, N, occ, rho, s));
+  const double* rho = rho_q;
+  if (!rho) {
+    double* own = (double*)scratch(ctx, S_RHO, (size_t)L.n_elems * kQ * sizeof(double), &err);
+    if (!own) return err;
+    MK_TRY(density(ctx, L, u, ld, N, occ, own, s));
+    rho = own;
+  }
   MK_TRY(frozen_potential(ctx, L, w, rho, xc, vq, s));
   MK_CUDA(cudaGetLastError());
   return MK_OK;
@@ -375,7 +391,7 @@ int mk_assemble_rhs(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, cons
                     const double* occ, int N, const double* w, double sigma, mk_xc xc, double* rhs, double* vq,
                     void* stream) {
   MK_ARG(ctx && m && u && lambdaH && occ && rhs && vq, "mk_assemble_rhs: null argument");
-  MK_TRY(mk_frozen_potential(ctx, m, u, ld, occ, N, w, xc, vq, stream));
+  MK_TRY(mk_frozen_potential(ctx, m, u, ld, occ, N, nullptr, w, xc, vq, stream));
   return mk_assemble_rhs_from_vq(ctx, m, u, ld, lambdaH, N, vq, sigma, rhs, stream);
 }
 

@@ -94,7 +94,8 @@ _SIGS = {
     "mk_mesh_get_info": [_vp, C.POINTER(mk_mesh_info)],
     "mk_mesh_get_topology": [_vp, C.c_int, _vp, _vp, _vp, _vp],
     "mk_prolongate": [_vp, _vp, _vp, C.c_int, C.c_int, _vp, C.c_int, _vp],
-    "mk_hartree_poisson": [_vp, _vp, _vp, C.c_int, C.POINTER(C.c_double), C.c_int, C.c_int, _vp,
+    "mk_density": [_vp, _vp, _vp, C.c_int, C.POINTER(C.c_double), C.c_int, _vp, _vp],
+    "mk_hartree_poisson": [_vp, _vp, _vp, C.c_int, C.POINTER(C.c_double), C.c_int, _vp, C.c_int, _vp,
                            C.POINTER(mk_solve_opts), C.POINTER(mk_solve_report), _vp],
     "mk_assemble_rhs": [_vp, _vp, _vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int, _vp,
                         C.c_double, mk_xc, _vp, _vp, _vp],
@@ -116,7 +117,7 @@ _SIGS = {
                                   C.POINTER(mk_solve_opts), C.POINTER(mk_solve_report), _vp],
     "mk_mesh_set_patch_elems": [_vp, C.c_int],
     "mk_autotune_patches": [_vp, _vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)],
-    "mk_frozen_potential": [_vp, _vp, _vp, C.c_int, C.POINTER(C.c_double), C.c_int, _vp, mk_xc, _vp, _vp],
+    "mk_frozen_potential": [_vp, _vp, _vp, C.c_int, C.POINTER(C.c_double), C.c_int, _vp, _vp, mk_xc, _vp, _vp],
     "mk_assemble_rhs_from_vq": [_vp, _vp, _vp, C.c_int, C.POINTER(C.c_double), C.c_int, _vp, C.c_double, _vp, _vp],
     "mk_mlp_param_count": [C.c_int],
     "mk_mlp_create": [_vp, C.c_int, C.POINTER(C.c_float), C.POINTER(_vp)],
@@ -376,13 +377,20 @@ def mk_prolongate(ctx, mesh, psiH, N, u, stream=None):
     _check(lib().mk_prolongate(ctx.h, mesh.h, _ptr(psiH), ldc, N, _ptr(u), ld, _stream(stream)))
 
 
-def mk_hartree_poisson(ctx, mesh, u, occ, N, w, bc="multipole", opt=None, stream=None):
+def mk_density(ctx, mesh, u, occ, N, rho_q, stream=None):
+    """rho_H at the quadrature points [n_elems, n_quad] (float64 device tensor rho_q)."""
+    ld = u.shape[1] if u.dim() == 2 else 1
+    occ_h, occ_p = _host_f64(occ)
+    _check(lib().mk_density(ctx.h, mesh.h, _ptr(u), ld, occ_p, N, _ptr(rho_q), _stream(stream)))
+
+
+def mk_hartree_poisson(ctx, mesh, u, occ, N, w, bc="multipole", opt=None, stream=None, rho_q=None):
     ld = u.shape[1] if u.dim() == 2 else 1
     occ_h, occ_p = _host_f64(occ)
     rep = mk_solve_report()
     o = opt or opts(rtol=1e-12)
-    code = lib().mk_hartree_poisson(ctx.h, mesh.h, _ptr(u), ld, occ_p, N, MK_BC[bc], _ptr(w), C.byref(o),
-                                    C.byref(rep), _stream(stream))
+    code = lib().mk_hartree_poisson(ctx.h, mesh.h, _ptr(u), ld, occ_p, N, None if rho_q is None else _ptr(rho_q),
+                                    MK_BC[bc], _ptr(w), C.byref(o), C.byref(rep), _stream(stream))
     _check(code)
     return rep.to_dict()
 
@@ -395,11 +403,11 @@ def mk_assemble_rhs(ctx, mesh, u, lamH, occ, N, w, sigma, xc, rhs, vq, alpha=0.7
                                  mk_xc(MK_XC[xc], alpha), _ptr(rhs), _ptr(vq), _stream(stream)))
 
 
-def mk_frozen_potential(ctx, mesh, u, occ, N, w, xc, vq, alpha=0.77298, stream=None):
+def mk_frozen_potential(ctx, mesh, u, occ, N, w, xc, vq, alpha=0.77298, stream=None, rho_q=None):
     ld = u.shape[1] if u.dim() == 2 else 1
     occ_h, occ_p = _host_f64(occ)
-    _check(lib().mk_frozen_potential(ctx.h, mesh.h, _ptr(u), ld, occ_p, N, _ptr(w), mk_xc(MK_XC[xc], alpha), _ptr(vq),
-                                     _stream(stream)))
+    _check(lib().mk_frozen_potential(ctx.h, mesh.h, _ptr(u), ld, occ_p, N, None if rho_q is None else _ptr(rho_q),
+                                     _ptr(w), mk_xc(MK_XC[xc], alpha), _ptr(vq), _stream(stream)))
 
 
 def mk_assemble_rhs_from_vq(ctx, mesh, u, lamH, N, vq, sigma, rhs, stream=None):

@@ -35,6 +35,7 @@ class CorrectionStep:
         self.w = torch.zeros(n, **f64)
         self.rhs = torch.zeros((n, self.ld), **f64)
         self.vq = torch.zeros((E, info["n_quad"]), **f64)
+        self.rho = torch.zeros((E, info["n_quad"]), **f64)  # rho_H at the quadrature points
         self.psihat = torch.zeros((n, self.ld), **f64)
         self.AH = torch.zeros((NH, NH), **f64)
         self.MH = torch.zeros((NH, NH), **f64)
@@ -69,16 +70,18 @@ class CorrectionStep:
             psiH = self.psiH
         ctx, mesh = self.ctx, self.mesh
         mk.mk_prolongate(ctx, mesh, psiH, N, self.u, stream=stream)
+        # rho_H at the quadrature points, once for the Poisson solve and the frozen potential
+        mk.mk_density(ctx, mesh, self.u, occ, N, self.rho, stream=stream)
         reps = {}
         if hartree_bc == "none":
             self.w.zero_()
             reps["poisson"] = None
         else:
             reps["poisson"] = mk.mk_hartree_poisson(ctx, mesh, self.u, occ, N, self.w, bc=hartree_bc,
-                                                    opt=poisson_opts, stream=stream)
+                                                    opt=poisson_opts, stream=stream, rho_q=self.rho)
         # A3 in two halves: the frozen potential vq first, so that the coarse pencil and its decomposition (which
         # need vq, not rhs or psi^) start on the side stream while the right-hand sides and the fine solve run
-        mk.mk_frozen_potential(ctx, mesh, self.u, occ, N, self.w, xc, self.vq, stream=stream)
+        mk.mk_frozen_potential(ctx, mesh, self.u, occ, N, self.w, xc, self.vq, stream=stream, rho_q=self.rho)
         main = torch.cuda.current_stream() if stream is None else torch.cuda.ExternalStream(stream)
         if self.overlap:
             self._ev_rhs.record(main)

@@ -496,3 +496,29 @@ def test_stiffness_operator_matrix_free(ctx, torch, name):
             got = y.double().cpu().numpy()
             assert rel(got, ref) < tol, (ld, dt, rel(got, ref))
             assert np.all(got[lv.fine.boundary] == 0)
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_shared_density(ctx, torch, name):
+    """mk_density matches the oracle's rho_H at the quadrature points, and passed to the Poisson solve and the
+    frozen potential it gives bitwise the results of those calls computing rho_H themselves."""
+    from paper_2103_02824_gb300 import mk
+    from oracle.poisson import density_at_quad
+    c = case(name)
+    m = gpu_mesh(ctx, name)
+    N, n, E, nq = c["N"], m.info["n_nodes"], m.info["n_elems"], m.info["n_quad"]
+    u = dev(torch, padded(c["out"]["u"], N))
+    rho = torch.zeros((E, nq), dtype=torch.float64, device="cuda")
+    mk.mk_density(ctx, m, u, c["occ"], N, rho)
+    torch.cuda.synchronize()
+    ref = density_at_quad(c["level"].fine, c["out"]["u"], c["occ"])
+    assert rel(rho.cpu().numpy().ravel(), np.asarray(ref).ravel()) < 1e-12
+    w1, w2 = torch.zeros(n, dtype=torch.float64, device="cuda"), torch.zeros(n, dtype=torch.float64, device="cuda")
+    o = mk.opts(precision="mixed", rtol=1e-10, coarse=True)
+    mk.mk_hartree_poisson(ctx, m, u, c["occ"], N, w1, opt=o)
+    mk.mk_hartree_poisson(ctx, m, u, c["occ"], N, w2, opt=o, rho_q=rho)
+    vq1, vq2 = (torch.zeros((E, nq), dtype=torch.float64, device="cuda") for _ in range(2))
+    mk.mk_frozen_potential(ctx, m, u, c["occ"], N, w1, c["xc"], vq1)
+    mk.mk_frozen_potential(ctx, m, u, c["occ"], N, w1, c["xc"], vq2, rho_q=rho)
+    torch.cuda.synchronize()
+    assert torch.equal(w1, w2) and torch.equal(vq1, vq2)
