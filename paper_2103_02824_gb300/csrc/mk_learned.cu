@@ -65,10 +65,13 @@ __device__ __forceinline__ void mlp_row32(const float* __restrict__ w, const flo
   }
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x (lower column) in the low half
-  return *reinterpret_cast<uint32_t*>(&v);
+// relu(lo), relu(hi) rounded to BF16 and packed (lo in the low half), one instruction
+__device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;\n" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
 }
+
 
 // D += A B for one m16n8k16 BF16 tile (FP32 accumulators), the warp-level tensor-core MMA.
 __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
@@ -93,8 +96,9 @@ __device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const __nv_bfloat16* p
 // Fragment layout of m16n8k16 (g = lane / 4, t = lane % 4): A holds (row g | g+8, cols 2t, 2t+1 | 2t+8, 2t+9),
 // B holds (k = 2t, 2t+1 | 2t+8, 2t+9; n = g), C holds (row g | g+8, cols 2t, 2t+1).  A comes from the input tile by
 // ldmatrix (matrices: rows 0-7 / 8-15 x k 0-7 / 8-15 of a k-step), B from the weights by ldmatrix (rows n of an
-// n-tile x consecutive 8-wide k blocks).  The C tiles of two neighbouring n-blocks are exactly the A fragment of
-// the next layer's k-block, so hidden activations stay in registers.  out[nt][0..1]: row g, outputs
+// n-tile x consecutive 8-wide k blocks).  The accumulators start at the bias, and one cvt.relu turns two of them
+// into a packed BF16 pair.  The C tiles of two neighbouring n-blocks are exactly the A fragment of the next
+// layer's k-block, so hidden activations stay in registers.  out[nt][0..1]: row g, outputs
 // nt*8 + 2t + {0,1}; out[nt][2..3]: row g + 8.
 __device__ __forceinline__ void mlp_tile_bf16(const __nv_bfloat16* __restrict__ Xs,
                                               const __nv_bfloat16* __restrict__ W1b,
@@ -110,38 +114,36 @@ __device__ __forceinline__ void mlp_tile_bf16(const __nv_bfloat16* __restrict__ 
   for (int nt = 0; nt < 8; ++nt) {
     uint32_t b[4];
     ldsm_x4(b, W1b + (nt * 8 + r8) * kS1 + 8 * mm);  // k blocks 0, 8, 16, 24
-    float c[4] = {0.f, 0.f, 0.f, 0.f};
+    const float b0 = bias[nt * 8 + 2 * t], b1 = bias[nt * 8 + 2 * t + 1];
+    float c[4] = {b0, b1, b0, b1};  // the accumulators start at the bias
     mma_bf16(c, a1[0], b[0], b[1]);
     mma_bf16(c, a1[1], b[2], b[3]);
-    const float b0 = bias[nt * 8 + 2 * t], b1 = bias[nt * 8 + 2 * t + 1];
-    h1[nt >> 1][(nt & 1) * 2 + 0] = pack_bf16(fmaxf(c[0] + b0, 0.f), fmaxf(c[1] + b1, 0.f));
-    h1[nt >> 1][(nt & 1) * 2 + 1] = pack_bf16(fmaxf(c[2] + b0, 0.f), fmaxf(c[3] + b1, 0.f));
+    h1[nt >> 1][(nt & 1) * 2 + 0] = pack_relu_bf16(c[0], c[1]);
+    h1[nt >> 1][(nt & 1) * 2 + 1] = pack_relu_bf16(c[2], c[3]);
   }
 #pragma unroll
   for (int nt = 0; nt < 8; ++nt) {
     uint32_t b[2][4];
     ldsm_x4(b[0], W2b + (nt * 8 + r8) * kS2 + 8 * mm);       // k blocks 0, 8, 16, 24
     ldsm_x4(b[1], W2b + (nt * 8 + r8) * kS2 + 32 + 8 * mm);  // k blocks 32, 40, 48, 56
-    float c[4] = {0.f, 0.f, 0.f, 0.f};
+    const float b0 = bias[kNH + nt * 8 + 2 * t], b1 = bias[kNH + nt * 8 + 2 * t + 1];
+    float c[4] = {b0, b1, b0, b1};
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) mma_bf16(c, h1[kk], b[kk >> 1][(kk & 1) * 2], b[kk >> 1][(kk & 1) * 2 + 1]);
-    const float b0 = bias[kNH + nt * 8 + 2 * t], b1 = bias[kNH + nt * 8 + 2 * t + 1];
-    h2[nt >> 1][(nt & 1) * 2 + 0] = pack_bf16(fmaxf(c[0] + b0, 0.f), fmaxf(c[1] + b1, 0.f));
-    h2[nt >> 1][(nt & 1) * 2 + 1] = pack_bf16(fmaxf(c[2] + b0, 0.f), fmaxf(c[3] + b1, 0.f));
+    h2[nt >> 1][(nt & 1) * 2 + 0] = pack_relu_bf16(c[0], c[1]);
+    h2[nt >> 1][(nt & 1) * 2 + 1] = pack_relu_bf16(c[2], c[3]);
   }
 #pragma unroll
   for (int nt = 0; nt < 2; ++nt) {
     uint32_t b[2][4];
     ldsm_x4(b[0], W3b + (nt * 8 + r8) * kS2 + 8 * mm);
     ldsm_x4(b[1], W3b + (nt * 8 + r8) * kS2 + 32 + 8 * mm);
-    float c[4] = {0.f, 0.f, 0.f, 0.f};
+    const float b0 = bias[2 * kNH + nt * 8 + 2 * t], b1 = bias[2 * kNH + nt * 8 + 2 * t + 1];
+    float c[4] = {b0, b1, b0, b1};
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) mma_bf16(c, h2[kk], b[kk >> 1][(kk & 1) * 2], b[kk >> 1][(kk & 1) * 2 + 1]);
-    const float b0 = bias[2 * kNH + nt * 8 + 2 * t], b1 = bias[2 * kNH + nt * 8 + 2 * t + 1];
-    out[nt][0] = c[0] + b0;
-    out[nt][1] = c[1] + b1;
-    out[nt][2] = c[2] + b0;
-    out[nt][3] = c[3] + b1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) out[nt][i] = c[i];
   }
 }
 
@@ -300,11 +302,14 @@ __global__ void __launch_bounds__(256, 2) k_learned_patch(
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __nv_bfloat16* Xs = reinterpret_cast<__nv_bfloat16*>(smraw + lay.xt) + warp * 16 * kS1;
     float* scs = reinterpret_cast<float*>(smraw + lay.sc) + warp * 16;
+    // row / Nw as (row * ceil(2^16 / Nw)) >> 16: the ceiling adds less than row / 2^16, which stays below 1 / Nw
+    // for row < 2^16 / Nw (8,192 for Nw = 8; a patch has at most 512 * 8 rows), so the quotient is exact
+    const unsigned mnw = (65536u + (unsigned)Nw - 1u) / (unsigned)Nw;
     for (int tile = warp; tile * 16 < nrows; tile += nwarps) {
       const int i = lane & 15;
       const int row = tile * 16 + i;
       const bool valid = row < nrows;
-      const int el = valid ? row / Nw : 0, jj = valid ? row - el * Nw : 0;
+      const int el = valid ? (int)(((unsigned)row * mnw) >> 16) : 0, jj = valid ? row - el * Nw : 0;
       if (lane < 16) {
         float rv[NLOC], ss = 0.f;
 #pragma unroll
@@ -332,7 +337,7 @@ __global__ void __launch_bounds__(256, 2) k_learned_patch(
         const int ri = g + 8 * hr;
         const int row2 = tile * 16 + ri;
         if (row2 < nrows) {
-          const int el2 = row2 / Nw, jj2 = row2 - el2 * Nw;
+          const int el2 = (int)(((unsigned)row2 * mnw) >> 16), jj2 = row2 - el2 * Nw;
           const float sc = scs[ri];
 #pragma unroll
           for (int nt = 0; nt < 2; ++nt)
