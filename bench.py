@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "fine-mesh DOF×orbitals solved/s at 1e-8 rel. residual; learned vs plain PCG"
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_apply_stream launch from an ncu capture of the same kernel
 # build on the same workload (None until such a capture exists for the current kernel)
-TRAFFIC = {("mol4_p2", 8): 67.72e6}  # ncu: 65.67 MB read + 2.05 MB written by one launch on mol4_p2
+TRAFFIC = {("mol4_p2", 8): 67.81e6}  # ncu: 65.67 MB read + 2.14 MB written by one launch on mol4_p2
 UNIT = "DOF*orbitals/s"
 
 

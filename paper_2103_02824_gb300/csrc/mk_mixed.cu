@@ -258,6 +258,20 @@ __global__ void k_stiff_factors(int64_t E, const int32_t* __restrict__ elem_id, 
   fac[i * 8 + 7] = 0.f;
 }
 
+// Shared memory of one stiffness-patch CTA: the layout of patch_apply with the element-matrix region holding the
+// eight factors of each element instead.
+__host__ __device__ inline PatchSmem stiff_smem(int nloc, int pe, int max_nodes, int W) {
+  PatchSmem L;
+  L.ye = 0;
+  L.as = L.ye + align16((size_t)nloc * pe * W * 4);
+  L.conn = L.as + align16((size_t)pe * 8 * 4 + 16);
+  L.inc = L.conn + align16((size_t)pe * nloc * 4 + 16);
+  L.ioff = L.inc + align16((size_t)pe * nloc * 2 + 16);
+  L.tgt = L.ioff + align16((size_t)(max_nodes + 1) * 4 + 16);
+  L.total = L.tgt + align16((size_t)max_nodes * 4 + 16);
+  return L;
+}
+
 template <int NLOC>
 __global__ void __launch_bounds__(128, 8) k_stiff_patch(const int32_t* __restrict__ elem_off,
                                                     const int32_t* __restrict__ node_off,
@@ -269,8 +283,8 @@ __global__ void __launch_bounds__(128, 8) k_stiff_patch(const int32_t* __restric
                                                     float* __restrict__ halo, int ncol, int ld, int pe, int max_nodes,
                                                     const StiffRef ref) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const PatchSmem lay = patch_smem(NLOC, pe, max_nodes, ncol, 4);  // its element-matrix region holds the factors
-  float* Ye = reinterpret_cast<float*>(smraw + lay.ye);            // [NLOC][pe][ncol]
+  const PatchSmem lay = stiff_smem(NLOC, pe, max_nodes, ncol);
+  float* Ye = reinterpret_cast<float*>(smraw + lay.ye);  // [NLOC][pe][ncol]
   const int p = blockIdx.x;
   const int e0 = elem_off[p], ne = elem_off[p + 1] - e0;
   const int n0 = node_off[p], nl = node_off[p + 1] - n0;
@@ -365,7 +379,7 @@ static int apply_stiff(mk_ctx* ctx, const mk_mesh* m, const float* x, float* y, 
     for (int q = 0; q < 55; ++q) ref.k[c][q] = q < R.npack ? (float)R.stiff[c][q] : 0.f;
   for (int col0 = 0; col0 < ld; col0 += 16) {
     const int W = std::min(16, ld - col0);
-    const size_t smem = patch_smem(L.nloc, P.max_elems, P.max_nodes, W, 4).total;
+    const size_t smem = stiff_smem(L.nloc, P.max_elems, P.max_nodes, W).total;
     if (smem > 227 * 1024) return fail(MK_ERR_UNSUPPORTED, "stiffness operator: patch too large for shared memory");
     prof_mark(ctx, PROF_APPLY32, true, s);
     if (L.nloc == 4) {
