@@ -49,9 +49,11 @@ def parse():
                     help="inner preconditioner of the mixed-precision correction solve (learned: FCG(1))")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve measurement")
-    ap.add_argument("--mode", default="step", choices=["step", "apply", "learned"],
+    ap.add_argument("--mode", default="step", choices=["step", "apply", "learned", "stiffness", "decompose"],
                     help="apply: time the FP32 element-by-element operator alone (kernel-level roofline); "
-                         "learned: time the learned preconditioner (BF16 network) alone")
+                         "learned: the learned preconditioner (BF16 network) alone; stiffness: the matrix-free "
+                         "Poisson operator K alone (one column); decompose: the warm coarse decomposition of the "
+                         "step's pencil alone")
     return ap.parse_args()
 
 
@@ -123,6 +125,62 @@ def learned_mode(a):
     print(json.dumps({"mode": "learned", "workload": a.workload, "N": N, "ms_per_application": ms,
                       "note": "includes the operator diagonal (element matrices + assembly) recomputed per call",
                       "network_tflops": flops / (ms * 1e-3) / 1e12}))
+
+
+def stiffness_mode(a):
+    """Times mk_operator_apply with no molecule: the matrix-free FP32 stiffness operator K on one column."""
+    import torch
+    from paper_2103_02824_gb300 import build, mk, synth
+    from paper_2103_02824_gb300.step import upload_workload
+    build.build()
+    wl = synth.workload(a.workload)
+    ctx = mk.Context(0)
+    mesh, _ = upload_workload(ctx, wl)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    x = torch.randn(mesh.info["n_nodes"], generator=g, device="cuda", dtype=torch.float32)
+    y = torch.empty_like(x)
+    for _ in range(a.warmup):
+        mk.mk_operator_apply(ctx, mesh, None, 0.0, x, y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        mk.mk_operator_apply(ctx, mesh, None, 0.0, x, y)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "stiffness", "workload": a.workload, "ms_per_application": e0.elapsed_time(e1) / a.steps,
+                      "note": "stiffness kernel and halo pass"}))
+
+
+def decompose_mode(a):
+    """Times the warm coarse decomposition (block Jacobi) of the step's coarse pencil alone: one Jacobi-form step
+    fills A_H, then the decomposition is repeated on it."""
+    import torch
+    from paper_2103_02824_gb300 import build, mk, synth
+    from paper_2103_02824_gb300.step import CorrectionStep, coarse_eigenpairs, upload_workload
+    build.build()
+    wl = synth.workload(a.workload)
+    ctx = mk.Context(0)
+    mesh, _ = upload_workload(ctx, wl)
+    N, occ = synth.n_orbitals(wl["Z"]), synth.occupations(wl["Z"])
+    psiH, lamH, basis = coarse_eigenpairs(ctx, mesh, wl["Z"], wl["R"], N, return_basis=True)
+    st = CorrectionStep(ctx, mesh, wl["Z"], wl["R"], N, overlap=False, basis=basis)
+    theta = mk.mk_lowest_ritz(ctx, mesh, st.mol, synth.lanczos_start(mesh.info["n_free"]), steps=60)
+    st.run(psiH, lamH, occ, 1.05 * max(0.0, -theta) + 0.5, xc=wl["xc"], hartree_bc="multipole",
+           solve_opts=mk.opts(precision="mixed", precond="jacobi", rtol=1e-8, check_every=10),
+           poisson_opts=mk.opts(precision="mixed", rtol=1e-8, check_every=10, coarse=True))
+    stream = torch.cuda.current_stream().cuda_stream
+    for _ in range(a.warmup):
+        st._decompose(stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        st._decompose(stream)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "decompose", "workload": a.workload, "N_H": st.NH,
+                      "ms_per_decomposition": e0.elapsed_time(e1) / a.steps}))
 
 
 def workload_config(wl, N, n_free, NH, E):
@@ -219,6 +277,10 @@ def main():
         return apply_mode(a)
     if a.mode == "learned":
         return learned_mode(a)
+    if a.mode == "stiffness":
+        return stiffness_mode(a)
+    if a.mode == "decompose":
+        return decompose_mode(a)
     import numpy as np
     import torch
     torch.cuda.set_device(local)
