@@ -260,7 +260,7 @@ enum Slot : int {
   S_LDINV,                      // mk_learned_precond: FP64 diagonal, FP32 inverse
   S_TLC, S_TLX, S_TLW,          // two-level setup: coarse element products, coarse matrices, Cholesky workspace
   S_TLT,                        // two-level apply: restricted residual and coarse solution (FP32)
-  S_TLQ,                        // multiplicative two-level: operator product and residual (FP32)
+  S_TLQ,                        // multiplicative two-level: the operator product A z (FP32)
   S_FINCTR,                     // arrival counter of the fused reductions of the mixed solve
   S_ELEMP64,                    // FP64 element matrices in patch order (apply64)
   S_BATCH,                      // batched solve: per-problem buffers

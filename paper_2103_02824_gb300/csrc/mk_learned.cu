@@ -28,6 +28,19 @@ constexpr int kWbHalves = kNH * kS1 + kNH * kS2 + 16 * kS2;
 constexpr int kBias = kNH + kNH + 16;
 constexpr int kLW = 8;              // orbital columns per pass of the patch kernel
 
+// Layer-1 input columns of the tensor-core tile (k = 0..31): the first half of the n_loc residual features at
+// k = 0.., the second half at k = 8.., the 12 geometry features at k = 16..27, zeros elsewhere.  With this order
+// the lane (g, t) of an m16n8k16 A fragment holds residual features 2t, 2t+1, H+2t, H+2t+1 (H = n_loc / 2) of rows
+// g and g+8, so the patch kernel builds the residual half of the fragment in registers, and the geometry half is
+// one ldmatrix from a per-element table.  Returns the network input index at column kt, or -1 for a zero column.
+__host__ __device__ inline int tile_feature(int kt, int nloc) {
+  const int H = nloc / 2;
+  if (kt < 8) return kt < H ? kt : -1;
+  if (kt < 16) return kt - 8 < nloc - H ? H + kt - 8 : -1;
+  if (kt < 28) return nloc + kt - 16;
+  return -1;
+}
+
 static inline int64_t mlp_count(int nin, int nout) {
   return (int64_t)kNH * nin + kNH + (int64_t)kNH * kNH + kNH + (int64_t)nout * kNH + nout;
 }
@@ -100,15 +113,11 @@ __device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const __nv_bfloat16* p
 // into a packed BF16 pair.  The C tiles of two neighbouring n-blocks are exactly the A fragment of the next
 // layer's k-block, so hidden activations stay in registers.  out[nt][0..1]: row g, outputs
 // nt*8 + 2t + {0,1}; out[nt][2..3]: row g + 8.
-__device__ __forceinline__ void mlp_tile_bf16(const __nv_bfloat16* __restrict__ Xs,
-                                              const __nv_bfloat16* __restrict__ W1b,
+__device__ __forceinline__ void mlp_tile_bf16(const uint32_t (&a1)[2][4], const __nv_bfloat16* __restrict__ W1b,
                                               const __nv_bfloat16* __restrict__ W2b,
                                               const __nv_bfloat16* __restrict__ W3b,
                                               const float* __restrict__ bias, float (&out)[2][4]) {
   const int lane = threadIdx.x & 31, r8 = lane & 7, mm = lane >> 3, t = lane & 3;
-  uint32_t a1[2][4];
-#pragma unroll
-  for (int ks = 0; ks < 2; ++ks) ldsm_x4(a1[ks], Xs + (r8 + 8 * (mm & 1)) * kS1 + 16 * ks + 8 * (mm >> 1));
   uint32_t h1[4][4], h2[4][4];
 #pragma unroll
   for (int nt = 0; nt < 8; ++nt) {
@@ -165,6 +174,25 @@ __global__ void k_mlp_forward32(int64_t S, const float* __restrict__ w, int64_t 
   for (int o = 0; o < NLOC; ++o) Y[s * NLOC + o] = y[o];
 }
 
+// The same with the layer-1 input fragments loaded from a 16-row tile Xs (row stride kS1 halves).
+__device__ __forceinline__ void mlp_tile_bf16(const __nv_bfloat16* __restrict__ Xs,
+                                              const __nv_bfloat16* __restrict__ W1b,
+                                              const __nv_bfloat16* __restrict__ W2b,
+                                              const __nv_bfloat16* __restrict__ W3b,
+                                              const float* __restrict__ bias, float (&out)[2][4]) {
+  const int lane = threadIdx.x & 31, r8 = lane & 7, mm = lane >> 3;
+  uint32_t a1[2][4];
+#pragma unroll
+  for (int ks = 0; ks < 2; ++ks) ldsm_x4(a1[ks], Xs + (r8 + 8 * (mm & 1)) * kS1 + 16 * ks + 8 * (mm >> 1));
+  mlp_tile_bf16(a1, W1b, W2b, W3b, bias, out);
+}
+
+// Two floats as a packed BF16 pair (lo in the low half), round to nearest even.
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
 // Y = network(X) on the tensor cores (BF16), one warp per 16 rows.
 template <int NLOC>
 __global__ void __launch_bounds__(256) k_mlp_forward16(int64_t S, const __nv_bfloat16* __restrict__ wb,
@@ -184,8 +212,10 @@ __global__ void __launch_bounds__(256) k_mlp_forward16(int64_t S, const __nv_bfl
   {
     const int i = lane & 15, half = lane >> 4;
     const int64_t row = tile * 16 + i;
-    for (int k = half * 16; k < half * 16 + 16; ++k)
-      Xs[i * kS1 + k] = __float2bfloat16_rn((row < S && k < NIN) ? X[row * NIN + k] : 0.f);
+    for (int k = half * 16; k < half * 16 + 16; ++k) {
+      const int f = tile_feature(k, NLOC);
+      Xs[i * kS1 + k] = __float2bfloat16_rn((row < S && f >= 0) ? X[row * NIN + f] : 0.f);
+    }
   }
   __syncwarp();
   float out[2][4];
@@ -217,7 +247,8 @@ __global__ void k_mlp_pack(const float* __restrict__ w, int nin, int nout, __nv_
   const float* b3 = W3 + nout * kNH;
   if (i < kNH * kS1) {
     const int u = i / kS1, k = i % kS1;
-    wb[i] = __float2bfloat16_rn(k < nin ? W1[u * nin + k] : 0.f);
+    const int f = k < kK1 ? tile_feature(k, nin - 12) : -1;
+    wb[i] = __float2bfloat16_rn(f >= 0 ? W1[u * nin + f] : 0.f);
   } else if (i < kNH * kS1 + kNH * kS2) {
     const int j = i - kNH * kS1, u = j / kS2, k = j % kS2;
     wb[i] = __float2bfloat16_rn(k < kNH ? W2[u * kNH + k] : 0.f);
@@ -230,7 +261,7 @@ __global__ void k_mlp_pack(const float* __restrict__ w, int nin, int nout, __nv_
 
 // ------------------------------------------------------------------------------------------------ preconditioner
 struct LearnSmem {
-  size_t ye, rs, conn, inc, ioff, tgt, geo, w, xt, sc, total;
+  size_t ye, rs, conn, inc, ioff, tgt, geo, w, gb, total;
 };
 __host__ __device__ inline LearnSmem learn_smem(int nloc, int pe, int max_nodes, bool tc, int64_t count, int nwarps) {
   LearnSmem L;
@@ -243,15 +274,15 @@ __host__ __device__ inline LearnSmem learn_smem(int nloc, int pe, int max_nodes,
   L.geo = L.tgt + align16((size_t)max_nodes * 4 + 16);
   L.w = L.geo + align16((size_t)pe * 16 * 4 + 16);
   const size_t wbytes = tc ? (size_t)kWbHalves * 2 + 16 + (size_t)kBias * 4 + 16 : (size_t)count * 4 + 16;
-  L.xt = L.w + align16(wbytes);
-  L.sc = L.xt + (tc ? align16((size_t)nwarps * 16 * kS1 * 2) : 0);
-  L.total = L.sc + (tc ? align16((size_t)nwarps * 16 * 4) : 0);
+  L.gb = L.w + align16(wbytes);                                        // BF16 geometry table [element][16]
+  L.total = L.gb + (tc ? align16((size_t)pe * 16 * 2) : 0);
   return L;
 }
 
 // One patch per CTA (the patches of the operator apply).  Phase 1: the network on every (element, column) row
 // of the patch, scaled by s / h_e, into shared memory [slot][element][column]; on the tensor cores (TC) one
-// warp takes 16 rows at a time, otherwise one thread per row in FP32.  Phase 2: per local node the incidences
+// warp takes 16 rows at a time (the layer-1 fragments built in registers, see tile_feature), otherwise one
+// thread per row in FP32.  Phase 2: per local node the incidences
 // in fixed order, then z = sum / multiplicity + r / diag (owned nodes) or the partial sum to the node's halo
 // slot (shared nodes, finished by k_learned_halo).  Columns [col0, col0 + Nw), Nw = min(kLW, N - col0).
 template <int NLOC, bool TC>
@@ -296,59 +327,70 @@ __global__ void __launch_bounds__(256, 2) k_learned_patch(
   __syncthreads();
   const int nrows = ne * Nw;
   if constexpr (TC) {
+    // the geometry features of the patch's elements in BF16, one 32-byte row per element (columns 12-15 zero)
+    __nv_bfloat16* gbw = reinterpret_cast<__nv_bfloat16*>(smraw + lay.gb);
+    for (int i = threadIdx.x; i < ne * 8; i += blockDim.x) {
+      const int el = i >> 3, c = 2 * (i & 7);
+      reinterpret_cast<uint32_t*>(gbw)[i] =
+          pack_bf16(c < 12 ? gs[el * 16 + 1 + c] : 0.f, c + 1 < 12 ? gs[el * 16 + 2 + c] : 0.f);
+    }
+    __syncthreads();
+    const __nv_bfloat16* gbt = gbw;
     const __nv_bfloat16* W1b = reinterpret_cast<const __nv_bfloat16*>(wsm);
     const __nv_bfloat16* W2b = W1b + kNH * kS1;
     const __nv_bfloat16* W3b = W2b + kNH * kS2;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __nv_bfloat16* Xs = reinterpret_cast<__nv_bfloat16*>(smraw + lay.xt) + warp * 16 * kS1;
-    float* scs = reinterpret_cast<float*>(smraw + lay.sc) + warp * 16;
+    const int g = lane >> 2, t = lane & 3, r8 = lane & 7, mm = lane >> 3;
+    constexpr int H = NLOC / 2;
+    const int fa = 2 * t, fb = 2 * t + 1;  // this lane's residual features fa, fb, H + fa, H + fb (those < H)
     // row / Nw as (row * ceil(2^16 / Nw)) >> 16: the ceiling adds less than row / 2^16, which stays below 1 / Nw
     // for row < 2^16 / Nw (8,192 for Nw = 8; a patch has at most 512 * 8 rows), so the quotient is exact
     const unsigned mnw = (65536u + (unsigned)Nw - 1u) / (unsigned)Nw;
     for (int tile = warp; tile * 16 < nrows; tile += nwarps) {
-      const int i = lane & 15;
-      const int row = tile * 16 + i;
-      const bool valid = row < nrows;
-      const int el = valid ? (int)(((unsigned)row * mnw) >> 16) : 0, jj = valid ? row - el * Nw : 0;
-      if (lane < 16) {
-        float rv[NLOC], ss = 0.f;
+      uint32_t a1[2][4];
+      int el[2], jj[2];
+      float sc[2];
 #pragma unroll
-        for (int a = 0; a < NLOC; ++a) {
-          rv[a] = valid ? rs[cs[el * NLOC + a] * kLW + jj] : 0.f;
-          ss = fmaf(rv[a], rv[a], ss);
-        }
+      for (int hr = 0; hr < 2; ++hr) {  // rows g and g + 8 of the tile
+        const int row = tile * 16 + g + 8 * hr;
+        const bool valid = row < nrows;
+        const int e = valid ? (int)(((unsigned)row * mnw) >> 16) : 0;
+        el[hr] = e;
+        jj[hr] = valid ? row - e * Nw : 0;
+        const uint16_t* ce = cs + e * NLOC;
+        const float* rj = rs + jj[hr];
+        const float v0 = (valid && fa < H) ? rj[ce[fa] * kLW] : 0.f;
+        const float v1 = (valid && fb < H) ? rj[ce[fb] * kLW] : 0.f;
+        const float v2 = (valid && fa < H) ? rj[ce[H + fa] * kLW] : 0.f;
+        const float v3 = (valid && fb < H) ? rj[ce[H + fb] * kLW] : 0.f;
+        float ss = fmaf(v3, v3, fmaf(v2, v2, fmaf(v1, v1, v0 * v0)));
+        ss += __shfl_xor_sync(0xffffffffu, ss, 1);  // the row's four lanes hold all its features
+        ss += __shfl_xor_sync(0xffffffffu, ss, 2);
         const float s = sqrtf(ss);
         const float inv = s > 0.f ? 1.f / s : 0.f;
-#pragma unroll
-        for (int a = 0; a < NLOC; ++a) Xs[i * kS1 + a] = __float2bfloat16_rn(rv[a] * inv);
-        scs[i] = valid ? s / gs[el * 16] : 0.f;
-      } else {
-#pragma unroll
-        for (int k = 0; k < 12; ++k) Xs[i * kS1 + NLOC + k] = __float2bfloat16_rn(valid ? gs[el * 16 + 1 + k] : 0.f);
-#pragma unroll
-        for (int k = NLOC + 12; k < kK1; ++k) Xs[i * kS1 + k] = __float2bfloat16_rn(0.f);
+        a1[0][hr] = pack_bf16(v0 * inv, v1 * inv);      // k = 2t, 2t+1
+        a1[0][2 + hr] = pack_bf16(v2 * inv, v3 * inv);  // k = 8 + 2t, 8 + 2t + 1
+        sc[hr] = valid ? s / gs[e * 16] : 0.f;
       }
-      __syncwarp();
+      {  // geometry k-step: matrix mm holds rows (mm & 1) * 8 .. + 7, columns 16 + 8 * (mm >> 1) .. + 7
+        const int row = tile * 16 + r8 + 8 * (mm & 1);
+        const int e = row < nrows ? (int)(((unsigned)row * mnw) >> 16) : 0;
+        ldsm_x4(a1[1], gbt + e * 16 + 8 * (mm >> 1));
+      }
       float out[2][4];
-      mlp_tile_bf16(Xs, W1b, W2b, W3b, bsm, out);
-      const int g = lane >> 2, t = lane & 3;
+      mlp_tile_bf16(a1, W1b, W2b, W3b, bsm, out);
 #pragma unroll
       for (int hr = 0; hr < 2; ++hr) {
-        const int ri = g + 8 * hr;
-        const int row2 = tile * 16 + ri;
-        if (row2 < nrows) {
-          const int el2 = (int)(((unsigned)row2 * mnw) >> 16), jj2 = row2 - el2 * Nw;
-          const float sc = scs[ri];
+        if (tile * 16 + g + 8 * hr < nrows) {
 #pragma unroll
           for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
               const int o = nt * 8 + 2 * t + q;
-              if (o < NLOC) Ye[((size_t)o * pe + el2) * kLW + jj2] = out[nt][2 * hr + q] * sc;
+              if (o < NLOC) Ye[((size_t)o * pe + el[hr]) * kLW + jj[hr]] = out[nt][2 * hr + q] * sc[hr];
             }
         }
       }
-      __syncwarp();
     }
   } else {
     const float* wf = reinterpret_cast<const float*>(wsm);

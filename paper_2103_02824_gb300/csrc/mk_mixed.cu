@@ -408,16 +408,21 @@ static int apply_stiff(mk_ctx* ctx, const mk_mesh* m, const float* x, float* y, 
 // A_H = P^T A P, then z = (Jacobi or learned part) + P y.  FP32; every sum has a fixed order.
 constexpr int kTLC = 8;  // orbital columns per pass
 
-constexpr int kTLS = 8;  // segments (CTAs) per coarse DOF in the restriction
+constexpr int kTLS = 32;  // segments (warps) per coarse DOF in the restriction
+constexpr int kTLW = 8;   // warps per CTA of the restriction
+static_assert(kTLS % kTLW == 0, "a restriction CTA holds whole segments of one or more coarse DOF");
 
-// tp[k][seg][j] = sum over segment seg of the support of coarse DOF k of P^T[k][i] r[i][j]; one CTA per
-// (coarse DOF, segment), so that every SM has rows to stream.
-__global__ void __launch_bounds__(256) k_tl_restrict(const int32_t* __restrict__ off, const int32_t* __restrict__ col,
-                                                    const float* __restrict__ val, const float* __restrict__ r,
-                                                    int ld, int N, float* __restrict__ tp) {
-  __shared__ float sh[kTLC][8];
-  const int k = blockIdx.x / kTLS, seg = blockIdx.x % kTLS;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+// tp[k][seg][j] = sum over segment seg of the support of coarse DOF k of P^T[k][i] v[i][j], v = r, or r - q when
+// q is given (boundary rows of both are zero: masked residual, masked operator); one CTA of kTLS warps per coarse
+// DOF, warp seg takes segment seg (lane-strided, then a fixed shuffle tree), so no CTA barrier is needed; a CTA
+// holds kTLW consecutive (coarse DOF, segment) warps.
+__global__ void __launch_bounds__(kTLW * 32) k_tl_restrict(const int32_t* __restrict__ off,
+                                                          const int32_t* __restrict__ col,
+                                                          const float* __restrict__ val, const float* __restrict__ r,
+                                                          const float* __restrict__ q, int ld, int N,
+                                                          float* __restrict__ tp) {
+  const int gw = blockIdx.x * kTLW + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  const int k = gw / kTLS, seg = gw % kTLS;
   const int b0 = off[k], len = off[k + 1] - b0;
   const int b = b0 + (int)((int64_t)len * seg / kTLS), e = b0 + (int)((int64_t)len * (seg + 1) / kTLS);
   for (int c0 = 0; c0 < N; c0 += kTLC) {
@@ -426,26 +431,23 @@ __global__ void __launch_bounds__(256) k_tl_restrict(const int32_t* __restrict__
 #pragma unroll
     for (int c = 0; c < kTLC; ++c) acc[c] = 0.f;
 #pragma unroll 4
-    for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
+    for (int i = b + lane; i < e; i += 32) {
       const float w = val[i];
-      const float* ri = r + (int64_t)col[i] * ld + c0;
+      const int64_t o = (int64_t)col[i] * ld + c0;
 #pragma unroll
       for (int c = 0; c < kTLC; ++c)
-        if (c < nc) acc[c] = fmaf(w, ri[c], acc[c]);
+        if (c < nc) acc[c] = fmaf(w, q ? r[o + c] - q[o + c] : r[o + c], acc[c]);
     }
 #pragma unroll
-    for (int c = 0; c < kTLC; ++c) {
+    for (int c = 0; c < kTLC; ++c)
+      if (c < nc) {  // nc is uniform over the warp
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], o);
-      if (lane == 0) sh[c][warp] = acc[c];
-    }
-    __syncthreads();
-    if (threadIdx.x < nc) {
-      float v = 0.f;
-      for (int w = 0; w < nw; ++w) v += sh[threadIdx.x][w];
-      tp[((int64_t)k * kTLS + seg) * ld + c0 + threadIdx.x] = v;
-    }
-    __syncthreads();
+        for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], o);
+      }
+    if (lane == 0)
+#pragma unroll
+      for (int c = 0; c < kTLC; ++c)
+        if (c < nc) tp[((int64_t)k * kTLS + seg) * ld + c0 + c] = acc[c];
   }
 }
 
@@ -593,28 +595,31 @@ __global__ void k_tl_resid(int64_t n, const uint8_t* __restrict__ bnd, const flo
   out[idx] = mode == 0 ? d : fmaf(w * dinv[i], d, out[idx]);
 }
 
+// z0_ready: z already holds the first sweep w D^-1 r (written by the FCG update kernel); defer_final: the last
+// sweep z += w D^-1 (r - q) is left to the caller's next kernel (q = the S_TLQ scratch, A z at that point).
 template <typename Apply>
 static int twolevel_mult_apply(mk_ctx* ctx, const mk_mesh* m, Apply&& apply32, const float* cinv, const float* dinv,
-                               const float* r, float* z, int ld, int N, cudaStream_t s) {
+                               const float* r, float* z, int ld, int N, cudaStream_t s, bool z0_ready = false,
+                               bool defer_final = false) {
   const Level& L = m->fine;
   const int nH = (int)m->coarse.n_free;
   int err = MK_OK;
   float* t = (float*)scratch(ctx, S_TLT, (size_t)(kTLS + 1) * nH * ld * sizeof(float), &err);
-  float* q = (float*)scratch(ctx, S_TLQ, (size_t)L.n_nodes * ld * 2 * sizeof(float), &err);
+  float* q = (float*)scratch(ctx, S_TLQ, (size_t)L.n_nodes * ld * sizeof(float), &err);
   if (!t || !q) return err;
   float* y = t + (size_t)kTLS * nH * ld;
-  float* rr = q + (size_t)L.n_nodes * ld;
   const int gb = (int)((L.n_nodes * N + 255) / 256);
-  MK_COUNT(), k_tl_jacobi<<<gb, 256, 0, s>>>(L.n_nodes, L.d_boundary, dinv, r, z, ld, N, kTLOmega);
+  if (!z0_ready) MK_COUNT(), k_tl_jacobi<<<gb, 256, 0, s>>>(L.n_nodes, L.d_boundary, dinv, r, z, ld, N, kTLOmega);
   MK_TRY(apply32(z, q));
-  MK_COUNT(), k_tl_resid<<<gb, 256, 0, s>>>(L.n_nodes, L.d_boundary, dinv, r, q, rr, ld, N, kTLOmega, 0);
-  MK_COUNT(), k_tl_restrict<<<nH * kTLS, 256, 0, s>>>(m->d_PT_off, m->d_PT_col, m->d_PT_val32, rr, ld, N, t);
+  MK_COUNT(), k_tl_restrict<<<nH * kTLS / kTLW, kTLW * 32, 0, s>>>(m->d_PT_off, m->d_PT_col, m->d_PT_val32, r, q,
+                                                                   ld, N, t);
   MK_COUNT(), k_tl_coarse<<<(nH + kTLRows - 1) / kTLRows, kTLRows * 32, (size_t)nH * kTLC * sizeof(float), s>>>(
       nH, cinv, t, ld, N, y);
   MK_COUNT(), k_tl_prolong<<<gb, 256, 0, s>>>(L.n_nodes, m->d_P_off, m->d_P_col, m->d_P_val32, y, dinv,
                                               L.d_boundary, r, z, ld, N, 1);
   MK_TRY(apply32(z, q));
-  MK_COUNT(), k_tl_resid<<<gb, 256, 0, s>>>(L.n_nodes, L.d_boundary, dinv, r, q, z, ld, N, kTLOmega, 1);
+  if (!defer_final)
+    MK_COUNT(), k_tl_resid<<<gb, 256, 0, s>>>(L.n_nodes, L.d_boundary, dinv, r, q, z, ld, N, kTLOmega, 1);
   MK_CUDA(cudaGetLastError());
   return MK_OK;
 }
@@ -627,7 +632,8 @@ static int twolevel_apply(mk_ctx* ctx, const mk_mesh* m, const float* cinv, cons
   float* t = (float*)scratch(ctx, S_TLT, (size_t)(kTLS + 1) * nH * ld * sizeof(float), &err);
   if (!t) return err;
   float* y = t + (size_t)kTLS * nH * ld;
-  MK_COUNT(), k_tl_restrict<<<nH * kTLS, 256, 0, s>>>(m->d_PT_off, m->d_PT_col, m->d_PT_val32, r, ld, N, t);
+  MK_COUNT(), k_tl_restrict<<<nH * kTLS / kTLW, kTLW * 32, 0, s>>>(m->d_PT_off, m->d_PT_col, m->d_PT_val32, r,
+                                                                   nullptr, ld, N, t);
   MK_COUNT(), k_tl_coarse<<<(nH + kTLRows - 1) / kTLRows, kTLRows * 32, (size_t)nH * kTLC * sizeof(float), s>>>(
       nH, cinv, t, ld, N, y);
   MK_COUNT(), k_tl_prolong<<<(int)((L.n_nodes * N + 255) / 256), 256, 0, s>>>(
@@ -679,8 +685,19 @@ __device__ __forceinline__ void finalize_body(int mode, const double* __restrict
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int pr = warp; pr < NS * ld; pr += nw) {
     const int k = pr / ld, jj = pr - k * ld;
+    const double* pp = part + k * ld + jj;
+    const int64_t bs = (int64_t)NS * ld;
     double v = 0.0;
-    for (int b = lane; b < nblk; b += 32) v += __ldcg(&part[(int64_t)b * NS * ld + k * ld + jj]);
+    int b = lane;
+    for (; b + 96 < nblk; b += 128) {  // four independent loads in flight, added in the same order as one by one
+      const double x0 = __ldcg(pp + b * bs), x1 = __ldcg(pp + (b + 32) * bs), x2 = __ldcg(pp + (b + 64) * bs),
+                   x3 = __ldcg(pp + (b + 96) * bs);
+      v += x0;
+      v += x1;
+      v += x2;
+      v += x3;
+    }
+    for (; b < nblk; b += 32) v += __ldcg(pp + b * bs);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
     if (lane == 0) sums[k * ld + jj] = v;
@@ -807,6 +824,12 @@ __global__ void k_mixed_residual(int64_t n, const uint8_t* __restrict__ bnd, con
   if (fin.ctr) finalize_if_last(fin, part, ld);
 }
 
+// The FP32 vector kernels below visit the nodes of a thread in chunks of kChunk grid-stride steps: the chunk's
+// loads are independent (issued together), its products are summed in FP32 in a fixed order, and each chunk sum
+// is added to the thread's FP64 accumulator.  That keeps the FP64 units (about 2 operations per clock per SM) off
+// the per-element path; the partials and their tree stay FP64 and the result stays independent of scheduling.
+constexpr int kChunk = 4;
+
 // p = Dinv r; partials of (r.z, r.r)
 __global__ void k_mixed_init(int64_t n, const float* __restrict__ dinv, const float* __restrict__ r,
                              float* __restrict__ p, int ld, double* __restrict__ part, FinArgs fin) {
@@ -814,14 +837,27 @@ __global__ void k_mixed_init(int64_t n, const float* __restrict__ dinv, const fl
   double acc[2] = {0.0, 0.0};
   const int rows = blockDim.x / ld;
   const int j = threadIdx.x % ld, rr = threadIdx.x / ld;
+  const int64_t stride = (int64_t)gridDim.x * rows;
   if (rr < rows)
-    for (int64_t nd = (int64_t)blockIdx.x * rows + rr; nd < n; nd += (int64_t)gridDim.x * rows) {
-      const int64_t t = nd * ld + j;
-      const float rv = r[t];
-      const float z = rv * dinv[nd];
-      p[t] = z;
-      acc[0] += (double)rv * z;
-      acc[1] += (double)rv * rv;
+    for (int64_t nd0 = (int64_t)blockIdx.x * rows + rr; nd0 < n; nd0 += kChunk * stride) {
+      float rv[kChunk], dv[kChunk];
+#pragma unroll
+      for (int u = 0; u < kChunk; ++u) {
+        const int64_t nd = nd0 + u * stride;
+        rv[u] = nd < n ? r[nd * ld + j] : 0.f;
+        dv[u] = nd < n ? dinv[nd] : 0.f;
+      }
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int u = 0; u < kChunk; ++u) {
+        const int64_t nd = nd0 + u * stride;
+        const float z = rv[u] * dv[u];
+        if (nd < n) p[nd * ld + j] = z;
+        s0 = fmaf(rv[u], z, s0);
+        s1 = fmaf(rv[u], rv[u], s1);
+      }
+      acc[0] += (double)s0;
+      acc[1] += (double)s1;
     }
   block_partials<2>(acc, sh, ld, part, blockIdx.x);
   if (fin.ctr) finalize_if_last(fin, part, ld);
@@ -834,10 +870,20 @@ __device__ __forceinline__ void mixed_pq_body(int bx, int gx, int64_t n, const f
   double acc[1] = {0.0};
   const int rows = blockDim.x / ld;
   const int j = threadIdx.x % ld, rr = threadIdx.x / ld;
+  const int64_t stride = (int64_t)gx * rows;
   if (rr < rows)
-    for (int64_t nd = (int64_t)bx * rows + rr; nd < n; nd += (int64_t)gx * rows) {
-      const int64_t t = nd * ld + j;
-      acc[0] += (double)p[t] * q[t];
+    for (int64_t nd0 = (int64_t)bx * rows + rr; nd0 < n; nd0 += kChunk * stride) {
+      float pv[kChunk], qv[kChunk];
+#pragma unroll
+      for (int u = 0; u < kChunk; ++u) {
+        const int64_t nd = nd0 + u * stride;
+        pv[u] = nd < n ? p[nd * ld + j] : 0.f;
+        qv[u] = nd < n ? q[nd * ld + j] : 0.f;
+      }
+      float s0 = 0.f;
+#pragma unroll
+      for (int u = 0; u < kChunk; ++u) s0 = fmaf(pv[u], qv[u], s0);
+      acc[0] += (double)s0;
     }
   block_partials<1>(acc, sh, ld, part, bx);
 }
@@ -857,17 +903,43 @@ __device__ __forceinline__ void mixed_update_body(int bx, int gx, int64_t n, con
   const int rows = blockDim.x / ld;
   const int j = threadIdx.x % ld, rr = threadIdx.x / ld;
   const float a = rr < rows ? (float)st[j].alpha : 0.f;
+  const int64_t stride = (int64_t)gx * rows;
   if (rr < rows)
-    for (int64_t nd = (int64_t)bx * rows + rr; nd < n; nd += (int64_t)gx * rows) {
-      const int64_t t = nd * ld + j;
-      float rv = r[t];
-      if (a != 0.f) {
-        d[t] += a * p[t];
-        rv -= a * q[t];
-        r[t] = rv;
+    for (int64_t nd0 = (int64_t)bx * rows + rr; nd0 < n; nd0 += kChunk * stride) {
+      float rv[kChunk], dv[kChunk];
+#pragma unroll
+      for (int u = 0; u < kChunk; ++u) {
+        const int64_t nd = nd0 + u * stride;
+        rv[u] = nd < n ? r[nd * ld + j] : 0.f;
+        dv[u] = nd < n ? dinv[nd] : 0.f;
       }
-      acc[0] += (double)rv * (rv * dinv[nd]);
-      acc[1] += (double)rv * rv;
+      if (a != 0.f) {
+        float pv[kChunk], qv[kChunk], dd[kChunk];
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u) {
+          const int64_t nd = nd0 + u * stride;
+          pv[u] = nd < n ? p[nd * ld + j] : 0.f;
+          qv[u] = nd < n ? q[nd * ld + j] : 0.f;
+          dd[u] = nd < n ? d[nd * ld + j] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u) {
+          const int64_t nd = nd0 + u * stride;
+          rv[u] -= a * qv[u];
+          if (nd < n) {
+            d[nd * ld + j] = dd[u] + a * pv[u];
+            r[nd * ld + j] = rv[u];
+          }
+        }
+      }
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int u = 0; u < kChunk; ++u) {
+        s0 = fmaf(rv[u], rv[u] * dv[u], s0);
+        s1 = fmaf(rv[u], rv[u], s1);
+      }
+      acc[0] += (double)s0;
+      acc[1] += (double)s1;
     }
   block_partials<2>(acc, sh, ld, part, bx);
 }
@@ -900,35 +972,80 @@ __global__ void k_fcg_pq(int64_t n, const float* __restrict__ p, const float* __
   double acc[2] = {0.0, 0.0};
   const int rows = blockDim.x / ld;
   const int j = threadIdx.x % ld, rr = threadIdx.x / ld;
+  const int64_t stride = (int64_t)gridDim.x * rows;
   if (rr < rows)
-    for (int64_t nd = (int64_t)blockIdx.x * rows + rr; nd < n; nd += (int64_t)gridDim.x * rows) {
-      const int64_t t = nd * ld + j;
-      acc[0] += (double)p[t] * q[t];
-      acc[1] += (double)p[t] * r[t];
+    for (int64_t nd0 = (int64_t)blockIdx.x * rows + rr; nd0 < n; nd0 += kChunk * stride) {
+      float pv[kChunk], qv[kChunk], rv[kChunk];
+#pragma unroll
+      for (int u = 0; u < kChunk; ++u) {
+        const int64_t nd = nd0 + u * stride;
+        pv[u] = nd < n ? p[nd * ld + j] : 0.f;
+        qv[u] = nd < n ? q[nd * ld + j] : 0.f;
+        rv[u] = nd < n ? r[nd * ld + j] : 0.f;
+      }
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int u = 0; u < kChunk; ++u) {
+        s0 = fmaf(pv[u], qv[u], s0);
+        s1 = fmaf(pv[u], rv[u], s1);
+      }
+      acc[0] += (double)s0;
+      acc[1] += (double)s1;
     }
   block_partials<2>(acc, sh, ld, part, blockIdx.x);
   if (fin.ctr) finalize_if_last(fin, part, ld);
 }
 
-// FCG(1): d += alpha p; r -= alpha q; partial r.r
+// FCG(1): d += alpha p; r -= alpha q; partial r.r.  With z0 given, also the first sweep of the multiplicative
+// two-level preconditioner on the new residual: z0 = w D^-1 r (columns < N, boundary rows 0).
 __global__ void k_fcg_update(int64_t n, const MixState* __restrict__ st, const float* __restrict__ p,
                              const float* __restrict__ q, float* __restrict__ d, float* __restrict__ r, int ld,
-                             double* __restrict__ part, FinArgs fin) {
+                             double* __restrict__ part, FinArgs fin, float* __restrict__ z0,
+                             const float* __restrict__ dinv, const uint8_t* __restrict__ bnd, int N, float w) {
   __shared__ double sh[256];
   double acc[1] = {0.0};
   const int rows = blockDim.x / ld;
   const int j = threadIdx.x % ld, rr = threadIdx.x / ld;
   const float a = rr < rows ? (float)st[j].alpha : 0.f;
+  const int64_t stride = (int64_t)gridDim.x * rows;
   if (rr < rows)
-    for (int64_t nd = (int64_t)blockIdx.x * rows + rr; nd < n; nd += (int64_t)gridDim.x * rows) {
-      const int64_t t = nd * ld + j;
-      float rv = r[t];
-      if (a != 0.f) {
-        d[t] += a * p[t];
-        rv -= a * q[t];
-        r[t] = rv;
+    for (int64_t nd0 = (int64_t)blockIdx.x * rows + rr; nd0 < n; nd0 += kChunk * stride) {
+      float rv[kChunk];
+#pragma unroll
+      for (int u = 0; u < kChunk; ++u) {
+        const int64_t nd = nd0 + u * stride;
+        rv[u] = nd < n ? r[nd * ld + j] : 0.f;
       }
-      acc[0] += (double)rv * rv;
+      if (a != 0.f) {
+        float pv[kChunk], qv[kChunk], dd[kChunk];
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u) {
+          const int64_t nd = nd0 + u * stride;
+          pv[u] = nd < n ? p[nd * ld + j] : 0.f;
+          qv[u] = nd < n ? q[nd * ld + j] : 0.f;
+          dd[u] = nd < n ? d[nd * ld + j] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u) {
+          const int64_t nd = nd0 + u * stride;
+          rv[u] -= a * qv[u];
+          if (nd < n) {
+            d[nd * ld + j] = dd[u] + a * pv[u];
+            r[nd * ld + j] = rv[u];
+          }
+        }
+      }
+      if (z0 && j < N) {
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u) {
+          const int64_t nd = nd0 + u * stride;
+          if (nd < n) z0[nd * ld + j] = bnd[nd] ? 0.f : w * dinv[nd] * rv[u];
+        }
+      }
+      float s0 = 0.f;
+#pragma unroll
+      for (int u = 0; u < kChunk; ++u) s0 = fmaf(rv[u], rv[u], s0);
+      acc[0] += (double)s0;
     }
   block_partials<1>(acc, sh, ld, part, blockIdx.x);
   if (fin.ctr) finalize_if_last(fin, part, ld);
@@ -942,6 +1059,46 @@ __global__ void k_fcg_p(int64_t n, const MixState* __restrict__ st, const float*
   const int j = (int)(t % ld);
   if (!st[j].active) return;
   p[t] = z[t] + (float)st[j].beta * p[t];
+}
+
+// The last sweep of the multiplicative two-level preconditioner, z += w D^-1 (r - t) (columns < N, boundary
+// rows 0; t = A z from inside the preconditioner), fused with the FCG(1) partial z.q of the next beta.
+__global__ void k_tl_final_pq(int64_t n, const uint8_t* __restrict__ bnd, const float* __restrict__ dinv,
+                              const float* __restrict__ r, const float* __restrict__ t, float* __restrict__ z,
+                              const float* __restrict__ q, int ld, int N, float w, double* __restrict__ part,
+                              FinArgs fin) {
+  __shared__ double sh[256];
+  double acc[1] = {0.0};
+  const int rows = blockDim.x / ld;
+  const int j = threadIdx.x % ld, rr = threadIdx.x / ld;
+  const int64_t stride = (int64_t)gridDim.x * rows;
+  if (rr < rows)
+    for (int64_t nd0 = (int64_t)blockIdx.x * rows + rr; nd0 < n; nd0 += kChunk * stride) {
+      float zv[kChunk], qv[kChunk];
+#pragma unroll
+      for (int u = 0; u < kChunk; ++u) {
+        const int64_t nd = nd0 + u * stride;
+        zv[u] = nd < n ? z[nd * ld + j] : 0.f;
+        qv[u] = nd < n ? q[nd * ld + j] : 0.f;
+      }
+      if (j < N) {
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u) {
+          const int64_t nd = nd0 + u * stride;
+          if (nd < n) {
+            const int64_t i = nd * ld + j;
+            zv[u] = bnd[nd] ? 0.f : fmaf(w * dinv[nd], r[i] - t[i], zv[u]);
+            z[i] = zv[u];
+          }
+        }
+      }
+      float s0 = 0.f;
+#pragma unroll
+      for (int u = 0; u < kChunk; ++u) s0 = fmaf(zv[u], qv[u], s0);
+      acc[0] += (double)s0;
+    }
+  block_partials<1>(acc, sh, ld, part, blockIdx.x);
+  if (fin.ctr) finalize_if_last(fin, part, ld);
 }
 
 __global__ void k_mixed_add(int64_t n, const float* __restrict__ d, double* __restrict__ x, int N, int ld) {
@@ -1084,7 +1241,8 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
   if (!scratch(ctx, S_HALO, (size_t)std::max<int64_t>(m->patches.n_halo_slots, 1) * ld * sizeof(float), &err))
     return err;
   if (cinv && !scratch(ctx, S_TLT, (size_t)(kTLS + 1) * m->coarse.n_free * ld * sizeof(float), &err)) return err;
-  if (cinv && !learned && !scratch(ctx, S_TLQ, (size_t)n * ld * 2 * sizeof(float), &err)) return err;
+  float* tlq = nullptr;  // A z inside the multiplicative two-level preconditioner
+  if (cinv && !learned && !(tlq = (float*)scratch(ctx, S_TLQ, (size_t)n * ld * sizeof(float), &err))) return err;
   if (stiff && !stiff_factors(m, s, &err)) return err;  // allocated here: nothing may allocate inside a capture
   if (fcg) {
     if (!scratch(ctx, S_LHALO, (size_t)std::max<int64_t>(m->patches.n_halo_slots, 1) * ld * sizeof(float), &err))
@@ -1124,9 +1282,19 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
       MK_TRY(apply32(p, q));
       if (fcg) {
         MK_COUNT(), k_fcg_pq<<<nblk, th, 0, s>>>(n, p, q, r, ld, part, fin(4, 2));
-        MK_COUNT(), k_fcg_update<<<nblk, th, 0, s>>>(n, st, p, q, d, r, ld, part, fin(5, 1));
-        MK_TRY(precond());
-        MK_COUNT(), k_mixed_pq<<<nblk, th, 0, s>>>(n, zb, q, ld, part, fin(6, 1));
+        if (tlq) {
+          // multiplicative two-level: the first sweep rides on the update, the last on the z.q reduction
+          MK_COUNT(), k_fcg_update<<<nblk, th, 0, s>>>(n, st, p, q, d, r, ld, part, fin(5, 1), zb, dinv,
+                                                       L.d_boundary, N, kTLOmega);
+          MK_TRY(twolevel_mult_apply(ctx, m, apply32, cinv, dinv, r, zb, ld, N, s, true, true));
+          MK_COUNT(), k_tl_final_pq<<<nblk, th, 0, s>>>(n, L.d_boundary, dinv, r, tlq, zb, q, ld, N, kTLOmega, part,
+                                                        fin(6, 1));
+        } else {
+          MK_COUNT(), k_fcg_update<<<nblk, th, 0, s>>>(n, st, p, q, d, r, ld, part, fin(5, 1), nullptr, nullptr,
+                                                       nullptr, N, 0.f);
+          MK_TRY(precond());
+          MK_COUNT(), k_mixed_pq<<<nblk, th, 0, s>>>(n, zb, q, ld, part, fin(6, 1));
+        }
         MK_COUNT(), k_fcg_p<<<gb, 256, 0, s>>>(n, st, zb, p, ld);
         return MK_OK;
       }
