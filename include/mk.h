@@ -126,11 +126,12 @@ typedef struct {
 int mk_ctx_create(mk_ctx** ctx, int device);
 int mk_ctx_destroy(mk_ctx* ctx);
 /* Waits for the device, then returns in *fault the context's device fault word and clears it: 0, or
- * MK_FAULT_* bits set by kernels whose bounded waits for their own asynchronous copies gave up (those kernels
- * return early and their outputs are invalid; the solves that launched them return MK_ERR_TIMEOUT).  A
- * diagnostic with no counterpart in the paper. */
+ * MK_FAULT_* bits set by kernels whose bounded waits for their own asynchronous copies or tensor-core operations
+ * gave up (those kernels return early and their outputs are invalid; the solves that launched them return
+ * MK_ERR_TIMEOUT).  A diagnostic with no counterpart in the paper. */
 #define MK_FAULT_PATCH_WAIT 1
 #define MK_FAULT_PATCH_RECORD 2
+#define MK_FAULT_TC_WAIT 4
 int mk_ctx_fault(mk_ctx* ctx, int* fault);
 /* Copies the calling thread's last error message into buf (always NUL-terminated); returns its length. */
 int mk_last_error(char* buf, size_t len);

@@ -174,8 +174,7 @@ struct mk_mlp {
   float* d_w = nullptr;
   float* d_m = nullptr;
   float* d_v = nullptr;
-  void* d_wb = nullptr;
-  float* d_bias = nullptr;
+  void* d_wb = nullptr;  // BF16 copy of the parameters in the tensor-core (tcgen05) operand layout
   long long t = 0;  // Adam steps taken
 };
 

@@ -1,7 +1,8 @@
 // Learned element-patch preconditioner: the network (FP32 master weights, Adam, BF16 inference copy), its
-// forward pass on CUDA cores (FP32) and on the warp tensor cores (BF16 MMA, FP32 accumulation), the fused
-// patch kernel that turns a residual into z = D^-1 r + (assembled network corrections) / multiplicity, the
-// deterministic training gradient, Adam, and the harvest of training samples from solver iterates.
+// forward pass on CUDA cores (FP32) and on the 5th-generation tensor cores (tcgen05: BF16 operands in shared
+// memory, FP32 accumulation in tensor memory), the fused patch kernels that turn a residual into
+// z = D^-1 r + (assembled network corrections) / multiplicity, the deterministic training gradient, Adam, and
+// the harvest of training samples from solver iterates.
 //
 // Definitions (the library's own; the paper's boundary-value problems use standard solvers):
 //   x   = [r_e / s, (v_k - centroid)/h_e],  s = ||r_e||_2, h_e = |det J_e|^(1/3)
@@ -21,25 +22,30 @@
 namespace mk {
 
 constexpr int kNH = MK_MLP_HIDDEN;  // hidden width (64)
-constexpr int kK1 = 32;             // layer-1 input width of the tensor-core tile (n_in <= 22, zero padded)
-constexpr int kS1 = 40;             // row stride in halves of the input tile and of W1 (conflict-free fragments)
-constexpr int kS2 = 72;             // row stride in halves of W2 and W3
-constexpr int kWbHalves = kNH * kS1 + kNH * kS2 + 16 * kS2;
-constexpr int kBias = kNH + kNH + 16;
 constexpr int kLW = 8;              // orbital columns per pass of the patch kernel
 
-// Layer-1 input columns of the tensor-core tile (k = 0..31): the first half of the n_loc residual features at
-// k = 0.., the second half at k = 8.., the 12 geometry features at k = 16..27, zeros elsewhere.  With this order
-// the lane (g, t) of an m16n8k16 A fragment holds residual features 2t, 2t+1, H+2t, H+2t+1 (H = n_loc / 2) of rows
-// g and g+8, so the patch kernel builds the residual half of the fragment in registers, and the geometry half is
-// one ldmatrix from a per-element table.  Returns the network input index at column kt, or -1 for a zero column.
-__host__ __device__ inline int tile_feature(int kt, int nloc) {
-  const int H = nloc / 2;
-  if (kt < 8) return kt < H ? kt : -1;
-  if (kt < 16) return kt - 8 < nloc - H ? H + kt - 8 : -1;
-  if (kt < 28) return nloc + kt - 16;
-  return -1;
+// ---- the BF16 network on the 5th-generation tensor cores (tcgen05)
+// Operands live in shared memory in the K-major, unswizzled canonical layout of tcgen05.mma: an R x K BF16 matrix
+// is a grid of core matrices of 8 rows x 8 columns, each 128 contiguous bytes (row r of a core matrix at byte
+// 16 r); core matrices adjacent in K are 128 bytes apart (the descriptor's leading-dimension byte offset) and
+// groups of 8 rows K * 16 bytes apart (its stride-dimension byte offset).
+constexpr int kK1 = 32;       // layer-1 input width: the n_in <= 22 features, the two bias inputs, zeros
+constexpr int kKOne = 28;     // input columns 28 and 29 hold 1.0 against the layer-1 bias (high, low BF16 parts)
+constexpr int kTcRows = 128;  // rows per tile: the MMA's M, the TMEM lanes, the threads of the CTA
+__host__ __device__ constexpr int umma_off(int row, int k, int K) {  // element (row, k) in halves
+  return (row >> 3) * (K * 8) + (k >> 3) * 64 + (row & 7) * 8 + (k & 7);
 }
+// Packed weights (halves, each matrix [out][in] in the layout above): W1 [64 x 32] with the layer-1 bias parts in
+// columns kKOne, kKOne + 1; W2 [64 x 64]; W3 [16 x 64] (rows >= n_out zero); the layer-2 and layer-3 biases as
+// [64 x 16] and [16 x 16] matrices whose columns 0 and 1 hold the high and low BF16 parts, multiplied by an
+// all-ones input tile.  high + low carries the FP32 bias to about 2^-16 relative.
+constexpr int kUW1 = 0;
+constexpr int kUW2 = kUW1 + kNH * kK1;
+constexpr int kUW3 = kUW2 + kNH * kNH;
+constexpr int kUB2 = kUW3 + 16 * kNH;
+constexpr int kUB3 = kUB2 + kNH * 16;
+constexpr int kWuHalves = kUB3 + 16 * 16;
+constexpr uint32_t kTmemCols = 64;  // every layer's accumulator starts at TMEM column 0 (layer 3 uses 16)
 
 static inline int64_t mlp_count(int nin, int nout) {
   return (int64_t)kNH * nin + kNH + (int64_t)kNH * kNH + kNH + (int64_t)nout * kNH + nout;
@@ -86,74 +92,194 @@ __device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi) {
 }
 
 
-// D += A B for one m16n8k16 BF16 tile (FP32 accumulators), the warp-level tensor-core MMA.
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+// Two floats as a packed BF16 pair (lo in the low half), round to nearest even.
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// ---- tcgen05 primitives (inline PTX).  tcgen05.mma reads A and B from shared memory through 64-bit matrix
+// descriptors and accumulates in tensor memory (TMEM: 128 lanes x 512 32-bit columns per SM); one thread issues
+// it, tcgen05.commit makes an mbarrier track its completion, and each warp reads back its quarter of the lanes
+// (warp w of the CTA: lanes 32 (w % 4) .. + 31) with tcgen05.ld.  For M = 128, row i of D is TMEM lane i and
+// column n is TMEM column base + n.
+// Shared-memory matrix descriptor: start address / 16 (bits 0-13), leading-dimension byte offset 128 / 16 (bits
+// 16-29: the next core matrix along K), stride-dimension byte offset sbo / 16 (bits 32-45: the next 8-row
+// group), the fixed 0b001 at bits 46-48, base offset 0, no swizzle (bits 61-63 = 0).
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+         (1ull << 46);
+}
+// Instruction descriptor of kind::f16: dense, FP32 accumulator (bits 4-5 = 1), BF16 A and B (bits 7-9 and 10-12 =
+// 1), neither negated, both K-major (bits 15, 16 = 0), N / 8 at bits 17-22, M / 16 at bits 24-28.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// D = A B^T (acc = 0) or D += A B^T (acc = 1), A [M x K], B [N x K], both K-major, one K = 16 step
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t acc) {
   asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// the mbarrier receives one arrival when every tcgen05.mma this thread issued before has completed
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+// by one whole warp: ncols TMEM columns (a power of two >= 32), the address written to *slot
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// 64 (16) consecutive 32-bit columns of this thread's TMEM lane, waited for inside the same statement so that no
+// use of the registers can be scheduled before the load has completed
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[64]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];\n"
+               "tcgen05.wait::ld.sync.aligned;\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+               : "r"(taddr)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n"
+               "tcgen05.wait::ld.sync.aligned;\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(taddr)
+               : "memory");
 }
 
-// Four 8 x 8 BF16 matrices from shared memory (ldmatrix): lanes 8m .. 8m + 7 give the row addresses of matrix m,
-// and register m of lane l receives row l / 4, columns 2 (l % 4) and + 1 of matrix m.
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const __nv_bfloat16* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(smem_u32(p)));
+// Barrier of one warpgroup (128 threads): id 0 is the CTA barrier (CTAs of one warpgroup), ids 1.. named ones.
+__device__ __forceinline__ void wg_barrier(int id) {
+  if (id == 0) __syncthreads();
+  else asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(kTcRows) : "memory");
+}
+// This thread's shared-memory writes become visible to the tensor cores, its TMEM reads are ordered before the
+// barrier, and tcgen05 work after the barrier is ordered after it.
+__device__ __forceinline__ void sync_for_mma(int barid) {
+  fence_proxy_async();
+  tc_fence_before();
+  wg_barrier(barid);
+  tc_fence_after();
 }
 
-// The network on 16 rows by one warp.  Xs: 16 x kS1 BF16 inputs (columns >= n_in zero); W1b/W2b/W3b: BF16
-// weights [out][in] with row strides kS1/kS2/kS2 halves (16-byte rows: every ldmatrix row address is aligned, and
-// the strides put the eight rows of a matrix in distinct bank groups); bias: FP32 b1 | b2 | b3 (zero padded to 16).
-// Fragment layout of m16n8k16 (g = lane / 4, t = lane % 4): A holds (row g | g+8, cols 2t, 2t+1 | 2t+8, 2t+9),
-// B holds (k = 2t, 2t+1 | 2t+8, 2t+9; n = g), C holds (row g | g+8, cols 2t, 2t+1).  A comes from the input tile by
-// ldmatrix (matrices: rows 0-7 / 8-15 x k 0-7 / 8-15 of a k-step), B from the weights by ldmatrix (rows n of an
-// n-tile x consecutive 8-wide k blocks).  The accumulators start at the bias, and one cvt.relu turns two of them
-// into a packed BF16 pair.  The C tiles of two neighbouring n-blocks are exactly the A fragment of the next
-// layer's k-block, so hidden activations stay in registers.  out[nt][0..1]: row g, outputs
-// nt*8 + 2t + {0,1}; out[nt][2..3]: row g + 8.
-__device__ __forceinline__ void mlp_tile_bf16(const uint32_t (&a1)[2][4], const __nv_bfloat16* __restrict__ W1b,
-                                              const __nv_bfloat16* __restrict__ W2b,
-                                              const __nv_bfloat16* __restrict__ W3b,
-                                              const float* __restrict__ bias, float (&out)[2][4]) {
-  const int lane = threadIdx.x & 31, r8 = lane & 7, mm = lane >> 3, t = lane & 3;
-  uint32_t h1[4][4], h2[4][4];
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    uint32_t b[4];
-    ldsm_x4(b, W1b + (nt * 8 + r8) * kS1 + 8 * mm);  // k blocks 0, 8, 16, 24
-    const float b0 = bias[nt * 8 + 2 * t], b1 = bias[nt * 8 + 2 * t + 1];
-    float c[4] = {b0, b1, b0, b1};  // the accumulators start at the bias
-    mma_bf16(c, a1[0], b[0], b[1]);
-    mma_bf16(c, a1[1], b[2], b[3]);
-    h1[nt >> 1][(nt & 1) * 2 + 0] = pack_relu_bf16(c[0], c[1]);
-    h1[nt >> 1][(nt & 1) * 2 + 1] = pack_relu_bf16(c[2], c[3]);
+// State of one warpgroup running the network on tcgen05 (kTcRows threads, one tile row each).  Pointers into the
+// activation tile are deliberately not __restrict__: the tile is read by the tensor cores between the threads'
+// stores, and a no-alias promise would let the compiler move those stores past the proxy fence and the barrier.
+struct TcState {
+  uint32_t tmem;         // TMEM address of this warpgroup's kTmemCols columns (lane 0)
+  uint32_t xh, w, one;   // shared addresses: activation tile [128 x 64], packed weights, all-ones tile [128 x 16]
+  uint64_t* bar;         // this warpgroup's MMA mbarrier
+  int barid;             // its barrier id
+  unsigned phase;        // parity of the mbarrier's next completion
+  bool ok;               // false once a bounded wait of this thread gave up
+};
+
+// Allocates ncols TMEM columns for the CTA (warp 0), initialises nbar MMA mbarriers and writes the all-ones tile
+// (threads 0-127, one row each).  The caller completes its staging and calls sync_for_mma(0) before reading *slot.
+__device__ __forceinline__ void tc_setup(uint32_t* slot, uint32_t ncols, uint64_t* bars, int nbar,
+                                         __nv_bfloat16* one) {
+  if (threadIdx.x < 32) tmem_alloc(slot, ncols);
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < nbar; ++b) mbar_init(bars + b, 1);
+    mbar_fence_init();
   }
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    uint32_t b[2][4];
-    ldsm_x4(b[0], W2b + (nt * 8 + r8) * kS2 + 8 * mm);       // k blocks 0, 8, 16, 24
-    ldsm_x4(b[1], W2b + (nt * 8 + r8) * kS2 + 32 + 8 * mm);  // k blocks 32, 40, 48, 56
-    const float b0 = bias[kNH + nt * 8 + 2 * t], b1 = bias[kNH + nt * 8 + 2 * t + 1];
-    float c[4] = {b0, b1, b0, b1};
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) mma_bf16(c, h1[kk], b[kk >> 1][(kk & 1) * 2], b[kk >> 1][(kk & 1) * 2 + 1]);
-    h2[nt >> 1][(nt & 1) * 2 + 0] = pack_relu_bf16(c[0], c[1]);
-    h2[nt >> 1][(nt & 1) * 2 + 1] = pack_relu_bf16(c[2], c[3]);
+  const int r = threadIdx.x;
+  if (r < kTcRows) {
+    *reinterpret_cast<uint4*>(one + umma_off(r, 0, 16)) = make_uint4(pack_bf16(1.f, 1.f), 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(one + umma_off(r, 8, 16)) = make_uint4(0u, 0u, 0u, 0u);
   }
-#pragma unroll
-  for (int nt = 0; nt < 2; ++nt) {
-    uint32_t b[2][4];
-    ldsm_x4(b[0], W3b + (nt * 8 + r8) * kS2 + 8 * mm);
-    ldsm_x4(b[1], W3b + (nt * 8 + r8) * kS2 + 32 + 8 * mm);
-    const float b0 = bias[2 * kNH + nt * 8 + 2 * t], b1 = bias[2 * kNH + nt * 8 + 2 * t + 1];
-    float c[4] = {b0, b1, b0, b1};
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) mma_bf16(c, h2[kk], b[kk >> 1][(kk & 1) * 2], b[kk >> 1][(kk & 1) * 2 + 1]);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) out[nt][i] = c[i];
+}
+// Every tcgen05 operation of the CTA has completed (all waited for): warp 0 frees the TMEM.
+__device__ __forceinline__ void tc_teardown(uint32_t tmem, uint32_t ncols) {
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tc_fence_after();
+    tmem_dealloc(tmem, ncols);
   }
+}
+__device__ __forceinline__ void mma_wait(TcState& S) {
+  if (S.ok && !mbar_wait(S.bar, S.phase)) S.ok = false;
+  S.phase ^= 1u;
+  tc_fence_after();
+}
+// relu(acc) of this thread's row as the next layer's input row (K = 64)
+__device__ __forceinline__ void store_hidden_row(__nv_bfloat16* xh, int row, const uint32_t (&a)[64]) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    uint4 v;
+    v.x = pack_relu_bf16(__uint_as_float(a[8 * c + 0]), __uint_as_float(a[8 * c + 1]));
+    v.y = pack_relu_bf16(__uint_as_float(a[8 * c + 2]), __uint_as_float(a[8 * c + 3]));
+    v.z = pack_relu_bf16(__uint_as_float(a[8 * c + 4]), __uint_as_float(a[8 * c + 5]));
+    v.w = pack_relu_bf16(__uint_as_float(a[8 * c + 6]), __uint_as_float(a[8 * c + 7]));
+    *reinterpret_cast<uint4*>(xh + umma_off(row, 8 * c, kNH)) = v;
+  }
+}
+// This thread's layer-1 input row (kK1 values) into the activation tile.
+__device__ __forceinline__ void store_input_row(__nv_bfloat16* xh, int row, const float (&f)[kK1]) {
+#pragma unroll
+  for (int c = 0; c < kK1 / 8; ++c)
+    *reinterpret_cast<uint4*>(xh + umma_off(row, 8 * c, kK1)) =
+        make_uint4(pack_bf16(f[8 * c + 0], f[8 * c + 1]), pack_bf16(f[8 * c + 2], f[8 * c + 3]),
+                   pack_bf16(f[8 * c + 4], f[8 * c + 5]), pack_bf16(f[8 * c + 6], f[8 * c + 7]));
+}
+
+// The network on one tile of kTcRows rows whose layer-1 inputs the warpgroup's threads have just stored (row =
+// thread index in the warpgroup); y receives this thread's row of the output layer (16 columns, those >= n_out
+// zero).  Each layer: the warpgroup's first thread issues the MMAs (the bias first, against the all-ones tile, for
+// layers 2 and 3; through the constant input columns for layer 1) and commits them to the mbarrier; every thread
+// waits, reads its accumulator row from TMEM and writes relu of it, in BF16, over the activation tile (the MMAs
+// reading that tile have completed by then).
+__device__ __forceinline__ void umma_mlp_tile(TcState& S, __nv_bfloat16* xh, float (&y)[16]) {
+  constexpr uint32_t i64 = umma_idesc_bf16(kTcRows, kNH), i16 = umma_idesc_bf16(kTcRows, 16);
+  const int tid = threadIdx.x & (kTcRows - 1);
+  const uint32_t lane = (uint32_t)(tid & ~31) << 16;  // this warp's TMEM lane quarter (warp index mod 4)
+  uint32_t a[64];
+  sync_for_mma(S.barid);
+  if (tid == 0 && S.ok) {
+#pragma unroll
+    for (int ks = 0; ks < kK1 / 16; ++ks)
+      umma_bf16(S.tmem, umma_desc(S.xh + 256 * ks, kK1 * 16), umma_desc(S.w + 2 * kUW1 + 256 * ks, kK1 * 16), i64,
+                ks > 0);
+    umma_commit(S.bar);
+  }
+  mma_wait(S);
+  tmem_ld64(S.tmem + lane, a);
+  store_hidden_row(xh, tid, a);
+  sync_for_mma(S.barid);
+  if (tid == 0 && S.ok) {
+    umma_bf16(S.tmem, umma_desc(S.one, 256), umma_desc(S.w + 2 * kUB2, 256), i64, 0);
+#pragma unroll
+    for (int ks = 0; ks < kNH / 16; ++ks)
+      umma_bf16(S.tmem, umma_desc(S.xh + 256 * ks, kNH * 16), umma_desc(S.w + 2 * kUW2 + 256 * ks, kNH * 16), i64, 1);
+    umma_commit(S.bar);
+  }
+  mma_wait(S);
+  tmem_ld64(S.tmem + lane, a);
+  store_hidden_row(xh, tid, a);
+  sync_for_mma(S.barid);
+  if (tid == 0 && S.ok) {
+    umma_bf16(S.tmem, umma_desc(S.one, 256), umma_desc(S.w + 2 * kUB3, 256), i16, 0);
+#pragma unroll
+    for (int ks = 0; ks < kNH / 16; ++ks)
+      umma_bf16(S.tmem, umma_desc(S.xh + 256 * ks, kNH * 16), umma_desc(S.w + 2 * kUW3 + 256 * ks, kNH * 16), i16, 1);
+    umma_commit(S.bar);
+  }
+  mma_wait(S);
+  uint32_t o[16];
+  tmem_ld16(S.tmem + lane, o);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) y[k] = __uint_as_float(o[k]);
 }
 
 // Y = network(X) on CUDA cores, one thread per row.
@@ -174,253 +300,162 @@ __global__ void k_mlp_forward32(int64_t S, const float* __restrict__ w, int64_t 
   for (int o = 0; o < NLOC; ++o) Y[s * NLOC + o] = y[o];
 }
 
-// The same with the layer-1 input fragments loaded from a 16-row tile Xs (row stride kS1 halves).
-__device__ __forceinline__ void mlp_tile_bf16(const __nv_bfloat16* __restrict__ Xs,
-                                              const __nv_bfloat16* __restrict__ W1b,
-                                              const __nv_bfloat16* __restrict__ W2b,
-                                              const __nv_bfloat16* __restrict__ W3b,
-                                              const float* __restrict__ bias, float (&out)[2][4]) {
-  const int lane = threadIdx.x & 31, r8 = lane & 7, mm = lane >> 3;
-  uint32_t a1[2][4];
-#pragma unroll
-  for (int ks = 0; ks < 2; ++ks) ldsm_x4(a1[ks], Xs + (r8 + 8 * (mm & 1)) * kS1 + 16 * ks + 8 * (mm >> 1));
-  mlp_tile_bf16(a1, W1b, W2b, W3b, bias, out);
-}
-
-// Two floats as a packed BF16 pair (lo in the low half), round to nearest even.
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<const uint32_t*>(&v);
-}
-
-// Y = network(X) on the tensor cores (BF16), one warp per 16 rows.
+// Y = network(X) on the tensor cores (tcgen05, BF16 operands, FP32 accumulation), 128 rows per tile; the CTAs
+// take tiles blockIdx.x, + gridDim.x, ...  A bounded wait that gave up sets MK_FAULT_TC_WAIT in *fault.
 template <int NLOC>
-__global__ void __launch_bounds__(256) k_mlp_forward16(int64_t S, const __nv_bfloat16* __restrict__ wb,
-                                                      const float* __restrict__ bias, const float* __restrict__ X,
-                                                      float* __restrict__ Y) {
+__global__ void __launch_bounds__(kTcRows) k_mlp_forward_tc(int64_t S, const __nv_bfloat16* __restrict__ wu,
+                                                           const float* __restrict__ X, float* __restrict__ Y,
+                                                           int* __restrict__ fault) {
   constexpr int NIN = NLOC + 12;
-  __shared__ __align__(16) __nv_bfloat16 wsm[kWbHalves];
-  __shared__ float bsm[kBias];
-  __shared__ __align__(16) __nv_bfloat16 xt[8][16 * kS1];
-  for (int k = threadIdx.x; k < kWbHalves; k += blockDim.x) wsm[k] = wb[k];
-  for (int k = threadIdx.x; k < kBias; k += blockDim.x) bsm[k] = bias[k];
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t tile = (int64_t)blockIdx.x * 8 + warp;
-  if (tile * 16 >= S) return;
-  __nv_bfloat16* Xs = xt[warp];
-  {
-    const int i = lane & 15, half = lane >> 4;
-    const int64_t row = tile * 16 + i;
-    for (int k = half * 16; k < half * 16 + 16; ++k) {
-      const int f = tile_feature(k, NLOC);
-      Xs[i * kS1 + k] = __float2bfloat16_rn((row < S && f >= 0) ? X[row * NIN + f] : 0.f);
-    }
+  __shared__ __align__(128) __nv_bfloat16 wsm[kWuHalves];
+  __shared__ __align__(128) __nv_bfloat16 xh[kTcRows * kNH];
+  __shared__ __align__(128) __nv_bfloat16 one[kTcRows * 16];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t slot;
+  for (int k = threadIdx.x; k < kWuHalves / 8; k += blockDim.x) cp_async16(wsm + 8 * k, wu + 8 * k);
+  tc_setup(&slot, kTmemCols, &bar, 1, one);
+  cp_async_wait_all();
+  sync_for_mma(0);
+  TcState st{slot, smem_u32(xh), smem_u32(wsm), smem_u32(one), &bar, 0, 0u, true};
+  const int64_t ntiles = (S + kTcRows - 1) / kTcRows;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t row = t * kTcRows + threadIdx.x;
+    const bool valid = row < S;
+    float f[kK1];
+#pragma unroll
+    for (int k = 0; k < kK1; ++k)
+      f[k] = k < NIN ? (valid ? X[row * NIN + k] : 0.f) : (k == kKOne || k == kKOne + 1) ? 1.f : 0.f;
+    store_input_row(xh, threadIdx.x, f);
+    float y[16];
+    umma_mlp_tile(st, xh, y);
+    if (valid)
+#pragma unroll
+      for (int o = 0; o < NLOC; ++o) Y[row * NLOC + o] = y[o];
   }
-  __syncwarp();
-  float out[2][4];
-  mlp_tile_bf16(Xs, wsm, wsm + kNH * kS1, wsm + kNH * kS1 + kNH * kS2, bsm, out);
-  const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-  for (int hr = 0; hr < 2; ++hr) {
-    const int64_t row = tile * 16 + g + 8 * hr;
-    if (row >= S) continue;
-#pragma unroll
-    for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int o = nt * 8 + 2 * t + q;
-        if (o < NLOC) Y[row * NLOC + o] = out[nt][2 * hr + q];
-      }
-  }
+  tc_teardown(slot, kTmemCols);
+  if (!st.ok) atomicOr(fault, MK_FAULT_TC_WAIT);
 }
 
-// BF16 copy of the parameters in the padded tensor-core layout, FP32 biases.
-__global__ void k_mlp_pack(const float* __restrict__ w, int nin, int nout, __nv_bfloat16* __restrict__ wb,
-                           float* __restrict__ bias) {
+// The BF16 copy of the parameters in the tcgen05 layout (kUW1 ... kUB3), one element per thread.
+__global__ void k_mlp_pack_umma(const float* __restrict__ w, int nin, int nout, __nv_bfloat16* __restrict__ wu) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kWuHalves) return;
   const float* W1 = w;
   const float* b1 = W1 + kNH * nin;
   const float* W2 = b1 + kNH;
   const float* b2 = W2 + kNH * kNH;
   const float* W3 = b2 + kNH;
   const float* b3 = W3 + nout * kNH;
-  if (i < kNH * kS1) {
-    const int u = i / kS1, k = i % kS1;
-    const int f = k < kK1 ? tile_feature(k, nin - 12) : -1;
-    wb[i] = __float2bfloat16_rn(f >= 0 ? W1[u * nin + f] : 0.f);
-  } else if (i < kNH * kS1 + kNH * kS2) {
-    const int j = i - kNH * kS1, u = j / kS2, k = j % kS2;
-    wb[i] = __float2bfloat16_rn(k < kNH ? W2[u * kNH + k] : 0.f);
-  } else if (i < kWbHalves) {
-    const int j = i - kNH * kS1 - kNH * kS2, o = j / kS2, k = j % kS2;
-    wb[i] = __float2bfloat16_rn((o < nout && k < kNH) ? W3[o * kNH + k] : 0.f);
+  // value v at (row, k) of a matrix with K columns starting at base; bias parts: high = bf16(b), low = bf16(b - high)
+  auto bias_part = [](float b, int k) -> float {
+    const float hi = __bfloat162float(__float2bfloat16_rn(b));
+    return k == 0 ? hi : k == 1 ? b - hi : 0.f;
+  };
+  int base, row, k, K;
+  float v;
+  if (i < kUW2) {
+    base = kUW1, K = kK1, row = (i - base) / K, k = (i - base) % K;
+    v = k < nin ? W1[row * nin + k] : (k == kKOne || k == kKOne + 1) ? bias_part(b1[row], k - kKOne) : 0.f;
+  } else if (i < kUW3) {
+    base = kUW2, K = kNH, row = (i - base) / K, k = (i - base) % K;
+    v = W2[row * kNH + k];
+  } else if (i < kUB2) {
+    base = kUW3, K = kNH, row = (i - base) / K, k = (i - base) % K;
+    v = row < nout ? W3[row * kNH + k] : 0.f;
+  } else if (i < kUB3) {
+    base = kUB2, K = 16, row = (i - base) / K, k = (i - base) % K;
+    v = bias_part(b2[row], k);
+  } else {
+    base = kUB3, K = 16, row = (i - base) / K, k = (i - base) % K;
+    v = row < nout ? bias_part(b3[row], k) : 0.f;
   }
-  if (i < kBias) bias[i] = i < kNH ? b1[i] : i < 2 * kNH ? b2[i - kNH] : (i - 2 * kNH < nout ? b3[i - 2 * kNH] : 0.f);
+  wu[base + umma_off(row, k, K)] = __float2bfloat16_rn(v);
 }
 
 // ------------------------------------------------------------------------------------------------ preconditioner
 struct LearnSmem {
-  size_t ye, rs, conn, inc, ioff, tgt, geo, w, gb, total;
+  size_t ye, rs, conn, inc, ioff, tgt, geo, w, xh, one, total;
 };
-__host__ __device__ inline LearnSmem learn_smem(int nloc, int pe, int max_nodes, bool tc, int64_t count, int nwarps) {
+constexpr int kTcGroups = 2;  // warpgroups (tiles in flight) per CTA of the tensor-core patch kernel
+
+// tc: the tensor-core kernel (network outputs in BF16, packed BF16 weights, one activation tile per warpgroup, the
+// all-ones tile); otherwise FP32 outputs and the FP32 parameters (count floats)
+__host__ __device__ inline LearnSmem learn_smem(int nloc, int pe, int max_nodes, bool tc, int64_t count) {
   LearnSmem L;
   L.ye = 0;
-  L.rs = L.ye + align16((size_t)nloc * pe * kLW * 4);                 // residual rows of the local nodes
+  L.rs = L.ye + align16((size_t)nloc * pe * kLW * (tc ? 2 : 4));      // residual rows of the local nodes
   L.conn = L.rs + align16((size_t)max_nodes * kLW * 4);              // local node of each element slot (uint16)
   L.inc = L.conn + align16((size_t)pe * nloc * 2 + 16);
   L.ioff = L.inc + align16((size_t)pe * nloc * 2 + 16);
   L.tgt = L.ioff + align16((size_t)(max_nodes + 1) * 4 + 16);
   L.geo = L.tgt + align16((size_t)max_nodes * 4 + 16);
   L.w = L.geo + align16((size_t)pe * 16 * 4 + 16);
-  const size_t wbytes = tc ? (size_t)kWbHalves * 2 + 16 + (size_t)kBias * 4 + 16 : (size_t)count * 4 + 16;
-  L.gb = L.w + align16(wbytes);                                        // BF16 geometry table [element][16]
-  L.total = L.gb + (tc ? align16((size_t)pe * 16 * 2) : 0);
+  L.xh = L.w + align16(tc ? (size_t)kWuHalves * 2 + 16 : (size_t)count * 4 + 16);
+  L.one = L.xh + (tc ? (size_t)kTcGroups * kTcRows * kNH * 2 : 0);
+  L.total = L.one + (tc ? (size_t)kTcRows * 16 * 2 : 0);
   return L;
 }
 
-// One patch per CTA (the patches of the operator apply).  Phase 1: the network on every (element, column) row
-// of the patch, scaled by s / h_e, into shared memory [slot][element][column]; on the tensor cores (TC) one
-// warp takes 16 rows at a time (the layer-1 fragments built in registers, see tile_feature), otherwise one
-// thread per row in FP32.  Phase 2: per local node the incidences
-// in fixed order, then z = sum / multiplicity + r / diag (owned nodes) or the partial sum to the node's halo
-// slot (shared nodes, finished by k_learned_halo).  Columns [col0, col0 + Nw), Nw = min(kLW, N - col0).
-template <int NLOC, bool TC>
-__global__ void __launch_bounds__(256, 2) k_learned_patch(
-    const int32_t* __restrict__ elem_off, const int32_t* __restrict__ node_off, const uint16_t* __restrict__ lconn,
-    const int32_t* __restrict__ node_gid, const int32_t* __restrict__ target, const int32_t* __restrict__ inc_off,
-    const uint16_t* __restrict__ inc,
-    const float* __restrict__ geomf, const void* __restrict__ wsrc, const float* __restrict__ bias, int64_t count,
-    const float* __restrict__ dinv, const float* __restrict__ inv_mult, const uint8_t* __restrict__ bnd,
-    const float* __restrict__ r, float* __restrict__ z, float* __restrict__ halo, int N, int col0, int ld, int pe,
-    int max_nodes) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int nwarps = blockDim.x >> 5;
-  const LearnSmem lay = learn_smem(NLOC, pe, max_nodes, TC, count, nwarps);
-  float* Ye = reinterpret_cast<float*>(smraw + lay.ye);
-  const int p = blockIdx.x;
-  const int e0 = elem_off[p], ne = elem_off[p + 1] - e0;
-  const int n0 = node_off[p], nl = node_off[p + 1] - n0;
-  const int ibase = e0 * NLOC;
-  const int Nw = min(kLW, N - col0);
-  const uint16_t* cs = stage_async(smraw + lay.conn, lconn + ibase, ne * NLOC * 2);
+// The patch's data in shared memory (cp.async, not yet waited for).
+struct LearnPatch {
+  int e0, ne, n0, nl, ibase, Nw;
+  const uint16_t *cs, *is;
+  const int32_t *os, *ts;
+  const float *gs, *rs;
+  const unsigned char* wsm;
+};
+template <int NLOC>
+__device__ __forceinline__ LearnPatch learn_stage(unsigned char* smraw, const LearnSmem& lay, int p,
+                                                  const int32_t* __restrict__ elem_off,
+                                                  const int32_t* __restrict__ node_off,
+                                                  const uint16_t* __restrict__ lconn,
+                                                  const int32_t* __restrict__ node_gid,
+                                                  const int32_t* __restrict__ target,
+                                                  const int32_t* __restrict__ inc_off,
+                                                  const uint16_t* __restrict__ inc, const float* __restrict__ geomf,
+                                                  const void* __restrict__ wsrc, int wbytes,
+                                                  const float* __restrict__ r, int N, int col0, int ld) {
+  LearnPatch P;
+  P.e0 = elem_off[p];
+  P.ne = elem_off[p + 1] - P.e0;
+  P.n0 = node_off[p];
+  P.nl = node_off[p + 1] - P.n0;
+  P.ibase = P.e0 * NLOC;
+  P.Nw = min(kLW, N - col0);
+  P.cs = stage_async(smraw + lay.conn, lconn + P.ibase, P.ne * NLOC * 2);
   // the residual rows of the patch's local nodes, columns [col0, col0 + 8) (16-byte copies; ld % 4 == 0)
   float* rs = reinterpret_cast<float*>(smraw + lay.rs);
   const int nvec = min(kLW, ld - col0) / 4;
-  for (int l = threadIdx.x; l < nl; l += blockDim.x) {
-    const float* src = r + (int64_t)node_gid[n0 + l] * ld + col0;
+  for (int l = threadIdx.x; l < P.nl; l += blockDim.x) {
+    const float* src = r + (int64_t)node_gid[P.n0 + l] * ld + col0;
     for (int v = 0; v < nvec; ++v) cp_async16(rs + l * kLW + 4 * v, src + 4 * v);
   }
-  const uint16_t* is = stage_async(smraw + lay.inc, inc + ibase, ne * NLOC * 2);
-  const int32_t* os = stage_async(smraw + lay.ioff, inc_off + n0, (nl + 1) * 4);
-  const int32_t* ts = stage_async(smraw + lay.tgt, target + n0, nl * 4);
-  const float* gs = stage_async(smraw + lay.geo, geomf + (int64_t)e0 * 16, ne * 16 * 4);
-  const unsigned char* wsm;
-  const float* bsm = nullptr;
-  if constexpr (TC) {
-    wsm = stage_async(smraw + lay.w, reinterpret_cast<const unsigned char*>(wsrc), kWbHalves * 2);
-    bsm = stage_async(smraw + lay.w + align16((size_t)kWbHalves * 2 + 16), bias, kBias * 4);
-  } else {
-    wsm = stage_async(smraw + lay.w, reinterpret_cast<const unsigned char*>(wsrc), (int)(count * 4));
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  const int nrows = ne * Nw;
-  if constexpr (TC) {
-    // the geometry features of the patch's elements in BF16, one 32-byte row per element (columns 12-15 zero)
-    __nv_bfloat16* gbw = reinterpret_cast<__nv_bfloat16*>(smraw + lay.gb);
-    for (int i = threadIdx.x; i < ne * 8; i += blockDim.x) {
-      const int el = i >> 3, c = 2 * (i & 7);
-      reinterpret_cast<uint32_t*>(gbw)[i] =
-          pack_bf16(c < 12 ? gs[el * 16 + 1 + c] : 0.f, c + 1 < 12 ? gs[el * 16 + 2 + c] : 0.f);
-    }
-    __syncthreads();
-    const __nv_bfloat16* gbt = gbw;
-    const __nv_bfloat16* W1b = reinterpret_cast<const __nv_bfloat16*>(wsm);
-    const __nv_bfloat16* W2b = W1b + kNH * kS1;
-    const __nv_bfloat16* W3b = W2b + kNH * kS2;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, t = lane & 3, r8 = lane & 7, mm = lane >> 3;
-    constexpr int H = NLOC / 2;
-    const int fa = 2 * t, fb = 2 * t + 1;  // this lane's residual features fa, fb, H + fa, H + fb (those < H)
-    // row / Nw as (row * ceil(2^16 / Nw)) >> 16: the ceiling adds less than row / 2^16, which stays below 1 / Nw
-    // for row < 2^16 / Nw (8,192 for Nw = 8; a patch has at most 512 * 8 rows), so the quotient is exact
-    const unsigned mnw = (65536u + (unsigned)Nw - 1u) / (unsigned)Nw;
-    for (int tile = warp; tile * 16 < nrows; tile += nwarps) {
-      uint32_t a1[2][4];
-      int el[2], jj[2];
-      float sc[2];
-#pragma unroll
-      for (int hr = 0; hr < 2; ++hr) {  // rows g and g + 8 of the tile
-        const int row = tile * 16 + g + 8 * hr;
-        const bool valid = row < nrows;
-        const int e = valid ? (int)(((unsigned)row * mnw) >> 16) : 0;
-        el[hr] = e;
-        jj[hr] = valid ? row - e * Nw : 0;
-        const uint16_t* ce = cs + e * NLOC;
-        const float* rj = rs + jj[hr];
-        const float v0 = (valid && fa < H) ? rj[ce[fa] * kLW] : 0.f;
-        const float v1 = (valid && fb < H) ? rj[ce[fb] * kLW] : 0.f;
-        const float v2 = (valid && fa < H) ? rj[ce[H + fa] * kLW] : 0.f;
-        const float v3 = (valid && fb < H) ? rj[ce[H + fb] * kLW] : 0.f;
-        float ss = fmaf(v3, v3, fmaf(v2, v2, fmaf(v1, v1, v0 * v0)));
-        ss += __shfl_xor_sync(0xffffffffu, ss, 1);  // the row's four lanes hold all its features
-        ss += __shfl_xor_sync(0xffffffffu, ss, 2);
-        const float s = sqrtf(ss);
-        const float inv = s > 0.f ? 1.f / s : 0.f;
-        a1[0][hr] = pack_bf16(v0 * inv, v1 * inv);      // k = 2t, 2t+1
-        a1[0][2 + hr] = pack_bf16(v2 * inv, v3 * inv);  // k = 8 + 2t, 8 + 2t + 1
-        sc[hr] = valid ? s / gs[e * 16] : 0.f;
-      }
-      {  // geometry k-step: matrix mm holds rows (mm & 1) * 8 .. + 7, columns 16 + 8 * (mm >> 1) .. + 7
-        const int row = tile * 16 + r8 + 8 * (mm & 1);
-        const int e = row < nrows ? (int)(((unsigned)row * mnw) >> 16) : 0;
-        ldsm_x4(a1[1], gbt + e * 16 + 8 * (mm >> 1));
-      }
-      float out[2][4];
-      mlp_tile_bf16(a1, W1b, W2b, W3b, bsm, out);
-#pragma unroll
-      for (int hr = 0; hr < 2; ++hr) {
-        if (tile * 16 + g + 8 * hr < nrows) {
-#pragma unroll
-          for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-              const int o = nt * 8 + 2 * t + q;
-              if (o < NLOC) Ye[((size_t)o * pe + el[hr]) * kLW + jj[hr]] = out[nt][2 * hr + q] * sc[hr];
-            }
-        }
-      }
-    }
-  } else {
-    const float* wf = reinterpret_cast<const float*>(wsm);
-    for (int row = threadIdx.x; row < nrows; row += blockDim.x) {
-      const int el = row / Nw, jj = row - el * Nw;
-      float x[NLOC + 12], y[NLOC], ss = 0.f;
-#pragma unroll
-      for (int a = 0; a < NLOC; ++a) {
-        x[a] = rs[cs[el * NLOC + a] * kLW + jj];
-        ss = fmaf(x[a], x[a], ss);
-      }
-      const float s = sqrtf(ss);
-      const float inv = s > 0.f ? 1.f / s : 0.f;
-#pragma unroll
-      for (int a = 0; a < NLOC; ++a) x[a] *= inv;
-#pragma unroll
-      for (int k = 0; k < 12; ++k) x[NLOC + k] = gs[el * 16 + 1 + k];
-      mlp_row32<NLOC>(wf, x, y);
-      const float sc = s / gs[el * 16];
-#pragma unroll
-      for (int o = 0; o < NLOC; ++o) Ye[((size_t)o * pe + el) * kLW + jj] = y[o] * sc;
-    }
-  }
-  __syncthreads();
-  for (int it = threadIdx.x; it < nl * Nw; it += blockDim.x) {
+  P.rs = rs;
+  P.is = stage_async(smraw + lay.inc, inc + P.ibase, P.ne * NLOC * 2);
+  P.os = stage_async(smraw + lay.ioff, inc_off + P.n0, (P.nl + 1) * 4);
+  P.ts = stage_async(smraw + lay.tgt, target + P.n0, P.nl * 4);
+  P.gs = stage_async(smraw + lay.geo, geomf + (int64_t)P.e0 * 16, P.ne * 16 * 4);
+  P.wsm = stage_async(smraw + lay.w, reinterpret_cast<const unsigned char*>(wsrc), wbytes);
+  return P;
+}
+
+// Phase 2 of the patch kernels: per local node the incidences in fixed order (FP32 sums), then z = sum /
+// multiplicity + r / diag (owned nodes) or the partial sum to the node's halo slot (shared nodes, finished by
+// k_learned_halo).
+__device__ __forceinline__ float ye_value(float v) { return v; }
+__device__ __forceinline__ float ye_value(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename YT>
+__device__ __forceinline__ void learn_assemble(const LearnPatch& P, const YT* __restrict__ Ye,
+                                               const float* __restrict__ dinv, const float* __restrict__ inv_mult,
+                                               const float* __restrict__ r, float* __restrict__ z,
+                                               float* __restrict__ halo, int col0, int ld) {
+  const int Nw = P.Nw;
+  for (int it = threadIdx.x; it < P.nl * Nw; it += blockDim.x) {
     const int l = it / Nw, jj = it - l * Nw;
-    const int b = os[l] - ibase, e = os[l + 1] - ibase;
+    const int b = P.os[l] - P.ibase, e = P.os[l + 1] - P.ibase;
     float acc = 0.f;
-    for (int k = b; k < e; ++k) acc += Ye[(size_t)is[k] * kLW + jj];
-    const int tg = ts[l];
+    for (int k = b; k < e; ++k) acc += ye_value(Ye[(size_t)P.is[k] * kLW + jj]);
+    const int tg = P.ts[l];
     if (tg >= 0) {
       const int nd = tg & (kOwnedBoundary - 1);
       const int64_t t = (int64_t)nd * ld + col0 + jj;
@@ -429,6 +464,111 @@ __global__ void __launch_bounds__(256, 2) k_learned_patch(
       halo[(int64_t)(-tg - 1) * ld + col0 + jj] = acc;
     }
   }
+}
+
+// One patch per CTA (the patches of the operator apply), the network in FP32 on CUDA cores, one thread per
+// (element, column) row: phase 1 writes network(x) * s / h_e into shared memory [slot][element][column], phase 2
+// assembles.  Columns [col0, col0 + Nw), Nw = min(kLW, N - col0).
+template <int NLOC>
+__global__ void __launch_bounds__(256, 2) k_learned_patch(
+    const int32_t* __restrict__ elem_off, const int32_t* __restrict__ node_off, const uint16_t* __restrict__ lconn,
+    const int32_t* __restrict__ node_gid, const int32_t* __restrict__ target, const int32_t* __restrict__ inc_off,
+    const uint16_t* __restrict__ inc, const float* __restrict__ geomf, const float* __restrict__ w, int64_t count,
+    const float* __restrict__ dinv, const float* __restrict__ inv_mult, const float* __restrict__ r,
+    float* __restrict__ z, float* __restrict__ halo, int N, int col0, int ld, int pe, int max_nodes) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const LearnSmem lay = learn_smem(NLOC, pe, max_nodes, false, count);
+  float* Ye = reinterpret_cast<float*>(smraw + lay.ye);
+  const LearnPatch P = learn_stage<NLOC>(smraw, lay, blockIdx.x, elem_off, node_off, lconn, node_gid, target, inc_off,
+                                         inc, geomf, w, (int)(count * 4), r, N, col0, ld);
+  cp_async_wait_all();
+  __syncthreads();
+  const int Nw = P.Nw, nrows = P.ne * Nw;
+  const float* wf = reinterpret_cast<const float*>(P.wsm);
+  for (int row = threadIdx.x; row < nrows; row += blockDim.x) {
+    const int el = row / Nw, jj = row - el * Nw;
+    float x[NLOC + 12], y[NLOC], ss = 0.f;
+#pragma unroll
+    for (int a = 0; a < NLOC; ++a) {
+      x[a] = P.rs[P.cs[el * NLOC + a] * kLW + jj];
+      ss = fmaf(x[a], x[a], ss);
+    }
+    const float s = sqrtf(ss);
+    const float inv = s > 0.f ? 1.f / s : 0.f;
+#pragma unroll
+    for (int a = 0; a < NLOC; ++a) x[a] *= inv;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) x[NLOC + k] = P.gs[el * 16 + 1 + k];
+    mlp_row32<NLOC>(wf, x, y);
+    const float sc = s / P.gs[el * 16];
+#pragma unroll
+    for (int o = 0; o < NLOC; ++o) Ye[((size_t)o * pe + el) * kLW + jj] = y[o] * sc;
+  }
+  __syncthreads();
+  learn_assemble(P, Ye, dinv, inv_mult, r, z, halo, col0, ld);
+}
+
+// The same with the network on the tensor cores (tcgen05, BF16 operands, FP32 accumulation in TMEM): kTcGroups
+// warpgroups, warpgroup g taking the tiles g, g + kTcGroups, ... of 128 (element, column) rows with its own
+// activation tile, mbarrier, named barrier and kTmemCols TMEM columns, so that kTcGroups tiles are in flight per
+// CTA.  One row per thread: it gathers and normalises its residual features, adds the element's geometry and the
+// bias inputs, and scales its outputs, stored in BF16 (the precision of the network).  A bounded wait that gave up
+// sets MK_FAULT_TC_WAIT in *fault (outputs invalid).
+template <int NLOC>
+__global__ void __launch_bounds__(kTcGroups * kTcRows, 2) k_learned_patch_tc(
+    const int32_t* __restrict__ elem_off, const int32_t* __restrict__ node_off, const uint16_t* __restrict__ lconn,
+    const int32_t* __restrict__ node_gid, const int32_t* __restrict__ target, const int32_t* __restrict__ inc_off,
+    const uint16_t* __restrict__ inc, const float* __restrict__ geomf, const __nv_bfloat16* __restrict__ wu,
+    const float* __restrict__ dinv, const float* __restrict__ inv_mult, const float* __restrict__ r,
+    float* __restrict__ z, float* __restrict__ halo, int N, int col0, int ld, int pe, int max_nodes,
+    int* __restrict__ fault) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ uint64_t bars[kTcGroups];
+  __shared__ uint32_t slot;
+  const LearnSmem lay = learn_smem(NLOC, pe, max_nodes, true, 0);
+  __nv_bfloat16* Ye = reinterpret_cast<__nv_bfloat16*>(smraw + lay.ye);
+  const int g = threadIdx.x / kTcRows, tid = threadIdx.x & (kTcRows - 1);
+  __nv_bfloat16* xh = reinterpret_cast<__nv_bfloat16*>(smraw + lay.xh) + g * kTcRows * kNH;
+  __nv_bfloat16* one = reinterpret_cast<__nv_bfloat16*>(smraw + lay.one);
+  const LearnPatch P = learn_stage<NLOC>(smraw, lay, blockIdx.x, elem_off, node_off, lconn, node_gid, target, inc_off,
+                                         inc, geomf, wu, kWuHalves * 2, r, N, col0, ld);
+  tc_setup(&slot, kTcGroups * kTmemCols, bars, kTcGroups, one);
+  cp_async_wait_all();
+  sync_for_mma(0);
+  TcState st{slot + g * kTmemCols, smem_u32(xh), smem_u32(P.wsm), smem_u32(one), bars + g, 1 + g, 0u, true};
+  const int Nw = P.Nw, nrows = P.ne * Nw;
+  // row / Nw as (row * ceil(2^16 / Nw)) >> 16: the ceiling adds less than row / 2^16, which stays below 1 / Nw
+  // for row < 2^16 / Nw (8,192 for Nw = 8; a patch has at most 512 * 8 rows), so the quotient is exact
+  const unsigned mnw = (65536u + (unsigned)Nw - 1u) / (unsigned)Nw;
+  for (int tile = g; tile * kTcRows < nrows; tile += kTcGroups) {
+    const int row = tile * kTcRows + tid;
+    const bool valid = row < nrows;
+    const int el = valid ? (int)(((unsigned)row * mnw) >> 16) : 0, jj = valid ? row - el * Nw : 0;
+    float f[kK1], ss = 0.f;
+#pragma unroll
+    for (int a = 0; a < NLOC; ++a) {
+      f[a] = valid ? P.rs[P.cs[el * NLOC + a] * kLW + jj] : 0.f;
+      ss = fmaf(f[a], f[a], ss);
+    }
+    const float s = sqrtf(ss);
+    const float inv = s > 0.f ? 1.f / s : 0.f;
+#pragma unroll
+    for (int a = 0; a < NLOC; ++a) f[a] *= inv;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) f[NLOC + k] = P.gs[el * 16 + 1 + k];
+#pragma unroll
+    for (int k = NLOC + 12; k < kK1; ++k) f[k] = (k == kKOne || k == kKOne + 1) ? 1.f : 0.f;
+    const float sc = valid ? s / P.gs[el * 16] : 0.f;
+    store_input_row(xh, tid, f);
+    float y[16];
+    umma_mlp_tile(st, xh, y);
+    if (valid)
+#pragma unroll
+      for (int o = 0; o < NLOC; ++o) Ye[((size_t)o * pe + el) * kLW + jj] = __float2bfloat16_rn(y[o] * sc);
+  }
+  tc_teardown(slot, kTcGroups * kTmemCols);  // its CTA barrier also completes Ye
+  if (!st.ok) atomicOr(fault, MK_FAULT_TC_WAIT);
+  learn_assemble(P, Ye, dinv, inv_mult, r, z, halo, col0, ld);
 }
 
 // Shared nodes: z = (sum of the node's halo slots in patch order) / multiplicity + r / diag.
@@ -458,28 +598,31 @@ int learned_apply(mk_ctx* ctx, const mk_mesh* m, const mk_mlp* mlp, const float*
   float* halo = (float*)scratch(ctx, S_LHALO, (size_t)std::max<int64_t>(P.n_halo_slots, 1) * ld * sizeof(float), &err);
   if (!halo) return err;
   const bool tc = precision == MK_MLP_BF16;
-  const int th = 256;
-  const LearnSmem lay = learn_smem(L.nloc, P.max_elems, P.max_nodes, tc, mlp->count, th / 32);
-  MK_ARG(lay.total <= 227 * 1024, "learned preconditioner: patch too large for shared memory");
-  const void* wsrc = tc ? mlp->d_wb : (const void*)mlp->d_w;
+  const LearnSmem lay = learn_smem(L.nloc, P.max_elems, P.max_nodes, tc, mlp->count);
+  MK_ARG(lay.total <= 227 * 1024 - 256, "learned preconditioner: patch too large for shared memory");
+  MK_ARG(((uintptr_t)mlp->d_wb & 15) == 0, "learned preconditioner: packed weights not 16-byte aligned");
   for (int col0 = 0; col0 < N; col0 += kLW) {
     const int Nw = std::min(kLW, N - col0);
-#define MK_LEARN_LAUNCH(NL, TCV)                                                                                   \
-  do {                                                                                                            \
-    auto kern = k_learned_patch<NL, TCV>;                                                                         \
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);                     \
-    MK_COUNT(), kern<<<P.n_patches, th, lay.total, s>>>(P.d_patch_elem_off, P.d_patch_node_off, P.d_lconn,        \
-                                                        P.d_node_gid, P.d_node_target, P.d_inc_off, P.d_inc,      \
-                                                        P.d_geomf, wsrc,                                          \
-                                                        mlp->d_bias, mlp->count, dinv, P.d_inv_mult, L.d_boundary, \
-                                                        r, z, halo, N, col0, ld, P.max_elems, P.max_nodes);       \
-  } while (0)
+    const __nv_bfloat16* wu = (const __nv_bfloat16*)mlp->d_wb;
+    auto launch_tc = [&](auto kern) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
+      MK_COUNT(), kern<<<P.n_patches, kTcGroups * kTcRows, lay.total, s>>>(
+          P.d_patch_elem_off, P.d_patch_node_off, P.d_lconn, P.d_node_gid, P.d_node_target, P.d_inc_off, P.d_inc,
+          P.d_geomf, wu, dinv, P.d_inv_mult, r, z, halo, N, col0, ld, P.max_elems, P.max_nodes, ctx->d_fault);
+    };
+    auto launch_fp32 = [&](auto kern) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
+      MK_COUNT(), kern<<<P.n_patches, 256, lay.total, s>>>(
+          P.d_patch_elem_off, P.d_patch_node_off, P.d_lconn, P.d_node_gid, P.d_node_target, P.d_inc_off, P.d_inc,
+          P.d_geomf, mlp->d_w, mlp->count, dinv, P.d_inv_mult, r, z, halo, N, col0, ld, P.max_elems, P.max_nodes);
+    };
     if (L.nloc == 4) {
-      if (tc) MK_LEARN_LAUNCH(4, true); else MK_LEARN_LAUNCH(4, false);
+      if (tc) launch_tc(k_learned_patch_tc<4>);
+      else launch_fp32(k_learned_patch<4>);
     } else {
-      if (tc) MK_LEARN_LAUNCH(10, true); else MK_LEARN_LAUNCH(10, false);
+      if (tc) launch_tc(k_learned_patch_tc<10>);
+      else launch_fp32(k_learned_patch<10>);
     }
-#undef MK_LEARN_LAUNCH
     const int64_t work = P.n_shared_nodes * Nw;
     if (work > 0)
       MK_COUNT(), k_learned_halo<<<(int)((work + 255) / 256), 256, 0, s>>>(P.n_shared_nodes, P.d_shared_node,
@@ -712,8 +855,8 @@ __global__ void k_harvest(int64_t E, const Geom* __restrict__ geom, const int32_
 }
 
 static int mlp_pack(const mk_mlp* mlp, cudaStream_t s) {
-  MK_COUNT(), k_mlp_pack<<<(kWbHalves + 255) / 256, 256, 0, s>>>(mlp->d_w, mlp->nin, mlp->nout,
-                                                                   (__nv_bfloat16*)mlp->d_wb, mlp->d_bias);
+  MK_COUNT(), k_mlp_pack_umma<<<(kWuHalves + 255) / 256, 256, 0, s>>>(mlp->d_w, mlp->nin, mlp->nout,
+                                                                        (__nv_bfloat16*)mlp->d_wb);
   MK_CUDA(cudaGetLastError());
   return MK_OK;
 }
@@ -742,8 +885,7 @@ int mk_mlp_create(mk_ctx* ctx, int nloc, const float* params, mk_mlp** out) {
   m->count = mlp_count(m->nin, m->nout);
   const size_t b = (size_t)m->count * sizeof(float);
   if (cudaMalloc(&m->d_w, b) != cudaSuccess || cudaMalloc(&m->d_m, b) != cudaSuccess ||
-      cudaMalloc(&m->d_v, b) != cudaSuccess || cudaMalloc(&m->d_wb, (size_t)kWbHalves * 2) != cudaSuccess ||
-      cudaMalloc(&m->d_bias, (size_t)kBias * 4) != cudaSuccess) {
+      cudaMalloc(&m->d_v, b) != cudaSuccess || cudaMalloc(&m->d_wb, (size_t)kWuHalves * 2) != cudaSuccess) {
     cudaGetLastError();
     mk_mlp_destroy(m);
     return fail(MK_ERR_OOM, "mk_mlp_create: allocation failed");
@@ -764,7 +906,6 @@ int mk_mlp_destroy(mk_mlp* m) {
   cudaFree(m->d_m);
   cudaFree(m->d_v);
   cudaFree(m->d_wb);
-  cudaFree(m->d_bias);
   delete m;
   return MK_OK;
 }
@@ -808,11 +949,13 @@ int mk_mlp_forward(mk_ctx* ctx, const mk_mlp* m, const float* X, int64_t S, floa
       MK_COUNT(), k_mlp_forward32<10><<<blocks, 128, smem, s>>>(S, m->d_w, m->count, X, Y);
     }
   } else {
-    const int blocks = (int)((S + 127) / 128);  // 8 warps x 16 rows
+    // at most 2 CTAs per SM in the grid-stride loop; each holds kTmemCols of the SM's 512 TMEM columns
+    const int blocks = (int)std::min<int64_t>((S + kTcRows - 1) / kTcRows, 2 * (int64_t)ctx->n_sms);
+    const __nv_bfloat16* wu = (const __nv_bfloat16*)m->d_wb;
     if (m->nloc == 4)
-      MK_COUNT(), k_mlp_forward16<4><<<blocks, 256, 0, s>>>(S, (const __nv_bfloat16*)m->d_wb, m->d_bias, X, Y);
+      MK_COUNT(), k_mlp_forward_tc<4><<<blocks, kTcRows, 0, s>>>(S, wu, X, Y, ctx->d_fault);
     else
-      MK_COUNT(), k_mlp_forward16<10><<<blocks, 256, 0, s>>>(S, (const __nv_bfloat16*)m->d_wb, m->d_bias, X, Y);
+      MK_COUNT(), k_mlp_forward_tc<10><<<blocks, kTcRows, 0, s>>>(S, wu, X, Y, ctx->d_fault);
   }
   MK_CUDA(cudaGetLastError());
   return MK_OK;
