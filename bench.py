@@ -361,7 +361,7 @@ def main():
     for _ in range(a.steps):
         step()
     torch.cuda.synchronize()
-    prof = {k: mk.profile_read(ctx, k) for k in (mk.PROF_APPLY64, mk.PROF_APPLY32, mk.PROF_HALO)}
+    prof = {k: mk.profile_read(ctx, k) for k in (mk.PROF_APPLY64, mk.PROF_APPLY32, mk.PROF_HALO, mk.PROF_LEARNED)}
     mk.profile_enable(ctx, False)
 
     # end to end through the C ABI with host buffers: pinned psi_H in, eigenvalues, coefficients, orbitals out
@@ -495,6 +495,22 @@ def main():
                     "ms_per_application": iso_ms, "achieved": nbytes / (iso_ms * 1e-3) / 1e9,
                     "frac": nbytes / (iso_ms * 1e-3) / 1e9 / peak, "applications": 20}}
 
+    # the learned preconditioner's patch kernel (tcgen05 network + node sums): algorithmic network FLOPs of one
+    # application (2 (n_in 64 + 64 64 + 64 n_out) per (element, orbital) row) over its CUDA-event duration inside
+    # the steps, against the sustained BF16 tensor peak (the kernel runs inside a long step)
+    roof_tc = None
+    ms_l, n_l = prof[mk.PROF_LEARNED]
+    if n_l:
+        nin, nout = nloc + 12, nloc
+        lflops = 2.0 * (nin * 64 + 64 * 64 + 64 * nout) * E * N
+        lpeak = peaks.get("bf16_tflops_sustained", 1712.6)
+        lach = lflops / (ms_l / n_l * 1e-3) / 1e12
+        roof_tc = {"kernel": "k_learned_patch_tc (learned preconditioner: BF16 network on tcgen05 + node sums)",
+                   "bound": "tensor", "achieved": lach, "peak": lpeak, "unit": "TFLOP/s", "frac": lach / lpeak,
+                   "applications": n_l, "ms_per_application": ms_l / n_l, "flops_per_application": lflops,
+                   "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained, of measured",
+                   "note": "issue- and latency-bound on the per-tile layer chain, not on the tensor pipe"}
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         try:
@@ -521,7 +537,7 @@ def main():
             "e2e": {"value": float(n_free) * N * a.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "gpu_launches_per_step": launches / a.steps,
-            "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
+            "clocks": clk, "roofline": roof, "roofline_learned": roof_tc, "cpu_baseline": cpu,
             "compare": compare, "training": train_info, "batch": batch,
             "solve_iterations": solve["iterations"], "solve_max_rel_residual": solve["max_rel_residual"],
             "poisson_iterations": reps["poisson"]["iterations"] if reps["poisson"] else None,

@@ -143,7 +143,8 @@ long long mk_launch_count(void);
 /* Optional timing of the operator applications with CUDA events recorded on the launching stream (diagnostic, no
  * counterpart in the paper).  mk_profile_enable(ctx, 1) clears and starts recording; mk_profile_read waits for
  * the recorded events and returns the summed duration and the number of timed applications of kind
- * 0 = FP64 element-by-element apply, 1 = FP32 patch apply, 2 = FP32 halo sum. */
+ * 0 = FP64 element-by-element apply, 1 = FP32 patch apply, 2 = FP32 halo sum, 3 = learned-preconditioner patch
+ * kernel (the network and the node sums, without the halo pass). */
 int mk_profile_enable(mk_ctx* ctx, int on);
 int mk_profile_read(mk_ctx* ctx, int kind, double* total_ms, long long* count);
 

@@ -184,7 +184,7 @@ void prof_mark(mk_ctx* ctx, int kind, bool begin, cudaStream_t s);
 void prof_capture(mk_ctx* ctx, bool on);
 void prof_prepare_capture(mk_ctx* ctx);
 void prof_harvest(mk_ctx* ctx);
-enum ProfKind { PROF_APPLY64 = 0, PROF_APPLY32 = 1, PROF_HALO = 2, PROF_OTHER = 3 };
+enum ProfKind { PROF_APPLY64 = 0, PROF_APPLY32 = 1, PROF_HALO = 2, PROF_LEARNED = 3 };
 }  // namespace mk
 
 struct mk_mesh {

@@ -616,6 +616,7 @@ int learned_apply(mk_ctx* ctx, const mk_mesh* m, const mk_mlp* mlp, const float*
           P.d_patch_elem_off, P.d_patch_node_off, P.d_lconn, P.d_node_gid, P.d_node_target, P.d_inc_off, P.d_inc,
           P.d_geomf, mlp->d_w, mlp->count, dinv, P.d_inv_mult, r, z, halo, N, col0, ld, P.max_elems, P.max_nodes);
     };
+    prof_mark(ctx, PROF_LEARNED, true, s);
     if (L.nloc == 4) {
       if (tc) launch_tc(k_learned_patch_tc<4>);
       else launch_fp32(k_learned_patch<4>);
@@ -623,6 +624,7 @@ int learned_apply(mk_ctx* ctx, const mk_mesh* m, const mk_mlp* mlp, const float*
       if (tc) launch_tc(k_learned_patch_tc<10>);
       else launch_fp32(k_learned_patch<10>);
     }
+    prof_mark(ctx, PROF_LEARNED, false, s);
     const int64_t work = P.n_shared_nodes * Nw;
     if (work > 0)
       MK_COUNT(), k_learned_halo<<<(int)((work + 255) / 256), 256, 0, s>>>(P.n_shared_nodes, P.d_shared_node,

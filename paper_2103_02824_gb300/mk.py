@@ -164,7 +164,7 @@ def ctx_fault(ctx) -> int:
     return int(f.value)
 
 
-PROF_APPLY64, PROF_APPLY32, PROF_HALO = 0, 1, 2
+PROF_APPLY64, PROF_APPLY32, PROF_HALO, PROF_LEARNED = 0, 1, 2, 3
 
 
 def profile_enable(ctx, on=True):
