@@ -72,6 +72,34 @@ def _bf16(a):
 
 
 @pytest.mark.parametrize("nloc", [4, 10])
+def test_forward_bf16_matches_rounded_network(ctx, torch, nloc):
+    """The tensor-core forward against the same network with the roundings it is specified to make (inputs,
+    weights and the two ReLU outputs to BF16, products accumulated in FP32 or better, FP32 biases): a tolerance
+    ten times tighter than the plain BF16 bound.  S spans more tiles than the grid has CTAs (a ragged last tile and
+    CTAs that take a second tile)."""
+    from paper_2103_02824_gb300 import mk
+    p = _params(nloc, seed=11)
+    mlp = mk.Mlp(ctx, nloc, p)
+    P = _oracle_params(p, nloc)
+    rng = np.random.default_rng(12)
+    S = 128 * 2 * torch.cuda.get_device_properties(0).multi_processor_count + 300
+    X = rng.standard_normal((S, nloc + 12)).astype(np.float32)
+    Y = torch.zeros((S, nloc), dtype=torch.float32, device="cuda")
+    mk.mk_mlp_forward(ctx, mlp, torch.from_numpy(X).cuda(), Y, "bf16")
+    torch.cuda.synchronize()
+    W1, W2, W3 = (_bf16(P[k].astype(np.float32)) for k in ("W1", "W2", "W3"))
+    h1 = _bf16(np.maximum(_bf16(X) @ W1.T + P["b1"], 0.0).astype(np.float32))
+    h2 = _bf16(np.maximum(h1 @ W2.T + P["b2"], 0.0).astype(np.float32))
+    ref = h2 @ W3.T + P["b3"]
+    err = np.abs(Y.cpu().numpy() - ref)
+    scale = np.abs(ref).max()
+    # an FP32 accumulation that lands next to a BF16 rounding boundary may round a hidden unit the other way
+    assert err.max() <= 3e-3 * scale, (err.max(), scale)
+    assert np.median(err) <= 1e-4 * scale
+    mlp.close()
+
+
+@pytest.mark.parametrize("nloc", [4, 10])
 def test_forward_fp32_and_bf16(ctx, torch, nloc):
     from paper_2103_02824_gb300 import mk
     p = _params(nloc)
