@@ -560,7 +560,7 @@ def reference(a, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": 1e3 * t / len(o["step_s"]), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": dict(workload_config(wl, o["N"], o["n_free"], None, None), precision="fp64", precond="jacobi",
+        "config": dict(workload_config(wl, o["N"], o["n_free"], o["n_free_coarse"], o["n_elems"]), precision="fp64", precond="jacobi",
                        rtol=1e-8),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{len(o['step_s'])} full oracle correction steps of the workload"},

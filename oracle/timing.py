@@ -49,7 +49,8 @@ def main():
             times.append(dt)
         res = out
     threads = int(os.environ.get("OMP_NUM_THREADS", "0") or 0) or os.cpu_count()
-    print(json.dumps(dict(workload=name, n_free=int(lv.fine.n_free), N=N, sigma=sigma, setup_s=t_setup,
+    print(json.dumps(dict(workload=name, n_free=int(lv.fine.n_free), n_elems=int(lv.fine.n_elems),
+                          n_free_coarse=int(lv.coarse.n_free), N=N, sigma=sigma, setup_s=t_setup,
                           step_s=times, lam=[float(x) for x in res["lam"]],
                           cg_iters=[int(x) for x in res["cg_iters"]], poisson_iters=res["poisson"]["iters"],
                           threads=threads)))
