@@ -338,8 +338,10 @@ int mk_autotune_patches(mk_ctx* ctx, mk_mesh* mesh, int ld, int* best_pe, double
  *            with residual r_k and converged solution x*; loss L = sum_s ||u_s y_s - e_s||^2 / sum_s u_s^2
  *            (the network predicts the error normalised like its input), Adam updates.
  * Parameters are FP32, flattened in the order W1 [H][n_in], b1 [H], W2 [H][H], b2 [H], W3 [n_out][H],
- * b3 [n_out], row-major.  Inference in BF16 (weights and activations rounded to BF16, FP32 accumulation, warp
- * tensor-core MMA) or FP32; training in FP32 with deterministic (fixed-order) gradient sums.
+ * b3 [n_out], row-major.  Inference in BF16 (inputs, weights and the two ReLU outputs rounded to BF16, products
+ * accumulated in FP32 on the tensor cores (tcgen05), biases kept to about 2^-16 relative as high + low BF16 parts)
+ * or FP32; training in FP32 with deterministic (fixed-order) gradient sums.  A BF16 call whose bounded wait for
+ * its tensor-core work gives up sets MK_FAULT_TC_WAIT in the context's fault word (outputs invalid).
  * --------------------------------------------------------------------------------------------------------- */
 #define MK_MLP_HIDDEN 64
 enum { MK_MLP_FP32 = 0, MK_MLP_BF16 = 1 };
