@@ -31,7 +31,7 @@ constexpr int kLW = 8;              // orbital columns per pass of the patch ker
 // groups of 8 rows K * 16 bytes apart (its stride-dimension byte offset).
 constexpr int kK1 = 32;       // layer-1 input width: the n_in <= 22 features, the two bias inputs, zeros
 constexpr int kKOne = 28;     // input columns 28 and 29 hold 1.0 against the layer-1 bias (high, low BF16 parts)
-constexpr int kTcRows = 128;  // rows per tile: the MMA's M, the TMEM lanes, the threads of the CTA
+constexpr int kTcRows = 128;  // rows per tile: the MMA's M, the TMEM lanes, the threads of a warpgroup
 __host__ __device__ constexpr int umma_off(int row, int k, int K) {  // element (row, k) in halves
   return (row >> 3) * (K * 8) + (k >> 3) * 64 + (row & 7) * 8 + (k & 7);
 }
@@ -45,7 +45,7 @@ constexpr int kUW3 = kUW2 + kNH * kNH;
 constexpr int kUB2 = kUW3 + 16 * kNH;
 constexpr int kUB3 = kUB2 + kNH * 16;
 constexpr int kWuHalves = kUB3 + 16 * 16;
-constexpr uint32_t kTmemCols = 64;  // every layer's accumulator starts at TMEM column 0 (layer 3 uses 16)
+constexpr uint32_t kTmemCols = 64;  // per warpgroup: every layer's accumulator starts at its column 0 (layer 3: 16)
 
 static inline int64_t mlp_count(int nin, int nout) {
   return (int64_t)kNH * nin + kNH + (int64_t)kNH * kNH + kNH + (int64_t)nout * kNH + nout;
