@@ -185,11 +185,17 @@ def decompose_mode(a):
 
 def workload_config(wl, N, n_free, NH, E):
     Z = ",".join(str(int(z)) for z in wl["Z"])
+    if wl.get("mesh") == "graded":
+        fine = (f"fine mesh bisected toward the nuclei to longest edge <= max({wl['h_min']:g}, {wl['alpha']:g} r) "
+                f"({E} tets, {n_free} free DOF)")
+        mol = f"synthetic {len(wl['Z'])}-nucleus cluster (seed 5, Z={Z})"
+    else:
+        fine = f"fine {wl['n_coarse'] * 2 ** wl['levels']}^3 cubes ({E} tets, {n_free} free DOF)"
+        mol = f"synthetic {len(wl['Z'])}-nucleus molecule (seed 2, Z={Z})"
     return {
-        "workload": f"{wl['name']}: synthetic {len(wl['Z'])}-nucleus molecule (seed 2, Z={Z}), P{wl['order']} "
-                    f"tetrahedra, box [-{wl['half']:g},{wl['half']:g}]^3, fine {wl['n_coarse'] * 2 ** wl['levels']}^3 "
-                    f"cubes ({E} tets, {n_free} free DOF), coarse {wl['n_coarse']}^3 cubes (N_H={NH}), N={N} orbitals, "
-                    f"{wl['xc'].upper()}, multipole Hartree BC",
+        "workload": f"{wl['name']}: {mol}, P{wl['order']} tetrahedra, box [-{wl['half']:g},{wl['half']:g}]^3, "
+                    f"{fine}, coarse {wl['n_coarse']}^3 cubes (N_H={NH}), N={N} orbitals, {wl['xc'].upper()}, "
+                    f"multipole Hartree BC",
         "n_free": n_free, "orbitals": N, "N_H": NH,
     }
 

@@ -22,7 +22,7 @@ def main():
     from oracle import linalg as olin
     from paper_2103_02824_gb300 import synth
     wl = synth.workload(name)
-    cc, ct, fc, ft, par = synth.nested_cube_meshes(wl["n_coarse"], wl["levels"], wl["half"])
+    cc, ct, fc, ft, par = synth.workload_meshes(wl)
     t0 = time.perf_counter()
     lv = Level(cc, ct, fc, ft, par, wl["order"], wl["Z"], wl["R"])
     t_setup = time.perf_counter() - t0

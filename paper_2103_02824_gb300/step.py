@@ -127,6 +127,6 @@ def coarse_eigenpairs(ctx, mesh, Z, R, N, return_basis=False):
 def upload_workload(ctx, wl):
     """Meshes of a named synthetic workload (see synth.workload) uploaded to the device."""
     from . import synth
-    cc, ct, fc, ft, par = synth.nested_cube_meshes(wl["n_coarse"], wl["levels"], wl["half"])
+    cc, ct, fc, ft, par = synth.workload_meshes(wl)
     mesh = mk.Mesh(ctx, fc, ft, cc, ct, par, wl["order"])
     return mesh, (cc, ct, fc, ft, par)

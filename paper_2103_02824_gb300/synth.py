@@ -6,7 +6,8 @@ closed-form trial functions evaluated at points that the caller supplies.
 
 Workload shapes follow the paper's experiments (Sec. 4): all-electron molecules with nuclear charges of H..O in
 boxes of half-width 6..15 bohr, N = 1..64 doubly occupied orbitals, meshes of tetrahedra obtained by uniform
-refinement of a cube mesh (the paper's coarsest mesh is such a mesh with 24,576 tetrahedra).
+refinement of a cube mesh (the paper's coarsest mesh is such a mesh with 24,576 tetrahedra), or by local
+bisection graded toward the nuclei (the paper's adaptive meshes are locally refined, Sec. 2).
 """
 from __future__ import annotations
 
@@ -75,6 +76,120 @@ def nested_cube_meshes(n_coarse: int, levels: int, half: float):
     pidx = np.array([perm_index[tuple(o)] for o in order.tolist()], dtype=np.int64)
     parent = (6 * coarse_cube + pidx).astype(np.int32)
     return cc, ct, fc, ft, parent
+
+
+def _edge_keys(a, b, nv_cap: int):
+    lo, hi = np.minimum(a, b), np.maximum(a, b)
+    return lo.astype(np.int64) * nv_cap + hi.astype(np.int64)
+
+
+def graded_mesh(n_coarse: int, half: float, centres, h_min: float = 0.05, alpha: float = 0.3,
+                max_elems: int = 4_000_000):
+    """A conforming tetrahedral mesh of [-half, half]^3 refined toward the points `centres` [M, 3] until every
+    element's longest edge is at most max(h_min, alpha * distance from its centroid to the nearest centre), nested
+    in the Kuhn mesh of n_coarse^3 cubes.
+
+    Refinement is newest-vertex bisection in Maubach's form: a tetrahedron (x0, x1, x2, x3) with tag k in {1, 2, 3}
+    is cut at the midpoint z of the edge x0-xk into (x0, .., x_{k-1}, z, x_{k+1}, .., x3) and
+    (x1, .., xk, z, x_{k+1}, .., x3), both with tag k - 1 (3 after 1).  The Kuhn tetrahedra, with their vertices in
+    path order and tag 3, are compatible with it: every refinement is conforming after closure (any tetrahedron that
+    holds an edge already cut is cut too, until none does), the elements fall into a bounded number of similarity
+    classes, and every fine tetrahedron lies inside the coarse one it descends from.
+
+    Returns (coarse_coords, coarse_tets, fine_coords, fine_tets, fine_parent) like nested_cube_meshes, with
+    positively oriented tetrahedra.  Deterministic: no randomness, stable orderings.
+    """
+    cc, ct = cube_mesh(n_coarse, half)
+    centres = np.asarray(centres, dtype=np.float64).reshape(-1, 3)
+    # path order (undo the orientation swap of the negative permutations)
+    T = ct.astype(np.int64).copy()
+    neg = np.array([_PERM_SIGN[p] < 0 for p in range(6)] * (T.shape[0] // 6))
+    T[neg, 2], T[neg, 3] = ct[neg, 3], ct[neg, 2]
+    K = np.full(T.shape[0], 3, dtype=np.int64)
+    A = np.arange(T.shape[0], dtype=np.int64)
+    V = [cc.astype(np.float64)]
+    nv = cc.shape[0]
+    cap = 1 << 31
+    split_k = np.zeros(0, dtype=np.int64)   # sorted keys of the edges already cut
+    split_m = np.zeros(0, dtype=np.int64)   # their midpoints
+    pairs = np.array([(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)])
+
+    def coords():
+        return np.concatenate(V, axis=0) if len(V) > 1 else V[0]
+
+    def midpoints(a, b):
+        nonlocal split_k, split_m, nv
+        keys = _edge_keys(a, b, cap)
+        pos = np.searchsorted(split_k, keys)
+        found = np.zeros(keys.size, dtype=bool)
+        ok = pos < split_k.size
+        found[ok] = split_k[pos[ok]] == keys[ok]
+        if not found.all():
+            uk, first = np.unique(keys[~found], return_index=True)
+            ia, ib = a[~found][first], b[~found][first]
+            X = coords()
+            V.append(0.5 * (X[ia] + X[ib]))
+            ids = nv + np.arange(uk.size, dtype=np.int64)
+            nv += uk.size
+            allk = np.concatenate([split_k, uk])
+            allm = np.concatenate([split_m, ids])
+            o = np.argsort(allk, kind="stable")
+            split_k, split_m = allk[o], allm[o]
+            pos = np.searchsorted(split_k, keys)
+        return split_m[pos]
+
+    def bisect(idx):
+        nonlocal T, K, A
+        t, k = T[idx], K[idx]
+        z = midpoints(t[:, 0], t[np.arange(idx.size), k])
+        c1 = t.copy()
+        c1[np.arange(idx.size), k] = z
+        c2 = np.empty_like(t)
+        for kk in (1, 2, 3):
+            sel = k == kk
+            if not sel.any():
+                continue
+            tk = t[sel]
+            row = np.concatenate([tk[:, 1:kk + 1], z[sel, None], tk[:, kk + 1:]], axis=1)
+            c2[sel] = row
+        nk = np.where(k > 1, k - 1, 3)
+        T[idx], K[idx] = c1, nk
+        T = np.concatenate([T, c2])
+        K = np.concatenate([K, nk])
+        A = np.concatenate([A, A[idx]])
+
+    def hanging(rows):
+        t = T[rows]
+        keys = _edge_keys(t[:, pairs[:, 0]], t[:, pairs[:, 1]], cap)
+        pos = np.searchsorted(split_k, keys)
+        hit = np.zeros(keys.shape, dtype=bool)
+        ok = pos < split_k.size
+        hit[ok] = split_k[pos[ok]] == keys[ok]
+        return rows[hit.any(axis=1)]
+
+    while True:
+        X = coords()
+        P = X[T]
+        diam = np.sqrt(((P[:, pairs[:, 0]] - P[:, pairs[:, 1]]) ** 2).sum(axis=2)).max(axis=1)
+        cen = P.mean(axis=1)
+        dist = np.sqrt(((cen[:, None, :] - centres[None, :, :]) ** 2).sum(axis=2)).min(axis=1)
+        mark = np.nonzero(diam > np.maximum(h_min, alpha * dist) * (1 + 1e-12))[0]
+        if mark.size == 0:
+            break
+        if T.shape[0] + mark.size > max_elems:
+            raise ValueError("graded_mesh: more than max_elems elements")
+        bisect(mark)
+        while True:  # closure: cut every tetrahedron that still holds a cut edge
+            h = hanging(np.arange(T.shape[0]))
+            if h.size == 0:
+                break
+            bisect(h)
+    X = coords()
+    P = X[T]
+    vol = np.einsum("ij,ij->i", np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]), P[:, 3] - P[:, 0])
+    flip = vol < 0
+    T[flip, 2], T[flip, 3] = T[flip, 3].copy(), T[flip, 2].copy()
+    return cc, ct, X, T.astype(np.int32), A.astype(np.int32)
 
 
 def molecule(seed: int, n_nuclei: int, zmax: int = 8, half: float = 3.0, dmin: float = 1.5):
@@ -163,6 +278,9 @@ def workload(name: str):
     'mol4_p2': 4 nuclei (seed 2), box [-15,15]^3, P2, coarse 4^3 cubes, fine 32^3 cubes (196,608
                tetrahedra, 250,047 free fine DOF), N = ceil(sum Z / 2) <= 16, LDA.
     'mol4_p2_small': the same molecule on fine 8^3 cubes (parity-test size).
+    'cluster12_p2': 12 nuclei (seed 5), box [-15,15]^3, P2, coarse 4^3 cubes, fine mesh graded toward the nuclei
+               (graded_mesh, longest edge <= max(0.05, 0.3 r): about 0.87 M tetrahedra), N <= 48, LDA.
+    'cluster12_p2_small': the same cluster graded with h_min = 1.5, alpha = 1.0 (9,782 tetrahedra).
     """
     if name == "h_p1":
         Z, R = hydrogen()
@@ -171,7 +289,20 @@ def workload(name: str):
         Z, R = molecule(2, 4)
         lv = {"mol4_p2": 3, "mol4_p2_mid": 2, "mol4_p2_small": 1}[name]
         return dict(name=name, Z=Z, R=R, order=2, half=15.0, n_coarse=4, levels=lv, xc="lda")
+    if name in ("cluster12_p2", "cluster12_p2_small"):
+        Z, R = molecule(5, 12)
+        h_min, alpha = {"cluster12_p2": (0.05, 0.3), "cluster12_p2_small": (1.5, 1.0)}[name]
+        return dict(name=name, Z=Z, R=R, order=2, half=15.0, n_coarse=4, mesh="graded", h_min=h_min, alpha=alpha,
+                    xc="lda")
     raise KeyError(name)
+
+
+def workload_meshes(wl):
+    """(coarse_coords, coarse_tets, fine_coords, fine_tets, fine_parent) of a workload: the uniformly refined cube
+    meshes, or the mesh graded toward its nuclei."""
+    if wl.get("mesh") == "graded":
+        return graded_mesh(wl["n_coarse"], wl["half"], wl["R"], h_min=wl["h_min"], alpha=wl["alpha"])
+    return nested_cube_meshes(wl["n_coarse"], wl["levels"], wl["half"])
 
 
 def n_orbitals(Z) -> int:

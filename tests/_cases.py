@@ -27,7 +27,7 @@ def case(name: str, trial: bool = False):
     """Oracle level + inputs + full oracle step for a named workload.  trial=True uses the closed-form trial
     orbitals of synth instead of coarse eigenvectors."""
     wl = synth.workload(name)
-    cc, ct, fc, ft, par = synth.nested_cube_meshes(wl["n_coarse"], wl["levels"], wl["half"])
+    cc, ct, fc, ft, par = synth.workload_meshes(wl)
     lv = Level(cc, ct, fc, ft, par, wl["order"], wl["Z"], wl["R"])
     N = synth.n_orbitals(wl["Z"])
     occ = synth.occupations(wl["Z"])
