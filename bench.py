@@ -183,6 +183,17 @@ def decompose_mode(a):
                       "ms_per_decomposition": e0.elapsed_time(e1) / a.steps}))
 
 
+def whole_job_ms(ms, dist, device):
+    """The timed region of the whole job: the largest of the ranks' own durations (ms), since the job ends when its
+    slowest rank does; ms itself on one rank (dist None)."""
+    if dist is None:
+        return ms
+    import torch
+    tt = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
 def workload_config(wl, N, n_free, NH, E):
     Z = ",".join(str(int(z)) for z in wl["Z"])
     if wl.get("mesh") == "graded":
@@ -352,11 +363,7 @@ def main():
     launches = mk.launch_count() - launches0
     ms_total = e0.elapsed_time(e1)
     clk = clocks.stop()
-    t_max = ms_total
-    if dist:
-        tt = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = whole_job_ms(ms_total, dist, "cuda")
     units = float(n_free) * N * a.steps * world
     value = units / (t_max * 1e-3)
     lam_head = st.lam.cpu().numpy().copy()
