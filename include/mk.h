@@ -76,6 +76,9 @@ typedef struct {
 } mk_xc;
 
 enum { MK_PREC_FP64 = 0, MK_PREC_MIXED = 1 };
+/* Preconditioners: JACOBI (diagonal), LEARNED (the element-patch network, FCG(1), mixed precision only).
+ * CHEBYSHEV is reserved (a polynomial preconditioner for the FP64 comparison); every solve rejects it with
+ * MK_ERR_UNSUPPORTED. */
 enum { MK_PRECOND_JACOBI = 0, MK_PRECOND_CHEBYSHEV = 1, MK_PRECOND_LEARNED = 2 };
 enum { MK_BC_ZERO = 0, MK_BC_MULTIPOLE = 1 };
 
