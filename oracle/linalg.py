@@ -144,3 +144,22 @@ def arrowhead_select(AH, MH, b, c, beta, gamma):
     coarse = V @ y[:n] - (y[n] / un) * t
     theta = y[n] / un
     return mu[k], np.concatenate([coarse, [theta]]), s
+
+
+def joint_ritz(AH, MH, B, C, GA, GM, k, drop_rtol=1e-12):
+    """Rayleigh-Ritz in the joint augmented space V_H + span{psi^_1, .., psi^_N} (the multilevel-correction form that
+    augments the coarse space with all corrections at once, instead of one at a time): the lowest k eigenpairs of
+        [[A_H, B], [B^T, G_A]] x = lambda [[M_H, C], [C^T, G_M]] x,
+    B = P^T H Psi^, C = P^T M Psi^, G_A = Psi^T H Psi^, G_M = Psi^T M Psi^.  Directions of the joint basis that are
+    linearly dependent (mass eigenvalues below drop_rtol times the largest; a psi^ already in V_H, or two equal
+    corrections) are removed before the dense solve.  Returns (lambda [k], X [N_H + N, k]) with X M-orthonormal,
+    coefficients of the coarse basis followed by those of the psi^_i."""
+    A = np.block([[AH, B], [B.T, GA]])
+    M = np.block([[MH, C], [C.T, GM]])
+    A, M = 0.5 * (A + A.T), 0.5 * (M + M.T)
+    s, U = sla.eigh(M)
+    keep = s > drop_rtol * s.max()
+    W = U[:, keep] / np.sqrt(s[keep])
+    T = W.T @ A @ W
+    lam, Y = sla.eigh(0.5 * (T + T.T))
+    return lam[:k], W @ Y[:, :k]
