@@ -35,6 +35,10 @@ METRIC = "fine-mesh DOF×orbitals solved/s at 1e-8 rel. residual; learned vs pla
 # build on the same workload (None until such a capture exists for the current kernel)
 TRAFFIC = {("mol4_p2", 8): 67.81e6}  # ncu: 65.67 MB read + 2.14 MB written by one launch on mol4_p2
 UNIT = "DOF*orbitals/s"
+OPERATOR_KERNEL = "k_apply_stream (FP32 element-by-element operator, persistent pipelined)"
+# FP64 FMA rate of the GB300: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz (maximum SM clock)
+FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP64_NOTE = "152 SMs x 2 FMA/clock x 2 flop x 2.07 GHz = 1.26 TFLOP/s; a probe measured 1.196"
 
 
 def parse():
@@ -49,6 +53,8 @@ def parse():
                     help="inner preconditioner of the mixed-precision correction solve (learned: FCG(1))")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve measurement")
+    ap.add_argument("--patch-kernel", default="pipelined", choices=["pipelined", "single"],
+                    help="--mode apply: the persistent pipelined operator kernel or the one-patch-per-CTA kernel")
     ap.add_argument("--mode", default="step", choices=["step", "apply", "learned", "stiffness", "decompose"],
                     help="apply: time the FP32 element-by-element operator alone (kernel-level roofline); "
                          "learned: the learned preconditioner (BF16 network) alone; stiffness: the matrix-free "
@@ -70,6 +76,7 @@ def apply_mode(a):
     N = synth.n_orbitals(wl["Z"])
     ld = max(4, (N + 3) // 4 * 4)
     mol = mk.Molecule(wl["Z"], wl["R"])
+    mk.ctx_set_option(ctx, mk.MK_OPT_PATCH_PIPELINE, a.patch_kernel == "pipelined")
     g = torch.Generator(device="cuda").manual_seed(5)
     x = torch.randn((info["n_nodes"], ld), generator=g, device="cuda", dtype=torch.float32)
     y = torch.empty_like(x)
@@ -165,8 +172,8 @@ def decompose_mode(a):
     N, occ = synth.n_orbitals(wl["Z"]), synth.occupations(wl["Z"])
     psiH, lamH, basis = coarse_eigenpairs(ctx, mesh, wl["Z"], wl["R"], N, return_basis=True)
     st = CorrectionStep(ctx, mesh, wl["Z"], wl["R"], N, overlap=False, basis=basis)
-    theta = mk.mk_lowest_ritz(ctx, mesh, st.mol, synth.lanczos_start(mesh.info["n_free"]), steps=60)
-    st.run(psiH, lamH, occ, 1.05 * max(0.0, -theta) + 0.5, xc=wl["xc"], hartree_bc="multipole",
+    _, sigma = mk.mk_correction_shift(ctx, mesh, st.mol, synth.lanczos_start(mesh.info["n_free"]), steps=60)
+    st.run(psiH, lamH, occ, sigma, xc=wl["xc"], hartree_bc="multipole",
            solve_opts=mk.opts(precision="mixed", precond="jacobi", rtol=1e-8, check_every=10),
            poisson_opts=mk.opts(precision="mixed", rtol=1e-8, check_every=10, coarse=True))
     stream = torch.cuda.current_stream().cuda_stream
@@ -319,8 +326,7 @@ def main():
     N, occ = synth.n_orbitals(wl["Z"]), synth.occupations(wl["Z"])
     n_free, NH, E = info["n_free"], info["n_free_coarse"], info["n_elems"]
     mol = mk.Molecule(wl["Z"], wl["R"])
-    theta = mk.mk_lowest_ritz(ctx, mesh, mol, synth.lanczos_start(n_free), steps=60)
-    sigma = 1.05 * max(0.0, -theta) + 0.5
+    theta, sigma = mk.mk_correction_shift(ctx, mesh, mol, synth.lanczos_start(n_free), steps=60)
     psiH, lamH, basis = coarse_eigenpairs(ctx, mesh, wl["Z"], wl["R"], N, return_basis=True)
     st = CorrectionStep(ctx, mesh, wl["Z"], wl["R"], N, basis=basis)
     psiH_dev = torch.zeros((NH, st.ld), dtype=torch.float64, device="cuda")
@@ -374,7 +380,8 @@ def main():
     for _ in range(a.steps):
         step()
     torch.cuda.synchronize()
-    prof = {k: mk.profile_read(ctx, k) for k in (mk.PROF_APPLY64, mk.PROF_APPLY32, mk.PROF_HALO, mk.PROF_LEARNED)}
+    prof = {k: mk.profile_read(ctx, k) for k in (mk.PROF_APPLY64, mk.PROF_APPLY32, mk.PROF_HALO, mk.PROF_LEARNED,
+                                                 mk.PROF_STIFF)}
     mk.profile_enable(ctx, False)
 
     # end to end through the C ABI with host buffers: pinned psi_H in, eigenvalues, coefficients, orbitals out
@@ -474,7 +481,9 @@ def main():
         for bm in bmeshes:
             bm.close()
 
-    # roofline of the dominant kernel (the element-by-element operator application)
+    # roofline of the dominant kernel (the element-by-element operator application of the correction problems):
+    # its algorithmic bytes over the average CUDA-event duration of its launches on the launching stream, every
+    # application of the profiled pass (inside the graphs too), the Poisson solve's stiffness kernel excluded
     kind = mk.PROF_APPLY32 if prof[mk.PROF_APPLY32][1] > 0 else mk.PROF_APPLY64
     ms_k, n_k = prof[kind]
     peaks = {}
@@ -488,25 +497,40 @@ def main():
     if kind == mk.PROF_APPLY64:
         flops = 2.0 * nloc * nloc * E * N
         achieved = flops / (ms_k / n_k * 1e-3) / 1e12 if n_k else None
-        peak = 1.196  # measured FP64 FMA throughput (TFLOP/s) of this machine's GB300
+        peak = FP64_TFLOPS
         roof = {"kernel": "k_apply_patch<10,double> (FP64 element-by-element operator)", "bound": "alu",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,
                 "traffic": None, "applications": n_k, "ms_per_application": ms_k / n_k if n_k else None,
-                "peak_source": "measured FP64 FMA probe, 1.196 TFLOP/s"}
+                "peak_source": f"FP64 FMA rate derived from the SM count and clock ({FP64_NOTE})"}
     else:
         nbytes = 2.0 * info["n_nodes"] * ld * 4 + E * (npack * 4 + nloc * 4 + 2 * nloc)
         achieved = nbytes / (ms_k / n_k * 1e-3) / 1e9 if n_k else None
         peak = peaks.get("hbm_gbs", 6780.7)
-        roof = {"kernel": "k_apply_stream (FP32 element-by-element operator, persistent pipelined)", "bound": "hbm",
+        roof = {"kernel": OPERATOR_KERNEL, "bound": "hbm",
                 "achieved": achieved,
                 "peak": peak, "unit": "GB/s", "frac": achieved / peak if achieved else None,
                 "traffic": TRAFFIC.get((a.workload, ld)),
-                "applications": n_k, "ms_per_application": ms_k / n_k if n_k else None,
+                "applications": n_k, "applications_per_step": n_k / a.steps,
+                "ms_per_application": ms_k / n_k if n_k else None,
                 "bytes_per_application": nbytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst), of measured",
-                "measured": "CUDA events around every application inside the steps",
+                "frac_of_nominal_8tbs": achieved / 8000.0 if achieved else None,
+                "target": "0.60 of HBM (north star)", "target_met": bool(achieved and achieved / peak >= 0.60),
+                "measured": "CUDA events around every application of the correction operator inside the steps",
                 "isolated": None if iso_ms is None else {
                     "ms_per_application": iso_ms, "achieved": nbytes / (iso_ms * 1e-3) / 1e9,
                     "frac": nbytes / (iso_ms * 1e-3) / 1e9 / peak, "applications": 20}}
+    # the Poisson solve's matrix-free stiffness operator (one column): 8 FP32 factors, 10 int32 node indices and
+    # 10 uint16 incidences per element, x read and y written once
+    roof_k = None
+    ms_s, n_s = prof[mk.PROF_STIFF]
+    if n_s:
+        sbytes = 2.0 * info["n_nodes"] * 4 + E * (8 * 4 + nloc * 4 + 2 * nloc)
+        sach = sbytes / (ms_s / n_s * 1e-3) / 1e9
+        speak = peaks.get("hbm_gbs", 6780.7)
+        roof_k = {"kernel": "k_stiff_patch<10> (matrix-free FP32 stiffness operator of the Hartree Poisson solve)",
+                  "bound": "hbm", "achieved": sach, "peak": speak, "unit": "GB/s", "frac": sach / speak,
+                  "applications": n_s, "applications_per_step": n_s / a.steps, "ms_per_application": ms_s / n_s,
+                  "bytes_per_application": sbytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst), of measured"}
 
     # the learned preconditioner's patch kernel (tcgen05 network + node sums): algorithmic network FLOPs of one
     # application (2 (n_in 64 + 64 64 + 64 n_out) per (element, orbital) row) over its CUDA-event duration inside
@@ -525,10 +549,18 @@ def main():
                    "note": "issue- and latency-bound on the per-tile layer chain, not on the tensor pipe"}
 
     cpu = None
+    parity = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         try:
-            o = run_oracle(a.workload, 1, 0, sigma=sigma)
+            o = run_oracle(a.workload, 1, 0)
             tstep = o["step_s"][0]
+            # the same step by the oracle, from its own inputs (coarse eigenpairs, Lanczos shift), at the same 1e-8
+            lam_o = np.asarray(o["lam"])
+            parity = {"max_abs_lambda_err_Ha": float(np.abs(lam_head - lam_o).max()),
+                      "sigma_gpu": sigma, "sigma_oracle": o["sigma"], "tolerance_Ha": 1e-6,
+                      "compared": f"all {N} eigenvalues of the headline step against the oracle's step on the same "
+                                  f"workload, both solved to 1e-8 FP64 relative residual"}
+            parity["ok"] = parity["max_abs_lambda_err_Ha"] <= 1e-6
             cpu = {"value": o["n_free"] * o["N"] / tstep, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"one full oracle correction step (A1-A8, scipy.sparse CSR + Jacobi-PCG to 1e-8, dense "
                              f"LAPACK eigensolves) on the same workload, {tstep:.1f} s; static assembly excluded "
@@ -550,13 +582,16 @@ def main():
             "e2e": {"value": float(n_free) * N * a.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "gpu_launches_per_step": launches / a.steps,
-            "clocks": clk, "roofline": roof, "roofline_learned": roof_tc, "cpu_baseline": cpu,
+            "clocks": clk, "roofline": roof, "roofline_learned": roof_tc, "roofline_stiffness": roof_k,
+            "cpu_baseline": cpu, "parity": parity,
             "compare": compare, "training": train_info, "batch": batch,
             "solve_iterations": solve["iterations"], "solve_max_rel_residual": solve["max_rel_residual"],
             "poisson_iterations": reps["poisson"]["iterations"] if reps["poisson"] else None,
             "lambda": [float(x) for x in lam_head],
         }
         print(json.dumps(line))
+        if parity is not None and not parity["ok"]:
+            raise SystemExit(f"parity failed: |lambda - oracle| = {parity['max_abs_lambda_err_Ha']:.3e} Ha > 1e-6")
     if dist:
         dist.destroy_process_group()
 

@@ -136,6 +136,20 @@ int mk_ctx_destroy(mk_ctx* ctx);
 #define MK_FAULT_PATCH_RECORD 2
 #define MK_FAULT_TC_WAIT 4
 int mk_ctx_fault(mk_ctx* ctx, int* fault);
+/* Context options (diagnostics and tests; no counterpart in the paper).  Errors: MK_ERR_INVALID_ARG.
+ *   MK_OPT_GRAPHS (default 1): 0 runs the inner iterations of the mixed-precision solves eagerly instead of
+ *     replaying them from a CUDA graph.
+ *   MK_OPT_PATCH_PIPELINE (default 1): 0 makes the element-by-element operator use its one-patch-per-CTA kernel
+ *     (the fallback, bitwise equal) instead of the persistent pipelined kernel.
+ *   MK_OPT_WAIT_LIMIT (default -1 = about a second): the number of polls (each suspending the thread up to about
+ *     1 us) after which the pipelined operator kernel's waits for its own copies give up; 0 makes the first wait
+ *     give up at once.  A kernel that gives up sets MK_FAULT_PATCH_WAIT, then still waits, with the default limit,
+ *     for every copy it issued before it ends; the call that launched it returns MK_ERR_TIMEOUT (solves) or leaves
+ *     the bit for mk_ctx_fault (mk_operator_apply), and the outputs are invalid. */
+#define MK_OPT_GRAPHS 1
+#define MK_OPT_PATCH_PIPELINE 2
+#define MK_OPT_WAIT_LIMIT 3
+int mk_ctx_set_option(mk_ctx* ctx, int option, int value);
 /* Copies the calling thread's last error message into buf (always NUL-terminated); returns its length. */
 int mk_last_error(char* buf, size_t len);
 /* Version string of the library build. */
@@ -146,8 +160,16 @@ long long mk_launch_count(void);
 /* Optional timing of the operator applications with CUDA events recorded on the launching stream (diagnostic, no
  * counterpart in the paper).  mk_profile_enable(ctx, 1) clears and starts recording; mk_profile_read waits for
  * the recorded events and returns the summed duration and the number of timed applications of kind
- * 0 = FP64 element-by-element apply, 1 = FP32 patch apply, 2 = FP32 halo sum, 3 = learned-preconditioner patch
- * kernel (the network and the node sums, without the halo pass). */
+ * 0 = FP64 element-by-element apply, 1 = FP32 patch apply of the correction operator (the pipelined or the
+ * one-patch-per-CTA kernel), 2 = FP32 halo sum, 3 = learned-preconditioner patch kernel (the network and the node
+ * sums, without the halo pass), 4 = FP32 matrix-free stiffness operator of the Poisson solve.  Every application is
+ * timed, including those inside the CUDA graphs of the inner iterations (each has its own event pair in the
+ * graph, up to 128 pairs of a kind per captured chunk). */
+#define MK_PROF_APPLY64 0
+#define MK_PROF_APPLY32 1
+#define MK_PROF_HALO 2
+#define MK_PROF_LEARNED 3
+#define MK_PROF_STIFF 4
 int mk_profile_enable(mk_ctx* ctx, int on);
 int mk_profile_read(mk_ctx* ctx, int kind, double* total_ms, long long* count);
 
@@ -273,7 +295,8 @@ int mk_small_eigensolve_shared(mk_ctx* ctx, int N_H, int N, const double* d, con
  * in the library (about 0.9 MB, held by every GPU that loads the library until the process exits), sized for
  * N_H <= 512 and N <= 16; larger sizes return MK_ERR_INVALID_ARG.  It runs on the current CUDA device.  The
  * first call on a device looks up the array's device address once (cudaGetSymbolAddress); make that first call
- * before any stream capture.  All calls share the one array: calls that overlap on the GPU (other streams or
+ * before any stream capture.  That address is kept for the life of the process: after cudaDeviceReset (or any other
+ * teardown of the device's primary context) it is stale, so do not call this entry point again in that process.  All calls share the one array: calls that overlap on the GPU (other streams or
  * host threads) race, so serialise them.  Nothing in the array needs to start at zero. */
 int mk_small_eigensolve_static(int N_H, int N, const double* d, const double* V, const double* b, const double* c,
                                const double* beta, const double* gamma, double* lambda, double* coef,
@@ -303,6 +326,11 @@ int mk_orbital_assemble(mk_ctx* ctx, const mk_mesh* mesh, const double* coef, co
  * sigma = 1.05 max(0, -theta) + 0.5 that keeps the correction operator positive definite. */
 int mk_lowest_ritz(mk_ctx* ctx, const mk_mesh* mesh, const mk_molecule* mol, const double* v0, int steps,
                    double* theta, void* stream);
+/* The shift of the correction problems (the reading that keeps K/2 + M_{V_ext} + sigma M positive definite, since
+ * the paper's operator a(.,.) + (V_ext .,.) is indefinite): theta from mk_lowest_ritz with the same arguments, then
+ * sigma = 1.05 max(0, -theta) + 0.5 (Ha).  Both are written to the host doubles theta and sigma. */
+int mk_correction_shift(mk_ctx* ctx, const mk_mesh* mesh, const mk_molecule* mol, const double* v0, int steps,
+                        double* theta, double* sigma, void* stream);
 
 /* ---------------------------------------------------------------------------------------------------------
  * Batching: many molecules (uneven meshes, uneven orbital counts) in shared launches, and autotuned patch sizes

@@ -107,11 +107,6 @@ __global__ void k_pad_sym(int n, int n2, const double* __restrict__ C, double* _
   Q[t] = (i == j) ? 1.0 : 0.0;
 }
 
-struct Rot {
-  int p, q;
-  double c, s;
-};
-
 __device__ __forceinline__ void pair_of(int r, int k, int n2, int* p, int* q) {
   int a, b;
   if (k == 0) {
@@ -123,133 +118,6 @@ __device__ __forceinline__ void pair_of(int r, int k, int n2, int* p, int* q) {
   }
   *p = min(a, b);
   *q = max(a, b);
-}
-
-// Rotation in the (p,q) plane that (nearly) zeroes S[p][q]: J = [[c, s], [-s, c]] with t = s/c the smaller root of
-// t^2 + 2 theta t - 1 = 0, theta = (S_qq - S_pp) / (2 S_pq).  Only the angle is taken in FP32 (GB300's FP64 rate
-// is low and every CTA derives every rotation of a round); c = (1 + t^2)^-1/2 and s = t c are formed from that t in
-// FP64 (FP32 seed, two Newton steps), so the rotation is orthogonal to FP64 precision.  The slightly inexact angle
-// leaves about 6e-8 |S_pq| behind, which the updates keep exactly and the next sweep removes.
-__device__ __forceinline__ Rot rot_from(int p, int q, double app, double aqq, double apq) {
-  double c = 1.0, s = 0.0;
-  const float fa = (float)apq;
-  if (fa != 0.0f) {
-    const float theta = (float)(aqq - app) / (2.0f * fa);
-    float tf;
-    if (!(fabsf(theta) <= 1e18f)) tf = isfinite(theta) ? 0.5f / theta : 0.0f;  // theta^2 would overflow
-    else tf = copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.0f));
-    const double t = (double)tf;
-    const double x = 1.0 + t * t;
-    double r = (double)rsqrtf((float)x);
-    r = r * (1.5 - 0.5 * x * r * r);
-    r = r * (1.5 - 0.5 * x * r * r);
-    c = r;
-    s = t * r;
-  }
-  return Rot{p, q, c, s};
-}
-
-__device__ __forceinline__ Rot make_rot(const double* __restrict__ S, int n2, int r, int k) {
-  int p, q;
-  pair_of(r, k, n2, &p, &q);
-  const double apq = S[(int64_t)p * n2 + q];
-  if (apq == 0.0) return Rot{p, q, 1.0, 0.0};
-  return rot_from(p, q, S[(int64_t)p * n2 + p], S[(int64_t)q * n2 + q], apq);
-}
-
-// Cyclic Jacobi on the symmetric n2 x n2 matrix (n2 even) in parallel round-robin order, accumulating Q <- Q J.
-// Cooperative launch.  Round r reads S_in and writes S_out (ping-pong): every CTA first derives all n2/2
-// rotations of the round from S_in into shared memory, then updates its share of the disjoint 2x2 blocks and
-// of Q; one grid barrier per round.  *final_buf tells which buffer holds the result.
-constexpr int kJacobiThreads = 512;  // half an SM: the solve kernels of the other stream still fit beside it
-__global__ void __launch_bounds__(kJacobiThreads) k_jacobi(int n2, double* __restrict__ S0, double* __restrict__ S1, double* __restrict__ Q,
-                         double* __restrict__ red, int max_sweeps, double tol, int* __restrict__ info) {
-  cg::grid_group grid = cg::this_grid();
-  extern __shared__ unsigned char smem_raw[];
-  Rot* rot = reinterpret_cast<Rot*>(smem_raw);
-  __shared__ double sh[kJacobiThreads];
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
-  const int np = n2 / 2;
-  const int64_t nblk2 = (int64_t)np * (np + 1) / 2;
-  double* Sin = S0;
-  double* Sout = S1;
-  int sweep = 0;
-  for (; sweep < max_sweeps; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int64_t t = tid; t < (int64_t)n2 * n2; t += nth) {
-      const double v = Sin[t];
-      tot += v * v;
-      if (t / n2 != t % n2) off += v * v;
-    }
-    for (int pass = 0; pass < 2; ++pass) {
-      sh[threadIdx.x] = pass == 0 ? off : tot;
-      __syncthreads();
-      for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-        if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
-        __syncthreads();
-      }
-      if (threadIdx.x == 0) red[2 * blockIdx.x + pass] = sh[0];
-      __syncthreads();
-    }
-    grid.sync();
-    double o = 0.0, f = 0.0;
-    for (int bl = 0; bl < (int)gridDim.x; ++bl) {
-      o += red[2 * bl];
-      f += red[2 * bl + 1];
-    }
-    grid.sync();
-    if (o <= tol * tol * f) break;
-    for (int r = 0; r < n2 - 1; ++r) {
-      for (int k = threadIdx.x; k < np; k += blockDim.x) rot[k] = make_rot(Sin, n2, r, k);
-      __syncthreads();
-      // one index space for the 2x2 block updates of S and the column-pair updates of Q, so that every
-      // thread issues its loads at once (one memory latency per round instead of two)
-      for (int64_t t = tid; t < nblk2 + (int64_t)n2 * np; t += nth) {
-        if (t >= nblk2) {
-          const int64_t u = t - nblk2;
-          const int row = (int)(u / np), k = (int)(u % np);
-          const Rot R = rot[k];
-          const double vp = Q[(int64_t)row * n2 + R.p], vq = Q[(int64_t)row * n2 + R.q];
-          Q[(int64_t)row * n2 + R.p] = R.c * vp - R.s * vq;
-          Q[(int64_t)row * n2 + R.q] = R.s * vp + R.c * vq;
-          continue;
-        }
-        // (k1, k2), k2 <= k1, from t = k1 (k1 + 1) / 2 + k2: an FP32 estimate, corrected exactly in integers
-        int k1 = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-        while ((int64_t)(k1 + 1) * (k1 + 2) / 2 <= t) ++k1;
-        while ((int64_t)k1 * (k1 + 1) / 2 > t) --k1;
-        const int k2 = (int)(t - (int64_t)k1 * (k1 + 1) / 2);  // k2 <= k1
-        const Rot A = rot[k2], B = rot[k1];                    // rows from pair k2, columns from pair k1
-        const double b00 = Sin[(int64_t)A.p * n2 + B.p], b01 = Sin[(int64_t)A.p * n2 + B.q];
-        const double b10 = Sin[(int64_t)A.q * n2 + B.p], b11 = Sin[(int64_t)A.q * n2 + B.q];
-        const double r00 = A.c * b00 - A.s * b10, r01 = A.c * b01 - A.s * b11;
-        const double r10 = A.s * b00 + A.c * b10, r11 = A.s * b01 + A.c * b11;
-        const double n00 = B.c * r00 - B.s * r01, n01 = B.s * r00 + B.c * r01;
-        double n10 = B.c * r10 - B.s * r11;
-        const double n11 = B.s * r10 + B.c * r11;
-        if (k1 == k2) n10 = n01;  // the diagonal block stays exactly symmetric
-        Sout[(int64_t)A.p * n2 + B.p] = n00;
-        Sout[(int64_t)A.p * n2 + B.q] = n01;
-        Sout[(int64_t)A.q * n2 + B.p] = n10;
-        Sout[(int64_t)A.q * n2 + B.q] = n11;
-        if (k1 != k2) {
-          Sout[(int64_t)B.p * n2 + A.p] = n00;
-          Sout[(int64_t)B.q * n2 + A.p] = n01;
-          Sout[(int64_t)B.p * n2 + A.q] = n10;
-          Sout[(int64_t)B.q * n2 + A.q] = n11;
-        }
-      }
-      grid.sync();
-      double* tmp = Sin;
-      Sin = Sout;
-      Sout = tmp;
-    }
-  }
-  if (tid == 0) {
-    info[0] = sweep;
-    info[1] = (Sin == S0) ? 0 : 1;
-  }
 }
 
 // ------------------------------------------------------------------------------------------------ block Jacobi
@@ -1039,10 +907,8 @@ int coarse_inverse32(mk_ctx* ctx, const mk_mesh* m, const double* A64, float* ou
 // of eigenvector k.
 int decompose(mk_ctx* ctx, int n, const double* X, bool w_is_x, const double* AH, double* d, double* V,
               cudaStream_t s) {
-  // block Jacobi (default) on n padded to a multiple of 2 kBW; MK_SCALAR_JACOBI=1 selects the scalar cyclic Jacobi
-  const char* sj = std::getenv("MK_SCALAR_JACOBI");
-  const bool block = !(sj && sj[0] == '1');
-  const int n2 = block ? (n + kBP - 1) / kBP * kBP : (n + 1) / 2 * 2;
+  // block Jacobi on n padded to a multiple of 2 kBW
+  const int n2 = (n + kBP - 1) / kBP * kBP;
   int err = MK_OK;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
@@ -1062,38 +928,18 @@ int decompose(mk_ctx* ctx, int n, const double* X, bool w_is_x, const double* AH
   int max_sweeps = 60;
   double tol = 1e-14;
   int n2v = n2;
-  if (block) {
-    int per_sm = 0;
-    MK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bjacobi, kBJThreads, 0));
-    MK_ARG(per_sm >= 1, "mk: block Jacobi kernel cannot be resident");
-    // one CTA per SM (half its registers): the fine solve's kernels on the other stream run beside it
-    int grid = std::min(ctx->n_sms, 4096);
-    MK_ARG(grid > n2 / kBP, "mk: block Jacobi needs more CTAs than block pairs (coarse space too large)");
-    void* args[] = {&n2v, &S0, &S1, &Q, &Ug, &red, &max_sweeps, &tol, &info};
-    MK_COUNT();
-    // the largest shared-memory carveout, so that an SM running this CTA can also take the fine solve's CTAs
-    MK_CUDA(cudaFuncSetAttribute(k_bjacobi, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 cudaSharedmemCarveoutMaxShared));
-    MK_CUDA(cudaLaunchCooperativeKernel((void*)k_bjacobi, grid, kBJThreads, args, 0, s));
-  } else {
-  const int np = n2 / 2;
-  const size_t smem = (size_t)np * sizeof(Rot);
-  if (smem > 48 * 1024) MK_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  MK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi, kJacobiThreads, smem));
-  MK_ARG(per_sm >= 1, "mk: Jacobi kernel cannot be resident (coarse space too large)");
+  MK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bjacobi, kBJThreads, 0));
+  MK_ARG(per_sm >= 1, "mk: block Jacobi kernel cannot be resident");
+  // one CTA per SM (half its registers): the fine solve's kernels on the other stream run beside it
   int grid = std::min(ctx->n_sms, 4096);
-  void* args[] = {&n2v, &S0, &S1, &Q, &red, &max_sweeps, &tol, &info};
+  MK_ARG(grid > n2 / kBP, "mk: block Jacobi needs more CTAs than block pairs (coarse space too large)");
+  void* args[] = {&n2v, &S0, &S1, &Q, &Ug, &red, &max_sweeps, &tol, &info};
   MK_COUNT();
-  MK_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi, grid, kJacobiThreads, args, smem, s));
-  }
-  if (std::getenv("MK_DEBUG")) {
-    int h[2];
-    cudaMemcpyAsync(h, info, sizeof(h), cudaMemcpyDeviceToHost, s);
-    cudaStreamSynchronize(s);
-    std::fprintf(stderr, "mk: %s Jacobi n=%d sweeps=%d (%s)\n", block ? "block" : "scalar", n, h[0],
-                 w_is_x ? "warm" : "cholesky");
-  }
+  // the largest shared-memory carveout, so that an SM running this CTA can also take the fine solve's CTAs
+  MK_CUDA(cudaFuncSetAttribute(k_bjacobi, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared));
+  MK_CUDA(cudaLaunchCooperativeKernel((void*)k_bjacobi, grid, kBJThreads, args, 0, s));
   MK_COUNT(), k_rank<<<(n + 127) / 128, 128, 0, s>>>(n, n2, S0, S1, info, d, perm);
   MK_COUNT(), k_gather_cols<<<(int)(((int64_t)n * n + 255) / 256), 256, 0, s>>>(n, n2, Q, perm, C);  // C = Q sorted
   gemm64(n, n, n, X, n, 1 - tx, C, n, 0, V, n, s);                   // V = W Q
@@ -1233,7 +1079,8 @@ static std::mutex g_static_mu;
 static double* g_static_ptr[64] = {nullptr};
 
 // Device address of g_static_ws on the current device, looked up once per device (host code cannot use the
-// array's name as a device address).
+// array's name as a device address) and kept for the process: a device reset would make it stale, which the
+// entry point's documentation rules out.
 static int static_workspace(double** out) {
   int dev = 0;
   MK_CUDA(cudaGetDevice(&dev));

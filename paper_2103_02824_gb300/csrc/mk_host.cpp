@@ -155,44 +155,43 @@ void build_ref_tables(int order, RefTables* t) {
 void prof_capture(mk_ctx* ctx, bool on) {
   ctx->capturing = on;
   if (on)
-    for (int k = 0; k < 4; ++k) {
-      ctx->cap_state[k] = 0;
-      ctx->gev_valid[k] = false;
-    }
+    for (int k = 0; k < kProfKinds; ++k) ctx->cap_n[k] = 0;
 }
 
-// Events used to time applications inside a graph; created before any capture starts.
+// The event pool of graph captures; made before any capture starts (nothing is created inside one).
 void prof_prepare_capture(mk_ctx* ctx) {
   if (!ctx->prof_on) return;
-  for (auto& pr : ctx->gev)
-    for (cudaEvent_t& e : pr)
-      if (!e) cudaEventCreate(&e);
+  for (auto& pool : ctx->cap_ev)
+    while (pool.size() < 2 * (size_t)kCapPairs) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return; }
+      pool.push_back(e);
+    }
 }
 
+// After a replay of the captured graph (its stream synchronised): adds every timed application of the replay.
 void prof_harvest(mk_ctx* ctx) {
   if (!ctx->prof_on) return;
-  for (int k = 0; k < 4; ++k) {
-    if (!ctx->gev_valid[k]) continue;
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, ctx->gev[k][0], ctx->gev[k][1]) == cudaSuccess) {
-      ctx->acc_ms[k] += ms;
-      ctx->acc_n[k] += 1;
-    } else {
-      cudaGetLastError();
+  for (int k = 0; k < kProfKinds; ++k)
+    for (int i = 0; i < ctx->cap_n[k]; ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ctx->cap_ev[k][2 * i], ctx->cap_ev[k][2 * i + 1]) == cudaSuccess) {
+        ctx->acc_ms[k] += ms;
+        ctx->acc_n[k] += 1;
+      } else {
+        cudaGetLastError();
+      }
     }
-  }
 }
 
 void prof_mark(mk_ctx* ctx, int kind, bool begin, cudaStream_t s) {
   if (!ctx->prof_on) return;
   if (ctx->capturing) {
-    int& st = ctx->cap_state[kind];
-    if ((begin && st != 0) || (!begin && st != 1)) return;
-    cudaEvent_t& e = ctx->gev[kind][begin ? 0 : 1];
-    if (!e) return;
-    cudaEventRecord(e, s);
-    st = begin ? 1 : 2;
-    if (!begin) ctx->gev_valid[kind] = true;
+    int& n = ctx->cap_n[kind];
+    const size_t idx = 2 * (size_t)n + (begin ? 0 : 1);
+    if (idx >= ctx->cap_ev[kind].size()) return;  // pool exhausted: this application goes untimed
+    cudaEventRecord(ctx->cap_ev[kind][idx], s);
+    if (!begin) ++n;
     return;
   }
   auto& ev = ctx->prof_ev[kind];
@@ -461,7 +460,7 @@ long long mk_launch_count(void) { return g_launch_count.load(std::memory_order_r
 int mk_profile_enable(mk_ctx* ctx, int on) {
   MK_ARG(ctx, "mk_profile_enable: null ctx");
   ctx->prof_on = on != 0;
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < kProfKinds; ++k) {
     ctx->prof_used[k] = 0;
     ctx->acc_ms[k] = 0.0;
     ctx->acc_n[k] = 0;
@@ -470,7 +469,7 @@ int mk_profile_enable(mk_ctx* ctx, int on) {
 }
 
 int mk_profile_read(mk_ctx* ctx, int kind, double* total_ms, long long* count) {
-  MK_ARG(ctx && total_ms && count && kind >= 0 && kind < 4, "mk_profile_read: bad argument");
+  MK_ARG(ctx && total_ms && count && kind >= 0 && kind < kProfKinds, "mk_profile_read: bad argument");
   double t = 0.0;
   for (int i = 0; i < ctx->prof_used[kind]; ++i) {
     float ms = 0.f;
@@ -493,8 +492,6 @@ int mk_ctx_create(mk_ctx** out, int device) {
   mk_ctx* c = new mk_ctx();
   c->device = device;
   MK_CUDA(cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, device));
-  const char* ng = std::getenv("MK_NO_GRAPHS");
-  c->no_graphs = ng && ng[0] == '1';
   MK_CUDA(cudaMalloc(&c->d_fault, sizeof(int)));
   MK_CUDA(cudaMemset(c->d_fault, 0, sizeof(int)));
   MK_CUDA(cudaStreamCreateWithFlags(&c->solve_stream, cudaStreamNonBlocking));
@@ -515,15 +512,27 @@ int mk_ctx_destroy(mk_ctx* c) {
   if (c->pinned) cudaFreeHost(c->pinned);
   for (auto& v : c->prof_ev)
     for (cudaEvent_t e : v) cudaEventDestroy(e);
-  for (auto& pr : c->gev)
-    for (cudaEvent_t e : pr)
-      if (e) cudaEventDestroy(e);
+  for (auto& v : c->cap_ev)
+    for (cudaEvent_t e : v) cudaEventDestroy(e);
   for (cudaEvent_t e : c->solve_ev)
     if (e) cudaEventDestroy(e);
   if (c->solve_stream) cudaStreamDestroy(c->solve_stream);
   cudaFree(c->d_fault);
   delete c;
   return MK_OK;
+}
+
+int mk_ctx_set_option(mk_ctx* c, int option, int value) {
+  MK_ARG(c, "mk_ctx_set_option: null ctx");
+  switch (option) {
+    case MK_OPT_GRAPHS: c->no_graphs = value == 0; return MK_OK;
+    case MK_OPT_PATCH_PIPELINE: c->patch_pipeline = value != 0; return MK_OK;
+    case MK_OPT_WAIT_LIMIT:
+      MK_ARG(value >= -1, "mk_ctx_set_option: wait limit must be >= 0, or -1 for the default");
+      c->wait_limit = value < 0 ? kWaitLimitDefault : value;
+      return MK_OK;
+    default: return fail(MK_ERR_INVALID_ARG, "mk_ctx_set_option: unknown option");
+  }
 }
 
 int mk_ctx_fault(mk_ctx* c, int* fault) {

@@ -40,6 +40,9 @@ int check_fault(mk_ctx* c, cudaStream_t s);
     if (!(cond)) return ::mk::fail(MK_ERR_INVALID_ARG, std::string(msg));      \
   } while (0)
 
+constexpr int kProfKinds = 5;   // PROF_* kinds timed by mk_profile_*
+constexpr int kCapPairs = 128;  // event pairs per kind available to one graph capture
+constexpr int kWaitLimitDefault = 1 << 20;  // the patch kernel's kWaitLimit
 constexpr int kQ = 27;          // quadrature points per element (3x3x3 conical product, exact to degree 5)
 constexpr int kMaxLoc = 10;     // P2
 constexpr int kMaxPacked = 55;  // packed symmetric 10x10
@@ -146,17 +149,19 @@ struct mk_ctx {
   size_t pinned_size = 0;
   // optional CUDA-event timing of operator applications (mk_profile_*): [kind][2*i], [2*i+1] start/stop
   bool prof_on = false;
-  std::vector<cudaEvent_t> prof_ev[4];
-  int prof_used[4] = {0, 0, 0, 0};
-  // inside a CUDA-graph capture only the first application of each kind is timed, with one event pair that
-  // every replay re-records; prof_harvest adds it after each replay
+  std::vector<cudaEvent_t> prof_ev[mk::kProfKinds];
+  int prof_used[mk::kProfKinds] = {};
+  // inside a CUDA-graph capture every application of a kind records its own event pair from a pool made before the
+  // capture (cap_ev); the graph re-records them on every replay and prof_harvest adds their durations after it
   bool capturing = false;
-  int cap_state[4] = {0, 0, 0, 0};
-  bool gev_valid[4] = {false, false, false, false};
-  cudaEvent_t gev[4][2] = {};
-  double acc_ms[4] = {0, 0, 0, 0};
-  long long acc_n[4] = {0, 0, 0, 0};
-  bool no_graphs = false;  // environment MK_NO_GRAPHS=1 disables graph replay of the inner PCG iterations
+  std::vector<cudaEvent_t> cap_ev[mk::kProfKinds];
+  int cap_n[mk::kProfKinds] = {};
+  double acc_ms[mk::kProfKinds] = {};
+  long long acc_n[mk::kProfKinds] = {};
+  // options (mk_ctx_set_option)
+  bool no_graphs = false;       // MK_OPT_GRAPHS = 0: the inner PCG iterations run eagerly instead of replayed
+  bool patch_pipeline = true;   // MK_OPT_PATCH_PIPELINE = 0: the one-patch-per-CTA operator kernel instead
+  int wait_limit = mk::kWaitLimitDefault;  // MK_OPT_WAIT_LIMIT: polls of the patch kernel's bounded copy waits
   // the inner PCG runs on this stream (graphs cannot be captured on the legacy default stream), ordered against
   // the caller's stream by two events
   cudaStream_t solve_stream = nullptr;
@@ -184,7 +189,7 @@ void prof_mark(mk_ctx* ctx, int kind, bool begin, cudaStream_t s);
 void prof_capture(mk_ctx* ctx, bool on);
 void prof_prepare_capture(mk_ctx* ctx);
 void prof_harvest(mk_ctx* ctx);
-enum ProfKind { PROF_APPLY64 = 0, PROF_APPLY32 = 1, PROF_HALO = 2, PROF_LEARNED = 3 };
+enum ProfKind { PROF_APPLY64 = 0, PROF_APPLY32 = 1, PROF_HALO = 2, PROF_LEARNED = 3, PROF_STIFF = 4 };
 }  // namespace mk
 
 struct mk_mesh {

@@ -38,10 +38,11 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_apply_stream(const unsign
                                                           const T* __restrict__ x, T* __restrict__ y,
                                                           T* __restrict__ halo, int col0, int ld, int pe,
                                                           int max_nodes, int max_rec, int n_patches, int64_t n_nodes,
-                                                          int64_t n_elems, int* __restrict__ fault) {
+                                                          int64_t n_elems, int* __restrict__ fault,
+                                                          int wait_limit) {
   extern __shared__ __align__(16) unsigned char smraw[];
   patch_apply_pipelined<NLOC, T, VEC, NCG>(rec, rec_off, Ae, mask, x, y, halo, col0, ld, pe, max_nodes, max_rec,
-                                           n_patches, n_nodes, n_elems, fault, smraw);
+                                           n_patches, n_nodes, n_elems, fault, wait_limit, smraw);
 }
 
 template <typename T, int VEC>
@@ -96,12 +97,12 @@ static int launch_stream_kernel(mk_ctx* ctx, const mk_mesh* m, const T* Ae, cons
   const int grid = (int)std::min<int64_t>(P.n_patches, (int64_t)ctx->n_sms * bps);
   MK_COUNT(), kern<<<grid, th, ssm, s>>>(P.d_rec, P.d_rec_off, Ae, mask, x, y, halo, col0, ld, P.max_elems,
                                          P.max_nodes, P.max_rec_bytes, P.n_patches, L.n_nodes, L.n_elems,
-                                         ctx->d_fault);
+                                         ctx->d_fault, ctx->wait_limit);
   return MK_OK;
 }
 
 // The pipelined patch kernel for columns [col0, col0 + W), if its shared memory fits and an instance exists for
-// this column width (*launched = 1); product items take 4 FP32 columns (2 with MK_PATCH_VEC=2) or 2 FP64 ones.
+// this column width (*launched = 1); product items take 4 FP32 columns or 2 FP64 ones.
 template <typename T>
 static int launch_stream(mk_ctx* ctx, const mk_mesh* m, const T* Ae, const T* x, T* y, T* halo, int col0, int W,
                          int ld, bool mask, cudaStream_t s, int* launched) {
@@ -110,8 +111,7 @@ static int launch_stream(mk_ctx* ctx, const mk_mesh* m, const T* Ae, const T* x,
   *launched = 0;
   const size_t ssm = stream_smem(nloc, P.max_elems, P.max_nodes, P.max_rec_bytes, W, (int)sizeof(T)).total;
   if (ssm > 227 * 1024) return MK_OK;
-  const char* ve = std::getenv("MK_PATCH_VEC");
-  const int pv = sizeof(T) == 8 ? 2 : (ve && ve[0] == '2') ? 2 : 4;
+  constexpr int pv = sizeof(T) == 8 ? 2 : 4;
   if (W % pv) return MK_OK;
   const int th = kStreamThreads;
   const int kind = sizeof(T) == 4 ? PROF_APPLY32 : PROF_APPLY64;
@@ -123,16 +123,11 @@ static int launch_stream(mk_ctx* ctx, const mk_mesh* m, const T* Ae, const T* x,
     if constexpr (sizeof(T) == 8) {                                      \
       if (W == 2) MK_SL(NL, 2, 1);                                       \
       else if (W == 4) MK_SL(NL, 2, 2);                                  \
-    } else if (pv == 4) {                                                \
+    } else {                                                             \
       if (W == 4) MK_SL(NL, 4, 1);                                       \
       else if (W == 8) MK_SL(NL, 4, 2);                                  \
       else if (W == 12) MK_SL(NL, 4, 3);                                 \
       else if (W == 16) MK_SL(NL, 4, 4);                                 \
-    } else {                                                             \
-      if (W == 4) MK_SL(NL, 2, 2);                                       \
-      else if (W == 8) MK_SL(NL, 2, 4);                                  \
-      else if (W == 12) MK_SL(NL, 2, 6);                                 \
-      else if (W == 16) MK_SL(NL, 2, 8);                                 \
     }                                                                    \
   } while (0)
   if (nloc == 4) MK_SD(4);
@@ -155,8 +150,7 @@ int apply_patch(mk_ctx* ctx, const mk_mesh* m, const T* Ae, const T* x, T* y, in
   const int vec = (ld % VEC == 0) ? VEC : 1;
   const int nloc = L.nloc;
   // the pipelined kernel stages x rows in 16-byte copies: x aligned, ld a multiple of 16 bytes
-  const char* pipe_env = std::getenv("MK_PATCH_PIPELINE");
-  const bool pipe_ok = !(pipe_env && pipe_env[0] == '0') && ld % (16 / (int)sizeof(T)) == 0 &&
+  const bool pipe_ok = ctx->patch_pipeline && ld % (16 / (int)sizeof(T)) == 0 &&
                        (reinterpret_cast<uintptr_t>(x) & 15) == 0 && (reinterpret_cast<uintptr_t>(y) & 15) == 0 &&
                        (reinterpret_cast<uintptr_t>(halo) & 15) == 0 && (reinterpret_cast<uintptr_t>(Ae) & 15) == 0 &&
                        P.d_rec != nullptr;
@@ -381,7 +375,7 @@ static int apply_stiff(mk_ctx* ctx, const mk_mesh* m, const float* x, float* y, 
     const int W = std::min(16, ld - col0);
     const size_t smem = stiff_smem(L.nloc, P.max_elems, P.max_nodes, W).total;
     if (smem > 227 * 1024) return fail(MK_ERR_UNSUPPORTED, "stiffness operator: patch too large for shared memory");
-    prof_mark(ctx, PROF_APPLY32, true, s);
+    prof_mark(ctx, PROF_STIFF, true, s);
     if (L.nloc == 4) {
       if (smem > 48 * 1024) cudaFuncSetAttribute(k_stiff_patch<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       MK_COUNT(), k_stiff_patch<4><<<P.n_patches, 128, smem, s>>>(P.d_patch_elem_off, P.d_patch_node_off, P.d_conn,
@@ -395,7 +389,7 @@ static int apply_stiff(mk_ctx* ctx, const mk_mesh* m, const float* x, float* y, 
                                                                    x + col0, y + col0, halo + col0, W, ld,
                                                                    P.max_elems, P.max_nodes, ref);
     }
-    prof_mark(ctx, PROF_APPLY32, false, s);
+    prof_mark(ctx, PROF_STIFF, false, s);
     MK_TRY(halo_pass<float>(ctx, m, halo, y, mask, W, 1, col0, ld, s));
   }
   MK_CUDA(cudaGetLastError());
@@ -1305,9 +1299,8 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
     };
     while (inner_active && total_it < o.maxit) {
       const int k = std::min(check, o.maxit - total_it);
-      // with profiling on, the first chunk of every inner solve runs eagerly so each operator application is
-      // timed by its own event pair on this stream
-      if (use_graph && k == check && !(ctx->prof_on && it == 0)) {
+      bool replayed = false;  // this chunk ran as a graph replay (its timed applications are harvested below)
+      if (use_graph && k == check) {
         if (!exec) {
           const long long c0 = g_launch_count.load();
           prof_prepare_capture(ctx);
@@ -1327,6 +1320,7 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
         }
         MK_CUDA(cudaGraphLaunch(exec, s));
         g_launch_count.fetch_add(graph_kernels);
+        replayed = true;
       } else {
         for (int c = 0; c < k; ++c) MK_TRY(iteration());
       }
@@ -1334,7 +1328,7 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
       total_it += k;
       MK_CUDA(cudaMemcpyAsync(hst, st, sizeof(MixState) * ld, cudaMemcpyDeviceToHost, s));
       MK_CUDA(cudaStreamSynchronize(s));
-      prof_harvest(ctx);
+      if (replayed) prof_harvest(ctx);
       inner_active = false;
       for (int j = 0; j < N; ++j) {
         inner_active |= hst[j].active != 0;

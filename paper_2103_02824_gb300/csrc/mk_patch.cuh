@@ -200,9 +200,11 @@ __device__ __forceinline__ void patch_apply(int p, const int32_t* __restrict__ e
 
 // ------------------------------------------------------------------------------------------------ pipelined apply
 // ------------------------------------------------------------------------------------------------ bulk copies
-// mbarrier and bulk (TMA, non-tensor) copy primitives.  Every wait is bounded: kWaitLimit polls of
-// mbarrier.try_wait (each suspending the thread for at most about kSuspendNs), then the caller is told.
-constexpr int kWaitLimit = 1 << 20;
+// mbarrier and bulk (TMA, non-tensor) copy primitives.  Every wait is bounded: a limit of polls of
+// mbarrier.try_wait (each suspending the thread for at most about kSuspendNs), then the caller is told.  kWaitLimit
+// is the default limit (about a second); a context may lower it for the waits of the patch kernel
+// (mk_ctx_set_option), but the drain after a wait gave up always uses kWaitLimit.
+constexpr int kWaitLimit = kWaitLimitDefault;
 constexpr unsigned kSuspendNs = 1000;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -230,8 +232,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
 __device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
   asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  for (int i = 0; i < kWaitLimit; ++i)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int limit = kWaitLimit) {
+  for (int i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -285,14 +287,16 @@ constexpr int kStreamP1 = 128;
 // its 16-byte loads are conflict-free at the packed row stride.
 // Requires blockDim.x == kStreamThreads; patches of pe consecutive elements (the last one shorter); Ae, x
 // 16-byte aligned; ld and col0 multiples of 16 / sizeof(T).  A record whose header is out of range, or a wait
-// that gives up, sets a bit of *fault and ends the CTA after a bounded wait for its copies.
+// that gives up (after wait_limit polls), sets a bit of *fault and ends the CTA after a bounded wait (the default
+// limit) for every copy it has issued.
 template <int NLOC, typename T, int VEC, int NCG>
 __device__ __forceinline__ void patch_apply_pipelined(const unsigned char* __restrict__ rec,
                                                       const int64_t* __restrict__ rec_off, const T* __restrict__ Ae,
                                                       int mask, const T* __restrict__ x, T* __restrict__ y,
                                                       T* __restrict__ halo, int col0, int ld, int pe, int max_nodes,
                                                       int max_rec, int n_patches, int64_t n_nodes, int64_t n_elems,
-                                                      int* __restrict__ fault, unsigned char* smraw) {
+                                                      int* __restrict__ fault, int wait_limit,
+                                                      unsigned char* smraw) {
   constexpr int NPS = padded_np(NLOC, (int)sizeof(T));
   constexpr int V2 = 16 / (int)sizeof(T);  // columns per sum item (one 16-byte vector)
   constexpr int W = NCG * VEC;
@@ -344,9 +348,11 @@ __device__ __forceinline__ void patch_apply_pipelined(const unsigned char* __res
     ++mat_issued;
   };
   // waits for the record of patch i and checks its header (sizes within the launch's bounds; the elements those
-  // of the patch index); both groups wait on it themselves (its buffer is rewritten only after patch i's sums)
+  // of the patch index); both groups wait on it themselves (its buffer is rewritten only after patch i's sums).
+  // Once a wait has failed no later one runs, so rec_waited counts exactly the leading phases seen complete.
   auto wait_rec = [&](int i) {
-    const bool w = mbar_wait(&barR[i % kRecBufs], (unsigned)((i / kRecBufs) & 1));
+    if (!ok) return;
+    const bool w = mbar_wait(&barR[i % kRecBufs], (unsigned)((i / kRecBufs) & 1), wait_limit);
     rec_waited += w;
     ok = ok && w;
     if (ok) {
@@ -453,8 +459,8 @@ __device__ __forceinline__ void patch_apply_pipelined(const unsigned char* __res
       }
     } else if (t < np_mine) {  // products of patch t
       wait_rec(t);
-      ok = ok && mbar_wait(&barM[t % kAStages], (unsigned)((t / kAStages) & 1));
-      ok = ok && mbar_wait(&barX[t & 1], (unsigned)((t >> 1) & 1));
+      ok = ok && mbar_wait(&barM[t % kAStages], (unsigned)((t / kAStages) & 1), wait_limit);
+      ok = ok && mbar_wait(&barX[t & 1], (unsigned)((t >> 1) & 1), wait_limit);
       const int32_t* h = hdr(t);
       const int ne = h[1];
       const unsigned char* rb = recbuf(t);

@@ -16,15 +16,8 @@
 
 namespace mk {
 
-// Elements per patch: 256 (P1) or 128 (P2); the environment variable MK_PATCH_ELEMS (a multiple of 32 in
-// [32, 512]) overrides it for tuning.  It is read when a mesh is uploaded.
-int patch_elems(int nloc) {
-  if (const char* e = std::getenv("MK_PATCH_ELEMS")) {
-    const int v = std::atoi(e);
-    if (v >= 32 && v <= 512 && v % 32 == 0) return v;
-  }
-  return nloc == 4 ? 256 : 128;
-}
+// Elements per patch when a mesh is uploaded: 256 (P1) or 128 (P2); mk_mesh_set_patch_elems changes it later.
+int patch_elems(int nloc) { return nloc == 4 ? 256 : 128; }
 
 static uint32_t spread10(uint32_t v) {
   v &= 0x3ff;

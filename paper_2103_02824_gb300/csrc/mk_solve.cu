@@ -505,4 +505,14 @@ int mk_lowest_ritz(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, const 
   return MK_OK;
 }
 
+int mk_correction_shift(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, const double* v0, int steps,
+                        double* theta, double* sigma, void* stream) {
+  MK_ARG(sigma, "mk_correction_shift: null sigma");
+  double th = 0.0;
+  MK_TRY(mk_lowest_ritz(ctx, m, mol, v0, steps, &th, stream));
+  if (theta) *theta = th;
+  *sigma = 1.05 * std::max(0.0, -th) + 0.5;
+  return MK_OK;
+}
+
 }  // extern "C"

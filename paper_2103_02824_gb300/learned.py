@@ -26,8 +26,8 @@ class Problem:
         self.ld = 4 if self.N <= 4 else 8 if self.N <= 8 else 16 if self.N <= 16 else (self.N + 3) // 4 * 4
         self.mol = mk.Molecule(self.Z, self.R)
         occ = synth.occupations(self.Z)
-        theta = mk.mk_lowest_ritz(ctx, mesh, self.mol, synth.lanczos_start(info["n_free"], lanczos_seed), steps=60)
-        self.sigma = 1.05 * max(0.0, -theta) + 0.5
+        _, self.sigma = mk.mk_correction_shift(ctx, mesh, self.mol, synth.lanczos_start(info["n_free"], lanczos_seed),
+                                               steps=60)
         psiH, lamH = coarse_eigenpairs(ctx, mesh, self.Z, self.R, self.N)
         f64 = dict(dtype=torch.float64, device="cuda")
         n, NH = info["n_nodes"], info["n_free_coarse"]

@@ -24,6 +24,7 @@ MK_ERR_TIMEOUT = -6
 MK_ERR_SINGULAR_AUG = -7
 MK_ERR_UNSUPPORTED = -8
 MK_MAX_RHS = 64
+MK_FAULT_PATCH_WAIT, MK_FAULT_PATCH_RECORD, MK_FAULT_TC_WAIT = 1, 2, 4
 
 MK_XC = {"none": 0, "slater": 1, "xalpha": 2, "lda": 3}
 MK_PREC_FP64, MK_PREC_MIXED = 0, 1
@@ -112,6 +113,9 @@ _SIGS = {
     "mk_small_eigensolve_static": [C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "mk_orbital_assemble": [_vp, _vp, _vp, _vp, _vp, C.c_int, C.c_int, _vp, _vp],
     "mk_lowest_ritz": [_vp, _vp, C.POINTER(mk_molecule), C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double), _vp],
+    "mk_correction_shift": [_vp, _vp, C.POINTER(mk_molecule), C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double),
+                            C.POINTER(C.c_double), _vp],
+    "mk_ctx_set_option": [_vp, C.c_int, C.c_int],
     "mk_batch_correction_solve": [_vp, C.c_int, C.POINTER(_vp), C.POINTER(mk_molecule), C.POINTER(C.c_double),
                                   C.POINTER(_vp), C.POINTER(_vp), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                   C.POINTER(mk_solve_opts), C.POINTER(mk_solve_report), _vp],
@@ -164,7 +168,12 @@ def ctx_fault(ctx) -> int:
     return int(f.value)
 
 
-PROF_APPLY64, PROF_APPLY32, PROF_HALO, PROF_LEARNED = 0, 1, 2, 3
+PROF_APPLY64, PROF_APPLY32, PROF_HALO, PROF_LEARNED, PROF_STIFF = 0, 1, 2, 3, 4
+MK_OPT_GRAPHS, MK_OPT_PATCH_PIPELINE, MK_OPT_WAIT_LIMIT = 1, 2, 3
+
+
+def ctx_set_option(ctx, option, value):
+    _check(lib().mk_ctx_set_option(ctx.h, option, int(value)))
 
 
 def profile_enable(ctx, on=True):
@@ -519,3 +528,12 @@ def mk_lowest_ritz(ctx, mesh, mol: Molecule, v0, steps=60, stream=None):
     th = C.c_double()
     _check(lib().mk_lowest_ritz(ctx.h, mesh.h, C.byref(mol.c), vp, steps, C.byref(th), _stream(stream)))
     return th.value
+
+
+def mk_correction_shift(ctx, mesh, mol: Molecule, v0, steps=60, stream=None):
+    """(theta, sigma): the lowest Ritz value and the shift the library derives from it."""
+    v, vp = _host_f64(v0)
+    th, sg = C.c_double(), C.c_double()
+    _check(lib().mk_correction_shift(ctx.h, mesh.h, C.byref(mol.c), vp, steps, C.byref(th), C.byref(sg),
+                                     _stream(stream)))
+    return th.value, sg.value

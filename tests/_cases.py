@@ -51,3 +51,9 @@ def case(name: str, trial: bool = False):
 def rel(a, b):
     a, b = np.asarray(a), np.asarray(b)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def maxrel(a, b):
+    """Element-wise: max |a - b| over all entries, relative to max |b| (a local error cannot hide under a norm)."""
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))

@@ -246,9 +246,12 @@ def test_fcg_learned_solve_matches_oracle(ctx, torch, gmesh):
 
 
 def test_learned_gain_on_unseen_molecule(ctx, torch, gmesh):
-    """Train on correction solves of four seeded molecules, evaluate FCG iterations on an unseen one against the
-    same solver with the network off (Jacobi) and with the untrained network.  The numbers are reported; the
-    assertions are that training lowers the loss and that every variant converges to the same FP64 answer."""
+    """Train on correction solves of four seeded molecules, evaluate FCG(1) on an unseen one against the same
+    solver with the network off (Jacobi PCG) and with the untrained network, in inner iterations and solve time.
+    Checked: training lowers the loss, the trained network needs no more iterations than the untrained one, and
+    every variant converges to the same FP64 answer.  The comparison with Jacobi is a recorded result, not a
+    claim: on these problems the element-local correction gives about the Jacobi iteration count at a higher cost
+    per iteration (the negative result stated with the benchmark's numbers in the design notes)."""
     from paper_2103_02824_gb300 import learned, mk, synth
     probs = [learned.Problem(ctx, gmesh, *synth.molecule(s, 4)) for s in (3, 4, 5, 6)]
     data = [learned.harvest(p, every=2, cap=10) for p in probs]
@@ -261,18 +264,24 @@ def test_learned_gain_on_unseen_molecule(ctx, torch, gmesh):
     hist = learned.train(ctx, mlp, X, U, E, steps=600, batch=4096, lr=1e-3, seed=1)
     assert np.mean(hist[-50:]) < np.mean(hist[:50])
     test = learned.Problem(ctx, gmesh, *synth.molecule(11, 4))
-    its = {}
+    its, ms = {}, {}
     ref = None
     for label, pc, net in (("jacobi", "jacobi", None), ("untrained", "learned", untrained),
                            ("trained", "learned", mlp)):
-        x, rep = test.solve(mk.opts(precision="mixed", precond=pc, mlp=net, rtol=1e-8, inner_rtol=1e-4,
-                                    check_every=1))
+        o = mk.opts(precision="mixed", precond=pc, mlp=net, rtol=1e-8, inner_rtol=1e-4, check_every=1)
+        test.solve(o)   # warm-up (element matrices, graphs' buffers)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        x, rep = test.solve(o)
+        e1.record()
+        torch.cuda.synchronize()
         assert rep["max_rel_residual"] <= 1e-8
-        its[label] = rep["iterations"]
+        its[label], ms[label] = rep["iterations"], e0.elapsed_time(e1)
         xs = x.cpu().numpy()[:, : test.N]
         ref = xs if ref is None else ref
         assert rel(xs, ref) < 1e-6
-    print("\nlearned preconditioner, inner iterations to 1e-8 on an unseen molecule:", its,
+    assert its["trained"] <= its["untrained"], its
+    print("\nlearned preconditioner on an unseen molecule (inner iterations to 1e-8, ms per solve):", its, ms,
           "loss first/last", float(np.mean(hist[:50])), float(np.mean(hist[-50:])))
     mlp.close()
     untrained.close()

@@ -38,9 +38,13 @@ def test_static_matches_shared_twice(torch):
         lam = torch.full((N,), 123.0, dtype=torch.float64, device="cuda")
         coef = torch.full((NH + 1, N), -5.0, dtype=torch.float64, device="cuda")
         st = torch.full((N,), 99, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         code = mk.mk_small_eigensolve_static(NH, N, d_d, d_V, *ins, lam, coef, st)
         torch.cuda.synchronize()
         assert code == mk.MK_OK, call
+        if call == 1:   # after the first call's one-time set-up: the call takes no device memory at all
+            assert torch.cuda.mem_get_info()[0] == free0
         assert torch.equal(st, ref_st)
         assert np.abs(lam.cpu().numpy() - ref_lam.cpu().numpy()).max() < 1e-10
         assert np.abs(coef.cpu().numpy() - ref_coef.cpu().numpy()).max() < 1e-8 * np.abs(ref_coef.cpu().numpy()).max()
