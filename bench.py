@@ -35,7 +35,7 @@ METRIC = "fine-mesh DOF×orbitals solved/s at 1e-8 rel. residual; learned vs pla
 # build on the same workload (None until such a capture exists for the current kernel)
 TRAFFIC = {("mol4_p2", 8): 67.81e6}  # ncu: 65.67 MB read + 2.14 MB written by one launch on mol4_p2
 UNIT = "DOF*orbitals/s"
-OPERATOR_KERNEL = "k_apply_stream (FP32 element-by-element operator, persistent pipelined)"
+OPERATOR_KERNEL = "k_apply_reg (FP32 element-by-element operator: element matrices staged in registers)"
 # FP64 FMA rate of the GB300: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz (maximum SM clock)
 FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP64_NOTE = "152 SMs x 2 FMA/clock x 2 flop x 2.07 GHz = 1.26 TFLOP/s; a probe measured 1.196"
@@ -53,8 +53,9 @@ def parse():
                     help="inner preconditioner of the mixed-precision correction solve (learned: FCG(1))")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve measurement")
-    ap.add_argument("--patch-kernel", default="pipelined", choices=["pipelined", "single"],
-                    help="--mode apply: the persistent pipelined operator kernel or the one-patch-per-CTA kernel")
+    ap.add_argument("--patch-kernel", default="reg", choices=["reg", "pipelined", "single"],
+                    help="--mode apply: the FP32 register-staged kernel (default), the two-group pipelined kernel, "
+                         "or the one-patch-per-CTA kernel")
     ap.add_argument("--mode", default="step", choices=["step", "apply", "learned", "stiffness", "decompose"],
                     help="apply: time the FP32 element-by-element operator alone (kernel-level roofline); "
                          "learned: the learned preconditioner (BF16 network) alone; stiffness: the matrix-free "
@@ -76,7 +77,7 @@ def apply_mode(a):
     N = synth.n_orbitals(wl["Z"])
     ld = max(4, (N + 3) // 4 * 4)
     mol = mk.Molecule(wl["Z"], wl["R"])
-    mk.ctx_set_option(ctx, mk.MK_OPT_PATCH_PIPELINE, a.patch_kernel == "pipelined")
+    mk.ctx_set_option(ctx, mk.MK_OPT_PATCH_PIPELINE, {"reg": 1, "pipelined": 2, "single": 0}[a.patch_kernel])
     g = torch.Generator(device="cuda").manual_seed(5)
     x = torch.randn((info["n_nodes"], ld), generator=g, device="cuda", dtype=torch.float32)
     y = torch.empty_like(x)
@@ -95,7 +96,7 @@ def apply_mode(a):
     peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6780.7) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6780.7
     gbs = nbytes / (ms / n * 1e-3) / 1e9
-    print(json.dumps({"mode": "apply", "workload": a.workload, "ld": ld, "applications": n,
+    print(json.dumps({"mode": "apply", "kernel": a.patch_kernel, "workload": a.workload, "ld": ld, "applications": n,
                       "patch_ms": ms / n, "halo_ms": hms / max(hn, 1), "bytes_per_application": nbytes,
                       "achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak}))
 

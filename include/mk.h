@@ -139,10 +139,13 @@ int mk_ctx_fault(mk_ctx* ctx, int* fault);
 /* Context options (diagnostics and tests; no counterpart in the paper).  Errors: MK_ERR_INVALID_ARG.
  *   MK_OPT_GRAPHS (default 1): 0 runs the inner iterations of the mixed-precision solves eagerly instead of
  *     replaying them from a CUDA graph.
- *   MK_OPT_PATCH_PIPELINE (default 1): 0 makes the element-by-element operator use its one-patch-per-CTA kernel
- *     (the fallback, bitwise equal) instead of the persistent pipelined kernel.
+ *   MK_OPT_PATCH_PIPELINE (default 1): the kernel of the element-by-element operator.  1: for FP32 the
+ *     register-staged kernel (one element per thread, its matrix loaded into registers, several patch CTAs per
+ *     SM), for FP64 the persistent two-group pipelined kernel;
+ *     2: the two-group pipelined kernel for FP32 as well; 0: the one-patch-per-CTA kernel (the fallback).  All
+ *     three give bitwise equal results.
  *   MK_OPT_WAIT_LIMIT (default -1 = about a second): the number of polls (each suspending the thread up to about
- *     1 us) after which the pipelined operator kernel's waits for its own copies give up; 0 makes the first wait
+ *     1 us) after which the persistent operator kernels' waits for their own copies give up; 0 makes the first wait
  *     give up at once.  A kernel that gives up sets MK_FAULT_PATCH_WAIT, then still waits, with the default limit,
  *     for every copy it issued before it ends; the call that launched it returns MK_ERR_TIMEOUT (solves) or leaves
  *     the bit for mk_ctx_fault (mk_operator_apply), and the outputs are invalid. */

@@ -190,7 +190,9 @@ void prof_mark(mk_ctx* ctx, int kind, bool begin, cudaStream_t s) {
     int& n = ctx->cap_n[kind];
     const size_t idx = 2 * (size_t)n + (begin ? 0 : 1);
     if (idx >= ctx->cap_ev[kind].size()) return;  // pool exhausted: this application goes untimed
-    cudaEventRecord(ctx->cap_ev[kind][idx], s);
+    // an external record node: the graph records the event again on every replay (a plain record during capture
+    // only marks a position for cross-stream dependencies)
+    cudaEventRecordWithFlags(ctx->cap_ev[kind][idx], s, cudaEventRecordExternal);
     if (!begin) ++n;
     return;
   }
@@ -526,7 +528,10 @@ int mk_ctx_set_option(mk_ctx* c, int option, int value) {
   MK_ARG(c, "mk_ctx_set_option: null ctx");
   switch (option) {
     case MK_OPT_GRAPHS: c->no_graphs = value == 0; return MK_OK;
-    case MK_OPT_PATCH_PIPELINE: c->patch_pipeline = value != 0; return MK_OK;
+    case MK_OPT_PATCH_PIPELINE:
+      MK_ARG(value >= 0 && value <= 2, "mk_ctx_set_option: patch kernel must be 0, 1 or 2");
+      c->patch_kernel = value;
+      return MK_OK;
     case MK_OPT_WAIT_LIMIT:
       MK_ARG(value >= -1, "mk_ctx_set_option: wait limit must be >= 0, or -1 for the default");
       c->wait_limit = value < 0 ? kWaitLimitDefault : value;

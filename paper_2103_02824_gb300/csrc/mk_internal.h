@@ -125,7 +125,7 @@ struct Patches {
   // (uint16 [nl+1]), the node targets (int32 [nl]) and the global ids of the local nodes (int32 [nl]); every
   // section starts on a 16-byte boundary
   unsigned char* d_rec = nullptr;
-  int64_t* d_rec_off = nullptr;          // [P+1]
+  int64_t* d_rec_off = nullptr;          // [P+1]: p * max_rec_bytes (every record padded to the same stride)
   int max_rec_bytes = 0;
   // matrix-free stiffness operator: per patch-ordered element |det J| (J^-1 J^-T)_{ij}, ij = 00,11,22,01,02,12, and
   // two zeros (computed on first use)
@@ -160,7 +160,9 @@ struct mk_ctx {
   long long acc_n[mk::kProfKinds] = {};
   // options (mk_ctx_set_option)
   bool no_graphs = false;       // MK_OPT_GRAPHS = 0: the inner PCG iterations run eagerly instead of replayed
-  bool patch_pipeline = true;   // MK_OPT_PATCH_PIPELINE = 0: the one-patch-per-CTA operator kernel instead
+  // MK_OPT_PATCH_PIPELINE: 1 = register-staged kernel (FP32) and two-group pipelined kernel (FP64), 2 = the two-group
+  // pipelined kernel for FP32 too, 0 = the one-patch-per-CTA kernel
+  int patch_kernel = 1;
   int wait_limit = mk::kWaitLimitDefault;  // MK_OPT_WAIT_LIMIT: polls of the patch kernel's bounded copy waits
   // the inner PCG runs on this stream (graphs cannot be captured on the legacy default stream), ordered against
   // the caller's stream by two events

@@ -10,6 +10,7 @@
 
 #include "mk_device.cuh"
 #include "mk_patch.cuh"
+#include "mk_regapply.cuh"
 
 namespace mk {
 
@@ -43,6 +44,20 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_apply_stream(const unsign
   extern __shared__ __align__(16) unsigned char smraw[];
   patch_apply_pipelined<NLOC, T, VEC, NCG>(rec, rec_off, Ae, mask, x, y, halo, col0, ld, pe, max_nodes, max_rec,
                                            n_patches, n_nodes, n_elems, fault, wait_limit, smraw);
+}
+
+// y = A x (FP32), one CTA per patch, one element per thread, the element matrices staged in registers and the x
+// rows in shared memory (see patch_apply_reg).  At most 128 registers a thread, so four 128-thread CTAs share an SM.
+template <int NLOC, int W>
+__global__ void __launch_bounds__(kRegMaxThreads, 2) k_apply_reg(const unsigned char* __restrict__ rec, int rec_stride,
+                                                                 const float* __restrict__ Ae, int mask,
+                                                                 const float* __restrict__ x, float* __restrict__ y,
+                                                                 float* __restrict__ halo, int col0, int ld, int pe,
+                                                                 int max_nodes, int64_t n_nodes, int64_t n_elems,
+                                                                 int* __restrict__ fault) {
+  extern __shared__ __align__(16) unsigned char smraw_reg[];
+  patch_apply_reg<NLOC, W>((int)blockIdx.x, rec, rec_stride, Ae, mask, x, y, halo, col0, ld, pe, max_nodes, n_nodes,
+                           n_elems, fault, smraw_reg);
 }
 
 template <typename T, int VEC>
@@ -138,6 +153,35 @@ static int launch_stream(mk_ctx* ctx, const mk_mesh* m, const T* Ae, const T* x,
   return r;
 }
 
+// The register-staged kernel for FP32 columns [col0, col0 + W), W in {4, 8} (*launched = 1 if it ran).
+static int launch_reg(mk_ctx* ctx, const mk_mesh* m, const float* Ae, const float* x, float* y, float* halo,
+                      int col0, int W, int ld, bool mask, cudaStream_t s, int* launched) {
+  const Patches& P = m->patches;
+  const Level& L = m->fine;
+  *launched = 0;
+  if ((W != 4 && W != 8) || P.max_elems > kRegMaxThreads) return MK_OK;
+  const size_t ssm = reg_smem(L.nloc, P.max_elems, P.max_nodes, P.max_rec_bytes, W).total;
+  if (ssm > 227 * 1024) return MK_OK;
+  const int th = (P.max_elems + 31) / 32 * 32;
+  prof_mark(ctx, PROF_APPLY32, true, s);
+#define MK_RG(NL, WW)                                                                                           \
+  do {                                                                                                          \
+    auto kern = k_apply_reg<NL, WW>;                                                                            \
+    if (ssm > 48 * 1024) MK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm)); \
+    MK_COUNT(), kern<<<P.n_patches, th, ssm, s>>>(P.d_rec, P.max_rec_bytes, Ae, mask, x, y, halo, col0, ld,     \
+                                                  P.max_elems, P.max_nodes, L.n_nodes, L.n_elems, ctx->d_fault); \
+  } while (0)
+  if (L.nloc == 4) {
+    if (W == 4) MK_RG(4, 4); else MK_RG(4, 8);
+  } else {
+    if (W == 4) MK_RG(10, 4); else MK_RG(10, 8);
+  }
+#undef MK_RG
+  prof_mark(ctx, PROF_APPLY32, false, s);
+  *launched = 1;
+  return MK_OK;
+}
+
 // y = A x with the patch operator (all ld columns), FP32 or FP64.
 template <typename T>
 int apply_patch(mk_ctx* ctx, const mk_mesh* m, const T* Ae, const T* x, T* y, int ld, bool mask, cudaStream_t s) {
@@ -150,7 +194,7 @@ int apply_patch(mk_ctx* ctx, const mk_mesh* m, const T* Ae, const T* x, T* y, in
   const int vec = (ld % VEC == 0) ? VEC : 1;
   const int nloc = L.nloc;
   // the pipelined kernel stages x rows in 16-byte copies: x aligned, ld a multiple of 16 bytes
-  const bool pipe_ok = ctx->patch_pipeline && ld % (16 / (int)sizeof(T)) == 0 &&
+  const bool pipe_ok = ctx->patch_kernel != 0 && ld % (16 / (int)sizeof(T)) == 0 &&
                        (reinterpret_cast<uintptr_t>(x) & 15) == 0 && (reinterpret_cast<uintptr_t>(y) & 15) == 0 &&
                        (reinterpret_cast<uintptr_t>(halo) & 15) == 0 && (reinterpret_cast<uintptr_t>(Ae) & 15) == 0 &&
                        P.d_rec != nullptr;
@@ -160,6 +204,20 @@ int apply_patch(mk_ctx* ctx, const mk_mesh* m, const T* Ae, const T* x, T* y, in
   if (pipe_ok && sizeof(T) == 4 && ld > 8 &&
       stream_smem(nloc, P.max_elems, P.max_nodes, P.max_rec_bytes, std::min(ld, 16), 4).total > 227 * 1024)
     wmax = 8;
+  if constexpr (sizeof(T) == 4) {
+    // FP32, default: the register-staged kernel, 8 columns per pass (4 for the last pass of an ld = 4 mod 8)
+    if (pipe_ok && ctx->patch_kernel == 1 && P.max_elems <= kRegMaxThreads) {
+      for (int col0 = 0; col0 < ld; col0 += 8) {
+        const int W = std::min(8, ld - col0);
+        int launched = 0;
+        MK_TRY(launch_reg(ctx, m, Ae, x, y, halo, col0, W, ld, mask, s, &launched));
+        if (!launched) return fail(MK_ERR_UNSUPPORTED, "patch operator: register-staged kernel does not fit");
+        MK_TRY(halo_pass<T>(ctx, m, halo, y, mask, W / 4, 4, col0, ld, s));
+      }
+      MK_CUDA(cudaGetLastError());
+      return MK_OK;
+    }
+  }
   for (int col0 = 0; col0 < ld; col0 += wmax) {
     const int W = std::min(wmax, ld - col0);
     const int ncolg = W / vec;

@@ -184,13 +184,16 @@ int build_patches(mk_mesh* m, int pe) {
   }
   // patch records (layout in Patches)
   auto a16 = [](int64_t b) { return (b + 15) / 16 * 16; };
+  // every record takes the same stride (the largest record's size), so that a kernel finds patch p's record at
+  // p * stride without first reading an offset
   std::vector<int64_t> rec_off(np + 1, 0);
+  P.max_rec_bytes = 0;
   for (int p = 0; p < np; ++p) {
     const int64_t ne = elem_off[p + 1] - elem_off[p], nl = node_off[p + 1] - node_off[p];
     const int64_t bytes = kRecHeader + 2 * a16(ne * nloc * 2) + a16((nl + 1) * 2) + 2 * a16(nl * 4);
-    rec_off[p + 1] = rec_off[p] + bytes;
     P.max_rec_bytes = std::max<int>(P.max_rec_bytes, (int)bytes);
   }
+  for (int p = 0; p < np; ++p) rec_off[p + 1] = rec_off[p] + P.max_rec_bytes;
   std::vector<unsigned char> rec((size_t)rec_off[np], 0);
   for (int p = 0; p < np; ++p) {
     const int32_t e0 = elem_off[p], ne = elem_off[p + 1] - e0, n0 = node_off[p], nl = node_off[p + 1] - n0;

@@ -1,5 +1,5 @@
-"""Failure detection on the device, without a fault: the pipelined operator kernel's bounded waits for its own
-asynchronous copies are made to give up (wait limit 0 through mk_ctx_set_option), the library reports it (the
+"""Failure detection on the device, without a fault: the persistent operator kernel's bounded waits for its own
+asynchronous copies (bulk copies and cp.async completing on mbarriers) are made to give up (wait limit 0 through mk_ctx_set_option), the library reports it (the
 context's fault word, MK_ERR_TIMEOUT from a solve), the kernel still waits for every copy it issued before it
 ends, and the same context then applies the operator and solves correctly again."""
 import numpy as np
@@ -40,10 +40,12 @@ def test_wait_that_gives_up_is_reported_and_the_context_recovers(torch):
     rhs_d = torch.from_numpy(rhs).cuda()
     try:
         assert mk.ctx_fault(ctx) == 0
+        # the FP32 operator on the persistent two-group kernel, the one whose copies complete on mbarriers
+        mk.ctx_set_option(ctx, mk.MK_OPT_PATCH_PIPELINE, 2)
         mk.ctx_set_option(ctx, mk.MK_OPT_WAIT_LIMIT, 0)
-        y = torch.full_like(x, 3.0)
-        mk.mk_operator_apply(ctx, m, mol, sigma, x, y)
+        mk.mk_operator_apply(ctx, m, mol, sigma, x, torch.full_like(x, 3.0))
         assert mk.ctx_fault(ctx) & mk.MK_FAULT_PATCH_WAIT      # read and cleared
+        # a mixed solve whose inner operator gives up returns MK_ERR_TIMEOUT
         xs = torch.from_numpy(u).cuda()
         rep = mk.mk_correction_solve(ctx, m, mol, sigma, rhs_d, xs, N,
                                      opt=mk.opts(precision="mixed", rtol=1e-12, maxit=10, check_every=5),
@@ -52,6 +54,7 @@ def test_wait_that_gives_up_is_reported_and_the_context_recovers(torch):
         assert mk.ctx_fault(ctx) & mk.MK_FAULT_PATCH_WAIT
     finally:
         mk.ctx_set_option(ctx, mk.MK_OPT_WAIT_LIMIT, -1)
+        mk.ctx_set_option(ctx, mk.MK_OPT_PATCH_PIPELINE, 1)
     # the same context after the failure: the operator and a full mixed-precision solve are right again
     y = torch.full_like(x, 3.0)
     mk.mk_operator_apply(ctx, m, mol, sigma, x, y)

@@ -434,9 +434,10 @@ def test_assemble_rhs_in_two_halves(ctx, torch, name):
 
 @pytest.mark.parametrize("name,pe", [("mol4_p2_mid", 32), ("mol4_p2_mid", 128), ("h_p1", 32)])
 def test_pipelined_patch_kernel_matches_single_patch_kernel(ctx, torch, name, pe):
-    """The persistent pipelined patch kernel (several patches per CTA, the next patch's copies in flight) and the
-    one-patch-per-CTA kernel sum in the same order, so they agree bitwise, FP32 and FP64, for every column
-    width; an ld that is not a multiple of 16 bytes takes the single-patch kernel, still against the oracle.
+    """The patch kernels -- the FP32 register-staged kernel, the persistent two-group pipelined kernel and the
+    one-patch-per-CTA kernel -- sum in the same order, so they agree bitwise, FP32 and FP64, for every column width
+    (ld = 12 takes a pass of 8 columns and one of 4); an ld that is not a multiple of 16 bytes takes the
+    single-patch kernel, still against the oracle.  Patch sizes 32 and 128, more patches than resident CTAs.
     Meshes with more patches than resident CTAs, so that CTAs loop over several patches."""
     from oracle.correction import Level
     from paper_2103_02824_gb300 import mk, synth
@@ -458,14 +459,14 @@ def test_pipelined_patch_kernel_matches_single_patch_kernel(ctx, torch, name, pe
             for dt, tol in ((torch.float64, 1e-13), (torch.float32, 3e-6)):
                 x = torch.from_numpy(X).to(dt).cuda()
                 outs = []
-                for pipe in (1, 0):
+                for pipe in (1, 2, 0):   # register-staged (FP32) / two-group (FP64), two-group, one per CTA
                     mk.ctx_set_option(ctx, mk.MK_OPT_PATCH_PIPELINE, pipe)
                     y = torch.full_like(x, 5.0)
                     mk.mk_operator_apply(ctx, m, mol, sigma, x, y)
                     torch.cuda.synchronize()
                     outs.append(y)
                 mk.ctx_set_option(ctx, mk.MK_OPT_PATCH_PIPELINE, 1)
-                assert torch.equal(outs[0], outs[1]), (ld, dt)
+                assert torch.equal(outs[0], outs[2]) and torch.equal(outs[1], outs[2]), (ld, dt)
                 assert rel(outs[0].double().cpu().numpy(), ref) < tol, (ld, dt)
                 assert maxrel(outs[0].double().cpu().numpy(), ref) < tol, (ld, dt)
         assert mk.ctx_fault(ctx) == 0  # no bounded wait gave up, no record failed its checks
