@@ -317,6 +317,29 @@ int mk_small_eigensolve(mk_ctx* ctx, int N_H, int N, const double* AH, const dou
                         const double* c, const double* beta, const double* gamma, double* lambda, double* coef,
                         int32_t* status, void* stream);
 
+/* ---------------------------------------------------------------------------------------------- joint space */
+/* Rayleigh-Ritz in the joint augmented space V_H + span{psi^_1, ..., psi^_N} (the multilevel-correction scheme
+ * that augments the coarse space with all the corrections at once rather than one at a time; Sec. 2, the
+ * original scheme the paper builds on): the lowest k eigenpairs of
+ *   [[A_H, B], [B^T, G_A]] x = lambda [[M_H, C], [C^T, G_M]] x,
+ * B = P^T H Psi^, C = P^T M Psi^, G_A = Psi^T H Psi^, G_M = Psi^T M Psi^ (mk_augmented_project's b, c, gramA,
+ * gramM; the Grams are symmetrised), with (A_H, M_H) given by their shared decomposition d [N_H], V [N_H*N_H]
+ * (mk_coarse_decompose).  The corrections are M-orthogonalised against V_H; directions whose mass in that basis is
+ * at most 1e-12 max(1, largest) (a correction in V_H, two equal corrections) are dropped; *n_kept (host, may be
+ * NULL) receives how many are kept.  The remaining problem is one dense symmetric FP64 eigensolve of size
+ * N_H + n_kept (cyclic block Jacobi, as for the coarse decomposition; N_H + N below 2432).
+ * Outputs (device FP64): lambda [k] ascending; X [(N_H + N) * k] row-major, column j = the coarse coefficients
+ * (free DOF) then the coefficients of psi^_1..psi^_N of Ritz vector j, M-orthonormal, sign arbitrary.
+ * Synchronises the stream once (the kept count decides the size of the dense problem).
+ * Errors: MK_ERR_INVALID_ARG (k > N_H + n_kept, sizes), MK_ERR_CUDA. */
+int mk_joint_ritz(mk_ctx* ctx, int N_H, int N, int k, const double* d, const double* V, const double* b,
+                  const double* c, const double* gramA, const double* gramM, double* lambda, double* X, int* n_kept,
+                  void* stream);
+/* The joint Ritz vectors on the fine mesh: psi_j = P X[0:N_H, j] + sum_i X[N_H + i, j] psi^_i for j < k, sign chosen
+ * so that (psi_j, u_j)_M >= 0 (u = P psi_H, the step's prolonged input orbitals).  psihat, u, psi [n_nodes*ld]. */
+int mk_joint_assemble(mk_ctx* ctx, const mk_mesh* mesh, int k, int N, const double* X, const double* psihat,
+                      const double* u, int ld, double* psi, void* stream);
+
 /* ---------------------------------------------------------------------------------------------- A8 */
 /* psi_i = P phi_{i,H} + theta_{2,i} psi^_i (Algorithm 3, output), sign chosen so that (psi_i, u_i)_M > 0.
  * coef [(N_H+1)*N] from mk_small_eigensolve, psihat/u/psi [n_nodes*ld] device. */

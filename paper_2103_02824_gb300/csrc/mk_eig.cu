@@ -906,7 +906,7 @@ int coarse_inverse32(mk_ctx* ctx, const mk_mesh* m, const double* A64, float* ou
 // start, C is then nearly diagonal), W = X^T when X = L^-1 (M_H = L L^T).  V row-major, V[i][k] = component i
 // of eigenvector k.
 int decompose(mk_ctx* ctx, int n, const double* X, bool w_is_x, const double* AH, double* d, double* V,
-              cudaStream_t s) {
+              cudaStream_t s, int slot = S_EIG2) {
   // block Jacobi on n padded to a multiple of 2 kBW
   const int n2 = (n + kBP - 1) / kBP * kBP;
   int err = MK_OK;
@@ -915,7 +915,7 @@ int decompose(mk_ctx* ctx, int n, const double* X, bool w_is_x, const double* AH
   const size_t oT = take((size_t)n * n * 8), oC = take((size_t)n * n * 8), oS0 = take((size_t)n2 * n2 * 8);
   const size_t oS1 = take((size_t)n2 * n2 * 8), oQ = take((size_t)n2 * n2 * 8), oRed = take(8192 * 8);
   const size_t oPerm = take((size_t)n * 4), oInfo = take(64), oU = take((size_t)2 * (n2 / kBP) * kBP * kBP * 8);
-  char* ws = (char*)scratch(ctx, S_EIG2, off, &err);
+  char* ws = (char*)scratch(ctx, slot, off, &err);
   if (!ws) return err;
   double *T = (double*)(ws + oT), *C = (double*)(ws + oC), *S0 = (double*)(ws + oS0), *S1 = (double*)(ws + oS1);
   double *Q = (double*)(ws + oQ), *red = (double*)(ws + oRed);
@@ -965,6 +965,115 @@ int secular(mk_ctx* ctx, int n, int N, const double* d, const double* V, const d
 }
 
 // At mesh upload: M_H = P^T M P and its inverse Cholesky factor, kept in the mesh handle.
+
+// ------------------------------------------------------------------------------------------------ joint space
+// Rayleigh-Ritz in V_H + span{psi^_1..psi^_N}.  With V the M_H-orthonormal eigenvectors of (A_H, M_H) (eigenvalues
+// D), M_H^-1 = V V^T, so the corrections' parts M-orthogonal to V_H are U = Psi^ - P V (V^T C), with Gram
+// S = G_M - (V^T C)^T (V^T C) and Hamiltonian block U^T H U = G_A - (V^T C)^T (V^T B) - (V^T B)^T (V^T C)
+// + (V^T C)^T D (V^T C).  S = Y diag(s) Y^T; the columns with s_j above 1e-12 max(1, s_max) give an M-orthonormal
+// basis U W of the corrections' new directions, W = Y_kept diag(s_kept)^-1/2 (linearly dependent ones dropped).  In
+// the basis [P V, U W] the joint pencil is the standard symmetric problem
+//   T = [[D, Z], [Z^T, W^T (U^T H U) W]],  Z = (V^T B - D V^T C) W,
+// whose eigenvectors (y_top, y_bot) give the joint Ritz vectors P V (y_top - (V^T C) W y_bot) + Psi^ W y_bot.
+// G = [V^T B | V^T C] [n][2N] as k_vt_bc writes it.
+__global__ void k_joint_small(int n, int N, const double* __restrict__ G, const double* __restrict__ d,
+                              const double* __restrict__ gA, const double* __restrict__ gM, double* __restrict__ S,
+                              double* __restrict__ A0) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * N) return;
+  const int i = t / N, j = t % N;
+  double sm = 0.0, sa = 0.0;
+  for (int r = 0; r < n; ++r) {
+    const double* g = G + (int64_t)r * 2 * N;
+    const double bi = g[i], bj = g[j], ci = g[N + i], cj = g[N + j];
+    sm += ci * cj;
+    sa += (ci * bj + bi * cj) - ci * d[r] * cj;
+  }
+  // the Grams symmetrised as the joint pencil is (each (i, j) and (j, i) sum the same terms in the same order)
+  S[t] = 0.5 * (gM[i * N + j] + gM[j * N + i]) - sm;
+  A0[t] = 0.5 * (gA[i * N + j] + gA[j * N + i]) - sa;
+}
+__global__ void k_joint_W(int N, int kp, int first, const double* __restrict__ s, const double* __restrict__ Y,
+                          double* __restrict__ W) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * kp) return;
+  const int i = t / kp, a = t % kp;
+  W[t] = Y[(int64_t)i * N + first + a] / sqrt(s[first + a]);
+}
+// Z [n][kp] = (V^T B - D V^T C) W and At [kp][kp] = W^T A0 W
+__global__ void k_joint_Z(int n, int N, int kp, const double* __restrict__ G, const double* __restrict__ d,
+                          const double* __restrict__ W, double* __restrict__ Z) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * kp) return;
+  const int r = (int)(t / kp), a = (int)(t % kp);
+  const double* g = G + (int64_t)r * 2 * N;
+  double z = 0.0;
+  for (int i = 0; i < N; ++i) z += (g[i] - d[r] * g[N + i]) * W[i * kp + a];
+  Z[t] = z;
+}
+__global__ void k_joint_At(int N, int kp, const double* __restrict__ A0, const double* __restrict__ W,
+                           double* __restrict__ At) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= kp * kp) return;
+  const int a = t / kp, b = t % kp;
+  double v = 0.0;
+  for (int i = 0; i < N; ++i) {
+    double w = 0.0;
+    for (int j = 0; j < N; ++j) w += A0[i * N + j] * W[j * kp + b];
+    v += W[i * kp + a] * w;
+  }
+  At[t] = v;
+}
+__global__ void k_joint_T(int n, int kp, const double* __restrict__ d, const double* __restrict__ Z,
+                          const double* __restrict__ At, double* __restrict__ T) {
+  const int nT = n + kp;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nT * nT) return;
+  const int r = (int)(t / nT), c = (int)(t % nT);
+  double v;
+  if (r < n && c < n) v = r == c ? d[r] : 0.0;
+  else if (r < n) v = Z[(int64_t)r * kp + (c - n)];
+  else if (c < n) v = Z[(int64_t)c * kp + (r - n)];
+  else v = 0.5 * (At[(r - n) * kp + (c - n)] + At[(c - n) * kp + (r - n)]);
+  T[t] = v;
+}
+// for Ritz vectors j < k: w = W y_bot (the corrections' coefficients, rows n.. of X) and
+// tmp = y_top - (V^T C) w (coarse coefficients in the eigenbasis V)
+__global__ void k_joint_coef(int n, int N, int kp, int k, const double* __restrict__ Yt, const double* __restrict__ W,
+                             const double* __restrict__ G, double* __restrict__ X, double* __restrict__ tmp) {
+  const int nT = n + kp;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)(n + N) * k) return;
+  const int r = (int)(t / k), j = (int)(t % k);
+  auto wcoef = [&](int i) {
+    double w = 0.0;
+    for (int a = 0; a < kp; ++a) w += W[i * kp + a] * Yt[(int64_t)(n + a) * nT + j];
+    return w;
+  };
+  if (r >= n) {
+    X[(int64_t)r * k + j] = wcoef(r - n);
+  } else {
+    double v = Yt[(int64_t)r * nT + j];
+    const double* g = G + (int64_t)r * 2 * N;
+    for (int i = 0; i < N; ++i) v -= g[N + i] * wcoef(i);
+    tmp[(int64_t)r * k + j] = v;
+  }
+}
+__global__ void k_joint_orbitals(int64_t n_nodes, const int32_t* __restrict__ off, const int32_t* __restrict__ col,
+                                 const double* __restrict__ val, const uint8_t* __restrict__ bnd,
+                                 const double* __restrict__ X, int n, int k, const double* __restrict__ psihat, int N,
+                                 int ld, double* __restrict__ psi) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_nodes * ld) return;
+  const int64_t nd = t / ld;
+  const int j = (int)(t % ld);
+  double v = 0.0;
+  if (j < k && !bnd[nd]) {
+    for (int q = off[nd]; q < off[nd + 1]; ++q) v += val[q] * X[(int64_t)col[q] * k + j];
+    for (int i = 0; i < N; ++i) v += X[(int64_t)(n + i) * k + j] * psihat[nd * ld + i];
+  }
+  psi[t] = v;
+}
 
 int mesh_mass_factor(mk_ctx* ctx, mk_mesh* m) {
   const Level& F = m->fine;
@@ -1033,6 +1142,79 @@ int mk_small_eigensolve(mk_ctx* ctx, int NH, int N, const double* AH, const doub
   MK_TRY(inverse_cholesky(ctx, NH, MH, Linv, S_EIG4, s));
   MK_TRY(decompose(ctx, NH, Linv, false, AH, d, V, s));
   return secular(ctx, NH, N, d, V, b, c, beta, gamma, lambda, coef, status, s);
+}
+
+int mk_joint_ritz(mk_ctx* ctx, int NH, int N, int k, const double* d, const double* V, const double* b,
+                  const double* c, const double* gramA, const double* gramM, double* lambda, double* X, int* n_kept,
+                  void* stream) {
+  MK_ARG(ctx && d && V && b && c && gramA && gramM && lambda && X, "mk_joint_ritz: null argument");
+  MK_ARG(NH >= 1 && N >= 1 && N <= MK_MAX_RHS && k >= 1, "mk_joint_ritz: bad sizes");
+  MK_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  int err = MK_OK;
+  const int nTmax = NH + N;
+  size_t off = 0;
+  auto take = [&](size_t doubles) { size_t o = off; off += (doubles + 31) / 32 * 32; return o; };
+  const size_t oG = take((size_t)NH * 2 * N), oS = take((size_t)N * N), oA0 = take((size_t)N * N);
+  const size_t oI = take((size_t)nTmax * nTmax), osv = take(N), oY = take((size_t)N * N), oW = take((size_t)N * N);
+  const size_t oZ = take((size_t)NH * N), oAt = take((size_t)N * N), oT = take((size_t)nTmax * nTmax);
+  const size_t omu = take(nTmax), oYt = take((size_t)nTmax * nTmax), otmp = take((size_t)NH * nTmax);
+  double* ws = (double*)scratch(ctx, S_JOINT, off * sizeof(double), &err);
+  if (!ws) return err;
+  double *G = ws + oG, *S = ws + oS, *A0 = ws + oA0, *I = ws + oI, *sv = ws + osv, *Y = ws + oY, *W = ws + oW;
+  double *Z = ws + oZ, *At = ws + oAt, *T = ws + oT, *mu = ws + omu, *Yt = ws + oYt, *tmp = ws + otmp;
+  MK_COUNT(), k_vt_bc<<<(int)(((int64_t)NH * 2 * N + 127) / 128), 128, 0, s>>>(NH, N, V, b, c, G);
+  MK_COUNT(), k_joint_small<<<(N * N + 127) / 128, 128, 0, s>>>(NH, N, G, d, gramA, gramM, S, A0);
+  MK_COUNT(), k_identity<<<(N * N + 255) / 256, 256, 0, s>>>(N, I);
+  MK_TRY(decompose(ctx, N, I, true, S, sv, Y, s, S_EIG5));
+  std::vector<double> hs(N);
+  MK_CUDA(cudaMemcpyAsync(hs.data(), sv, N * sizeof(double), cudaMemcpyDeviceToHost, s));
+  MK_CUDA(cudaStreamSynchronize(s));
+  const double smax = std::max(1.0, hs[N - 1]);
+  int first = 0;
+  while (first < N && !(hs[first] > 1e-12 * smax)) ++first;  // ascending: the dropped directions come first
+  const int kp = N - first;
+  const int nT = NH + kp;
+  if (n_kept) *n_kept = kp;
+  MK_ARG(k <= nT, "mk_joint_ritz: k exceeds the dimension of the joint space");
+  if (kp > 0) {
+    MK_COUNT(), k_joint_W<<<(N * kp + 127) / 128, 128, 0, s>>>(N, kp, first, sv, Y, W);
+    MK_COUNT(), k_joint_Z<<<(int)(((int64_t)NH * kp + 127) / 128), 128, 0, s>>>(NH, N, kp, G, d, W, Z);
+    MK_COUNT(), k_joint_At<<<(kp * kp + 127) / 128, 128, 0, s>>>(N, kp, A0, W, At);
+  }
+  MK_COUNT(), k_joint_T<<<(int)(((int64_t)nT * nT + 255) / 256), 256, 0, s>>>(NH, kp, d, Z, At, T);
+  MK_COUNT(), k_identity<<<(int)(((int64_t)nT * nT + 255) / 256), 256, 0, s>>>(nT, I);
+  MK_TRY(decompose(ctx, nT, I, true, T, mu, Yt, s, S_EIG5));
+  MK_COUNT(), k_joint_coef<<<(int)(((int64_t)(NH + N) * k + 127) / 128), 128, 0, s>>>(NH, N, kp, k, Yt, W, G, X, tmp);
+  gemm64(NH, k, NH, V, NH, 0, tmp, k, 0, X, k, s);  // coarse coefficients V tmp into rows [0, NH) of X
+  MK_CUDA(cudaMemcpyAsync(lambda, mu, k * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
+int mk_joint_assemble(mk_ctx* ctx, const mk_mesh* m, int k, int N, const double* X, const double* psihat,
+                      const double* u, int ld, double* psi, void* stream) {
+  MK_ARG(ctx && m && X && psihat && u && psi, "mk_joint_assemble: null argument");
+  MK_ARG(N >= 1 && k >= 1 && N <= ld && k <= ld && ld <= MK_MAX_RHS, "mk_joint_assemble: bad N/k/ld");
+  MK_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const Level& F = m->fine;
+  int err = MK_OK;
+  const size_t eb = (size_t)F.n_elems * (F.nloc * (F.nloc + 1) / 2) * sizeof(double);
+  double* Me = (double*)scratch(ctx, S_ELEM64B, eb, &err);
+  double* Mu = (double*)scratch(ctx, S_VEC1, (size_t)F.n_nodes * ld * sizeof(double), &err);
+  double* dots = (double*)scratch(ctx, S_COEF, 64 * sizeof(double), &err);
+  if (!Me || !Mu || !dots) return err;
+  const int64_t work = F.n_nodes * ld;
+  MK_COUNT(), k_joint_orbitals<<<(int)((work + 255) / 256), 256, 0, s>>>(F.n_nodes, m->d_P_off, m->d_P_col, m->d_P_val,
+                                                                         F.d_boundary, X, (int)m->coarse.n_free, k,
+                                                                         psihat, N, ld, psi);
+  MK_TRY(element_matrices(ctx, F, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s));
+  MK_TRY(apply64(ctx, m, Me, u, Mu, k, ld, true, s));
+  MK_TRY(column_dots(ctx, F.n_nodes, psi, Mu, k, ld, dots, s));
+  MK_COUNT(), k_flip<<<(int)((work + 255) / 256), 256, 0, s>>>(F.n_nodes, dots, psi, k, ld);
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
 }
 
 int mk_orbital_assemble(mk_ctx* ctx, const mk_mesh* m, const double* coef, const double* psihat, const double* u,

@@ -270,6 +270,7 @@ enum Slot : int {
   S_FINCTR,                     // arrival counter of the fused reductions of the mixed solve
   S_ELEMP64,                    // FP64 element matrices in patch order (apply64)
   S_BATCH,                      // batched solve: per-problem buffers
+  S_JOINT, S_EIG5,              // joint augmented space: its matrices, its dense decompositions
   S_COUNT
 };
 void* scratch(mk_ctx* ctx, int slot, size_t bytes, int* err);

@@ -116,6 +116,9 @@ _SIGS = {
     "mk_correction_shift": [_vp, _vp, C.POINTER(mk_molecule), C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double),
                             C.POINTER(C.c_double), _vp],
     "mk_ctx_set_option": [_vp, C.c_int, C.c_int],
+    "mk_joint_ritz": [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.POINTER(C.c_int),
+                      _vp],
+    "mk_joint_assemble": [_vp, _vp, C.c_int, C.c_int, _vp, _vp, _vp, C.c_int, _vp, _vp],
     "mk_batch_correction_solve": [_vp, C.c_int, C.POINTER(_vp), C.POINTER(mk_molecule), C.POINTER(C.c_double),
                                   C.POINTER(_vp), C.POINTER(_vp), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                   C.POINTER(mk_solve_opts), C.POINTER(mk_solve_report), _vp],
@@ -515,6 +518,20 @@ def mk_small_eigensolve_static(NH, N, d, V, b, c, beta, gamma, lam, coef, status
     """Allocation-free variant (fixed library workspace; N_H <= 512, N <= 16); returns the status code."""
     return lib().mk_small_eigensolve_static(NH, N, _ptr(d), _ptr(V), _ptr(b), _ptr(c), _ptr(beta), _ptr(gamma),
                                             _ptr(lam), _ptr(coef), _ptr(status), _stream(stream))
+
+
+def mk_joint_ritz(ctx, NH, N, k, d, V, b, c, gramA, gramM, lam, X, stream=None):
+    """Lowest k Ritz pairs of the joint augmented space; returns the number of correction directions kept."""
+    kept = C.c_int()
+    _check(lib().mk_joint_ritz(ctx.h, NH, N, k, _ptr(d), _ptr(V), _ptr(b), _ptr(c), _ptr(gramA), _ptr(gramM),
+                               _ptr(lam), _ptr(X), C.byref(kept), _stream(stream)))
+    return kept.value
+
+
+def mk_joint_assemble(ctx, mesh, k, N, X, psihat, u, psi, stream=None):
+    ld = psihat.shape[1] if psihat.dim() == 2 else 1
+    _check(lib().mk_joint_assemble(ctx.h, mesh.h, k, N, _ptr(X), _ptr(psihat), _ptr(u), ld, _ptr(psi),
+                                   _stream(stream)))
 
 
 def mk_orbital_assemble(ctx, mesh, coef, psihat, u, N, psi, stream=None):
