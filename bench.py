@@ -53,6 +53,8 @@ def parse():
                     help="inner preconditioner of the mixed-precision correction solve (learned: FCG(1))")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve measurement")
+    ap.add_argument("--no-eval", action="store_true",
+                    help="skip the learned-vs-plain evaluation on the 16 unseen 8-nucleus molecules")
     ap.add_argument("--patch-kernel", default="reg", choices=["reg", "pipelined", "single"],
                     help="--mode apply: the FP32 register-staged kernel (default), the two-group pipelined kernel, "
                          "or the one-patch-per-CTA kernel")
@@ -191,6 +193,57 @@ def decompose_mode(a):
                       "ms_per_decomposition": e0.elapsed_time(e1) / a.steps}))
 
 
+def eval_learned(ctx, mlp, max_molecules=16):
+    """The learned preconditioner against plain PCG on the molecules it is evaluated on (never trained on): the
+    correction solves of 16 seeded 8-nucleus molecules on the 857,375-DOF P2 mesh (fine 48^3 cubes of [-15,15]^3,
+    coarse 6^3), N = 13-25 orbitals, to 1e-8 FP64 relative residual, each molecule in four forms: mixed precision
+    with the learned FCG(1), mixed precision with Jacobi PCG, plain FP64 Jacobi PCG, plain FP64 PCG with the
+    degree-4 Chebyshev preconditioner.  One timed solve per molecule and form (CUDA events), after one untimed solve
+    of each form on the first molecule.  Returns DOF x orbitals / s over all molecules per form, with iterations."""
+    import numpy as np
+    import torch
+    from paper_2103_02824_gb300 import learned, mk, synth
+    from paper_2103_02824_gb300.step import upload_workload
+    t0 = time.perf_counter()
+    mesh, _ = upload_workload(ctx, synth.workload("mol8_p2"))
+    forms = {"learned_mixed": mk.opts(precision="mixed", precond="learned", mlp=mlp, rtol=1e-8, check_every=10),
+             "jacobi_mixed": mk.opts(precision="mixed", precond="jacobi", rtol=1e-8, check_every=10),
+             "jacobi_fp64": mk.opts(precision="fp64", precond="jacobi", rtol=1e-8, check_every=10),
+             "chebyshev_fp64": mk.opts(precision="fp64", precond="chebyshev", rtol=1e-8, check_every=10)}
+    res = {k: {"ms": 0.0, "units": 0.0, "iterations": []} for k in forms}
+    Ns = []
+    n_free = mesh.info["n_free"]
+    for i, seed in enumerate(synth.EVAL_SEEDS[:max_molecules]):
+        prob = learned.Problem(ctx, mesh, *synth.molecule(seed, 8))
+        Ns.append(prob.N)
+        for name, o in forms.items():
+            if i == 0:
+                prob.solve(o)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, rep = prob.solve(o)
+            e1.record()
+            torch.cuda.synchronize()
+            assert rep["max_rel_residual"] <= 1e-8, (name, seed, rep["max_rel_residual"])
+            r = res[name]
+            r["ms"] += e0.elapsed_time(e1)
+            r["units"] += float(n_free) * prob.N
+            r["iterations"].append(rep["iterations"])
+        del prob
+    mesh.close()
+    out = {"workload": f"mol8_p2: synthetic 8-nucleus molecules synth.molecule(seed, 8), seeds "
+                       f"{synth.EVAL_SEEDS[0]}-{synth.EVAL_SEEDS[max_molecules - 1]}, P2 tetrahedra, box [-15,15]^3, "
+                       f"fine 48^3 cubes (663,552 tets, {n_free} free DOF), coarse 6^3 cubes (N_H=1331), LDA",
+           "orbitals": Ns, "rtol": 1e-8, "unit": UNIT, "seconds": time.perf_counter() - t0}
+    for name, r in res.items():
+        out[name] = {"value": r["units"] / (r["ms"] * 1e-3), "ms_total": r["ms"],
+                     "mean_iterations": float(np.mean(r["iterations"])), "iterations": r["iterations"]}
+    out["learned_over_jacobi_mixed"] = out["learned_mixed"]["value"] / out["jacobi_mixed"]["value"]
+    out["learned_over_jacobi_fp64"] = out["learned_mixed"]["value"] / out["jacobi_fp64"]["value"]
+    return out
+
+
 def whole_job_ms(ms, dist, device):
     """The timed region of the whole job: the largest of the ranks' own durations (ms), since the job ends when its
     slowest rank does; ms itself on one rank (dist None)."""
@@ -268,25 +321,29 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": reasons, "samples": len(rows)}
 
 
-def train_network(ctx, order, seeds=(3, 4, 5, 6), steps=600, batch=8192):
+TRAIN_SEEDS = tuple(range(1000, 1064))  # 64 seeded 4-nucleus molecules (never the benchmark or evaluation ones)
+
+
+def train_network(ctx, order, seeds=TRAIN_SEEDS, steps=1500, batch=8192):
     """The learned preconditioner's network, trained before any timing on correction solves of other seeded
-    molecules (never the benchmark molecule) on the mid-size mesh of the same kind (the inputs are
-    resolution-free)."""
+    molecules (never the benchmark molecule nor the evaluation molecules) on the mid-size mesh of the same kind (the
+    inputs are resolution-free)."""
     import numpy as np
     from paper_2103_02824_gb300 import learned, mk, synth
     from paper_2103_02824_gb300.step import upload_workload
     t0 = time.perf_counter()
     wl = synth.workload("mol4_p2_mid")
     mesh, _ = upload_workload(ctx, wl)
-    data = [learned.harvest(learned.Problem(ctx, mesh, *synth.molecule(s, 4)), every=2, cap=10) for s in seeds]
+    data = [learned.harvest(learned.Problem(ctx, mesh, *synth.molecule(s, 4)), every=4, cap=5) for s in seeds]
     import torch
     X, U, E = (torch.cat([d[k] for d in data]) for k in range(3))
     mlp = mk.Mlp(ctx, 10 if order == 2 else 4, synth.mlp_init(10 if order == 2 else 4, 0))
     hist = learned.train(ctx, mlp, X, U, E, steps=steps, batch=batch, lr=1e-3, seed=1)
     del X, U, E, data
     mesh.close()
-    return mlp, {"molecules": f"synth.molecule(seed, 4), seeds {list(seeds)}, on mol4_p2_mid (fine 16^3 cubes)",
-                 "samples_from": "FP64 PCG iterates 0, 2, ..., 18 of each correction solve",
+    return mlp, {"molecules": f"synth.molecule(seed, 4), seeds {seeds[0]}-{seeds[-1]} ({len(seeds)} molecules), on "
+                              f"mol4_p2_mid (fine 16^3 cubes)",
+                 "samples_from": "FP64 PCG iterates 0, 4, ..., 16 of each correction solve",
                  "steps": steps, "batch": batch, "loss_first50": float(np.mean(hist[:50])),
                  "loss_last50": float(np.mean(hist[-50:])), "train_s": time.perf_counter() - t0}
 
@@ -482,6 +539,11 @@ def main():
         for bm in bmeshes:
             bm.close()
 
+    # the metric's own comparison, learned vs plain PCG, on the molecules the network is evaluated on
+    evaluation = None
+    if mlp is not None and world == 1 and not a.no_eval:
+        evaluation = eval_learned(ctx, mlp)
+
     # roofline of the dominant kernel (the element-by-element operator application of the correction problems):
     # its algorithmic bytes over the average CUDA-event duration of its launches on the launching stream, every
     # application of the profiled pass (inside the graphs too), the Poisson solve's stiffness kernel excluded
@@ -585,7 +647,7 @@ def main():
             "gpu_launches": launches, "gpu_launches_per_step": launches / a.steps,
             "clocks": clk, "roofline": roof, "roofline_learned": roof_tc, "roofline_stiffness": roof_k,
             "cpu_baseline": cpu, "parity": parity,
-            "compare": compare, "training": train_info, "batch": batch,
+            "compare": compare, "training": train_info, "batch": batch, "learned_vs_plain": evaluation,
             "solve_iterations": solve["iterations"], "solve_max_rel_residual": solve["max_rel_residual"],
             "poisson_iterations": reps["poisson"]["iterations"] if reps["poisson"] else None,
             "lambda": [float(x) for x in lam_head],

@@ -76,9 +76,10 @@ typedef struct {
 } mk_xc;
 
 enum { MK_PREC_FP64 = 0, MK_PREC_MIXED = 1 };
-/* Preconditioners: JACOBI (diagonal), LEARNED (the element-patch network, FCG(1), mixed precision only).
- * CHEBYSHEV is reserved (a polynomial preconditioner for the FP64 comparison); every solve rejects it with
- * MK_ERR_UNSUPPORTED. */
+/* Preconditioners: JACOBI (diagonal); CHEBYSHEV (FP64 only): z = p(D^-1 A) D^-1 r, the degree-4 Chebyshev
+ * polynomial of the Chebyshev iteration (D the diagonal) on [a, 1.1 b] with a, b the extreme Ritz values of 16
+ * Lanczos steps on D^-1/2 A D^-1/2, three operator applications per preconditioner call (a plain comparison for
+ * the learned form); LEARNED (the element-patch network, FCG(1), mixed precision only). */
 enum { MK_PRECOND_JACOBI = 0, MK_PRECOND_CHEBYSHEV = 1, MK_PRECOND_LEARNED = 2 };
 enum { MK_BC_ZERO = 0, MK_BC_MULTIPOLE = 1 };
 
@@ -240,7 +241,7 @@ int mk_assemble_rhs_from_vq(mk_ctx* ctx, const mk_mesh* mesh, const double* u, i
  * x [n_nodes*ld] device: initial guess in, solution psi^ out (boundary rows 0).  opts->precision selects plain
  * FP64 PCG or FP32 inner PCG with FP64 residual refinement; either way convergence is judged on the FP64
  * residual.  The report is filled (stream synchronised).  Errors: MK_ERR_NOT_CONVERGED (x still written),
- * MK_ERR_BREAKDOWN (sigma too small), MK_ERR_INVALID_ARG, MK_ERR_UNSUPPORTED (precond not built). */
+ * MK_ERR_BREAKDOWN (sigma too small), MK_ERR_INVALID_ARG (bad options, e.g. CHEBYSHEV with MIXED). */
 int mk_correction_solve(mk_ctx* ctx, const mk_mesh* mesh, const mk_molecule* mol, double sigma, const double* rhs,
                         double* x, int ld, int N, const mk_solve_opts* opts, mk_solve_report* report, void* stream);
 

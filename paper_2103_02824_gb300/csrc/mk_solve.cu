@@ -112,7 +112,99 @@ __global__ void k_pupdate(int64_t n, const ColState* __restrict__ st, const doub
   p[t] = z[t] + st[j].beta * p[t];
 }
 
-// Plain FP64 Jacobi-PCG on all columns at once.  `Ae` packed element matrices of the SPD operator, `diag` its
+// Lowest (upper = false) or highest eigenvalue of a symmetric tridiagonal matrix (diagonal a, off-diagonal b) by
+// Sturm-sequence bisection (host, tiny).
+static double tridiag_extreme(const std::vector<double>& a, const std::vector<double>& b, bool upper) {
+  const int n = (int)a.size();
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < n; ++i) {
+    double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < n ? std::fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    int count = 0;  // eigenvalues below mid
+    double d = 1.0;
+    for (int i = 0; i < n; ++i) {
+      d = a[i] - mid - (i > 0 ? b[i - 1] * b[i - 1] / d : 0.0);
+      if (d == 0.0) d = -1e-300;
+      if (d < 0) ++count;
+    }
+    if (upper ? count >= n : count >= 1) hi = mid; else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+__global__ void k_scale(int64_t n, double* __restrict__ v, const double* __restrict__ num,
+                        const double* __restrict__ den, int mode) {
+  // mode 0: v *= 1/sqrt(num[0]);  used by Lanczos normalisation
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  (void)den;
+  if (mode == 0) v[i] *= 1.0 / sqrt(num[0]);
+}
+
+__global__ void k_lanczos_w(int64_t n, const uint8_t* __restrict__ bnd, double* __restrict__ w,
+                            const double* __restrict__ v, const double* __restrict__ vprev, double alpha,
+                            double beta) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  w[i] = bnd[i] ? 0.0 : w[i] - alpha * v[i] - beta * vprev[i];
+}
+
+// ------------------------------------------------------------------------------------------------ Chebyshev
+// Polynomial preconditioner z = p(D^-1 A) D^-1 r of degree kChebDegree: the Chebyshev iteration for A z = r with
+// the diagonal D, started at z = 0, on an interval [a, b] of the spectrum of D^-1 A (Saad, Iterative Methods for
+// Sparse Linear Systems, Sec. 12.3).  The same polynomial for every column and every call, so a fixed symmetric
+// linear map; it is positive definite whenever b bounds the spectrum from above and a > 0 (the residual polynomial
+// then stays below 1 on (0, b]).  b is 1.1 times, a once, the extreme Ritz values of kChebLanczos Lanczos steps
+// on D^-1/2 A D^-1/2.
+constexpr int kChebDegree = 4;
+constexpr int kChebLanczos = 16;
+struct ChebCoef {
+  double theta, delta, sigma1;
+};
+// one step: res -= A d; d = c1 d + c2 D^-1 res; z += d (interior rows; columns < N)
+__global__ void k_cheb_step(int64_t n, const uint8_t* __restrict__ bnd, const double* __restrict__ diag,
+                            double* __restrict__ res, const double* __restrict__ Ad, double* __restrict__ d,
+                            double* __restrict__ z, int N, int ld, double c1, double c2, int first) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * ld) return;
+  const int64_t nd = t / ld;
+  const int j = (int)(t % ld);
+  if (j >= N || bnd[nd]) {
+    if (first) { d[t] = 0.0; z[t] = 0.0; }
+    return;
+  }
+  double rv = res[t];
+  if (!first) rv -= Ad[t];
+  res[t] = rv;
+  const double dv = (first ? 0.0 : c1 * d[t]) + c2 * rv / diag[nd];
+  d[t] = dv;
+  z[t] = first ? dv : z[t] + dv;
+}
+__global__ void k_copy_cols(int64_t n, const double* __restrict__ a, double* __restrict__ b, int ld) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n * ld) b[t] = a[t];
+}
+// u = D^-1/2 v (inverse) or D^1/2 v on the interior rows (the Lanczos steps on D^-1/2 A D^-1/2, one column)
+__global__ void k_lz_scale(int64_t n, const uint8_t* __restrict__ bnd, const double* __restrict__ diag,
+                           const double* v, double* u, int inverse) {  // u may be v
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  u[i] = bnd[i] ? 0.0 : (inverse ? v[i] / sqrt(diag[i]) : v[i] * sqrt(diag[i]));
+}
+__global__ void k_lz_start(int64_t n, const uint8_t* __restrict__ bnd, double* __restrict__ v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  // a fixed start vector with no special symmetry: a hash of the node index in (0.5, 1.5)
+  uint32_t h = (uint32_t)i * 2654435761u;
+  h ^= h >> 16;
+  v[i] = bnd[i] ? 0.0 : 0.5 + (double)(h & 0xffffu) / 65536.0;
+}
+
+// Plain FP64 PCG on all columns at once: Jacobi, or the Chebyshev polynomial preconditioner.  `Ae` packed element matrices of the SPD operator, `diag` its
 // assembled diagonal (boundary rows 1).  x: initial guess in, solution out (boundary rows forced to 0).
 int pcg64(mk_ctx* ctx, const mk_mesh* m, const double* Ae, const double* diag, const double* b, double* x, int N,
           int ld, const mk_solve_opts& o, mk_solve_report* rep, cudaStream_t s) {
@@ -141,9 +233,77 @@ int pcg64(mk_ctx* ctx, const mk_mesh* m, const double* Ae, const double* diag, c
     ctx->pinned_size = sizeof(ColState) * MK_MAX_RHS * 2;
   }
   ColState* hst = (ColState*)ctx->pinned;
+  const bool cheb = o.precond == MK_PRECOND_CHEBYSHEV;
+  double* CR = nullptr;   // Chebyshev: its residual, direction and operator product
+  double* CD = nullptr;
+  double* CQ = nullptr;
+  ChebCoef cc{};
+  if (cheb) {
+    CR = (double*)scratch(ctx, S_VEC1, vb, &err);
+    CD = (double*)scratch(ctx, S_VEC2, vb, &err);
+    CQ = (double*)scratch(ctx, S_VEC3, vb, &err);
+    if (!CR || !CD || !CQ) return err;
+    // the interval from Lanczos on D^-1/2 A D^-1/2 (one column, in R, Z, P, Q)
+    const int gn = (int)((n + 255) / 256);
+    double* v = R;
+    double* vp = Z;
+    double* w = P;
+    double* u = Q;
+    MK_COUNT(), k_lz_start<<<gn, 256, 0, s>>>(n, L.d_boundary, v);
+    MK_TRY(column_dots(ctx, n, v, v, 1, 1, d1, s));
+    MK_COUNT(), k_scale<<<gn, 256, 0, s>>>(n, v, d1, nullptr, 0);
+    MK_CUDA(cudaMemsetAsync(vp, 0, n * sizeof(double), s));
+    std::vector<double> al, be;
+    double beta = 0.0;
+    for (int k = 0; k < kChebLanczos; ++k) {
+      MK_COUNT(), k_lz_scale<<<gn, 256, 0, s>>>(n, L.d_boundary, diag, v, u, 1);   // u = D^-1/2 v
+      MK_TRY(apply_patch<double>(ctx, m, Ap, u, w, 1, true, s));                      // w = A u
+      MK_COUNT(), k_lz_scale<<<gn, 256, 0, s>>>(n, L.d_boundary, diag, w, w, 1);   // w = D^-1/2 A D^-1/2 v
+      MK_TRY(column_dots(ctx, n, v, w, 1, 1, d2, s));
+      double alpha;
+      MK_CUDA(cudaMemcpyAsync(&alpha, d2, sizeof(double), cudaMemcpyDeviceToHost, s));
+      MK_CUDA(cudaStreamSynchronize(s));
+      MK_COUNT(), k_lanczos_w<<<gn, 256, 0, s>>>(n, L.d_boundary, w, v, vp, alpha, beta);
+      MK_TRY(column_dots(ctx, n, w, w, 1, 1, d3, s));
+      double bb;
+      MK_CUDA(cudaMemcpyAsync(&bb, d3, sizeof(double), cudaMemcpyDeviceToHost, s));
+      MK_CUDA(cudaStreamSynchronize(s));
+      al.push_back(alpha);
+      beta = std::sqrt(std::max(bb, 0.0));
+      if (beta == 0.0 || k + 1 == kChebLanczos) break;
+      be.push_back(beta);
+      MK_CUDA(cudaMemcpyAsync(vp, v, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      MK_CUDA(cudaMemcpyAsync(v, w, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      MK_COUNT(), k_scale<<<gn, 256, 0, s>>>(n, v, d3, nullptr, 0);
+    }
+    be.resize(al.size() > 0 ? al.size() - 1 : 0);
+    const double lo = tridiag_extreme(al, be, false), hi = 1.1 * tridiag_extreme(al, be, true);
+    MK_ARG(lo > 0.0 && hi > lo, "Chebyshev preconditioner: the operator is not positive definite");
+    cc.theta = 0.5 * (hi + lo);
+    cc.delta = 0.5 * (hi - lo);
+    cc.sigma1 = cc.theta / cc.delta;
+  }
+  // z = p(D^-1 A) D^-1 r for all columns (Chebyshev)
+  auto cheb_apply = [&](const double* r, double* z) -> int {
+    MK_COUNT(), k_copy_cols<<<gb, th, 0, s>>>(n, r, CR, ld);
+    double rho = 1.0 / cc.sigma1;
+    MK_COUNT(), k_cheb_step<<<gb, th, 0, s>>>(n, L.d_boundary, diag, CR, CQ, CD, z, N, ld, 0.0, 1.0 / cc.theta, 1);
+    for (int k = 1; k < kChebDegree; ++k) {
+      MK_TRY(apply_patch<double>(ctx, m, Ap, CD, CQ, ld, true, s));
+      const double rho_new = 1.0 / (2.0 * cc.sigma1 - rho);
+      MK_COUNT(), k_cheb_step<<<gb, th, 0, s>>>(n, L.d_boundary, diag, CR, CQ, CD, z, N, ld, rho_new * rho,
+                                                2.0 * rho_new / cc.delta, 0);
+      rho = rho_new;
+    }
+    return MK_OK;
+  };
 
   MK_TRY(apply_patch<double>(ctx, m, Ap, x, Q, ld, true, s));
   MK_COUNT(), k_residual<<<gb, th, 0, s>>>(n, L.d_boundary, b, Q, diag, R, Z, P, N, ld);
+  if (cheb) {
+    MK_TRY(cheb_apply(R, Z));
+    MK_COUNT(), k_copy_cols<<<gb, th, 0, s>>>(n, Z, P, ld);
+  }
   // x boundary rows to 0 (Q := 0 then mask trick): write x = x - 0 on interior, 0 on boundary
   MK_TRY(column_dots(ctx, n, b, b, N, ld, d1, s));
   MK_TRY(column_dots(ctx, n, R, Z, N, ld, d2, s));
@@ -168,6 +328,7 @@ int pcg64(mk_ctx* ctx, const mk_mesh* m, const double* Ae, const double* diag, c
     MK_TRY(column_dots(ctx, n, P, Q, N, ld, d1, s));
     MK_COUNT(), k_alpha<<<1, MK_MAX_RHS, 0, s>>>(st, d1, N);
     MK_COUNT(), k_update<<<gb, th, 0, s>>>(n, st, P, Q, diag, x, R, Z, N, ld);
+    if (cheb) MK_TRY(cheb_apply(R, Z));
     MK_TRY(column_dots(ctx, n, R, Z, N, ld, d2, s));
     MK_TRY(column_dots(ctx, n, R, R, N, ld, d3, s));
     MK_COUNT(), k_beta<<<1, MK_MAX_RHS, 0, s>>>(st, d2, d3, N, o.rtol);
@@ -222,6 +383,7 @@ static bool valid_opts(const mk_solve_opts* o) {
   if (o->precond == MK_PRECOND_LEARNED)
     return o->precision == MK_PREC_MIXED && o->mlp != nullptr &&
            (o->mlp_precision == MK_MLP_FP32 || o->mlp_precision == MK_MLP_BF16);
+  if (o->precond == MK_PRECOND_CHEBYSHEV) return o->precision == MK_PREC_FP64;
   return o->precond == MK_PRECOND_JACOBI;
 }
 
@@ -240,23 +402,6 @@ __global__ void k_axpy_interior(int64_t n, const uint8_t* __restrict__ bnd, cons
   const int64_t nd = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (nd >= n || bnd[nd]) return;
   w[nd] += d[nd];
-}
-
-__global__ void k_scale(int64_t n, double* __restrict__ v, const double* __restrict__ num,
-                        const double* __restrict__ den, int mode) {
-  // mode 0: v *= 1/sqrt(num[0]);  used by Lanczos normalisation
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  (void)den;
-  if (mode == 0) v[i] *= 1.0 / sqrt(num[0]);
-}
-
-__global__ void k_lanczos_w(int64_t n, const uint8_t* __restrict__ bnd, double* __restrict__ w,
-                            const double* __restrict__ v, const double* __restrict__ vprev, double alpha,
-                            double beta) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  w[i] = bnd[i] ? 0.0 : w[i] - alpha * v[i] - beta * vprev[i];
 }
 
 __global__ void k_scatter_free(int64_t nf, const int32_t* __restrict__ free_idx, const double* __restrict__ src,
@@ -408,7 +553,7 @@ int mk_correction_solve(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, d
     return solve_mixed(ctx, m, mol, sigma, rhs, nullptr, nullptr, x, ld, N, *opts, report, s);
   }
   MK_ARG(opts->precision == MK_PREC_FP64, "mk_correction_solve: bad precision");
-  if (opts->precond != MK_PRECOND_JACOBI) return fail(MK_ERR_UNSUPPORTED, "FP64 path supports Jacobi only");
+
   int err = MK_OK;
   double* Ae = (double*)scratch(ctx, S_ELEM64, (size_t)L.n_elems * (L.nloc * (L.nloc + 1) / 2) * sizeof(double), &err);
   double* diag = (double*)scratch(ctx, S_DIAG64, L.n_nodes * sizeof(double), &err);
@@ -418,29 +563,6 @@ int mk_correction_solve(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, d
   MK_TRY(element_matrices(ctx, L, nullptr, 0.0, 0.0, sigma, nullptr, Ae, s, H0));
   MK_TRY(assemble_diagonal(ctx, L, Ae, diag, s));
   return pcg64(ctx, m, Ae, diag, rhs, x, N, ld, *opts, report, s);
-}
-
-// Symmetric tridiagonal lowest eigenvalue by Sturm-sequence bisection (host, tiny).
-static double tridiag_lowest(const std::vector<double>& a, const std::vector<double>& b) {
-  const int n = (int)a.size();
-  double lo = 1e300, hi = -1e300;
-  for (int i = 0; i < n; ++i) {
-    double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < n ? std::fabs(b[i]) : 0.0);
-    lo = std::min(lo, a[i] - r);
-    hi = std::max(hi, a[i] + r);
-  }
-  for (int it = 0; it < 200; ++it) {
-    double mid = 0.5 * (lo + hi);
-    int count = 0;
-    double d = 1.0;
-    for (int i = 0; i < n; ++i) {
-      d = a[i] - mid - (i > 0 ? b[i - 1] * b[i - 1] / d : 0.0);
-      if (d == 0.0) d = -1e-300;
-      if (d < 0) ++count;
-    }
-    if (count >= 1) hi = mid; else lo = mid;
-  }
-  return 0.5 * (lo + hi);
 }
 
 int mk_lowest_ritz(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, const double* v0, int steps,
@@ -500,7 +622,7 @@ int mk_lowest_ritz(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, const 
     MK_COUNT(), k_scale<<<(int)((n + 255) / 256), 256, 0, s>>>(n, v, dd, nullptr, 0);
   }
   b.resize(a.size() > 0 ? a.size() - 1 : 0);
-  *theta = tridiag_lowest(a, b);
+  *theta = tridiag_extreme(a, b, false);
   MK_CUDA(cudaGetLastError());
   return MK_OK;
 }

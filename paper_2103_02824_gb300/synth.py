@@ -271,7 +271,7 @@ def mlp_init(nloc: int, seed: int, nh: int = 64, out_scale: float = 0.1) -> np.n
     return np.concatenate(parts).astype(np.float32)
 
 
-def workload(name: str):
+def workload(name: str, seed: int = 2000):
     """Named workloads of the paper's kind, with their sizes.
 
     'h_p1'  : hydrogen, box [-10,10]^3, P1, coarse 4^3 cubes, fine 16^3 cubes (24,576 tetrahedra).
@@ -281,6 +281,10 @@ def workload(name: str):
     'cluster12_p2': 12 nuclei (seed 5), box [-15,15]^3, P2, coarse 4^3 cubes, fine mesh graded toward the nuclei
                (graded_mesh, longest edge <= max(0.05, 0.3 r): about 0.87 M tetrahedra), N <= 48, LDA.
     'cluster12_p2_small': the same cluster graded with h_min = 1.5, alpha = 1.0 (9,782 tetrahedra).
+    'mol8_p2'     : the evaluation molecules of the learned preconditioner: 8 nuclei (molecule(seed, 8), seeds
+               2000-2015; `seed` picks one), box [-15,15]^3, P2, coarse 6^3 cubes (N_H = 1,331), fine 48^3 cubes
+               (663,552 tetrahedra, 857,375 free DOF), N = ceil(sum Z / 2) <= 32, LDA.
+    'mol8_p2_small': the same molecules on fine 12^3 cubes (10,368 tetrahedra, 12,167 free DOF).
     """
     if name == "h_p1":
         Z, R = hydrogen()
@@ -294,7 +298,14 @@ def workload(name: str):
         h_min, alpha = {"cluster12_p2": (0.05, 0.3), "cluster12_p2_small": (1.5, 1.0)}[name]
         return dict(name=name, Z=Z, R=R, order=2, half=15.0, n_coarse=4, mesh="graded", h_min=h_min, alpha=alpha,
                     xc="lda")
+    if name in ("mol8_p2", "mol8_p2_small"):
+        Z, R = molecule(seed, 8)
+        return dict(name=name, Z=Z, R=R, order=2, half=15.0, n_coarse=6, levels=3 if name == "mol8_p2" else 1,
+                    xc="lda", seed=seed)
     raise KeyError(name)
+
+
+EVAL_SEEDS = tuple(range(2000, 2016))  # molecules the learned preconditioner is evaluated on (never trained on)
 
 
 def workload_meshes(wl):
