@@ -394,8 +394,10 @@ def main():
         prec = "fp64" if kind == "fp64" else "mixed"
         pc = "learned" if kind == "learned" else "jacobi"
         so = mk.opts(precision=prec, precond=pc, mlp=mlp if pc == "learned" else None, rtol=1e-8, check_every=10)
-        # the Hartree Poisson solve of the mixed forms uses the two-level (coarse-space) preconditioner
-        po = mk.opts(precision=prec, rtol=1e-8, check_every=10, coarse=prec == "mixed")
+        # the Hartree Poisson solve of the mixed forms uses the multigrid V-cycle on the mesh hierarchy (the
+        # two-level coarse-space preconditioner where the mesh has no hierarchy)
+        pc = ("multigrid" if mesh.multigrid else True) if prec == "mixed" else False
+        po = mk.opts(precision=prec, rtol=1e-8, check_every=10, coarse=pc)
         return so, po
 
     def make_step(kind):

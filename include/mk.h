@@ -101,9 +101,13 @@ typedef struct {
   int trace_every, trace_cap;
   double* trace_x;
   double* trace_r;
-  /* MIXED only: add the exact coarse-space correction P A_H^-1 P^T r to the preconditioner (two-level additive:
-   * Jacobi or learned fine part plus the Galerkin coarse operator A_H = P^T A P on V_H, inverted densely once
-   * per mesh for the Poisson operator and once per (molecule, sigma) for the correction operator) */
+  /* MIXED only.  1: add the exact coarse-space correction P A_H^-1 P^T r to the preconditioner (two-level:
+   * Jacobi or learned fine part plus the Galerkin coarse operator A_H = P^T A P on V_H, inverted densely once per
+   * mesh for the Poisson operator and once per (molecule, sigma) for the correction operator; for the Poisson
+   * solve the multiplicative form Jacobi sweep / coarse correction / Jacobi sweep).  2 (Hartree Poisson solve
+   * only, on a mesh with mk_mesh_set_hierarchy): the multigrid V(1,1) cycle over the fine mesh, the intermediate
+   * levels and V_H (damped Jacobi, w = 0.8, one sweep before and after each coarse-level correction; the dense
+   * inverse on V_H) -- the multigrid solver the paper names for its boundary-value problems (Sec. 3.1). */
   int coarse;
 } mk_solve_opts;
 
@@ -188,6 +192,19 @@ int mk_profile_read(mk_ctx* ctx, int kind, double* total_ms, long long* count);
 int mk_mesh_upload(mk_ctx* ctx, const mk_mesh_desc* fine, const mk_mesh_desc* coarse, const int32_t* fine_parent,
                    mk_mesh** out);
 int mk_mesh_destroy(mk_mesh* mesh);
+/* Intermediate levels of a nested hierarchy between the coarse and the fine mesh of `mesh`, for the multigrid
+ * preconditioner of the Hartree Poisson solve (mk_solve_opts.coarse = 2): levels[0..n_mid) from coarsest to
+ * finest, levels[0] nested in the coarse mesh, each next one in the previous, the fine mesh in the last;
+ * parents[k] [levels[k].n_elems] gives the element of the next coarser mesh that contains each element of
+ * levels[k], and parents[n_mid] [fine n_elems] the element of levels[n_mid - 1] containing each fine element
+ * (n_mid = 0: the fine mesh directly on V_H; parents may then be NULL).  Host arrays, read during the call.  Built
+ * here on the host and kept by the handle: each level's numbering and boundary, its stiffness matrix on the
+ * interior nodes (FP32 CSR) and inverse diagonal, the interpolation between consecutive levels (coarse basis
+ * functions at the finer nodes, exact on nested meshes) and its transpose.  Replaces an earlier hierarchy;
+ * synchronises the device.  Errors: MK_ERR_INVALID_ARG (orders differ, a level not nested in its parent),
+ * MK_ERR_OOM. */
+int mk_mesh_set_hierarchy(mk_mesh* mesh, int n_mid, const mk_mesh_desc* levels, const int32_t* const* parents);
+
 int mk_mesh_get_info(const mk_mesh* mesh, mk_mesh_info* info);
 /* Host copies of the A0 results, for checking: level 0 = fine, 1 = coarse.  Any pointer may be NULL.
  * nodes [n_nodes*3], boundary [n_nodes] (1 = boundary), elem [n_elems*nloc] node indices, colour [n_elems]. */

@@ -439,6 +439,130 @@ static void free_level(Level& L) {
   L.d_geom = nullptr;
 }
 
+
+// ------------------------------------------------------------------------------------------------ nested levels
+// Interpolation from the coarser level C into the finer level F of a nested pair (each fine element inside its
+// parent): one row per fine node, the coarse basis functions of the parent evaluated at the node (exact: V_C is a
+// subspace of V_F).  Columns: the free DOF of C (free_cols) or the nodes of C, boundary nodes of C left out either
+// way; entries below 1e-12 dropped.  Errors: a fine node outside its element's parent, an unused fine node.
+static int build_interp(const Level& F, const Level& C, const std::vector<int32_t>& parent, bool free_cols,
+                        std::vector<int32_t>& P_off, std::vector<int32_t>& P_col, std::vector<double>& P_val) {
+  const int nloc = F.nloc;
+  std::vector<int64_t> first(F.n_nodes, -1);
+  for (int64_t i = 0; i < F.n_elems * nloc; ++i)
+    if (first[F.elem[i]] < 0) first[F.elem[i]] = i;
+  P_off.assign(F.n_nodes + 1, 0);
+  P_col.clear();
+  P_val.clear();
+  for (int64_t nd = 0; nd < F.n_nodes; ++nd) {
+    if (first[nd] < 0) return fail(MK_ERR_INVALID_ARG, "nested levels: unused fine node");
+    const int64_t e = first[nd] / nloc;
+    const int32_t T = parent[e];
+    const Geom& g = C.geom[T];
+    const double dx[3] = {F.nodes[nd * 3] - g.x0[0], F.nodes[nd * 3 + 1] - g.x0[1], F.nodes[nd * 3 + 2] - g.x0[2]};
+    double sref[3];
+    for (int rr = 0; rr < 3; ++rr)
+      sref[rr] = g.Jinv[rr * 3] * dx[0] + g.Jinv[rr * 3 + 1] * dx[1] + g.Jinv[rr * 3 + 2] * dx[2];
+    const double lam[4] = {1.0 - sref[0] - sref[1] - sref[2], sref[0], sref[1], sref[2]};
+    for (double l : lam)
+      if (l < -1e-9 || l > 1.0 + 1e-9) return fail(MK_ERR_INVALID_ARG, "nested levels: fine element outside its parent");
+    double phi[kMaxLoc];
+    basis_host(C.order, lam, phi, nullptr);
+    for (int b = 0; b < C.nloc; ++b) {
+      const int32_t cn = C.elem[(int64_t)T * C.nloc + b];
+      const int32_t cf = C.node_to_free[cn];
+      if (cf >= 0 && std::fabs(phi[b]) > 1e-12) {
+        P_col.push_back(free_cols ? cf : cn);
+        P_val.push_back(phi[b]);
+      }
+    }
+    P_off[nd + 1] = (int32_t)P_col.size();
+  }
+  return MK_OK;
+}
+
+// The transpose of a CSR matrix with n_cols columns (rows of the result in column order, entries in row order).
+static void transpose_csr(int64_t n_cols, const std::vector<int32_t>& off, const std::vector<int32_t>& col,
+                          const std::vector<double>& val, std::vector<int32_t>& toff, std::vector<int32_t>& tcol,
+                          std::vector<double>& tval) {
+  const int64_t n_rows = (int64_t)off.size() - 1;
+  toff.assign(n_cols + 1, 0);
+  for (int32_t c : col) toff[c + 1]++;
+  for (int64_t k = 0; k < n_cols; ++k) toff[k + 1] += toff[k];
+  tcol.assign(col.size(), 0);
+  tval.assign(col.size(), 0.0);
+  std::vector<int32_t> pos(toff.begin(), toff.end() - 1);
+  for (int64_t r = 0; r < n_rows; ++r)
+    for (int32_t k = off[r]; k < off[r + 1]; ++k) {
+      const int32_t p = pos[col[k]]++;
+      tcol[p] = (int32_t)r;
+      tval[p] = val[k];
+    }
+}
+
+// The stiffness matrix (grad phi_a, grad phi_b) of a level on its interior nodes (node indexing; boundary rows and
+// columns left out), CSR with sorted columns, and its diagonal: per element |det J| (J^-1 J^-T)_ij times the
+// reference components (Sec. 2, the bilinear form of the Hartree equation).
+static void stiffness_csr(const Level& L, const RefTables& R, std::vector<int32_t>& off, std::vector<int32_t>& col,
+                          std::vector<double>& val, std::vector<double>& diag) {
+  const int nloc = L.nloc;
+  std::vector<std::pair<int64_t, double>> trip;  // key row * n + col
+  trip.reserve((size_t)L.n_elems * nloc * nloc);
+  const int I6[6] = {0, 1, 2, 0, 0, 1}, J6[6] = {0, 1, 2, 1, 2, 2};
+  for (int64_t e = 0; e < L.n_elems; ++e) {
+    const Geom& g = L.geom[e];
+    double fac[6];
+    for (int c = 0; c < 6; ++c)
+      fac[c] = std::fabs(g.det) * (g.Jinv[I6[c] * 3] * g.Jinv[J6[c] * 3] + g.Jinv[I6[c] * 3 + 1] * g.Jinv[J6[c] * 3 + 1] +
+                                   g.Jinv[I6[c] * 3 + 2] * g.Jinv[J6[c] * 3 + 2]);
+    for (int a = 0; a < nloc; ++a) {
+      const int32_t na = L.elem[e * nloc + a];
+      if (L.boundary[na]) continue;
+      for (int b = 0; b < nloc; ++b) {
+        const int32_t nb = L.elem[e * nloc + b];
+        if (L.boundary[nb]) continue;
+        double k = 0.0;
+        for (int c = 0; c < 6; ++c) k += fac[c] * R.stiff[c][sym_index(a, b, nloc)];
+        trip.emplace_back((int64_t)na * L.n_nodes + nb, k);
+      }
+    }
+  }
+  std::sort(trip.begin(), trip.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+  off.assign(L.n_nodes + 1, 0);
+  col.clear();
+  val.clear();
+  diag.assign(L.n_nodes, 0.0);
+  for (size_t i = 0; i < trip.size();) {
+    const int64_t key = trip[i].first;
+    double v = 0.0;
+    for (; i < trip.size() && trip[i].first == key; ++i) v += trip[i].second;  // element order within the key
+    const int64_t r = key / L.n_nodes, c = key % L.n_nodes;
+    col.push_back((int32_t)c);
+    val.push_back(v);
+    off[r + 1]++;
+    if (r == c) diag[r] = v;
+  }
+  for (int64_t k = 0; k < L.n_nodes; ++k) off[k + 1] += off[k];
+}
+
+static int upload_csr(Csr32& d, const std::vector<int32_t>& off, const std::vector<int32_t>& col,
+                      const std::vector<double>& val) {
+  d.n_rows = (int64_t)off.size() - 1;
+  d.nnz = (int64_t)col.size();
+  std::vector<float> v32(val.begin(), val.end());
+  MK_TRY(upload(&d.d_off, off.data(), off.size()));
+  MK_TRY(upload(&d.d_col, col.data(), std::max<size_t>(col.size(), 1)));
+  MK_TRY(upload(&d.d_val, v32.data(), std::max<size_t>(v32.size(), 1)));
+  return MK_OK;
+}
+
+void free_csr(Csr32& c) {
+  cudaFree(c.d_off);
+  cudaFree(c.d_col);
+  cudaFree(c.d_val);
+  c = Csr32{};
+}
+
 int mesh_mass_factor(mk_ctx* ctx, mk_mesh* m);  // mk_eig.cu
 
 }  // namespace mk
@@ -567,36 +691,10 @@ int mk_mesh_upload(mk_ctx* ctx, const mk_mesh_desc* fine, const mk_mesh_desc* co
   m->parent.assign(fine_parent, fine_parent + F.n_elems);
   for (int32_t p : m->parent)
     if (p < 0 || p >= C.n_elems) { delete m; return fail(MK_ERR_INVALID_ARG, "mk_mesh_upload: parent out of range"); }
-  // prolongation rows: first occurrence of each fine node, coarse basis of the parent evaluated there
-  const int nloc = F.nloc;
-  std::vector<int64_t> first(F.n_nodes, -1);
-  for (int64_t i = 0; i < F.n_elems * nloc; ++i)
-    if (first[F.elem[i]] < 0) first[F.elem[i]] = i;
-  std::vector<int32_t> P_off(F.n_nodes + 1, 0), P_col;
+  std::vector<int32_t> P_off, P_col;
   std::vector<double> P_val;
-  for (int64_t nd = 0; nd < F.n_nodes; ++nd) {
-    if (first[nd] < 0) { delete m; return fail(MK_ERR_INVALID_ARG, "mk_mesh_upload: unused fine node"); }
-    int64_t e = first[nd] / nloc;
-    int32_t T = m->parent[e];
-    const Geom& g = C.geom[T];
-    double dx[3] = {F.nodes[nd * 3] - g.x0[0], F.nodes[nd * 3 + 1] - g.x0[1], F.nodes[nd * 3 + 2] - g.x0[2]};
-    double s[3];
-    for (int rr = 0; rr < 3; ++rr) s[rr] = g.Jinv[rr * 3] * dx[0] + g.Jinv[rr * 3 + 1] * dx[1] + g.Jinv[rr * 3 + 2] * dx[2];
-    double lam[4] = {1.0 - s[0] - s[1] - s[2], s[0], s[1], s[2]};
-    for (double l : lam)
-      if (l < -1e-9 || l > 1.0 + 1e-9) { delete m; return fail(MK_ERR_INVALID_ARG, "mk_mesh_upload: fine element outside its parent"); }
-    double phi[kMaxLoc];
-    basis_host(C.order, lam, phi, nullptr);
-    for (int b = 0; b < C.nloc; ++b) {
-      int32_t cn = C.elem[(int64_t)T * C.nloc + b];
-      int32_t cf = C.node_to_free[cn];
-      if (cf >= 0 && std::fabs(phi[b]) > 1e-12) {
-        P_col.push_back(cf);
-        P_val.push_back(phi[b]);
-      }
-    }
-    P_off[nd + 1] = (int32_t)P_col.size();
-  }
+  r = build_interp(F, C, m->parent, true, P_off, P_col, P_val);
+  if (r != MK_OK) { delete m; return r; }
   // transpose: coarse free DOF -> fine nodes (increasing)
   std::vector<int32_t> PT_off(C.n_free + 1, 0), PT_col(P_col.size());
   std::vector<double> PT_val(P_col.size());
@@ -654,6 +752,13 @@ int mk_mesh_destroy(mk_mesh* m) {
   cudaFree(m->d_K64diag);
   cudaFree(m->d_cinv_corr);
   if (m->static_ev) cudaEventDestroy(m->static_ev);
+  for (MgLevel& g : m->mg) {
+    free_level(g.L);
+    free_csr(g.K); free_csr(g.P); free_csr(g.R);
+    cudaFree(g.d_dinv);
+  }
+  free_csr(m->mgP);
+  free_csr(m->mgR);
   delete m;
   return MK_OK;
 }
@@ -681,6 +786,85 @@ int mk_mesh_get_topology(const mk_mesh* m, int level, double* nodes, uint8_t* bo
   if (boundary) std::memcpy(boundary, L.boundary.data(), L.boundary.size());
   if (elem) std::memcpy(elem, L.elem.data(), L.elem.size() * sizeof(int32_t));
   if (colour) std::memcpy(colour, L.colour.data(), L.colour.size() * sizeof(int32_t));
+  return MK_OK;
+}
+
+
+int mk_mesh_set_hierarchy(mk_mesh* m, int n_mid, const mk_mesh_desc* levels, const int32_t* const* parents) {
+  MK_ARG(m && n_mid >= 0 && n_mid <= 16 && (n_mid == 0 || (levels && parents)), "mk_mesh_set_hierarchy: bad argument");
+  MK_CUDA(cudaSetDevice(m->device));
+  MK_CUDA(cudaDeviceSynchronize());
+  const RefTables& R = m->ctx->h_ref[m->fine.order];
+  std::vector<MgLevel> mg(n_mid);
+  auto cleanup = [&]() {
+    for (MgLevel& g : mg) {
+      free_level(g.L);
+      free_csr(g.K); free_csr(g.P); free_csr(g.R);
+      cudaFree(g.d_dinv);
+    }
+  };
+  int r = MK_OK;
+  std::vector<int32_t> off, col, toff, tcol;
+  std::vector<double> val, tval, diag;
+  for (int k = 0; k < n_mid && r == MK_OK; ++k) {
+    MgLevel& g = mg[k];
+    r = build_level(&levels[k], g.L, "hierarchy level");
+    if (r != MK_OK) break;
+    if (g.L.order != m->fine.order) { r = fail(MK_ERR_INVALID_ARG, "mk_mesh_set_hierarchy: orders differ"); break; }
+    const Level& C = k == 0 ? m->coarse : mg[k - 1].L;
+    std::vector<int32_t> par(parents[k], parents[k] + g.L.n_elems);
+    for (int32_t p : par)
+      if (p < 0 || p >= C.n_elems) { r = fail(MK_ERR_INVALID_ARG, "mk_mesh_set_hierarchy: parent out of range"); break; }
+    if (r != MK_OK) break;
+    r = build_interp(g.L, C, par, k == 0, off, col, val);
+    if (r != MK_OK) break;
+    transpose_csr(k == 0 ? C.n_free : C.n_nodes, off, col, val, toff, tcol, tval);
+    r = upload_csr(g.P, off, col, val);
+    if (r == MK_OK) r = upload_csr(g.R, toff, tcol, tval);
+    if (r != MK_OK) break;
+    stiffness_csr(g.L, R, off, col, val, diag);
+    r = upload_csr(g.K, off, col, val);
+    if (r != MK_OK) break;
+    std::vector<float> dinv(g.L.n_nodes, 0.f);
+    for (int64_t i = 0; i < g.L.n_nodes; ++i)
+      if (!g.L.boundary[i] && diag[i] > 0) dinv[i] = (float)(1.0 / diag[i]);
+    r = upload(&g.d_dinv, dinv.data(), dinv.size());
+    if (r == MK_OK) r = upload(&g.L.d_boundary, g.L.boundary.data(), g.L.boundary.size());
+  }
+  // the fine mesh from the finest intermediate level (or from V_H)
+  Csr32 P, Rt;
+  if (r == MK_OK) {
+    if (n_mid > 0) {
+      std::vector<int32_t> par(parents[n_mid], parents[n_mid] + m->fine.n_elems);
+      for (int32_t p : par)
+        if (p < 0 || p >= mg[n_mid - 1].L.n_elems) r = fail(MK_ERR_INVALID_ARG, "mk_mesh_set_hierarchy: parent out of range");
+      if (r == MK_OK) r = build_interp(m->fine, mg[n_mid - 1].L, par, false, off, col, val);
+      if (r == MK_OK) transpose_csr(mg[n_mid - 1].L.n_nodes, off, col, val, toff, tcol, tval);
+    } else {
+      r = build_interp(m->fine, m->coarse, m->parent, true, off, col, val);
+      if (r == MK_OK) transpose_csr(m->coarse.n_free, off, col, val, toff, tcol, tval);
+    }
+    if (r == MK_OK) r = upload_csr(P, off, col, val);
+    if (r == MK_OK) r = upload_csr(Rt, toff, tcol, tval);
+  }
+  if (r != MK_OK) {
+    cleanup();
+    free_csr(P);
+    free_csr(Rt);
+    return r;
+  }
+  // replace an earlier hierarchy
+  for (MgLevel& g : m->mg) {
+    free_level(g.L);
+    free_csr(g.K); free_csr(g.P); free_csr(g.R);
+    cudaFree(g.d_dinv);
+  }
+  free_csr(m->mgP);
+  free_csr(m->mgR);
+  m->mg = std::move(mg);
+  m->mgP = P;
+  m->mgR = Rt;
+  m->has_mg = true;
   return MK_OK;
 }
 

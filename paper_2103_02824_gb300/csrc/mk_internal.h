@@ -134,6 +134,23 @@ struct Patches {
 constexpr int kRecHeader = 32;
 int patch_elems(int nloc);
 
+// A CSR matrix on the device (FP32 values): rows [n_rows], off [n_rows + 1].
+struct Csr32 {
+  int64_t n_rows = 0, nnz = 0;
+  int32_t* d_off = nullptr;
+  int32_t* d_col = nullptr;
+  float* d_val = nullptr;
+};
+// An intermediate level of the multigrid hierarchy of the Hartree Poisson solve: its mesh, the stiffness matrix on
+// its interior nodes (node indexing, boundary rows empty), the inverse diagonal (boundary 0), the interpolation P
+// from the next coarser level (rows: this level's nodes; columns: the coarser level's interior nodes, or the free
+// DOF of V_H for the coarsest intermediate level) and its transpose R.
+struct MgLevel {
+  Level L;
+  Csr32 K, P, R;
+  float* d_dinv = nullptr;
+};
+
 }  // namespace mk
 
 struct mk_ctx {
@@ -229,6 +246,11 @@ struct mk_mesh {
   mutable double* d_K64diag = nullptr;
   mutable float* d_cinv_corr = nullptr;
   mutable std::vector<double> cinv_corr_key;
+  // multigrid hierarchy (mk_mesh_set_hierarchy): intermediate levels coarsest first, and the interpolation from the
+  // finest intermediate level (or from V_H when there is none) into the fine mesh with its transpose
+  std::vector<mk::MgLevel> mg;
+  mk::Csr32 mgP, mgR;
+  bool has_mg = false;
 };
 
 namespace mk {
@@ -271,9 +293,11 @@ enum Slot : int {
   S_ELEMP64,                    // FP64 element matrices in patch order (apply64)
   S_BATCH,                      // batched solve: per-problem buffers
   S_JOINT, S_EIG5,              // joint augmented space: its matrices, its dense decompositions
+  S_MG,                         // multigrid V-cycle: per-level right-hand sides, iterates, operator products
   S_COUNT
 };
 void* scratch(mk_ctx* ctx, int slot, size_t bytes, int* err);
+void free_csr(Csr32& c);
 // element patches of the fine mesh (mk_patches.cpp): pe elements per patch, 0 = the default for the order
 int build_patches(mk_mesh* m, int pe = 0);
 void free_patches(Patches& p);

@@ -649,6 +649,133 @@ __global__ void k_tl_resid(int64_t n, const uint8_t* __restrict__ bnd, const flo
 
 // z0_ready: z already holds the first sweep w D^-1 r (written by the FCG update kernel); defer_final: the last
 // sweep z += w D^-1 (r - q) is left to the caller's next kernel (q = the S_TLQ scratch, A z at that point).
+// ------------------------------------------------------------------------------------------------ multigrid
+// The V(1,1) cycle of the Hartree Poisson operator on the nested hierarchy fine mesh > intermediate levels > V_H
+// (one column, FP32), the preconditioner of the multigrid FCG: on each level from the fine one down, x = w D^-1 b
+// (one damped Jacobi sweep from zero), the residual b - A x restricted to the next level by P^T; on V_H the dense
+// inverse of P^T K P; then on each level back up, x += P x_coarse and one more sweep x += w D^-1 (b - A x).  The
+// same smoother before and after and restriction = transpose of interpolation: a symmetric positive definite
+// preconditioner for w below 2 / lambda_max(D^-1 A) on every level.
+__global__ void k_mg_jac0(int64_t n, const float* __restrict__ dinv, const float* __restrict__ b,
+                          float* __restrict__ x, float w) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = w * dinv[i] * b[i];
+}
+__global__ void k_mg_post(int64_t n, const float* __restrict__ dinv, const float* __restrict__ b,
+                          const float* __restrict__ q, float* __restrict__ x, float w) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = fmaf(w * dinv[i], b[i] - q[i], x[i]);
+}
+// y = K x (CSR, one warp per row)
+__global__ void k_mg_spmv(int64_t n, const int32_t* __restrict__ off, const int32_t* __restrict__ col,
+                          const float* __restrict__ val, const float* __restrict__ x, float* __restrict__ y) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  float acc = 0.f;
+  for (int k = off[row] + lane; k < off[row + 1]; k += 32) acc = fmaf(val[k], x[col[k]], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) y[row] = acc;
+}
+// out = R (b - q) (R = P^T, one warp per coarse row)
+__global__ void k_mg_restrict(int64_t n, const int32_t* __restrict__ off, const int32_t* __restrict__ col,
+                              const float* __restrict__ val, const float* __restrict__ b,
+                              const float* __restrict__ q, float* __restrict__ out) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  float acc = 0.f;
+  for (int k = off[row] + lane; k < off[row + 1]; k += 32) acc = fmaf(val[k], b[col[k]] - q[col[k]], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) out[row] = acc;
+}
+// x += P xc on the rows with a nonzero inverse diagonal (interior rows)
+__global__ void k_mg_prolong(int64_t n, const int32_t* __restrict__ off, const int32_t* __restrict__ col,
+                             const float* __restrict__ val, const float* __restrict__ dinv,
+                             const float* __restrict__ xc, float* __restrict__ x) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || dinv[i] == 0.f) return;
+  float acc = x[i];
+  for (int k = off[i]; k < off[i + 1]; ++k) acc = fmaf(val[k], xc[col[k]], acc);
+  x[i] = acc;
+}
+// y = Ainv t on V_H (dense, one warp per row)
+__global__ void k_mg_dense(int n, const float* __restrict__ Ainv, const float* __restrict__ t, float* __restrict__ y) {
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  float acc = 0.f;
+  for (int k = lane; k < n; k += 32) acc = fmaf(Ainv[(int64_t)row * n + k], t[k], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) y[row] = acc;
+}
+
+// z = V-cycle(r) on the fine level (one column); apply32 is the fine operator (matrix-free stiffness), dinv the
+// fine inverse diagonal (0 on boundary rows), cinv the dense FP32 inverse of P^T K P on V_H.
+template <typename Apply>
+static int mg_apply(mk_ctx* ctx, const mk_mesh* m, Apply&& apply32, const float* dinv, const float* cinv,
+                    const float* r, float* z, cudaStream_t s) {
+  const int nm = (int)m->mg.size();
+  const int64_t nf = m->fine.n_nodes, nH = m->coarse.n_free;
+  // scratch: the fine operator product, then per intermediate level b, x, q, then b and x on V_H
+  size_t total = (size_t)nf;
+  for (const MgLevel& g : m->mg) total += 3 * (size_t)g.L.n_nodes;
+  total += 2 * (size_t)nH;
+  int err = MK_OK;
+  float* ws = (float*)scratch(ctx, S_MG, total * sizeof(float), &err);
+  if (!ws) return err;
+  float* qf = ws;
+  std::vector<float*> b(nm), x(nm), q(nm);
+  float* p = ws + nf;
+  for (int k = 0; k < nm; ++k) {
+    const int64_t n = m->mg[k].L.n_nodes;
+    b[k] = p; x[k] = p + n; q[k] = p + 2 * n;
+    p += 3 * n;
+  }
+  float* bH = p;
+  float* xH = p + nH;
+  const float w = kTLOmega;
+  auto blocks = [](int64_t n) { return (int)((n + 255) / 256); };
+  auto wblocks = [](int64_t n) { return (int)((n * 32 + 255) / 256); };
+  // down: fine level
+  MK_COUNT(), k_mg_jac0<<<blocks(nf), 256, 0, s>>>(nf, dinv, r, z, w);
+  MK_TRY(apply32(z, qf));
+  float* bc = nm > 0 ? b[nm - 1] : bH;
+  MK_COUNT(), k_mg_restrict<<<wblocks(m->mgR.n_rows), 256, 0, s>>>(m->mgR.n_rows, m->mgR.d_off, m->mgR.d_col,
+                                                                   m->mgR.d_val, r, qf, bc);
+  // down: intermediate levels, finest first
+  for (int k = nm - 1; k >= 0; --k) {
+    const MgLevel& g = m->mg[k];
+    const int64_t n = g.L.n_nodes;
+    MK_COUNT(), k_mg_jac0<<<blocks(n), 256, 0, s>>>(n, g.d_dinv, b[k], x[k], w);
+    MK_COUNT(), k_mg_spmv<<<wblocks(n), 256, 0, s>>>(n, g.K.d_off, g.K.d_col, g.K.d_val, x[k], q[k]);
+    float* bnext = k > 0 ? b[k - 1] : bH;
+    MK_COUNT(), k_mg_restrict<<<wblocks(g.R.n_rows), 256, 0, s>>>(g.R.n_rows, g.R.d_off, g.R.d_col, g.R.d_val, b[k],
+                                                                  q[k], bnext);
+  }
+  // V_H
+  MK_COUNT(), k_mg_dense<<<(int)((nH * 32 + 255) / 256), 256, 0, s>>>((int)nH, cinv, bH, xH);
+  // up: intermediate levels, coarsest first
+  for (int k = 0; k < nm; ++k) {
+    const MgLevel& g = m->mg[k];
+    const int64_t n = g.L.n_nodes;
+    const float* xc = k > 0 ? x[k - 1] : xH;
+    MK_COUNT(), k_mg_prolong<<<blocks(n), 256, 0, s>>>(n, g.P.d_off, g.P.d_col, g.P.d_val, g.d_dinv, xc, x[k]);
+    MK_COUNT(), k_mg_spmv<<<wblocks(n), 256, 0, s>>>(n, g.K.d_off, g.K.d_col, g.K.d_val, x[k], q[k]);
+    MK_COUNT(), k_mg_post<<<blocks(n), 256, 0, s>>>(n, g.d_dinv, b[k], q[k], x[k], w);
+  }
+  // up: fine level
+  MK_COUNT(), k_mg_prolong<<<blocks(nf), 256, 0, s>>>(nf, m->mgP.d_off, m->mgP.d_col, m->mgP.d_val, dinv,
+                                                      nm > 0 ? x[nm - 1] : xH, z);
+  MK_TRY(apply32(z, qf));
+  MK_COUNT(), k_mg_post<<<blocks(nf), 256, 0, s>>>(nf, dinv, r, qf, z, w);
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
 template <typename Apply>
 static int twolevel_mult_apply(mk_ctx* ctx, const mk_mesh* m, Apply&& apply32, const float* cinv, const float* dinv,
                                const float* r, float* z, int ld, int N, cudaStream_t s, bool z0_ready = false,
@@ -1245,8 +1372,10 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
   float* q = (float*)scratch(ctx, S_Q32, (size_t)n * ld * sizeof(float), &err);
   float* d = (float*)scratch(ctx, S_X32, (size_t)n * ld * sizeof(float), &err);
   const bool learned = o.precond == MK_PRECOND_LEARNED && o.mlp;
+  // the multigrid V-cycle (Poisson operator on a mesh with a hierarchy) instead of the two-level form
+  const bool mg = stiff && o.coarse == 2 && m->has_mg && cinv != nullptr;
   // an explicit preconditioned residual z (FCG(1), which is PCG for a fixed SPD preconditioner) whenever the
-  // preconditioner is more than the diagonal: learned, two-level, or both
+  // preconditioner is more than the diagonal: learned, two-level, multigrid
   const bool fcg = learned || cinv != nullptr;
   float* zb = fcg ? (float*)scratch(ctx, S_Z32, (size_t)n * ld * sizeof(float), &err) : nullptr;
   if (fcg && !zb) return err;
@@ -1294,7 +1423,13 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
     return err;
   if (cinv && !scratch(ctx, S_TLT, (size_t)(kTLS + 1) * m->coarse.n_free * ld * sizeof(float), &err)) return err;
   float* tlq = nullptr;  // A z inside the multiplicative two-level preconditioner
-  if (cinv && !learned && !(tlq = (float*)scratch(ctx, S_TLQ, (size_t)n * ld * sizeof(float), &err))) return err;
+  if (cinv && !learned && !mg && !(tlq = (float*)scratch(ctx, S_TLQ, (size_t)n * ld * sizeof(float), &err))) return err;
+  if (mg) {  // the V-cycle's scratch must exist before a capture starts
+    size_t total = (size_t)n;
+    for (const MgLevel& g : m->mg) total += 3 * (size_t)g.L.n_nodes;
+    total += 2 * (size_t)m->coarse.n_free;
+    if (!scratch(ctx, S_MG, total * sizeof(float), &err)) return err;
+  }
   if (stiff && !stiff_factors(m, s, &err)) return err;  // allocated here: nothing may allocate inside a capture
   if (fcg) {
     if (!scratch(ctx, S_LHALO, (size_t)std::max<int64_t>(m->patches.n_halo_slots, 1) * ld * sizeof(float), &err))
@@ -1312,6 +1447,7 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
     if (refine >= max_refine || total_it >= o.maxit) break;
     ++refine;
     auto precond = [&]() -> int {  // zb = M(r)
+      if (mg) return mg_apply(ctx, m, apply32, dinv, cinv, r, zb, s);
       if (learned) {
         MK_TRY(learned_apply(ctx, m, o.mlp, dinv, r, zb, ld, N, o.mlp_precision, s));
         if (cinv) MK_TRY(twolevel_apply(ctx, m, cinv, dinv, r, zb, ld, N, true, s));

@@ -378,7 +378,7 @@ int pcg64(mk_ctx* ctx, const mk_mesh* m, const double* Ae, const double* diag, c
 }
 
 static bool valid_opts(const mk_solve_opts* o) {
-  if (!o || !(o->rtol > 0) || o->maxit <= 0) return false;
+  if (!o || !(o->rtol > 0) || o->maxit <= 0 || o->coarse < 0 || o->coarse > 2) return false;
   if (o->coarse && o->precision != MK_PREC_MIXED) return false;
   if (o->precond == MK_PRECOND_LEARNED)
     return o->precision == MK_PREC_MIXED && o->mlp != nullptr &&
@@ -473,7 +473,8 @@ int mk_hartree_poisson(mk_ctx* ctx, const mk_mesh* m, const double* u, int ld, c
   MK_COUNT(), k_combine_rhs<<<(int)((L.n_nodes + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, F, y, coef, F, 1, 1);
   MK_CUDA(cudaMemsetAsync(d, 0, L.n_nodes * sizeof(double), s));
   const float* cinv = nullptr;
-  if (opts->precision == MK_PREC_MIXED && opts->coarse) {  // two-level: the coarse inverse of P^T K P (cached)
+  MK_ARG(opts->coarse != 2 || m->has_mg, "mk_hartree_poisson: multigrid needs the mesh hierarchy (mk_mesh_set_hierarchy)");
+  if (opts->precision == MK_PREC_MIXED && opts->coarse) {  // two-level or multigrid: the inverse of P^T K P on V_H
     MK_TRY(tl_prepare(m, s));
     cinv = coarse_inverse_cached(ctx, m, Ke, nullptr, s, &err);
     if (!cinv) return err;
@@ -546,6 +547,7 @@ int mk_correction_solve(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, d
   MK_ARG(ctx && m && mol && rhs && x, "mk_correction_solve: null argument");
   MK_ARG(N >= 1 && N <= ld && N <= MK_MAX_RHS, "mk_correction_solve: bad N/ld");
   MK_ARG(valid_opts(opts), "mk_correction_solve: bad opts");
+  MK_ARG(opts->coarse != 2, "mk_correction_solve: multigrid is for the Hartree Poisson solve");
   MK_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
   const Level& L = m->fine;

@@ -116,6 +116,7 @@ _SIGS = {
     "mk_correction_shift": [_vp, _vp, C.POINTER(mk_molecule), C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double),
                             C.POINTER(C.c_double), _vp],
     "mk_ctx_set_option": [_vp, C.c_int, C.c_int],
+    "mk_mesh_set_hierarchy": [_vp, C.c_int, C.POINTER(mk_mesh_desc), C.POINTER(C.POINTER(C.c_int32))],
     "mk_joint_ritz": [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.POINTER(C.c_int),
                       _vp],
     "mk_joint_assemble": [_vp, _vp, C.c_int, C.c_int, _vp, _vp, _vp, C.c_int, _vp, _vp],
@@ -249,7 +250,7 @@ def opts(precision="fp64", precond="jacobi", rtol=1e-8, maxit=20000, inner_rtol=
     correction (mixed precision)."""
     o = mk_solve_opts(MK_PREC_MIXED if precision == "mixed" else MK_PREC_FP64, MK_PRECOND[precond], rtol, maxit,
                       inner_rtol, max_refine, check_every)
-    o.coarse = 1 if coarse else 0
+    o.coarse = 2 if coarse in (2, "multigrid") else (1 if coarse else 0)
     if mlp is not None:
         o.mlp = mlp.h.value
         o.mlp_precision = MK_MLP_BF16 if mlp_precision == "bf16" else MK_MLP_FP32
@@ -370,6 +371,24 @@ class Mesh:
         _check(lib().mk_mesh_get_topology(self.h, level, nodes.ctypes.data, bnd.ctypes.data, elem.ctypes.data,
                                           col.ctypes.data))
         return nodes, bnd.astype(bool), elem, col
+
+    def set_hierarchy(self, meshes, parents):
+        """Intermediate levels (coarsest first) of the multigrid hierarchy: meshes [(coords, tets)], parents as
+        synth.cube_hierarchy returns them."""
+        keep = []
+        descs = (mk_mesh_desc * max(len(meshes), 1))()
+        for k, (c, t) in enumerate(meshes):
+            c, cp = _host_f64(c)
+            t = np.ascontiguousarray(t, dtype=np.int32)
+            keep.extend([c, t])
+            descs[k] = mk_mesh_desc(self.info["order"], c.shape[0], cp, t.shape[0],
+                                    t.ctypes.data_as(C.POINTER(C.c_int32)))
+        pars = (C.POINTER(C.c_int32) * max(len(parents), 1))()
+        for k, p in enumerate(parents):
+            p = np.ascontiguousarray(p, dtype=np.int32)
+            keep.append(p)
+            pars[k] = p.ctypes.data_as(C.POINTER(C.c_int32))
+        _check(lib().mk_mesh_set_hierarchy(self.h, len(meshes), descs, pars))
 
     def close(self):
         if self.h:

@@ -124,9 +124,14 @@ def coarse_eigenpairs(ctx, mesh, Z, R, N, return_basis=False):
     return out + (V,) if return_basis else out
 
 
-def upload_workload(ctx, wl):
-    """Meshes of a named synthetic workload (see synth.workload) uploaded to the device."""
+def upload_workload(ctx, wl, hierarchy=True):
+    """Meshes of a named synthetic workload (see synth.workload) uploaded to the device; for the uniformly refined
+    workloads also the intermediate levels of the multigrid hierarchy (mesh.multigrid True)."""
     from . import synth
     cc, ct, fc, ft, par = synth.workload_meshes(wl)
     mesh = mk.Mesh(ctx, fc, ft, cc, ct, par, wl["order"])
+    mesh.multigrid = False
+    if hierarchy and wl.get("mesh") != "graded":
+        mesh.set_hierarchy(*synth.cube_hierarchy(wl["n_coarse"], wl["levels"], wl["half"]))
+        mesh.multigrid = True
     return mesh, (cc, ct, fc, ft, par)

@@ -78,6 +78,22 @@ def nested_cube_meshes(n_coarse: int, levels: int, half: float):
     return cc, ct, fc, ft, parent
 
 
+def cube_hierarchy(n_coarse: int, levels: int, half: float):
+    """The intermediate meshes between the coarse (n_coarse^3 cubes) and the fine (n_coarse 2^levels cubes per side)
+    Kuhn meshes of nested_cube_meshes, coarsest first, with the parent maps of the nested chain: returns
+    (meshes, parents), meshes[k] = (coords, tets) of n_coarse 2^(k+1) cubes per side for k < levels - 1,
+    parents[k] the element of the next coarser mesh containing each element of meshes[k], and parents[-1] that of
+    the finest intermediate mesh for each fine element."""
+    meshes, parents = [], []
+    for k in range(1, levels):
+        _, _, c, t, par = nested_cube_meshes(n_coarse * 2 ** (k - 1), 1, half)
+        meshes.append((c, t))
+        parents.append(par)
+    if levels >= 2:
+        parents.append(nested_cube_meshes(n_coarse * 2 ** (levels - 1), 1, half)[4])
+    return meshes, parents
+
+
 def _edge_keys(a, b, nv_cap: int):
     lo, hi = np.minimum(a, b), np.maximum(a, b)
     return lo.astype(np.int64) * nv_cap + hi.astype(np.int64)

@@ -126,3 +126,20 @@ def test_correction_step_on_graded_mesh_keeps_the_ritz_bounds():
     lu, _, _, nu = run(synth.nested_cube_meshes(4, 2, 10.0))
     assert lfg - 1e-10 <= lg <= lHg + 1e-12 and lg > -0.5
     assert ng < nu and (lg + 0.5) < (lu + 0.5)
+
+
+def test_cube_hierarchy_is_nested():
+    """The intermediate levels of the multigrid hierarchy: 6 n^3 tetrahedra per level, and every element's
+    vertices lie in its parent (barycentric coordinates in [0, 1]) down the whole chain."""
+    meshes, parents = synth.cube_hierarchy(2, 3, 5.0)
+    cc, ct = synth.cube_mesh(2, 5.0)
+    fc, ft = synth.cube_mesh(16, 5.0)
+    chain = [(cc, ct)] + meshes + [(fc, ft)]
+    assert [t.shape[0] for _, t in chain] == [6 * n ** 3 for n in (2, 4, 8, 16)]
+    for (pc, pt), (c, t), par in zip(chain[:-1], chain[1:], parents):
+        x = pc[pt[par]]                                   # parent vertices [E, 4, 3]
+        J = np.stack([x[:, 1] - x[:, 0], x[:, 2] - x[:, 0], x[:, 3] - x[:, 0]], axis=2)
+        for k in range(4):
+            s = np.linalg.solve(J, (c[t[:, k]] - x[:, 0])[..., None])[..., 0]
+            lam = np.concatenate([1.0 - s.sum(axis=1, keepdims=True), s], axis=1)
+            assert lam.min() > -1e-12 and lam.max() < 1.0 + 1e-12
