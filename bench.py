@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "fine-mesh DOF×orbitals solved/s at 1e-8 rel. residual; learned vs plain PCG"
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_apply_stream launch from an ncu capture of the same kernel
 # build on the same workload (None until such a capture exists for the current kernel)
-TRAFFIC = {("mol4_p2", 8): 67.81e6}  # ncu: 65.67 MB read + 2.14 MB written by one launch on mol4_p2
+TRAFFIC = {("mol4_p2", 8): 68.51e6}  # ncu: 66.21 MB read + 2.30 MB written by one k_apply_reg launch on mol4_p2
 UNIT = "DOF*orbitals/s"
 OPERATOR_KERNEL = "k_apply_reg (FP32 element-by-element operator: element matrices staged in registers)"
 # FP64 FMA rate of the GB300: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz (maximum SM clock)
@@ -53,6 +53,7 @@ def parse():
                     help="inner preconditioner of the mixed-precision correction solve (learned: FCG(1))")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve measurement")
+    ap.add_argument("--no-paper", action="store_true", help="skip the paper-form step (inner SCF) measurement")
     ap.add_argument("--no-eval", action="store_true",
                     help="skip the learned-vs-plain evaluation on the 16 unseen 8-nucleus molecules")
     ap.add_argument("--patch-kernel", default="reg", choices=["reg", "pipelined", "single"],
@@ -485,6 +486,52 @@ def main():
                          "poisson_iterations": r["poisson"]["iterations"] if r["poisson"] else None,
                          "max_abs_lambda_diff_vs_headline_Ha": float(np.abs(lam_k - lam_head).max())}
 
+    # the paper's own form of the step (Algorithm 1 steps 5-7 with Algorithm 2's inner SCF and Algorithm 3's
+    # precomputations), applied to the headline step's output: its orbitals and eigenvalues, and the Hartree
+    # potential of their density (a second correction on the same mesh pair, as Algorithm 1 chains its steps)
+    paper = None
+    if world == 1 and not a.no_paper:
+        from paper_2103_02824_gb300.step import PaperStep
+        pst = PaperStep(ctx, mesh, wl["Z"], wl["R"], N, ld=st.ld)
+        so, po = arm_opts(head_kind)
+        u_in, lam_in = st.psi.clone(), st.lam.cpu().numpy().copy()
+        w_in = torch.zeros_like(st.w)
+        mk.mk_hartree_poisson(ctx, mesh, u_in, occ, N, w_in, bc="multipole", opt=po)
+
+        def paper_run():
+            return pst.run(u_in, lam_in, occ, sigma, w_in, xc=wl["xc"], solve_opts=so, poisson_opts=po,
+                           inner_tol=1e-10, max_inner=200)
+        for _ in range(max(1, a.warmup)):
+            pr = paper_run()
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record()
+        for _ in range(a.steps):
+            pr = paper_run()
+        c1.record()
+        torch.cuda.synchronize()
+        p_ms = c0.elapsed_time(c1) / a.steps
+        # the inner part alone: Algorithm 3's precomputations, then the inner iterations
+        i0, i1, i2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        lam_p, coef_p = torch.zeros_like(pst.lam), torch.zeros_like(pst.coef)
+        i0.record()
+        inner = mk.Inner(ctx, mesh, pst.mol, pst.phit, N, pst.wt, pst.vxc)
+        i1.record()
+        ir = inner.run(occ, lam_p, coef_p, tol=1e-10, max_inner=200)
+        i2.record()
+        torch.cuda.synchronize()
+        inner.close()
+        lam_paper = pst.lam.cpu().numpy()
+        paper = {"ms_per_step": p_ms, "value": float(n_free) * N / (p_ms * 1e-3), "unit": UNIT,
+                 "inner_iterations": pr["inner"]["iters"], "inner_last_change": pr["inner"]["delta"],
+                 "precompute_ms": i0.elapsed_time(i1), "inner_ms": i1.elapsed_time(i2),
+                 "inner_ms_per_iteration": i1.elapsed_time(i2) / max(1, ir["iters"]),
+                 "solve_iterations": pr["solve"]["iterations"], "poisson_iterations": pr["poisson"]["iterations"],
+                 "lambda": [float(x) for x in lam_paper],
+                 "input": "the headline step's output orbitals and eigenvalues, w = their Hartree potential",
+                 "max_abs_lambda_diff_vs_headline_Ha": float(np.abs(lam_paper - lam_head).max())}
+        pst.close()
+
     # the same operator kernel timed alone (no concurrent stream), for comparison with its in-step duration
     iso_ms = None
     if a.precision == "mixed":
@@ -649,7 +696,8 @@ def main():
             "gpu_launches": launches, "gpu_launches_per_step": launches / a.steps,
             "clocks": clk, "roofline": roof, "roofline_learned": roof_tc, "roofline_stiffness": roof_k,
             "cpu_baseline": cpu, "parity": parity,
-            "compare": compare, "training": train_info, "batch": batch, "learned_vs_plain": evaluation,
+            "compare": compare, "paper_form": paper, "training": train_info, "batch": batch,
+            "learned_vs_plain": evaluation,
             "solve_iterations": solve["iterations"], "solve_max_rel_residual": solve["max_rel_residual"],
             "poisson_iterations": reps["poisson"]["iterations"] if reps["poisson"] else None,
             "lambda": [float(x) for x in lam_head],

@@ -262,6 +262,15 @@ int mk_assemble_rhs_from_vq(mk_ctx* ctx, const mk_mesh* mesh, const double* u, i
 int mk_correction_solve(mk_ctx* ctx, const mk_mesh* mesh, const mk_molecule* mol, double sigma, const double* rhs,
                         double* x, int ld, int N, const mk_solve_opts* opts, mk_solve_report* report, void* stream);
 
+/* The paper's own form of step 5 (Eq. (Aux_Linear_Problem) as Algorithm 1 writes it): the frozen potential on the
+ * left, (K/2 + M_{V_ext} + M_{vq} + sigma M) x_i = rhs_i, with vq [n_elems * n_quad] device (e.g. the previous
+ * Hartree potential plus V_xc of the step's input orbitals, from mk_frozen_potential) and rhs_i = (lambda_i +
+ * sigma) M u_i (mk_assemble_rhs_from_vq with a zero vq).  x, opts, report and errors as mk_correction_solve;
+ * opts->coarse must be 0 (the cached coarse operators are those without vq). */
+int mk_correction_solve_vq(mk_ctx* ctx, const mk_mesh* mesh, const mk_molecule* mol, const double* vq, double sigma,
+                           const double* rhs, double* x, int ld, int N, const mk_solve_opts* opts,
+                           mk_solve_report* report, void* stream);
+
 /* The operator of the correction problems alone (Eq. (Aux_Linear_Problem) with the shift): y = (K/2 + M_{V_ext} +
  * sigma M) x on the free DOF (boundary rows of y written as 0), all ld columns, matrix-free element by element with
  * the patch scatter (owner-computes in shared memory, halo slots summed in patch order; bitwise reproducible).
@@ -363,6 +372,43 @@ int mk_joint_assemble(mk_ctx* ctx, const mk_mesh* mesh, int k, int N, const doub
  * coef [(N_H+1)*N] from mk_small_eigensolve, psihat/u/psi [n_nodes*ld] device. */
 int mk_orbital_assemble(mk_ctx* ctx, const mk_mesh* mesh, const double* coef, const double* psihat,
                         const double* u, int ld, int N, double* psi, void* stream);
+
+/* ---------------------------------------------------------------------------------------------- inner SCF */
+/* The paper's step 7 (Eq. (Nonlinear_Eig_Hh_Full)) by the inner iteration of Algorithm 2 with the precomputations
+ * of Algorithm 3: the orbitals in V_H + span{phi~_i}, the Hartree potential in w_b + V_H + span{w~0}, where
+ * w~ = w_b + w~0 is the Hartree potential of the corrections' density (mk_hartree_poisson of phi~) split into its
+ * boundary values w_b (zero inside) and the rest w~0 (zero on the boundary); the boundary values stay fixed.
+ *
+ * mk_inner_create (Algorithm 3, step 1): integrates on the fine mesh, once, everything an inner iteration needs,
+ * so that an iteration costs O(N_H) coarse work: A1 = P^T H1 P, b1_i = P^T H1 phi~_i, beta1_i (H1 = K/2 + V_ext +
+ * V_xc + w_b), A3 = P^T M_{w~0} P, b3_i, beta3_i (Eq. (FG)), c_i, gamma_i, the bordered Hartree system (P^T K P,
+ * P^T K w~0, (K w~0, w~0)) with the lifts of w_b, and per coarse element the tensors (psi_a psi_b, psi_c),
+ * (phi~_i psi_a, psi_b) (Eq. (Ah4def)), (phi~_i^2, psi_a) (Eq. (rhsdef)) and (w~0, phi~_i^2) on the fine
+ * quadrature.  phit [n_nodes*ld] device (the corrections phi~, boundary rows 0), wt [n_nodes] device, vxc_q
+ * [n_elems * n_quad] device (V_xc of the step's input orbitals at the quadrature points: mk_frozen_potential with
+ * w = 0).  The handle owns its device memory (about (3 + 2N) N_H^2 + N n_elem_coarse n_loc^2 doubles) until
+ * mk_inner_destroy.  Synchronises the stream.  MK_ERR_INVALID_ARG if P^T K P is not positive definite or
+ * n_loc^3 + N (n_loc^2 + n_loc + 1) > 8192.  When w~0 already lies in V_H (Schur complement of the border at most
+ * 1e-12 (K w~0, w~0)), the extra Hartree direction is dropped (theta_1 = 0); mk_inner_info reports it.
+ *
+ * mk_inner_run (Algorithm 2): from w = w~ (w_H = 0, theta_1 = 1), for s = 1 .. max_inner: (a) the per-orbital
+ * eigenproblems in V_H + span{phi~_i} with the current Hartree potential and the selection of
+ * mk_small_eigensolve_shared (lambda [N], coef [(N_H+1)*N] as there); (b) the Hartree potential of the density
+ * sum_i occ_i (phi_{i,H} + theta_{2,i} phi~_i)^2 in W, mixed: (w_H, theta_1) <- (1 - mix) old + mix new; (c) stop
+ * once s > 1 and the largest change of any coefficient is below tol.  occ [N] host.  Outputs: lambda, coef,
+ * status [N] (or NULL), wH [N_H] (or NULL) device, from the last iteration (w_H and theta_1 after its update);
+ * theta1, iters, delta (the last change) host or NULL.  Synchronises the stream after every iteration.
+ * mk_inner_potential: w = w_b + P w_H + theta_1 w~0 [n_nodes] device, the inner Hartree potential after the last
+ * mk_inner_run.  The output orbitals are mk_orbital_assemble(coef, phit, phit): P phi_H + theta_2 phi~. */
+typedef struct mk_inner mk_inner;
+int mk_inner_create(mk_ctx* ctx, const mk_mesh* mesh, const mk_molecule* mol, const double* phit, int ld, int N,
+                    const double* wt, const double* vxc_q, mk_inner** out, void* stream);
+int mk_inner_run(mk_ctx* ctx, mk_inner* inner, const double* occ, double tol, int max_inner, double mix,
+                 double* lambda, double* coef, int32_t* status, double* wH, double* theta1, int* iters, double* delta,
+                 void* stream);
+int mk_inner_potential(mk_ctx* ctx, const mk_inner* inner, double* w, void* stream);
+int mk_inner_info(const mk_inner* inner, int* w_in_VH, double* schur);
+int mk_inner_destroy(mk_inner* inner);
 
 /* ---------------------------------------------------------------------------------------------- shift */
 /* Lowest Ritz value of `steps` Lanczos steps on the pencil (K/2 + M_{V_ext}, M) over the free fine DOF, from the

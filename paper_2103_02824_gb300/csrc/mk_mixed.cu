@@ -1306,9 +1306,10 @@ int pcg_mixed(mk_ctx* ctx, const mk_mesh* m, const double* A64, const double* b,
               const mk_solve_opts& o, mk_solve_report* rep, cudaStream_t s, const float* cinv, bool stiff,
               const double* diag_pre);
 
+// vq: an optional potential at the quadrature points added to the operator (K/2 + M_Vext + M_vq + sigma M)
 int solve_mixed(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, double sigma, const double* b,
-                const double*, const double*, double* x, int ld, int N, const mk_solve_opts& o, mk_solve_report* rep,
-                cudaStream_t s) {
+                const double* vq, const double*, double* x, int ld, int N, const mk_solve_opts& o,
+                mk_solve_report* rep, cudaStream_t s) {
   if (o.precond != MK_PRECOND_JACOBI && o.precond != MK_PRECOND_LEARNED)
     return fail(MK_ERR_UNSUPPORTED, "mixed path: Jacobi or learned preconditioner");
   if (o.precond == MK_PRECOND_LEARNED && !o.mlp) return fail(MK_ERR_INVALID_ARG, "learned preconditioner: no network");
@@ -1319,9 +1320,10 @@ int solve_mixed(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, double si
   if (!A64) return err;
   const double* H0 = static_matrices(ctx, m, mol, s, &err);
   if (!H0) return err;
-  MK_TRY(element_matrices(ctx, L, nullptr, 0.0, 0.0, sigma, nullptr, A64, s, H0));
+  MK_TRY(element_matrices(ctx, L, nullptr, 0.0, 0.0, sigma, vq, A64, s, H0));
   const float* cinv = nullptr;
   if (o.coarse) {  // two-level: the coarse inverse of this molecule's shifted operator (cached)
+    if (vq) return fail(MK_ERR_UNSUPPORTED, "two-level preconditioner: not with a potential in the operator");
     std::vector<double> key;
     key.push_back(sigma);
     for (int k = 0; k < mol->n_nuclei; ++k) {

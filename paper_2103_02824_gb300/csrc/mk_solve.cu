@@ -567,6 +567,30 @@ int mk_correction_solve(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, d
   return pcg64(ctx, m, Ae, diag, rhs, x, N, ld, *opts, report, s);
 }
 
+int mk_correction_solve_vq(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, const double* vq, double sigma,
+                           const double* rhs, double* x, int ld, int N, const mk_solve_opts* opts,
+                           mk_solve_report* report, void* stream) {
+  MK_ARG(ctx && m && mol && vq && rhs && x, "mk_correction_solve_vq: null argument");
+  MK_ARG(N >= 1 && N <= ld && N <= MK_MAX_RHS, "mk_correction_solve_vq: bad N/ld");
+  MK_ARG(valid_opts(opts), "mk_correction_solve_vq: bad opts");
+  MK_ARG(opts->coarse == 0, "mk_correction_solve_vq: no coarse preconditioner with a potential in the operator");
+  MK_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const Level& L = m->fine;
+  if (opts->precision == MK_PREC_MIXED)
+    return solve_mixed(ctx, m, mol, sigma, rhs, vq, nullptr, x, ld, N, *opts, report, s);
+  MK_ARG(opts->precision == MK_PREC_FP64, "mk_correction_solve_vq: bad precision");
+  int err = MK_OK;
+  double* Ae = (double*)scratch(ctx, S_ELEM64, (size_t)L.n_elems * (L.nloc * (L.nloc + 1) / 2) * sizeof(double), &err);
+  double* diag = (double*)scratch(ctx, S_DIAG64, L.n_nodes * sizeof(double), &err);
+  if (!Ae || !diag) return err;
+  const double* H0 = static_matrices(ctx, m, mol, s, &err);
+  if (!H0) return err;
+  MK_TRY(element_matrices(ctx, L, nullptr, 0.0, 0.0, sigma, vq, Ae, s, H0));
+  MK_TRY(assemble_diagonal(ctx, L, Ae, diag, s));
+  return pcg64(ctx, m, Ae, diag, rhs, x, N, ld, *opts, report, s);
+}
+
 int mk_lowest_ritz(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, const double* v0, int steps,
                    double* theta, void* stream) {
   MK_ARG(ctx && m && mol && v0 && theta && steps >= 1, "mk_lowest_ritz: bad argument");

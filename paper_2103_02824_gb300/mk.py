@@ -127,6 +127,14 @@ _SIGS = {
     "mk_autotune_patches": [_vp, _vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "mk_frozen_potential": [_vp, _vp, _vp, C.c_int, C.POINTER(C.c_double), C.c_int, _vp, _vp, mk_xc, _vp, _vp],
     "mk_assemble_rhs_from_vq": [_vp, _vp, _vp, C.c_int, C.POINTER(C.c_double), C.c_int, _vp, C.c_double, _vp, _vp],
+    "mk_correction_solve_vq": [_vp, _vp, C.POINTER(mk_molecule), _vp, C.c_double, _vp, _vp, C.c_int, C.c_int,
+                               C.POINTER(mk_solve_opts), C.POINTER(mk_solve_report), _vp],
+    "mk_inner_create": [_vp, _vp, C.POINTER(mk_molecule), _vp, C.c_int, C.c_int, _vp, _vp, C.POINTER(_vp), _vp],
+    "mk_inner_run": [_vp, _vp, C.POINTER(C.c_double), C.c_double, C.c_int, C.c_double, _vp, _vp, _vp, _vp,
+                     C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_double), _vp],
+    "mk_inner_potential": [_vp, _vp, _vp, _vp],
+    "mk_inner_info": [_vp, C.POINTER(C.c_int), C.POINTER(C.c_double)],
+    "mk_inner_destroy": [_vp],
     "mk_mlp_param_count": [C.c_int],
     "mk_mlp_create": [_vp, C.c_int, C.POINTER(C.c_float), C.POINTER(_vp)],
     "mk_mlp_destroy": [_vp],
@@ -458,6 +466,60 @@ def mk_correction_solve(ctx, mesh, mol: Molecule, sigma, rhs, x, N, opt=None, st
     d = rep.to_dict()
     d["code"] = code
     return d
+
+
+def mk_correction_solve_vq(ctx, mesh, mol: Molecule, vq, sigma, rhs, x, N, opt=None, stream=None, allow=()):
+    """The paper's form of the correction solve: (K/2 + M_Vext + M_vq + sigma M) x = rhs."""
+    ld = x.shape[1] if x.dim() == 2 else 1
+    rep = mk_solve_report()
+    o = opt or opts()
+    code = lib().mk_correction_solve_vq(ctx.h, mesh.h, C.byref(mol.c), _ptr(vq), float(sigma), _ptr(rhs), _ptr(x),
+                                        ld, N, C.byref(o), C.byref(rep), _stream(stream))
+    _check(code, allow)
+    d = rep.to_dict()
+    d["code"] = code
+    return d
+
+
+class Inner:
+    """Handle of the inner SCF iteration (Algorithm 2 with Algorithm 3's precomputations; see include/mk.h):
+    created from the corrections phit [n_nodes, ld], their Hartree potential wt [n_nodes] and V_xc at the
+    quadrature points vxc_q [n_elems, n_quad] (all device float64)."""
+
+    def __init__(self, ctx, mesh, mol: Molecule, phit, N, wt, vxc_q, stream=None):
+        self.ctx, self.mesh, self.N = ctx, mesh, N
+        self.NH = mesh.info["n_free_coarse"]
+        ld = phit.shape[1] if phit.dim() == 2 else 1
+        h = _vp()
+        _check(lib().mk_inner_create(ctx.h, mesh.h, C.byref(mol.c), _ptr(phit), ld, N, _ptr(wt), _ptr(vxc_q),
+                                     C.byref(h), _stream(stream)))
+        self.h = h
+        wv, sc = C.c_int(), C.c_double()
+        _check(lib().mk_inner_info(self.h, C.byref(wv), C.byref(sc)))
+        self.w_in_VH, self.schur = bool(wv.value), sc.value
+
+    def run(self, occ, lam, coef, status=None, wH=None, tol=1e-10, max_inner=200, mix=0.5, stream=None):
+        """Returns dict(theta1, iters, delta); lam [N], coef [(N_H+1), N], status [N] int32, wH [N_H] device."""
+        occ_h, occ_p = _host_f64(occ)
+        th, it, dl = C.c_double(), C.c_int(), C.c_double()
+        _check(lib().mk_inner_run(self.ctx.h, self.h, occ_p, float(tol), int(max_inner), float(mix), _ptr(lam),
+                                  _ptr(coef), _ptr(status), _ptr(wH), C.byref(th), C.byref(it), C.byref(dl),
+                                  _stream(stream)))
+        return dict(theta1=th.value, iters=it.value, delta=dl.value)
+
+    def potential(self, w, stream=None):
+        _check(lib().mk_inner_potential(self.ctx.h, self.h, _ptr(w), _stream(stream)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mk_inner_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def mk_batch_correction_solve(ctx, meshes, mols, sigmas, rhs_list, x_list, Ns, opt=None, stream=None, allow=()):

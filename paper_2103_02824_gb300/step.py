@@ -135,3 +135,75 @@ def upload_workload(ctx, wl, hierarchy=True):
         mesh.set_hierarchy(*synth.cube_hierarchy(wl["n_coarse"], wl["levels"], wl["half"]))
         mesh.multigrid = True
     return mesh, (cc, ct, fc, ft, par)
+
+
+class PaperStep:
+    """The correction step in the paper's own form (Algorithm 1, steps 5-7, with Algorithm 2's inner iteration and
+    Algorithm 3's precomputations), through the C ABI: the frozen potential w_prev + V_xc(rho^l) of the step's input
+    orbitals on the left of the correction problems (mk_correction_solve_vq), the Hartree potential w~ of the
+    corrections' density (mk_hartree_poisson), then the nonlinear eigenproblem in V_H + span{phi~_i} by the inner
+    SCF (mk_inner_*).  Buffers are device tensors owned here."""
+
+    def __init__(self, ctx, mesh, Z, R, N: int, ld: int | None = None):
+        import torch
+        self.ctx, self.mesh, self.N = ctx, mesh, N
+        self.ld = ld or max(4, (N + 3) // 4 * 4)
+        self.mol = mk.Molecule(Z, R)
+        info = mesh.info
+        n, E, NH = info["n_nodes"], info["n_elems"], info["n_free_coarse"]
+        self.NH = NH
+        f64 = dict(dtype=torch.float64, device=torch.device("cuda"))
+        self.u = torch.zeros((n, self.ld), **f64)
+        self.zero_n = torch.zeros(n, **f64)
+        self.zero_q = torch.zeros((E, info["n_quad"]), **f64)
+        self.vq = torch.zeros((E, info["n_quad"]), **f64)       # w_prev + V_xc(rho^l): the operator's potential
+        self.vxc = torch.zeros((E, info["n_quad"]), **f64)      # V_xc(rho^l) alone
+        self.rhs = torch.zeros((n, self.ld), **f64)
+        self.phit = torch.zeros((n, self.ld), **f64)
+        self.wt = torch.zeros(n, **f64)
+        self.lam = torch.zeros(N, **f64)
+        self.coef = torch.zeros((NH + 1, N), **f64)
+        self.status = torch.zeros(N, dtype=torch.int32, device=f64["device"])
+        self.wH = torch.zeros(NH, **f64)
+        self.w = torch.zeros(n, **f64)
+        self.psi = torch.zeros((n, self.ld), **f64)
+        self.inner = None
+
+    def run(self, U, lam, occ, sigma, w_prev, xc="lda", solve_opts=None, poisson_opts=None, inner_tol=1e-10,
+            max_inner=200, mix=0.5, stream=None):
+        """U: device [n_nodes, >=N] or numpy [n_nodes, N] (the step's input orbitals on the fine mesh); lam, occ:
+        numpy [N]; w_prev: device or numpy [n_nodes].  Returns reports."""
+        import torch
+        N = self.N
+        if isinstance(U, np.ndarray):
+            self.u.zero_()
+            self.u[:, :N] = torch.from_numpy(U).to(self.u.device)
+        elif U is not self.u:
+            self.u.copy_(U)
+        if isinstance(w_prev, np.ndarray):
+            w_prev = torch.from_numpy(np.ascontiguousarray(w_prev)).to(self.u.device)
+        ctx, mesh = self.ctx, self.mesh
+        mk.mk_frozen_potential(ctx, mesh, self.u, occ, N, w_prev, xc, self.vq, stream=stream)
+        mk.mk_frozen_potential(ctx, mesh, self.u, occ, N, self.zero_n, xc, self.vxc, stream=stream)
+        # step 5: (K/2 + V_ext + w_prev + V_xc + sigma) phi~_i = (lambda_i + sigma) M u_i
+        mk.mk_assemble_rhs_from_vq(ctx, mesh, self.u, lam, N, self.zero_q, sigma, self.rhs, stream=stream)
+        self.phit.copy_(self.u)
+        reps = {"solve": mk.mk_correction_solve_vq(ctx, mesh, self.mol, self.vq, sigma, self.rhs, self.phit, N,
+                                                   opt=solve_opts, stream=stream)}
+        # step 6: the Hartree potential of the corrections' density
+        reps["poisson"] = mk.mk_hartree_poisson(ctx, mesh, self.phit, occ, N, self.wt, bc="multipole",
+                                                opt=poisson_opts, stream=stream)
+        # step 7: Algorithm 3's precomputations, then Algorithm 2's inner iteration
+        if self.inner is not None:
+            self.inner.close()
+        self.inner = mk.Inner(ctx, mesh, self.mol, self.phit, N, self.wt, self.vxc, stream=stream)
+        reps["inner"] = self.inner.run(occ, self.lam, self.coef, self.status, self.wH, tol=inner_tol,
+                                       max_inner=max_inner, mix=mix, stream=stream)
+        mk.mk_orbital_assemble(ctx, mesh, self.coef, self.phit, self.phit, N, self.psi, stream=stream)
+        self.inner.potential(self.w, stream=stream)
+        return reps
+
+    def close(self):
+        if self.inner is not None:
+            self.inner.close()
+            self.inner = None
