@@ -273,6 +273,20 @@ def workload_config(wl, N, n_free, NH, E):
     }
 
 
+def host_cpu():
+    """The host's CPU model (lscpu) and core count, recorded beside the CPU baseline."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"model": model, "nproc": os.cpu_count(), "threads_used": 1}
+
+
 def run_oracle(workload, steps, warmup, sigma=None, timeout=1800):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1", PYTHONPATH=ROOT)
     cmd = [sys.executable, "-m", "oracle.timing", workload, str(steps), str(warmup)]
@@ -532,6 +546,27 @@ def main():
                  "max_abs_lambda_diff_vs_headline_Ha": float(np.abs(lam_paper - lam_head).max())}
         pst.close()
 
+    # the joint augmented space V_H + span{psi^_1..psi^_N} (the original multilevel-correction form) from the
+    # headline step's blocks: Rayleigh-Ritz for the lowest N pairs, then the joint orbitals on the fine mesh
+    joint = None
+    if world == 1 and not a.no_paper:
+        lam_j = torch.zeros(N, dtype=torch.float64, device="cuda")
+        X_j = torch.zeros((NH + N, N), dtype=torch.float64, device="cuda")
+        psi_j = torch.zeros_like(st.psi)
+        step()
+        torch.cuda.synchronize()
+        j0, j1, j2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        j0.record()
+        kept = mk.mk_joint_ritz(ctx, NH, N, N, st.d, st.V, st.b, st.c, st.gramA, st.gramM, lam_j, X_j)
+        j1.record()
+        mk.mk_joint_assemble(ctx, mesh, N, N, X_j, st.psihat, st.u, psi_j)
+        j2.record()
+        torch.cuda.synchronize()
+        lj = lam_j.cpu().numpy()
+        joint = {"ritz_ms": j0.elapsed_time(j1), "assemble_ms": j1.elapsed_time(j2), "corrections_kept": kept,
+                 "lambda": [float(x) for x in lj],
+                 "sum_lambda_joint_minus_per_orbital_Ha": float(lj.sum() - np.sort(lam_head).sum())}
+
     # the same operator kernel timed alone (no concurrent stream), for comparison with its in-step duration
     iso_ms = None
     if a.precision == "mixed":
@@ -673,7 +708,7 @@ def main():
                       "compared": f"all {N} eigenvalues of the headline step against the oracle's step on the same "
                                   f"workload, both solved to 1e-8 FP64 relative residual"}
             parity["ok"] = parity["max_abs_lambda_err_Ha"] <= 1e-6
-            cpu = {"value": o["n_free"] * o["N"] / tstep, "unit": UNIT, "cores": 1, "kind": "oracle",
+            cpu = {"value": o["n_free"] * o["N"] / tstep, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                    "sample": f"one full oracle correction step (A1-A8, scipy.sparse CSR + Jacobi-PCG to 1e-8, dense "
                              f"LAPACK eigensolves) on the same workload, {tstep:.1f} s; static assembly excluded "
                              f"({o['setup_s']:.1f} s)"}
@@ -696,7 +731,7 @@ def main():
             "gpu_launches": launches, "gpu_launches_per_step": launches / a.steps,
             "clocks": clk, "roofline": roof, "roofline_learned": roof_tc, "roofline_stiffness": roof_k,
             "cpu_baseline": cpu, "parity": parity,
-            "compare": compare, "paper_form": paper, "training": train_info, "batch": batch,
+            "compare": compare, "paper_form": paper, "joint_space": joint, "training": train_info, "batch": batch,
             "learned_vs_plain": evaluation,
             "solve_iterations": solve["iterations"], "solve_max_rel_residual": solve["max_rel_residual"],
             "poisson_iterations": reps["poisson"]["iterations"] if reps["poisson"] else None,
@@ -723,7 +758,7 @@ def reference(a, rank, world):
         "dtype": "f64", "data": "synthetic", "impl": "reference",
         "config": dict(workload_config(wl, o["N"], o["n_free"], o["n_free_coarse"], o["n_elems"]), precision="fp64", precond="jacobi",
                        rtol=1e-8),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                          "sample": f"{len(o['step_s'])} full oracle correction steps of the workload"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
