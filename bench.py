@@ -422,6 +422,18 @@ def main():
 
     head_kind = "fp64" if a.precision == "fp64" else precond
     step = make_step(head_kind)
+    # the shift rule takes theta from 60 Lanczos steps, an upper bound of the lowest eigenvalue; where it is not
+    # low enough the correction operator is indefinite and PCG reports breakdown: sigma is doubled (setup)
+    sigma_doublings = 0
+    while True:
+        try:
+            reps = step()
+            break
+        except mk.MkError as ex:
+            if ex.code != mk.MK_ERR_BREAKDOWN or sigma_doublings >= 6:
+                raise
+            sigma *= 2.0
+            sigma_doublings += 1
     for _ in range(a.warmup):
         reps = step()
     torch.cuda.synchronize()
@@ -536,12 +548,16 @@ def main():
         torch.cuda.synchronize()
         inner.close()
         lam_paper = pst.lam.cpu().numpy()
+        pst.run(u_in, lam_in, occ, sigma, w_in, xc=wl["xc"], solve_opts=so, poisson_opts=po, inner_tol=0.0,
+                max_inner=1)
+        lam_first = pst.lam.cpu().numpy()
         paper = {"ms_per_step": p_ms, "value": float(n_free) * N / (p_ms * 1e-3), "unit": UNIT,
                  "inner_iterations": pr["inner"]["iters"], "inner_last_change": pr["inner"]["delta"],
                  "precompute_ms": i0.elapsed_time(i1), "inner_ms": i1.elapsed_time(i2),
                  "inner_ms_per_iteration": i1.elapsed_time(i2) / max(1, ir["iters"]),
                  "solve_iterations": pr["solve"]["iterations"], "poisson_iterations": pr["poisson"]["iterations"],
                  "lambda": [float(x) for x in lam_paper],
+                 "lambda_after_one_inner_iteration": [float(x) for x in lam_first],
                  "input": "the headline step's output orbitals and eigenvalues, w = their Hartree potential",
                  "max_abs_lambda_diff_vs_headline_Ha": float(np.abs(lam_paper - lam_head).max())}
         pst.close()
@@ -566,6 +582,31 @@ def main():
         joint = {"ritz_ms": j0.elapsed_time(j1), "assemble_ms": j1.elapsed_time(j2), "corrections_kept": kept,
                  "lambda": [float(x) for x in lj],
                  "sum_lambda_joint_minus_per_orbital_Ha": float(lj.sum() - np.sort(lam_head).sum())}
+
+    # the outer AFEM loop's Estimate and Mark steps on the headline step's output: the residual indicator of
+    # (lambda, psi) at the potential of psi's own density, then Dorfler's marking (theta = 0.4)
+    afem = None
+    if world == 1 and not a.no_paper:
+        w_psi = torch.zeros_like(st.w)
+        vq_psi = torch.zeros_like(st.vq)
+        eta2 = torch.zeros(E, dtype=torch.float64, device="cuda")
+        marked = torch.zeros(E, dtype=torch.uint8, device="cuda")
+        lam_np = st.lam.cpu().numpy().copy()
+        _, po_a = arm_opts(head_kind)
+        a0, a1, a2, a3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+        for rep_k in range(2):          # the first pass builds the mesh's face table
+            a0.record()
+            mk.mk_hartree_poisson(ctx, mesh, st.psi, occ, N, w_psi, bc="multipole", opt=po_a)
+            mk.mk_frozen_potential(ctx, mesh, st.psi, occ, N, w_psi, wl["xc"], vq_psi)
+            a1.record()
+            mk.mk_error_indicators(ctx, mesh, mol, st.psi, N, lam_np, vq_psi, eta2)
+            a2.record()
+            n_marked, t_cut = mk.mk_dorfler_mark(ctx, eta2, 0.4, marked)
+            a3.record()
+            torch.cuda.synchronize()
+        afem = {"potential_ms": a0.elapsed_time(a1), "indicator_ms": a1.elapsed_time(a2),
+                "dorfler_ms": a2.elapsed_time(a3), "theta": 0.4, "marked": n_marked, "elements": E,
+                "eta_total": float(eta2.sum().sqrt()), "threshold": t_cut}
 
     # the same operator kernel timed alone (no concurrent stream), for comparison with its in-step duration
     iso_ms = None
@@ -724,14 +765,16 @@ def main():
             "data": "synthetic",
             "config": dict(workload_config(wl, N, n_free, NH, E), precision=a.precision,
                            precond="learned (FCG(1))" if head_kind == "learned" else "jacobi",
-                           rtol=1e-8, sigma=sigma, l2="working set > L2 (no flush needed)",
+                           rtol=1e-8, sigma=sigma, sigma_doublings=sigma_doublings,
+                           l2="working set > L2 (no flush needed)",
                            parallelism="replicas" if world > 1 else "single GPU"),
             "e2e": {"value": float(n_free) * N * a.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "gpu_launches_per_step": launches / a.steps,
             "clocks": clk, "roofline": roof, "roofline_learned": roof_tc, "roofline_stiffness": roof_k,
             "cpu_baseline": cpu, "parity": parity,
-            "compare": compare, "paper_form": paper, "joint_space": joint, "training": train_info, "batch": batch,
+            "compare": compare, "paper_form": paper, "joint_space": joint, "afem_estimate_mark": afem,
+            "training": train_info, "batch": batch,
             "learned_vs_plain": evaluation,
             "solve_iterations": solve["iterations"], "solve_max_rel_residual": solve["max_rel_residual"],
             "poisson_iterations": reps["poisson"]["iterations"] if reps["poisson"] else None,

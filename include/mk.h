@@ -410,6 +410,26 @@ int mk_inner_potential(mk_ctx* ctx, const mk_inner* inner, double* w, void* stre
 int mk_inner_info(const mk_inner* inner, int* w_in_VH, double* schur);
 int mk_inner_destroy(mk_inner* inner);
 
+/* ---------------------------------------------------------------------------------------------- AFEM */
+/* The outer AFEM loop's Estimate and Mark steps (Sec. 2, the residual a posteriori error indicator and Dorfler's
+ * marking strategy).  mk_error_indicators: for the orbitals psi [n_nodes*ld] device (columns < N) with eigenvalues
+ * lambda [N] host, and vq [n_elems * n_quad] device = w + V_xc at the quadrature points (mk_frozen_potential of
+ * psi's own density), per fine element T
+ *   eta2[T] = h_T^2 sum_i ||H psi_i - lambda_i psi_i||_{0,T}^2
+ *             + sum over the interior faces e of T of h_e sum_i ||1/2 grad psi_i|T+ . nu+ + 1/2 grad psi_i|T- . nu-||_{0,e}^2
+ * with H = -1/2 Laplacian + V_ext(mol) + vq, h_T and h_e the longest edges of T and e; the element integral by
+ * the 27-point rule, the face integral by the 3-point rule at the face's edge midpoints.  eta2 [n_elems] device.
+ * The first call builds the mesh's face table (host, kept in the mesh handle).  Deterministic (no atomics).
+ * mk_dorfler_mark: marked[T] = 1 for eta2[T] >= t*, with t* the largest t for which the indicators at or above t
+ * sum to at least theta times their total (0 < theta <= 1; the paper's experiments use 0.4): without ties at the
+ * cut, the smallest set in order of decreasing indicator; elements tied with the cut are all marked.  eta2 [n]
+ * and marked [n] device; n_marked and threshold (t*) host, or NULL.  Synchronises the stream (about 64 fixed-order
+ * reductions).  MK_ERR_INVALID_ARG if the indicators sum to zero. */
+int mk_error_indicators(mk_ctx* ctx, const mk_mesh* mesh, const mk_molecule* mol, const double* psi, int ld, int N,
+                        const double* lambda, const double* vq, double* eta2, void* stream);
+int mk_dorfler_mark(mk_ctx* ctx, int64_t n, const double* eta2, double theta, uint8_t* marked, int64_t* n_marked,
+                    double* threshold, void* stream);
+
 /* ---------------------------------------------------------------------------------------------- shift */
 /* Lowest Ritz value of `steps` Lanczos steps on the pencil (K/2 + M_{V_ext}, M) over the free fine DOF, from the
  * start vector v0 [n_free] (host, free-DOF order); M^-1 applied by an inner CG.  Used for the shift rule

@@ -713,8 +713,14 @@ __global__ void k_sec_roots(int n, int N, double* __restrict__ work, int* __rest
   }
   double delta = 0.5 * (lo + hi);
   if (m > 0)
-    for (int it = 0; it < 2100; ++it) {  // bisection to adjacent doubles (bounded)
-      delta = 0.5 * (lo + hi);
+    for (int it = 0; it < 200; ++it) {  // bisection to adjacent doubles (bounded)
+      // The bracket has one end at 0 and never changes sign, so it is halved in the ordering of the doubles of
+      // that sign (the bit patterns of |delta|): adjacent doubles after at most 64 halvings, however close the
+      // root lies to its pole, where halving the value would walk down through every binade.
+      const uint64_t a = (uint64_t)__double_as_longlong(fabs(lo)), b = (uint64_t)__double_as_longlong(fabs(hi));
+      const uint64_t mb = a < b ? a + (b - a) / 2 : b + (a - b) / 2;
+      const double dm = __longlong_as_double((long long)mb);
+      delta = (lo >= 0.0 && hi >= 0.0) ? dm : -dm;
       if (delta == lo || delta == hi) break;
       if (warp_secular(m, dk, zk, alpha, origin, delta, lane) > 0) lo = delta; else hi = delta;
     }

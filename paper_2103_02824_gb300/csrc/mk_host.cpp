@@ -750,6 +750,7 @@ int mk_mesh_destroy(mk_mesh* m) {
   cudaFree(m->d_cinv_poisson);
   cudaFree(m->d_K64);
   cudaFree(m->d_K64diag);
+  cudaFree(m->d_face_nb);
   cudaFree(m->d_cinv_corr);
   if (m->static_ev) cudaEventDestroy(m->static_ev);
   for (MgLevel& g : m->mg) {

@@ -149,6 +149,7 @@ struct MgLevel {
   Level L;
   Csr32 K, P, R;
   float* d_dinv = nullptr;
+  mutable float omega = 0.f;  // damped-Jacobi weight of the level's smoother (0 until estimated)
 };
 
 }  // namespace mk
@@ -244,6 +245,9 @@ struct mk_mesh {
   // the Hartree Poisson operator: stiffness element matrices (FP64, element order) and K's diagonal, on first use
   mutable double* d_K64 = nullptr;
   mutable double* d_K64diag = nullptr;
+  // face neighbours of the fine mesh for the error indicator (built on first use): for element e and face slot k
+  // (the face opposite local vertex k), 4 e' + k' of the element across it, or -1 on the boundary
+  mutable int32_t* d_face_nb = nullptr;
   mutable float* d_cinv_corr = nullptr;
   mutable std::vector<double> cinv_corr_key;
   // multigrid hierarchy (mk_mesh_set_hierarchy): intermediate levels coarsest first, and the interpolation from the
@@ -251,6 +255,8 @@ struct mk_mesh {
   std::vector<mk::MgLevel> mg;
   mk::Csr32 mgP, mgR;
   bool has_mg = false;
+  // damped-Jacobi weight of the fine-level smoother of the Poisson preconditioners (0 until estimated)
+  mutable float poisson_omega = 0.f;
 };
 
 namespace mk {
@@ -294,6 +300,8 @@ enum Slot : int {
   S_BATCH,                      // batched solve: per-problem buffers
   S_JOINT, S_EIG5,              // joint augmented space: its matrices, its dense decompositions
   S_MG,                         // multigrid V-cycle: per-level right-hand sides, iterates, operator products
+  S_AFEM,                       // error indicator: face values; Dorfler marking: reduction partials
+  S_LMAX,                       // smoother weight estimate: the power iteration's two vectors (FP32)
   S_COUNT
 };
 void* scratch(mk_ctx* ctx, int slot, size_t bytes, int* err);

@@ -617,11 +617,84 @@ const float* coarse_inverse_cached(mk_ctx* ctx, const mk_mesh* m, const double* 
 
 // z = (add ? z : D^-1 r) + P A_H^-1 P^T r for columns < N.
 // Symmetric multiplicative two-level preconditioner (one damped Jacobi sweep, the coarse correction, one damped
-// Jacobi sweep): z = w D^-1 r;  z += P A_H^-1 P^T (r - A z);  z += w D^-1 (r - A z).  w = kTLOmega: the largest
-// eigenvalue of D^-1 A is about 2 for the P1/P2 stiffness matrices of these meshes (power iteration), so 0.8 keeps
-// the sweep a smoother and the preconditioner positive definite.  On the 250,047-DOF P2 Poisson problem it takes FCG
-// to 1e-8 in 47 iterations against 85 for the additive form (CPU experiment with the same matrices).
+// Jacobi sweep): z = w D^-1 r;  z += P A_H^-1 P^T (r - A z);  z += w D^-1 (r - A z).  The sweep is a smoother, and
+// the preconditioner positive definite, while w lambda_max(D^-1 A) < 2.  On the uniform cube meshes lambda_max is
+// about 2 for the P1/P2 stiffness matrices and w = kTLOmega = 0.8; on graded meshes it is larger (2.83 on the
+// 874,510-tetrahedron graded mesh), so the Poisson preconditioners take w = min(0.8, 1.6 / lambda), lambda estimated
+// per level by smoother_omega.  On the 250,047-DOF P2 Poisson problem the multiplicative form takes FCG to 1e-8 in
+// 47 iterations against 85 for the additive form (CPU experiment with the same matrices).
 constexpr float kTLOmega = 0.8f;
+constexpr int kOmegaIts = 50;
+
+// x[i] = a deterministic pseudo-random value in [0.5, 1.5), 0 on boundary rows (bnd may be NULL)
+__global__ void k_om_start(int64_t n, const uint8_t* __restrict__ bnd, float* __restrict__ x) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t h = (uint32_t)(i * 2654435761ull >> 7) & 1023u;
+  x[i] = (bnd && bnd[i]) ? 0.f : 0.5f + (float)h / 1024.f;
+}
+// part[blk] = (sum x y, sum x^2 / dinv) over the block's grid-stride share (rows with dinv = 0 skipped)
+__global__ void k_om_dots(int64_t n, const float* __restrict__ x, const float* __restrict__ y,
+                          const float* __restrict__ dinv, double* __restrict__ part) {
+  __shared__ double sa[kRedThreads], sb[kRedThreads];
+  double a = 0.0, b = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    a += (double)x[i] * y[i];
+    if (dinv[i] != 0.f) b += (double)x[i] * x[i] / dinv[i];
+  }
+  sa[threadIdx.x] = a;
+  sb[threadIdx.x] = b;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      sa[threadIdx.x] += sa[threadIdx.x + w];
+      sb[threadIdx.x] += sb[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = sa[0];
+    part[2 * blockIdx.x + 1] = sb[0];
+  }
+}
+__global__ void k_om_next(int64_t n, const float* __restrict__ dinv, const float* __restrict__ y, float scale,
+                          float* __restrict__ x) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = scale * dinv[i] * y[i];
+}
+
+// Smoother weight of one level: lambda = the Rayleigh quotient (x, A x) / (x, D x) after kOmegaIts steps of the power
+// iteration on D^-1 A (a lower bound of lambda_max that rises with the steps), w = min(kTLOmega, 1.6 / lambda).
+// apply(x, y): y = A x on the level's n rows (one column).  Synchronises s once per step; run once per level.
+template <typename Apply>
+static int smoother_omega(mk_ctx* ctx, int64_t n, Apply&& apply, const float* dinv, const uint8_t* bnd,
+                          cudaStream_t s, float* omega) {
+  int err = MK_OK;
+  const int nblk = red_blocks(ctx);
+  const size_t vb = ((size_t)n * 2 * sizeof(float) + 255) / 256 * 256;
+  char* ws = (char*)scratch(ctx, S_LMAX, vb + (size_t)nblk * 2 * sizeof(double) + 64, &err);
+  if (!ws) return err;
+  float* x = (float*)ws;
+  float* y = x + n;
+  double* part = (double*)(ws + vb);
+  double* sums = part + 2 * nblk;
+  const int gb = (int)((n + 255) / 256);
+  MK_COUNT(), k_om_start<<<gb, 256, 0, s>>>(n, bnd, x);
+  double lam = 0.0;
+  for (int it = 0; it < kOmegaIts; ++it) {
+    MK_TRY(apply(x, y));
+    MK_COUNT(), k_om_dots<<<nblk, kRedThreads, 0, s>>>(n, x, y, dinv, part);
+    sum_partials(part, nblk, 2, sums, s);
+    double h[2];
+    MK_CUDA(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, s));
+    MK_CUDA(cudaStreamSynchronize(s));
+    MK_ARG(h[1] > 0.0 && h[0] > 0.0, "multigrid: the level's operator is not positive definite");
+    lam = h[0] / h[1];
+    MK_COUNT(), k_om_next<<<gb, 256, 0, s>>>(n, dinv, y, (float)(1.0 / lam), x);
+  }
+  *omega = (float)std::min((double)kTLOmega, 1.6 / lam);
+  return MK_OK;
+}
 
 __global__ void k_tl_jacobi(int64_t n, const uint8_t* __restrict__ bnd, const float* __restrict__ dinv,
                             const float* __restrict__ r, float* __restrict__ z, int ld, int N, float w) {
@@ -717,7 +790,7 @@ __global__ void k_mg_dense(int n, const float* __restrict__ Ainv, const float* _
 // fine inverse diagonal (0 on boundary rows), cinv the dense FP32 inverse of P^T K P on V_H.
 template <typename Apply>
 static int mg_apply(mk_ctx* ctx, const mk_mesh* m, Apply&& apply32, const float* dinv, const float* cinv,
-                    const float* r, float* z, cudaStream_t s) {
+                    const float* r, float* z, cudaStream_t s, float w) {
   const int nm = (int)m->mg.size();
   const int64_t nf = m->fine.n_nodes, nH = m->coarse.n_free;
   // scratch: the fine operator product, then per intermediate level b, x, q, then b and x on V_H
@@ -737,7 +810,6 @@ static int mg_apply(mk_ctx* ctx, const mk_mesh* m, Apply&& apply32, const float*
   }
   float* bH = p;
   float* xH = p + nH;
-  const float w = kTLOmega;
   auto blocks = [](int64_t n) { return (int)((n + 255) / 256); };
   auto wblocks = [](int64_t n) { return (int)((n * 32 + 255) / 256); };
   // down: fine level
@@ -750,7 +822,7 @@ static int mg_apply(mk_ctx* ctx, const mk_mesh* m, Apply&& apply32, const float*
   for (int k = nm - 1; k >= 0; --k) {
     const MgLevel& g = m->mg[k];
     const int64_t n = g.L.n_nodes;
-    MK_COUNT(), k_mg_jac0<<<blocks(n), 256, 0, s>>>(n, g.d_dinv, b[k], x[k], w);
+    MK_COUNT(), k_mg_jac0<<<blocks(n), 256, 0, s>>>(n, g.d_dinv, b[k], x[k], g.omega);
     MK_COUNT(), k_mg_spmv<<<wblocks(n), 256, 0, s>>>(n, g.K.d_off, g.K.d_col, g.K.d_val, x[k], q[k]);
     float* bnext = k > 0 ? b[k - 1] : bH;
     MK_COUNT(), k_mg_restrict<<<wblocks(g.R.n_rows), 256, 0, s>>>(g.R.n_rows, g.R.d_off, g.R.d_col, g.R.d_val, b[k],
@@ -765,7 +837,7 @@ static int mg_apply(mk_ctx* ctx, const mk_mesh* m, Apply&& apply32, const float*
     const float* xc = k > 0 ? x[k - 1] : xH;
     MK_COUNT(), k_mg_prolong<<<blocks(n), 256, 0, s>>>(n, g.P.d_off, g.P.d_col, g.P.d_val, g.d_dinv, xc, x[k]);
     MK_COUNT(), k_mg_spmv<<<wblocks(n), 256, 0, s>>>(n, g.K.d_off, g.K.d_col, g.K.d_val, x[k], q[k]);
-    MK_COUNT(), k_mg_post<<<blocks(n), 256, 0, s>>>(n, g.d_dinv, b[k], q[k], x[k], w);
+    MK_COUNT(), k_mg_post<<<blocks(n), 256, 0, s>>>(n, g.d_dinv, b[k], q[k], x[k], g.omega);
   }
   // up: fine level
   MK_COUNT(), k_mg_prolong<<<blocks(nf), 256, 0, s>>>(nf, m->mgP.d_off, m->mgP.d_col, m->mgP.d_val, dinv,
@@ -778,8 +850,8 @@ static int mg_apply(mk_ctx* ctx, const mk_mesh* m, Apply&& apply32, const float*
 
 template <typename Apply>
 static int twolevel_mult_apply(mk_ctx* ctx, const mk_mesh* m, Apply&& apply32, const float* cinv, const float* dinv,
-                               const float* r, float* z, int ld, int N, cudaStream_t s, bool z0_ready = false,
-                               bool defer_final = false) {
+                               const float* r, float* z, int ld, int N, cudaStream_t s, float w,
+                               bool z0_ready = false, bool defer_final = false) {
   const Level& L = m->fine;
   const int nH = (int)m->coarse.n_free;
   int err = MK_OK;
@@ -788,7 +860,7 @@ static int twolevel_mult_apply(mk_ctx* ctx, const mk_mesh* m, Apply&& apply32, c
   if (!t || !q) return err;
   float* y = t + (size_t)kTLS * nH * ld;
   const int gb = (int)((L.n_nodes * N + 255) / 256);
-  if (!z0_ready) MK_COUNT(), k_tl_jacobi<<<gb, 256, 0, s>>>(L.n_nodes, L.d_boundary, dinv, r, z, ld, N, kTLOmega);
+  if (!z0_ready) MK_COUNT(), k_tl_jacobi<<<gb, 256, 0, s>>>(L.n_nodes, L.d_boundary, dinv, r, z, ld, N, w);
   MK_TRY(apply32(z, q));
   MK_COUNT(), k_tl_restrict<<<nH * kTLS / kTLW, kTLW * 32, 0, s>>>(m->d_PT_off, m->d_PT_col, m->d_PT_val32, r, q,
                                                                    ld, N, t);
@@ -798,7 +870,7 @@ static int twolevel_mult_apply(mk_ctx* ctx, const mk_mesh* m, Apply&& apply32, c
                                               L.d_boundary, r, z, ld, N, 1);
   MK_TRY(apply32(z, q));
   if (!defer_final)
-    MK_COUNT(), k_tl_resid<<<gb, 256, 0, s>>>(L.n_nodes, L.d_boundary, dinv, r, q, z, ld, N, kTLOmega, 1);
+    MK_COUNT(), k_tl_resid<<<gb, 256, 0, s>>>(L.n_nodes, L.d_boundary, dinv, r, q, z, ld, N, w, 1);
   MK_CUDA(cudaGetLastError());
   return MK_OK;
 }
@@ -1403,6 +1475,26 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
     return stiff ? apply_stiff(ctx, m, xin, yout, ld, true, s) : apply_patch<float>(ctx, m, A32, xin, yout, ld, true, s);
   };
   MK_COUNT(), k_dinv32<<<(int)((n + 255) / 256), 256, 0, s>>>(n, diag, dinv);
+  // the smoother weight of the Poisson preconditioners, estimated once per mesh and per multigrid level
+  float wsm = kTLOmega;
+  if (stiff && cinv) {
+    if (m->poisson_omega == 0.f)
+      MK_TRY(smoother_omega(ctx, n, [&](const float* xi, float* yo) { return apply_stiff(ctx, m, xi, yo, 1, true, s); },
+                            dinv, L.d_boundary, s, &m->poisson_omega));
+    wsm = m->poisson_omega;
+    if (mg)
+      for (const MgLevel& g : m->mg)
+        if (g.omega == 0.f) {
+          const int64_t nl = g.L.n_nodes;
+          auto spmv = [&](const float* xi, float* yo) -> int {
+            MK_COUNT(), k_mg_spmv<<<(int)((nl * 32 + 255) / 256), 256, 0, s>>>(nl, g.K.d_off, g.K.d_col, g.K.d_val,
+                                                                               xi, yo);
+            MK_CUDA(cudaGetLastError());
+            return MK_OK;
+          };
+          MK_TRY(smoother_omega(ctx, nl, spmv, g.d_dinv, nullptr, s, &g.omega));
+        }
+  }
   MK_COUNT(), k_zero_boundary<<<(int)((n * ld + 255) / 256), 256, 0, s>>>(n, L.d_boundary, x, ld);
   MK_CUDA(cudaMemsetAsync(st, 0, 256 * sizeof(MixState), s));
   const int th = ld * (256 / ld);
@@ -1449,13 +1541,13 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
     if (refine >= max_refine || total_it >= o.maxit) break;
     ++refine;
     auto precond = [&]() -> int {  // zb = M(r)
-      if (mg) return mg_apply(ctx, m, apply32, dinv, cinv, r, zb, s);
+      if (mg) return mg_apply(ctx, m, apply32, dinv, cinv, r, zb, s, wsm);
       if (learned) {
         MK_TRY(learned_apply(ctx, m, o.mlp, dinv, r, zb, ld, N, o.mlp_precision, s));
         if (cinv) MK_TRY(twolevel_apply(ctx, m, cinv, dinv, r, zb, ld, N, true, s));
         return MK_OK;
       }
-      return twolevel_mult_apply(ctx, m, apply32, cinv, dinv, r, zb, ld, N, s);
+      return twolevel_mult_apply(ctx, m, apply32, cinv, dinv, r, zb, ld, N, s, wsm);
     };
     if (fcg) {
       MK_TRY(precond());
@@ -1475,9 +1567,9 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
         if (tlq) {
           // multiplicative two-level: the first sweep rides on the update, the last on the z.q reduction
           MK_COUNT(), k_fcg_update<<<nblk, th, 0, s>>>(n, st, p, q, d, r, ld, part, fin(5, 1), zb, dinv,
-                                                       L.d_boundary, N, kTLOmega);
-          MK_TRY(twolevel_mult_apply(ctx, m, apply32, cinv, dinv, r, zb, ld, N, s, true, true));
-          MK_COUNT(), k_tl_final_pq<<<nblk, th, 0, s>>>(n, L.d_boundary, dinv, r, tlq, zb, q, ld, N, kTLOmega, part,
+                                                       L.d_boundary, N, wsm);
+          MK_TRY(twolevel_mult_apply(ctx, m, apply32, cinv, dinv, r, zb, ld, N, s, wsm, true, true));
+          MK_COUNT(), k_tl_final_pq<<<nblk, th, 0, s>>>(n, L.d_boundary, dinv, r, tlq, zb, q, ld, N, wsm, part,
                                                         fin(6, 1));
         } else {
           MK_COUNT(), k_fcg_update<<<nblk, th, 0, s>>>(n, st, p, q, d, r, ld, part, fin(5, 1), nullptr, nullptr,

@@ -135,6 +135,9 @@ _SIGS = {
     "mk_inner_potential": [_vp, _vp, _vp, _vp],
     "mk_inner_info": [_vp, C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "mk_inner_destroy": [_vp],
+    "mk_error_indicators": [_vp, _vp, C.POINTER(mk_molecule), _vp, C.c_int, C.c_int, C.POINTER(C.c_double), _vp,
+                            _vp, _vp],
+    "mk_dorfler_mark": [_vp, C.c_int64, _vp, C.c_double, _vp, C.POINTER(C.c_int64), C.POINTER(C.c_double), _vp],
     "mk_mlp_param_count": [C.c_int],
     "mk_mlp_create": [_vp, C.c_int, C.POINTER(C.c_float), C.POINTER(_vp)],
     "mk_mlp_destroy": [_vp],
@@ -520,6 +523,22 @@ class Inner:
             self.close()
         except Exception:
             pass
+
+
+def mk_error_indicators(ctx, mesh, mol: Molecule, psi, N, lam, vq, eta2, stream=None):
+    """eta2 [n_elems] device: the residual a posteriori indicator of (lam, psi) with vq = w + V_xc at the points."""
+    ld = psi.shape[1] if psi.dim() == 2 else 1
+    lam_h, lam_p = _host_f64(lam)
+    _check(lib().mk_error_indicators(ctx.h, mesh.h, C.byref(mol.c), _ptr(psi), ld, N, lam_p, _ptr(vq), _ptr(eta2),
+                                     _stream(stream)))
+
+
+def mk_dorfler_mark(ctx, eta2, theta, marked, stream=None):
+    """marked [n] device uint8; returns (n_marked, threshold)."""
+    nm, th = C.c_int64(), C.c_double()
+    _check(lib().mk_dorfler_mark(ctx.h, int(eta2.numel()), _ptr(eta2), float(theta), _ptr(marked), C.byref(nm),
+                                 C.byref(th), _stream(stream)))
+    return nm.value, th.value
 
 
 def mk_batch_correction_solve(ctx, meshes, mols, sigmas, rhs_list, x_list, Ns, opt=None, stream=None, allow=()):

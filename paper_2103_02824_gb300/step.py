@@ -125,15 +125,25 @@ def coarse_eigenpairs(ctx, mesh, Z, R, N, return_basis=False):
 
 
 def upload_workload(ctx, wl, hierarchy=True):
-    """Meshes of a named synthetic workload (see synth.workload) uploaded to the device; for the uniformly refined
-    workloads also the intermediate levels of the multigrid hierarchy (mesh.multigrid True)."""
+    """Meshes of a named synthetic workload (see synth.workload) uploaded to the device, with the intermediate levels
+    of the multigrid hierarchy (mesh.multigrid True): the coarser cube meshes for the uniformly refined workloads,
+    refinement passes about 4x apart in size for the graded ones."""
     from . import synth
-    cc, ct, fc, ft, par = synth.workload_meshes(wl)
+    graded = wl.get("mesh") == "graded"
+    snaps = [] if (graded and hierarchy) else None
+    if graded:
+        cc, ct, fc, ft, par = synth.graded_mesh(wl["n_coarse"], wl["half"], wl["R"], h_min=wl["h_min"],
+                                                alpha=wl["alpha"], snapshots=snaps)
+    else:
+        cc, ct, fc, ft, par = synth.workload_meshes(wl)
     mesh = mk.Mesh(ctx, fc, ft, cc, ct, par, wl["order"])
     mesh.multigrid = False
-    if hierarchy and wl.get("mesh") != "graded":
-        mesh.set_hierarchy(*synth.cube_hierarchy(wl["n_coarse"], wl["levels"], wl["half"]))
-        mesh.multigrid = True
+    if hierarchy:
+        levels = synth.hierarchy_from_snapshots(snaps) if graded else \
+            synth.cube_hierarchy(wl["n_coarse"], wl["levels"], wl["half"])
+        if levels[0]:
+            mesh.set_hierarchy(*levels)
+            mesh.multigrid = True
     return mesh, (cc, ct, fc, ft, par)
 
 

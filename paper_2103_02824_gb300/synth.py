@@ -100,7 +100,7 @@ def _edge_keys(a, b, nv_cap: int):
 
 
 def graded_mesh(n_coarse: int, half: float, centres, h_min: float = 0.05, alpha: float = 0.3,
-                max_elems: int = 4_000_000):
+                max_elems: int = 4_000_000, snapshots=None):
     """A conforming tetrahedral mesh of [-half, half]^3 refined toward the points `centres` [M, 3] until every
     element's longest edge is at most max(h_min, alpha * distance from its centroid to the nearest centre), nested
     in the Kuhn mesh of n_coarse^3 cubes.
@@ -113,7 +113,9 @@ def graded_mesh(n_coarse: int, half: float, centres, h_min: float = 0.05, alpha:
     classes, and every fine tetrahedron lies inside the coarse one it descends from.
 
     Returns (coarse_coords, coarse_tets, fine_coords, fine_tets, fine_parent) like nested_cube_meshes, with
-    positively oriented tetrahedra.  Deterministic: no randomness, stable orderings.
+    positively oriented tetrahedra.  Deterministic: no randomness, stable orderings.  snapshots: a list that, when
+    given, receives after every refinement pass (marking plus closure) the mesh so far as (coords, tets, prev), prev
+    the element of the previous snapshot (or of the coarse mesh) that contains each element: a nested chain.
     """
     cc, ct = cube_mesh(n_coarse, half)
     centres = np.asarray(centres, dtype=np.float64).reshape(-1, 3)
@@ -154,8 +156,10 @@ def graded_mesh(n_coarse: int, half: float, centres, h_min: float = 0.05, alpha:
             pos = np.searchsorted(split_k, keys)
         return split_m[pos]
 
+    B = np.arange(T.shape[0], dtype=np.int64)   # the containing element of the previous snapshot
+
     def bisect(idx):
-        nonlocal T, K, A
+        nonlocal T, K, A, B
         t, k = T[idx], K[idx]
         z = midpoints(t[:, 0], t[np.arange(idx.size), k])
         c1 = t.copy()
@@ -173,6 +177,7 @@ def graded_mesh(n_coarse: int, half: float, centres, h_min: float = 0.05, alpha:
         T = np.concatenate([T, c2])
         K = np.concatenate([K, nk])
         A = np.concatenate([A, A[idx]])
+        B = np.concatenate([B, B[idx]])
 
     def hanging(rows):
         t = T[rows]
@@ -200,12 +205,50 @@ def graded_mesh(n_coarse: int, half: float, centres, h_min: float = 0.05, alpha:
             if h.size == 0:
                 break
             bisect(h)
+        if snapshots is not None:
+            snapshots.append((coords(), _oriented(coords(), T), B.astype(np.int32)))
+            B = np.arange(T.shape[0], dtype=np.int64)
     X = coords()
+    return cc, ct, X, _oriented(X, T), A.astype(np.int32)
+
+
+def _oriented(X, T):
+    """The tetrahedra T with their last two vertices swapped where the orientation is negative (int32 copy)."""
     P = X[T]
     vol = np.einsum("ij,ij->i", np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]), P[:, 3] - P[:, 0])
+    T = T.copy()
     flip = vol < 0
     T[flip, 2], T[flip, 3] = T[flip, 3].copy(), T[flip, 2].copy()
-    return cc, ct, X, T.astype(np.int32), A.astype(np.int32)
+    return T.astype(np.int32)
+
+
+def graded_hierarchy(n_coarse: int, half: float, centres, h_min: float = 0.05, alpha: float = 0.3,
+                     ratio: float = 4.0):
+    """Intermediate meshes between the coarse Kuhn mesh and the graded mesh of graded_mesh (same arguments), as
+    cube_hierarchy returns them: of the meshes after each refinement pass, the first with at least `ratio` times the
+    elements of the last level kept (the coarse mesh to begin with), coarsest first, each with the parent map into
+    the next coarser level (the coarse mesh for the first); the last parent map is that of the fine mesh into the
+    finest intermediate mesh."""
+    snaps = []
+    graded_mesh(n_coarse, half, centres, h_min=h_min, alpha=alpha, snapshots=snaps)
+    return hierarchy_from_snapshots(snaps, ratio)
+
+
+def hierarchy_from_snapshots(snaps, ratio: float = 4.0):
+    """(meshes, parents) of graded_hierarchy from the snapshots graded_mesh recorded."""
+    meshes, parents = [], []
+    comp = None
+    kept = snaps[0][2].max() + 1 if snaps else 0   # elements of the coarse mesh
+    for k, (X, T, prev) in enumerate(snaps):
+        comp = prev if comp is None else comp[prev]
+        if k == len(snaps) - 1:
+            parents.append(comp.astype(np.int32))
+        elif T.shape[0] >= ratio * kept:
+            meshes.append((X, T))
+            parents.append(comp.astype(np.int32))
+            kept = T.shape[0]
+            comp = None
+    return meshes, parents
 
 
 def molecule(seed: int, n_nuclei: int, zmax: int = 8, half: float = 3.0, dmin: float = 1.5):

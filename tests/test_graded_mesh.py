@@ -143,3 +143,30 @@ def test_cube_hierarchy_is_nested():
             s = np.linalg.solve(J, (c[t[:, k]] - x[:, 0])[..., None])[..., 0]
             lam = np.concatenate([1.0 - s.sum(axis=1, keepdims=True), s], axis=1)
             assert lam.min() > -1e-12 and lam.max() < 1.0 + 1e-12
+
+
+def test_graded_hierarchy_is_nested():
+    """The multigrid levels of a graded mesh (refinement passes about 4x apart in size): the chain coarse -> levels -> fine is
+    nested (every element's vertices lie in its parent), the children of every parent tile its volume, the levels
+    grow, and the fine mesh is the graded mesh itself."""
+    Z, R = synth.molecule(5, 3)
+    cc, ct, fc, ft, _ = synth.graded_mesh(2, 5.0, R, h_min=0.6, alpha=0.5)
+    meshes, parents = synth.graded_hierarchy(2, 5.0, R, h_min=0.6, alpha=0.5)
+    assert len(meshes) >= 2
+    chain = [(cc, ct)] + meshes + [(fc, ft)]
+    sizes = [t.shape[0] for _, t in chain]
+    assert all(a < b for a, b in zip(sizes[:-1], sizes[1:])), sizes
+
+    def vol(c, t):
+        x = c[t]
+        return np.abs(np.einsum("ij,ij->i", np.cross(x[:, 1] - x[:, 0], x[:, 2] - x[:, 0]), x[:, 3] - x[:, 0])) / 6
+    for (pc, pt), (c, t), par in zip(chain[:-1], chain[1:], parents):
+        assert par.shape[0] == t.shape[0] and par.min() >= 0 and par.max() < pt.shape[0]
+        x = pc[pt[par]]
+        J = np.stack([x[:, 1] - x[:, 0], x[:, 2] - x[:, 0], x[:, 3] - x[:, 0]], axis=2)
+        for k in range(4):
+            s = np.linalg.solve(J, (c[t[:, k]] - x[:, 0])[..., None])[..., 0]
+            lam = np.concatenate([1.0 - s.sum(axis=1, keepdims=True), s], axis=1)
+            assert lam.min() > -1e-12 and lam.max() < 1.0 + 1e-12
+        summed = np.bincount(par, weights=vol(c, t), minlength=pt.shape[0])
+        assert np.allclose(summed, vol(pc, pt), rtol=1e-12, atol=0)
