@@ -430,7 +430,7 @@ def main():
             reps = step()
             break
         except mk.MkError as ex:
-            if ex.code != mk.MK_ERR_BREAKDOWN or sigma_doublings >= 6:
+            if ex.code != mk.MK_ERR_BREAKDOWN or sigma_doublings >= 10:
                 raise
             sigma *= 2.0
             sigma_doublings += 1

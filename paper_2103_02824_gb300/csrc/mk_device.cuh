@@ -121,6 +121,8 @@ int column_dots32(mk_ctx* ctx, int64_t n_nodes, const float* a, const float* b, 
 int element_matrices(mk_ctx* ctx, const Level& L, const mk_molecule* mol, double half_k, double vext_scale,
                      double mass_shift, const double* vq, double* out, cudaStream_t s,
                      const double* base = nullptr);
+// cached M element matrices of the fine mesh (nullptr and *err set on failure)
+const double* mass_matrices(mk_ctx* ctx, const mk_mesh* m, cudaStream_t s, int* err);
 // cached K/2 + M_{V_ext} element matrices of the fine mesh for a molecule (nullptr and *err set on failure)
 const double* static_matrices(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, cudaStream_t s, int* err);
 // assembled diagonal of the packed element matrices, boundary rows set to 1

@@ -1207,15 +1207,15 @@ int mk_joint_assemble(mk_ctx* ctx, const mk_mesh* m, int k, int N, const double*
   const Level& F = m->fine;
   int err = MK_OK;
   const size_t eb = (size_t)F.n_elems * (F.nloc * (F.nloc + 1) / 2) * sizeof(double);
-  double* Me = (double*)scratch(ctx, S_ELEM64B, eb, &err);
   double* Mu = (double*)scratch(ctx, S_VEC1, (size_t)F.n_nodes * ld * sizeof(double), &err);
   double* dots = (double*)scratch(ctx, S_COEF, 64 * sizeof(double), &err);
-  if (!Me || !Mu || !dots) return err;
+  if (!Mu || !dots) return err;
+  const double* Me = mass_matrices(ctx, m, s, &err);
+  if (!Me) return err;
   const int64_t work = F.n_nodes * ld;
   MK_COUNT(), k_joint_orbitals<<<(int)((work + 255) / 256), 256, 0, s>>>(F.n_nodes, m->d_P_off, m->d_P_col, m->d_P_val,
                                                                          F.d_boundary, X, (int)m->coarse.n_free, k,
                                                                          psihat, N, ld, psi);
-  MK_TRY(element_matrices(ctx, F, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s));
   MK_TRY(apply64(ctx, m, Me, u, Mu, k, ld, true, s));
   MK_TRY(column_dots(ctx, F.n_nodes, psi, Mu, k, ld, dots, s));
   MK_COUNT(), k_flip<<<(int)((work + 255) / 256), 256, 0, s>>>(F.n_nodes, dots, psi, k, ld);
@@ -1232,14 +1232,14 @@ int mk_orbital_assemble(mk_ctx* ctx, const mk_mesh* m, const double* coef, const
   const Level& F = m->fine;
   int err = MK_OK;
   const size_t eb = (size_t)F.n_elems * (F.nloc * (F.nloc + 1) / 2) * sizeof(double);
-  double* Me = (double*)scratch(ctx, S_ELEM64B, eb, &err);
   double* Mu = (double*)scratch(ctx, S_VEC1, (size_t)F.n_nodes * ld * sizeof(double), &err);
   double* dots = (double*)scratch(ctx, S_COEF, 64 * sizeof(double), &err);
-  if (!Me || !Mu || !dots) return err;
+  if (!Mu || !dots) return err;
+  const double* Me = mass_matrices(ctx, m, s, &err);
+  if (!Me) return err;
   const int64_t work = F.n_nodes * ld;
   MK_COUNT(), k_orbitals<<<(int)((work + 255) / 256), 256, 0, s>>>(F.n_nodes, m->d_P_off, m->d_P_col, m->d_P_val, F.d_boundary,
                                                        coef, (int)m->coarse.n_free, psihat, N, ld, psi);
-  MK_TRY(element_matrices(ctx, F, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s));
   MK_TRY(apply64(ctx, m, Me, u, Mu, N, ld, true, s));
   MK_TRY(column_dots(ctx, F.n_nodes, psi, Mu, N, ld, dots, s));
   MK_COUNT(), k_flip<<<(int)((work + 255) / 256), 256, 0, s>>>(F.n_nodes, dots, psi, N, ld);

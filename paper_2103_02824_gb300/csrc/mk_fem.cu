@@ -127,6 +127,40 @@ int element_matrices(mk_ctx* ctx, const Level& L, const mk_molecule* mol, double
 // K/2 + M_{V_ext} element matrices of the fine mesh for `mol`, computed once per (mesh, molecule) and kept in the
 // mesh handle: they depend on neither the density nor the shift (the paper's static blocks, assembled in
 // advance).  The molecule is compared by value; a different one replaces the cached set.
+// M element matrices of the fine mesh (packed, FP64, element order), computed once per mesh and kept in the mesh
+// handle (they depend on the geometry only).  Readers on another stream are ordered after the write by an event.
+const double* mass_matrices(mk_ctx* ctx, const mk_mesh* m, cudaStream_t s, int* err) {
+  const Level& L = m->fine;
+  if (!m->mass_ev && cudaEventCreateWithFlags(&m->mass_ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    m->mass_ev = nullptr;
+    *err = fail(MK_ERR_CUDA, "mass element matrices: event creation failed");
+    return nullptr;
+  }
+  if (m->d_M64) {
+    if (cudaStreamWaitEvent(s, m->mass_ev, 0) != cudaSuccess) {
+      *err = fail(MK_ERR_CUDA, "mass element matrices: cudaStreamWaitEvent failed");
+      return nullptr;
+    }
+    return m->d_M64;
+  }
+  const size_t bytes = (size_t)L.n_elems * (L.nloc * (L.nloc + 1) / 2) * sizeof(double);
+  if (cudaMalloc(&m->d_M64, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    m->d_M64 = nullptr;
+    *err = fail(MK_ERR_OOM, "mass element matrices: allocation failed");
+    return nullptr;
+  }
+  const int r = element_matrices(ctx, L, nullptr, 0.0, 0.0, 1.0, nullptr, m->d_M64, s);
+  if (r != MK_OK || cudaEventRecord(m->mass_ev, s) != cudaSuccess) {
+    cudaFree(m->d_M64);
+    m->d_M64 = nullptr;
+    *err = r != MK_OK ? r : fail(MK_ERR_CUDA, "mass element matrices: cudaEventRecord failed");
+    return nullptr;
+  }
+  return m->d_M64;
+}
+
 const double* static_matrices(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, cudaStream_t s, int* err) {
   const Level& L = m->fine;
   std::vector<double> key;

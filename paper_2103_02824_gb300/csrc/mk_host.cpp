@@ -745,6 +745,8 @@ int mk_mesh_destroy(mk_mesh* m) {
   free_patches(m->patches);
   cudaFree(m->d_MH_Linv);
   cudaFree(m->d_static);
+  cudaFree(m->d_M64);
+  if (m->mass_ev) cudaEventDestroy(m->mass_ev);
   cudaFree(m->d_P_val32);
   cudaFree(m->d_PT_val32);
   cudaFree(m->d_cinv_poisson);

@@ -541,7 +541,7 @@ int mk_inner_create(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, const
   const size_t eb = (size_t)E * (nl * (nl + 1) / 2) * sizeof(double);
   double* H1e = (double*)scratch(ctx, S_ELEM64, eb, &err);
   double* M3e = (double*)scratch(ctx, S_ELEM64B, eb, &err);
-  double* Me = (double*)scratch(ctx, S_ELEM64C, eb, &err);
+  const double* Me = mass_matrices(ctx, m, s, &err);
   double* Ke = (double*)scratch(ctx, S_ELEM64D, eb, &err);
   double* Y = (double*)scratch(ctx, S_VEC1, (size_t)n * ld * sizeof(double), &err);
   double* V1 = (double*)scratch(ctx, S_VEC2, (size_t)n * sizeof(double), &err);
@@ -570,7 +570,6 @@ int mk_inner_create(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, const
   int r;
   if ((r = element_matrices(ctx, F, nullptr, 0.0, 0.0, 0.0, vq, H1e, s, H0)) != MK_OK) return bail(r);
   if ((r = element_matrices(ctx, F, nullptr, 0.0, 0.0, 0.0, wq0, M3e, s)) != MK_OK) return bail(r);
-  if ((r = element_matrices(ctx, F, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s)) != MK_OK) return bail(r);
   if ((r = element_matrices(ctx, F, nullptr, 1.0, 0.0, 0.0, nullptr, Ke, s)) != MK_OK) return bail(r);
   // coarse blocks: A1 = P^T H1 P, A3 = P^T M_{w~0} P, C_H = P^T K P
   if ((r = coarse_matrices(ctx, m, H1e, M3e, h->A1, h->A3, S_COARSE, s)) != MK_OK) return bail(r);

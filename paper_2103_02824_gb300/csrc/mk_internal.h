@@ -237,6 +237,9 @@ struct mk_mesh {
   mutable double* d_static = nullptr;
   mutable std::vector<double> static_key;
   mutable cudaEvent_t static_ev = nullptr;  // recorded after the set was written
+  // M element matrices (FP64, element order), built on first use, and the event recorded after they were written
+  mutable double* d_M64 = nullptr;
+  mutable cudaEvent_t mass_ev = nullptr;
   // two-level preconditioner (built on first use): FP32 values of P and P^T, and FP32 dense inverses of the
   // Galerkin coarse operators P^T K P (Poisson) and P^T (K/2 + M_Vext + sigma M) P (the key: molecule, sigma)
   mutable float* d_P_val32 = nullptr;

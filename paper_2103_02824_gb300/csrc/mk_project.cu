@@ -252,15 +252,15 @@ extern "C" int mk_augmented_project(mk_ctx* ctx, const mk_mesh* m, const mk_mole
   int err = MK_OK;
   const size_t eb = (size_t)F.n_elems * (nl * (nl + 1) / 2) * sizeof(double);
   double* He = (double*)scratch(ctx, S_ELEM64, eb, &err);
-  double* Me = (double*)scratch(ctx, S_ELEM64B, eb, &err);
   double* Y = (double*)scratch(ctx, S_VEC1, (size_t)F.n_nodes * ld * sizeof(double), &err);
   double* MY = (double*)scratch(ctx, S_VEC2, (size_t)F.n_nodes * ld * sizeof(double), &err);
   double* G = (double*)scratch(ctx, S_GRAM, (size_t)2 * N * N * sizeof(double), &err);
-  if (!He || !Me || !Y || !MY || !G) return err;
+  if (!He || !Y || !MY || !G) return err;
+  const double* Me = mass_matrices(ctx, m, s, &err);
+  if (!Me) return err;
   const double* H0 = static_matrices(ctx, m, mol, s, &err);
   if (!H0) return err;
   MK_TRY(element_matrices(ctx, F, nullptr, 0.0, 0.0, 0.0, vq, He, s, H0));
-  MK_TRY(element_matrices(ctx, F, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s));
   MK_TRY(apply64(ctx, m, He, psihat, Y, N, ld, true, s));
   MK_TRY(apply64(ctx, m, Me, psihat, MY, N, ld, true, s));
   MK_TRY(restrict_to_coarse(ctx, m, Y, ld, N, b, N, s));

@@ -517,13 +517,13 @@ int mk_assemble_rhs_from_vq(mk_ctx* ctx, const mk_mesh* m, const double* u, int 
   const Level& L = m->fine;
   int err = MK_OK;
   const size_t eb = (size_t)L.n_elems * (L.nloc * (L.nloc + 1) / 2) * sizeof(double);
-  double* Me = (double*)scratch(ctx, S_ELEM64B, eb, &err);
   double* Ve = (double*)scratch(ctx, S_ELEM64, eb, &err);
   double* Mu = (double*)scratch(ctx, S_VEC1, (size_t)L.n_nodes * ld * sizeof(double), &err);
   double* Vu = (double*)scratch(ctx, S_VEC2, (size_t)L.n_nodes * ld * sizeof(double), &err);
-  if (!Me || !Ve || !Mu || !Vu) return err;
+  if (!Ve || !Mu || !Vu) return err;
+  const double* Me = mass_matrices(ctx, m, s, &err);
+  if (!Me) return err;
   MK_TRY(element_matrices(ctx, L, nullptr, 0.0, 0.0, 0.0, vq, Ve, s));
-  MK_TRY(element_matrices(ctx, L, nullptr, 0.0, 0.0, 1.0, nullptr, Me, s));
   MK_TRY(apply64(ctx, m, Me, u, Mu, N, ld, true, s));
   MK_TRY(apply64(ctx, m, Ve, u, Vu, N, ld, true, s));
   ColParams coef{};

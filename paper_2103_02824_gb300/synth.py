@@ -99,69 +99,71 @@ def _edge_keys(a, b, nv_cap: int):
     return lo.astype(np.int64) * nv_cap + hi.astype(np.int64)
 
 
-def graded_mesh(n_coarse: int, half: float, centres, h_min: float = 0.05, alpha: float = 0.3,
-                max_elems: int = 4_000_000, snapshots=None):
-    """A conforming tetrahedral mesh of [-half, half]^3 refined toward the points `centres` [M, 3] until every
-    element's longest edge is at most max(h_min, alpha * distance from its centroid to the nearest centre), nested
-    in the Kuhn mesh of n_coarse^3 cubes.
+class NVBMesh:
+    """A tetrahedral mesh in Maubach's form for newest-vertex bisection: vertices X [nv, 3], tetrahedra T [E, 4] with
+    their vertices in bisection order and tags K [E] in {1, 2, 3}.  A tetrahedron (x0, x1, x2, x3) with tag k is cut
+    at the midpoint z of the edge x0-xk into (x0, .., x_{k-1}, z, x_{k+1}, .., x3), which keeps its index, and
+    (x1, .., xk, z, x_{k+1}, .., x3), appended after the existing elements in the order of the cut ones; both take
+    tag k - 1 (3 after 1).  A new midpoint is numbered after the existing vertices in the order of the first element
+    (lowest index) that cuts its edge.  The Kuhn tetrahedra, with their vertices in path order and tag 3, are
+    compatible with it: every refinement is conforming after closure (any tetrahedron that holds an edge already cut
+    is cut too, until none does), the elements fall into a bounded number of similarity classes, and every
+    tetrahedron lies inside the one it descends from.  A (ancestor) and B (the element of the last `mark_level`)
+    track the nesting."""
 
-    Refinement is newest-vertex bisection in Maubach's form: a tetrahedron (x0, x1, x2, x3) with tag k in {1, 2, 3}
-    is cut at the midpoint z of the edge x0-xk into (x0, .., x_{k-1}, z, x_{k+1}, .., x3) and
-    (x1, .., xk, z, x_{k+1}, .., x3), both with tag k - 1 (3 after 1).  The Kuhn tetrahedra, with their vertices in
-    path order and tag 3, are compatible with it: every refinement is conforming after closure (any tetrahedron that
-    holds an edge already cut is cut too, until none does), the elements fall into a bounded number of similarity
-    classes, and every fine tetrahedron lies inside the coarse one it descends from.
+    _PAIRS = np.array([(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)])
+    _CAP = 1 << 31
 
-    Returns (coarse_coords, coarse_tets, fine_coords, fine_tets, fine_parent) like nested_cube_meshes, with
-    positively oriented tetrahedra.  Deterministic: no randomness, stable orderings.  snapshots: a list that, when
-    given, receives after every refinement pass (marking plus closure) the mesh so far as (coords, tets, prev), prev
-    the element of the previous snapshot (or of the coarse mesh) that contains each element: a nested chain.
-    """
-    cc, ct = cube_mesh(n_coarse, half)
-    centres = np.asarray(centres, dtype=np.float64).reshape(-1, 3)
-    # path order (undo the orientation swap of the negative permutations)
-    T = ct.astype(np.int64).copy()
-    neg = np.array([_PERM_SIGN[p] < 0 for p in range(6)] * (T.shape[0] // 6))
-    T[neg, 2], T[neg, 3] = ct[neg, 3], ct[neg, 2]
-    K = np.full(T.shape[0], 3, dtype=np.int64)
-    A = np.arange(T.shape[0], dtype=np.int64)
-    V = [cc.astype(np.float64)]
-    nv = cc.shape[0]
-    cap = 1 << 31
-    split_k = np.zeros(0, dtype=np.int64)   # sorted keys of the edges already cut
-    split_m = np.zeros(0, dtype=np.int64)   # their midpoints
-    pairs = np.array([(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)])
+    def __init__(self, X, T, K):
+        self.V = [np.asarray(X, dtype=np.float64)]
+        self.nv = self.V[0].shape[0]
+        self.T = np.asarray(T, dtype=np.int64).copy()
+        self.K = np.asarray(K, dtype=np.int64).copy()
+        self.A = np.arange(self.T.shape[0], dtype=np.int64)
+        self.B = self.A.copy()
+        self.split_k = np.zeros(0, dtype=np.int64)   # sorted keys of the edges already cut
+        self.split_m = np.zeros(0, dtype=np.int64)   # their midpoints
 
-    def coords():
-        return np.concatenate(V, axis=0) if len(V) > 1 else V[0]
+    @classmethod
+    def kuhn(cls, n: int, half: float):
+        """The Kuhn mesh of n^3 cubes in Maubach's form (path order, tag 3)."""
+        cc, ct = cube_mesh(n, half)
+        T = ct.astype(np.int64).copy()
+        neg = np.array([_PERM_SIGN[p] < 0 for p in range(6)] * (T.shape[0] // 6))
+        T[neg, 2], T[neg, 3] = ct[neg, 3], ct[neg, 2]
+        return cls(cc, T, np.full(T.shape[0], 3, dtype=np.int64))
 
-    def midpoints(a, b):
-        nonlocal split_k, split_m, nv
-        keys = _edge_keys(a, b, cap)
-        pos = np.searchsorted(split_k, keys)
+    def coords(self):
+        if len(self.V) > 1:
+            self.V = [np.concatenate(self.V, axis=0)]
+        return self.V[0]
+
+    def _midpoints(self, a, b):
+        keys = _edge_keys(a, b, self._CAP)
+        pos = np.searchsorted(self.split_k, keys)
         found = np.zeros(keys.size, dtype=bool)
-        ok = pos < split_k.size
-        found[ok] = split_k[pos[ok]] == keys[ok]
+        ok = pos < self.split_k.size
+        found[ok] = self.split_k[pos[ok]] == keys[ok]
         if not found.all():
             uk, first = np.unique(keys[~found], return_index=True)
+            o = np.argsort(first, kind="stable")          # in order of first appearance (element order)
+            uk, first = uk[o], first[o]
             ia, ib = a[~found][first], b[~found][first]
-            X = coords()
-            V.append(0.5 * (X[ia] + X[ib]))
-            ids = nv + np.arange(uk.size, dtype=np.int64)
-            nv += uk.size
-            allk = np.concatenate([split_k, uk])
-            allm = np.concatenate([split_m, ids])
-            o = np.argsort(allk, kind="stable")
-            split_k, split_m = allk[o], allm[o]
-            pos = np.searchsorted(split_k, keys)
-        return split_m[pos]
+            X = self.coords()
+            self.V.append(0.5 * (X[ia] + X[ib]))
+            ids = self.nv + np.arange(uk.size, dtype=np.int64)
+            self.nv += uk.size
+            allk = np.concatenate([self.split_k, uk])
+            allm = np.concatenate([self.split_m, ids])
+            srt = np.argsort(allk, kind="stable")
+            self.split_k, self.split_m = allk[srt], allm[srt]
+            pos = np.searchsorted(self.split_k, keys)
+        return self.split_m[pos]
 
-    B = np.arange(T.shape[0], dtype=np.int64)   # the containing element of the previous snapshot
-
-    def bisect(idx):
-        nonlocal T, K, A, B
-        t, k = T[idx], K[idx]
-        z = midpoints(t[:, 0], t[np.arange(idx.size), k])
+    def bisect(self, idx):
+        """Bisect the elements idx (ascending)."""
+        t, k = self.T[idx], self.K[idx]
+        z = self._midpoints(t[:, 0], t[np.arange(idx.size), k])
         c1 = t.copy()
         c1[np.arange(idx.size), k] = z
         c2 = np.empty_like(t)
@@ -170,46 +172,78 @@ def graded_mesh(n_coarse: int, half: float, centres, h_min: float = 0.05, alpha:
             if not sel.any():
                 continue
             tk = t[sel]
-            row = np.concatenate([tk[:, 1:kk + 1], z[sel, None], tk[:, kk + 1:]], axis=1)
-            c2[sel] = row
+            c2[sel] = np.concatenate([tk[:, 1:kk + 1], z[sel, None], tk[:, kk + 1:]], axis=1)
         nk = np.where(k > 1, k - 1, 3)
-        T[idx], K[idx] = c1, nk
-        T = np.concatenate([T, c2])
-        K = np.concatenate([K, nk])
-        A = np.concatenate([A, A[idx]])
-        B = np.concatenate([B, B[idx]])
+        self.T[idx], self.K[idx] = c1, nk
+        self.T = np.concatenate([self.T, c2])
+        self.K = np.concatenate([self.K, nk])
+        self.A = np.concatenate([self.A, self.A[idx]])
+        self.B = np.concatenate([self.B, self.B[idx]])
 
-    def hanging(rows):
-        t = T[rows]
-        keys = _edge_keys(t[:, pairs[:, 0]], t[:, pairs[:, 1]], cap)
-        pos = np.searchsorted(split_k, keys)
+    def hanging(self):
+        """Elements (ascending) that hold an edge already cut."""
+        keys = _edge_keys(self.T[:, self._PAIRS[:, 0]], self.T[:, self._PAIRS[:, 1]], self._CAP)
+        pos = np.searchsorted(self.split_k, keys)
         hit = np.zeros(keys.shape, dtype=bool)
-        ok = pos < split_k.size
-        hit[ok] = split_k[pos[ok]] == keys[ok]
-        return rows[hit.any(axis=1)]
+        ok = pos < self.split_k.size
+        hit[ok] = self.split_k[pos[ok]] == keys[ok]
+        return np.nonzero(hit.any(axis=1))[0]
 
+    def refine(self, idx):
+        """Bisect the elements idx (ascending), then close: bisect every element holding a cut edge until none
+        does.  Returns the number of bisection rounds."""
+        rounds = 0
+        if np.size(idx):
+            self.bisect(np.asarray(idx, dtype=np.int64))
+            rounds += 1
+        while True:
+            h = self.hanging()
+            if h.size == 0:
+                return rounds
+            self.bisect(h)
+            rounds += 1
+
+    def mark_level(self):
+        """Start a new level of the nested chain: B becomes the identity of the current elements."""
+        self.B = np.arange(self.T.shape[0], dtype=np.int64)
+
+
+def graded_mesh(n_coarse: int, half: float, centres, h_min: float = 0.05, alpha: float = 0.3,
+                max_elems: int = 4_000_000, snapshots=None, maubach=None):
+    """A conforming tetrahedral mesh of [-half, half]^3 refined toward the points `centres` [M, 3] until every
+    element's longest edge is at most max(h_min, alpha * distance from its centroid to the nearest centre), nested
+    in the Kuhn mesh of n_coarse^3 cubes, by newest-vertex bisection (NVBMesh): every pass bisects the elements that
+    violate the rule, then closes the mesh.
+
+    Returns (coarse_coords, coarse_tets, fine_coords, fine_tets, fine_parent) like nested_cube_meshes, with
+    positively oriented tetrahedra.  Deterministic: no randomness, stable orderings.  snapshots: a list that, when
+    given, receives after every refinement pass the mesh so far as (coords, tets, prev), prev the element of the
+    previous snapshot (or of the coarse mesh) that contains each element: a nested chain.  maubach: a list that,
+    when given, receives the final NVBMesh (its tetrahedra in bisection order, with their tags).
+    """
+    cc, ct = cube_mesh(n_coarse, half)
+    centres = np.asarray(centres, dtype=np.float64).reshape(-1, 3)
+    nvb = NVBMesh.kuhn(n_coarse, half)
+    pairs = NVBMesh._PAIRS
     while True:
-        X = coords()
-        P = X[T]
+        X = nvb.coords()
+        P = X[nvb.T]
         diam = np.sqrt(((P[:, pairs[:, 0]] - P[:, pairs[:, 1]]) ** 2).sum(axis=2)).max(axis=1)
         cen = P.mean(axis=1)
         dist = np.sqrt(((cen[:, None, :] - centres[None, :, :]) ** 2).sum(axis=2)).min(axis=1)
         mark = np.nonzero(diam > np.maximum(h_min, alpha * dist) * (1 + 1e-12))[0]
         if mark.size == 0:
             break
-        if T.shape[0] + mark.size > max_elems:
+        if nvb.T.shape[0] + mark.size > max_elems:
             raise ValueError("graded_mesh: more than max_elems elements")
-        bisect(mark)
-        while True:  # closure: cut every tetrahedron that still holds a cut edge
-            h = hanging(np.arange(T.shape[0]))
-            if h.size == 0:
-                break
-            bisect(h)
+        nvb.refine(mark)
         if snapshots is not None:
-            snapshots.append((coords(), _oriented(coords(), T), B.astype(np.int32)))
-            B = np.arange(T.shape[0], dtype=np.int64)
-    X = coords()
-    return cc, ct, X, _oriented(X, T), A.astype(np.int32)
+            snapshots.append((nvb.coords(), _oriented(nvb.coords(), nvb.T), nvb.B.astype(np.int32)))
+            nvb.mark_level()
+    if maubach is not None:
+        maubach.append(nvb)
+    X = nvb.coords()
+    return cc, ct, X, _oriented(X, nvb.T), nvb.A.astype(np.int32)
 
 
 def _oriented(X, T):
@@ -354,6 +388,10 @@ def workload(name: str, seed: int = 2000):
         return dict(name=name, Z=Z, R=R, order=2, half=15.0, n_coarse=4, levels=lv, xc="lda")
     if name in ("cluster12_p2", "cluster12_p2_small"):
         Z, R = molecule(5, 12)
+        # nuclei on the lattice of the Kuhn mesh refined 6 times (spacing 30 / 4 / 64 = 0.117 bohr), so that the
+        # graded mesh has a vertex at every nucleus and no quadrature point falls next to a Coulomb singularity
+        step = 2 * 15.0 / 4 / 2 ** 6
+        R = np.round(R / step) * step
         h_min, alpha = {"cluster12_p2": (0.05, 0.3), "cluster12_p2_small": (1.5, 1.0)}[name]
         return dict(name=name, Z=Z, R=R, order=2, half=15.0, n_coarse=4, mesh="graded", h_min=h_min, alpha=alpha,
                     xc="lda")
