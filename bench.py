@@ -611,6 +611,27 @@ def main():
         afem = {"potential_ms": a0.elapsed_time(a1), "indicator_ms": a1.elapsed_time(a2),
                 "dorfler_ms": a2.elapsed_time(a3), "theta": 0.4, "marked": n_marked, "elements": E,
                 "eta_total": float(eta2.sum().sqrt()), "threshold": t_cut}
+        # Refine: newest-vertex bisection of the marked elements with closure, on the fine mesh in Maubach's form
+        # (the uniform workloads' fine mesh is the Kuhn mesh of its cubes, element for element)
+        if wl.get("mesh") != "graded":
+            nvb = synth.NVBMesh.kuhn(wl["n_coarse"] * 2 ** wl["levels"], wl["half"])
+            nv0 = nvb.coords().shape[0]
+            cap_v, cap_e = nv0 + 4 * E, 3 * E
+            Xd = torch.zeros((cap_v, 3), dtype=torch.float64, device="cuda")
+            Td = torch.zeros((cap_e, 4), dtype=torch.int32, device="cuda")
+            Kd = torch.zeros(cap_e, dtype=torch.int8, device="cuda")
+            Pd = torch.zeros(cap_e, dtype=torch.int32, device="cuda")
+            times = []
+            for rep_k in range(3):
+                Xd[:nv0] = torch.from_numpy(nvb.coords()).cuda()
+                Td[:E] = torch.from_numpy(nvb.T.astype(np.int32)).cuda()
+                Kd[:E] = torch.from_numpy(nvb.K.astype(np.int8)).cuda()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                nv1, E1, rnd = mk.mk_refine(ctx, Xd, Td, Kd, Pd, marked, nv0, E)
+                times.append(time.perf_counter() - t0)
+            afem.update({"refine_ms": 1e3 * min(times), "refined_elements": E1, "refined_vertices": nv1,
+                         "refine_rounds": rnd})
 
     # the same operator kernel timed alone (no concurrent stream), for comparison with its in-step duration
     iso_ms = None
@@ -686,6 +707,14 @@ def main():
     nloc = info["nloc"]
     npack = nloc * (nloc + 1) // 2
     ld = st.ld
+    # the library records one event pair per launch, and a launch covers a block of columns: up to 32 (the FP32
+    # register-staged operator), 8 (the learned network) or 4 (the FP64 operator); an application to all columns is
+    # `passes` launches
+    passes = -(-ld // (4 if kind == mk.PROF_APPLY64 else 32))
+    n_k, ms_pass = n_k // passes, ms_k / n_k if n_k else None
+    ms_k = ms_pass * passes * n_k if n_k else 0.0
+    if iso_ms is not None:
+        iso_ms *= passes
     if kind == mk.PROF_APPLY64:
         flops = 2.0 * nloc * nloc * E * N
         achieved = flops / (ms_k / n_k * 1e-3) / 1e12 if n_k else None
@@ -729,6 +758,8 @@ def main():
     # the steps, against the sustained BF16 tensor peak (the kernel runs inside a long step)
     roof_tc = None
     ms_l, n_l = prof[mk.PROF_LEARNED]
+    lpasses = -(-N // 8)
+    n_l //= lpasses                                # applications (a launch covers 8 orbital columns)
     if n_l:
         nin, nout = nloc + 12, nloc
         lflops = 2.0 * (nin * 64 + 64 * 64 + 64 * nout) * E * N

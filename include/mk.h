@@ -429,6 +429,23 @@ int mk_error_indicators(mk_ctx* ctx, const mk_mesh* mesh, const mk_molecule* mol
                         const double* lambda, const double* vq, double* eta2, void* stream);
 int mk_dorfler_mark(mk_ctx* ctx, int64_t n, const double* eta2, double theta, uint8_t* marked, int64_t* n_marked,
                     double* threshold, void* stream);
+/* The Refine step (Sec. 2: marked elements refined so that the mesh stays shape regular and conforming): newest-vertex
+ * bisection in Maubach's form with conforming closure.  The mesh: coords [n_vertices*3] FP64, tets [n_elems*4] int32
+ * with every tetrahedron's vertices in bisection order and tags [n_elems] int8 in {1,2,3} (the Kuhn tetrahedra of a
+ * cube mesh in path order with tag 3 are such a mesh).  A tetrahedron (x0,x1,x2,x3) with tag k is cut at the midpoint
+ * z of x0-xk into (x0,..,x_{k-1},z,x_{k+1},..,x3), which keeps its index, and (x1,..,xk,z,x_{k+1},..,x3), appended in
+ * the order of the cut elements; both get tag k-1 (3 after 1).  The first round cuts the marked elements (marked
+ * [n_elems] uint8), every later round the elements that hold an edge already cut, until none does.  A new midpoint
+ * is numbered after the existing vertices in the order of the lowest-index element that cuts its edge in its round.
+ * coords, tets, tags are refined in place (device buffers with room for max_vertices and max_elems); parent
+ * [max_elems] device receives, per output element, the input element that contains it.  *n_vertices_out,
+ * *n_elems_out and *rounds (or NULL) are host.  The output tetrahedra keep the bisection order, so their orientation
+ * alternates; orient them (swap the last two vertices where the volume is negative) before mk_mesh_upload.
+ * MK_ERR_INVALID_ARG if the result would exceed max_vertices or max_elems (the buffers' contents are then
+ * unspecified).  Synchronises the stream twice per round. */
+int mk_refine(mk_ctx* ctx, int64_t n_vertices, int64_t n_elems, double* coords, int32_t* tets, int8_t* tags,
+              int32_t* parent, const uint8_t* marked, int64_t max_vertices, int64_t max_elems, int64_t* n_vertices_out,
+              int64_t* n_elems_out, int* rounds, void* stream);
 
 /* ---------------------------------------------------------------------------------------------- shift */
 /* Lowest Ritz value of `steps` Lanczos steps on the pencil (K/2 + M_{V_ext}, M) over the free fine DOF, from the

@@ -48,16 +48,16 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_apply_stream(const unsign
 
 // y = A x (FP32), one CTA per patch, one element per thread, the element matrices staged in registers and the x
 // rows in shared memory (see patch_apply_reg).  At most 128 registers a thread, so four 128-thread CTAs share an SM.
-template <int NLOC, int W>
+template <int NLOC, int WMAX>
 __global__ void __launch_bounds__(kRegMaxThreads, 2) k_apply_reg(const unsigned char* __restrict__ rec, int rec_stride,
                                                                  const float* __restrict__ Ae, int mask,
                                                                  const float* __restrict__ x, float* __restrict__ y,
-                                                                 float* __restrict__ halo, int col0, int ld, int pe,
-                                                                 int max_nodes, int64_t n_nodes, int64_t n_elems,
-                                                                 int* __restrict__ fault) {
+                                                                 float* __restrict__ halo, int col0, int W, int ld,
+                                                                 int pe, int max_nodes, int64_t n_nodes,
+                                                                 int64_t n_elems, int* __restrict__ fault) {
   extern __shared__ __align__(16) unsigned char smraw_reg[];
-  patch_apply_reg<NLOC, W>((int)blockIdx.x, rec, rec_stride, Ae, mask, x, y, halo, col0, ld, pe, max_nodes, n_nodes,
-                           n_elems, fault, smraw_reg);
+  patch_apply_reg<NLOC, WMAX>((int)blockIdx.x, rec, rec_stride, Ae, mask, x, y, halo, col0, W, ld, pe, max_nodes,
+                              n_nodes, n_elems, fault, smraw_reg);
 }
 
 template <typename T, int VEC>
@@ -159,8 +159,9 @@ static int launch_reg(mk_ctx* ctx, const mk_mesh* m, const float* Ae, const floa
   const Patches& P = m->patches;
   const Level& L = m->fine;
   *launched = 0;
-  if ((W != 4 && W != 8) || P.max_elems > kRegMaxThreads) return MK_OK;
-  const size_t ssm = reg_smem(L.nloc, P.max_elems, P.max_nodes, P.max_rec_bytes, W).total;
+  if (W < 4 || W > 32 || W % 4 != 0 || P.max_elems > kRegMaxThreads) return MK_OK;
+  const int wmax = W <= 8 ? 8 : 32;
+  const size_t ssm = reg_smem(L.nloc, P.max_elems, P.max_nodes, P.max_rec_bytes, wmax).total;
   if (ssm > 227 * 1024) return MK_OK;
   const int th = (P.max_elems + 31) / 32 * 32;
   prof_mark(ctx, PROF_APPLY32, true, s);
@@ -168,13 +169,13 @@ static int launch_reg(mk_ctx* ctx, const mk_mesh* m, const float* Ae, const floa
   do {                                                                                                          \
     auto kern = k_apply_reg<NL, WW>;                                                                            \
     if (ssm > 48 * 1024) MK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm)); \
-    MK_COUNT(), kern<<<P.n_patches, th, ssm, s>>>(P.d_rec, P.max_rec_bytes, Ae, mask, x, y, halo, col0, ld,     \
+    MK_COUNT(), kern<<<P.n_patches, th, ssm, s>>>(P.d_rec, P.max_rec_bytes, Ae, mask, x, y, halo, col0, W, ld,  \
                                                   P.max_elems, P.max_nodes, L.n_nodes, L.n_elems, ctx->d_fault); \
   } while (0)
   if (L.nloc == 4) {
-    if (W == 4) MK_RG(4, 4); else MK_RG(4, 8);
+    if (wmax == 8) MK_RG(4, 8); else MK_RG(4, 32);
   } else {
-    if (W == 4) MK_RG(10, 4); else MK_RG(10, 8);
+    if (wmax == 8) MK_RG(10, 8); else MK_RG(10, 32);
   }
 #undef MK_RG
   prof_mark(ctx, PROF_APPLY32, false, s);
@@ -205,14 +206,19 @@ int apply_patch(mk_ctx* ctx, const mk_mesh* m, const T* Ae, const T* x, T* y, in
       stream_smem(nloc, P.max_elems, P.max_nodes, P.max_rec_bytes, std::min(ld, 16), 4).total > 227 * 1024)
     wmax = 8;
   if constexpr (sizeof(T) == 4) {
-    // FP32, default: the register-staged kernel, 8 columns per pass (4 for the last pass of an ld = 4 mod 8)
+    // FP32, default: the register-staged kernel, up to 32 columns per launch (every element matrix read once)
     if (pipe_ok && ctx->patch_kernel == 1 && P.max_elems <= kRegMaxThreads) {
-      for (int col0 = 0; col0 < ld; col0 += 8) {
-        const int W = std::min(8, ld - col0);
+      for (int col0 = 0; col0 < ld;) {
+        int W = std::min(32, ld - col0);
         int launched = 0;
         MK_TRY(launch_reg(ctx, m, Ae, x, y, halo, col0, W, ld, mask, s, &launched));
+        if (!launched && W > 8) {  // the wide block's x rows do not fit: 8 columns per launch
+          W = 8;
+          MK_TRY(launch_reg(ctx, m, Ae, x, y, halo, col0, W, ld, mask, s, &launched));
+        }
         if (!launched) return fail(MK_ERR_UNSUPPORTED, "patch operator: register-staged kernel does not fit");
         MK_TRY(halo_pass<T>(ctx, m, halo, y, mask, W / 4, 4, col0, ld, s));
+        col0 += W;
       }
       MK_CUDA(cudaGetLastError());
       return MK_OK;

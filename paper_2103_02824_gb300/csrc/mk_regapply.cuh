@@ -38,7 +38,8 @@ __host__ __device__ inline RegSmem reg_smem(int nloc, int pe, int max_nodes, int
 // would all hit one 16-byte bank group.
 __device__ __forceinline__ int ye_row(int r) { return r ^ ((r >> 3) & 7); }
 
-// Columns [col0, col0 + W) of y = A x for patch p (elements [p pe, p pe + ne), one per thread; W in {4, 8}).
+// Columns [col0, col0 + W) of y = A x for patch p (elements [p pe, p pe + ne), one per thread; W a multiple of 4,
+// at most WMAX in {8, 32}: the element matrices are read once for all W columns).
 // The record of patch p sits at rec + p * rec_stride (every record padded to that stride): the header {e0, ne, n0,
 // nl, off_pos, off_ioff, off_tgt, off_gid}, the local connectivity (uint16, at byte kRecHeader), the incidence
 // place of each (element, slot) (uint16), the start of each local node's run (uint16), the node targets (int32)
@@ -46,18 +47,18 @@ __device__ __forceinline__ int ye_row(int r) { return r ^ ((r >> 3) & 7); }
 // out together (neither needs an earlier load), then the x rows, whose ids come with the record.  Products and
 // node sums then run in passes of 4 columns, from shared memory only.  A record whose header is out of range sets
 // MK_FAULT_PATCH_RECORD and the CTA writes nothing.
-template <int NLOC, int W>
+template <int NLOC, int WMAX>
 __device__ __forceinline__ void patch_apply_reg(int p, const unsigned char* __restrict__ rec, int rec_stride,
                                                 const float* __restrict__ Ae, int mask, const float* __restrict__ x,
-                                                float* __restrict__ y, float* __restrict__ halo, int col0, int ld,
-                                                int pe, int max_nodes, int64_t n_nodes, int64_t n_elems,
+                                                float* __restrict__ y, float* __restrict__ halo, int col0, int W,
+                                                int ld, int pe, int max_nodes, int64_t n_nodes, int64_t n_elems,
                                                 int* __restrict__ fault, unsigned char* __restrict__ smraw) {
   constexpr int NPS = padded_np(NLOC, 4);
   constexpr int NV = NPS / 4;  // 16-byte vectors per element matrix
-  constexpr int XCH = W / 4;   // 16-byte chunks of an x row
-  static_assert(W == 4 || W == 8, "column pass");
-  constexpr int XS = reg_xs_stride(W);  // x row stride (floats): 48 bytes for W = 8, so gathers spread over banks
-  const RegSmem lay = reg_smem(NLOC, pe, max_nodes, rec_stride, W);
+  static_assert(WMAX == 8 || WMAX == 32, "column block");
+  const int XCH = W / 4;       // 16-byte chunks of an x row
+  constexpr int XS = reg_xs_stride(WMAX);  // x row stride (floats): 48 bytes for WMAX = 8, so gathers spread over banks
+  const RegSmem lay = reg_smem(NLOC, pe, max_nodes, rec_stride, WMAX);
   unsigned char* Rs = smraw + lay.rec;
   float* Xs = reinterpret_cast<float*>(smraw + lay.xs);
   float* Ye = reinterpret_cast<float*>(smraw + lay.ye);
@@ -114,8 +115,9 @@ __device__ __forceinline__ void patch_apply_reg(int p, const unsigned char* __re
   cp_async_wait_all();
   __syncthreads();
   // (3) per pass of 4 columns: element products (two columns at a time), then the node sums
-#pragma unroll
-  for (int pass = 0; pass < W / 4; ++pass) {
+  const int npass = W / 4;
+#pragma unroll 2
+  for (int pass = 0; pass < npass; ++pass) {
     if (mine) {
 #pragma unroll
       for (int c = 0; c < 4; c += 2) {
@@ -171,7 +173,7 @@ __device__ __forceinline__ void patch_apply_reg(int p, const unsigned char* __re
         stv<float, 4>(halo + (int64_t)(-tg - 1) * ld + cc, acc);
       }
     }
-    if (pass + 1 < W / 4) __syncthreads();  // the next pass rewrites the products
+    if (pass + 1 < npass) __syncthreads();  // the next pass rewrites the products
   }
 }
 

@@ -138,6 +138,8 @@ _SIGS = {
     "mk_error_indicators": [_vp, _vp, C.POINTER(mk_molecule), _vp, C.c_int, C.c_int, C.POINTER(C.c_double), _vp,
                             _vp, _vp],
     "mk_dorfler_mark": [_vp, C.c_int64, _vp, C.c_double, _vp, C.POINTER(C.c_int64), C.POINTER(C.c_double), _vp],
+    "mk_refine": [_vp, C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, _vp, C.c_int64, C.c_int64, C.POINTER(C.c_int64),
+                  C.POINTER(C.c_int64), C.POINTER(C.c_int), _vp],
     "mk_mlp_param_count": [C.c_int],
     "mk_mlp_create": [_vp, C.c_int, C.POINTER(C.c_float), C.POINTER(_vp)],
     "mk_mlp_destroy": [_vp],
@@ -539,6 +541,38 @@ def mk_dorfler_mark(ctx, eta2, theta, marked, stream=None):
     _check(lib().mk_dorfler_mark(ctx.h, int(eta2.numel()), _ptr(eta2), float(theta), _ptr(marked), C.byref(nm),
                                  C.byref(th), _stream(stream)))
     return nm.value, th.value
+
+
+def mk_refine(ctx, coords, tets, tags, parent, marked, n_vertices, n_elems, stream=None):
+    """Newest-vertex bisection of the marked elements with closure, in place in the device buffers coords
+    [max_v, 3] float64, tets [max_e, 4] int32, tags [max_e] int8, parent [max_e] int32 (marked [n_elems] uint8);
+    returns (n_vertices, n_elems, rounds)."""
+    nv, ne, r = C.c_int64(), C.c_int64(), C.c_int()
+    _check(lib().mk_refine(ctx.h, int(n_vertices), int(n_elems), _ptr(coords), _ptr(tets), _ptr(tags), _ptr(parent),
+                           _ptr(marked), int(coords.shape[0]), int(tets.shape[0]), C.byref(nv), C.byref(ne),
+                           C.byref(r), _stream(stream)))
+    return nv.value, ne.value, r.value
+
+
+def refine_mesh(ctx, X, T, K, marked, max_vertices=None, max_elems=None):
+    """Host arrays in and out around mk_refine (X [nv, 3], T [E, 4] in bisection order, K [E], marked [E] bool):
+    returns (X', T', K', parent, rounds)."""
+    import torch
+    nv, E = X.shape[0], T.shape[0]
+    max_v = max_vertices or 4 * nv + 1024
+    max_e = max_elems or 8 * E + 1024
+    dev = torch.device("cuda")
+    Xd = torch.zeros((max_v, 3), dtype=torch.float64, device=dev)
+    Xd[:nv] = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float64)).to(dev)
+    Td = torch.zeros((max_e, 4), dtype=torch.int32, device=dev)
+    Td[:E] = torch.from_numpy(np.ascontiguousarray(T, dtype=np.int32)).to(dev)
+    Kd = torch.zeros(max_e, dtype=torch.int8, device=dev)
+    Kd[:E] = torch.from_numpy(np.ascontiguousarray(K, dtype=np.int8)).to(dev)
+    Pd = torch.zeros(max_e, dtype=torch.int32, device=dev)
+    Md = torch.from_numpy(np.ascontiguousarray(marked, dtype=np.uint8)).to(dev)
+    nv2, E2, r = mk_refine(ctx, Xd, Td, Kd, Pd, Md, nv, E)
+    torch.cuda.synchronize()
+    return (Xd[:nv2].cpu().numpy(), Td[:E2].cpu().numpy(), Kd[:E2].cpu().numpy(), Pd[:E2].cpu().numpy(), r)
 
 
 def mk_batch_correction_solve(ctx, meshes, mols, sigmas, rhs_list, x_list, Ns, opt=None, stream=None, allow=()):

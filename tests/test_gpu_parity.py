@@ -463,7 +463,8 @@ def test_assemble_rhs_in_two_halves(ctx, torch, name):
 def test_pipelined_patch_kernel_matches_single_patch_kernel(ctx, torch, name, pe):
     """The patch kernels -- the FP32 register-staged kernel, the persistent two-group pipelined kernel and the
     one-patch-per-CTA kernel -- sum in the same order, so they agree bitwise, FP32 and FP64, for every column width
-    (ld = 12 takes a pass of 8 columns and one of 4); an ld that is not a multiple of 16 bytes takes the
+    (the register-staged kernel takes up to 32 columns per launch: ld = 12, 28 and 40 exercise its wide block and
+    its remainder); an ld that is not a multiple of 16 bytes takes the
     single-patch kernel, still against the oracle.  Patch sizes 32 and 128, more patches than resident CTAs.
     Meshes with more patches than resident CTAs, so that CTAs loop over several patches."""
     from oracle.correction import Level
@@ -478,7 +479,7 @@ def test_pipelined_patch_kernel_matches_single_patch_kernel(ctx, torch, name, pe
         mol = mk.Molecule(wl["Z"], wl["R"])
         n = m.info["n_nodes"]
         A = lv.operator(sigma)
-        for ld in (4, 8, 12, 16, 6):
+        for ld in (4, 8, 12, 16, 28, 40, 6):
             X = np.random.default_rng(ld).standard_normal((n, ld))
             X[lv.fine.boundary] = 0.0
             ref = np.zeros((n, ld))
