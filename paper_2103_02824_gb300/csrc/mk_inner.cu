@@ -59,6 +59,7 @@ struct mk_inner {
 namespace mk {
 
 constexpr int kInThreads = 256;
+constexpr int kInChunks = 16;  // CTAs per coarse element in the tensor precomputation
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   sh[threadIdx.x] = v;
@@ -133,20 +134,22 @@ __global__ void __launch_bounds__(kInThreads) k_in_tensors(const int32_t* __rest
                                                            const Geom* __restrict__ cgeom,
                                                            const RefTables* __restrict__ ref,
                                                            const double* __restrict__ phit, int ld, int N,
-                                                           const double* __restrict__ w0, int64_t Ec,
-                                                           double* __restrict__ Tc, double* __restrict__ Ah4,
-                                                           double* __restrict__ rc, double* __restrict__ g3p) {
+                                                           const double* __restrict__ w0, int nchunk,
+                                                           double* __restrict__ part) {
   constexpr int NL2 = NLOC * NLOC, NL3 = NL2 * NLOC;
   __shared__ double ps[kQ][NLOC];
   __shared__ double wd[kQ], wq[kQ];
   __shared__ double ph[kQ][MK_MAX_RHS];
   extern __shared__ double acc[];
-  const int T = blockIdx.x;
+  // block = (coarse element T, chunk ch of its children); the chunks' partial sums are added in chunk order later
+  const int T = blockIdx.x / nchunk, ch = blockIdx.x % nchunk;
   const Geom cg = cgeom[T];
   const int K = in_tensor_count(NLOC, N);
   for (int t = threadIdx.x; t < K; t += blockDim.x) acc[t] = 0.0;
+  const int c0 = child_off[T], len = child_off[T + 1] - c0;
+  const int kb = c0 + (int)((int64_t)len * ch / nchunk), ke = c0 + (int)((int64_t)len * (ch + 1) / nchunk);
 #pragma unroll 1
-  for (int k = child_off[T]; k < child_off[T + 1]; ++k) {
+  for (int k = kb; k < ke; ++k) {
     const int64_t e = child[k];
     if ((int)threadIdx.x < kQ) {
       const Geom g = fgeom[e];
@@ -190,19 +193,33 @@ __global__ void __launch_bounds__(kInThreads) k_in_tensors(const int32_t* __rest
     }
     __syncthreads();
   }
-  for (int t0 = threadIdx.x; t0 < K; t0 += blockDim.x) {
-    int t = t0;
-    if (t < NL3) {
-      Tc[(int64_t)T * NL3 + t] = acc[t0];
-    } else if ((t -= NL3) < N * NL2) {
-      const int i = t / NL2;
-      Ah4[((int64_t)i * Ec + T) * NL2 + (t - i * NL2)] = acc[t0];
-    } else if ((t -= N * NL2) < N * NLOC) {
-      const int i = t / NLOC;
-      rc[((int64_t)i * Ec + T) * NLOC + (t - i * NLOC)] = acc[t0];
-    } else {
-      g3p[(int64_t)T * N + (t - N * NLOC)] = acc[t0];
-    }
+  for (int t0 = threadIdx.x; t0 < K; t0 += blockDim.x) part[(int64_t)blockIdx.x * K + t0] = acc[t0];
+}
+
+// the chunks of every coarse element summed in chunk order, into the tensors' layouts:
+//   Tc[T][a][b][c], Ah4[i][T][a][b], rc[i][T][a], g3p[T][i]
+template <int NLOC>
+__global__ void k_in_tensor_reduce(int64_t Ec, int N, int nchunk, const double* __restrict__ part,
+                                   double* __restrict__ Tc, double* __restrict__ Ah4, double* __restrict__ rc,
+                                   double* __restrict__ g3p) {
+  constexpr int NL2 = NLOC * NLOC, NL3 = NL2 * NLOC;
+  const int K = in_tensor_count(NLOC, N);
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= Ec * K) return;
+  const int64_t T = g / K;
+  int t = (int)(g - T * K);
+  double v = 0.0;
+  for (int c = 0; c < nchunk; ++c) v += part[(T * nchunk + c) * K + t];
+  if (t < NL3) {
+    Tc[T * NL3 + t] = v;
+  } else if ((t -= NL3) < N * NL2) {
+    const int i = t / NL2;
+    Ah4[((int64_t)i * Ec + T) * NL2 + (t - i * NL2)] = v;
+  } else if ((t -= N * NL2) < N * NLOC) {
+    const int i = t / NLOC;
+    rc[((int64_t)i * Ec + T) * NLOC + (t - i * NLOC)] = v;
+  } else {
+    g3p[T * N + (t - N * NLOC)] = v;
   }
 }
 
@@ -597,16 +614,26 @@ int mk_inner_create(mk_ctx* ctx, const mk_mesh* m, const mk_molecule* mol, const
   MK_COUNT(), k_in_ltl<<<blocks_for((int64_t)NH * NH), 256, 0, s>>>(NH, Li, h->CHinv);
   MK_COUNT(), k_in_gemv<<<blocks_for((int64_t)NH * 32), 256, 0, s>>>(NH, h->CHinv, dvec, h->y);
   MK_COUNT(), k_in_dot<<<1, kInThreads, 0, s>>>(NH, dvec, h->y, h->sc + IS_DY);
-  // the coarse-element tensors and their assembled parts
+  // the coarse-element tensors and their assembled parts: kInChunks CTAs per coarse element, then the chunks
+  // summed in order
+  const int K = in_tensor_count(nl, N);
+  double* tpart = (double*)scratch(ctx, S_EIG5, (size_t)Ec * kInChunks * K * sizeof(double), &err);
+  if (!tpart) return bail(err);
+  const int tgrid = (int)(Ec * kInChunks);
   if (nl == 4) {
     MK_CUDA(cudaFuncSetAttribute(k_in_tensors<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc_bytes));
-    MK_COUNT(), k_in_tensors<4><<<(int)Ec, kInThreads, acc_bytes, s>>>(m->d_child_off, m->d_child, F.d_geom, F.d_elem, C.d_geom,
-                                                             ref, phit, ld, N, h->w0, Ec, h->Tc, h->Ah4, rc, g3p);
+    MK_COUNT(), k_in_tensors<4><<<tgrid, kInThreads, acc_bytes, s>>>(m->d_child_off, m->d_child, F.d_geom, F.d_elem,
+                                                                    C.d_geom, ref, phit, ld, N, h->w0, kInChunks,
+                                                                    tpart);
+    MK_COUNT(), k_in_tensor_reduce<4><<<blocks_for(Ec * K), 256, 0, s>>>(Ec, N, kInChunks, tpart, h->Tc, h->Ah4, rc,
+                                                                         g3p);
   } else {
     MK_CUDA(cudaFuncSetAttribute(k_in_tensors<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc_bytes));
-    MK_COUNT(), k_in_tensors<10><<<(int)Ec, kInThreads, acc_bytes, s>>>(m->d_child_off, m->d_child, F.d_geom,
-                                                                      F.d_elem, C.d_geom, ref, phit, ld, N, h->w0,
-                                                                      Ec, h->Tc, h->Ah4, rc, g3p);
+    MK_COUNT(), k_in_tensors<10><<<tgrid, kInThreads, acc_bytes, s>>>(m->d_child_off, m->d_child, F.d_geom, F.d_elem,
+                                                                     C.d_geom, ref, phit, ld, N, h->w0, kInChunks,
+                                                                     tpart);
+    MK_COUNT(), k_in_tensor_reduce<10><<<blocks_for(Ec * K), 256, 0, s>>>(Ec, N, kInChunks, tpart, h->Tc, h->Ah4,
+                                                                          rc, g3p);
   }
   MK_CUDA(cudaMemsetAsync(h->rvec, 0, NHN * sizeof(double), s));
   for (int col = 0; col < C.n_colours; ++col) {
