@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--patch-kernel", default="reg", choices=["reg", "pipelined", "single"],
                     help="--mode apply: the FP32 register-staged kernel (default), the two-group pipelined kernel, "
                          "or the one-patch-per-CTA kernel")
-    ap.add_argument("--mode", default="step", choices=["step", "apply", "learned", "stiffness", "decompose"],
+    ap.add_argument("--mode", default="step", choices=["step", "apply", "learned", "stiffness", "decompose", "serve"],
                     help="apply: time the FP32 element-by-element operator alone (kernel-level roofline); "
                          "learned: the learned preconditioner (BF16 network) alone; stiffness: the matrix-free "
                          "Poisson operator K alone (one column); decompose: the warm coarse decomposition of the "
@@ -363,6 +363,93 @@ def train_network(ctx, order, seeds=TRAIN_SEEDS, steps=1500, batch=8192):
                  "loss_last50": float(np.mean(hist[-50:])), "train_s": time.perf_counter() - t0}
 
 
+# the serving sweep: 32 molecules (seeds 5000-5031, 1-16 nuclei), each on its own uniform mesh chosen log-uniformly
+# between about 50k and 900k free DOF, every orbital's correction problem solved
+SERVE_MESHES = ((5, 2), (6, 2), (4, 3), (5, 3), (6, 3))   # (coarse cubes per side, levels): 20^3 .. 48^3 fine cubes
+
+
+def serve_mode(a):
+    """The correction solves (A4) of 32 molecules of uneven size in shared launches (the batched solve, orbitals in
+    blocks of at most 16 columns per problem, every block of a molecule on the same mesh and shift) against the same
+    solves one molecule after another (mixed precision, and plain FP64 PCG), and the molecules' Hartree Poisson solves
+    (A2, multigrid, one after another).  Inputs: each molecule's coarse ground state of the bare Hamiltonian, its
+    shift, the Hartree potential of its coarse density and its right-hand sides (setup, untimed)."""
+    import numpy as np
+    import torch
+    from paper_2103_02824_gb300 import build, learned, mk, synth
+    from paper_2103_02824_gb300.step import upload_workload
+    build.build()
+    ctx = mk.Context(0)
+    mols, meshes, probs = [], [], []
+    t0 = time.perf_counter()
+    for k in range(32):
+        rng = np.random.default_rng(5000 + k)
+        n_nuc = int(rng.integers(1, 17))
+        target = float(np.exp(rng.uniform(np.log(5e4), np.log(1.5e6))))
+        dofs = [(2 * nc * 2 ** lv - 1) ** 3 for nc, lv in SERVE_MESHES]
+        nc, lv = SERVE_MESHES[int(np.argmin([abs(np.log(d / target)) for d in dofs]))]
+        Z, R = synth.molecule(5000 + k, n_nuc)
+        wl = dict(name=f"serve{k}", Z=Z, R=R, order=2, half=15.0, n_coarse=nc, levels=lv, xc="lda")
+        mesh, _ = upload_workload(ctx, wl)
+        meshes.append(mesh)
+        probs.append(learned.Problem(ctx, mesh, Z, R))
+        mols.append(dict(seed=5000 + k, nuclei=n_nuc, N=probs[-1].N, free_dof=mesh.info["n_free"]))
+    setup_s = time.perf_counter() - t0
+    units = sum(float(p.mesh.info["n_free"]) * p.N for p in probs)
+    # orbital blocks of <= 16 columns: one batch problem each
+    blocks = []
+    for p in probs:
+        for c0 in range(0, p.N, 16):
+            nb = min(16, p.N - c0)
+            ldb = 4 if nb <= 4 else 8 if nb <= 8 else 16
+            rb = torch.zeros((p.u.shape[0], ldb), dtype=torch.float64, device="cuda")
+            rb[:, :nb] = p.rhs[:, c0:c0 + nb]
+            xb = torch.zeros_like(rb)
+            xb[:, :nb] = p.u[:, c0:c0 + nb]
+            blocks.append((p, rb, xb, nb))
+    bopt = mk.opts(precision="mixed", rtol=1e-8, check_every=10)
+    fopt = mk.opts(precision="fp64", rtol=1e-8)
+
+    def batched():
+        xs = [xb.clone() for (_, _, xb, _) in blocks]
+        return mk.mk_batch_correction_solve(ctx, [p.mesh for (p, _, _, _) in blocks], [p.mol for (p, _, _, _) in blocks],
+                                            [p.sigma for (p, _, _, _) in blocks], [rb for (_, rb, _, _) in blocks], xs,
+                                            [nb for (_, _, _, nb) in blocks], opt=bopt)
+
+    def timed(fn, reps=2):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+
+    ms_b, reps_b = timed(batched)
+    ms_m, _ = timed(lambda: [p.solve(bopt) for p in probs])
+    ms_f, reps_f = timed(lambda: [p.solve(fopt) for p in probs], reps=1)
+    # the Hartree Poisson solves, multigrid, one molecule after another
+    occs = [synth.occupations(p.Z) for p in probs]
+    ws = [torch.zeros(p.u.shape[0], dtype=torch.float64, device="cuda") for p in probs]
+    popt = mk.opts(precision="mixed", rtol=1e-8, check_every=10, coarse="multigrid")
+    ms_p, _ = timed(lambda: [mk.mk_hartree_poisson(ctx, p.mesh, p.u, o, p.N, w, opt=popt)
+                             for p, o, w in zip(probs, occs, ws)])
+    line = {"mode": "serve", "molecules": len(probs), "batch_problems": len(blocks),
+            "orbitals": [m["N"] for m in mols], "free_dof": [m["free_dof"] for m in mols],
+            "unit": UNIT, "dof_orbitals": units, "setup_s": setup_s,
+            "correction_solves_batched_ms": ms_b, "value_batched": units / (ms_b * 1e-3),
+            "correction_solves_sequential_mixed_ms": ms_m, "value_sequential_mixed": units / (ms_m * 1e-3),
+            "correction_solves_sequential_fp64_ms": ms_f, "value_sequential_fp64": units / (ms_f * 1e-3),
+            "max_rel_residual_batched": max(r["max_rel_residual"] for r in reps_b),
+            "hartree_solves_sequential_multigrid_ms": ms_p,
+            "note": "A4 batched; the A2 Poisson solves run one after another (not batched)"}
+    print(json.dumps(line))
+    for m in meshes:
+        m.close()
+
+
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -376,6 +463,8 @@ def main():
         return learned_mode(a)
     if a.mode == "stiffness":
         return stiffness_mode(a)
+    if a.mode == "serve":
+        return serve_mode(a)
     if a.mode == "decompose":
         return decompose_mode(a)
     import numpy as np
