@@ -370,7 +370,7 @@ SERVE_MESHES = ((5, 2), (6, 2), (4, 3), (5, 3), (6, 3))   # (coarse cubes per si
 
 def serve_mode(a):
     """The correction solves (A4) of 32 molecules of uneven size in shared launches (the batched solve, orbitals in
-    blocks of at most 16 columns per problem, every block of a molecule on the same mesh and shift) against the same
+    blocks of at most 32 columns per problem, every block of a molecule on the same mesh and shift) against the same
     solves one molecule after another (mixed precision, and plain FP64 PCG), and the molecules' Hartree Poisson solves
     (A2, multigrid, one after another).  Inputs: each molecule's coarse ground state of the bare Hamiltonian, its
     shift, the Hartree potential of its coarse density and its right-hand sides (setup, untimed)."""
@@ -396,12 +396,12 @@ def serve_mode(a):
         mols.append(dict(seed=5000 + k, nuclei=n_nuc, N=probs[-1].N, free_dof=mesh.info["n_free"]))
     setup_s = time.perf_counter() - t0
     units = sum(float(p.mesh.info["n_free"]) * p.N for p in probs)
-    # orbital blocks of <= 16 columns: one batch problem each
+    # orbital blocks of <= 32 columns: one batch problem each
     blocks = []
     for p in probs:
-        for c0 in range(0, p.N, 16):
-            nb = min(16, p.N - c0)
-            ldb = 4 if nb <= 4 else 8 if nb <= 8 else 16
+        for c0 in range(0, p.N, 32):
+            nb = min(32, p.N - c0)
+            ldb = 4 if nb <= 4 else 8 if nb <= 8 else 16 if nb <= 16 else 32
             rb = torch.zeros((p.u.shape[0], ldb), dtype=torch.float64, device="cuda")
             rb[:, :nb] = p.rhs[:, c0:c0 + nb]
             xb = torch.zeros_like(rb)

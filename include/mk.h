@@ -467,8 +467,11 @@ int mk_correction_shift(mk_ctx* ctx, const mk_mesh* mesh, const mk_molecule* mol
  * [n_nodes_k * ld[k]], columns < N[k]), as mk_correction_solve with *opts (MK_PREC_MIXED, Jacobi, no coarse
  * correction).  The FP64 residual refinement runs per problem; every inner FP32 PCG iteration runs as seven kernel
  * launches for the whole batch (one grid over the element patches of all meshes, the halo sums, the dot products
- * and updates of all problems), replayed from one CUDA graph per chunk of opts->check_every iterations.  All meshes
- * must use the same element order; ld[k] in {4, 8, 16}; K <= MK_MAX_BATCH.  reports[k] (host) is filled for every
+ * and updates of all problems), replayed from one CUDA graph per chunk of opts->check_every iterations; the operator
+ * is the register-staged kernel of the single solve (every element matrix read once for all of a problem's
+ * columns), or the one-patch-per-CTA kernel where the meshes have no patch records or MK_OPT_PATCH_PIPELINE is not
+ * 1.  All meshes must use the same element order; ld[k] in {4, 8, 16, 32} (32 only with the register-staged
+ * kernel); K <= MK_MAX_BATCH.  reports[k] (host) is filled for every
  * problem.  Each problem's result is bit-identical to mk_correction_solve's with the same options (same kernels,
  * same summation orders; a converged problem idles while others iterate).  Returns MK_ERR_NOT_CONVERGED or
  * MK_ERR_BREAKDOWN if any problem did (see the reports).  Synchronises the stream. */

@@ -1702,6 +1702,8 @@ extern "C" int mk_operator_apply(mk_ctx* ctx, const mk_mesh* m, const mk_molecul
 // kernel body is the single-problem one, so each problem's arithmetic is exactly that of its own solve.
 namespace mk {
 
+constexpr int kBatchCols = 32;  // columns a batched problem may have (its per-column scalars)
+
 struct BatchProb {
   // patch operator
   const int32_t *elem_off, *node_off, *conn, *target, *inc_off, *shared_node, *shared_off;
@@ -1709,14 +1711,23 @@ struct BatchProb {
   const uint8_t* bnd;
   const float* A32;
   float* halo;
-  int64_t n_shared, n;
+  int64_t n_shared, n, n_elems;
   int pe, max_nodes, first_block, ld, N;
+  const unsigned char* rec;  // patch records (the register-staged operator)
+  int rec_stride;
   // PCG state
   const float* dinv;
   float *r, *p, *q, *d;
   MixState* st;
   double* part;
 };
+
+// whether any column of problem P is still iterating (the same value for every thread of a CTA)
+__device__ __forceinline__ bool batch_active(const BatchProb& P) {
+  bool any = false;
+  for (int j = 0; j < P.N; ++j) any = any || P.st[j].active != 0;
+  return any;
+}
 
 __device__ __forceinline__ int batch_find(const int64_t* __restrict__ off, int K, int64_t t) {
   int lo = 0, hi = K;  // largest k with off[k] <= t
@@ -1732,8 +1743,22 @@ __global__ void __launch_bounds__(256) k_bapply(const BatchProb* __restrict__ pr
   extern __shared__ __align__(16) unsigned char smraw[];
   const int b = blk_prob[blockIdx.x];
   const BatchProb& P = probs[b];
+  if (!batch_active(P)) return;  // a problem whose columns all converged: its q is not read again
   patch_apply<NLOC, float, 4>((int)blockIdx.x - P.first_block, P.elem_off, P.node_off, P.conn, P.A32, P.target,
                               P.inc_off, P.inc, P.bnd, 1, P.p, P.q, P.halo, P.ld / 4, 0, P.ld, P.pe, P.max_nodes, smraw);
+}
+
+// the register-staged operator body (the single solve's default operator) over the patches of all problems
+template <int NLOC>
+__global__ void __launch_bounds__(kRegMaxThreads, 2) k_bapply_reg(const BatchProb* __restrict__ probs,
+                                                                  const int32_t* __restrict__ blk_prob,
+                                                                  int* __restrict__ fault) {
+  extern __shared__ __align__(16) unsigned char smraw_breg[];
+  const int b = blk_prob[blockIdx.x];
+  const BatchProb& P = probs[b];
+  if (!batch_active(P)) return;  // a problem whose columns all converged: its q is not read again
+  patch_apply_reg<NLOC, 32>((int)blockIdx.x - P.first_block, P.rec, P.rec_stride, P.A32, 1, P.p, P.q, P.halo, 0,
+                            P.ld, P.ld, P.pe, P.max_nodes, P.n, P.n_elems, fault, smraw_breg);
 }
 
 __global__ void k_bhalo(const BatchProb* __restrict__ probs, int K, const int64_t* __restrict__ off) {
@@ -1785,7 +1810,8 @@ extern "C" int mk_batch_correction_solve(mk_ctx* ctx, int K, const mk_mesh* cons
   for (int k = 0; k < K; ++k) {
     MK_ARG(meshes[k] && rhs[k] && x[k], "mk_batch_correction_solve: null problem");
     MK_ARG(meshes[k]->fine.nloc == nloc, "mk_batch_correction_solve: all meshes must use one element order");
-    MK_ARG(ld[k] == 4 || ld[k] == 8 || ld[k] == 16, "mk_batch_correction_solve: ld must be 4, 8 or 16");
+    MK_ARG(ld[k] == 4 || ld[k] == 8 || ld[k] == 16 || ld[k] == 32,
+           "mk_batch_correction_solve: ld must be 4, 8, 16 or 32");
     MK_ARG(N[k] >= 1 && N[k] <= ld[k], "mk_batch_correction_solve: bad N");
   }
   MK_CUDA(cudaSetDevice(ctx->device));
@@ -1801,7 +1827,9 @@ extern "C" int mk_batch_correction_solve(mk_ctx* ctx, int K, const mk_mesh* cons
   auto take = [&](size_t bytes) { size_t o2 = off; off += (bytes + 255) / 256 * 256; return o2; };
   std::vector<size_t> oA64(K), oA32(K), oDiag(K), oDinv(K), oAx(K), oR(K), oP(K), oQ(K), oD(K), oH(K), oPart(K);
   int64_t nblocks = 0, hitems = 0, pitems = 0;
-  size_t smem = 0;
+  size_t smem = 0, smem_reg = 0;
+  int th_reg = 32;
+  bool reg_ok = true, wide = false;
   for (int k = 0; k < K; ++k) {
     const Level& L = meshes[k]->fine;
     const Patches& P = meshes[k]->patches;
@@ -1820,20 +1848,29 @@ extern "C" int mk_batch_correction_solve(mk_ctx* ctx, int K, const mk_mesh* cons
     nblocks += P.n_patches;
     hitems += P.n_shared_nodes * (ld[k] / 4);
     pitems += (int64_t)n * ld[k];
-    smem = std::max(smem, patch_smem(nloc, P.max_elems, P.max_nodes, ld[k], 4).total);
+    smem = std::max(smem, patch_smem(nloc, P.max_elems, P.max_nodes, std::min(ld[k], 16), 4).total);
+    smem_reg = std::max(smem_reg, reg_smem(nloc, P.max_elems, P.max_nodes, P.max_rec_bytes, 32).total);
+    th_reg = std::max(th_reg, (P.max_elems + 31) / 32 * 32);
+    reg_ok = reg_ok && P.d_rec != nullptr && P.max_elems <= kRegMaxThreads;
+    wide = wide || ld[k] > 16;
   }
+  // the register-staged operator (one element per thread) when every mesh has patch records and it fits; the
+  // one-patch-per-CTA operator otherwise, at most 16 columns
+  const bool use_reg = reg_ok && ctx->patch_kernel == 1 && smem_reg <= 227 * 1024;
+  MK_ARG(use_reg || !wide, "mk_batch_correction_solve: ld = 32 needs the register-staged operator");
+  if (use_reg) smem = smem_reg;
   MK_ARG(smem <= 227 * 1024, "mk_batch_correction_solve: patch too large for shared memory");
-  const size_t oSt = take((size_t)K * 16 * sizeof(MixState)), oProbs = take((size_t)K * sizeof(BatchProb));
+  const size_t oSt = take((size_t)K * kBatchCols * sizeof(MixState)), oProbs = take((size_t)K * sizeof(BatchProb));
   const size_t oBlk = take((size_t)nblocks * 4), oHoff = take((size_t)(K + 1) * 8), oPoff = take((size_t)(K + 1) * 8);
   int err = MK_OK;
   char* ws = (char*)scratch(ctx, S_BATCH, off, &err);
   if (!ws) return err;
-  if (ctx->pinned_size < (size_t)K * 16 * sizeof(MixState)) {
+  if (ctx->pinned_size < (size_t)K * kBatchCols * sizeof(MixState)) {
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
     ctx->pinned = nullptr;
     ctx->pinned_size = 0;
-    MK_CUDA(cudaMallocHost(&ctx->pinned, (size_t)K * 16 * sizeof(MixState)));
-    ctx->pinned_size = (size_t)K * 16 * sizeof(MixState);
+    MK_CUDA(cudaMallocHost(&ctx->pinned, (size_t)K * kBatchCols * sizeof(MixState)));
+    ctx->pinned_size = (size_t)K * kBatchCols * sizeof(MixState);
   }
   MixState* hst = (MixState*)ctx->pinned;
   MixState* dst = (MixState*)(ws + oSt);
@@ -1861,6 +1898,9 @@ extern "C" int mk_batch_correction_solve(mk_ctx* ctx, int K, const mk_mesh* cons
     B.n = L.n_nodes;
     B.pe = P.max_elems;
     B.max_nodes = P.max_nodes;
+    B.n_elems = L.n_elems;
+    B.rec = P.d_rec;
+    B.rec_stride = P.max_rec_bytes;
     B.first_block = (int)b0;
     B.ld = ld[k];
     B.N = N[k];
@@ -1869,7 +1909,7 @@ extern "C" int mk_batch_correction_solve(mk_ctx* ctx, int K, const mk_mesh* cons
     B.p = (float*)(ws + oP[k]);
     B.q = (float*)(ws + oQ[k]);
     B.d = (float*)(ws + oD[k]);
-    B.st = dst + (size_t)k * 16;
+    B.st = dst + (size_t)k * kBatchCols;
     B.part = (double*)(ws + oPart[k]);
     for (int i = 0; i < P.n_patches; ++i) blk[b0 + i] = k;
     b0 += P.n_patches;
@@ -1884,7 +1924,7 @@ extern "C" int mk_batch_correction_solve(mk_ctx* ctx, int K, const mk_mesh* cons
   MK_CUDA(cudaMemcpyAsync(dblk, blk.data(), (size_t)nblocks * 4, cudaMemcpyHostToDevice, s));
   MK_CUDA(cudaMemcpyAsync(dhoff, hoff.data(), (size_t)(K + 1) * 8, cudaMemcpyHostToDevice, s));
   MK_CUDA(cudaMemcpyAsync(dpoff, poff.data(), (size_t)(K + 1) * 8, cudaMemcpyHostToDevice, s));
-  MK_CUDA(cudaMemsetAsync(dst, 0, (size_t)K * 16 * sizeof(MixState), s));
+  MK_CUDA(cudaMemsetAsync(dst, 0, (size_t)K * kBatchCols * sizeof(MixState), s));
   MK_CUDA(cudaStreamSynchronize(s));  // the host tables above may go out of scope only after the copies
   // per problem: operator K/2 + M_Vext + sigma M (FP64 element matrices, FP32 patch copy), Jacobi diagonal
   for (int k = 0; k < K; ++k) {
@@ -1901,14 +1941,24 @@ extern "C" int mk_batch_correction_solve(mk_ctx* ctx, int K, const mk_mesh* cons
     MK_COUNT(), k_zero_boundary<<<(int)((L.n_nodes * ld[k] + 255) / 256), 256, 0, s>>>(L.n_nodes, L.d_boundary, x[k],
                                                                                          ld[k]);
   }
-  if (nloc == 4) MK_CUDA(cudaFuncSetAttribute(k_bapply<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  else MK_CUDA(cudaFuncSetAttribute(k_bapply<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (use_reg) {
+    if (nloc == 4) MK_CUDA(cudaFuncSetAttribute(k_bapply_reg<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    else MK_CUDA(cudaFuncSetAttribute(k_bapply_reg<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  } else {
+    if (nloc == 4) MK_CUDA(cudaFuncSetAttribute(k_bapply<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    else MK_CUDA(cudaFuncSetAttribute(k_bapply<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }
   const int check = std::max(1, o.check_every);
   const double inner2 = o.inner_rtol * o.inner_rtol;
   const int max_refine = o.max_refine > 0 ? o.max_refine : 20;
   auto iteration = [&]() -> int {  // one inner PCG iteration of every problem
-    if (nloc == 4) MK_COUNT(), k_bapply<4><<<(int)nblocks, 256, smem, s>>>(dprobs, dblk);
-    else MK_COUNT(), k_bapply<10><<<(int)nblocks, 256, smem, s>>>(dprobs, dblk);
+    if (use_reg) {
+      if (nloc == 4) MK_COUNT(), k_bapply_reg<4><<<(int)nblocks, th_reg, smem, s>>>(dprobs, dblk, ctx->d_fault);
+      else MK_COUNT(), k_bapply_reg<10><<<(int)nblocks, th_reg, smem, s>>>(dprobs, dblk, ctx->d_fault);
+    } else {
+      if (nloc == 4) MK_COUNT(), k_bapply<4><<<(int)nblocks, 256, smem, s>>>(dprobs, dblk);
+      else MK_COUNT(), k_bapply<10><<<(int)nblocks, 256, smem, s>>>(dprobs, dblk);
+    }
     if (hitems > 0) MK_COUNT(), k_bhalo<<<(int)((hitems + 255) / 256), 256, 0, s>>>(dprobs, K, dhoff);
     MK_COUNT(), k_bpq<<<dim3(nblk, K), 256, 0, s>>>(dprobs);
     MK_COUNT(), k_bfinalize<<<K, kFinThreads, 0, s>>>(2, dprobs, nblk, 1, o.rtol, inner2);
@@ -1931,12 +1981,12 @@ extern "C" int mk_batch_correction_solve(mk_ctx* ctx, int K, const mk_mesh* cons
                                                          N[k], ld[k], B.part, FinArgs{});
       MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(0, B.part, nblk, 2, ld[k], N[k], B.st, o.rtol, inner2);
     }
-    MK_CUDA(cudaMemcpyAsync(hst, dst, (size_t)K * 16 * sizeof(MixState), cudaMemcpyDeviceToHost, s));
+    MK_CUDA(cudaMemcpyAsync(hst, dst, (size_t)K * kBatchCols * sizeof(MixState), cudaMemcpyDeviceToHost, s));
     MK_CUDA(cudaStreamSynchronize(s));
     bool any = false;
     for (int k = 0; k < K; ++k) {
       bool a = false;
-      for (int j = 0; j < N[k]; ++j) a |= hst[k * 16 + j].outer_active != 0;
+      for (int j = 0; j < N[k]; ++j) a |= hst[k * kBatchCols + j].outer_active != 0;
       conv[k] = !a;
       any |= a;
     }
@@ -1971,13 +2021,13 @@ extern "C" int mk_batch_correction_solve(mk_ctx* ctx, int K, const mk_mesh* cons
         for (int c = 0; c < kk; ++c) MK_TRY(iteration());
       }
       total_it += kk;
-      MK_CUDA(cudaMemcpyAsync(hst, dst, (size_t)K * 16 * sizeof(MixState), cudaMemcpyDeviceToHost, s));
+      MK_CUDA(cudaMemcpyAsync(hst, dst, (size_t)K * kBatchCols * sizeof(MixState), cudaMemcpyDeviceToHost, s));
       MK_CUDA(cudaStreamSynchronize(s));
       inner_active = false;
       for (int k = 0; k < K; ++k)
         for (int j = 0; j < N[k]; ++j) {
-          inner_active |= hst[k * 16 + j].active != 0;
-          if (hst[k * 16 + j].breakdown) status = MK_ERR_BREAKDOWN;
+          inner_active |= hst[k * kBatchCols + j].active != 0;
+          if (hst[k * kBatchCols + j].breakdown) status = MK_ERR_BREAKDOWN;
         }
       if (status == MK_ERR_BREAKDOWN) break;
     }
@@ -1999,7 +2049,7 @@ extern "C" int mk_batch_correction_solve(mk_ctx* ctx, int K, const mk_mesh* cons
     double mx = 0.0;
     int its = 0;
     for (int j = 0; j < N[k]; ++j) {
-      const MixState& c = hst[k * 16 + j];
+      const MixState& c = hst[k * kBatchCols + j];
       R.iters[j] = c.iters;
       R.rel_residual[j] = std::sqrt(c.rr64) / c.bn;
       mx = std::max(mx, R.rel_residual[j]);

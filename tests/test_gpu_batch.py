@@ -51,6 +51,36 @@ def test_batch_matches_single_solves(env, torch):
     print("\nbatched problems: N", [p.N for p in probs], "inner iterations", [r["iterations"] for r in reps])
 
 
+def test_batch_with_32_columns_matches_single_solves(env, torch):
+    """A 22-orbital molecule in a 32-column problem beside a narrow one: one register-staged launch covers all 32
+    columns, and the results are bit-identical to the single solves."""
+    from paper_2103_02824_gb300 import learned, mk, synth
+    ctx, small, mid = env
+    wide = learned.Problem(ctx, small[0], *synth.molecule(2002, 8))
+    narrow = learned.Problem(ctx, small[1], *synth.molecule(3, 4))
+    assert 16 < wide.N <= 32
+
+    def padded(t, ld):
+        out = torch.zeros((t.shape[0], ld), dtype=t.dtype, device=t.device)
+        out[:, :t.shape[1]] = t
+        return out
+    rhs = [padded(wide.rhs, 32), narrow.rhs]
+    x0 = [padded(wide.u, 32), narrow.u]
+    opt = mk.opts(precision="mixed", rtol=1e-10, inner_rtol=1e-4, check_every=5)
+    singles = []
+    for p, r, x in zip((wide, narrow), rhs, x0):
+        xs = x.clone()
+        rep = mk.mk_correction_solve(ctx, p.mesh, p.mol, p.sigma, r, xs, p.N, opt=opt)
+        assert rep["max_rel_residual"] <= 1e-10
+        singles.append(xs)
+    xb = [x.clone() for x in x0]
+    reps = mk.mk_batch_correction_solve(ctx, [wide.mesh, narrow.mesh], [wide.mol, narrow.mol],
+                                        [wide.sigma, narrow.sigma], rhs, xb, [wide.N, narrow.N], opt=opt)
+    torch.cuda.synchronize()
+    for x, y, r in zip(singles, xb, reps):
+        assert r["max_rel_residual"] <= 1e-10 and torch.equal(x, y), float((x - y).abs().max())
+
+
 def test_autotune_patches(env, torch):
     from paper_2103_02824_gb300 import mk, synth
     ctx, small, mid = env
