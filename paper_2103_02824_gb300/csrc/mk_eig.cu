@@ -674,7 +674,28 @@ __device__ __forceinline__ double warp_secular(int m, const double* __restrict__
   return __shfl_sync(0xffffffffu, f, 0) + (alpha - (origin + delta));
 }
 
-// Phase 2, one warp per root: bisection on the offset from the nearer pole, then the root's score.
+// The secular function and its derivative at origin + delta (warp-wide sums, the same values on every lane):
+// f = sum_t z_t^2 / (mu - d_t) + alpha - mu,  f' = -sum_t z_t^2 / (mu - d_t)^2 - 1 < 0.
+__device__ __forceinline__ void warp_secular_d(int m, const double* __restrict__ dk, const double* __restrict__ zk,
+                                               double alpha, double origin, double delta, int lane, double* f,
+                                               double* fp) {
+  double a = 0.0, b = 0.0;
+  for (int t = lane; t < m; t += 32) {
+    const double q = zk[t] / ((origin - dk[t]) + delta);
+    a += zk[t] * q;
+    b += q * q;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, off);
+    b += __shfl_down_sync(0xffffffffu, b, off);
+  }
+  *f = __shfl_sync(0xffffffffu, a, 0) + (alpha - (origin + delta));
+  *fp = -__shfl_sync(0xffffffffu, b, 0) - 1.0;
+}
+
+// Phase 2, one warp per root: a pole-aware Newton-type iteration on the offset from the nearer pole, kept inside its
+// bracket, then the root's score.
 __global__ void k_sec_roots(int n, int N, double* __restrict__ work, int* __restrict__ iwork) {
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
@@ -711,19 +732,40 @@ __global__ void k_sec_roots(int n, int N, double* __restrict__ work, int* __rest
       }
     }
   }
+  // The bracket [lo, hi] has one end at 0 and never changes sign.  Its midpoint is taken in the ordering of the
+  // doubles of that sign (the bit patterns of |delta|), so that halving reaches adjacent doubles in at most 64 steps
+  // however close the root lies to its pole.
+  auto bitmid = [](double l, double h) {
+    const uint64_t a = (uint64_t)__double_as_longlong(fabs(l)), b = (uint64_t)__double_as_longlong(fabs(h));
+    const uint64_t mb = a < b ? a + (b - a) / 2 : b + (a - b) / 2;
+    const double dm = __longlong_as_double((long long)mb);
+    return (l >= 0.0 && h >= 0.0) ? dm : -dm;
+  };
+  // Each step models f near the root as the pole term at the origin, s / delta with s = z_o^2, exactly, plus the rest
+  // linearised at the current point (value and slope matched), and takes the root of that model on the bracket's side
+  // (a quadratic); where the model gives no root inside the bracket, the bracket is halved instead.
   double delta = 0.5 * (lo + hi);
-  if (m > 0)
-    for (int it = 0; it < 200; ++it) {  // bisection to adjacent doubles (bounded)
-      // The bracket has one end at 0 and never changes sign, so it is halved in the ordering of the doubles of
-      // that sign (the bit patterns of |delta|): adjacent doubles after at most 64 halvings, however close the
-      // root lies to its pole, where halving the value would walk down through every binade.
-      const uint64_t a = (uint64_t)__double_as_longlong(fabs(lo)), b = (uint64_t)__double_as_longlong(fabs(hi));
-      const uint64_t mb = a < b ? a + (b - a) / 2 : b + (a - b) / 2;
-      const double dm = __longlong_as_double((long long)mb);
-      delta = (lo >= 0.0 && hi >= 0.0) ? dm : -dm;
-      if (delta == lo || delta == hi) break;
-      if (warp_secular(m, dk, zk, alpha, origin, delta, lane) > 0) lo = delta; else hi = delta;
+  if (m > 0) {
+    const double sp = zk[oi] * zk[oi];
+    for (int it = 0; it < 200; ++it) {  // bounded
+      double f, fp;
+      warp_secular_d(m, dk, zk, alpha, origin, delta, lane, &f, &fp);
+      if (f > 0) lo = delta; else hi = delta;  // f decreases: the root lies above delta when f > 0
+      if (f == 0.0) break;
+      const double a = fp + sp / (delta * delta);       // slope of the rest (negative)
+      const double b = (f - sp / delta) - a * delta;    // model: a x^2 + b x + sp = 0
+      const double disc = b * b - 4.0 * a * sp;
+      double nd = lo;                                   // outside the open bracket: halve instead
+      if (a < 0.0 && disc >= 0.0) {
+        const double q = -0.5 * (b + copysign(sqrt(disc), b));
+        const double r1 = q / a, r2 = sp / q;            // the two roots have opposite signs
+        nd = ((r1 > 0.0) == (hi > 0.0)) ? r1 : r2;
+      }
+      if (!(nd > lo && nd < hi)) nd = bitmid(lo, hi);
+      if (nd == lo || nd == hi || nd == delta) break;
+      delta = nd;
     }
+  }
   // score of the eigenvector y_t = z_t/(mu - d_t), y_last = 1, against phi~ = (p, ||u||)
   double yy = 0.0, yp = 0.0;
   for (int t = lane; t < m; t += 32) {
@@ -1206,7 +1248,6 @@ int mk_joint_assemble(mk_ctx* ctx, const mk_mesh* m, int k, int N, const double*
   cudaStream_t s = (cudaStream_t)stream;
   const Level& F = m->fine;
   int err = MK_OK;
-  const size_t eb = (size_t)F.n_elems * (F.nloc * (F.nloc + 1) / 2) * sizeof(double);
   double* Mu = (double*)scratch(ctx, S_VEC1, (size_t)F.n_nodes * ld * sizeof(double), &err);
   double* dots = (double*)scratch(ctx, S_COEF, 64 * sizeof(double), &err);
   if (!Mu || !dots) return err;
@@ -1231,7 +1272,6 @@ int mk_orbital_assemble(mk_ctx* ctx, const mk_mesh* m, const double* coef, const
   cudaStream_t s = (cudaStream_t)stream;
   const Level& F = m->fine;
   int err = MK_OK;
-  const size_t eb = (size_t)F.n_elems * (F.nloc * (F.nloc + 1) / 2) * sizeof(double);
   double* Mu = (double*)scratch(ctx, S_VEC1, (size_t)F.n_nodes * ld * sizeof(double), &err);
   double* dots = (double*)scratch(ctx, S_COEF, 64 * sizeof(double), &err);
   if (!Mu || !dots) return err;
