@@ -153,10 +153,15 @@ int mk_ctx_fault(mk_ctx* ctx, int* fault);
  *     1 us) after which the persistent operator kernels' waits for their own copies give up; 0 makes the first wait
  *     give up at once.  A kernel that gives up sets MK_FAULT_PATCH_WAIT, then still waits, with the default limit,
  *     for every copy it issued before it ends; the call that launched it returns MK_ERR_TIMEOUT (solves) or leaves
- *     the bit for mk_ctx_fault (mk_operator_apply), and the outputs are invalid. */
+ *     the bit for mk_ctx_fault (mk_operator_apply), and the outputs are invalid.
+ *   MK_OPT_DECOMPOSE_CTAS (default 0 = one per SM): the number of CTAs of the cooperative block-Jacobi kernel of
+ *     mk_coarse_decompose(_warm); clamped to the SM count, and at least one more than the block pairs of a round
+ *     (else the decomposition returns MK_ERR_INVALID_ARG).  Fewer CTAs leave more of each SM to kernels running
+ *     beside it on another stream. */
 #define MK_OPT_GRAPHS 1
 #define MK_OPT_PATCH_PIPELINE 2
 #define MK_OPT_WAIT_LIMIT 3
+#define MK_OPT_DECOMPOSE_CTAS 4
 int mk_ctx_set_option(mk_ctx* ctx, int option, int value);
 /* Copies the calling thread's last error message into buf (always NUL-terminated); returns its length. */
 int mk_last_error(char* buf, size_t len);
@@ -305,8 +310,14 @@ int mk_coarse_pencil(mk_ctx* ctx, const mk_mesh* mesh, const mk_molecule* mol, c
 /* Shared part of the small eigenproblem of Eq. (Eigenvalue_H_h): all eigenpairs of the coarse pencil (AH, MH),
  * d [N_H] ascending and V [N_H*N_H] row-major (V[r*N_H + k] = component r of eigenvector k), M_H-orthonormal.
  * MH is the mesh's own P^T M P, whose Cholesky factor mk_mesh_upload computed (M_H is fixed for a mesh pair).
- * FP64: C = L^-1 AH L^-T by two GEMMs, cyclic Jacobi (cooperative launch), V = L^-T Q. */
+ * C = L^-1 AH L^-T by two FP64 GEMMs, then cyclic block Jacobi in two phases (cooperative launches): the sweeps
+ * of the linear phase in FP32, its Q made orthogonal in FP64 and C projected onto it, then FP64 sweeps to
+ * off(S) <= 1e-14 |S|; V = L^-T Q. */
 int mk_coarse_decompose(mk_ctx* ctx, const mk_mesh* mesh, const double* AH, double* d, double* V, void* stream);
+/* Report of the most recent decomposition on this context (mk_coarse_decompose, _warm, and the dense solves of
+ * mk_joint_ritz / mk_joint_assemble): the sweeps of its FP32 and FP64 phases.  Synchronises the device.
+ * Errors: MK_ERR_INVALID_ARG (null argument, or no decomposition yet). */
+int mk_decompose_info(mk_ctx* ctx, int* sweeps32, int* sweeps64);
 /* The same decomposition started from a known M_H-orthonormal basis V0 [N_H*N_H] (e.g. the eigenvectors of the
  * density-independent pencil (P^T (K/2 + M_Vext) P, M_H), which stays fixed for a molecule as the paper's static
  * blocks do): C = V0^T AH V0 is then close to diagonal and Jacobi needs fewer sweeps; V = V0 Q.  The result is

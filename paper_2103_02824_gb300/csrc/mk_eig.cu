@@ -228,19 +228,18 @@ __device__ void bj_pair_solve(BJSmem& S, double v, double* __restrict__ Uout) {
   __syncthreads();
 }
 
-// The round-r pair holding block K, and whether K is its second block.
+// The round-r pair holding block K, and whether K is its second block.  Round r pairs block nb - 1 with r (pair 0)
+// and every other block K with (2r - K) mod (nb - 1), in pair m = min((K - r) mod (nb - 1), (r - K) mod (nb - 1)).
 __device__ __forceinline__ void bj_pair_of_block(int r, int K, int nb, int* pair, int* half) {
-  for (int m = 0; m < nb / 2; ++m) {
-    int a, b;
-    pair_of(r, m, nb, &a, &b);
-    if (a == K || b == K) {
-      *pair = m;
-      *half = (b == K) ? 1 : 0;
-      return;
-    }
+  int m = 0;
+  if (K != nb - 1 && K != r) {
+    const int d1 = ((K - r) % (nb - 1) + (nb - 1)) % (nb - 1);
+    m = min(d1, (nb - 1) - d1);
   }
-  *pair = 0;
-  *half = 0;
+  int a, b;
+  pair_of(r, m, nb, &a, &b);
+  *pair = m;
+  *half = (b == K) ? 1 : 0;
 }
 
 // This thread's entry (tid / kBP, tid % kBP) of the sub-block [I', J'] x [I', J'] of S after round r, i.e. of
@@ -425,6 +424,365 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjacobi(int n2, double* __res
     info[0] = sweep;
     info[1] = (Sin == S0) ? 0 : 1;
   }
+}
+
+// ------------------------------------------------------------------------------------ block Jacobi, FP32 phase
+// The same cyclic block Jacobi (rounds of nb / 2 disjoint block pairs, the next round's pair blocks formed by the
+// solver CTAs while the others apply the current round, one grid barrier per round), all in FP32: S, Q and every
+// transform.  The round's latency is what bounds it, so its two parts run at warp level: each pair solve in one
+// warp (the block in registers, no block barrier), each 16 x 16 item of the application in one warp.  It takes the sweeps of the linear phase of the convergence, where most of the work lies, at the
+// FP32 rate; it stops once off(S)^2 <= tol^2 |S|^2, or when a sweep no longer halves off(S)^2 (the FP32 floor),
+// or after max_sweeps.  Its Q is orthogonal to FP32 precision only: the FP64 finish re-orthonormalises it and
+// projects the FP64 matrix onto it before the FP64 sweeps.  *info = {sweeps, buffer holding the result}.
+struct BJ32Smem {
+  float a[1][kBP * kBP];  // the block a round's pair solve diagonalises
+  float sa[kBP * kBP], sb[kBP * kBP], sc[kBP * kBP], sd[kBP * kBP];
+  float bb[3 * kBW * kBW];
+  double sh[kBJThreads];
+  float wa[kBJThreads / 32][kBP * kBP], wb[kBJThreads / 32][kBP * kBP], wt[kBJThreads / 32][kBP * kBP];  // per warp
+};
+
+// The entry (tid / kBP, tid % kBP) of the next round's sub-block [I', J'] x [I', J'] of S after round r, from S
+// before the round and the round's U (as bj_next_block, in FP32).
+__device__ float bj32_next_block(BJ32Smem& S, const float* __restrict__ Sin, const float* __restrict__ Ur, int n2,
+                                 int nb, int r, int Ip, int Jp) {
+  const int tid = threadIdx.x, ti = tid / kBP, tj = tid % kBP;
+  int x, hx, y, hy;
+  bj_pair_of_block(r, Ip, nb, &x, &hx);
+  bj_pair_of_block(r, Jp, nb, &y, &hy);
+  int Ix, Jx, Iy, Jy;
+  pair_of(r, x, nb, &Ix, &Jx);
+  pair_of(r, y, nb, &Iy, &Jy);
+  const float t1 = Sin[(int64_t)bj_index(Ix, Jx, ti) * n2 + bj_index(Ix, Jx, tj)];
+  const float t2 = Sin[(int64_t)bj_index(Ix, Jx, ti) * n2 + bj_index(Iy, Jy, tj)];
+  const float t3 = Sin[(int64_t)bj_index(Iy, Jy, ti) * n2 + bj_index(Iy, Jy, tj)];
+  S.sb[tid] = Ur[(int64_t)x * kBP * kBP + tid];
+  S.sc[tid] = Ur[(int64_t)y * kBP * kBP + tid];
+  for (int part = 0; part < 3; ++part) {
+    S.sa[tid] = part == 0 ? t1 : part == 1 ? t2 : t3;
+    const float* Ul = part == 2 ? S.sc : S.sb;
+    const float* Urt = part == 0 ? S.sb : S.sc;
+    const int hl = part == 2 ? hy : hx, hr = part == 0 ? hx : hy;
+    __syncthreads();
+    if (tid < kBP * kBW) {
+      const int i = tid / kBW, j = tid % kBW;
+      float w = 0.0f;
+      for (int m = 0; m < kBP; ++m) w = fmaf(S.sa[i * kBP + m], Urt[m * kBP + hr * kBW + j], w);
+      S.sd[tid] = w;
+    }
+    __syncthreads();
+    if (tid < kBW * kBW) {
+      const int i = tid / kBW, j = tid % kBW;
+      float o = 0.0f;
+      for (int m = 0; m < kBP; ++m) o = fmaf(Ul[m * kBP + hl * kBW + i], S.sd[m * kBW + j], o);
+      S.bb[part * kBW * kBW + tid] = o;
+    }
+    __syncthreads();
+  }
+  float v;
+  if (ti < kBW && tj < kBW) v = S.bb[ti * kBW + tj];
+  else if (ti < kBW) v = S.bb[kBW * kBW + ti * kBW + (tj - kBW)];
+  else if (tj < kBW) v = S.bb[kBW * kBW + tj * kBW + (ti - kBW)];
+  else v = S.bb[2 * kBW * kBW + (ti - kBW) * kBW + (tj - kBW)];
+  __syncthreads();
+  return v;
+}
+
+// Partner of index x in inner round k of the cyclic ordering of kBP = 16 indices used by pair_of (round k pairs
+// 15 with k and every other x with (2k - x) mod 15).
+__host__ __device__ constexpr int bj_partner(int k, int x) {
+  return x == kBP - 1 ? k : (x == k ? kBP - 1 : ((2 * k - x) % (kBP - 1) + (kBP - 1)) % (kBP - 1));
+}
+
+__device__ __forceinline__ float bj_sel8(const float (&v)[8], int r) {
+  float o = v[0];
+#pragma unroll
+  for (int q = 1; q < 8; ++q) o = (r == q) ? v[q] : o;
+  return o;
+}
+
+// One warp's version of bj32_pair_solve: the same inner sweep, with the block in registers.  Lane l holds row
+// i = l / 2, columns 8 (l % 2) .. 8 (l % 2) + 7 of A and of U; the inner rounds are unrolled, so every partner
+// column has a fixed register; entries of other rows come by shuffles, with no block barrier.  Each rotation is
+// computed from the diagonal entries and from a_pq as row p = min(p, q) holds it, the same values in the lanes of
+// both rows.  Ab: the symmetric block [kBP * kBP] (row-major, shared memory); U to Uout.  Called by all 32 lanes.
+__device__ void bj32_pair_solve_warp(const float* __restrict__ Ab, float* __restrict__ Uout) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, i = lane >> 1, h = lane & 1;
+  float a[8], u[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    a[r] = Ab[i * kBP + 8 * h + r];
+    u[r] = (8 * h + r == i) ? 1.0f : 0.0f;
+  }
+#pragma unroll
+  for (int k = 0; k < kBP - 1; ++k) {
+    const int y = bj_partner(k, i);
+    const int p = min(i, y), q = max(i, y);
+    const float dv = bj_sel8(a, i & 7);  // a_ii, in the lane of row i that holds column i
+    const float ev = bj_sel8(a, y & 7);  // a_iy, in the lane of row i that holds column y
+    const float app = __shfl_sync(FULL, dv, 2 * p + (p >> 3));
+    const float aqq = __shfl_sync(FULL, dv, 2 * q + (q >> 3));
+    const float apq = __shfl_sync(FULL, ev, 2 * p + (q >> 3));
+    // t = sgn(theta) / (|theta| + sqrt(theta^2 + 1)), theta = (a_qq - a_pp) / (2 a_pq); t ~ 1 / (2 theta) where
+    // theta^2 would overflow (equal diagonal entries give theta = 0 and t = +-1 however small a_pq is).  The
+    // quotients and the root use the fast approximate forms (a few ulp): an angle off by that much only leaves a
+    // residue of the same size, which the later sweeps remove, and c, s stay a rotation to FP32 rounding.
+    float t = 0.0f;
+    if (apq != 0.0f) {
+      const float theta = __fdividef(aqq - app, 2.0f * apq);
+      if (!(fabsf(theta) <= 1e18f)) t = isfinite(theta) ? __fdividef(0.5f, theta) : 0.0f;
+      else {
+        const float g = fmaf(theta, theta, 1.0f);
+        t = copysignf(__fdividef(1.0f, fabsf(theta) + g * rsqrtf(g)), theta);
+      }
+    }
+    const float c = rsqrtf(fmaf(t, t, 1.0f)), s = t * c;
+    const float cs = c, co = (i == p) ? -s : s;  // index p: c row_p - s row_q; index q: s row_p + c row_q
+    float cj[8], oj[8], ay[8], rm[8], rmo[8], uc[8], uo[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      cj[r] = __shfl_sync(FULL, cs, 2 * (8 * h + r));
+      oj[r] = __shfl_sync(FULL, co, 2 * (8 * h + r));
+      ay[r] = __shfl_sync(FULL, a[r], 2 * y + h);
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) rm[r] = cs * a[r] + co * ay[r];  // row i of J^T A
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      rmo[r] = __shfl_xor_sync(FULL, rm[r], 1);
+      uc[r] = u[r];  // the row before this round (u is rewritten column by column below)
+      uo[r] = __shfl_xor_sync(FULL, u[r], 1);
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int y0 = bj_partner(k, r), y1 = bj_partner(k, 8 + r);  // the partner of column 8h + r, for h = 0, 1
+      const float r0 = (y0 < 8) ? rm[y0 & 7] : rmo[y0 & 7];         // row i at column y0 (h = 0: own half first)
+      const float r1 = (y1 >= 8) ? rm[y1 & 7] : rmo[y1 & 7];        // row i at column y1 (h = 1)
+      const float u0 = (y0 < 8) ? uc[y0 & 7] : uo[y0 & 7];
+      const float u1 = (y1 >= 8) ? uc[y1 & 7] : uo[y1 & 7];
+      const float rv = h ? r1 : r0, uv = h ? u1 : u0;
+      const float na = cj[r] * rm[r] + oj[r] * rv;
+      a[r] = (8 * h + r == y) ? 0.0f : na;  // a rotated pair's own entry is annihilated
+      u[r] = cj[r] * uc[r] + oj[r] * uv;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) Uout[i * kBP + 8 * h + r] = u[r];
+}
+
+__global__ void __launch_bounds__(kBJThreads, 2) k_bjacobi32(int n2, float* __restrict__ S0, float* __restrict__ S1,
+                                                           float* __restrict__ Q, float* __restrict__ Ug,
+                                                           double* __restrict__ red, int max_sweeps, double tol,
+                                                           int* __restrict__ info) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ BJ32Smem S;
+  const int tid = threadIdx.x;
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + tid;
+  const int64_t gnth = (int64_t)gridDim.x * blockDim.x;
+  const int nb = n2 / kBW, npr = nb / 2;
+  const int ti = tid / kBP, tj = tid % kBP;
+  const bool solver = (int)blockIdx.x < npr;
+  const int na = (int)gridDim.x - npr;
+  float* Sin = S0;
+  float* Sout = S1;
+  double prev = -1.0;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int64_t t = gtid; t < (int64_t)n2 * n2; t += gnth) {
+      const double v = Sin[t];
+      tot += v * v;
+      if (t / n2 != t % n2) off += v * v;
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+      S.sh[tid] = pass == 0 ? off : tot;
+      __syncthreads();
+      for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (tid < st) S.sh[tid] += S.sh[tid + st];
+        __syncthreads();
+      }
+      if (tid == 0) red[2 * blockIdx.x + pass] = S.sh[0];
+      __syncthreads();
+    }
+    grid.sync();
+    double o = 0.0, f = 0.0;
+    for (int bl = 0; bl < (int)gridDim.x; ++bl) {
+      o += red[2 * bl];
+      f += red[2 * bl + 1];
+    }
+    grid.sync();
+    // converged, or at the FP32 floor (a sweep that does not halve off^2); the same decision in every CTA
+    if (o <= tol * tol * f || (prev >= 0.0 && o > 0.5 * prev)) break;
+    prev = o;
+    if (solver) {
+      int I, J;
+      pair_of(0, blockIdx.x, nb, &I, &J);
+      S.a[0][tid] = Sin[(int64_t)bj_index(I, J, ti) * n2 + bj_index(I, J, tj)];
+      __syncthreads();
+      if (tid < 32) bj32_pair_solve_warp(S.a[0], Ug + (int64_t)blockIdx.x * kBP * kBP);
+    }
+    grid.sync();
+    for (int r = 0; r < nb - 1; ++r) {
+      const float* Ur = Ug + (int64_t)(r & 1) * npr * kBP * kBP;
+      if (solver) {
+        if (r + 1 < nb - 1) {
+          int Ip, Jp;
+          pair_of(r + 1, blockIdx.x, nb, &Ip, &Jp);
+          const float v = bj32_next_block(S, Sin, Ur, n2, nb, r, Ip, Jp);
+          S.a[0][tid] = v;
+          __syncthreads();
+          if (tid < 32) bj32_pair_solve_warp(S.a[0], Ug + ((int64_t)((r + 1) & 1) * npr + blockIdx.x) * kBP * kBP);
+          __syncthreads();  // S.a is rewritten by the next round's block
+        }
+      } else {
+        // S_out = U^T S_in U by block pairs (a >= b, the transpose written too), Q <- Q U in place; one 16 x 16
+        // item per warp (lane: row i = lane / 2, columns 8 (lane % 2) ..), every warp of the CTA on its own item
+        const int nS = npr * (npr + 1) / 2, nQ = (n2 / kBP) * npr;
+        const int wp = tid >> 5, lane = tid & 31, i = lane >> 1, h = lane & 1;
+        float* Wa = S.wa[wp];
+        float* Wb = S.wb[wp];
+        float* Wt = S.wt[wp];
+        const int nw = kBJThreads / 32;
+        for (int item = ((int)blockIdx.x - npr) * nw + wp; item < nS + nQ; item += na * nw) {
+          const bool sitem = item < nS;
+          int a = 0, b, row, c0;
+          if (sitem) {
+            a = (int)((sqrtf(8.0f * (float)item + 1.0f) - 1.0f) * 0.5f);  // item = a (a + 1) / 2 + b, b <= a
+            while ((a + 1) * (a + 2) / 2 <= item) ++a;
+            while (a * (a + 1) / 2 > item) --a;
+            b = item - a * (a + 1) / 2;
+            int Ia, Ja, Ib, Jb;
+            pair_of(r, a, nb, &Ia, &Ja);
+            pair_of(r, b, nb, &Ib, &Jb);
+            row = bj_index(Ia, Ja, i);
+            c0 = h ? Jb * kBW : Ib * kBW;
+          } else {
+            const int u = item - nS, rt = u / npr;
+            b = u % npr;
+            int Ib, Jb;
+            pair_of(r, b, nb, &Ib, &Jb);
+            row = rt * kBP + i;
+            c0 = h ? Jb * kBW : Ib * kBW;
+          }
+          const float* src = sitem ? Sin : Q;
+          float x[8], xo[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            Wb[lane * 8 + q] = Ur[(int64_t)b * kBP * kBP + lane * 8 + q];
+            if (sitem) Wa[lane * 8 + q] = Ur[(int64_t)a * kBP * kBP + lane * 8 + q];
+            x[q] = src[(int64_t)row * n2 + c0 + q];
+          }
+#pragma unroll
+          for (int q = 0; q < 8; ++q) xo[q] = __shfl_xor_sync(0xffffffffu, x[q], 1);
+          __syncwarp();
+          float t[8];  // (X U_b)[i][8h + q]
+#pragma unroll
+          for (int q = 0; q < 8; ++q) t[q] = 0.0f;
+#pragma unroll
+          for (int m = 0; m < kBP; ++m) {
+            const float xm = (m < 8) == (h == 0) ? x[m & 7] : xo[m & 7];  // row i, column m of the item
+#pragma unroll
+            for (int q = 0; q < 8; ++q) t[q] = fmaf(xm, Wb[m * kBP + 8 * h + q], t[q]);
+          }
+          if (sitem) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) Wt[i * kBP + 8 * h + q] = t[q];
+            __syncwarp();
+            float o[8];  // (U_a^T X U_b)[i][8h + q]
+#pragma unroll
+            for (int q = 0; q < 8; ++q) o[q] = 0.0f;
+#pragma unroll
+            for (int m = 0; m < kBP; ++m) {
+              const float um = Wa[m * kBP + i];
+#pragma unroll
+              for (int q = 0; q < 8; ++q) o[q] = fmaf(um, Wt[m * kBP + 8 * h + q], o[q]);
+            }
+            if (a == b) {  // the diagonal block stays exactly symmetric
+              __syncwarp();
+#pragma unroll
+              for (int q = 0; q < 8; ++q) Wt[i * kBP + 8 * h + q] = o[q];
+              __syncwarp();
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                const int j = 8 * h + q;
+                o[q] = i <= j ? Wt[i * kBP + j] : Wt[j * kBP + i];
+              }
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              Sout[(int64_t)row * n2 + c0 + q] = o[q];
+              if (a != b) Sout[(int64_t)(c0 + q) * n2 + row] = o[q];
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) Q[(int64_t)row * n2 + c0 + q] = t[q];
+          }
+          __syncwarp();  // the next item rewrites this warp's staging
+        }
+      }
+      grid.sync();
+      float* tmp = Sin;
+      Sin = Sout;
+      Sout = tmp;
+    }
+  }
+  if (gtid == 0) {
+    info[0] = sweep;
+    info[1] = (Sin == S0) ? 0 : 1;
+  }
+}
+
+// FP64 n2 x n2 S -> FP32 copy, Q32 = I.
+__global__ void k_bj_to32(int64_t nn, int n2, const double* __restrict__ S, float* __restrict__ S32,
+                          float* __restrict__ Q32) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nn) return;
+  S32[t] = (float)S[t];
+  Q32[t] = (t / n2 == t % n2) ? 1.0f : 0.0f;
+}
+
+__global__ void k_f32_to_f64(int64_t nn, const float* __restrict__ a, double* __restrict__ b) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nn) b[t] = (double)a[t];
+}
+
+// One Newton-Schulz step X' = X + X E / 2 with E = I - G (G = X^T X, FP64): the correction X E in FP32 (E is
+// small, so its FP32 rounding is far below the FP64 rounding of X'), X' in FP64.  n x n row-major, 32 x 32 tiles.
+__global__ void k_ns_step(int n, const double* __restrict__ X, const double* __restrict__ G, double* __restrict__ Xo) {
+  __shared__ float As[32][33], Bs[32][33];
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    for (int r = ty; r < 32; r += 8) {
+      const int i = i0 + r, k = k0 + tx;
+      As[r][tx] = (i < n && k < n) ? (float)X[(int64_t)i * n + k] : 0.0f;
+      const int kk = k0 + r, j = j0 + tx;
+      Bs[r][tx] = (kk < n && j < n) ? (float)((kk == j ? 1.0 : 0.0) - G[(int64_t)kk * n + j]) : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      const float bv = Bs[k][tx];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fmaf(As[ty + 8 * q][k], bv, acc[q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = i0 + ty + 8 * q, j = j0 + tx;
+    if (i < n && j < n) Xo[(int64_t)i * n + j] = X[(int64_t)i * n + j] + 0.5 * (double)acc[q];
+  }
+}
+
+// S = (T + T^T) / 2 for an n x n matrix T.
+__global__ void k_symmetrize(int n, const double* __restrict__ T, double* __restrict__ S) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n) return;
+  const int i = (int)(t / n), j = (int)(t % n);
+  S[t] = 0.5 * (T[t] + T[(int64_t)j * n + i]);
 }
 
 // C[M x N] = op(A) op(B), op(X) = X or X^T (row-major storage), FP64, 32x32 tiles.
@@ -963,30 +1321,66 @@ int decompose(mk_ctx* ctx, int n, const double* X, bool w_is_x, const double* AH
   const size_t oT = take((size_t)n * n * 8), oC = take((size_t)n * n * 8), oS0 = take((size_t)n2 * n2 * 8);
   const size_t oS1 = take((size_t)n2 * n2 * 8), oQ = take((size_t)n2 * n2 * 8), oRed = take(8192 * 8);
   const size_t oPerm = take((size_t)n * 4), oInfo = take(64), oU = take((size_t)2 * (n2 / kBP) * kBP * kBP * 8);
+  const size_t oG = take((size_t)n2 * n2 * 8), oX2 = take((size_t)n2 * n2 * 8);
+  const size_t oS32a = take((size_t)n2 * n2 * 4), oS32b = take((size_t)n2 * n2 * 4), oQ32 = take((size_t)n2 * n2 * 4);
   char* ws = (char*)scratch(ctx, slot, off, &err);
   if (!ws) return err;
   double *T = (double*)(ws + oT), *C = (double*)(ws + oC), *S0 = (double*)(ws + oS0), *S1 = (double*)(ws + oS1);
   double *Q = (double*)(ws + oQ), *red = (double*)(ws + oRed);
   int *perm = (int*)(ws + oPerm), *info = (int*)(ws + oInfo);
   double* Ug = (double*)(ws + oU);
+  double *G = (double*)(ws + oG), *X2 = (double*)(ws + oX2);
+  float *S32a = (float*)(ws + oS32a), *S32b = (float*)(ws + oS32b), *Q32 = (float*)(ws + oQ32);
+  float* Ug32 = (float*)(ws + oU);  // the FP32 phase's transforms, in the FP64 phase's (later) place
   const int tx = w_is_x ? 1 : 0;                                     // op for W^T
   gemm64(n, n, n, X, n, tx, AH, n, 0, T, n, s);                      // T = W^T AH
   gemm64(n, n, n, T, n, 0, X, n, 1 - tx, C, n, s);                   // C = T W
-  MK_COUNT(), k_pad_sym<<<(int)(((int64_t)n2 * n2 + 255) / 256), 256, 0, s>>>(n, n2, C, S0, Q, 0.0);
-  int max_sweeps = 60;
-  double tol = 1e-14;
+  const int64_t nn2 = (int64_t)n2 * n2;
+  const int ew = (int)((nn2 + 255) / 256);
+  MK_COUNT(), k_pad_sym<<<ew, 256, 0, s>>>(n, n2, C, S0, Q, 0.0);
   int n2v = n2;
-  int per_sm = 0;
+  int per_sm = 0, per_sm32 = 0;
   MK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bjacobi, kBJThreads, 0));
-  MK_ARG(per_sm >= 1, "mk: block Jacobi kernel cannot be resident");
-  // one CTA per SM (half its registers): the fine solve's kernels on the other stream run beside it
+  MK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm32, k_bjacobi32, kBJThreads, 0));
+  MK_ARG(per_sm >= 1 && per_sm32 >= 1, "mk: block Jacobi kernel cannot be resident");
+  // at most one CTA per SM (half its registers): the fine solve's kernels on the other stream run beside it
   int grid = std::min(ctx->n_sms, 4096);
+  if (ctx->decompose_ctas > 0) grid = std::min(grid, ctx->decompose_ctas);
   MK_ARG(grid > n2 / kBP, "mk: block Jacobi needs more CTAs than block pairs (coarse space too large)");
-  void* args[] = {&n2v, &S0, &S1, &Q, &Ug, &red, &max_sweeps, &tol, &info};
-  MK_COUNT();
   // the largest shared-memory carveout, so that an SM running this CTA can also take the fine solve's CTAs
+  MK_CUDA(cudaFuncSetAttribute(k_bjacobi32, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared));
   MK_CUDA(cudaFuncSetAttribute(k_bjacobi, cudaFuncAttributePreferredSharedMemoryCarveout,
                                cudaSharedmemCarveoutMaxShared));
+  // (1) the sweeps of the linear phase in FP32, to off(S) <= 1e-5 |S| or the FP32 floor
+  {
+    int max32 = 40;
+    double tol32 = 1e-5;
+    int* info32 = info + 4;
+    MK_COUNT(), k_bj_to32<<<ew, 256, 0, s>>>(nn2, n2, S0, S32a, Q32);
+    void* a32[] = {&n2v, &S32a, &S32b, &Q32, &Ug32, &red, &max32, &tol32, &info32};
+    MK_COUNT();
+    MK_CUDA(cudaLaunchCooperativeKernel((void*)k_bjacobi32, grid, kBJThreads, a32, 0, s));
+  }
+  // (2) its Q made orthogonal in FP64 (two Newton-Schulz steps: ~1e-6 -> ~1e-12 -> FP64 rounding) and the FP64
+  // matrix projected onto it: S0 <- Q^T S0 Q, symmetrised; the FP64 sweeps then accumulate into this Q
+  {
+    MK_COUNT(), k_f32_to_f64<<<ew, 256, 0, s>>>(nn2, Q32, Q);
+    const dim3 tg((n2 + 31) / 32, (n2 + 31) / 32);
+    gemm64(n2, n2, n2, Q, n2, 1, Q, n2, 0, G, n2, s);                 // G = Q^T Q
+    MK_COUNT(), k_ns_step<<<tg, 256, 0, s>>>(n2, Q, G, X2);
+    gemm64(n2, n2, n2, X2, n2, 1, X2, n2, 0, G, n2, s);
+    MK_COUNT(), k_ns_step<<<tg, 256, 0, s>>>(n2, X2, G, Q);
+    gemm64(n2, n2, n2, S0, n2, 0, Q, n2, 0, G, n2, s);                // G = S0 Q
+    gemm64(n2, n2, n2, Q, n2, 1, G, n2, 0, S1, n2, s);                // S1 = Q^T S0 Q
+    MK_COUNT(), k_symmetrize<<<ew, 256, 0, s>>>(n2, S1, S0);
+  }
+  ctx->last_decompose_info = info;
+  // (3) the FP64 sweeps to off(S) <= 1e-14 |S|
+  int max_sweeps = 60;
+  double tol = 1e-14;
+  void* args[] = {&n2v, &S0, &S1, &Q, &Ug, &red, &max_sweeps, &tol, &info};
+  MK_COUNT();
   MK_CUDA(cudaLaunchCooperativeKernel((void*)k_bjacobi, grid, kBJThreads, args, 0, s));
   MK_COUNT(), k_rank<<<(n + 127) / 128, 128, 0, s>>>(n, n2, S0, S1, info, d, perm);
   MK_COUNT(), k_gather_cols<<<(int)(((int64_t)n * n + 255) / 256), 256, 0, s>>>(n, n2, Q, perm, C);  // C = Q sorted
@@ -1148,6 +1542,18 @@ int mesh_mass_factor(mk_ctx* ctx, mk_mesh* m) {
 using namespace mk;
 
 extern "C" {
+
+int mk_decompose_info(mk_ctx* ctx, int* sweeps32, int* sweeps64) {
+  MK_ARG(ctx && sweeps32 && sweeps64, "mk_decompose_info: null argument");
+  MK_ARG(ctx->last_decompose_info, "mk_decompose_info: no decomposition on this context yet");
+  MK_CUDA(cudaSetDevice(ctx->device));
+  MK_CUDA(cudaDeviceSynchronize());
+  int h[5];
+  MK_CUDA(cudaMemcpy(h, ctx->last_decompose_info, sizeof(h), cudaMemcpyDeviceToHost));
+  *sweeps64 = h[0];
+  *sweeps32 = h[4];
+  return MK_OK;
+}
 
 int mk_coarse_decompose(mk_ctx* ctx, const mk_mesh* m, const double* AH, double* d, double* V, void* stream) {
   MK_ARG(ctx && m && AH && d && V && m->d_MH_Linv, "mk_coarse_decompose: null argument");

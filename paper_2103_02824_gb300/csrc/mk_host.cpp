@@ -660,6 +660,10 @@ int mk_ctx_set_option(mk_ctx* c, int option, int value) {
       MK_ARG(value >= -1, "mk_ctx_set_option: wait limit must be >= 0, or -1 for the default");
       c->wait_limit = value < 0 ? kWaitLimitDefault : value;
       return MK_OK;
+    case MK_OPT_DECOMPOSE_CTAS:
+      MK_ARG(value >= 0, "mk_ctx_set_option: decomposition CTAs must be >= 0 (0 = one per SM)");
+      c->decompose_ctas = value;
+      return MK_OK;
     default: return fail(MK_ERR_INVALID_ARG, "mk_ctx_set_option: unknown option");
   }
 }

@@ -182,6 +182,8 @@ struct mk_ctx {
   // pipelined kernel for FP32 too, 0 = the one-patch-per-CTA kernel
   int patch_kernel = 1;
   int wait_limit = mk::kWaitLimitDefault;  // MK_OPT_WAIT_LIMIT: polls of the patch kernel's bounded copy waits
+  int decompose_ctas = 0;  // MK_OPT_DECOMPOSE_CTAS: CTAs of the block-Jacobi kernel (0 = one per SM)
+  const int* last_decompose_info = nullptr;  // device {sweeps64, buffer, -, -, sweeps32} of the last decomposition
   // the inner PCG runs on this stream (graphs cannot be captured on the legacy default stream), ordered against
   // the caller's stream by two events
   cudaStream_t solve_stream = nullptr;

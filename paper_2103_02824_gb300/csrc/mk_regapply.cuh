@@ -121,25 +121,26 @@ __device__ __forceinline__ void patch_apply_reg(int p, const unsigned char* __re
     if (mine) {
 #pragma unroll
       for (int c = 0; c < 4; c += 2) {
-        Vec<float, 2> xv[NLOC];
+        // two columns per instruction (packed FP32 FMA, each lane the fused multiply-add of the scalar form, in the
+        // same order: bitwise the products of the other patch kernels)
+        float2 xv[NLOC];
 #pragma unroll
-        for (int b = 0; b < NLOC; ++b) xv[b] = ldv<float, 2>(Xs + (size_t)lnd[b] * XS + pass * 4 + c);
-        Vec<float, 2> acc[NLOC];
+        for (int b = 0; b < NLOC; ++b)
+          xv[b] = *reinterpret_cast<const float2*>(Xs + (size_t)lnd[b] * XS + pass * 4 + c);
+        float2 acc[NLOC];
 #pragma unroll
-        for (int a = 0; a < NLOC; ++a) acc[a].v[0] = acc[a].v[1] = 0;
+        for (int a = 0; a < NLOC; ++a) acc[a] = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int a = 0; a < NLOC; ++a)
 #pragma unroll
           for (int b = a; b < NLOC; ++b) {
             const float wv = A[sym_index(a, b, NLOC)];
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-              acc[a].v[q] += wv * xv[b].v[q];
-              if (b != a) acc[b].v[q] += wv * xv[a].v[q];
-            }
+            const float2 w2 = make_float2(wv, wv);
+            acc[a] = __ffma2_rn(w2, xv[b], acc[a]);
+            if (b != a) acc[b] = __ffma2_rn(w2, xv[a], acc[b]);
           }
 #pragma unroll
-        for (int a = 0; a < NLOC; ++a) stv<float, 2>(Ye + (size_t)pos[a] * 4 + c, acc[a]);
+        for (int a = 0; a < NLOC; ++a) *reinterpret_cast<float2*>(Ye + (size_t)pos[a] * 4 + c) = acc[a];
       }
     }
     __syncthreads();

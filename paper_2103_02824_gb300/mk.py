@@ -108,6 +108,7 @@ _SIGS = {
     "mk_coarse_pencil": [_vp, _vp, C.POINTER(mk_molecule), _vp, _vp, _vp, _vp],
     "mk_operator_apply": [_vp, _vp, C.POINTER(mk_molecule), C.c_double, C.c_int, _vp, _vp, C.c_int, _vp],
     "mk_coarse_decompose": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "mk_decompose_info": [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "mk_coarse_decompose_warm": [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp],
     "mk_small_eigensolve_shared": [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "mk_small_eigensolve_static": [C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
@@ -186,7 +187,7 @@ def ctx_fault(ctx) -> int:
 
 
 PROF_APPLY64, PROF_APPLY32, PROF_HALO, PROF_LEARNED, PROF_STIFF = 0, 1, 2, 3, 4
-MK_OPT_GRAPHS, MK_OPT_PATCH_PIPELINE, MK_OPT_WAIT_LIMIT = 1, 2, 3
+MK_OPT_GRAPHS, MK_OPT_PATCH_PIPELINE, MK_OPT_WAIT_LIMIT, MK_OPT_DECOMPOSE_CTAS = 1, 2, 3, 4
 
 
 def ctx_set_option(ctx, option, value):
@@ -637,6 +638,13 @@ def mk_coarse_pencil(ctx, mesh, mol: Molecule, vq, AH, MH, stream=None):
 
 def mk_coarse_decompose(ctx, mesh, AH, d, V, stream=None):
     _check(lib().mk_coarse_decompose(ctx.h, mesh.h, _ptr(AH), _ptr(d), _ptr(V), _stream(stream)))
+
+
+def mk_decompose_info(ctx):
+    """Sweeps of the FP32 and FP64 phases of the context's most recent decomposition (synchronises)."""
+    s32, s64 = C.c_int(0), C.c_int(0)
+    _check(lib().mk_decompose_info(ctx.h, C.byref(s32), C.byref(s64)))
+    return {"sweeps32": s32.value, "sweeps64": s64.value}
 
 
 def mk_coarse_decompose_warm(ctx, NH, AH, V0, d, V, stream=None):
