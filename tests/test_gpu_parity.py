@@ -265,6 +265,10 @@ def test_coarse_pencil_and_decompose(ctx, torch, name):
     mk.mk_coarse_pencil(ctx, m, mk.Molecule(c["wl"]["Z"], c["wl"]["R"]), dev(torch, c["vq"]), AH, MH)
     mk.mk_coarse_decompose(ctx, m, AH, d, V)
     torch.cuda.synchronize()
+    # the FP32 phase takes the linear sweeps; the FP64 phase finishes (more sweeps where the spectrum has exact
+    # multiplicities, as the centred hydrogen atom's does)
+    sw = mk.mk_decompose_info(ctx)
+    assert sw["sweeps32"] >= 1 and 1 <= sw["sweeps64"] <= 8, sw
     assert rel(AH.cpu().numpy(), o["AH"]) < 1e-12 and maxrel(AH.cpu().numpy(), o["AH"]) < 1e-12
     assert rel(MH.cpu().numpy(), o["MH"]) < 1e-13 and maxrel(MH.cpu().numpy(), o["MH"]) < 1e-13
     ev = sla.eigh(o["AH"], o["MH"], eigvals_only=True)
@@ -281,6 +285,42 @@ def test_coarse_pencil_and_decompose(ctx, torch, name):
     torch.cuda.synchronize()
     assert np.abs(lam.cpu().numpy() - o["lam"]).max() < 1e-10
     assert np.abs(coef.cpu().numpy() - o["coef"]).max() < 1e-8 * np.abs(o["coef"]).max()
+
+
+def test_decompose_on_fewer_ctas_and_degenerate_spectra(ctx, torch):
+    """The cooperative decomposition on a smaller grid (MK_OPT_DECOMPOSE_CTAS) gives the same spectrum, and pencils
+    whose FP32 phase has nothing to do (the identity) or meets exact multiplicities (diag(0, 0, 1, 1, ...) rotated by
+    a random orthogonal matrix) still come out right."""
+    import scipy.linalg as sla
+    from paper_2103_02824_gb300 import mk
+    rng = np.random.default_rng(5)
+    n = 100
+    Qr, _ = np.linalg.qr(rng.normal(size=(n, n)))
+    ev = np.repeat(np.arange(n // 2, dtype=np.float64), 2)
+    A = (Qr * ev[None, :]) @ Qr.T
+    A = 0.5 * (A + A.T)
+    I = torch.eye(n, dtype=torch.float64, device="cuda")
+    z = lambda *s: torch.zeros(s, dtype=torch.float64, device="cuda")
+    out = {}
+    try:
+        for ctas in (0, 48):
+            mk.ctx_set_option(ctx, mk.MK_OPT_DECOMPOSE_CTAS, ctas)
+            for tag, M in (("pairs", A), ("identity", np.eye(n))):
+                d, V = z(n), z(n, n)
+                mk.mk_coarse_decompose_warm(ctx, n, dev(torch, M), I, d, V)
+                torch.cuda.synchronize()
+                dh, Vh = d.cpu().numpy(), V.cpu().numpy()
+                ref = sla.eigh(M, eigvals_only=True)
+                scale = max(1.0, np.abs(ref).max())
+                assert np.abs(dh - ref).max() < 1e-12 * scale, (tag, ctas)
+                assert np.abs(Vh.T @ Vh - np.eye(n)).max() < 1e-12, (tag, ctas)
+                assert np.abs(M @ Vh - Vh * dh[None, :]).max() < 1e-11 * scale, (tag, ctas)
+                out[tag, ctas] = dh
+    finally:
+        mk.ctx_set_option(ctx, mk.MK_OPT_DECOMPOSE_CTAS, 0)
+    assert np.abs(out["pairs", 0] - out["pairs", 48]).max() < 1e-12
+    with pytest.raises(mk.MkError):
+        mk.ctx_set_option(ctx, mk.MK_OPT_DECOMPOSE_CTAS, -1)
 
 
 @pytest.mark.parametrize("name", CASES)
