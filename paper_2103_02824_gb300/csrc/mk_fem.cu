@@ -422,32 +422,34 @@ int frozen_potential(mk_ctx* ctx, const Level& L, const double* w, const double*
 }
 
 // ------------------------------------------------------------------------------------------------ Poisson pieces
-// F[node(e,a)] += sum_q w_q |det| rho_q phi_a(x_q), one colour at a time
+// F[node(e,a)] += sum_q w_q |det| rho_q phi_a(x_q), one colour at a time.  One warp per element: lane q forms
+// c_q = w_q |det| rho_q (a coalesced read of the element's kQ values), lanes a < NLOC sum c_q phi_q[a] over q in
+// order with c_q broadcast by shuffle (the same products and order as one thread per element), then scatter.
 template <int NLOC>
 __global__ void k_load_colour(const int32_t* __restrict__ celems, int count, const RefTables* __restrict__ ref,
                               const int32_t* __restrict__ elem, const Geom* __restrict__ geom,
                               const double* __restrict__ rho, double scale, double* __restrict__ F) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= count) return;
+  static_assert(kQ <= 32, "one quadrature point per lane");
+  const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= count) return;  // the whole warp leaves together
   const int e = celems[i];
   const double det = fabs(geom[e].det);
-  double fa[NLOC];
-#pragma unroll
-  for (int a = 0; a < NLOC; ++a) fa[a] = 0.0;
+  const double c = lane < kQ ? ref->qw[lane] * det * rho[(int64_t)e * kQ + lane] : 0.0;
+  const int a = lane < NLOC ? lane : 0;
+  double fa = 0.0;
   for (int q = 0; q < kQ; ++q) {
-    const double c = ref->qw[q] * det * rho[(int64_t)e * kQ + q];
-#pragma unroll
-    for (int a = 0; a < NLOC; ++a) fa[a] += c * ref->phi[q][a];
+    const double cq = __shfl_sync(0xffffffffu, c, q);
+    fa += cq * ref->phi[q][a];
   }
-#pragma unroll
-  for (int a = 0; a < NLOC; ++a) F[elem[(int64_t)e * NLOC + a]] += scale * fa[a];
+  if (lane < NLOC) F[elem[(int64_t)e * NLOC + lane]] += scale * fa;
 }
 
 int load_vector(mk_ctx* ctx, const Level& L, const double* rho, double scale, double* F, cudaStream_t s) {
   MK_CUDA(cudaMemsetAsync(F, 0, L.n_nodes * sizeof(double), s));
   for (int c = 0; c < L.n_colours; ++c) {
     const int64_t off = L.colour_off[c], cnt = L.colour_off[c + 1] - off;
-    const int blocks = (int)((cnt + 127) / 128);
+    const int blocks = (int)((cnt * 32 + 127) / 128);  // four elements (warps) per block
     if (L.nloc == 4)
       MK_COUNT(), k_load_colour<4><<<blocks, 128, 0, s>>>(L.d_colour_elems + off, (int)cnt, ctx->d_ref[1], L.d_elem, L.d_geom,
                                              rho, scale, F);
