@@ -560,7 +560,16 @@ def main():
         step()
     torch.cuda.synchronize()
     prof = {k: mk.profile_read(ctx, k) for k in (mk.PROF_APPLY64, mk.PROF_APPLY32, mk.PROF_HALO, mk.PROF_LEARNED,
-                                                 mk.PROF_STIFF)}
+                                                 mk.PROF_STIFF, mk.PROF_PAIRS)}
+    # the refinement residuals of the mixed solves on FP32 pairs against the FP64 operator applications of the same
+    # steps (the right-hand sides and the projection); both kernels take 4 columns per launch
+    pairs_vs_fp64 = None
+    if a.precision == "mixed":
+        (mp, n_p), (m64, n64) = prof[mk.PROF_PAIRS], prof[mk.PROF_APPLY64]
+        pairs_vs_fp64 = {"pairs_us_per_launch": 1e3 * mp / n_p if n_p else None, "pairs_launches_per_step": n_p / a.steps,
+                         "fp64_us_per_launch": 1e3 * m64 / n64 if n64 else None, "fp64_launches_per_step": n64 / a.steps,
+                         "note": "CUDA events inside the overlapped steps; k_apply_pair (FP32 pairs, about 48 "
+                                 "significant bits) for the solves' residuals, k_apply_patch<10,double> for the rest"}
     mk.profile_enable(ctx, False)
 
     # end to end through the C ABI with host buffers: pinned psi_H in, eigenvalues, coefficients, orbitals out
@@ -908,6 +917,7 @@ def main():
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "gpu_launches_per_step": launches / a.steps,
             "clocks": clk, "roofline": roof, "roofline_learned": roof_tc, "roofline_stiffness": roof_k,
+            "residual_pairs_vs_fp64": pairs_vs_fp64,
             "cpu_baseline": cpu, "parity": parity,
             "compare": compare, "paper_form": paper, "joint_space": joint, "afem_estimate_mark": afem,
             "training": train_info, "batch": batch,

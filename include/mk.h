@@ -75,7 +75,7 @@ typedef struct {
   double alpha; /* X-alpha only */
 } mk_xc;
 
-enum { MK_PREC_FP64 = 0, MK_PREC_MIXED = 1 };
+enum { MK_PREC_FP64 = 0, MK_PREC_MIXED = 1, MK_PREC_PAIRS = 2 };
 /* Preconditioners: JACOBI (diagonal); CHEBYSHEV (FP64 only): z = p(D^-1 A) D^-1 r, the degree-4 Chebyshev
  * polynomial of the Chebyshev iteration (D the diagonal) on [a, 1.1 b] with a, b the extreme Ritz values of 16
  * Lanczos steps on D^-1/2 A D^-1/2, three operator applications per preconditioner call (a plain comparison for
@@ -157,11 +157,15 @@ int mk_ctx_fault(mk_ctx* ctx, int* fault);
  *   MK_OPT_DECOMPOSE_CTAS (default 0 = one per SM): the number of CTAs of the cooperative block-Jacobi kernel of
  *     mk_coarse_decompose(_warm); clamped to the SM count, and at least one more than the block pairs of a round
  *     (else the decomposition returns MK_ERR_INVALID_ARG).  Fewer CTAs leave more of each SM to kernels running
- *     beside it on another stream. */
+ *     beside it on another stream.
+ *   MK_OPT_PAIR_RESIDUAL (default 1): the FP64 residual b - A x of every refinement step of the mixed-precision
+ *     solves computed on the FP32 units from FP32 pairs (each FP64 value as hi + lo, error-free products and sums,
+ *     about 48 significant bits; see MK_PREC_PAIRS), FP64 node sums; 0: plain FP64 products. */
 #define MK_OPT_GRAPHS 1
 #define MK_OPT_PATCH_PIPELINE 2
 #define MK_OPT_WAIT_LIMIT 3
 #define MK_OPT_DECOMPOSE_CTAS 4
+#define MK_OPT_PAIR_RESIDUAL 5
 int mk_ctx_set_option(mk_ctx* ctx, int option, int value);
 /* Copies the calling thread's last error message into buf (always NUL-terminated); returns its length. */
 int mk_last_error(char* buf, size_t len);
@@ -175,7 +179,8 @@ long long mk_launch_count(void);
  * the recorded events and returns the summed duration and the number of timed applications of kind
  * 0 = FP64 element-by-element apply, 1 = FP32 patch apply of the correction operator (the pipelined or the
  * one-patch-per-CTA kernel), 2 = FP32 halo sum, 3 = learned-preconditioner patch kernel (the network and the node
- * sums, without the halo pass), 4 = FP32 matrix-free stiffness operator of the Poisson solve.  Every application is
+ * sums, without the halo pass), 4 = FP32 matrix-free stiffness operator of the Poisson solve, 5 = the FP64-accurate
+ * operator on FP32 pairs (one launch per 4 columns, without the split of x and the halo pass).  Every application is
  * timed, including those inside the CUDA graphs of the inner iterations (each has its own event pair in the
  * graph, up to 128 pairs of a kind per captured chunk). */
 #define MK_PROF_APPLY64 0
@@ -183,6 +188,7 @@ long long mk_launch_count(void);
 #define MK_PROF_HALO 2
 #define MK_PROF_LEARNED 3
 #define MK_PROF_STIFF 4
+#define MK_PROF_PAIRS 5
 int mk_profile_enable(mk_ctx* ctx, int on);
 int mk_profile_read(mk_ctx* ctx, int kind, double* total_ms, long long* count);
 
@@ -280,7 +286,10 @@ int mk_correction_solve_vq(mk_ctx* ctx, const mk_mesh* mesh, const mk_molecule* 
  * sigma M) x on the free DOF (boundary rows of y written as 0), all ld columns, matrix-free element by element with
  * the patch scatter (owner-computes in shared memory, halo slots summed in patch order; bitwise reproducible).
  * precision MK_PREC_FP64: x, y are double [n_nodes*ld]; MK_PREC_MIXED: x, y are float [n_nodes*ld] (the FP32
- * operator of the mixed solve).  Element matrices are rebuilt on every call.  mol = NULL (with sigma = 0): the
+ * operator of the mixed solve); MK_PREC_PAIRS: x, y are double, the products formed on the FP32 units from FP32
+ * pairs (a value v as hi = fl32(v) plus lo = fl32(v - hi); exact products and two-sums; the error is a few units of
+ * 2^-48 relative to sum_j |a_ij x_j|, against 2^-53 for FP64), the element and node sums rounded to FP64 (the
+ * refinement residual of the mixed solves, MK_OPT_PAIR_RESIDUAL).  Element matrices are rebuilt on every call.  mol = NULL (with sigma = 0): the
  * stiffness operator K of the Hartree Poisson problem (Sec. 2, the Hartree equation) instead, in FP32 matrix-free
  * (per element |det J| J^-1 J^-T times the reference stiffness components), in FP64 from stored element matrices. */
 int mk_operator_apply(mk_ctx* ctx, const mk_mesh* mesh, const mk_molecule* mol, double sigma, int precision,

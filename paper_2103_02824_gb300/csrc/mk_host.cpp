@@ -664,6 +664,10 @@ int mk_ctx_set_option(mk_ctx* c, int option, int value) {
       MK_ARG(value >= 0, "mk_ctx_set_option: decomposition CTAs must be >= 0 (0 = one per SM)");
       c->decompose_ctas = value;
       return MK_OK;
+    case MK_OPT_PAIR_RESIDUAL:
+      MK_ARG(value == 0 || value == 1, "mk_ctx_set_option: pair residual must be 0 or 1");
+      c->pair_residual = value == 1;
+      return MK_OK;
     default: return fail(MK_ERR_INVALID_ARG, "mk_ctx_set_option: unknown option");
   }
 }

@@ -40,7 +40,7 @@ int check_fault(mk_ctx* c, cudaStream_t s);
     if (!(cond)) return ::mk::fail(MK_ERR_INVALID_ARG, std::string(msg));      \
   } while (0)
 
-constexpr int kProfKinds = 5;   // PROF_* kinds timed by mk_profile_*
+constexpr int kProfKinds = 6;   // PROF_* kinds timed by mk_profile_*
 constexpr int kCapPairs = 128;  // event pairs per kind available to one graph capture
 constexpr int kWaitLimitDefault = 1 << 20;  // the patch kernel's kWaitLimit
 constexpr int kQ = 27;          // quadrature points per element (3x3x3 conical product, exact to degree 5)
@@ -183,6 +183,7 @@ struct mk_ctx {
   int patch_kernel = 1;
   int wait_limit = mk::kWaitLimitDefault;  // MK_OPT_WAIT_LIMIT: polls of the patch kernel's bounded copy waits
   int decompose_ctas = 0;  // MK_OPT_DECOMPOSE_CTAS: CTAs of the block-Jacobi kernel (0 = one per SM)
+  bool pair_residual = true;  // MK_OPT_PAIR_RESIDUAL: the mixed solves' refinement residuals on FP32 pairs
   const int* last_decompose_info = nullptr;  // device {sweeps64, buffer, -, -, sweeps32} of the last decomposition
   // the inner PCG runs on this stream (graphs cannot be captured on the legacy default stream), ordered against
   // the caller's stream by two events
@@ -211,7 +212,7 @@ void prof_mark(mk_ctx* ctx, int kind, bool begin, cudaStream_t s);
 void prof_capture(mk_ctx* ctx, bool on);
 void prof_prepare_capture(mk_ctx* ctx);
 void prof_harvest(mk_ctx* ctx);
-enum ProfKind { PROF_APPLY64 = 0, PROF_APPLY32 = 1, PROF_HALO = 2, PROF_LEARNED = 3, PROF_STIFF = 4 };
+enum ProfKind { PROF_APPLY64 = 0, PROF_APPLY32 = 1, PROF_HALO = 2, PROF_LEARNED = 3, PROF_STIFF = 4, PROF_PAIRS = 5 };
 }  // namespace mk
 
 struct mk_mesh {
@@ -307,6 +308,8 @@ enum Slot : int {
   S_MG,                         // multigrid V-cycle: per-level right-hand sides, iterates, operator products
   S_AFEM,                       // error indicator: face values; Dorfler marking: reduction partials
   S_LMAX,                       // smoother weight estimate: the power iteration's two vectors (FP32)
+  S_PAIRA,                      // FP32-pair parts of the mixed solve's element matrices (hi, lo; patch order)
+  S_PAIRX,                      // FP32-pair parts of an FP64 operand (hi, lo)
   S_COUNT
 };
 void* scratch(mk_ctx* ctx, int slot, size_t bytes, int* err);

@@ -274,6 +274,124 @@ template int apply_patch<float>(mk_ctx*, const mk_mesh*, const float*, const flo
 template int apply_patch<double>(mk_ctx*, const mk_mesh*, const double*, const double*, double*, int, bool,
                                  cudaStream_t);
 
+// ------------------------------------------------------------------------------------------------ FP32-pair apply
+// The FP64-accurate operator on the FP32 units (patch_apply_pair): element matrices split into FP32 pairs once per
+// solve, x split before each application, node sums and halo in FP64.
+template <int NLOC, int VEC, int NCG>
+__global__ void __launch_bounds__(256) k_apply_pair(const int32_t* __restrict__ elem_off,
+                                                    const int32_t* __restrict__ node_off,
+                                                    const int32_t* __restrict__ conn, const float* __restrict__ Ah,
+                                                    const float* __restrict__ Al, const int32_t* __restrict__ target,
+                                                    const int32_t* __restrict__ inc_off,
+                                                    const uint16_t* __restrict__ inc, int mask,
+                                                    const float* __restrict__ xh, const float* __restrict__ xl,
+                                                    double* __restrict__ y, double* __restrict__ halo, int ncolg,
+                                                    int col0, int ld, int pe, int max_nodes) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  patch_apply_pair<NLOC, VEC, NCG>(blockIdx.x, elem_off, node_off, conn, Ah, Al, target, inc_off, inc, mask, xh, xl,
+                                   y, halo, ncolg, col0, ld, pe, max_nodes, smraw);
+}
+
+// v -> (hi, lo) = (fl32(v), fl32(v - hi)), for n values
+__global__ void k_split_pairs(int64_t n, const double* __restrict__ v, float* __restrict__ hi, float* __restrict__ lo) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const double a = v[t];
+  const float h = (float)a;
+  hi[t] = h;
+  lo[t] = (float)(a - (double)h);
+}
+
+// The pair parts of the FP64 element matrices in patch order with padded rows (as pack_elements).
+__global__ void k_pack_pairs(int64_t E, int np, int nps, const int32_t* __restrict__ elem_id,
+                             const double* __restrict__ A64, float* __restrict__ Ah, float* __restrict__ Al) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= E * nps) return;
+  const int64_t i = t / nps;
+  const int k = (int)(t - i * nps);
+  const double a = k < np ? A64[(int64_t)elem_id[i] * np + k] : 0.0;
+  const float h = (float)a;
+  Ah[t] = h;
+  Al[t] = (float)(a - (double)h);
+}
+
+int pack_pairs(mk_ctx* ctx, const mk_mesh* m, const double* A64, float* Ah, float* Al, cudaStream_t s) {
+  (void)ctx;
+  const Level& L = m->fine;
+  const int np = L.nloc * (L.nloc + 1) / 2;
+  const int nps = padded_np(L.nloc, 4);
+  const int64_t work = L.n_elems * nps;
+  MK_COUNT(), k_pack_pairs<<<(int)((work + 255) / 256), 256, 0, s>>>(L.n_elems, np, nps, m->patches.d_elem_id, A64,
+                                                                     Ah, Al);
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
+// y = A x (all ld columns, FP64 in and out) from the pair parts Ah, Al of the element matrices.
+int apply_pair(mk_ctx* ctx, const mk_mesh* m, const float* Ah, const float* Al, const double* x, double* y, int ld,
+               bool mask, cudaStream_t s) {
+  const Patches& P = m->patches;
+  const Level& L = m->fine;
+  const int64_t n = L.n_nodes;
+  int err = MK_OK;
+  double* halo = (double*)scratch(ctx, S_HALO64, (size_t)std::max<int64_t>(P.n_halo_slots, 1) * ld * sizeof(double), &err);
+  float* xh = (float*)scratch(ctx, S_PAIRX, (size_t)2 * n * ld * sizeof(float), &err);
+  if (!halo || !xh) return err;
+  float* xl = xh + (size_t)n * ld;
+  MK_COUNT(), k_split_pairs<<<(int)((n * ld + 255) / 256), 256, 0, s>>>(n * ld, x, xh, xl);
+  constexpr int VEC = 2;
+  const int vec = (ld % VEC == 0) ? VEC : 1;
+  const int nloc = L.nloc;
+  const int wmax = 4;
+  for (int col0 = 0; col0 < ld; col0 += wmax) {
+    const int W = std::min(wmax, ld - col0);
+    const int ncolg = W / vec;
+    const size_t smem = pair_smem(nloc, P.max_elems, P.max_nodes, W).total;
+    if (smem > 227 * 1024) return fail(MK_ERR_UNSUPPORTED, "pair operator: patch too large for shared memory");
+    const int th = std::min(256, (P.max_elems * ncolg + 31) / 32 * 32);
+    prof_mark(ctx, PROF_PAIRS, true, s);
+#define MK_PAIR_LAUNCH(NL, V, G)                                                                                   \
+  do {                                                                                                            \
+    auto kern = k_apply_pair<NL, V, G>;                                                                           \
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
+    MK_COUNT(), kern<<<P.n_patches, th, smem, s>>>(P.d_patch_elem_off, P.d_patch_node_off, P.d_conn, Ah, Al,      \
+                                                    P.d_node_target, P.d_inc_off, P.d_inc, mask, xh, xl, y, halo, \
+                                                    ncolg, col0, ld, P.max_elems, P.max_nodes);                  \
+  } while (0)
+#define MK_PAIR_DISPATCH(NL)                                  \
+  do {                                                        \
+    if (vec == VEC) {                                         \
+      if (ncolg == 1) MK_PAIR_LAUNCH(NL, VEC, 1);             \
+      else if (ncolg == 2) MK_PAIR_LAUNCH(NL, VEC, 2);        \
+      else MK_PAIR_LAUNCH(NL, VEC, 0);                        \
+    } else {                                                  \
+      if (ncolg == 1) MK_PAIR_LAUNCH(NL, 1, 1);               \
+      else MK_PAIR_LAUNCH(NL, 1, 0);                          \
+    }                                                         \
+  } while (0)
+    if (nloc == 4) MK_PAIR_DISPATCH(4);
+    else MK_PAIR_DISPATCH(10);
+#undef MK_PAIR_DISPATCH
+#undef MK_PAIR_LAUNCH
+    prof_mark(ctx, PROF_PAIRS, false, s);
+    MK_TRY(halo_pass<double>(ctx, m, halo, y, mask, ncolg, vec, col0, ld, s));
+  }
+  MK_CUDA(cudaGetLastError());
+  return MK_OK;
+}
+
+// y = A x on FP32 pairs from FP64 element matrices in their original order (packed on every call).
+int apply64_pairs(mk_ctx* ctx, const mk_mesh* m, const double* A64, const double* x, double* y, int ld, bool mask,
+                  cudaStream_t s) {
+  const Level& L = m->fine;
+  const size_t na = (size_t)L.n_elems * padded_np(L.nloc, 4);
+  int err = MK_OK;
+  float* Ah = (float*)scratch(ctx, S_PAIRA, 2 * na * sizeof(float), &err);
+  if (!Ah) return err;
+  MK_TRY(pack_pairs(ctx, m, A64, Ah, Ah + na, s));
+  return apply_pair(ctx, m, Ah, Ah + na, x, y, ld, mask, s);
+}
+
 // Element matrices of the patch operator from FP64 originals (patch order).
 template <typename T>
 int pack_elements(mk_ctx* ctx, const mk_mesh* m, const double* A64, T* A, cudaStream_t s) {
@@ -1472,10 +1590,20 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
   if (diag_pre) MK_CUDA(cudaMemcpyAsync(diag, diag_pre, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   else MK_TRY(assemble_diagonal(ctx, L, A64, diag, s));
   if (!stiff) MK_TRY(pack_elements<float>(ctx, m, A64, A32, s));
-  // the FP64 element matrices in patch order, packed once for every residual of this solve
-  double* A64p = (double*)scratch(ctx, S_ELEMP64, (size_t)L.n_elems * padded_np(L.nloc, 8) * sizeof(double), &err);
-  if (!A64p) return err;
-  MK_TRY(pack_elements<double>(ctx, m, A64, A64p, s));
+  // the element matrices for every refinement residual of this solve, packed once in patch order: as FP32 pairs
+  // (the products on the FP32 units, MK_OPT_PAIR_RESIDUAL) or in FP64
+  const bool pairs = ctx->pair_residual;
+  double* A64p = nullptr;
+  float* Aph = nullptr;
+  const size_t npa = (size_t)L.n_elems * padded_np(L.nloc, 4);
+  if (pairs) {
+    if (!(Aph = (float*)scratch(ctx, S_PAIRA, 2 * npa * sizeof(float), &err))) return err;
+    MK_TRY(pack_pairs(ctx, m, A64, Aph, Aph + npa, s));
+  } else {
+    A64p = (double*)scratch(ctx, S_ELEMP64, (size_t)L.n_elems * padded_np(L.nloc, 8) * sizeof(double), &err);
+    if (!A64p) return err;
+    MK_TRY(pack_elements<double>(ctx, m, A64, A64p, s));
+  }
   // the inner FP32 operator: the packed element matrices, or the matrix-free stiffness operator
   auto apply32 = [&](const float* xin, float* yout) -> int {
     return stiff ? apply_stiff(ctx, m, xin, yout, ld, true, s) : apply_patch<float>(ctx, m, A32, xin, yout, ld, true, s);
@@ -1537,7 +1665,8 @@ static int pcg_mixed_on(mk_ctx* ctx, const mk_mesh* m, const double* A64, const 
     MK_CUDA(cudaMemsetAsync(zb, 0, (size_t)n * ld * sizeof(float), s));  // columns >= N stay zero
   }
   for (;;) {
-    MK_TRY(apply_patch<double>(ctx, m, A64p, x, Ax, ld, true, s));  // FP64 residual of the current x
+    if (pairs) MK_TRY(apply_pair(ctx, m, Aph, Aph + npa, x, Ax, ld, true, s));  // residual of the current x
+    else MK_TRY(apply_patch<double>(ctx, m, A64p, x, Ax, ld, true, s));
     MK_COUNT(), k_mixed_residual<<<nblk, th, 0, s>>>(n, L.d_boundary, b, Ax, r, d, N, ld, part, fin(0, 2));
     MK_CUDA(cudaMemcpyAsync(hst, st, sizeof(MixState) * ld, cudaMemcpyDeviceToHost, s));
     MK_CUDA(cudaStreamSynchronize(s));
@@ -1666,7 +1795,8 @@ extern "C" int mk_operator_apply(mk_ctx* ctx, const mk_mesh* m, const mk_molecul
                                  const void* x, void* y, int ld, void* stream) {
   MK_ARG(ctx && m && x && y && ld >= 1 && ld <= 256, "mk_operator_apply: bad argument");
   MK_ARG(mol || sigma == 0.0, "mk_operator_apply: the stiffness operator (no molecule) takes sigma = 0");
-  MK_ARG(precision == MK_PREC_FP64 || precision == MK_PREC_MIXED, "mk_operator_apply: bad precision");
+  MK_ARG(precision == MK_PREC_FP64 || precision == MK_PREC_MIXED || precision == MK_PREC_PAIRS,
+         "mk_operator_apply: bad precision");
   MK_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
   const Level& L = m->fine;
@@ -1688,6 +1818,13 @@ extern "C" int mk_operator_apply(mk_ctx* ctx, const mk_mesh* m, const mk_molecul
     if (!A) return err;
     MK_TRY(pack_elements<double>(ctx, m, A64, A, s));
     return apply_patch<double>(ctx, m, A, (const double*)x, (double*)y, ld, true, s);
+  }
+  if (precision == MK_PREC_PAIRS) {
+    const size_t na = (size_t)L.n_elems * padded_np(L.nloc, 4);
+    float* Ah = (float*)scratch(ctx, S_OPB, 2 * na * sizeof(float), &err);
+    if (!Ah) return err;
+    MK_TRY(pack_pairs(ctx, m, A64, Ah, Ah + na, s));
+    return apply_pair(ctx, m, Ah, Ah + na, (const double*)x, (double*)y, ld, true, s);
   }
   float* A = (float*)scratch(ctx, S_OPB, (size_t)L.n_elems * padded_np(L.nloc, 4) * sizeof(float), &err);
   if (!A) return err;
@@ -1973,10 +2110,14 @@ extern "C" int mk_batch_correction_solve(mk_ctx* ctx, int K, const mk_mesh* cons
   cudaGraphExec_t exec = nullptr;
   long long graph_kernels = 0;
   for (int refine = 0;; ++refine) {
-    for (int k = 0; k < K; ++k) {  // FP64 residual of every problem
+    for (int k = 0; k < K; ++k) {  // FP64 residual of every problem (on FP32 pairs, as the single solves)
       const BatchProb& B = hp[k];
-      MK_TRY(apply64(ctx, meshes[k], (const double*)(ws + oA64[k]), x[k], (double*)(ws + oAx[k]), ld[k], ld[k], true,
-                     s));
+      if (ctx->pair_residual)
+        MK_TRY(apply64_pairs(ctx, meshes[k], (const double*)(ws + oA64[k]), x[k], (double*)(ws + oAx[k]), ld[k], true,
+                             s));
+      else
+        MK_TRY(apply64(ctx, meshes[k], (const double*)(ws + oA64[k]), x[k], (double*)(ws + oAx[k]), ld[k], ld[k],
+                       true, s));
       MK_COUNT(), k_mixed_residual<<<nblk, 256, 0, s>>>(B.n, B.bnd, rhs[k], (const double*)(ws + oAx[k]), B.r, B.d,
                                                          N[k], ld[k], B.part, FinArgs{});
       MK_COUNT(), k_mixed_finalize<<<1, kFinThreads, 0, s>>>(0, B.part, nblk, 2, ld[k], N[k], B.st, o.rtol, inner2);

@@ -198,6 +198,140 @@ __device__ __forceinline__ void patch_apply(int p, const int32_t* __restrict__ e
   }
 }
 
+// ------------------------------------------------------------------------------------------------ FP32-pair apply
+// y = A x to about 48 significant bits on the FP32 units: A and x split into pairs hi + lo of FP32 values
+// (hi = fl32(v), lo = fl32(v - hi)), each product hi_a hi_x formed exactly (the rounded product and its error by an
+// FMA), the cross terms hi_a lo_x + lo_a hi_x added to that error (lo_a lo_x, 2^-48 of the product, is dropped), and
+// the sum kept as hi + lo by an exact two-sum of the leading parts.  The element sums are then rounded to FP64 and
+// the node sums run in FP64 exactly as in patch_apply.  GB300 runs FP32 at 64 times its FP64 rate, so the dozen
+// FP32 operations per product take a fraction of the time of one FP64 multiply-add; the result differs from the FP64
+// operator by a few units of 2^-48 relative to sum |a_ij x_j|.  The _rn intrinsics keep the compiler from fusing
+// the steps of the error-free transformations.
+__device__ __forceinline__ void pair_madd(float& hi, float& lo, float wh, float wl, float xh, float xl) {
+  const float p = __fmul_rn(wh, xh);
+  float e = __fmaf_rn(wh, xh, -p);  // wh xh = p + e exactly
+  e = __fmaf_rn(wh, xl, e);
+  e = __fmaf_rn(wl, xh, e);
+  const float s = __fadd_rn(hi, p);
+  const float bb = __fsub_rn(s, hi);
+  const float t = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));  // hi + p = s + t exactly
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(t, e));
+}
+
+// Shared-memory layout of one FP32-pair patch CTA: FP64 products [NLOC][pe][W], hi and lo element matrices (FP32,
+// padded rows), connectivity, incidences, node runs and targets.
+struct PairSmem {
+  size_t ye, ah, al, conn, inc, ioff, tgt, total;
+};
+__host__ __device__ inline PairSmem pair_smem(int nloc, int pe, int max_nodes, int W) {
+  PairSmem L;
+  const size_t am = (size_t)pe * padded_np(nloc, 4) * 4 + 16;
+  L.ye = 0;
+  L.ah = L.ye + align16((size_t)nloc * pe * W * 8);
+  L.al = L.ah + align16(am);
+  L.conn = L.al + align16(am);
+  L.inc = L.conn + align16((size_t)pe * nloc * 4 + 16);
+  L.ioff = L.inc + align16((size_t)pe * nloc * 2 + 16);
+  L.tgt = L.ioff + align16((size_t)(max_nodes + 1) * 4 + 16);
+  L.total = L.tgt + align16((size_t)max_nodes * 4 + 16);
+  return L;
+}
+
+// One patch per CTA, as patch_apply: Ah, Al the pair parts of the element matrices (patch order, padded rows),
+// xh, xl the pair parts of x [n_nodes * ld]; y and the halo slots in FP64.
+template <int NLOC, int VEC, int NCG = 0>
+__device__ __forceinline__ void patch_apply_pair(int p, const int32_t* __restrict__ elem_off,
+                                                 const int32_t* __restrict__ node_off,
+                                                 const int32_t* __restrict__ conn, const float* __restrict__ Ah,
+                                                 const float* __restrict__ Al, const int32_t* __restrict__ target,
+                                                 const int32_t* __restrict__ inc_off,
+                                                 const uint16_t* __restrict__ inc, int mask,
+                                                 const float* __restrict__ xh, const float* __restrict__ xl,
+                                                 double* __restrict__ y, double* __restrict__ halo, int ncolg,
+                                                 int col0, int ld, int pe, int max_nodes, unsigned char* smraw) {
+  constexpr int NPS = padded_np(NLOC, 4);
+  const int ncg = NCG > 0 ? NCG : ncolg;
+  const int W = ncg * VEC;
+  const PairSmem lay = pair_smem(NLOC, pe, max_nodes, W);
+  double* Ye = reinterpret_cast<double*>(smraw + lay.ye);  // [NLOC][pe][W]
+  const int e0 = elem_off[p], ne = elem_off[p + 1] - e0;
+  const int n0 = node_off[p], nl = node_off[p + 1] - n0;
+  const int ibase = e0 * NLOC;
+  const float* Ahs = stage_async(smraw + lay.ah, Ah + (int64_t)e0 * NPS, ne * NPS * 4);
+  const float* Als = stage_async(smraw + lay.al, Al + (int64_t)e0 * NPS, ne * NPS * 4);
+  const int32_t* cs = stage_async(smraw + lay.conn, conn + ibase, ne * NLOC * 4);
+  const uint16_t* is = stage_async(smraw + lay.inc, inc + ibase, ne * NLOC * 2);
+  const int32_t* os = stage_async(smraw + lay.ioff, inc_off + n0, (nl + 1) * 4);
+  const int32_t* ts = stage_async(smraw + lay.tgt, target + n0, nl * 4);
+  cp_async_wait_all();
+  __syncthreads();
+  for (int it = threadIdx.x; it < ne * ncg; it += blockDim.x) {
+    const int el = it / ncg, g = it - el * ncg;
+    Vec<float, VEC> xvh[NLOC], xvl[NLOC];
+#pragma unroll
+    for (int a = 0; a < NLOC; ++a) {
+      const int64_t o = (int64_t)cs[el * NLOC + a] * ld + col0 + g * VEC;
+      xvh[a] = ldv<float, VEC>(xh + o);
+      xvl[a] = ldv<float, VEC>(xl + o);
+    }
+    const float* AH = Ahs + el * NPS;
+    const float* AL = Als + el * NPS;
+    float hi[NLOC][VEC], lo[NLOC][VEC];
+#pragma unroll
+    for (int a = 0; a < NLOC; ++a)
+#pragma unroll
+      for (int c = 0; c < VEC; ++c) hi[a][c] = lo[a][c] = 0.0f;
+#pragma unroll
+    for (int a = 0; a < NLOC; ++a)
+#pragma unroll
+      for (int b = a; b < NLOC; ++b) {
+        const float wh = AH[sym_index(a, b, NLOC)], wl = AL[sym_index(a, b, NLOC)];
+#pragma unroll
+        for (int c = 0; c < VEC; ++c) {
+          pair_madd(hi[a][c], lo[a][c], wh, wl, xvh[b].v[c], xvl[b].v[c]);
+          if (b != a) pair_madd(hi[b][c], lo[b][c], wh, wl, xvh[a].v[c], xvl[a].v[c]);
+        }
+      }
+#pragma unroll
+    for (int a = 0; a < NLOC; ++a) {
+      Vec<double, VEC> o;
+#pragma unroll
+      for (int c = 0; c < VEC; ++c) o.v[c] = (double)hi[a][c] + (double)lo[a][c];
+      stv<double, VEC>(Ye + ((size_t)a * pe + el) * W + g * VEC, o);
+    }
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < nl * ncg; it += blockDim.x) {  // the node sums of patch_apply, in FP64
+    const int l = it / ncg, g = it - l * ncg;
+    const int b = os[l] - ibase, e = os[l + 1] - ibase;
+    Vec<double, VEC> acc;
+#pragma unroll
+    for (int c = 0; c < VEC; ++c) acc.v[c] = 0;
+    auto ye = [&](int k) { return ldv<double, VEC>(Ye + (size_t)is[k] * W + g * VEC); };
+    int k = b;
+    for (; k + 4 <= e; k += 4) {
+      const Vec<double, VEC> v0 = ye(k), v1 = ye(k + 1), v2 = ye(k + 2), v3 = ye(k + 3);
+#pragma unroll
+      for (int c = 0; c < VEC; ++c) acc.v[c] = (((acc.v[c] + v0.v[c]) + v1.v[c]) + v2.v[c]) + v3.v[c];
+    }
+    for (; k < e; ++k) {
+      const Vec<double, VEC> v = ye(k);
+#pragma unroll
+      for (int c = 0; c < VEC; ++c) acc.v[c] += v.v[c];
+    }
+    const int t = ts[l];
+    if (t >= 0) {
+      if (mask && (t & kOwnedBoundary))
+#pragma unroll
+        for (int c = 0; c < VEC; ++c) acc.v[c] = 0;
+      stv<double, VEC>(y + (int64_t)(t & (kOwnedBoundary - 1)) * ld + col0 + g * VEC, acc);
+    } else {
+      stv<double, VEC>(halo + (int64_t)(-t - 1) * ld + col0 + g * VEC, acc);
+    }
+  }
+}
+
 // ------------------------------------------------------------------------------------------------ pipelined apply
 // ------------------------------------------------------------------------------------------------ bulk copies
 // mbarrier and bulk (TMA, non-tensor) copy primitives.  Every wait is bounded: a limit of polls of

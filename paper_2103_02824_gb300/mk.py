@@ -27,7 +27,7 @@ MK_MAX_RHS = 64
 MK_FAULT_PATCH_WAIT, MK_FAULT_PATCH_RECORD, MK_FAULT_TC_WAIT = 1, 2, 4
 
 MK_XC = {"none": 0, "slater": 1, "xalpha": 2, "lda": 3}
-MK_PREC_FP64, MK_PREC_MIXED = 0, 1
+MK_PREC_FP64, MK_PREC_MIXED, MK_PREC_PAIRS = 0, 1, 2
 MK_PRECOND = {"jacobi": 0, "chebyshev": 1, "learned": 2}
 MK_BC = {"zero": 0, "multipole": 1}
 
@@ -186,8 +186,8 @@ def ctx_fault(ctx) -> int:
     return int(f.value)
 
 
-PROF_APPLY64, PROF_APPLY32, PROF_HALO, PROF_LEARNED, PROF_STIFF = 0, 1, 2, 3, 4
-MK_OPT_GRAPHS, MK_OPT_PATCH_PIPELINE, MK_OPT_WAIT_LIMIT, MK_OPT_DECOMPOSE_CTAS = 1, 2, 3, 4
+PROF_APPLY64, PROF_APPLY32, PROF_HALO, PROF_LEARNED, PROF_STIFF, PROF_PAIRS = 0, 1, 2, 3, 4, 5
+MK_OPT_GRAPHS, MK_OPT_PATCH_PIPELINE, MK_OPT_WAIT_LIMIT, MK_OPT_DECOMPOSE_CTAS, MK_OPT_PAIR_RESIDUAL = 1, 2, 3, 4, 5
 
 
 def ctx_set_option(ctx, option, value):
@@ -621,11 +621,11 @@ def mk_small_eigensolve(ctx, NH, N, AH, MH, b, c, beta, gamma, lam, coef, status
                                      _ptr(lam), _ptr(coef), _ptr(status), _stream(stream)))
 
 
-def mk_operator_apply(ctx, mesh, mol: Molecule, sigma, x, y, stream=None):
+def mk_operator_apply(ctx, mesh, mol: Molecule, sigma, x, y, stream=None, pairs=False):
     """y = (K/2 + M_Vext + sigma M) x, or y = K x (the Poisson operator) with mol None and sigma 0; float32 tensors
-    select the FP32 operator, float64 the FP64 one."""
+    select the FP32 operator, float64 the FP64 one (pairs=True: FP64 operands, products on FP32 pairs)."""
     import torch
-    prec = MK_PREC_MIXED if x.dtype == torch.float32 else MK_PREC_FP64
+    prec = MK_PREC_MIXED if x.dtype == torch.float32 else (MK_PREC_PAIRS if pairs else MK_PREC_FP64)
     assert y.dtype == x.dtype
     ld = x.shape[1] if x.dim() == 2 else 1
     _check(lib().mk_operator_apply(ctx.h, mesh.h, None if mol is None else C.byref(mol.c), float(sigma), prec,

@@ -190,6 +190,51 @@ def test_operator_apply_patch(ctx, torch, name):
 
 
 @pytest.mark.parametrize("name", CASES)
+def test_operator_apply_pairs(ctx, torch, name):
+    """The FP64-accurate operator on FP32 pairs (MK_PREC_PAIRS) against the oracle's assembled operator, entry by
+    entry within 2^-42 (|A| |x|)_i (a few units of 2^-48 per product, with room for the FP64 sums; plain FP32
+    products miss this by 2^18), for even, odd and single columns; and the mixed solve to 1e-12 with its refinement
+    residuals on pairs (the default) and in FP64."""
+    from paper_2103_02824_gb300 import mk
+    c = case(name)
+    lv = c["level"]
+    m = gpu_mesh(ctx, name)
+    mol = mk.Molecule(c["wl"]["Z"], c["wl"]["R"])
+    n = m.info["n_nodes"]
+    A = lv.operator(c["sigma"])
+    absA = abs(A)
+    for ld in (8, 3, 1):
+        X = np.random.default_rng(12 + ld).standard_normal((n, ld))
+        X[lv.fine.boundary] = 0.0
+        ref = np.zeros((n, ld))
+        ref[lv.fine.free] = A @ X[lv.fine.free]
+        bound = np.zeros((n, ld))
+        bound[lv.fine.free] = absA @ np.abs(X[lv.fine.free])
+        x = torch.from_numpy(X).cuda()
+        y = torch.full_like(x, 7.0)
+        mk.mk_operator_apply(ctx, m, mol, c["sigma"], x, y, pairs=True)
+        torch.cuda.synchronize()
+        got = y.cpu().numpy()
+        assert np.all(np.abs(got - ref) <= 2.0 ** -42 * bound + 1e-300), (ld, np.max(np.abs(got - ref) / (bound + 1e-300)))
+        assert np.all(got[lv.fine.boundary] == 0)
+    N, ld = c["N"], 8
+    reps = {}
+    try:
+        for on in (1, 0):
+            mk.ctx_set_option(ctx, mk.MK_OPT_PAIR_RESIDUAL, on)
+            rhs = dev(torch, padded(c["out"]["rhs"], ld))
+            x = dev(torch, padded(c["out"]["u"], ld))
+            rep = mk.mk_correction_solve(ctx, m, mol, c["sigma"], rhs, x, N,
+                                         opt=mk.opts(precision="mixed", rtol=1e-12, inner_rtol=1e-4, check_every=5))
+            assert rep["max_rel_residual"] <= 1e-12
+            assert maxrel(x.cpu().numpy()[:, :N], c["out"]["psihat"]) < 1e-8
+            reps[on] = rep["iterations"]
+    finally:
+        mk.ctx_set_option(ctx, mk.MK_OPT_PAIR_RESIDUAL, 1)
+    print(f"\n{name}: mixed solve iterations, pair residual {reps[1]}, FP64 residual {reps[0]}")
+
+
+@pytest.mark.parametrize("name", CASES)
 def test_correction_solve_mixed(ctx, torch, name):
     """FP32 inner PCG + FP64 refinement reaches the FP64 residual target and the oracle's solution."""
     from paper_2103_02824_gb300 import mk
