@@ -41,3 +41,24 @@ def test_no_device_fails_loudly(libpath):
     with pytest.raises(mk.MkError) as e:
         mk.Context(0)
     assert e.value.code == mk.MK_ERR_CUDA
+
+
+def test_binding_constants_match_header():
+    """Every integer constant the header defines (#define or enum) that the binding also names has the same value
+    there (the profiling kinds are PROF_* in the binding, MK_PROF_* in the header)."""
+    import os
+    import re
+    text = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "mk.h")).read()
+    consts = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(MK_\w+)\s+(-?\d+)\s*$", text, re.M)}
+    for body in re.findall(r"enum\s*\{([^}]*)\}", text):
+        for m in re.finditer(r"(MK_\w+)\s*=\s*(-?\d+)", body):
+            consts[m.group(1)] = int(m.group(2))
+    checked = 0
+    for name, value in consts.items():
+        alias = name[3:] if name.startswith("MK_PROF_") else name
+        if hasattr(mk, alias):
+            assert getattr(mk, alias) == value, (name, getattr(mk, alias), value)
+            checked += 1
+    for needed in ("MK_OPT_DECOMPOSE_CTAS", "MK_OPT_PAIR_RESIDUAL", "MK_PREC_PAIRS", "MK_PROF_PAIRS"):
+        assert needed in consts, needed
+    assert checked >= 15, checked
