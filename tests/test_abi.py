@@ -59,6 +59,14 @@ def test_binding_constants_match_header():
         if hasattr(mk, alias):
             assert getattr(mk, alias) == value, (name, getattr(mk, alias), value)
             checked += 1
+    # the binding's string maps
+    for table, prefix, names in ((mk.MK_XC, "MK_XC_", {"none": "NONE", "slater": "SLATER", "xalpha": "XALPHA",
+                                                       "lda": "LDA_PZ"}),
+                                 (mk.MK_PRECOND, "MK_PRECOND_", {k: k.upper() for k in mk.MK_PRECOND}),
+                                 (mk.MK_BC, "MK_BC_", {k: k.upper() for k in mk.MK_BC})):
+        for key, value in table.items():
+            assert consts[prefix + names[key]] == value, (prefix, key)
+            checked += 1
     for needed in ("MK_OPT_DECOMPOSE_CTAS", "MK_OPT_PAIR_RESIDUAL", "MK_PREC_PAIRS", "MK_PROF_PAIRS"):
         assert needed in consts, needed
-    assert checked >= 15, checked
+    assert checked >= 25, checked
